@@ -1,0 +1,236 @@
+"""FP64 CPU oracle for the forest-of-octrees raycaster (ctypes wrapper).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import this package.  It shares no
+code with the CUDA library in ``paper_1809_01334_gb300/csrc``; the two meet
+only in the seeded inputs of ``paper_1809_01334_gb300.inputs``, which hold no
+raycasting arithmetic.
+
+The C source (``ocr_oracle.c``) states, function by function, which equation
+or algorithm of the paper it writes out.  Every function is pinned by
+``tests/test_oracle_pins.py`` to closed forms, invariants or brute force.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_build", "libocr_oracle.so")
+_lib = None
+
+RK4, DOPRI5 = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C99 + OpenMP)."""
+    src = os.path.join(_HERE, "ocr_oracle.c")
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
+            os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "ocr_oracle.h"))):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-D_DEFAULT_SOURCE", "-fopenmp", "-fPIC",
+                               "-shared", "-o", tmp, src, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class Forest_(C.Structure):
+    _fields_ = [("nleaves", C.c_int), ("max_level", C.c_int),
+                ("anchor", C.POINTER(C.c_int32)), ("level", C.POINTER(C.c_uint8)),
+                ("nodal", C.POINTER(C.c_float)), ("tf", C.POINTER(C.c_float)),
+                ("s_min", C.c_double), ("s_max", C.c_double)]
+
+
+class Camera_(C.Structure):
+    _fields_ = [("o", C.c_double * 3), ("v", C.c_double * 3), ("t", C.c_double * 3),
+                ("u", C.c_double * 3), ("ell", C.c_double), ("near_", C.c_double),
+                ("far_", C.c_double), ("w", C.c_int), ("h", C.c_int), ("ortho", C.c_int)]
+
+
+class Integrator_(C.Structure):
+    _fields_ = [("method", C.c_int), ("nsteps", C.c_int), ("tol", C.c_double),
+                ("c_rk", C.c_double), ("max_depth", C.c_int), ("bg", C.c_double * 3)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        P = C.POINTER
+        d = P(C.c_double)
+        _lib.orc_combine.argtypes = [d, d, d]
+        _lib.orc_inverse.argtypes = [d, d]
+        _lib.orc_cut.argtypes = [d, C.c_double, d]
+        _lib.orc_average.argtypes = [d, d, d]
+        _lib.orc_tf_eval.argtypes = [P(Forest_), C.c_double, d]
+        _lib.orc_trilinear.argtypes = [P(C.c_float), C.c_double, C.c_double, C.c_double]
+        _lib.orc_trilinear.restype = C.c_double
+        _lib.orc_pixel_ray.argtypes = [P(Camera_), C.c_int, C.c_int, d, d, d, d]
+        _lib.orc_leaf_rect.argtypes = [P(Forest_), P(Camera_), C.c_int, P(C.c_int32), d,
+                                       C.c_double, P(C.c_int)]
+        _lib.orc_leaf_rect.restype = C.c_int
+        _lib.orc_ray_leaf.argtypes = [P(Forest_), C.c_int, d, d, C.c_double, C.c_double, d, d]
+        _lib.orc_ray_leaf.restype = C.c_int
+        _lib.orc_segment_ab.argtypes = [P(Forest_), P(Integrator_), C.c_int, d, d, C.c_double,
+                                        C.c_double, d, P(C.c_int64)]
+        _lib.orc_cull.argtypes = [P(Forest_), P(Camera_), P(C.c_int32), P(C.c_uint8),
+                                  P(C.c_uint8), C.c_double]
+        _lib.orc_render.argtypes = [P(Forest_), P(Camera_), P(Integrator_), P(C.c_int), C.c_int,
+                                    d, P(C.c_int32), P(C.c_uint8), C.c_double, C.c_double,
+                                    C.c_int, P(C.c_int64)]
+        _lib.orc_render.restype = C.c_int64
+    return _lib
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+class OracleForest:
+    """Keeps the numpy arrays alive while the C struct points into them."""
+
+    def __init__(self, forest, tf):
+        if forest.geometry != "cube":
+            raise ValueError("oracle forest: only the unit-cube geometry is implemented")
+        self.anchor = np.ascontiguousarray(forest.anchor, dtype=np.int32)
+        self.level = np.ascontiguousarray(forest.level, dtype=np.uint8)
+        self.nodal = np.ascontiguousarray(forest.nodal, dtype=np.float32)
+        self.tf = np.ascontiguousarray(tf.knots, dtype=np.float32).reshape(-1)
+        self.s = Forest_(forest.nleaves, forest.max_level, _ptr(self.anchor, C.c_int32),
+                         _ptr(self.level, C.c_uint8), _ptr(self.nodal, C.c_float),
+                         _ptr(self.tf, C.c_float), float(tf.s_min), float(tf.s_max))
+
+
+def camera_struct(cam) -> Camera_:
+    c = Camera_()
+    c.o[:] = cam.o
+    c.v[:] = cam.v
+    c.t[:] = cam.t
+    c.u[:] = cam.u
+    c.ell, c.near_, c.far_ = cam.ell, cam.near, cam.far
+    c.w, c.h, c.ortho = cam.w, cam.h, int(cam.ortho)
+    return c
+
+
+def integrator_struct(integ: dict, bg=(0.0, 0.0, 0.0)) -> Integrator_:
+    s = Integrator_()
+    if integ["method"] == "rk4":
+        s.method, s.nsteps = RK4, int(integ.get("nsteps", 4))
+    elif integ["method"] == "dopri5":
+        s.method, s.nsteps = DOPRI5, 0
+        s.tol = float(integ.get("tol", 1e-6))
+        s.c_rk = float(integ.get("c_rk", 0.5))
+        s.max_depth = int(integ.get("max_depth", 16))
+    else:
+        raise ValueError(integ["method"])
+    s.bg[:] = bg
+    return s
+
+
+# -------------------------------------------------------------- primitives --
+def combine(near, far):
+    out = np.zeros(4)
+    lib().orc_combine(_ptr(np.ascontiguousarray(near, float), C.c_double),
+                      _ptr(np.ascontiguousarray(far, float), C.c_double), _ptr(out, C.c_double))
+    return out
+
+
+def inverse(s):
+    out = np.zeros(4)
+    lib().orc_inverse(_ptr(np.ascontiguousarray(s, float), C.c_double), _ptr(out, C.c_double))
+    return out
+
+
+def cut(s, frac):
+    out = np.zeros(4)
+    lib().orc_cut(_ptr(np.ascontiguousarray(s, float), C.c_double), float(frac),
+                  _ptr(out, C.c_double))
+    return out
+
+
+def average(s1, s2):
+    out = np.zeros(4)
+    lib().orc_average(_ptr(np.ascontiguousarray(s1, float), C.c_double),
+                      _ptr(np.ascontiguousarray(s2, float), C.c_double), _ptr(out, C.c_double))
+    return out
+
+
+def tf_eval(of: OracleForest, s: float):
+    out = np.zeros(4)
+    lib().orc_tf_eval(C.byref(of.s), float(s), _ptr(out, C.c_double))
+    return out
+
+
+def trilinear(nodal8, u, v, w):
+    a = np.ascontiguousarray(nodal8, dtype=np.float32)
+    return lib().orc_trilinear(_ptr(a, C.c_float), float(u), float(v), float(w))
+
+
+def pixel_ray(cam, i, j):
+    org, d, lims = np.zeros(3), np.zeros(3), np.zeros(2)
+    cs = camera_struct(cam)
+    lib().orc_pixel_ray(C.byref(cs), i, j, _ptr(org, C.c_double), _ptr(d, C.c_double),
+                        _ptr(lims[0:1], C.c_double), _ptr(lims[1:2], C.c_double))
+    return org, d, float(lims[0]), float(lims[1])
+
+
+def ray_leaf(of: OracleForest, leaf, org, d, amin, amax):
+    a = np.zeros(2)
+    hit = lib().orc_ray_leaf(C.byref(of.s), int(leaf), _ptr(np.asarray(org, float), C.c_double),
+                             _ptr(np.asarray(d, float), C.c_double), float(amin), float(amax),
+                             _ptr(a[0:1], C.c_double), _ptr(a[1:2], C.c_double))
+    return bool(hit), float(a[0]), float(a[1])
+
+
+def segment_ab(of: OracleForest, integ: dict, leaf, org, d, a_in, a_out):
+    out = np.zeros(4)
+    st = C.c_int64(0)
+    ist = integrator_struct(integ)
+    lib().orc_segment_ab(C.byref(of.s), C.byref(ist), int(leaf),
+                         _ptr(np.ascontiguousarray(org, float), C.c_double),
+                         _ptr(np.ascontiguousarray(d, float), C.c_double), float(a_in),
+                         float(a_out), _ptr(out, C.c_double), C.byref(st))
+    return out, int(st.value)
+
+
+def cull(forest, tf, cam, band_px: float = 4e-3):
+    """Visible flag, pixel rectangle {i0,i1,j0,j1} and tie flag of every leaf."""
+    of = OracleForest(forest, tf)
+    cs = camera_struct(cam)
+    n = forest.nleaves
+    rect = np.zeros((n, 4), dtype=np.int32)
+    vis = np.zeros(n, dtype=np.uint8)
+    unc = np.zeros(n, dtype=np.uint8)
+    lib().orc_cull(C.byref(of.s), C.byref(cs), _ptr(rect, C.c_int32), _ptr(vis, C.c_uint8),
+                   _ptr(unc, C.c_uint8), float(band_px))
+    return {"rect": rect, "visible": vis.astype(bool), "uncertain": unc.astype(bool)}
+
+
+def render(forest, tf, cam, integ: dict, rows=None, bg=(0.0, 0.0, 0.0), nthreads: int = 0,
+           band_px: float = 4e-3, band_rel: float = 1e-5):
+    """Render the listed rows (default: all).  Returns rgba [nrows, w, 4] (FP64),
+    per-ray segment counts, per-ray tie flags, total segments and RK steps."""
+    of = OracleForest(forest, tf)
+    cs = camera_struct(cam)
+    ist = integrator_struct(integ, bg)
+    if rows is None:
+        rows_arr = np.arange(cam.h, dtype=np.int32)
+    else:
+        rows_arr = np.ascontiguousarray(rows, dtype=np.int32)
+    nr = int(rows_arr.shape[0])
+    rgba = np.zeros((nr, cam.w, 4), dtype=np.float64)
+    counts = np.zeros((nr, cam.w), dtype=np.int32)
+    unc = np.zeros((nr, cam.w), dtype=np.uint8)
+    steps = C.c_int64(0)
+    total = lib().orc_render(C.byref(of.s), C.byref(cs), C.byref(ist), _ptr(rows_arr, C.c_int),
+                             nr, _ptr(rgba, C.c_double), _ptr(counts, C.c_int32),
+                             _ptr(unc, C.c_uint8), float(band_px), float(band_rel),
+                             int(nthreads), C.byref(steps))
+    if total < 0:
+        raise MemoryError("oracle render: allocation failed")
+    return {"rgba": rgba, "counts": counts, "uncertain": unc.astype(bool),
+            "segments": int(total), "steps": int(steps.value), "rows": rows_arr}

@@ -1,0 +1,565 @@
+/* FP64 CPU oracle for the forest-of-octrees raycaster.
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the CPU
+ * baseline leg of the benchmark, never by the product path.  It shares no
+ * code with the CUDA library.  Parity of every function here is pinned by the
+ * CPU test suite against closed forms, invariants and brute force (see
+ * tests/test_oracle_pins.py); no function is "parity unpinned".
+ *
+ * Equation numbers follow the paper's sections (Sec. 2.x, Eq. 2.y).
+ */
+#include "ocr_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Segment algebra, Sec. 2.4-2.5.  A segment is (A, B_r, B_g, B_b).           */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. 2.14: (A2, B2) (+) (A1, B1) = (A2 A1, B2 + A2 B1), 2 = nearer. */
+void orc_combine(const double *n, const double *f, double *out) {
+  double r[4];
+  r[0] = n[0] * f[0];
+  for (int c = 1; c < 4; ++c) r[c] = n[c] + n[0] * f[c];
+  memcpy(out, r, sizeof r);
+}
+
+/* Eq. 2.15: inverse (1/A, -B/A). */
+void orc_inverse(const double *s, double *out) {
+  double r[4];
+  r[0] = 1.0 / s[0];
+  for (int c = 1; c < 4; ++c) r[c] = -s[c] / s[0];
+  memcpy(out, r, sizeof r);
+}
+
+/* Eq. 2.17: the piece of relative length frac: A_i = A^frac,
+ * B_i = B (1 - A_i) / (1 - A); for A = 1, B_i = B frac.  1 - A^f is formed
+ * as -expm1(f ln A) so that A -> 1 loses no digits. */
+void orc_cut(const double *s, double frac, double *out) {
+  double r[4];
+  double la = log(s[0]);
+  r[0] = exp(frac * la);
+  double ratio = (la == 0.0) ? frac : expm1(frac * la) / expm1(la);
+  for (int c = 1; c < 4; ++c) r[c] = s[c] * ratio;
+  memcpy(out, r, sizeof r);
+}
+
+/* Eq. 2.18: geometric mean of A, arithmetic mean of B. */
+void orc_average(const double *s1, const double *s2, double *out) {
+  double r[4];
+  r[0] = sqrt(s1[0] * s2[0]);
+  for (int c = 1; c < 4; ++c) r[c] = 0.5 * (s1[c] + s2[c]);
+  memcpy(out, r, sizeof r);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Field and transfer function                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Piecewise-linear interpolation between 8 knots spaced uniformly over
+ * [s_min, s_max], constant outside. */
+void orc_tf_eval(const orc_forest *F, double s, double *kq) {
+  double z = (s - F->s_min) / (F->s_max - F->s_min) * 7.0;
+  if (z < 0.0) z = 0.0;
+  if (z > 7.0) z = 7.0;
+  int k = (int)floor(z);
+  if (k > 6) k = 6;
+  double w = z - k;
+  for (int c = 0; c < 4; ++c)
+    kq[c] = (1.0 - w) * (double)F->tf[4 * k + c] + w * (double)F->tf[4 * (k + 1) + c];
+}
+
+/* Trilinear Lagrange interpolation of the 8 corner values. */
+double orc_trilinear(const float *nd, double u, double v, double w) {
+  double s = 0.0;
+  for (int c = 0; c < 8; ++c) {
+    double wx = (c & 1) ? u : 1.0 - u;
+    double wy = (c & 2) ? v : 1.0 - v;
+    double wz = (c & 4) ? w : 1.0 - w;
+    s += (double)nd[c] * wx * wy * wz;
+  }
+  return s;
+}
+
+static void leaf_box(const orc_forest *F, int leaf, double *lo, double *h) {
+  double scale = ldexp(1.0, -F->max_level);
+  *h = ldexp(1.0, -(int)F->level[leaf]);
+  for (int a = 0; a < 3; ++a) lo[a] = F->anchor[3 * leaf + a] * scale;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Camera, Sec. 2.2                                                          */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. 2.2: r = v + ell ((i - (w-1)/2) t + (j - (h-1)/2) u), rays o + alpha r,
+ * alpha in [1, f/n] (the near plane is the projection plane).  The
+ * orthographic variant moves the origin by the same offset and uses the
+ * direction v/n, alpha >= 0. */
+void orc_pixel_ray(const orc_camera *C, int i, int j, double *org, double *dir, double *amin,
+                   double *amax) {
+  double di = i - 0.5 * (C->w - 1), dj = j - 0.5 * (C->h - 1);
+  if (C->ortho) {
+    for (int a = 0; a < 3; ++a) {
+      org[a] = C->o[a] + C->ell * (di * C->t[a] + dj * C->u[a]);
+      dir[a] = C->v[a] / C->near_;
+    }
+    *amin = 0.0;
+    *amax = C->far_;
+  } else {
+    for (int a = 0; a < 3; ++a) {
+      org[a] = C->o[a];
+      dir[a] = C->v[a] + C->ell * (di * C->t[a] + dj * C->u[a]);
+    }
+    *amin = 1.0;
+    *amax = C->far_ / C->near_;
+  }
+}
+
+/* Eq. 2.3: X = (t, u, v/n)^T (x - o). */
+static void camera_transform(const orc_camera *C, const double *x, double *X) {
+  double d[3] = {x[0] - C->o[0], x[1] - C->o[1], x[2] - C->o[2]};
+  X[0] = C->t[0] * d[0] + C->t[1] * d[1] + C->t[2] * d[2];
+  X[1] = C->u[0] * d[0] + C->u[1] * d[1] + C->u[2] * d[2];
+  X[2] = (C->v[0] * d[0] + C->v[1] * d[1] + C->v[2] * d[2]) / C->near_;
+}
+
+static int axis_visible(double pmin, double pmax, int lim) {
+  double lo = ceil(pmin), hi = floor(pmax);
+  if (lo < 0.0) lo = 0.0;
+  if (hi > lim) hi = lim;
+  return lo <= hi;
+}
+
+/* Sec. 2.2 / App. A.2: the camera-space AABB is the min/max of the 8
+ * transformed corners; it is clipped to the visible depth range and the
+ * corners of the clipped brick are projected into the image plane; the
+ * rectangle holds the pixel centres inside that projection.  pext receives
+ * the projected extents {i_min, i_max, j_min, j_max} in pixel units (may be
+ * NULL).  *vis_unc is set when moving any threshold by band_px pixels (or the
+ * depth clip by band_px relative) would change the visibility decision. */
+int orc_leaf_rect(const orc_forest *F, const orc_camera *C, int leaf, int32_t *rect,
+                  double *pext, double band_px, int *vis_unc) {
+  double lo[3], h;
+  leaf_box(F, leaf, lo, &h);
+  double bmin[3] = {INFINITY, INFINITY, INFINITY}, bmax[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int c = 0; c < 8; ++c) {
+    double x[3] = {lo[0] + ((c & 1) ? h : 0.0), lo[1] + ((c & 2) ? h : 0.0),
+                   lo[2] + ((c & 4) ? h : 0.0)};
+    double X[3];
+    camera_transform(C, x, X);
+    for (int a = 0; a < 3; ++a) {
+      if (X[a] < bmin[a]) bmin[a] = X[a];
+      if (X[a] > bmax[a]) bmax[a] = X[a];
+    }
+  }
+  double zlo_lim = C->ortho ? 0.0 : C->near_;
+  double zlo = bmin[2] > zlo_lim ? bmin[2] : zlo_lim;
+  double zhi = bmax[2] < C->far_ ? bmax[2] : C->far_;
+  int unc = 0;
+  rect[0] = 0; rect[1] = -1; rect[2] = 0; rect[3] = -1;
+  if (pext) { pext[0] = pext[2] = INFINITY; pext[1] = pext[3] = -INFINITY; }
+  if (fabs(zhi - zlo) <= band_px * 1e-3 * (fabs(zhi) + fabs(zlo))) unc = 1;
+  if (!(zlo <= zhi)) {
+    if (vis_unc) *vis_unc = unc;
+    return 0;
+  }
+  /* project the 8 corners of the depth-clipped brick to pixel coordinates */
+  double pmin[2] = {INFINITY, INFINITY}, pmax[2] = {-INFINITY, -INFINITY};
+  for (int c = 0; c < 8; ++c) {
+    double X[3] = {(c & 1) ? bmax[0] : bmin[0], (c & 2) ? bmax[1] : bmin[1], (c & 4) ? zhi : zlo};
+    for (int a = 0; a < 2; ++a) {
+      double plane = C->ortho ? X[a] : X[a] * C->near_ / X[2];
+      double p = plane / C->ell + 0.5 * ((a == 0 ? C->w : C->h) - 1);
+      if (p < pmin[a]) pmin[a] = p;
+      if (p > pmax[a]) pmax[a] = p;
+    }
+  }
+  int lim[2] = {C->w - 1, C->h - 1};
+  int vis = 1, vis_in = 1, vis_out = 1;
+  for (int a = 0; a < 2; ++a) {
+    vis = vis && axis_visible(pmin[a], pmax[a], lim[a]);
+    vis_in = vis_in && axis_visible(pmin[a] + band_px, pmax[a] - band_px, lim[a]);
+    vis_out = vis_out && axis_visible(pmin[a] - band_px, pmax[a] + band_px, lim[a]);
+  }
+  if (vis_in != vis_out) unc = 1;
+  if (vis_unc) *vis_unc = unc;
+  if (pext) { pext[0] = pmin[0]; pext[1] = pmax[0]; pext[2] = pmin[1]; pext[3] = pmax[1]; }
+  if (!vis) return 0;
+  for (int a = 0; a < 2; ++a) {
+    double lo_f = ceil(pmin[a]), hi_f = floor(pmax[a]);
+    if (lo_f < 0.0) lo_f = 0.0;
+    if (hi_f > lim[a]) hi_f = lim[a];
+    rect[2 * a] = (int32_t)lo_f;
+    rect[2 * a + 1] = (int32_t)hi_f;
+  }
+  return 1;
+}
+
+/* Slab test: the ray's parameter interval inside the axis-aligned leaf box. */
+int orc_ray_leaf(const orc_forest *F, int leaf, const double *org, const double *dir, double amin,
+                 double amax, double *a_in, double *a_out) {
+  double lo[3], h;
+  leaf_box(F, leaf, lo, &h);
+  double t0 = amin, t1 = amax;
+  for (int a = 0; a < 3; ++a) {
+    double b0 = lo[a], b1 = lo[a] + h;
+    if (dir[a] == 0.0) {
+      if (org[a] < b0 || org[a] > b1) { /* parallel to the slab and outside it */
+        *a_in = INFINITY;
+        *a_out = -INFINITY;
+        return 0;
+      }
+      continue;
+    }
+    double s0 = (b0 - org[a]) / dir[a], s1 = (b1 - org[a]) / dir[a];
+    if (s0 > s1) { double tmp = s0; s0 = s1; s1 = tmp; }
+    if (s0 > t0) t0 = s0;
+    if (s1 < t1) t1 = s1;
+  }
+  *a_in = t0;
+  *a_out = t1;
+  return t1 > t0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Segment values, Sec. 2.3 and 2.7                                          */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  const orc_forest *F;
+  const float *nodal;
+  double lo[3], h;
+  double org[3], dir[3];
+  double a_out, rlen; /* x runs from the far end: alpha(x) = a_out - x / |r| */
+} seg_ctx;
+
+/* kappa and q at distance x from the far end of the segment. */
+static void medium_at(const seg_ctx *S, double x, double *kq) {
+  double alpha = S->a_out - x / S->rlen;
+  double u[3];
+  for (int a = 0; a < 3; ++a) u[a] = (S->org[a] + alpha * S->dir[a] - S->lo[a]) / S->h;
+  double s = orc_trilinear(S->nodal, u[0], u[1], u[2]);
+  orc_tf_eval(S->F, s, kq);
+}
+
+/* Classical RK4 on A' = -kappa A, B' = q - kappa B (Eq. 2.22), x from the far
+ * end, state continued across nsteps equal steps starting from (1, 0). */
+static void rk4_segment(const seg_ctx *S, double dx, int nsteps, double *y) {
+  y[0] = 1.0; y[1] = y[2] = y[3] = 0.0;
+  double hs = dx / nsteps;
+  for (int n = 0; n < nsteps; ++n) {
+    double x0 = n * hs;
+    double kq0[4], kq1[4], kq2[4];
+    medium_at(S, x0, kq0);
+    medium_at(S, x0 + 0.5 * hs, kq1);
+    medium_at(S, x0 + hs, kq2);
+    double k1[4], k2[4], k3[4], k4[4], yt[4];
+    /* f(x, Y) = (-kappa A, q - kappa B) */
+#define RHS(kq, Y, K) do { (K)[0] = -(kq)[0] * (Y)[0]; \
+      for (int c = 1; c < 4; ++c) (K)[c] = (kq)[c] - (kq)[0] * (Y)[c]; } while (0)
+    RHS(kq0, y, k1);
+    for (int c = 0; c < 4; ++c) yt[c] = y[c] + 0.5 * hs * k1[c];
+    RHS(kq1, yt, k2);
+    for (int c = 0; c < 4; ++c) yt[c] = y[c] + 0.5 * hs * k2[c];
+    RHS(kq1, yt, k3);
+    for (int c = 0; c < 4; ++c) yt[c] = y[c] + hs * k3[c];
+    RHS(kq2, yt, k4);
+    for (int c = 0; c < 4; ++c) y[c] += hs / 6.0 * (k1[c] + 2.0 * k2[c] + 2.0 * k3[c] + k4[c]);
+  }
+}
+
+/* Dormand-Prince 5(4) tableau (Dormand & Prince, J. Comput. Appl. Math. 6,
+ * 1980): nodes c, coefficients a, fifth-order weights b and fourth-order
+ * weights bs.  The seventh stage sits at the end point (c = 1). */
+static const double DP_C[7] = {0.0, 1.0 / 5, 3.0 / 10, 4.0 / 5, 8.0 / 9, 1.0, 1.0};
+static const double DP_A[7][6] = {
+    {0, 0, 0, 0, 0, 0},
+    {1.0 / 5, 0, 0, 0, 0, 0},
+    {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
+    {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
+    {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
+    {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
+    {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}};
+static const double DP_B[7] = {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0};
+static const double DP_BS[7] = {5179.0 / 57600, 0, 7571.0 / 16695, 393.0 / 640,
+                                -92097.0 / 339200, 187.0 / 2100, 1.0 / 40};
+
+/* One Dormand-Prince step over [x1, x2] from (1, 0), Eq. 2.23.  Returns the
+ * fifth-order values, the largest dx kappa(xi_j) and the embedded error. */
+static void dopri_step(const seg_ctx *S, double x1, double x2, double *y5, double *kmax,
+                       double *err) {
+  double dx = x2 - x1;
+  double K[7][4];
+  *kmax = 0.0;
+  for (int i = 0; i < 7; ++i) {
+    double Y[4] = {1.0, 0.0, 0.0, 0.0};
+    for (int j = 0; j < i; ++j)
+      for (int c = 0; c < 4; ++c) Y[c] += dx * DP_A[i][j] * K[j][c];
+    double kq[4];
+    medium_at(S, x1 + DP_C[i] * dx, kq);
+    if (dx * kq[0] > *kmax) *kmax = dx * kq[0];
+    RHS(kq, Y, K[i]);
+  }
+  double e = 0.0;
+  for (int c = 0; c < 4; ++c) {
+    double s5 = (c == 0) ? 1.0 : 0.0, s4 = s5;
+    for (int i = 0; i < 7; ++i) {
+      s5 += dx * DP_B[i] * K[i][c];
+      s4 += dx * DP_BS[i] * K[i][c];
+    }
+    y5[c] = s5;
+    if (fabs(s5 - s4) > e) e = fabs(s5 - s4);
+  }
+  *err = e;
+}
+
+/* Algorithm 1: if a stage sees dx kappa > c_RK (or the embedded error exceeds
+ * tol), split at the midpoint and return segeval(mid, x2) (+) segeval(x1, mid). */
+static void segeval(const seg_ctx *S, const orc_integrator *I, double x1, double x2, int depth,
+                    double *out, int64_t *nsteps) {
+  double y5[4], kmax, err;
+  dopri_step(S, x1, x2, y5, &kmax, &err);
+  ++*nsteps;
+  if (depth < I->max_depth && (kmax > I->c_rk || err > I->tol)) {
+    double xm = 0.5 * (x1 + x2), near_s[4], far_s[4];
+    segeval(S, I, x1, xm, depth + 1, far_s, nsteps);
+    segeval(S, I, xm, x2, depth + 1, near_s, nsteps);
+    orc_combine(near_s, far_s, out);
+    return;
+  }
+  memcpy(out, y5, sizeof y5);
+}
+
+void orc_segment_ab(const orc_forest *F, const orc_integrator *I, int leaf, const double *org,
+                    const double *dir, double a_in, double a_out, double *seg4, int64_t *nsteps) {
+  seg_ctx S;
+  S.F = F;
+  S.nodal = F->nodal + 8 * (size_t)leaf;
+  leaf_box(F, leaf, S.lo, &S.h);
+  memcpy(S.org, org, sizeof S.org);
+  memcpy(S.dir, dir, sizeof S.dir);
+  S.a_out = a_out;
+  S.rlen = sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+  double dx = S.rlen * (a_out - a_in);
+  int64_t dummy = 0;
+  if (!nsteps) nsteps = &dummy;
+  if (I->method == ORC_RK4) {
+    rk4_segment(&S, dx, I->nsteps, seg4);
+    *nsteps += I->nsteps;
+  } else {
+    segeval(&S, I, 0.0, dx, 0, seg4, nsteps);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Culling and rendering                                                     */
+/* ------------------------------------------------------------------------ */
+
+void orc_cull(const orc_forest *F, const orc_camera *C, int32_t *rect, uint8_t *visible,
+              uint8_t *uncertain, double band_px) {
+#pragma omp parallel for schedule(static)
+  for (int l = 0; l < F->nleaves; ++l) {
+    int32_t r[4];
+    int unc = 0;
+    int vis = orc_leaf_rect(F, C, l, r, NULL, band_px, &unc);
+    if (rect) memcpy(rect + 4 * (size_t)l, r, sizeof r);
+    visible[l] = (uint8_t)vis;
+    if (uncertain) uncertain[l] = (uint8_t)unc;
+  }
+}
+
+typedef struct {
+  double a_in, a_out, s[4];
+} orc_seg;
+
+static int cmp_seg(const void *pa, const void *pb) {
+  const orc_seg *a = (const orc_seg *)pa, *b = (const orc_seg *)pb;
+  if (a->a_in != b->a_in) return a->a_in < b->a_in ? -1 : 1;
+  return (a->a_out < b->a_out) ? -1 : (a->a_out > b->a_out);
+}
+
+static int cmp_dbl(const void *pa, const void *pb) {
+  double a = *(const double *)pa, b = *(const double *)pb;
+  return (a > b) - (a < b);
+}
+
+/* Back-to-front compositing of one pixel's segments (Eq. 2.10 applied from the
+ * farthest segment to the nearest, starting from the background).  Where
+ * segments overlap, the ray is cut at every segment end into elementary
+ * intervals; each segment covering an interval is cut to it (Eq. 2.17) and the
+ * covering pieces are averaged (Eq. 2.18, geometric mean of A, arithmetic mean
+ * of B, over all covering pieces). */
+static void composite(orc_seg *sg, int n, const double *bg, double *rgba) {
+  double I[3] = {bg[0], bg[1], bg[2]}, T = 1.0;
+  qsort(sg, (size_t)n, sizeof *sg, cmp_seg);
+  int overlap = 0;
+  for (int k = 0; k + 1 < n; ++k)
+    if (sg[k + 1].a_in < sg[k].a_out) overlap = 1;
+  if (!overlap) {
+    for (int k = n - 1; k >= 0; --k) {
+      for (int c = 0; c < 3; ++c) I[c] = sg[k].s[0] * I[c] + sg[k].s[1 + c];
+      T *= sg[k].s[0];
+    }
+  } else {
+    double *pts = (double *)malloc(sizeof(double) * 2 * (size_t)n);
+    for (int k = 0; k < n; ++k) { pts[2 * k] = sg[k].a_in; pts[2 * k + 1] = sg[k].a_out; }
+    qsort(pts, 2 * (size_t)n, sizeof(double), cmp_dbl);
+    for (int p = 2 * n - 2; p >= 0; --p) { /* elementary intervals, far to near */
+      double lo = pts[p], hi = pts[p + 1];
+      if (!(hi > lo)) continue;
+      double logA = 0.0, Bs[3] = {0, 0, 0};
+      int cover = 0;
+      for (int k = 0; k < n; ++k) {
+        if (sg[k].a_in <= lo && sg[k].a_out >= hi) {
+          double piece[4];
+          orc_cut(sg[k].s, (hi - lo) / (sg[k].a_out - sg[k].a_in), piece);
+          logA += log(piece[0]);
+          for (int c = 0; c < 3; ++c) Bs[c] += piece[1 + c];
+          ++cover;
+        }
+      }
+      if (!cover) continue;
+      double A = exp(logA / cover);
+      for (int c = 0; c < 3; ++c) I[c] = A * I[c] + Bs[c] / cover;
+      T *= A;
+    }
+    free(pts);
+  }
+  rgba[0] = I[0]; rgba[1] = I[1]; rgba[2] = I[2]; rgba[3] = 1.0 - T;
+}
+
+int64_t orc_render(const orc_forest *F, const orc_camera *C, const orc_integrator *I,
+                   const int *rows, int nrows, double *rgba, int32_t *counts,
+                   uint8_t *uncertain, double band_px, double band_rel, int nthreads,
+                   int64_t *nsteps_total) {
+  const int W = C->w, H = C->h;
+  if (!rows) nrows = H;
+  /* candidate rectangle of every leaf: its pixel rectangle widened by one
+   * pixel, so that a ray hitting the leaf is never missed through rounding */
+  int32_t *rect = (int32_t *)malloc(sizeof(int32_t) * 4 * (size_t)F->nleaves);
+  uint8_t *vis = (uint8_t *)malloc((size_t)F->nleaves);
+  double *pext = (double *)malloc(sizeof(double) * 4 * (size_t)F->nleaves);
+  int *rowpos = (int *)malloc(sizeof(int) * (size_t)H);
+  if (!rect || !vis || !pext || !rowpos) {
+    free(rect); free(vis); free(pext); free(rowpos);
+    return -1;
+  }
+  for (int j = 0; j < H; ++j) rowpos[j] = -1;
+  for (int r = 0; r < nrows; ++r) rowpos[rows ? rows[r] : r] = r;
+#pragma omp parallel for schedule(static)
+  for (int l = 0; l < F->nleaves; ++l) {
+    int unc = 0;
+    vis[l] = (uint8_t)orc_leaf_rect(F, C, l, rect + 4 * (size_t)l, pext + 4 * (size_t)l, band_px,
+                                    &unc);
+  }
+  /* rows -> candidate leaves (CSR) */
+  int64_t *rstart = (int64_t *)calloc((size_t)nrows + 1, sizeof(int64_t));
+  for (int l = 0; l < F->nleaves; ++l) {
+    if (!vis[l]) continue;
+    int j0 = rect[4 * l + 2] - 1, j1 = rect[4 * l + 3] + 1;
+    if (j0 < 0) j0 = 0;
+    if (j1 > H - 1) j1 = H - 1;
+    for (int j = j0; j <= j1; ++j)
+      if (rowpos[j] >= 0) rstart[rowpos[j] + 1]++;
+  }
+  for (int r = 0; r < nrows; ++r) rstart[r + 1] += rstart[r];
+  int32_t *rleaf = (int32_t *)malloc(sizeof(int32_t) * (size_t)(rstart[nrows] > 0 ? rstart[nrows] : 1));
+  int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nrows + 1));
+  memcpy(fill, rstart, sizeof(int64_t) * (size_t)(nrows + 1));
+  for (int l = 0; l < F->nleaves; ++l) {
+    if (!vis[l]) continue;
+    int j0 = rect[4 * l + 2] - 1, j1 = rect[4 * l + 3] + 1;
+    if (j0 < 0) j0 = 0;
+    if (j1 > H - 1) j1 = H - 1;
+    for (int j = j0; j <= j1; ++j)
+      if (rowpos[j] >= 0) rleaf[fill[rowpos[j]]++] = l;
+  }
+  int64_t total = 0, steps = 0;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel reduction(+ : total, steps)
+  {
+    int cap_pairs = 1024, cap_seg = 256;
+    int32_t *pl = (int32_t *)malloc(sizeof(int32_t) * cap_pairs); /* leaf per pair */
+    int32_t *pi = (int32_t *)malloc(sizeof(int32_t) * cap_pairs); /* column per pair */
+    int32_t *cstart = (int32_t *)malloc(sizeof(int32_t) * (size_t)(W + 1));
+    int32_t *pord = (int32_t *)malloc(sizeof(int32_t) * cap_pairs);
+    orc_seg *sg = (orc_seg *)malloc(sizeof(orc_seg) * cap_seg);
+#pragma omp for schedule(dynamic, 1)
+    for (int r = 0; r < nrows; ++r) {
+      int j = rows ? rows[r] : r;
+      int np = 0;
+      for (int64_t q = rstart[r]; q < rstart[r + 1]; ++q) {
+        int l = rleaf[q];
+        int i0 = rect[4 * l] - 1, i1 = rect[4 * l + 1] + 1;
+        if (i0 < 0) i0 = 0;
+        if (i1 > W - 1) i1 = W - 1;
+        for (int i = i0; i <= i1; ++i) {
+          if (np == cap_pairs) {
+            cap_pairs *= 2;
+            pl = (int32_t *)realloc(pl, sizeof(int32_t) * cap_pairs);
+            pi = (int32_t *)realloc(pi, sizeof(int32_t) * cap_pairs);
+            pord = (int32_t *)realloc(pord, sizeof(int32_t) * cap_pairs);
+          }
+          pl[np] = l;
+          pi[np] = i;
+          ++np;
+        }
+      }
+      /* bucket the candidate pairs by column */
+      memset(cstart, 0, sizeof(int32_t) * (size_t)(W + 1));
+      for (int p = 0; p < np; ++p) cstart[pi[p] + 1]++;
+      for (int i = 0; i < W; ++i) cstart[i + 1] += cstart[i];
+      for (int p = 0; p < np; ++p) pord[cstart[pi[p]]++] = p;
+      for (int i = W; i > 0; --i) cstart[i] = cstart[i - 1];
+      cstart[0] = 0;
+      for (int i = 0; i < W; ++i) {
+        double org[3], dir[3], amin, amax;
+        orc_pixel_ray(C, i, j, org, dir, &amin, &amax);
+        int ns = 0, unc = 0;
+        for (int q = cstart[i]; q < cstart[i + 1]; ++q) {
+          int l = pl[pord[q]];
+          double a_in, a_out;
+          int hit = orc_ray_leaf(F, l, org, dir, amin, amax, &a_in, &a_out);
+          if (isfinite(a_in) && isfinite(a_out)) {
+            double scale = fabs(a_out) > fabs(a_in) ? fabs(a_out) : fabs(a_in);
+            if (fabs(a_out - a_in) <= band_rel * scale) unc = 1;
+          }
+          if (!hit) continue;
+          /* a hit outside the leaf's own rectangle, or within band_px of its edge */
+          {
+            const double *pe = pext + 4 * (size_t)l;
+            if (i < pe[0] + band_px || i > pe[1] - band_px || j < pe[2] + band_px ||
+                j > pe[3] - band_px)
+              unc = 1;
+          }
+          if (ns == cap_seg) {
+            cap_seg *= 2;
+            sg = (orc_seg *)realloc(sg, sizeof(orc_seg) * cap_seg);
+          }
+          sg[ns].a_in = a_in;
+          sg[ns].a_out = a_out;
+          int64_t st = 0;
+          orc_segment_ab(F, I, l, org, dir, a_in, a_out, sg[ns].s, &st);
+          steps += st;
+          ++ns;
+        }
+        size_t pix = (size_t)r * W + i;
+        composite(sg, ns, I->bg, rgba + 4 * pix);
+        if (counts) counts[pix] = ns;
+        if (uncertain) uncertain[pix] = (uint8_t)unc;
+        total += ns;
+      }
+    }
+    free(pl); free(pi); free(cstart); free(pord); free(sg);
+  }
+  free(rect); free(vis); free(pext); free(rowpos); free(rstart); free(rleaf); free(fill);
+  if (nsteps_total) *nsteps_total = steps;
+  return total;
+}

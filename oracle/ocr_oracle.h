@@ -1,0 +1,101 @@
+/* FP64 CPU oracle for the forest-of-octrees raycaster (Burstedde 2018,
+ * "Distributed-Memory Forest-of-Octrees Raycasting").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or constant with the CUDA library under
+ * paper_1809_01334_gb300/csrc, and neither includes the other.
+ *
+ * Everything is plain, slow, obviously-correct double-precision C:
+ *   - segment algebra: combine (Eq. 2.14), inverse (Eq. 2.15), cut (Eq. 2.17),
+ *     average (Eq. 2.18);
+ *   - camera rays (Eq. 2.2), camera transform (Eq. 2.3), axis-aligned bounding
+ *     boxes projected to pixel rectangles (Sec. 2.2, App. A.2);
+ *   - per-segment (A, B) by explicit Runge-Kutta on the decoupled ODEs
+ *     (Eqs. 2.22-2.23) with the adaptive bisection of Algorithm 1;
+ *   - per-pixel compositing by the classical back-to-front recursion
+ *     I <- A I + B (Eq. 2.10), with overlaps resolved by cut + average (Sec. 2.5).
+ */
+#ifndef OCR_ORACLE_H
+#define OCR_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Forest of one unit-cube tree with the identity map. */
+typedef struct {
+  int nleaves;
+  int max_level;            /* anchors are integers in units of 2^-max_level */
+  const int32_t *anchor;    /* [nleaves*3] */
+  const uint8_t *level;     /* [nleaves] */
+  const float *nodal;       /* [nleaves*8], corner c = bx + 2 by + 4 bz */
+  const float *tf;          /* [8*4]: kappa, q_r, q_g, q_b at the 8 knots */
+  double s_min, s_max;      /* knot k sits at s_min + k (s_max - s_min) / 7 */
+} orc_forest;
+
+typedef struct {
+  double o[3], v[3], t[3], u[3];
+  double ell, near_, far_;
+  int w, h, ortho;
+} orc_camera;
+
+enum { ORC_RK4 = 0, ORC_DOPRI5 = 1 };
+typedef struct {
+  int method;      /* ORC_RK4: nsteps equal classical RK4 steps; ORC_DOPRI5: Algorithm 1 */
+  int nsteps;
+  double tol;      /* DOPRI5: split when the embedded error estimate exceeds tol */
+  double c_rk;     /* split when dx * kappa(xi_j) > c_rk at any stage point */
+  int max_depth;   /* bisection depth cap */
+  double bg[3];    /* background intensity I_b per channel */
+} orc_integrator;
+
+/* Segment algebra on (A, B_r, B_g, B_b). */
+void orc_combine(const double *near_seg, const double *far_seg, double *out);
+void orc_inverse(const double *s, double *out);
+void orc_cut(const double *s, double frac, double *out);
+void orc_average(const double *s1, const double *s2, double *out);
+
+/* Transfer function and trilinear field evaluation. */
+void orc_tf_eval(const orc_forest *F, double s, double *kq /* [4] */);
+double orc_trilinear(const float *nodal8, double u, double v, double w);
+
+/* Ray of pixel (i, j): origin, direction and admissible alpha range. */
+void orc_pixel_ray(const orc_camera *C, int i, int j, double *org, double *dir,
+                   double *amin, double *amax);
+
+/* Pixel rectangle of a leaf's camera-space bounding box.  Returns 1 if the
+ * leaf is visible.  rect = {i0, i1, j0, j1} (inclusive; {0,-1,0,-1} when not
+ * visible).  pext (may be NULL) receives the continuous projected extents;
+ * *vis_unc is set when a threshold within band_px would flip visibility. */
+int orc_leaf_rect(const orc_forest *F, const orc_camera *C, int leaf, int32_t *rect,
+                  double *pext, double band_px, int *vis_unc);
+
+/* Slab intersection of a ray with a leaf; returns 1 and [a_in, a_out] if the
+ * clipped interval is non-empty. */
+int orc_ray_leaf(const orc_forest *F, int leaf, const double *org, const double *dir,
+                 double amin, double amax, double *a_in, double *a_out);
+
+/* (A, B) of the segment [a_in, a_out] of the ray inside the leaf. */
+void orc_segment_ab(const orc_forest *F, const orc_integrator *I, int leaf,
+                    const double *org, const double *dir, double a_in, double a_out,
+                    double *seg4, int64_t *nsteps);
+
+/* Visibility of every leaf.  rect may be NULL. */
+void orc_cull(const orc_forest *F, const orc_camera *C, int32_t *rect, uint8_t *visible,
+              uint8_t *uncertain, double band_px);
+
+/* Render the listed image rows (rows == NULL: all rows).  rgba[nrows*w*4],
+ * counts[nrows*w] (segments per ray), uncertain[nrows*w] (a decision of this
+ * ray fell within the tie band).  Returns the total number of segments, or a
+ * negative number on allocation failure. */
+int64_t orc_render(const orc_forest *F, const orc_camera *C, const orc_integrator *I,
+                   const int *rows, int nrows, double *rgba, int32_t *counts,
+                   uint8_t *uncertain, double band_px, double band_rel, int nthreads,
+                   int64_t *nsteps_total);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
