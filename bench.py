@@ -1,0 +1,290 @@
+#!/usr/bin/env python
+"""Throughput of the forest-of-octrees raycaster: ray segments per second.
+
+One step = one whole render of the adaptive cube workload: 2,053,451 leaves
+(levels 2-8, 2:1 balanced, trilinear FP32 data from 16 seeded Gaussians),
+perspective 45-degree camera at 1920x1080, Dormand-Prince 5(4) at tolerance
+1e-6 inside the midpoint bisection (c_RK = 1/2): pruning, per-leaf segments
+and the merge of every ray's segments into its pixel.  The metric is the
+number of ray segments the render integrates divided by its device time.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+For N > 1 launch with torchrun; each rank renders its own copy of the
+workload (independent replicas, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ray-segments/s"
+UNIT = "segments/s"
+WORKLOAD = ("adaptive unit cube, levels 2-8 (2,053,451 leaves, 2:1 balanced, trilinear FP32), "
+            "perspective 45deg 1920x1080, DOPRI5 tol 1e-6, c_RK 0.5")
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-row-stride", type=int, default=1,
+                   help="CPU baseline renders every n-th image row")
+    p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    p.add_argument("--image", default="1920x1080",
+                   help="image size WxH (smaller sizes only for profiling captures)")
+    return p.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.lines: list[str] = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={CLOCK_FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def cpu_baseline(forest, tf, cam, integ, stride: int):
+    """The FP64 oracle, as it stands, on this host's cores: every stride-th row."""
+    import numpy as np
+    import oracle as O
+    rows = np.arange(0, cam.h, stride, dtype=np.int32)
+    O.build()
+    t0 = time.perf_counter()
+    r = O.render(forest, tf, cam, integ, rows=rows)
+    dt = time.perf_counter() - t0
+    cores = os.cpu_count()
+    return {"value": r["segments"] / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"every {stride}th row of the 1920x1080 image ({len(rows)} rows, "
+                      f"{r['segments']} segments, {dt:.1f} s)"}
+
+
+def run_reference(args, world, rank):
+    """The oracle as the reference arm: each step renders a bounded sample of rows."""
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle as O
+    from paper_1809_01334_gb300 import inputs as I
+    O.build()
+    forest, tf, cam, integ = I.preset_c2()
+    nrows = 16
+    times, segs = [], []
+    for k in range(args.warmup + args.steps):
+        rows = np.arange(k * 37 % (cam.h - nrows), cam.h, cam.h // nrows, dtype=np.int32)[:nrows]
+        t0 = time.perf_counter()
+        r = O.render(forest, tf, cam, integ, rows=rows)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            segs.append(r["segments"])
+    value = sum(segs) / sum(times)
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"{nrows} rows per step"},
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": UNIT,
+                             "sample": f"{nrows} image rows per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1809_01334_gb300 import Renderer
+    from paper_1809_01334_gb300 import inputs as I
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    w, h = (int(x) for x in args.image.split("x"))
+    forest, tf, cam, integ = I.preset_c2(w=w, h=h)
+    r = Renderer(forest, tf, integ, device=dev)
+    r.set_camera(cam)
+    out = torch.empty((cam.h, cam.w, 4), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    # the segment count of this workload is deterministic: take it once
+    _, st0 = r.render(out, fill_counters=True)
+    segments, launches = st0["segments"], st0["launches"]
+
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    for _ in range(args.warmup):
+        flush.zero_()
+        r.render(out)
+    torch.cuda.synchronize(dev)
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    merge_ms, prune_ms = [], []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()  # outside the timed interval of the step
+            evs[k][0].record(stream)
+            _, st = r.render(out, time_phases=True)
+            evs[k][1].record(stream)
+            merge_ms.append(st["ms_merge"])
+            prune_ms.append(st["ms_prune"])
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = sum(step_ms) / len(step_ms)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+
+    # end to end through the public API from pinned host memory: nodal data in,
+    # image out, every step
+    nodal_h = torch.from_numpy(np.ascontiguousarray(forest.nodal, np.float32)).pin_memory()
+    out_h = torch.empty(out.shape, dtype=out.dtype).pin_memory()
+    nodal_d = torch.empty_like(r.nodal)
+    r.set_data(nodal_d, r.tf)
+    e2e_ms = []
+    for k in range(0 if args.no_e2e else args.warmup + args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        nodal_d.copy_(nodal_h, non_blocking=True)
+        r.render(out)
+        out_h.copy_(out, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        if k >= args.warmup:
+            e2e_ms.append(a.elapsed_time(b))
+    e2e = sum(e2e_ms) / len(e2e_ms) if e2e_ms else float("nan")
+    te = torch.tensor([e2e], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+
+    if rank == 0:
+        peaks, src = measured_peaks()
+        mm = sum(merge_ms) / len(merge_ms)
+        # algorithmic bytes of the merge passes: every (node, ray) aggregate is
+        # written once and read once by its parent (16 B each), plus one read of
+        # each leaf's record (anchor 16 B + 8 corner values 32 B)
+        alg_bytes = 32 * st0["slots"] + 48 * forest.nleaves
+        achieved = alg_bytes / (mm * 1e-3) / 1e9
+        line = {
+            "metric": METRIC, "value": world * segments / (ms_max * 1e-3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD if (w, h) == (1920, 1080) else
+                       WORKLOAD.replace("1920x1080", f"{w}x{h}"),
+                       "image": [cam.w, cam.h], "leaves": forest.nleaves,
+                       "segments_per_step": segments, "rk_steps_per_step": st0["rk_steps"],
+                       "slots_per_step": st0["slots"], "leaf_tests_per_step": st0["leaf_tests"],
+                       "mpixel_per_s": world * cam.w * cam.h / (ms_max * 1e-3) / 1e6,
+                       "l2": "flushed (512 MB write) before every timed step",
+                       "parallelism": f"replicas x{world}"},
+            "gpu_launches": launches * args.steps,
+            "e2e": {"value": world * segments / (float(te.item()) * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(forest.nodal.nbytes),
+                    "d2h_bytes_per_step": int(out.numel() * 4)},
+            "roofline": {"bound": "hbm", "kernel": "coarsen (all levels)",
+                         "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                         "peak_source": src, "ms_merge": mm,
+                         "ms_prune": sum(prune_ms) / len(prune_ms)},
+            "clocks": clk.summary(),
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(forest, tf, cam, integ, args.cpu_row_stride)
+        print(json.dumps(line), flush=True)
+    r.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,143 @@
+/* ocraycast: forest-of-octrees raycasting on one NVIDIA GB300 (sm_103a).
+ *
+ * C ABI of the CUDA library built from paper_1809_01334_gb300/csrc.  The
+ * operations follow C. Burstedde, "Distributed-Memory Forest-of-Octrees
+ * Raycasting" (2018):
+ *
+ *   prune   - drop the leaves whose camera-space bounding box covers no pixel
+ *             centre (Sec. 3.1, Sec. 2.2);
+ *   segment - intersect each remaining leaf with every ray of its pixel
+ *             rectangle and integrate A' = -kappa A, B' = q - kappa B along
+ *             the piece (Sec. 2.3, Eqs. 2.22-2.23, Algorithm 1);
+ *   merge   - aggregate the segments of each ray up the octree with the
+ *             segment group action (Eq. 2.14, Sec. 3.3) into its pixel,
+ *             I_v = A I_b + B (Sec. 2.4), without a global depth sort.
+ *
+ * Conventions
+ *  - Every entry point returns OCR_OK (0) or a negative OCR_ERR_* code and
+ *    never aborts.  ocr_strerror() names the code.
+ *  - "d_" pointers are device pointers owned by the caller; "h_" pointers
+ *    are host pointers read during the call only.  The library owns only its
+ *    internal copies of the forest topology and a scratch arena, both freed
+ *    by ocr_destroy().
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it; ocr_render blocks the host once per
+ *    call, after pruning, to size its scratch memory.
+ *  - Only the single unit-cube tree with the identity map is implemented in
+ *    this version (OCR_GEOM_CUBE); other geometries return
+ *    OCR_ERR_UNSUPPORTED.
+ */
+#ifndef OCRAYCAST_H
+#define OCRAYCAST_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OCR_OK 0
+#define OCR_ERR_INVALID (-1)     /* bad argument, forest not complete or not Morton-sorted */
+#define OCR_ERR_CUDA (-2)        /* a CUDA runtime call failed */
+#define OCR_ERR_OOM (-3)         /* device or host allocation failed */
+#define OCR_ERR_UNSUPPORTED (-4) /* geometry or option not implemented */
+#define OCR_ERR_DEVICE (-5)      /* a kernel's own bounds check fired */
+#define OCR_ERR_STATE (-6)       /* call order violated (no data / no camera set) */
+
+#define OCR_GEOM_CUBE 0
+
+#define OCR_RK4 0    /* nsteps equal classical RK4 steps per segment */
+#define OCR_DOPRI5 1 /* Dormand-Prince 5(4) inside the bisection of Algorithm 1 */
+
+typedef struct ocr_forest ocr_forest;
+
+/* Linear forest of one octree over the unit cube (Sec. 2.1, Sec. 3).
+ * Leaves are listed in Morton order of their anchors and tile the cube.
+ * anchor[3*k + a] is leaf k's lower corner along axis a in integer units of
+ * 2^-max_level; level[k] its level (edge length 2^-level).  max_level <= 20. */
+typedef struct {
+  int geometry;          /* OCR_GEOM_CUBE */
+  int max_level;
+  int64_t nleaves;
+  const int32_t *h_anchor; /* [nleaves * 3] */
+  const uint8_t *h_level;  /* [nleaves] */
+} ocr_forest_desc;
+
+/* Pinhole camera of Sec. 2.2, Eq. 2.2: ray (i, j) is o + alpha r with
+ * r = v + ell ((i - (w-1)/2) t + (j - (h-1)/2) u), alpha in [1, far/near]
+ * (near = |v|, the projection plane).  ortho != 0: the origin moves to
+ * o + ell ((i - (w-1)/2) t + (j - (h-1)/2) u), the direction is v/near and
+ * alpha in [0, far].  Values are read as float32. */
+typedef struct {
+  double o[3], v[3], t[3], u[3];
+  double ell, near_, far_;
+  int w, h, ortho;
+} ocr_camera;
+
+/* Per-segment integrator.  RK4: nsteps equal steps from the far end, each
+ * combined by Eq. 2.14.  DOPRI5: a step over [x1, x2] is replaced by its two
+ * halves, combined near (+) far, while dx * kappa(xi) > c_rk at a stage
+ * point or the embedded error estimate exceeds tol, up to max_depth halvings
+ * (Algorithm 1).  bg is the background intensity I_b per channel. */
+typedef struct {
+  int method;
+  int nsteps;
+  float tol, c_rk;
+  int max_depth;
+  float bg[3];
+} ocr_integrator;
+
+/* Optional extras of ocr_render.  Device buffers are written when non-NULL:
+ *   d_counts  [w*h]      int32   segments on each ray (row-major, j*w + i)
+ *   d_visible [nleaves]  uint8   1 if the leaf survived pruning
+ *   d_rects   [nleaves*4] int32  pixel rectangle {i0, i1, j0, j1} (inclusive;
+ *                                {0,-1,0,-1} when pruned)
+ * The counters are filled when fill_counters != 0, and the phase times
+ * (device time between CUDA events recorded on `stream`) when time_phases != 0;
+ * either blocks the host once more, at the end of the call. */
+typedef struct {
+  int32_t *d_counts;
+  uint8_t *d_visible;
+  int32_t *d_rects;
+  int fill_counters;
+  int time_phases;
+  int64_t visible_leaves; /* leaves that survived pruning */
+  int64_t segments;       /* ray segments integrated (sum of d_counts) */
+  int64_t rk_steps;       /* Runge-Kutta steps taken over all segments */
+  int64_t leaf_tests;     /* (leaf, ray) slab tests performed */
+  int64_t slots;          /* (node, ray) aggregates formed while merging */
+  int64_t launches;       /* kernels launched by this call */
+  float ms_prune;         /* pruning, rectangle unions, slot layout, host readback */
+  float ms_merge;         /* all coarsening passes (segments + merge), incl. the pixel pass */
+} ocr_stats;
+
+/* Copy the forest topology to the device and derive its internal octree
+ * nodes (the coarsening hierarchy of Sec. 3.3).  Returns OCR_ERR_INVALID if
+ * the leaves are not Morton-sorted or do not tile the cube. */
+int ocr_build_forest(const ocr_forest_desc *desc, void *stream, ocr_forest **out);
+
+/* Attach the field and the transfer function (not copied, not owned):
+ * d_nodal [nleaves*8] float32, corner c = bx + 2 by + 4 bz of each leaf
+ * (trilinear data); d_tf [8*4] float32, (kappa, q_r, q_g, q_b) at 8 knots
+ * spaced uniformly over [s_min, s_max], piecewise linear, constant outside. */
+int ocr_forest_set_data(ocr_forest *F, const float *d_nodal, const float *d_tf, float s_min,
+                        float s_max, void *stream);
+
+int ocr_set_integrator(ocr_forest *F, const ocr_integrator *integ);
+
+/* Set the camera (host struct, copied).  ncams must be 1 in this version. */
+int ocr_set_camera(ocr_forest *F, const ocr_camera *cams, int ncams);
+
+/* Render one image: d_rgba [h*w*4] float32, row-major, (I_r, I_g, I_b, 1 - A)
+ * per pixel.  stats may be NULL. */
+int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats);
+
+/* Device memory held by the library for this forest (topology + scratch). */
+int64_t ocr_device_bytes(const ocr_forest *F);
+
+void ocr_destroy(ocr_forest *F);
+const char *ocr_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

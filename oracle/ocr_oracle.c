@@ -141,7 +141,8 @@ static int axis_visible(double pmin, double pmax, int lim) {
  * rectangle holds the pixel centres inside that projection.  pext receives
  * the projected extents {i_min, i_max, j_min, j_max} in pixel units (may be
  * NULL).  *vis_unc is set when moving any threshold by band_px pixels (or the
- * depth clip by band_px relative) would change the visibility decision. */
+ * depth clip by band_px relative) would change the rectangle or the
+ * visibility decision. */
 int orc_leaf_rect(const orc_forest *F, const orc_camera *C, int leaf, int32_t *rect,
                   double *pext, double band_px, int *vis_unc) {
   double lo[3], h;
@@ -187,6 +188,12 @@ int orc_leaf_rect(const orc_forest *F, const orc_camera *C, int leaf, int32_t *r
     vis_out = vis_out && axis_visible(pmin[a] - band_px, pmax[a] + band_px, lim[a]);
   }
   if (vis_in != vis_out) unc = 1;
+  for (int a = 0; a < 2; ++a) { /* an edge of the rectangle itself is a near tie */
+    if (pmin[a] > -1.0 && pmin[a] < lim[a] + 1.0 && fabs(pmin[a] - nearbyint(pmin[a])) < band_px)
+      unc = 1;
+    if (pmax[a] > -1.0 && pmax[a] < lim[a] + 1.0 && fabs(pmax[a] - nearbyint(pmax[a])) < band_px)
+      unc = 1;
+  }
   if (vis_unc) *vis_unc = unc;
   if (pext) { pext[0] = pmin[0]; pext[1] = pmax[0]; pext[2] = pmin[1]; pext[3] = pmax[1]; }
   if (!vis) return 0;

@@ -68,7 +68,8 @@ void orc_pixel_ray(const orc_camera *C, int i, int j, double *org, double *dir,
 /* Pixel rectangle of a leaf's camera-space bounding box.  Returns 1 if the
  * leaf is visible.  rect = {i0, i1, j0, j1} (inclusive; {0,-1,0,-1} when not
  * visible).  pext (may be NULL) receives the continuous projected extents;
- * *vis_unc is set when a threshold within band_px would flip visibility. */
+ * *vis_unc is set when a threshold within band_px of a decision would change
+ * the rectangle or the visibility. */
 int orc_leaf_rect(const orc_forest *F, const orc_camera *C, int leaf, int32_t *rect,
                   double *pext, double band_px, int *vis_unc);
 

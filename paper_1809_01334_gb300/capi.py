@@ -1,0 +1,152 @@
+"""ctypes binding of the C ABI in include/ocraycast.h (argument marshalling only).
+
+Every function here has the name of the C entry point without the ``ocr_``
+prefix and does nothing but convert arguments: the whole render path runs in
+the CUDA library ``_build/libocraycast.so``.  If that library is missing this
+module raises on first use; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libocraycast.so")
+
+OK, ERR_INVALID, ERR_CUDA, ERR_OOM, ERR_UNSUPPORTED, ERR_DEVICE, ERR_STATE = 0, -1, -2, -3, -4, -5, -6
+GEOM_CUBE = 0
+RK4, DOPRI5 = 0, 1
+
+EXPORTS = ["ocr_build_forest", "ocr_forest_set_data", "ocr_set_integrator", "ocr_set_camera",
+           "ocr_render", "ocr_device_bytes", "ocr_destroy", "ocr_strerror"]
+
+
+class ForestDesc(C.Structure):
+    _fields_ = [("geometry", C.c_int), ("max_level", C.c_int), ("nleaves", C.c_int64),
+                ("h_anchor", C.POINTER(C.c_int32)), ("h_level", C.POINTER(C.c_uint8))]
+
+
+class Camera(C.Structure):
+    _fields_ = [("o", C.c_double * 3), ("v", C.c_double * 3), ("t", C.c_double * 3),
+                ("u", C.c_double * 3), ("ell", C.c_double), ("near_", C.c_double),
+                ("far_", C.c_double), ("w", C.c_int), ("h", C.c_int), ("ortho", C.c_int)]
+
+
+class Integrator(C.Structure):
+    _fields_ = [("method", C.c_int), ("nsteps", C.c_int), ("tol", C.c_float), ("c_rk", C.c_float),
+                ("max_depth", C.c_int), ("bg", C.c_float * 3)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("d_counts", C.c_void_p), ("d_visible", C.c_void_p), ("d_rects", C.c_void_p),
+                ("fill_counters", C.c_int), ("time_phases", C.c_int),
+                ("visible_leaves", C.c_int64), ("segments", C.c_int64), ("rk_steps", C.c_int64),
+                ("leaf_tests", C.c_int64), ("slots", C.c_int64), ("launches", C.c_int64),
+                ("ms_prune", C.c_float), ("ms_merge", C.c_float)]
+
+
+class OcrError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library; raise if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library {LIB_PATH} is missing: run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'` first")
+        L = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        L.ocr_build_forest.argtypes = [C.POINTER(ForestDesc), vp, C.POINTER(vp)]
+        L.ocr_forest_set_data.argtypes = [vp, vp, vp, C.c_float, C.c_float, vp]
+        L.ocr_set_integrator.argtypes = [vp, C.POINTER(Integrator)]
+        L.ocr_set_camera.argtypes = [vp, C.POINTER(Camera), C.c_int]
+        L.ocr_render.argtypes = [vp, vp, vp, C.POINTER(Stats)]
+        L.ocr_device_bytes.argtypes = [vp]
+        L.ocr_device_bytes.restype = C.c_int64
+        L.ocr_destroy.argtypes = [vp]
+        L.ocr_destroy.restype = None
+        L.ocr_strerror.argtypes = [C.c_int]
+        L.ocr_strerror.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return lib().ocr_strerror(int(code)).decode()
+    except Exception:  # the library itself is unavailable
+        return f"error {code}"
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise OcrError(rc, what)
+
+
+def _ptr(x):
+    """Device or host address of a tensor / numpy array / int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def build_forest(level, anchor, max_level: int, stream=None, geometry: int = GEOM_CUBE):
+    """ocr_build_forest.  level: uint8 [N], anchor: int32 [N, 3] (host numpy)."""
+    import numpy as np
+    lv = np.ascontiguousarray(level, dtype=np.uint8)
+    an = np.ascontiguousarray(anchor, dtype=np.int32)
+    d = ForestDesc(geometry, int(max_level), int(lv.shape[0]),
+                   an.ctypes.data_as(C.POINTER(C.c_int32)), lv.ctypes.data_as(C.POINTER(C.c_uint8)))
+    h = C.c_void_p()
+    _check(lib().ocr_build_forest(C.byref(d), _ptr(stream), C.byref(h)), "ocr_build_forest")
+    return h
+
+
+def forest_set_data(h, d_nodal, d_tf, s_min: float, s_max: float, stream=None):
+    _check(lib().ocr_forest_set_data(h, _ptr(d_nodal), _ptr(d_tf), float(s_min), float(s_max),
+                                     _ptr(stream)), "ocr_forest_set_data")
+
+
+def set_integrator(h, method: int, nsteps: int = 4, tol: float = 1e-6, c_rk: float = 0.5,
+                   max_depth: int = 16, bg=(0.0, 0.0, 0.0)):
+    s = Integrator(int(method), int(nsteps), float(tol), float(c_rk), int(max_depth))
+    s.bg[:] = bg
+    _check(lib().ocr_set_integrator(h, C.byref(s)), "ocr_set_integrator")
+
+
+def set_camera(h, o, v, t, u, ell, near, far, w, h_px, ortho=False):
+    c = Camera()
+    c.o[:], c.v[:], c.t[:], c.u[:] = o, v, t, u
+    c.ell, c.near_, c.far_ = float(ell), float(near), float(far)
+    c.w, c.h, c.ortho = int(w), int(h_px), int(bool(ortho))
+    _check(lib().ocr_set_camera(h, C.byref(c), 1), "ocr_set_camera")
+
+
+def render(h, d_rgba, stream=None, d_counts=None, d_visible=None, d_rects=None,
+           fill_counters: bool = False, time_phases: bool = False) -> dict:
+    s = Stats(_ptr(d_counts), _ptr(d_visible), _ptr(d_rects), int(bool(fill_counters)),
+              int(bool(time_phases)))
+    _check(lib().ocr_render(h, _ptr(d_rgba), _ptr(stream), C.byref(s)), "ocr_render")
+    return {"visible_leaves": s.visible_leaves, "segments": s.segments, "rk_steps": s.rk_steps,
+            "leaf_tests": s.leaf_tests, "slots": s.slots, "launches": s.launches,
+            "ms_prune": s.ms_prune, "ms_merge": s.ms_merge}
+
+
+def device_bytes(h) -> int:
+    return int(lib().ocr_device_bytes(h))
+
+
+def destroy(h):
+    if h:
+        lib().ocr_destroy(h)

@@ -1,0 +1,472 @@
+// Host side of the C ABI declared in include/ocraycast.h.
+//
+// ocr_build_forest validates the linear octree (Morton order, complete
+// tiling of the unit cube) and derives its internal nodes: the coarsening
+// hierarchy along which ray segments are aggregated (Sec. 3.3).  ocr_render
+// enqueues, on the caller's stream: pruning of the leaves (Sec. 3.1), the
+// rectangle unions of the internal nodes, the prefix sum that lays out one
+// aggregate per (node, ray), and one coarsening pass per octree level, the
+// deepest first, ending with the pass that writes the pixels.
+#include "../../include/ocraycast.h"
+#include "ocr_common.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+using namespace ocr;
+
+struct ocr_forest {
+  int N = 0, M = 0, L = 0;
+  int root = 0;                       // unified id of the tree root
+  std::vector<int> level_base;        // internal index of the first node of level l
+  std::vector<int> level_count;       // number of internal nodes at level l
+  std::vector<int> h_group_nodes;     // [L + 1] group boundaries, deepest level first, then M
+  int4 *d_geo = nullptr;              // [N + M + 1]
+  int *d_child = nullptr;             // [(M + 1) * 8]
+  int *d_group_nodes = nullptr;       // [L + 1]
+  // data
+  const float *d_nodal = nullptr;
+  const float *d_tf = nullptr;
+  float s_min = 0.f, s_max = 1.f;
+  bool has_data = false, has_cam = false, has_integ = false;
+  Integ integ{};
+  Cam cam{};
+  // scratch
+  int4 *d_rect = nullptr;             // [N + M + 1]
+  long long *d_off = nullptr;         // [M + 1]
+  long long *d_block_sums = nullptr;  // [nblk + 1]
+  int block_sums_cap = 0;
+  long long *d_group_slots = nullptr; // [L + 1]
+  long long *h_group_slots = nullptr; // pinned [L + 1 + 8]
+  unsigned long long *d_stats = nullptr;  // [8]
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  float4 *d_entries = nullptr;
+  long long entries_cap = 0;
+  int *d_chunk_node = nullptr;        // [chunk_cap]
+  long long chunk_cap = 0;
+  int64_t bytes = 0;
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) { return e == cudaErrorMemoryAllocation ? OCR_ERR_OOM : OCR_ERR_CUDA; }
+
+#define OCR_CUDA(call)                          \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+uint64_t spread3(uint32_t v) {
+  uint64_t x = v & 0x1fffff;
+  x = (x | x << 32) & 0x1f00000000ffffull;
+  x = (x | x << 16) & 0x1f0000ff0000ffull;
+  x = (x | x << 8) & 0x100f00f00f00f00full;
+  x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+  x = (x | x << 2) & 0x1249249249249249ull;
+  return x;
+}
+
+uint32_t compact3(uint64_t x) {
+  x &= 0x1249249249249249ull;
+  x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
+  x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
+  x = (x ^ (x >> 8)) & 0x1f0000ff0000ffull;
+  x = (x ^ (x >> 16)) & 0x1f00000000ffffull;
+  x = (x ^ (x >> 32)) & 0x1fffffull;
+  return (uint32_t)x;
+}
+
+uint64_t morton(int x, int y, int z) {
+  return spread3((uint32_t)x) | spread3((uint32_t)y) << 1 | spread3((uint32_t)z) << 2;
+}
+
+template <typename T>
+int dev_alloc(T **p, size_t n, int64_t &bytes) {
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_fail(e);
+  }
+  bytes += (int64_t)(n * sizeof(T));
+  return OCR_OK;
+}
+
+void free_all(ocr_forest *F) {
+  cudaFree(F->d_geo);
+  cudaFree(F->d_child);
+  cudaFree(F->d_group_nodes);
+  cudaFree(F->d_rect);
+  cudaFree(F->d_off);
+  cudaFree(F->d_block_sums);
+  cudaFree(F->d_group_slots);
+  cudaFree(F->d_stats);
+  cudaFree(F->d_entries);
+  cudaFree(F->d_chunk_node);
+  if (F->h_group_slots) cudaFreeHost(F->h_group_slots);
+  for (cudaEvent_t &e : F->ev)
+    if (e) cudaEventDestroy(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ocr_strerror(int code) {
+  switch (code) {
+    case OCR_OK: return "ok";
+    case OCR_ERR_INVALID: return "invalid argument or forest";
+    case OCR_ERR_CUDA: return "CUDA runtime error";
+    case OCR_ERR_OOM: return "out of memory";
+    case OCR_ERR_UNSUPPORTED: return "not supported";
+    case OCR_ERR_DEVICE: return "device-side check failed";
+    case OCR_ERR_STATE: return "data, integrator or camera not set";
+    default: return "unknown error";
+  }
+}
+
+int ocr_build_forest(const ocr_forest_desc *desc, void *stream, ocr_forest **out) {
+  if (!desc || !out) return OCR_ERR_INVALID;
+  *out = nullptr;
+  if (desc->geometry != OCR_GEOM_CUBE) return OCR_ERR_UNSUPPORTED;
+  const int L = desc->max_level;
+  const int64_t N64 = desc->nleaves;
+  if (L < 0 || L > 20 || N64 < 1 || N64 > (1ll << 30) || !desc->h_anchor || !desc->h_level)
+    return OCR_ERR_INVALID;
+  const int N = (int)N64;
+  cudaStream_t st = (cudaStream_t)stream;
+
+  // validate: aligned anchors, strictly increasing Morton keys, contiguous tiling
+  std::vector<uint64_t> key(N);
+  const uint64_t full = 1ull << (3 * L);
+  uint64_t expect = 0;
+  for (int k = 0; k < N; ++k) {
+    const int lv = desc->h_level[k];
+    if (lv > L) return OCR_ERR_INVALID;
+    const int32_t *a = desc->h_anchor + 3 * (size_t)k;
+    const int32_t mask = (1 << (L - lv)) - 1;
+    for (int d = 0; d < 3; ++d)
+      if (a[d] < 0 || a[d] >= (1 << L) || (a[d] & mask)) return OCR_ERR_INVALID;
+    key[k] = morton(a[0], a[1], a[2]);
+    if (key[k] != expect) return OCR_ERR_INVALID;  // not sorted, overlapping or gapped
+    expect += 1ull << (3 * (L - lv));
+  }
+  if (expect != full) return OCR_ERR_INVALID;
+
+  ocr_forest *F = new (std::nothrow) ocr_forest();
+  if (!F) return OCR_ERR_OOM;
+  F->N = N;
+  F->L = L;
+
+  // internal nodes, level by level from the deepest: parents of the nodes below
+  std::vector<std::vector<uint64_t>> ikeys(L > 0 ? L : 1);
+  std::vector<std::vector<uint64_t>> by_level_leaf(L + 1);
+  std::vector<std::vector<int>> by_level_leaf_id(L + 1);
+  for (int k = 0; k < N; ++k) {
+    by_level_leaf[desc->h_level[k]].push_back(key[k]);
+    by_level_leaf_id[desc->h_level[k]].push_back(k);
+  }
+  for (int l = L - 1; l >= 0; --l) {
+    const uint64_t pmask = ~((1ull << (3 * (L - l))) - 1);
+    std::vector<uint64_t> kids;
+    kids.reserve(by_level_leaf[l + 1].size() + (l + 1 < L ? ikeys[l + 1].size() : 0));
+    std::merge(by_level_leaf[l + 1].begin(), by_level_leaf[l + 1].end(),
+               (l + 1 < L ? ikeys[l + 1].begin() : ikeys[l].end()),
+               (l + 1 < L ? ikeys[l + 1].end() : ikeys[l].end()), std::back_inserter(kids));
+    std::vector<uint64_t> &par = ikeys[l];
+    for (uint64_t c : kids) {
+      const uint64_t p = c & pmask;
+      if (par.empty() || par.back() != p) par.push_back(p);
+    }
+  }
+  int M = 0;
+  F->level_base.assign(L > 0 ? L : 1, 0);
+  F->level_count.assign(L > 0 ? L : 1, 0);
+  for (int l = L - 1; l >= 0; --l) {
+    F->level_base[l] = M;
+    F->level_count[l] = (int)ikeys[l].size();
+    M += F->level_count[l];
+  }
+  F->M = M;
+  F->root = (L == 0 || M == 0) ? 0 : N + F->level_base[0];
+  if (M == 0 && N != 1) {
+    free_all(F);
+    delete F;
+    return OCR_ERR_INVALID;
+  }
+
+  std::vector<int4> geo((size_t)N + M + 1);
+  std::vector<int> child((size_t)(M + 1) * 8, -1);
+  for (int k = 0; k < N; ++k) {
+    const int32_t *a = desc->h_anchor + 3 * (size_t)k;
+    geo[k] = make_int4(a[0], a[1], a[2], desc->h_level[k]);
+  }
+  for (int l = L - 1; l >= 0; --l)
+    for (int q = 0; q < F->level_count[l]; ++q) {
+      const uint64_t kk = ikeys[l][q];
+      geo[(size_t)N + F->level_base[l] + q] =
+          make_int4((int)compact3(kk), (int)compact3(kk >> 1), (int)compact3(kk >> 2), l);
+    }
+  geo[(size_t)N + M] = make_int4(0, 0, 0, -1);
+  // children: every node at level l + 1 is the octant-th child of its parent
+  auto attach = [&](int l, uint64_t ckey, int cid) -> bool {
+    const uint64_t pkey = ckey & ~((1ull << (3 * (L - l))) - 1);
+    const int octant = (int)((ckey >> (3 * (L - l - 1))) & 7);
+    const std::vector<uint64_t> &par = ikeys[l];
+    auto it = std::lower_bound(par.begin(), par.end(), pkey);
+    if (it == par.end() || *it != pkey) return false;
+    const int pid = F->level_base[l] + (int)(it - par.begin());
+    if (child[(size_t)pid * 8 + octant] != -1) return false;
+    child[(size_t)pid * 8 + octant] = cid;
+    return true;
+  };
+  bool ok = true;
+  for (int l = L - 1; l >= 0 && ok; --l) {
+    for (size_t q = 0; q < by_level_leaf[l + 1].size() && ok; ++q)
+      ok = attach(l, by_level_leaf[l + 1][q], by_level_leaf_id[l + 1][q]);
+    if (l + 1 < L)
+      for (int q = 0; q < F->level_count[l + 1] && ok; ++q)
+        ok = attach(l, ikeys[l + 1][q], N + F->level_base[l + 1] + q);
+  }
+  for (int p = 0; p < M && ok; ++p)
+    for (int q = 0; q < 8; ++q)
+      if (child[(size_t)p * 8 + q] < 0) ok = false;
+  if (!ok) {
+    free_all(F);
+    delete F;
+    return OCR_ERR_INVALID;
+  }
+  child[(size_t)M * 8] = F->root;  // super-root: one child, the tree root
+
+  // group boundaries: internal levels from the deepest, then M
+  for (int l = L - 1; l >= 0; --l) F->h_group_nodes.push_back(F->level_base[l]);
+  F->h_group_nodes.push_back(M);
+
+  int rc;
+  if ((rc = dev_alloc(&F->d_geo, geo.size(), F->bytes)) ||
+      (rc = dev_alloc(&F->d_child, child.size(), F->bytes)) ||
+      (rc = dev_alloc(&F->d_group_nodes, F->h_group_nodes.size(), F->bytes)) ||
+      (rc = dev_alloc(&F->d_rect, (size_t)N + M + 1, F->bytes)) ||
+      (rc = dev_alloc(&F->d_off, (size_t)M + 1, F->bytes)) ||
+      (rc = dev_alloc(&F->d_group_slots, F->h_group_nodes.size(), F->bytes)) ||
+      (rc = dev_alloc(&F->d_stats, 8, F->bytes))) {
+    free_all(F);
+    delete F;
+    return rc;
+  }
+  F->block_sums_cap = area_scan_blocks(M) + 1;
+  if ((rc = dev_alloc(&F->d_block_sums, F->block_sums_cap, F->bytes))) {
+    free_all(F);
+    delete F;
+    return rc;
+  }
+  if (cudaMallocHost((void **)&F->h_group_slots, sizeof(long long) * (F->h_group_nodes.size() + 8)) !=
+      cudaSuccess) {
+    F->h_group_slots = nullptr;
+    free_all(F);
+    delete F;
+    return OCR_ERR_OOM;
+  }
+  cudaError_t e = cudaMemcpyAsync(F->d_geo, geo.data(), geo.size() * sizeof(int4),
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(F->d_child, child.data(), child.size() * sizeof(int),
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(F->d_group_nodes, F->h_group_nodes.data(),
+                        F->h_group_nodes.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host vectors die on return
+  if (e != cudaSuccess) {
+    free_all(F);
+    delete F;
+    return cuda_fail(e);
+  }
+  *out = F;
+  return OCR_OK;
+}
+
+int ocr_forest_set_data(ocr_forest *F, const float *d_nodal, const float *d_tf, float s_min,
+                        float s_max, void *stream) {
+  (void)stream;
+  if (!F || !d_nodal || !d_tf || !(s_max > s_min) || !std::isfinite(s_min) ||
+      !std::isfinite(s_max))
+    return OCR_ERR_INVALID;
+  if (((uintptr_t)d_nodal & 15) || ((uintptr_t)d_tf & 15)) return OCR_ERR_INVALID;
+  F->d_nodal = d_nodal;
+  F->d_tf = d_tf;
+  F->s_min = s_min;
+  F->s_max = s_max;
+  F->has_data = true;
+  return OCR_OK;
+}
+
+int ocr_set_integrator(ocr_forest *F, const ocr_integrator *I) {
+  if (!F || !I) return OCR_ERR_INVALID;
+  if (I->method == OCR_RK4) {
+    if (I->nsteps < 1 || I->nsteps > 4096) return OCR_ERR_INVALID;
+  } else if (I->method == OCR_DOPRI5) {
+    if (!(I->tol > 0.f) || !(I->c_rk > 0.f) || I->max_depth < 0 || I->max_depth > 24)
+      return OCR_ERR_INVALID;
+  } else {
+    return OCR_ERR_UNSUPPORTED;
+  }
+  F->integ.method = I->method;
+  F->integ.nsteps = I->nsteps;
+  F->integ.tol = I->tol;
+  F->integ.c_rk = I->c_rk;
+  F->integ.max_depth = I->max_depth;
+  for (int c = 0; c < 3; ++c) F->integ.bg[c] = I->bg[c];
+  F->has_integ = true;
+  return OCR_OK;
+}
+
+int ocr_set_camera(ocr_forest *F, const ocr_camera *cams, int ncams) {
+  if (!F || !cams) return OCR_ERR_INVALID;
+  if (ncams != 1) return OCR_ERR_UNSUPPORTED;
+  const ocr_camera &c = cams[0];
+  if (c.w < 1 || c.h < 1 || (int64_t)c.w * c.h > (1ll << 31) - 1 || !(c.near_ > 0.0) ||
+      !(c.far_ > c.near_) || !(c.ell > 0.0))
+    return OCR_ERR_INVALID;
+  Cam &k = F->cam;
+  for (int a = 0; a < 3; ++a) {
+    k.o[a] = (float)c.o[a];
+    k.v[a] = (float)(c.ortho ? c.v[a] / c.near_ : c.v[a]);
+    k.lt[a] = (float)(c.ell * c.t[a]);
+    k.lu[a] = (float)(c.ell * c.u[a]);
+    k.t[a] = (float)c.t[a];
+    k.u[a] = (float)c.u[a];
+    k.vn[a] = (float)(c.v[a] / c.near_);
+  }
+  k.n = (float)c.near_;
+  k.f = (float)c.far_;
+  k.ell = (float)c.ell;
+  k.cw = 0.5f * (float)(c.w - 1);
+  k.ch = 0.5f * (float)(c.h - 1);
+  k.w = c.w;
+  k.h = c.h;
+  k.ortho = c.ortho ? 1 : 0;
+  k.amin = c.ortho ? 0.f : 1.f;
+  k.amax = (float)(c.ortho ? c.far_ : c.far_ / c.near_);
+  F->has_cam = true;
+  return OCR_OK;
+}
+
+int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats) {
+  if (!F || !d_rgba) return OCR_ERR_INVALID;
+  if (!F->has_data || !F->has_cam || !F->has_integ) return OCR_ERR_STATE;
+  if ((uintptr_t)d_rgba & 15) return OCR_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int G = (int)F->h_group_nodes.size();  // L + 1
+  Topo T{F->d_geo, F->d_child, F->N, F->M, F->L};
+  Field Fd{F->d_nodal, reinterpret_cast<const float4 *>(F->d_tf), F->s_min,
+           7.f / (F->s_max - F->s_min)};
+  Scratch S{F->d_rect, F->d_off, F->d_entries, F->d_stats, nullptr, nullptr, nullptr};
+  if (stats) {
+    S.counts = stats->d_counts;
+    S.visible = stats->d_visible;
+    if (S.counts)
+      OCR_CUDA(cudaMemsetAsync(S.counts, 0, sizeof(int) * (size_t)F->cam.w * F->cam.h, st));
+  }
+  const bool timed = stats && stats->time_phases;
+  if (timed && !F->ev[0])
+    for (cudaEvent_t &e : F->ev) OCR_CUDA(cudaEventCreate(&e));
+  int64_t launches = 0;
+  OCR_CUDA(cudaMemsetAsync(F->d_stats, 0, 8 * sizeof(unsigned long long), st));
+  if (timed) OCR_CUDA(cudaEventRecord(F->ev[0], st));
+
+  // prune: leaf rectangles; internal rectangles bottom-up; slot layout
+  OCR_CUDA(launch_cull_leaves(T, F->cam, S, st));
+  ++launches;
+  for (int l = F->L - 1; l >= 0; --l) {
+    OCR_CUDA(launch_union_level(T, F->level_base[l], F->level_base[l] + F->level_count[l], F->cam,
+                                S, st));
+    launches += F->level_count[l] > 0;
+  }
+  OCR_CUDA(launch_area_scan(T, S, F->d_block_sums, F->block_sums_cap, F->d_group_slots,
+                            F->d_group_nodes, G, st));
+  launches += area_scan_blocks(F->M) > 0 ? 4 : 1;
+  OCR_CUDA(cudaMemcpyAsync(F->h_group_slots, F->d_group_slots, sizeof(long long) * G,
+                           cudaMemcpyDeviceToHost, st));
+  OCR_CUDA(cudaStreamSynchronize(st));
+  const long long total = F->h_group_slots[G - 1];
+  if (total > F->entries_cap) {
+    cudaFree(F->d_entries);
+    F->d_entries = nullptr;
+    F->bytes -= F->entries_cap * (int64_t)sizeof(float4);
+    F->entries_cap = 0;
+    const long long cap = total + total / 8 + 1024;
+    int rc = dev_alloc(&F->d_entries, (size_t)cap, F->bytes);
+    if (rc) return rc;
+    F->entries_cap = cap;
+  }
+  S.entries = F->d_entries;
+  const long long nchunks = (total + kChunk - 1) / kChunk + 1;
+  if (nchunks > F->chunk_cap) {
+    cudaFree(F->d_chunk_node);
+    F->d_chunk_node = nullptr;
+    F->bytes -= F->chunk_cap * (int64_t)sizeof(int);
+    F->chunk_cap = 0;
+    const long long cap = nchunks + nchunks / 8 + 64;
+    int rc = dev_alloc(&F->d_chunk_node, (size_t)cap, F->bytes);
+    if (rc) return rc;
+    F->chunk_cap = cap;
+  }
+  S.chunk_node = F->d_chunk_node;
+  OCR_CUDA(launch_chunk_map(T, S, st));
+  launches += F->M > 0;
+  if (timed) OCR_CUDA(cudaEventRecord(F->ev[1], st));
+
+  // coarsening passes, deepest level first; group g covers level L - 1 - g
+  for (int g = 0; g + 1 < G; ++g) {
+    OCR_CUDA(launch_coarsen(T, Fd, F->cam, F->integ, S, F->h_group_nodes[g],
+                            F->h_group_nodes[g + 1], F->h_group_slots[g], F->h_group_slots[g + 1],
+                            nullptr, st));
+    launches += F->h_group_slots[g + 1] > F->h_group_slots[g];
+  }
+  // the super-root pass writes every pixel
+  OCR_CUDA(launch_coarsen(T, Fd, F->cam, F->integ, S, F->M, F->M, 0,
+                          (long long)F->cam.w * F->cam.h, reinterpret_cast<float4 *>(d_rgba), st));
+  ++launches;
+  if (timed) OCR_CUDA(cudaEventRecord(F->ev[2], st));
+
+  if (stats) {
+    stats->launches = launches;
+    if (stats->d_rects)
+      OCR_CUDA(cudaMemcpyAsync(stats->d_rects, F->d_rect, sizeof(int4) * (size_t)F->N,
+                               cudaMemcpyDeviceToDevice, st));
+    if (timed) {
+      OCR_CUDA(cudaEventSynchronize(F->ev[2]));
+      OCR_CUDA(cudaEventElapsedTime(&stats->ms_prune, F->ev[0], F->ev[1]));
+      OCR_CUDA(cudaEventElapsedTime(&stats->ms_merge, F->ev[1], F->ev[2]));
+    }
+    if (stats->fill_counters) {
+      unsigned long long h[8];
+      OCR_CUDA(cudaMemcpyAsync(F->h_group_slots + G, F->d_stats, sizeof(h), cudaMemcpyDeviceToHost,
+                               st));
+      OCR_CUDA(cudaStreamSynchronize(st));
+      memcpy(h, F->h_group_slots + G, sizeof(h));
+      stats->segments = (int64_t)h[0];
+      stats->rk_steps = (int64_t)h[1];
+      stats->leaf_tests = (int64_t)h[2];
+      stats->slots = (int64_t)h[3];
+      stats->visible_leaves = (int64_t)h[5];
+      if (h[4]) return OCR_ERR_DEVICE;
+    }
+  }
+  return OCR_OK;
+}
+
+int64_t ocr_device_bytes(const ocr_forest *F) { return F ? F->bytes : 0; }
+
+void ocr_destroy(ocr_forest *F) {
+  if (!F) return;
+  free_all(F);
+  delete F;
+}
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+// Internal declarations shared by the host API (ocr_capi.cu) and the kernels
+// (ocr_kernels.cu).  Not part of the public C ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ocr {
+
+// Camera constants in float32, derived once per ocr_set_camera.
+//  perspective: ray (i, j) = o + alpha r, r = v + (i - cw) lt + (j - ch) lu
+//  orthographic: origin o + (i - cw) lt + (j - ch) lu, direction v (= v/n)
+// (t, u, vn) are the rows of the camera transform X = (t, u, v/n)^T (x - o).
+struct Cam {
+  float o[3], v[3], lt[3], lu[3];
+  float t[3], u[3], vn[3];
+  float n, f, ell, cw, ch;
+  float amin, amax;
+  int w, h, ortho;
+};
+
+struct Integ {
+  int method;  // 0 = RK4 x nsteps, 1 = DOPRI5 inside Algorithm 1
+  int nsteps;
+  float tol, c_rk;
+  int max_depth;
+  float bg[3];
+};
+
+// Unified node numbering: [0, N) leaves in Morton order, [N, N + M) internal
+// octree nodes grouped by level from the deepest to the root, N + M the
+// super-root whose only child is the tree root.  geo = {x, y, z, level} with
+// anchors in units of 2^-L (level -1 for the super-root).
+struct Topo {
+  const int4 *geo;     // [N + M + 1]
+  const int *child;    // [(M + 1) * 8]  unified ids, -1 = none; slot = octant bx + 2 by + 4 bz
+  int N, M, L;
+};
+
+struct Field {
+  const float *nodal;  // [N * 8]
+  const float4 *tf;    // [8] (kappa, q_r, q_g, q_b) at the knots
+  float s_min, inv_ds7;  // knot position z = (s - s_min) * inv_ds7, inv_ds7 = 7 / (s_max - s_min)
+};
+
+struct Scratch {
+  int4 *rect;                // [N + M + 1] {i0, i1, j0, j1}; empty = {0, -1, 0, -1}
+  long long *off;            // [M + 1] exclusive prefix of internal-node rectangle areas
+  float4 *entries;           // [total slots] per (internal node, ray) aggregate (A, B_r, B_g, B_b)
+  unsigned long long *stats; // [8] 0 segments, 1 rk steps, 2 leaf tests, 3 slots, 4 device errors
+  int *counts;               // optional [w * h]
+  unsigned char *visible;    // optional [N]
+  int *chunk_node;           // [ceil(total / kChunk) + 1] internal node holding slot c * kChunk
+};
+
+// Slots are processed in chunks of kChunk consecutive slots, one chunk per CTA.
+constexpr int kChunk = 128;
+
+// Launch wrappers (ocr_kernels.cu).  All enqueue on `stream` and return the
+// launch error.
+cudaError_t launch_cull_leaves(const Topo &T, const Cam &C, Scratch S, cudaStream_t stream);
+cudaError_t launch_union_level(const Topo &T, int node_begin, int node_end, const Cam &C,
+                               Scratch S, cudaStream_t stream);
+cudaError_t launch_area_scan(const Topo &T, Scratch S, long long *d_block_sums, int nblk_cap,
+                             long long *d_level_slots, const int *d_level_nodes, int nlevels,
+                             cudaStream_t stream);
+int area_scan_blocks(int M);
+cudaError_t launch_chunk_map(const Topo &T, Scratch S, cudaStream_t stream);
+cudaError_t launch_coarsen(const Topo &T, const Field &Fd, const Cam &C, const Integ &I, Scratch S,
+                           int node_begin, int node_end, long long slot_begin, long long slot_end,
+                           float4 *rgba, cudaStream_t stream);
+
+}  // namespace ocr

@@ -1,0 +1,663 @@
+// CUDA kernels of the forest-of-octrees raycaster (sm_103a).
+//
+//   cull_leaves   - pixel rectangle of each leaf's camera-space bounding box
+//                   (Sec. 2.2, Sec. 3.1): the pruning step
+//   union_level   - rectangle of each internal octree node = bounding box of
+//                   its children's rectangles (one launch per level)
+//   area_scan     - exclusive prefix of the internal nodes' rectangle areas:
+//                   the slot (node, ray) layout of the per-level aggregates,
+//                   in Morton order (the load balance of Sec. 3.1 / 3.2)
+//   coarsen       - one octree level of Sec. 3.3: for every (node, ray) slot
+//                   of the level, the node's leaf children are intersected
+//                   with the ray and integrated in shared memory (Sec. 3.2,
+//                   Eqs. 2.22-2.23, Algorithm 1); the children's segments are
+//                   then combined nearest-first with Eq. 2.14 in the ray's
+//                   octant order, and the node's aggregate is stored.  The
+//                   last pass (the super-root) writes I_v = A I_b + B.
+#include "ocr_common.h"
+
+#include <cstdio>
+
+namespace ocr {
+namespace {
+
+constexpr float kOne = 1.0f;
+
+__device__ __forceinline__ float4 seg_identity() { return make_float4(1.f, 0.f, 0.f, 0.f); }
+
+// Eq. 2.14: (A2, B2) (+) (A1, B1) = (A2 A1, B2 + A2 B1), n = nearer, f = farther.
+__device__ __forceinline__ float4 seg_combine(float4 n, float4 f) {
+  return make_float4(n.x * f.x, fmaf(n.x, f.y, n.y), fmaf(n.x, f.z, n.z), fmaf(n.x, f.w, n.w));
+}
+
+__device__ __forceinline__ void pixel_ray(const Cam &c, int i, int j, float3 &org, float3 &dir) {
+  float di = (float)i - c.cw, dj = (float)j - c.ch;
+  float ox = fmaf(dj, c.lu[0], fmaf(di, c.lt[0], 0.f));
+  float oy = fmaf(dj, c.lu[1], fmaf(di, c.lt[1], 0.f));
+  float oz = fmaf(dj, c.lu[2], fmaf(di, c.lt[2], 0.f));
+  if (c.ortho) {
+    org = make_float3(c.o[0] + ox, c.o[1] + oy, c.o[2] + oz);
+    dir = make_float3(c.v[0], c.v[1], c.v[2]);
+  } else {
+    org = make_float3(c.o[0], c.o[1], c.o[2]);
+    dir = make_float3(c.v[0] + ox, c.v[1] + oy, c.v[2] + oz);
+  }
+}
+
+__device__ __forceinline__ float recip_or_zero(float d) { return d != 0.f ? 1.f / d : 0.f; }
+
+// Slab test of the ray against the axis-aligned box [lo, lo + h]^3, clipped to
+// [amin, amax].  A zero direction component keeps the ray inside the slab or
+// misses it entirely.
+__device__ __forceinline__ bool slab(float3 org, float3 dir, float3 inv, float3 lo, float h,
+                                     float amin, float amax, float &a_in, float &a_out) {
+  float t0 = amin, t1 = amax;
+  const float o[3] = {org.x, org.y, org.z}, d[3] = {dir.x, dir.y, dir.z};
+  const float iv[3] = {inv.x, inv.y, inv.z}, l[3] = {lo.x, lo.y, lo.z};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float b0 = l[a], b1 = l[a] + h;
+    if (d[a] == 0.f) {
+      if (o[a] < b0 || o[a] > b1) return false;
+    } else {
+      float s0 = (b0 - o[a]) * iv[a], s1 = (b1 - o[a]) * iv[a];
+      t0 = fmaxf(t0, fminf(s0, s1));
+      t1 = fminf(t1, fmaxf(s0, s1));
+    }
+  }
+  a_in = t0;
+  a_out = t1;
+  return t1 > t0;
+}
+
+__device__ __forceinline__ float3 node_lo(int4 g, float scale) {
+  return make_float3((float)g.x * scale, (float)g.y * scale, (float)g.z * scale);
+}
+
+// ------------------------------------------------------------------ medium --
+// The trilinear field along a straight segment is a cubic in the segment
+// parameter tau (tau = 0 at the far end, 1 at the near end): its four
+// coefficients are formed once per segment and each evaluation is three FMAs.
+struct Cubic {
+  float p0, p1, p2, p3;
+};
+
+__device__ __forceinline__ Cubic field_cubic(const float *__restrict__ nd, float3 a, float3 d) {
+  const float4 lo = __ldg(reinterpret_cast<const float4 *>(nd));
+  const float4 hi = __ldg(reinterpret_cast<const float4 *>(nd) + 1);
+  const float n0 = lo.x, n1 = lo.y, n2 = lo.z, n3 = lo.w, n4 = hi.x, n5 = hi.y, n6 = hi.z,
+              n7 = hi.w;
+  // monomial form of the trilinear interpolant in (U, V, W)
+  const float c0 = n0, cu = n1 - n0, cv = n2 - n0, cw = n4 - n0;
+  const float cuv = (n3 - n2) - (n1 - n0), cuw = (n5 - n4) - (n1 - n0),
+              cvw = (n6 - n4) - (n2 - n0);
+  const float cuvw = ((n7 - n6) - (n5 - n4)) - ((n3 - n2) - (n1 - n0));
+  // substitute U = a.x + tau d.x, V = a.y + tau d.y, W = a.z + tau d.z
+  Cubic c;
+  const float ab = a.x * a.y, ac = a.x * a.z, bc = a.y * a.z;
+  c.p0 = c0 + cu * a.x + cv * a.y + cw * a.z + cuv * ab + cuw * ac + cvw * bc + cuvw * ab * a.z;
+  c.p1 = cu * d.x + cv * d.y + cw * d.z + cuv * (a.x * d.y + a.y * d.x) +
+         cuw * (a.x * d.z + a.z * d.x) + cvw * (a.y * d.z + a.z * d.y) +
+         cuvw * (ab * d.z + ac * d.y + bc * d.x);
+  c.p2 = cuv * d.x * d.y + cuw * d.x * d.z + cvw * d.y * d.z +
+         cuvw * (a.x * d.y * d.z + a.y * d.x * d.z + a.z * d.x * d.y);
+  c.p3 = cuvw * d.x * d.y * d.z;
+  return c;
+}
+
+struct TF {
+  const float4 *v, *s;  // knot values and slopes (shared memory)
+  float s_min, inv;
+};
+
+// (kappa, q_r, q_g, q_b) at parameter tau: piecewise-linear transfer function
+// of the field value, constant outside the knot range.
+__device__ __forceinline__ float4 medium(const Cubic &c, const TF &tf, float tau) {
+  const float s = fmaf(fmaf(fmaf(c.p3, tau, c.p2), tau, c.p1), tau, c.p0);
+  float z = (s - tf.s_min) * tf.inv;
+  z = fminf(fmaxf(z, 0.f), 7.f);
+  const int k = min((int)z, 6);
+  const float w = z - (float)k;
+  const float4 a = tf.v[k], d = tf.s[k];
+  return make_float4(fmaf(w, d.x, a.x), fmaf(w, d.y, a.y), fmaf(w, d.z, a.z), fmaf(w, d.w, a.w));
+}
+
+// Right-hand side of Eq. 2.22 for the state Y = (A, B_r, B_g, B_b).
+__device__ __forceinline__ float4 rhs(float4 kq, float4 Y) {
+  return make_float4(-kq.x * Y.x, fmaf(-kq.x, Y.y, kq.y), fmaf(-kq.x, Y.z, kq.z),
+                     fmaf(-kq.x, Y.w, kq.w));
+}
+
+__device__ __forceinline__ float4 axpy(float a, float4 x, float4 y) {
+  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+
+// Classical RK4 from (1, 0) over one step of length H with the medium at the
+// step's far end (k0), midpoint (kh) and near end (k1).
+__device__ __forceinline__ float4 rk4_step(float H, float4 k0, float4 kh, float4 k1) {
+  const float4 one = seg_identity();
+  const float4 K1 = rhs(k0, one);
+  const float4 K2 = rhs(kh, axpy(0.5f * H, K1, one));
+  const float4 K3 = rhs(kh, axpy(0.5f * H, K2, one));
+  const float4 K4 = rhs(k1, axpy(H, K3, one));
+  float4 s = axpy(2.f, K2, K1);
+  s = axpy(2.f, K3, s);
+  s.x += K4.x; s.y += K4.y; s.z += K4.z; s.w += K4.w;
+  return axpy(H * (1.f / 6.f), s, one);
+}
+
+// Dormand & Prince (1980) 5(4) tableau.
+namespace dp {
+constexpr float c2 = 1.f / 5, c3 = 3.f / 10, c4 = 4.f / 5, c5 = 8.f / 9;
+constexpr float a21 = 1.f / 5;
+constexpr float a31 = 3.f / 40, a32 = 9.f / 40;
+constexpr float a41 = 44.f / 45, a42 = -56.f / 15, a43 = 32.f / 9;
+constexpr float a51 = 19372.f / 6561, a52 = -25360.f / 2187, a53 = 64448.f / 6561,
+                a54 = -212.f / 729;
+constexpr float a61 = 9017.f / 3168, a62 = -355.f / 33, a63 = 46732.f / 5247, a64 = 49.f / 176,
+                a65 = -5103.f / 18656;
+constexpr float b1 = 35.f / 384, b3 = 500.f / 1113, b4 = 125.f / 192, b5 = -2187.f / 6784,
+                b6 = 11.f / 84;
+// e = b - b* (fifth- minus fourth-order weights), seventh stage at the end point
+constexpr float e1 = 71.f / 57600, e3 = -71.f / 16695, e4 = 71.f / 1920, e5 = -17253.f / 339200,
+                e6 = 22.f / 525, e7 = -1.f / 40;
+}  // namespace dp
+
+__device__ __forceinline__ float4 lin4(float a, float4 x, float b, float4 y) {
+  return make_float4(fmaf(a, x.x, b * y.x), fmaf(a, x.y, b * y.y), fmaf(a, x.z, b * y.z),
+                     fmaf(a, x.w, b * y.w));
+}
+
+// (A, B) of one segment of world length dx: RK4 x nsteps, or DOPRI5 inside
+// the midpoint bisection of Algorithm 1, walked far half first so that each
+// accepted piece is nearer than everything accumulated so far.
+__device__ float4 integrate_segment(const Cubic &cu, const TF &tf, float dx, const Integ &I,
+                                    int &steps) {
+  float4 acc = seg_identity();
+  if (I.method == 0) {
+    const int n = I.nsteps;
+    const float H = dx / (float)n, dt = 1.f / (float)n;
+    float4 k0 = medium(cu, tf, 0.f);
+    for (int s = 0; s < n; ++s) {
+      const float t0 = (float)s * dt;
+      const float4 kh = medium(cu, tf, t0 + 0.5f * dt);
+      const float4 k1 = medium(cu, tf, (s + 1 == n) ? 1.f : t0 + dt);
+      acc = seg_combine(rk4_step(H, k0, kh, k1), acc);
+      k0 = k1;
+    }
+    steps += n;
+    return acc;
+  }
+  int depth = 0;
+  unsigned idx = 0;
+  float4 kq0 = medium(cu, tf, 0.f);
+  const float4 one = seg_identity();
+  for (;;) {
+    const float dtau = ldexpf(1.f, -depth);
+    const float t0 = (float)idx * dtau;
+    const float H = dx * dtau;
+    const float4 kq2 = medium(cu, tf, fmaf(dp::c2, dtau, t0));
+    const float4 kq3 = medium(cu, tf, fmaf(dp::c3, dtau, t0));
+    const float4 kq4 = medium(cu, tf, fmaf(dp::c4, dtau, t0));
+    const float4 kq5 = medium(cu, tf, fmaf(dp::c5, dtau, t0));
+    const float4 kq6 = medium(cu, tf, t0 + dtau);
+    const float4 K1 = rhs(kq0, one);
+    const float4 K2 = rhs(kq2, axpy(H * dp::a21, K1, one));
+    const float4 K3 = rhs(kq3, axpy(H, lin4(dp::a31, K1, dp::a32, K2), one));
+    float4 t = lin4(dp::a41, K1, dp::a42, K2);
+    t = axpy(dp::a43, K3, t);
+    const float4 K4 = rhs(kq4, axpy(H, t, one));
+    t = lin4(dp::a51, K1, dp::a52, K2);
+    t = axpy(dp::a53, K3, t);
+    t = axpy(dp::a54, K4, t);
+    const float4 K5 = rhs(kq5, axpy(H, t, one));
+    t = lin4(dp::a61, K1, dp::a62, K2);
+    t = axpy(dp::a63, K3, t);
+    t = axpy(dp::a64, K4, t);
+    t = axpy(dp::a65, K5, t);
+    const float4 K6 = rhs(kq6, axpy(H, t, one));
+    t = lin4(dp::b1, K1, dp::b3, K3);
+    t = axpy(dp::b4, K4, t);
+    t = axpy(dp::b5, K5, t);
+    t = axpy(dp::b6, K6, t);
+    const float4 Y5 = axpy(H, t, one);
+    const float4 K7 = rhs(kq6, Y5);
+    float4 e = lin4(dp::e1, K1, dp::e3, K3);
+    e = axpy(dp::e4, K4, e);
+    e = axpy(dp::e5, K5, e);
+    e = axpy(dp::e6, K6, e);
+    e = axpy(dp::e7, K7, e);
+    const float err = H * fmaxf(fmaxf(fabsf(e.x), fabsf(e.y)), fmaxf(fabsf(e.z), fabsf(e.w)));
+    const float kmax =
+        fmaxf(fmaxf(fmaxf(kq0.x, kq2.x), fmaxf(kq3.x, kq4.x)), fmaxf(kq5.x, kq6.x));
+    ++steps;
+    if (depth < I.max_depth && (H * kmax > I.c_rk || err > I.tol)) {
+      ++depth;  // far half first; it starts where this step started
+      idx <<= 1;
+      continue;
+    }
+    acc = seg_combine(Y5, acc);
+    kq0 = kq6;
+    ++idx;
+    while (depth > 0 && !(idx & 1u)) {
+      idx >>= 1;
+      --depth;
+    }
+    if (depth == 0) break;
+  }
+  return acc;
+}
+
+// ----------------------------------------------------------------- culling --
+__device__ __forceinline__ int4 empty_rect() { return make_int4(0, -1, 0, -1); }
+
+// Pixel rectangle of the camera-space bounding box of the cube [lo, lo+h]^3:
+// the box is mapped by X = (t, u, v/n)^T (x - o) (an affine map, so its AABB is
+// centre +- half-extent), clipped to the visible depth range, and projected.
+__device__ int4 box_rect(const Cam &c, float3 lo, float h) {
+  const float hh = 0.5f * h;
+  const float cx = lo.x + hh - c.o[0], cy = lo.y + hh - c.o[1], cz = lo.z + hh - c.o[2];
+  float X[3], E[3];
+  const float *rows[3] = {c.t, c.u, c.vn};
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const float *R = rows[r];
+    X[r] = fmaf(R[0], cx, fmaf(R[1], cy, R[2] * cz));
+    E[r] = hh * (fabsf(R[0]) + fabsf(R[1]) + fabsf(R[2]));
+  }
+  const float zlo = fmaxf(X[2] - E[2], c.ortho ? 0.f : c.n);
+  const float zhi = fminf(X[2] + E[2], c.f);
+  if (!(zlo <= zhi)) return empty_rect();
+  float pmin[2], pmax[2];
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const float x0 = X[a] - E[a], x1 = X[a] + E[a];
+    float lo_p, hi_p;
+    if (c.ortho) {
+      lo_p = x0 / c.ell;
+      hi_p = x1 / c.ell;
+    } else {
+      const float sl = c.n / (zlo * c.ell), sh = c.n / (zhi * c.ell);
+      lo_p = fminf(fminf(x0 * sl, x0 * sh), fminf(x1 * sl, x1 * sh));
+      hi_p = fmaxf(fmaxf(x0 * sl, x0 * sh), fmaxf(x1 * sl, x1 * sh));
+    }
+    const float cen = a == 0 ? c.cw : c.ch;
+    pmin[a] = lo_p + cen;
+    pmax[a] = hi_p + cen;
+  }
+  const float wl = (float)(c.w - 1), hl = (float)(c.h - 1);
+  const float i0 = fmaxf(ceilf(pmin[0]), 0.f), i1 = fminf(floorf(pmax[0]), wl);
+  const float j0 = fmaxf(ceilf(pmin[1]), 0.f), j1 = fminf(floorf(pmax[1]), hl);
+  if (!(i0 <= i1 && j0 <= j1)) return empty_rect();
+  return make_int4((int)i0, (int)i1, (int)j0, (int)j1);
+}
+
+__global__ void cull_leaves_kernel(Topo T, Cam c, Scratch S) {
+  const float scale = ldexpf(1.f, -T.L);
+  unsigned nvis = 0;
+  // the loop bound is warp-uniform so that the ballot below sees full warps
+  const int stride = gridDim.x * blockDim.x;
+  for (int k0 = blockIdx.x * blockDim.x; k0 < T.N; k0 += stride) {
+    const int k = k0 + threadIdx.x;
+    bool vis = false;
+    if (k < T.N) {
+      const int4 g = T.geo[k];
+      const int4 r = box_rect(c, node_lo(g, scale), ldexpf(1.f, -g.w));
+      S.rect[k] = r;
+      vis = r.x <= r.y;
+      if (S.visible) S.visible[k] = (unsigned char)vis;
+    }
+    nvis += __popc(__ballot_sync(0xffffffffu, vis));
+  }
+  if ((threadIdx.x & 31) == 0 && nvis) atomicAdd(S.stats + 5, (unsigned long long)nvis);
+}
+
+__global__ void union_level_kernel(Topo T, int nb, int ne, Scratch S) {
+  for (int k = nb + blockIdx.x * blockDim.x + threadIdx.x; k < ne; k += gridDim.x * blockDim.x) {
+    int4 u = make_int4(INT_MAX, INT_MIN, INT_MAX, INT_MIN);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int id = T.child[8 * k + c];
+      if (id < 0) continue;
+      const int4 r = S.rect[id];
+      if (r.x > r.y) continue;
+      u.x = min(u.x, r.x); u.y = max(u.y, r.y); u.z = min(u.z, r.z); u.w = max(u.w, r.w);
+    }
+    S.rect[T.N + k] = (u.x <= u.y) ? u : empty_rect();
+  }
+}
+
+// ------------------------------------------------------------------- scan --
+constexpr int kScanThreads = 256, kScanItems = 4, kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ long long rect_area(int4 r) {
+  return r.x > r.y ? 0ll : (long long)(r.y - r.x + 1) * (long long)(r.w - r.z + 1);
+}
+
+__device__ long long block_exclusive_scan(long long v, long long *warp_tot, long long &total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    long long w = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0ll;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    warp_tot[lane] = w;  // inclusive prefix of warp totals
+  }
+  __syncthreads();
+  total = warp_tot[(blockDim.x >> 5) - 1];
+  const long long before = wid ? warp_tot[wid - 1] : 0ll;
+  const long long r = before + x - v;
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) area_reduce_kernel(Topo T, Scratch S,
+                                                                   long long *block_sums) {
+  __shared__ long long wt[32];
+  const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  long long s = 0;
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q)
+    if (base + q < T.M) s += rect_area(S.rect[T.N + base + q]);
+  long long tot;
+  block_exclusive_scan(s, wt, tot);
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) block_sums_scan_kernel(long long *block_sums, int n) {
+  __shared__ long long wt[32];
+  long long carry = 0;
+  for (int b = 0; b < n; b += blockDim.x) {
+    const int k = b + threadIdx.x;
+    const long long v = k < n ? block_sums[k] : 0ll;
+    long long tot;
+    const long long ex = block_exclusive_scan(v, wt, tot);
+    if (k < n) block_sums[k] = carry + ex;
+    carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) block_sums[n] = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) area_downsweep_kernel(Topo T, Scratch S,
+                                                                      const long long *block_sums,
+                                                                      int nblk) {
+  __shared__ long long wt[32];
+  const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  long long a[kScanItems], s = 0;
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    a[q] = (base + q < T.M) ? rect_area(S.rect[T.N + base + q]) : 0ll;
+    s += a[q];
+  }
+  long long tot;
+  long long run = block_sums[blockIdx.x] + block_exclusive_scan(s, wt, tot);
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    if (base + q < T.M) S.off[base + q] = run;
+    run += a[q];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) S.off[T.M] = block_sums[nblk];
+}
+
+// chunk_node[c] = the internal node whose slot range holds slot c * kChunk
+__global__ void chunk_map_kernel(Topo T, Scratch S) {
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < T.M; n += gridDim.x * blockDim.x) {
+    const long long a = S.off[n], b = S.off[n + 1];
+    if (b <= a) continue;
+    for (long long c = (a + kChunk - 1) / kChunk; c * kChunk < b; ++c) S.chunk_node[c] = n;
+  }
+}
+
+__global__ void gather_level_slots_kernel(const long long *off, const int *level_nodes, int n,
+                                          long long *out) {
+  const int k = threadIdx.x;
+  if (k < n) out[k] = off[level_nodes[k]];
+}
+
+// ---------------------------------------------------------------- coarsen --
+constexpr int kCoarsenThreads = kChunk;
+
+struct Hit {
+  int leaf;
+  int slot_child;  // (thread slot << 3) | child octant
+  float a_in, a_out;
+};
+
+template <bool FINAL>
+__global__ void __launch_bounds__(kCoarsenThreads)
+    coarsen_kernel(Topo T, Field Fd, Cam c, Integ I, Scratch S, int nb, int ne, long long s0,
+                   long long s1, float4 *rgba) {
+  constexpr int NT = kCoarsenThreads;
+  __shared__ float4 s_tfv[8], s_tfs[8];
+  __shared__ float4 s_seg[8][NT];
+  __shared__ Hit s_hit[8 * NT];
+  __shared__ int2 s_pix[NT];
+  __shared__ int s_nhit;
+  __shared__ unsigned long long s_cnt[4];
+
+  const int tid = threadIdx.x;
+  if (tid < 8) {
+    const float4 v = Fd.tf[tid];
+    const float4 w = Fd.tf[tid < 7 ? tid + 1 : 7];
+    s_tfv[tid] = v;
+    s_tfs[tid] = make_float4(w.x - v.x, w.y - v.y, w.z - v.z, w.w - v.w);
+  }
+  if (tid < 4) s_cnt[tid] = 0ull;
+  if (tid == 0) s_nhit = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s_seg[q][tid] = seg_identity();
+
+  // non-final passes work on whole chunks of the global slot space, so that
+  // chunk_node gives the first node of the CTA without a search
+  const long long chunk = FINAL ? 0 : s0 / NT + blockIdx.x;
+  const long long slot = FINAL ? s0 + (long long)blockIdx.x * NT + tid : chunk * NT + tid;
+  const bool active = slot >= s0 && slot < s1;
+  int node = T.M;  // super-root in the final pass
+  int i = 0, j = 0;
+  if (active) {
+    if (FINAL) {
+      i = (int)(slot % c.w);
+      j = (int)(slot / c.w);
+    } else {
+      // the chunk's slots lie in the nodes [chunk_node[chunk], chunk_node[chunk + 1]]
+      const long long nch = (S.off[T.M] + NT - 1) / NT;
+      int lo = max(S.chunk_node[chunk], nb);
+      int hi = (chunk + 1 < nch) ? min(S.chunk_node[chunk + 1], ne - 1) + 1 : ne;
+      while (lo < hi) {  // first node whose offset exceeds the slot
+        const int mid = (lo + hi) >> 1;
+        if (S.off[mid] <= slot) lo = mid + 1; else hi = mid;
+      }
+      node = lo - 1;
+      const int4 r = S.rect[T.N + node];
+      const long long local = slot - S.off[node];
+      const int rw = r.y - r.x + 1;
+      i = r.x + (int)(local % rw);
+      j = r.z + (int)(local / rw);
+    }
+  }
+  s_pix[tid] = make_int2(i, j);
+  int ch[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) ch[q] = active ? __ldg(T.child + 8 * node + q) : -1;
+  __syncthreads();
+
+  float3 org, dir;
+  pixel_ray(c, i, j, org, dir);
+  const float3 inv = make_float3(recip_or_zero(dir.x), recip_or_zero(dir.y), recip_or_zero(dir.z));
+  const float scale = ldexpf(1.f, -T.L);
+
+  // phase 1: slab tests against the leaf children whose rectangle holds the ray
+  unsigned local_tests = 0, local_hits = 0;
+  if (active) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int id = ch[q];
+      if (id < 0 || id >= T.N) continue;
+      const int4 r = S.rect[id];
+      if (i < r.x || i > r.y || j < r.z || j > r.w) continue;
+      ++local_tests;
+      const int4 g = T.geo[id];
+      float a0, a1;
+      if (slab(org, dir, inv, node_lo(g, scale), ldexpf(1.f, -g.w), c.amin, c.amax, a0, a1)) {
+        const int h = atomicAdd(&s_nhit, 1);
+        s_hit[h] = Hit{id, (tid << 3) | q, a0, a1};
+        ++local_hits;
+      }
+    }
+    if (local_hits && S.counts) atomicAdd(S.counts + (size_t)j * c.w + i, (int)local_hits);
+  }
+  __syncthreads();
+
+  // phase 2: integrate the hits, one per thread, into s_seg[child][slot]
+  const int nh = s_nhit;
+  TF tf{s_tfv, s_tfs, Fd.s_min, Fd.inv_ds7};
+  int steps = 0;
+  for (int h = tid; h < nh; h += NT) {
+    const Hit H = s_hit[h];
+    const int st = H.slot_child >> 3, q = H.slot_child & 7;
+    const int2 p = s_pix[st];
+    float3 o2, d2;
+    pixel_ray(c, p.x, p.y, o2, d2);
+    const int4 g = T.geo[H.leaf];
+    const float ih = ldexpf(1.f, g.w);  // 1 / edge length
+    const float3 lo = node_lo(g, scale);
+    // reference coordinates of the far end and their change to the near end
+    const float3 ufar = make_float3((fmaf(H.a_out, d2.x, o2.x) - lo.x) * ih,
+                                    (fmaf(H.a_out, d2.y, o2.y) - lo.y) * ih,
+                                    (fmaf(H.a_out, d2.z, o2.z) - lo.z) * ih);
+    const float da = H.a_in - H.a_out;
+    const float3 du = make_float3(da * d2.x * ih, da * d2.y * ih, da * d2.z * ih);
+    const float dx = (H.a_out - H.a_in) * sqrtf(d2.x * d2.x + d2.y * d2.y + d2.z * d2.z);
+    const Cubic cu = field_cubic(Fd.nodal + 8 * (size_t)H.leaf, ufar, du);
+    s_seg[q][st] = integrate_segment(cu, tf, dx, I, steps);
+  }
+  __syncthreads();
+
+  // phase 3: combine the children nearest-first.  Along a ray with direction
+  // signs (sx, sy, sz) the octants come in increasing order of q ^ mask; the
+  // same sequence is formed by combining along x, then y, then z, each pair
+  // nearer-first (Eq. 2.14 is associative), with every index static.
+  if (active) {
+    float4 cs[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int id = ch[q];
+      float4 s = seg_identity();
+      if (id >= 0 && id < T.N) {
+        s = s_seg[q][tid];
+      } else if (id >= T.N) {
+        const int4 r = S.rect[id];
+        if (i >= r.x && i <= r.y && j >= r.z && j <= r.w) {
+          const long long e =
+              S.off[id - T.N] + (long long)(j - r.z) * (r.y - r.x + 1) + (i - r.x);
+          s = S.entries[e];
+        }
+      }
+      cs[q] = s;
+    }
+    const bool fx = dir.x < 0.f, fy = dir.y < 0.f, fz = dir.z < 0.f;
+    float4 px[4], py[2];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      px[q] = fx ? seg_combine(cs[2 * q + 1], cs[2 * q]) : seg_combine(cs[2 * q], cs[2 * q + 1]);
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      py[q] = fy ? seg_combine(px[2 * q + 1], px[2 * q]) : seg_combine(px[2 * q], px[2 * q + 1]);
+    const float4 acc = fz ? seg_combine(py[1], py[0]) : seg_combine(py[0], py[1]);
+    if (FINAL) {
+      rgba[slot] = make_float4(fmaf(acc.x, I.bg[0], acc.y), fmaf(acc.x, I.bg[1], acc.z),
+                               fmaf(acc.x, I.bg[2], acc.w), kOne - acc.x);
+    } else {
+      S.entries[slot] = acc;
+    }
+  }
+
+  // counters: segments, RK steps, leaf tests, slots
+  unsigned long long v[4] = {local_hits, (unsigned long long)steps, local_tests,
+                             active ? 1ull : 0ull};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    unsigned long long x = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if ((tid & 31) == 0 && x) atomicAdd(&s_cnt[q], x);
+  }
+  __syncthreads();
+  if (tid < 4 && s_cnt[tid]) atomicAdd(S.stats + tid, s_cnt[tid]);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- launchers --
+static int grid_for(long long n, int threads, int cap = 152 * 16) {
+  long long g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  return (int)(g > cap ? cap : g);
+}
+
+cudaError_t launch_cull_leaves(const Topo &T, const Cam &C, Scratch S, cudaStream_t stream) {
+  cull_leaves_kernel<<<grid_for(T.N, 256), 256, 0, stream>>>(T, C, S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_union_level(const Topo &T, int nb, int ne, const Cam &C, Scratch S,
+                               cudaStream_t stream) {
+  (void)C;
+  if (ne <= nb) return cudaSuccess;
+  union_level_kernel<<<grid_for(ne - nb, 256), 256, 0, stream>>>(T, nb, ne, S);
+  return cudaGetLastError();
+}
+
+int area_scan_blocks(int M) { return (M + kScanTile - 1) / kScanTile; }
+
+cudaError_t launch_area_scan(const Topo &T, Scratch S, long long *block_sums, int nblk_cap,
+                             long long *level_slots, const int *level_nodes, int nlevels,
+                             cudaStream_t stream) {
+  const int nblk = area_scan_blocks(T.M);
+  if (nblk + 1 > nblk_cap) return cudaErrorInvalidValue;
+  if (nblk > 0) {
+    area_reduce_kernel<<<nblk, kScanThreads, 0, stream>>>(T, S, block_sums);
+    block_sums_scan_kernel<<<1, 1024, 0, stream>>>(block_sums, nblk);
+    area_downsweep_kernel<<<nblk, kScanThreads, 0, stream>>>(T, S, block_sums, nblk);
+  } else {
+    cudaMemsetAsync(S.off, 0, sizeof(long long), stream);
+  }
+  if (nlevels > 1024) return cudaErrorInvalidValue;
+  gather_level_slots_kernel<<<1, 1024, 0, stream>>>(S.off, level_nodes, nlevels, level_slots);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chunk_map(const Topo &T, Scratch S, cudaStream_t stream) {
+  if (T.M < 1) return cudaSuccess;
+  chunk_map_kernel<<<grid_for(T.M, 256), 256, 0, stream>>>(T, S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarsen(const Topo &T, const Field &Fd, const Cam &C, const Integ &I,
+                           Scratch S, int nb, int ne, long long s0, long long s1, float4 *rgba,
+                           cudaStream_t stream) {
+  if (s1 <= s0) return cudaSuccess;
+  const long long nblk = rgba ? (s1 - s0 + kCoarsenThreads - 1) / kCoarsenThreads
+                              : (s1 - 1) / kCoarsenThreads - s0 / kCoarsenThreads + 1;
+  if (nblk > 0x7fffffffll) return cudaErrorInvalidValue;
+  if (rgba)
+    coarsen_kernel<true><<<(unsigned)nblk, kCoarsenThreads, 0, stream>>>(T, Fd, C, I, S, nb, ne,
+                                                                          s0, s1, rgba);
+  else
+    coarsen_kernel<false><<<(unsigned)nblk, kCoarsenThreads, 0, stream>>>(T, Fd, C, I, S, nb, ne,
+                                                                           s0, s1, nullptr);
+  return cudaGetLastError();
+}
+
+}  // namespace ocr

@@ -1,0 +1,95 @@
+"""Renderer: the library's handle plus the torch tensors it reads and writes."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import capi
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+class Renderer:
+    """Owns one ``ocr_forest`` handle.
+
+    ``forest``: an ``inputs.Forest``; ``tf``: an ``inputs.TransferFunction``;
+    ``integ``: {"method": "rk4", "nsteps": n} or {"method": "dopri5", "tol",
+    "c_rk", "max_depth"}.  Nodal data and knots are copied to the device once;
+    ``set_data`` replaces them (e.g. with tensors the caller updates).
+    """
+
+    def __init__(self, forest, tf, integ: dict, device="cuda", bg=(0.0, 0.0, 0.0)):
+        if not torch.cuda.is_available():
+            raise RuntimeError("Renderer needs a CUDA device")
+        self.device = torch.device(device)
+        self.forest = forest
+        s = _stream_ptr(None)
+        self.h = capi.build_forest(forest.level, forest.anchor, forest.max_level, stream=s)
+        self.nodal = torch.from_numpy(np.ascontiguousarray(forest.nodal, np.float32)).to(self.device)
+        self.tf = torch.from_numpy(np.ascontiguousarray(tf.knots, np.float32)).to(self.device)
+        self.s_min, self.s_max = float(tf.s_min), float(tf.s_max)
+        capi.forest_set_data(self.h, self.nodal, self.tf, self.s_min, self.s_max, s)
+        self.set_integrator(integ, bg)
+        self.cam = None
+
+    def set_data(self, nodal: torch.Tensor, tf: torch.Tensor, s_min=None, s_max=None):
+        assert nodal.is_cuda and nodal.dtype == torch.float32 and nodal.is_contiguous()
+        assert tf.is_cuda and tf.dtype == torch.float32 and tf.is_contiguous()
+        self.nodal, self.tf = nodal, tf
+        if s_min is not None:
+            self.s_min, self.s_max = float(s_min), float(s_max)
+        capi.forest_set_data(self.h, self.nodal, self.tf, self.s_min, self.s_max,
+                             _stream_ptr(None))
+
+    def set_integrator(self, integ: dict, bg=(0.0, 0.0, 0.0)):
+        if integ["method"] == "rk4":
+            capi.set_integrator(self.h, capi.RK4, nsteps=integ.get("nsteps", 4), bg=bg)
+        elif integ["method"] == "dopri5":
+            capi.set_integrator(self.h, capi.DOPRI5, tol=integ.get("tol", 1e-6),
+                                c_rk=integ.get("c_rk", 0.5), max_depth=integ.get("max_depth", 16),
+                                bg=bg)
+        else:
+            raise ValueError(integ["method"])
+
+    def set_camera(self, cam):
+        capi.set_camera(self.h, cam.o, cam.v, cam.t, cam.u, cam.ell, cam.near, cam.far, cam.w,
+                        cam.h, cam.ortho)
+        self.cam = cam
+
+    def render(self, out: torch.Tensor | None = None, stream=None, with_index=False,
+               fill_counters=False, time_phases=False):
+        """Render into ``out`` ([h, w, 4] float32 on the device).  With
+        ``with_index`` also return per-ray segment counts, per-leaf visibility
+        and pixel rectangles."""
+        cam = self.cam
+        if out is None:
+            out = torch.empty((cam.h, cam.w, 4), dtype=torch.float32, device=self.device)
+        extra = {}
+        if with_index:
+            extra["counts"] = torch.empty((cam.h, cam.w), dtype=torch.int32, device=self.device)
+            extra["visible"] = torch.empty(self.forest.nleaves, dtype=torch.uint8, device=self.device)
+            extra["rects"] = torch.empty((self.forest.nleaves, 4), dtype=torch.int32,
+                                         device=self.device)
+        st = capi.render(self.h, out, _stream_ptr(stream), d_counts=extra.get("counts"),
+                         d_visible=extra.get("visible"), d_rects=extra.get("rects"),
+                         fill_counters=fill_counters or with_index, time_phases=time_phases)
+        st.update(extra)
+        return out, st
+
+    def device_bytes(self) -> int:
+        return capi.device_bytes(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            capi.destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

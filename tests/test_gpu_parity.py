@@ -1,0 +1,128 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Images: max |delta| <= 1e-4 per RGBA channel.  Index results (visible-leaf
+set, pixel rectangles, per-ray segment counts): bit-exact, except for the
+decisions the oracle flags as lying within the FP32 tie band (a pixel centre
+within 4e-3 px of a rectangle edge, or a chord shorter than 2e-6 relative),
+which are counted and must stay rare.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1809_01334_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+BAND_PX, BAND_REL = 4e-3, 2e-6
+
+
+def _renderer(forest, tf, integ, cam, bg=(0.0, 0.0, 0.0)):
+    from paper_1809_01334_gb300 import Renderer
+    r = Renderer(forest, tf, integ, bg=bg)
+    r.set_camera(cam)
+    return r
+
+
+def _compare(forest, tf, cam, integ, rows=None, bg=(0.0, 0.0, 0.0), max_unc_frac=0.02):
+    r = _renderer(forest, tf, integ, cam, bg)
+    img, st = r.render(with_index=True)
+    torch.cuda.synchronize()
+    ref = O.render(forest, tf, cam, integ, rows=rows, bg=bg, band_px=BAND_PX, band_rel=BAND_REL)
+    rr = ref["rows"]
+    got = img.cpu().numpy().astype(np.float64)[rr]
+    err = np.abs(got - ref["rgba"]).max()
+    assert err <= TOL, f"max |delta| = {err:.3e}"
+    counts = st["counts"].cpu().numpy()[rr]
+    unc = ref["uncertain"]
+    assert unc.mean() <= max_unc_frac, f"tie-band rays {unc.mean():.3%}"
+    bad = (counts != ref["counts"]) & ~unc
+    assert not bad.any(), f"{bad.sum()} rays with different segment counts"
+    cull = O.cull(forest, tf, cam, band_px=BAND_PX)
+    vis = st["visible"].cpu().numpy().astype(bool)
+    assert not ((vis != cull["visible"]) & ~cull["uncertain"]).any()
+    rects = st["rects"].cpu().numpy()
+    same = (rects == cull["rect"]).all(axis=1)
+    assert not (~same & ~cull["uncertain"] & cull["visible"]).any()
+    if rows is None:
+        assert st["segments"] == int(counts.sum())
+        assert st["visible_leaves"] == int(vis.sum())
+    r.close()
+    return err, st, ref
+
+
+def test_c1_uniform_orthographic_rk4():
+    """C1: 512 leaves, orthographic 64x64, RK4 x 4: every ray has 8 segments."""
+    f, tf, cam, integ = I.preset_c1()
+    err, st, ref = _compare(f, tf, cam, integ, max_unc_frac=0.0)
+    assert st["segments"] == 64 * 64 * 8 and st["visible_leaves"] == 512
+    assert st["rk_steps"] == 64 * 64 * 8 * 4
+
+
+@pytest.mark.parametrize("integ", [{"method": "rk4", "nsteps": 4},
+                                   {"method": "dopri5", "tol": 1e-6, "c_rk": 0.5, "max_depth": 16}])
+def test_small_adaptive_perspective(integ):
+    """Adaptive 2:1-balanced mesh (levels 3-4), perspective 48x40 image."""
+    f, tf, cam = I.preset_small()
+    _compare(f, tf, cam, integ)
+
+
+@pytest.mark.parametrize("shape", [(37, 23), (1, 1), (129, 3), (5, 97)])
+def test_ragged_images(shape):
+    """Image sizes that are not multiples of any tile, including 1x1.  With an
+    odd width the centre column of this target-centred camera (up = +z) runs
+    exactly through the grid edge x = y = 1/2, and the 1x1 ray through the
+    cube's centre vertex: genuine ties, which the oracle flags; every other
+    ray must match."""
+    f, tf, cam = I.preset_small(w=shape[0], h=shape[1], cam_seed=3)
+    _compare(f, tf, cam, {"method": "dopri5", "tol": 1e-6, "c_rk": 0.5, "max_depth": 16},
+             max_unc_frac=1.0 / shape[0] + 0.02)
+
+
+def test_adaptive_levels_1_to_5_with_background():
+    fld = I.gaussian_field(16, 99)
+    f = I.adaptive_cube_forest(fld, 1, 5, 0.3, balance=True)
+    assert len(np.unique(f.level)) >= 3
+    tf = I.transfer_function(f.nodal, 5)
+    cam = I.perspective_camera(21, 64, 48, dist=(1.6, 2.0))
+    _compare(f, tf, cam, {"method": "dopri5", "tol": 1e-6, "c_rk": 0.5, "max_depth": 16},
+             bg=(0.3, 0.2, 0.1))
+
+
+def test_single_leaf_forest_and_empty_view():
+    fld = I.gaussian_field(4, 1809)
+    f = I.uniform_cube_forest(0, fld)
+    tf = I.transfer_function(f.nodal)
+    cam = I.perspective_camera(7, 20, 16, dist=(1.5, 1.6))
+    _compare(f, tf, cam, {"method": "rk4", "nsteps": 8})
+    # a camera looking away from the cube: background everywhere, nothing visible
+    away = I.Camera(o=(0.5, 0.5, 3.0), v=(0.0, 0.0, 0.1), t=(1.0, 0, 0), u=(0, 1.0, 0),
+                    ell=0.001, near=0.1, far=100.0, w=16, h=8)
+    f2, tf2, _ = I.preset_small()
+    r = _renderer(f2, tf2, {"method": "rk4", "nsteps": 4}, away, bg=(0.5, 0.25, 0.125))
+    img, st = r.render(with_index=True)
+    assert st["segments"] == 0 and st["visible_leaves"] == 0
+    np.testing.assert_array_equal(img.cpu().numpy().reshape(-1, 4),
+                                  np.tile([0.5, 0.25, 0.125, 0.0], (16 * 8, 1)))
+
+
+def test_deterministic():
+    f, tf, cam = I.preset_small()
+    r = _renderer(f, tf, {"method": "dopri5", "tol": 1e-6, "c_rk": 0.5, "max_depth": 16}, cam)
+    a, _ = r.render()
+    a = a.clone()
+    b, _ = r.render()
+    assert torch.equal(a, b)
+
+
+def test_c2_full_size_sampled_rows():
+    """C2 at its full size (2,053,451 leaves, 1920x1080, DOPRI5 tol 1e-6) in
+    the launch configuration the benchmark times; the oracle checks 12 rows
+    spread over the image, every pixel of them."""
+    f, tf, cam, integ = I.preset_c2()
+    rows = np.linspace(cam.h * 0.2, cam.h * 0.8, 12).astype(np.int32)
+    err, st, ref = _compare(f, tf, cam, integ, rows=rows)
+    assert st["visible_leaves"] == f.nleaves
+    assert st["segments"] > 20_000_000
