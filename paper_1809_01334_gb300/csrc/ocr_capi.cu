@@ -27,6 +27,8 @@ struct ocr_forest {
   std::vector<int> h_group_nodes;     // [L + 1] group boundaries, deepest level first, then M
   int4 *d_geo = nullptr;              // [N + M + 1]
   int *d_child = nullptr;             // [(M + 1) * 8]
+  int2 *d_leaves = nullptr;           // [M] leaf range of each internal node
+  int lt = 0;                         // tile level: deepest level with stored aggregates
   int *d_group_nodes = nullptr;       // [L + 1]
   // data
   const float *d_nodal = nullptr;
@@ -100,6 +102,7 @@ int dev_alloc(T **p, size_t n, int64_t &bytes) {
 void free_all(ocr_forest *F) {
   cudaFree(F->d_geo);
   cudaFree(F->d_child);
+  cudaFree(F->d_leaves);
   cudaFree(F->d_group_nodes);
   cudaFree(F->d_rect);
   cudaFree(F->d_off);
@@ -242,6 +245,16 @@ int ocr_build_forest(const ocr_forest_desc *desc, void *stream, ocr_forest **out
     return OCR_ERR_INVALID;
   }
   child[(size_t)M * 8] = F->root;  // super-root: one child, the tree root
+  // leaves of each internal node: a contiguous range of the Morton-sorted leaves
+  std::vector<int2> lrange((size_t)(M > 0 ? M : 1));
+  for (int l = L - 1; l >= 0; --l)
+    for (int q = 0; q < F->level_count[l]; ++q) {
+      const uint64_t k0 = ikeys[l][q], k1 = k0 + (1ull << (3 * (L - l)));
+      const int a = (int)(std::lower_bound(key.begin(), key.end(), k0) - key.begin());
+      const int b = (int)(std::lower_bound(key.begin(), key.end(), k1) - key.begin());
+      lrange[(size_t)F->level_base[l] + q] = make_int2(a, b);
+    }
+  F->lt = L > kSubtreeDepth ? L - kSubtreeDepth : 0;
 
   // group boundaries: internal levels from the deepest, then M
   for (int l = L - 1; l >= 0; --l) F->h_group_nodes.push_back(F->level_base[l]);
@@ -250,6 +263,7 @@ int ocr_build_forest(const ocr_forest_desc *desc, void *stream, ocr_forest **out
   int rc;
   if ((rc = dev_alloc(&F->d_geo, geo.size(), F->bytes)) ||
       (rc = dev_alloc(&F->d_child, child.size(), F->bytes)) ||
+      (rc = dev_alloc(&F->d_leaves, lrange.size(), F->bytes)) ||
       (rc = dev_alloc(&F->d_group_nodes, F->h_group_nodes.size(), F->bytes)) ||
       (rc = dev_alloc(&F->d_rect, (size_t)N + M + 1, F->bytes)) ||
       (rc = dev_alloc(&F->d_off, (size_t)M + 1, F->bytes)) ||
@@ -276,6 +290,9 @@ int ocr_build_forest(const ocr_forest_desc *desc, void *stream, ocr_forest **out
                                   cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(F->d_child, child.data(), child.size() * sizeof(int),
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(F->d_leaves, lrange.data(), lrange.size() * sizeof(int2),
                         cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(F->d_group_nodes, F->h_group_nodes.data(),
@@ -362,7 +379,7 @@ int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats) {
   if ((uintptr_t)d_rgba & 15) return OCR_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   const int G = (int)F->h_group_nodes.size();  // L + 1
-  Topo T{F->d_geo, F->d_child, F->N, F->M, F->L};
+  Topo T{F->d_geo, F->d_child, F->d_leaves, F->N, F->M, F->L, F->lt};
   Field Fd{F->d_nodal, reinterpret_cast<const float4 *>(F->d_tf), F->s_min,
            7.f / (F->s_max - F->s_min)};
   Scratch S{F->d_rect, F->d_off, F->d_entries, F->d_stats, nullptr, nullptr, nullptr};
@@ -421,12 +438,20 @@ int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats) {
   launches += F->M > 0;
   if (timed) OCR_CUDA(cudaEventRecord(F->ev[1], st));
 
-  // coarsening passes, deepest level first; group g covers level L - 1 - g
+  // group g covers level L - 1 - g.  Levels below the tile level hold no
+  // slots; the tile level runs the subtree pass, the levels above it the
+  // coarsening passes, deepest first.
   for (int g = 0; g + 1 < G; ++g) {
-    OCR_CUDA(launch_coarsen(T, Fd, F->cam, F->integ, S, F->h_group_nodes[g],
-                            F->h_group_nodes[g + 1], F->h_group_slots[g], F->h_group_slots[g + 1],
-                            nullptr, st));
-    launches += F->h_group_slots[g + 1] > F->h_group_slots[g];
+    const int level = F->L - 1 - g;
+    const long long a = F->h_group_slots[g], b = F->h_group_slots[g + 1];
+    if (b <= a) continue;
+    if (level == F->lt)
+      OCR_CUDA(launch_subtree(T, Fd, F->cam, F->integ, S, F->h_group_nodes[g],
+                              F->h_group_nodes[g + 1], a, b, st));
+    else
+      OCR_CUDA(launch_coarsen(T, Fd, F->cam, F->integ, S, F->h_group_nodes[g],
+                              F->h_group_nodes[g + 1], a, b, nullptr, st));
+    ++launches;
   }
   // the super-root pass writes every pixel
   OCR_CUDA(launch_coarsen(T, Fd, F->cam, F->integ, S, F->M, F->M, 0,

@@ -30,11 +30,22 @@ struct Integ {
 // octree nodes grouped by level from the deepest to the root, N + M the
 // super-root whose only child is the tree root.  geo = {x, y, z, level} with
 // anchors in units of 2^-L (level -1 for the super-root).
+// Internal nodes deeper than the tile level lt keep no per-ray aggregates: the
+// subtree pass handles each tile-level node's whole subtree (depth L - lt <= 3)
+// in one thread per ray.
 struct Topo {
   const int4 *geo;     // [N + M + 1]
   const int *child;    // [(M + 1) * 8]  unified ids, -1 = none; slot = octant bx + 2 by + 4 bz
-  int N, M, L;
+  const int2 *leaves;  // [M] Morton range [first, last + 1) of each internal node's leaves
+  int N, M, L, lt;
 };
+
+// Subtree pass: a ray crosses at most 3 * 2^D - 2 = 22 cells of a depth-3
+// subtree; the per-ray list holds 24 to leave room for rays running exactly
+// along cell faces (closed slab tests accept both sides).  Overflow is counted
+// as a device error.
+constexpr int kSubtreeDepth = 3;
+constexpr int kMaxSubtreeHits = 24;
 
 struct Field {
   const float *nodal;  // [N * 8]
@@ -65,6 +76,9 @@ cudaError_t launch_area_scan(const Topo &T, Scratch S, long long *d_block_sums, 
                              cudaStream_t stream);
 int area_scan_blocks(int M);
 cudaError_t launch_chunk_map(const Topo &T, Scratch S, cudaStream_t stream);
+cudaError_t launch_subtree(const Topo &T, const Field &Fd, const Cam &C, const Integ &I, Scratch S,
+                           int node_begin, int node_end, long long slot_begin, long long slot_end,
+                           cudaStream_t stream);
 cudaError_t launch_coarsen(const Topo &T, const Field &Fd, const Cam &C, const Integ &I, Scratch S,
                            int node_begin, int node_end, long long slot_begin, long long slot_end,
                            float4 *rgba, cudaStream_t stream);

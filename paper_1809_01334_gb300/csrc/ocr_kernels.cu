@@ -334,6 +334,11 @@ __device__ __forceinline__ long long rect_area(int4 r) {
   return r.x > r.y ? 0ll : (long long)(r.y - r.x + 1) * (long long)(r.w - r.z + 1);
 }
 
+// slots of internal node k: its rectangle's area, or none below the tile level
+__device__ __forceinline__ long long node_slots(const Topo &T, const Scratch &S, int k) {
+  return T.geo[T.N + k].w > T.lt ? 0ll : rect_area(S.rect[T.N + k]);
+}
+
 __device__ long long block_exclusive_scan(long long v, long long *warp_tot, long long &total) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   long long x = v;
@@ -368,7 +373,7 @@ __global__ void __launch_bounds__(kScanThreads) area_reduce_kernel(Topo T, Scrat
   long long s = 0;
 #pragma unroll
   for (int q = 0; q < kScanItems; ++q)
-    if (base + q < T.M) s += rect_area(S.rect[T.N + base + q]);
+    if (base + q < T.M) s += node_slots(T, S, base + q);
   long long tot;
   block_exclusive_scan(s, wt, tot);
   if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
@@ -397,7 +402,7 @@ __global__ void __launch_bounds__(kScanThreads) area_downsweep_kernel(Topo T, Sc
   long long a[kScanItems], s = 0;
 #pragma unroll
   for (int q = 0; q < kScanItems; ++q) {
-    a[q] = (base + q < T.M) ? rect_area(S.rect[T.N + base + q]) : 0ll;
+    a[q] = (base + q < T.M) ? node_slots(T, S, base + q) : 0ll;
     s += a[q];
   }
   long long tot;
@@ -428,21 +433,290 @@ __global__ void gather_level_slots_kernel(const long long *off, const int *level
 // ---------------------------------------------------------------- coarsen --
 constexpr int kCoarsenThreads = kChunk;
 
-struct Hit {
-  int leaf;
-  int slot_child;  // (thread slot << 3) | child octant
+// Node and pixel of a slot of the non-final passes.  The CTA's chunk of slots
+// lies in the nodes [chunk_node[chunk], chunk_node[chunk + 1]].
+__device__ __forceinline__ void slot_lookup(const Topo &T, const Scratch &S, int nb, int ne,
+                                            long long chunk, long long slot, int &node, int &i,
+                                            int &j) {
+  const long long nch = (S.off[T.M] + kChunk - 1) / kChunk;
+  int lo = max(S.chunk_node[chunk], nb);
+  int hi = (chunk + 1 < nch) ? min(S.chunk_node[chunk + 1], ne - 1) + 1 : ne;
+  while (lo < hi) {  // first node whose offset exceeds the slot
+    const int mid = (lo + hi) >> 1;
+    if (S.off[mid] <= slot) lo = mid + 1; else hi = mid;
+  }
+  node = lo - 1;
+  const int4 r = S.rect[T.N + node];
+  const long long local = slot - S.off[node];
+  const int rw = r.y - r.x + 1;
+  i = r.x + (int)(local % rw);
+  j = r.z + (int)(local / rw);
+}
+
+__device__ __forceinline__ unsigned spread3_9(unsigned v) {  // 3 bits -> positions 0, 3, 6
+  return (v & 1u) | ((v & 2u) << 2) | ((v & 4u) << 4);
+}
+
+// The segment of one leaf along one ray: slab interval, reference coordinates
+// of its far end and their change to the near end, field cubic, integration.
+__device__ __forceinline__ float4 leaf_segment(const Topo &T, const Field &Fd, const Cam &c,
+                                               const Integ &I, const TF &tf, int leaf, float3 org,
+                                               float3 dir, float3 inv, float scale, int &steps) {
+  const int4 g = __ldg(T.geo + leaf);
+  const float ih = ldexpf(1.f, g.w);  // 1 / edge length
+  const float3 lo = node_lo(g, scale);
   float a_in, a_out;
-};
+  slab(org, dir, inv, lo, ldexpf(1.f, -g.w), c.amin, c.amax, a_in, a_out);
+  const float3 ufar = make_float3((fmaf(a_out, dir.x, org.x) - lo.x) * ih,
+                                  (fmaf(a_out, dir.y, org.y) - lo.y) * ih,
+                                  (fmaf(a_out, dir.z, org.z) - lo.z) * ih);
+  const float da = a_in - a_out;
+  const float3 du = make_float3(da * dir.x * ih, da * dir.y * ih, da * dir.z * ih);
+  const float dx =
+      fmaxf(a_out - a_in, 0.f) * sqrtf(dir.x * dir.x + dir.y * dir.y + dir.z * dir.z);
+  const Cubic cu = field_cubic(Fd.nodal + 8 * (size_t)leaf, ufar, du);
+  return integrate_segment(cu, tf, dx, I, steps);
+}
+
+// Subtree pass (Sec. 3.2 + Sec. 3.3 for the deepest levels).  A CTA owns a
+// chunk of kChunk consecutive (tile-level node, ray) slots, one thread each.
+//  A. per node of the chunk, the leaves of its subtree whose pixel rectangle
+//     meets the chunk's rows are gathered in shared memory (Morton order);
+//     every ray scans that list, slab-tests the leaves whose rectangle holds
+//     its pixel and appends the hits to its own list;
+//  B. each ray sorts its hits by their Morton key inside the tile node with
+//     every axis mirrored where the ray runs towards negative coordinates:
+//     the ray's front-to-back order for disjoint cells;
+//  C. each warp integrates the hits of its 32 rays, one hit per lane, in
+//     batches, and
+//  D. every lane folds its own ray's results nearest-first with Eq. 2.14.
+constexpr int kCand = 128;     // candidate leaves per round of phase A
+constexpr int kWarpBatch = 64; // hits per warp batch of phase C
+
+__global__ void __launch_bounds__(kChunk, 6)
+    subtree_kernel(Topo T, Field Fd, Cam c, Integ I, Scratch S, int nb, int ne, long long s0,
+                   long long s1) {
+  constexpr int NT = kChunk, NW = NT / 32;
+  __shared__ float4 s_tfv[8], s_tfs[8];
+  __shared__ float4 s_ro[NT], s_rd[NT], s_ri[NT];        // ray origin, direction, 1/direction
+  __shared__ int s_node[NT];                             // node of each slot, -1 inactive
+  __shared__ int s_tnode[NT];                            // distinct nodes of the chunk
+  __shared__ int4 s_cbox[kCand];                         // candidate leaf: rectangle ∩ chunk band
+  __shared__ int s_cl[kCand], s_cpre[kCand];             // candidate leaf index, pair prefix
+  __shared__ int s_cnt[NT];                              // hits of each ray
+  __shared__ unsigned char s_live[NT];
+  __shared__ unsigned s_flip[NT];
+  __shared__ unsigned s_list[kMaxSubtreeHits][NT];       // (mirrored key << 22) | leaf - base
+  __shared__ float4 s_res[NW][kWarpBatch];
+  __shared__ int s_wcnt[NW], s_nn, s_leaf_base;
+  __shared__ unsigned long long s_acc[4];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid < 8) {
+    const float4 v = Fd.tf[tid];
+    const float4 w = Fd.tf[tid < 7 ? tid + 1 : 7];
+    s_tfv[tid] = v;
+    s_tfs[tid] = make_float4(w.x - v.x, w.y - v.y, w.z - v.z, w.w - v.w);
+  }
+  if (tid < 4) s_acc[tid] = 0ull;
+
+  // slot -> node, pixel, ray; rays that miss the node's box skip all leaves
+  const long long chunk = s0 / NT + blockIdx.x, cs = chunk * NT;
+  const long long slot = cs + tid;
+  const bool active = slot >= s0 && slot < s1;
+  int node = -1, i = 0, j = 0;
+  if (active) slot_lookup(T, S, nb, ne, chunk, slot, node, i, j);
+  float3 org, dir;
+  pixel_ray(c, i, j, org, dir);
+  const float3 inv = make_float3(recip_or_zero(dir.x), recip_or_zero(dir.y), recip_or_zero(dir.z));
+  const float scale = ldexpf(1.f, -T.L);
+  bool live = false;
+  if (active) {
+    const int4 gn = __ldg(T.geo + T.N + node);
+    float a0, a1;
+    live = slab(org, dir, inv, node_lo(gn, scale), ldexpf(1.f, -gn.w), c.amin, c.amax, a0, a1);
+  }
+  const unsigned flip =
+      (dir.x < 0.f ? 0x49u : 0u) | (dir.y < 0.f ? 0x92u : 0u) | (dir.z < 0.f ? 0x124u : 0u);
+  s_ro[tid] = make_float4(org.x, org.y, org.z, 0.f);
+  s_rd[tid] = make_float4(dir.x, dir.y, dir.z, 0.f);
+  s_ri[tid] = make_float4(inv.x, inv.y, inv.z, 0.f);
+  s_node[tid] = active ? node : -1;
+  s_live[tid] = live;
+  s_flip[tid] = flip;
+  __syncthreads();
+
+  // distinct nodes of the chunk (a node's slots are contiguous)
+  {
+    const bool head = active && (tid == 0 || s_node[tid - 1] != node);
+    const unsigned bal = __ballot_sync(0xffffffffu, head);
+    if (lane == 0) s_wcnt[wid] = __popc(bal);
+    __syncthreads();
+    int base = 0;
+    for (int w = 0; w < wid; ++w) base += s_wcnt[w];
+    if (head) s_tnode[base + __popc(bal & ((1u << lane) - 1u))] = node;
+    if (tid == NT - 1) {
+      int tot = 0;
+      for (int w = 0; w < NW; ++w) tot += s_wcnt[w];
+      s_nn = tot;
+    }
+    __syncthreads();
+    if (tid == 0) s_leaf_base = s_nn ? __ldg(T.leaves + s_tnode[0]).x : 0;
+  }
+  __syncthreads();
+
+  // A. candidates and hits: (candidate leaf, pixel) pairs, spread evenly
+  // over the CTA by a prefix sum of their counts
+  unsigned ntest = 0;
+  const int nn = s_nn, leaf_base = s_leaf_base;
+  s_cnt[tid] = 0;
+  for (int q = 0; q < nn; ++q) {
+    const int nd = s_tnode[q];
+    const int2 lr = __ldg(T.leaves + nd);
+    const int4 rn = __ldg(S.rect + T.N + nd);
+    const long long off = __ldg(S.off + nd);
+    const int rw = rn.y - rn.x + 1;
+    const long long la = max(cs, off) - off;  // node-local slots inside the chunk
+    const long long lb = min(min(cs + NT, s1), __ldg(S.off + nd + 1)) - off;
+    const int jr0 = rn.z + (int)(la / rw), jr1 = rn.z + (int)((lb - 1) / rw);
+    const unsigned dm = (1u << (T.L - __ldg(T.geo + T.N + nd).w)) - 1u;
+    for (int l0 = lr.x; l0 < lr.y; l0 += kCand) {
+      const int l = l0 + tid;
+      int cnt = 0;
+      int4 box = empty_rect();  // overlap of the leaf's rectangle with the chunk band
+      if (tid < kCand && l < lr.y) {
+        const int4 r = __ldg(S.rect + l);
+        box = make_int4(max(r.x, rn.x), min(r.y, rn.y), max(r.z, jr0), min(r.w, jr1));
+        if (box.x <= box.y && box.z <= box.w) cnt = (box.y - box.x + 1) * (box.w - box.z + 1);
+      }
+      // exclusive prefix of the pair counts over the CTA
+      int x = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      __syncthreads();  // previous round's pair table fully consumed
+      if (lane == 31) s_wcnt[wid] = x;
+      __syncthreads();
+      int base = 0, tot = 0;
+      for (int w = 0; w < NW; ++w) {
+        if (w < wid) base += s_wcnt[w];
+        tot += s_wcnt[w];
+      }
+      s_cpre[tid] = base + x - cnt;
+      s_cbox[tid] = box;
+      s_cl[tid] = l;
+      __syncthreads();
+      for (int pq = tid; pq < tot; pq += NT) {
+        int lo = 0, hi = kCand;  // candidate: last k with s_cpre[k] <= pq
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (s_cpre[mid] <= pq) lo = mid; else hi = mid;
+        }
+        const int4 b = s_cbox[lo];
+        const int loc = pq - s_cpre[lo], bw = b.y - b.x + 1;
+        const int jj = b.z + loc / bw, ii = b.x + loc % bw;
+        const long long ls = (long long)(jj - rn.z) * rw + (ii - rn.x);
+        if (ls < la || ls >= lb) continue;
+        const int t = (int)(off + ls - cs);
+        if (!s_live[t]) continue;
+        ++ntest;
+        const int lf = s_cl[lo];
+        const int4 g = __ldg(T.geo + lf);
+        const float4 ro = s_ro[t], rd = s_rd[t], ri = s_ri[t];
+        float b0, b1;
+        if (!slab(make_float3(ro.x, ro.y, ro.z), make_float3(rd.x, rd.y, rd.z),
+                  make_float3(ri.x, ri.y, ri.z), node_lo(g, scale), ldexpf(1.f, -g.w), c.amin,
+                  c.amax, b0, b1))
+          continue;
+        const unsigned key = spread3_9((unsigned)g.x & dm) | (spread3_9((unsigned)g.y & dm) << 1) |
+                             (spread3_9((unsigned)g.z & dm) << 2);
+        const int k = atomicAdd(&s_cnt[t], 1);
+        if (k < kMaxSubtreeHits)
+          s_list[k][t] = ((key ^ s_flip[t]) << 22) | (unsigned)(lf - leaf_base);
+      }
+    }
+  }
+  __syncthreads();
+  const unsigned nhit = (unsigned)s_cnt[tid];
+
+  // B. sort the ray's hits into its front-to-back order
+  const int n = min((int)nhit, kMaxSubtreeHits);
+  for (int a = 1; a < n; ++a) {
+    const unsigned v = s_list[a][tid];
+    int b = a - 1;
+    while (b >= 0 && s_list[b][tid] > v) {
+      s_list[b + 1][tid] = s_list[b][tid];
+      --b;
+    }
+    s_list[b + 1][tid] = v;
+  }
+
+  // C + D. per warp: integrate the warp's hits, one per lane; fold per ray
+  int pre = n;  // inclusive prefix of the hit counts over the warp's lanes
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, pre, o);
+    if (lane >= o) pre += y;
+  }
+  const int Hw = __shfl_sync(0xffffffffu, pre, 31);
+  const int my0 = pre - n;
+  float4 acc = seg_identity();
+  int steps = 0;
+  TF tf{s_tfv, s_tfs, Fd.s_min, Fd.inv_ds7};
+  for (int b0 = 0; b0 < Hw; b0 += kWarpBatch) {
+    const int b1 = min(Hw, b0 + kWarpBatch);
+    for (int hb = b0; hb < b1; hb += 32) {
+      const int h = hb + lane;
+      // owner lane: the first lane whose inclusive prefix exceeds h
+      int lo = 0;
+#pragma unroll
+      for (int st = 16; st > 0; st >>= 1) {
+        const int p = __shfl_sync(0xffffffffu, pre, lo + st - 1);
+        if (p <= h) lo += st;
+      }
+      const int ow = lo;
+      const int owpre = __shfl_sync(0xffffffffu, my0, ow & 31);
+      if (h < b1) {
+        const int t = wid * 32 + ow;
+        const int leaf = leaf_base + (int)(s_list[h - owpre][t] & 0x3fffffu);
+        const float4 ro = s_ro[t], rd = s_rd[t], ri = s_ri[t];
+        s_res[wid][h - b0] = leaf_segment(T, Fd, c, I, tf, leaf, make_float3(ro.x, ro.y, ro.z),
+                                          make_float3(rd.x, rd.y, rd.z),
+                                          make_float3(ri.x, ri.y, ri.z), scale, steps);
+      }
+    }
+    __syncwarp();
+    for (int h = max(my0, b0); h < min(my0 + n, b1); ++h) acc = seg_combine(acc, s_res[wid][h - b0]);
+    __syncwarp();
+  }
+  if (active) {
+    S.entries[slot] = acc;
+    if (nhit > (unsigned)kMaxSubtreeHits) atomicAdd(S.stats + 4, 1ull);
+    if (nhit && S.counts) atomicAdd(S.counts + (size_t)j * c.w + i, (int)nhit);
+  }
+  unsigned long long v[4] = {nhit, (unsigned long long)steps, ntest, active ? 1ull : 0ull};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    unsigned long long x = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0 && x) atomicAdd(&s_acc[q], x);
+  }
+  __syncthreads();
+  if (tid < 4 && s_acc[tid]) atomicAdd(S.stats + tid, s_acc[tid]);
+}
 
 template <bool FINAL>
-__global__ void __launch_bounds__(kCoarsenThreads)
+__global__ void __launch_bounds__(kCoarsenThreads, 8)
     coarsen_kernel(Topo T, Field Fd, Cam c, Integ I, Scratch S, int nb, int ne, long long s0,
                    long long s1, float4 *rgba) {
   constexpr int NT = kCoarsenThreads;
   __shared__ float4 s_tfv[8], s_tfs[8];
-  __shared__ float4 s_seg[8][NT];
-  __shared__ Hit s_hit[8 * NT];
+  __shared__ float4 s_seg[8][NT];           // child segment of each slot (identity if none)
+  __shared__ unsigned short s_hit[8 * NT];  // (slot << 3) | child octant of each hit
   __shared__ int2 s_pix[NT];
+  __shared__ int s_node[NT];
   __shared__ int s_nhit;
   __shared__ unsigned long long s_cnt[4];
 
@@ -470,48 +744,46 @@ __global__ void __launch_bounds__(kCoarsenThreads)
       i = (int)(slot % c.w);
       j = (int)(slot / c.w);
     } else {
-      // the chunk's slots lie in the nodes [chunk_node[chunk], chunk_node[chunk + 1]]
-      const long long nch = (S.off[T.M] + NT - 1) / NT;
-      int lo = max(S.chunk_node[chunk], nb);
-      int hi = (chunk + 1 < nch) ? min(S.chunk_node[chunk + 1], ne - 1) + 1 : ne;
-      while (lo < hi) {  // first node whose offset exceeds the slot
-        const int mid = (lo + hi) >> 1;
-        if (S.off[mid] <= slot) lo = mid + 1; else hi = mid;
-      }
-      node = lo - 1;
-      const int4 r = S.rect[T.N + node];
-      const long long local = slot - S.off[node];
-      const int rw = r.y - r.x + 1;
-      i = r.x + (int)(local % rw);
-      j = r.z + (int)(local / rw);
+      slot_lookup(T, S, nb, ne, chunk, slot, node, i, j);
     }
   }
   s_pix[tid] = make_int2(i, j);
+  s_node[tid] = node;
   int ch[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) ch[q] = active ? __ldg(T.child + 8 * node + q) : -1;
-  __syncthreads();
 
   float3 org, dir;
   pixel_ray(c, i, j, org, dir);
   const float3 inv = make_float3(recip_or_zero(dir.x), recip_or_zero(dir.y), recip_or_zero(dir.z));
   const float scale = ldexpf(1.f, -T.L);
 
+  // a ray that misses the node's box misses every child: its aggregate is the
+  // identity and all child work is skipped
+  bool live = active;
+  if (!FINAL && active) {
+    const int4 g = __ldg(T.geo + T.N + node);
+    float a0, a1;
+    live = slab(org, dir, inv, node_lo(g, scale), ldexpf(1.f, -g.w), c.amin, c.amax, a0, a1);
+  }
+  __syncthreads();
+
   // phase 1: slab tests against the leaf children whose rectangle holds the ray
   unsigned local_tests = 0, local_hits = 0;
-  if (active) {
+  if (live) {
+    int4 rc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      rc[q] = (ch[q] >= 0 && ch[q] < T.N) ? __ldg(S.rect + ch[q]) : empty_rect();
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const int id = ch[q];
-      if (id < 0 || id >= T.N) continue;
-      const int4 r = S.rect[id];
+      const int4 r = rc[q];
       if (i < r.x || i > r.y || j < r.z || j > r.w) continue;
       ++local_tests;
-      const int4 g = T.geo[id];
+      const int4 g = __ldg(T.geo + ch[q]);
       float a0, a1;
       if (slab(org, dir, inv, node_lo(g, scale), ldexpf(1.f, -g.w), c.amin, c.amax, a0, a1)) {
-        const int h = atomicAdd(&s_nhit, 1);
-        s_hit[h] = Hit{id, (tid << 3) | q, a0, a1};
+        s_hit[atomicAdd(&s_nhit, 1)] = (unsigned short)((tid << 3) | q);
         ++local_hits;
       }
     }
@@ -519,28 +791,20 @@ __global__ void __launch_bounds__(kCoarsenThreads)
   }
   __syncthreads();
 
-  // phase 2: integrate the hits, one per thread, into s_seg[child][slot]
+  // phase 2: integrate the hits, one per thread, into s_seg[child][slot]; the
+  // slab interval is recomputed (same inputs, same arithmetic as phase 1)
   const int nh = s_nhit;
   TF tf{s_tfv, s_tfs, Fd.s_min, Fd.inv_ds7};
   int steps = 0;
   for (int h = tid; h < nh; h += NT) {
-    const Hit H = s_hit[h];
-    const int st = H.slot_child >> 3, q = H.slot_child & 7;
+    const int key = s_hit[h];
+    const int st = key >> 3, q = key & 7;
     const int2 p = s_pix[st];
+    const int leaf = __ldg(T.child + 8 * s_node[st] + q);
     float3 o2, d2;
     pixel_ray(c, p.x, p.y, o2, d2);
-    const int4 g = T.geo[H.leaf];
-    const float ih = ldexpf(1.f, g.w);  // 1 / edge length
-    const float3 lo = node_lo(g, scale);
-    // reference coordinates of the far end and their change to the near end
-    const float3 ufar = make_float3((fmaf(H.a_out, d2.x, o2.x) - lo.x) * ih,
-                                    (fmaf(H.a_out, d2.y, o2.y) - lo.y) * ih,
-                                    (fmaf(H.a_out, d2.z, o2.z) - lo.z) * ih);
-    const float da = H.a_in - H.a_out;
-    const float3 du = make_float3(da * d2.x * ih, da * d2.y * ih, da * d2.z * ih);
-    const float dx = (H.a_out - H.a_in) * sqrtf(d2.x * d2.x + d2.y * d2.y + d2.z * d2.z);
-    const Cubic cu = field_cubic(Fd.nodal + 8 * (size_t)H.leaf, ufar, du);
-    s_seg[q][st] = integrate_segment(cu, tf, dx, I, steps);
+    const float3 iv2 = make_float3(recip_or_zero(d2.x), recip_or_zero(d2.y), recip_or_zero(d2.z));
+    s_seg[q][st] = leaf_segment(T, Fd, c, I, tf, leaf, o2, d2, iv2, scale, steps);
   }
   __syncthreads();
 
@@ -552,6 +816,10 @@ __global__ void __launch_bounds__(kCoarsenThreads)
     float4 cs[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
+      if (!live) {
+        cs[q] = seg_identity();
+        continue;
+      }
       const int id = ch[q];
       float4 s = seg_identity();
       if (id >= 0 && id < T.N) {
@@ -641,6 +909,16 @@ cudaError_t launch_area_scan(const Topo &T, Scratch S, long long *block_sums, in
 cudaError_t launch_chunk_map(const Topo &T, Scratch S, cudaStream_t stream) {
   if (T.M < 1) return cudaSuccess;
   chunk_map_kernel<<<grid_for(T.M, 256), 256, 0, stream>>>(T, S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_subtree(const Topo &T, const Field &Fd, const Cam &C, const Integ &I,
+                           Scratch S, int nb, int ne, long long s0, long long s1,
+                           cudaStream_t stream) {
+  if (s1 <= s0) return cudaSuccess;
+  const long long nblk = (s1 - 1) / kChunk - s0 / kChunk + 1;
+  if (nblk > 0x7fffffffll) return cudaErrorInvalidValue;
+  subtree_kernel<<<(unsigned)nblk, kChunk, 0, stream>>>(T, Fd, C, I, S, nb, ne, s0, s1);
   return cudaGetLastError();
 }
 
