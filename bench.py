@@ -30,6 +30,16 @@ METRIC = "ray-segments/s"
 UNIT = "segments/s"
 WORKLOAD = ("adaptive unit cube, levels 2-8 (2,053,451 leaves, 2:1 balanced, trilinear FP32), "
             "perspective 45deg 1920x1080, DOPRI5 tol 1e-6, c_RK 0.5")
+# Algorithmic FP32 operations (FADD/FMUL/FFMA/FMNMX, one each) of the render
+# path, counted from the kernel source: per (leaf, ray) slab test, per segment
+# set-up (slab interval, reference coordinates, the field's cubic along the
+# segment, the first medium evaluation) and per Dormand-Prince step (five
+# medium evaluations, seven stages on (A, B_r, B_g, B_b), the embedded error,
+# the split test and the Eq. 2.14 fold).
+FP32_OPS_SLAB = 30
+FP32_OPS_SEGMENT = 128
+FP32_OPS_DOPRI_STEP = 234
+FP32_LANES_PER_SM = 128
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -201,7 +211,7 @@ def main():
 
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
-    merge_ms, prune_ms = [], []
+    merge_ms, prune_ms, sub_ms = [], [], []
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -213,6 +223,7 @@ def main():
             evs[k][1].record(stream)
             merge_ms.append(st["ms_merge"])
             prune_ms.append(st["ms_prune"])
+            sub_ms.append(st["ms_subtree"])
         torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
@@ -249,11 +260,15 @@ def main():
     if rank == 0:
         peaks, src = measured_peaks()
         mm = sum(merge_ms) / len(merge_ms)
-        # algorithmic bytes of the merge passes: every (node, ray) aggregate is
-        # written once and read once by its parent (16 B each), plus one read of
-        # each leaf's record (anchor 16 B + 8 corner values 32 B)
-        alg_bytes = 32 * st0["slots"] + 48 * forest.nleaves
-        achieved = alg_bytes / (mm * 1e-3) / 1e9
+        sm = sum(sub_ms) / len(sub_ms)
+        # the dominant kernel is the subtree pass: FP32-ALU bound (its DRAM
+        # traffic is a few percent of peak); peak = SMs x FP32 lanes x clock
+        ops = (FP32_OPS_SLAB * st0["subtree_leaf_tests"] +
+               FP32_OPS_SEGMENT * st0["subtree_segments"] +
+               FP32_OPS_DOPRI_STEP * st0["subtree_rk_steps"])
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak_ops = nsm * FP32_LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6
+        achieved = ops / (sm * 1e-3)
         line = {
             "metric": METRIC, "value": world * segments / (ms_max * 1e-3), "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -271,11 +286,13 @@ def main():
             "e2e": {"value": world * segments / (float(te.item()) * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": int(forest.nodal.nbytes),
                     "d2h_bytes_per_step": int(out.numel() * 4)},
-            "roofline": {"bound": "hbm", "kernel": "coarsen (all levels)",
-                         "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                         "peak_source": src, "ms_merge": mm,
-                         "ms_prune": sum(prune_ms) / len(prune_ms)},
+            "roofline": {"bound": "alu", "kernel": "subtree_kernel",
+                         "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                         "unit": "TFP32op/s", "frac": achieved / peak_ops, "traffic": None,
+                         "fp32_ops_per_launch": ops, "ms_per_launch": sm,
+                         "peak_source": f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                                        f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({src})",
+                         "ms_merge": mm, "ms_prune": sum(prune_ms) / len(prune_ms)},
             "clocks": clk.summary(),
         }
         if world == 1 and not args.no_cpu_baseline:

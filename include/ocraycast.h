@@ -8,7 +8,7 @@
  *             centre (Sec. 3.1, Sec. 2.2);
  *   segment - intersect each remaining leaf with every ray of its pixel
  *             rectangle and integrate A' = -kappa A, B' = q - kappa B along
- *             the piece (Sec. 2.3, Eqs. 2.22-2.23, Algorithm 1);
+ *             the piece (Sec. 2.3, Eqs. 2.29 and 2.31, Algorithm 1);
  *   merge   - aggregate the segments of each ray up the octree with the
  *             segment group action (Eq. 2.14, Sec. 3.3) into its pixel,
  *             I_v = A I_b + B (Sec. 2.4), without a global depth sort.
@@ -62,7 +62,7 @@ typedef struct {
   const uint8_t *h_level;  /* [nleaves] */
 } ocr_forest_desc;
 
-/* Pinhole camera of Sec. 2.2, Eq. 2.2: ray (i, j) is o + alpha r with
+/* Pinhole camera of Sec. 2.2, Eq. 2.5: ray (i, j) is o + alpha r with
  * r = v + ell ((i - (w-1)/2) t + (j - (h-1)/2) u), alpha in [1, far/near]
  * (near = |v|, the projection plane).  ortho != 0: the origin moves to
  * o + ell ((i - (w-1)/2) t + (j - (h-1)/2) u), the direction is v/near and
@@ -105,9 +105,13 @@ typedef struct {
   int64_t rk_steps;       /* Runge-Kutta steps taken over all segments */
   int64_t leaf_tests;     /* (leaf, ray) slab tests performed */
   int64_t slots;          /* (node, ray) aggregates formed while merging */
+  int64_t subtree_segments; /* segments integrated by the subtree pass */
+  int64_t subtree_rk_steps; /* RK steps taken by the subtree pass */
+  int64_t subtree_leaf_tests; /* (leaf, ray) slab tests of the subtree pass */
   int64_t launches;       /* kernels launched by this call */
   float ms_prune;         /* pruning, rectangle unions, slot layout, host readback */
-  float ms_merge;         /* all coarsening passes (segments + merge), incl. the pixel pass */
+  float ms_merge;         /* subtree pass + coarsening passes + pixel pass */
+  float ms_subtree;       /* the subtree pass alone */
 } ocr_stats;
 
 /* Copy the forest topology to the device and derive its internal octree

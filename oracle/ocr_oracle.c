@@ -37,7 +37,7 @@ void orc_inverse(const double *s, double *out) {
   memcpy(out, r, sizeof r);
 }
 
-/* Eq. 2.17: the piece of relative length frac: A_i = A^frac,
+/* Eq. 2.20: the piece of relative length frac: A_i = A^frac,
  * B_i = B (1 - A_i) / (1 - A); for A = 1, B_i = B frac.  1 - A^f is formed
  * as -expm1(f ln A) so that A -> 1 loses no digits. */
 void orc_cut(const double *s, double frac, double *out) {
@@ -49,7 +49,7 @@ void orc_cut(const double *s, double frac, double *out) {
   memcpy(out, r, sizeof r);
 }
 
-/* Eq. 2.18: geometric mean of A, arithmetic mean of B. */
+/* Eq. 2.21: geometric mean of A, arithmetic mean of B. */
 void orc_average(const double *s1, const double *s2, double *out) {
   double r[4];
   r[0] = sqrt(s1[0] * s2[0]);
@@ -96,7 +96,7 @@ static void leaf_box(const orc_forest *F, int leaf, double *lo, double *h) {
 /* Camera, Sec. 2.2                                                          */
 /* ------------------------------------------------------------------------ */
 
-/* Eq. 2.2: r = v + ell ((i - (w-1)/2) t + (j - (h-1)/2) u), rays o + alpha r,
+/* Eq. 2.5: r = v + ell ((i - (w-1)/2) t + (j - (h-1)/2) u), rays o + alpha r,
  * alpha in [1, f/n] (the near plane is the projection plane).  The
  * orthographic variant moves the origin by the same offset and uses the
  * direction v/n, alpha >= 0. */
@@ -120,7 +120,7 @@ void orc_pixel_ray(const orc_camera *C, int i, int j, double *org, double *dir, 
   }
 }
 
-/* Eq. 2.3: X = (t, u, v/n)^T (x - o). */
+/* Eq. 2.6: X = (t, u, v/n)^T (x - o). */
 static void camera_transform(const orc_camera *C, const double *x, double *X) {
   double d[3] = {x[0] - C->o[0], x[1] - C->o[1], x[2] - C->o[2]};
   X[0] = C->t[0] * d[0] + C->t[1] * d[1] + C->t[2] * d[2];
@@ -254,7 +254,7 @@ static void medium_at(const seg_ctx *S, double x, double *kq) {
   orc_tf_eval(S->F, s, kq);
 }
 
-/* Classical RK4 on A' = -kappa A, B' = q - kappa B (Eq. 2.22), x from the far
+/* Classical RK4 on A' = -kappa A, B' = q - kappa B (Eq. 2.29), x from the far
  * end, state continued across nsteps equal steps starting from (1, 0). */
 static void rk4_segment(const seg_ctx *S, double dx, int nsteps, double *y) {
   y[0] = 1.0; y[1] = y[2] = y[3] = 0.0;
@@ -296,7 +296,7 @@ static const double DP_B[7] = {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0
 static const double DP_BS[7] = {5179.0 / 57600, 0, 7571.0 / 16695, 393.0 / 640,
                                 -92097.0 / 339200, 187.0 / 2100, 1.0 / 40};
 
-/* One Dormand-Prince step over [x1, x2] from (1, 0), Eq. 2.23.  Returns the
+/* One Dormand-Prince step over [x1, x2] from (1, 0), Eq. 2.31.  Returns the
  * fifth-order values, the largest dx kappa(xi_j) and the embedded error. */
 static void dopri_step(const seg_ctx *S, double x1, double x2, double *y5, double *kmax,
                        double *err) {
@@ -395,11 +395,11 @@ static int cmp_dbl(const void *pa, const void *pb) {
   return (a > b) - (a < b);
 }
 
-/* Back-to-front compositing of one pixel's segments (Eq. 2.10 applied from the
+/* Back-to-front compositing of one pixel's segments (Eq. 2.11 applied from the
  * farthest segment to the nearest, starting from the background).  Where
  * segments overlap, the ray is cut at every segment end into elementary
- * intervals; each segment covering an interval is cut to it (Eq. 2.17) and the
- * covering pieces are averaged (Eq. 2.18, geometric mean of A, arithmetic mean
+ * intervals; each segment covering an interval is cut to it (Eq. 2.20) and the
+ * covering pieces are averaged (Eq. 2.21, geometric mean of A, arithmetic mean
  * of B, over all covering pieces). */
 static void composite(orc_seg *sg, int n, const double *bg, double *rgba) {
   double I[3] = {bg[0], bg[1], bg[2]}, T = 1.0;

@@ -7,14 +7,14 @@
  * paper_1809_01334_gb300/csrc, and neither includes the other.
  *
  * Everything is plain, slow, obviously-correct double-precision C:
- *   - segment algebra: combine (Eq. 2.14), inverse (Eq. 2.15), cut (Eq. 2.17),
- *     average (Eq. 2.18);
- *   - camera rays (Eq. 2.2), camera transform (Eq. 2.3), axis-aligned bounding
+ *   - segment algebra: combine (Eq. 2.14), inverse (Eq. 2.15), cut (Eq. 2.20),
+ *     average (Eq. 2.21);
+ *   - camera rays (Eq. 2.5), camera transform (Eq. 2.6), axis-aligned bounding
  *     boxes projected to pixel rectangles (Sec. 2.2, App. A.2);
  *   - per-segment (A, B) by explicit Runge-Kutta on the decoupled ODEs
- *     (Eqs. 2.22-2.23) with the adaptive bisection of Algorithm 1;
+ *     (Eqs. 2.29 and 2.31) with the adaptive bisection of Algorithm 1;
  *   - per-pixel compositing by the classical back-to-front recursion
- *     I <- A I + B (Eq. 2.10), with overlaps resolved by cut + average (Sec. 2.5).
+ *     I <- A I + B (Eq. 2.11), with overlaps resolved by cut + average (Sec. 2.5).
  */
 #ifndef OCR_ORACLE_H
 #define OCR_ORACLE_H

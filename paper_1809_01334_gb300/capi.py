@@ -41,8 +41,11 @@ class Stats(C.Structure):
     _fields_ = [("d_counts", C.c_void_p), ("d_visible", C.c_void_p), ("d_rects", C.c_void_p),
                 ("fill_counters", C.c_int), ("time_phases", C.c_int),
                 ("visible_leaves", C.c_int64), ("segments", C.c_int64), ("rk_steps", C.c_int64),
-                ("leaf_tests", C.c_int64), ("slots", C.c_int64), ("launches", C.c_int64),
-                ("ms_prune", C.c_float), ("ms_merge", C.c_float)]
+                ("leaf_tests", C.c_int64), ("slots", C.c_int64),
+                ("subtree_segments", C.c_int64), ("subtree_rk_steps", C.c_int64),
+                ("subtree_leaf_tests", C.c_int64),
+                ("launches", C.c_int64), ("ms_prune", C.c_float), ("ms_merge", C.c_float),
+                ("ms_subtree", C.c_float)]
 
 
 class OcrError(RuntimeError):
@@ -139,8 +142,11 @@ def render(h, d_rgba, stream=None, d_counts=None, d_visible=None, d_rects=None,
               int(bool(time_phases)))
     _check(lib().ocr_render(h, _ptr(d_rgba), _ptr(stream), C.byref(s)), "ocr_render")
     return {"visible_leaves": s.visible_leaves, "segments": s.segments, "rk_steps": s.rk_steps,
-            "leaf_tests": s.leaf_tests, "slots": s.slots, "launches": s.launches,
-            "ms_prune": s.ms_prune, "ms_merge": s.ms_merge}
+            "leaf_tests": s.leaf_tests, "slots": s.slots,
+            "subtree_segments": s.subtree_segments, "subtree_rk_steps": s.subtree_rk_steps,
+            "subtree_leaf_tests": s.subtree_leaf_tests,
+            "launches": s.launches, "ms_prune": s.ms_prune, "ms_merge": s.ms_merge,
+            "ms_subtree": s.ms_subtree}
 
 
 def device_bytes(h) -> int:

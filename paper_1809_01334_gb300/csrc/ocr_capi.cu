@@ -44,8 +44,8 @@ struct ocr_forest {
   int block_sums_cap = 0;
   long long *d_group_slots = nullptr; // [L + 1]
   long long *h_group_slots = nullptr; // pinned [L + 1 + 8]
-  unsigned long long *d_stats = nullptr;  // [8]
-  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  unsigned long long *d_stats = nullptr;  // [kStats]
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // start, layout, subtree, end
   float4 *d_entries = nullptr;
   long long entries_cap = 0;
   int *d_chunk_node = nullptr;        // [chunk_cap]
@@ -268,7 +268,7 @@ int ocr_build_forest(const ocr_forest_desc *desc, void *stream, ocr_forest **out
       (rc = dev_alloc(&F->d_rect, (size_t)N + M + 1, F->bytes)) ||
       (rc = dev_alloc(&F->d_off, (size_t)M + 1, F->bytes)) ||
       (rc = dev_alloc(&F->d_group_slots, F->h_group_nodes.size(), F->bytes)) ||
-      (rc = dev_alloc(&F->d_stats, 8, F->bytes))) {
+      (rc = dev_alloc(&F->d_stats, kStats, F->bytes))) {
     free_all(F);
     delete F;
     return rc;
@@ -279,7 +279,8 @@ int ocr_build_forest(const ocr_forest_desc *desc, void *stream, ocr_forest **out
     delete F;
     return rc;
   }
-  if (cudaMallocHost((void **)&F->h_group_slots, sizeof(long long) * (F->h_group_nodes.size() + 8)) !=
+  if (cudaMallocHost((void **)&F->h_group_slots,
+                     sizeof(long long) * (F->h_group_nodes.size() + kStats)) !=
       cudaSuccess) {
     F->h_group_slots = nullptr;
     free_all(F);
@@ -393,7 +394,7 @@ int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats) {
   if (timed && !F->ev[0])
     for (cudaEvent_t &e : F->ev) OCR_CUDA(cudaEventCreate(&e));
   int64_t launches = 0;
-  OCR_CUDA(cudaMemsetAsync(F->d_stats, 0, 8 * sizeof(unsigned long long), st));
+  OCR_CUDA(cudaMemsetAsync(F->d_stats, 0, kStats * sizeof(unsigned long long), st));
   if (timed) OCR_CUDA(cudaEventRecord(F->ev[0], st));
 
   // prune: leaf rectangles; internal rectangles bottom-up; slot layout
@@ -441,14 +442,18 @@ int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats) {
   // group g covers level L - 1 - g.  Levels below the tile level hold no
   // slots; the tile level runs the subtree pass, the levels above it the
   // coarsening passes, deepest first.
+  bool subtree_ran = false;
   for (int g = 0; g + 1 < G; ++g) {
     const int level = F->L - 1 - g;
     const long long a = F->h_group_slots[g], b = F->h_group_slots[g + 1];
     if (b <= a) continue;
-    if (level == F->lt)
+    if (level == F->lt) {
+      if (timed) OCR_CUDA(cudaEventRecord(F->ev[2], st));
       OCR_CUDA(launch_subtree(T, Fd, F->cam, F->integ, S, F->h_group_nodes[g],
                               F->h_group_nodes[g + 1], a, b, st));
-    else
+      if (timed) OCR_CUDA(cudaEventRecord(F->ev[3], st));
+      subtree_ran = true;
+    } else
       OCR_CUDA(launch_coarsen(T, Fd, F->cam, F->integ, S, F->h_group_nodes[g],
                               F->h_group_nodes[g + 1], a, b, nullptr, st));
     ++launches;
@@ -457,7 +462,7 @@ int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats) {
   OCR_CUDA(launch_coarsen(T, Fd, F->cam, F->integ, S, F->M, F->M, 0,
                           (long long)F->cam.w * F->cam.h, reinterpret_cast<float4 *>(d_rgba), st));
   ++launches;
-  if (timed) OCR_CUDA(cudaEventRecord(F->ev[2], st));
+  if (timed) OCR_CUDA(cudaEventRecord(F->ev[4], st));
 
   if (stats) {
     stats->launches = launches;
@@ -465,22 +470,27 @@ int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats) {
       OCR_CUDA(cudaMemcpyAsync(stats->d_rects, F->d_rect, sizeof(int4) * (size_t)F->N,
                                cudaMemcpyDeviceToDevice, st));
     if (timed) {
-      OCR_CUDA(cudaEventSynchronize(F->ev[2]));
+      OCR_CUDA(cudaEventSynchronize(F->ev[4]));
       OCR_CUDA(cudaEventElapsedTime(&stats->ms_prune, F->ev[0], F->ev[1]));
-      OCR_CUDA(cudaEventElapsedTime(&stats->ms_merge, F->ev[1], F->ev[2]));
+      OCR_CUDA(cudaEventElapsedTime(&stats->ms_merge, F->ev[1], F->ev[4]));
+      stats->ms_subtree = 0.f;
+      if (subtree_ran) OCR_CUDA(cudaEventElapsedTime(&stats->ms_subtree, F->ev[2], F->ev[3]));
     }
     if (stats->fill_counters) {
-      unsigned long long h[8];
+      unsigned long long h[kStats];
       OCR_CUDA(cudaMemcpyAsync(F->h_group_slots + G, F->d_stats, sizeof(h), cudaMemcpyDeviceToHost,
                                st));
       OCR_CUDA(cudaStreamSynchronize(st));
       memcpy(h, F->h_group_slots + G, sizeof(h));
-      stats->segments = (int64_t)h[0];
-      stats->rk_steps = (int64_t)h[1];
-      stats->leaf_tests = (int64_t)h[2];
-      stats->slots = (int64_t)h[3];
-      stats->visible_leaves = (int64_t)h[5];
-      if (h[4]) return OCR_ERR_DEVICE;
+      stats->segments = (int64_t)(h[kStatSegments] + h[kStatCoarse + kStatSegments]);
+      stats->rk_steps = (int64_t)(h[kStatSteps] + h[kStatCoarse + kStatSteps]);
+      stats->leaf_tests = (int64_t)(h[kStatTests] + h[kStatCoarse + kStatTests]);
+      stats->slots = (int64_t)(h[kStatSlots] + h[kStatCoarse + kStatSlots]);
+      stats->subtree_segments = (int64_t)h[kStatSegments];
+      stats->subtree_rk_steps = (int64_t)h[kStatSteps];
+      stats->subtree_leaf_tests = (int64_t)h[kStatTests];
+      stats->visible_leaves = (int64_t)h[kStatVisible];
+      if (h[kStatErrors]) return OCR_ERR_DEVICE;
     }
   }
   return OCR_OK;

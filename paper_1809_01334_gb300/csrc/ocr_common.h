@@ -57,11 +57,18 @@ struct Scratch {
   int4 *rect;                // [N + M + 1] {i0, i1, j0, j1}; empty = {0, -1, 0, -1}
   long long *off;            // [M + 1] exclusive prefix of internal-node rectangle areas
   float4 *entries;           // [total slots] per (internal node, ray) aggregate (A, B_r, B_g, B_b)
-  unsigned long long *stats; // [8] 0 segments, 1 rk steps, 2 leaf tests, 3 slots, 4 device errors
+  unsigned long long *stats; // [kStats] counters, see below
   int *counts;               // optional [w * h]
   unsigned char *visible;    // optional [N]
   int *chunk_node;           // [ceil(total / kChunk) + 1] internal node holding slot c * kChunk
 };
+
+// Device counters: [0, 4) subtree pass, [kStatCoarse, kStatCoarse + 4) coarse
+// passes, each {segments, RK steps, leaf slab tests, slots}; then device
+// errors and visible leaves.
+constexpr int kStats = 16;
+constexpr int kStatSegments = 0, kStatSteps = 1, kStatTests = 2, kStatSlots = 3;
+constexpr int kStatCoarse = 8, kStatErrors = 4, kStatVisible = 5;
 
 // Slots are processed in chunks of kChunk consecutive slots, one chunk per CTA.
 constexpr int kChunk = 128;

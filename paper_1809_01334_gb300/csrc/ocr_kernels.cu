@@ -10,7 +10,7 @@
 //   coarsen       - one octree level of Sec. 3.3: for every (node, ray) slot
 //                   of the level, the node's leaf children are intersected
 //                   with the ray and integrated in shared memory (Sec. 3.2,
-//                   Eqs. 2.22-2.23, Algorithm 1); the children's segments are
+//                   Eqs. 2.29 and 2.31, Algorithm 1); the children's segments are
 //                   then combined nearest-first with Eq. 2.14 in the ray's
 //                   octant order, and the node's aggregate is stored.  The
 //                   last pass (the super-root) writes I_v = A I_b + B.
@@ -122,7 +122,7 @@ __device__ __forceinline__ float4 medium(const Cubic &c, const TF &tf, float tau
   return make_float4(fmaf(w, d.x, a.x), fmaf(w, d.y, a.y), fmaf(w, d.z, a.z), fmaf(w, d.w, a.w));
 }
 
-// Right-hand side of Eq. 2.22 for the state Y = (A, B_r, B_g, B_b).
+// Right-hand side of Eq. 2.29 for the state Y = (A, B_r, B_g, B_b).
 __device__ __forceinline__ float4 rhs(float4 kq, float4 Y) {
   return make_float4(-kq.x * Y.x, fmaf(-kq.x, Y.y, kq.y), fmaf(-kq.x, Y.z, kq.z),
                      fmaf(-kq.x, Y.w, kq.w));
@@ -309,7 +309,7 @@ __global__ void cull_leaves_kernel(Topo T, Cam c, Scratch S) {
     }
     nvis += __popc(__ballot_sync(0xffffffffu, vis));
   }
-  if ((threadIdx.x & 31) == 0 && nvis) atomicAdd(S.stats + 5, (unsigned long long)nvis);
+  if ((threadIdx.x & 31) == 0 && nvis) atomicAdd(S.stats + kStatVisible, (unsigned long long)nvis);
 }
 
 __global__ void union_level_kernel(Topo T, int nb, int ne, Scratch S) {
@@ -692,7 +692,7 @@ __global__ void __launch_bounds__(kChunk, 6)
   }
   if (active) {
     S.entries[slot] = acc;
-    if (nhit > (unsigned)kMaxSubtreeHits) atomicAdd(S.stats + 4, 1ull);
+    if (nhit > (unsigned)kMaxSubtreeHits) atomicAdd(S.stats + kStatErrors, 1ull);
     if (nhit && S.counts) atomicAdd(S.counts + (size_t)j * c.w + i, (int)nhit);
   }
   unsigned long long v[4] = {nhit, (unsigned long long)steps, ntest, active ? 1ull : 0ull};
@@ -862,7 +862,7 @@ __global__ void __launch_bounds__(kCoarsenThreads, 8)
     if ((tid & 31) == 0 && x) atomicAdd(&s_cnt[q], x);
   }
   __syncthreads();
-  if (tid < 4 && s_cnt[tid]) atomicAdd(S.stats + tid, s_cnt[tid]);
+  if (tid < 4 && s_cnt[tid]) atomicAdd(S.stats + kStatCoarse + tid, s_cnt[tid]);
 }
 
 }  // namespace

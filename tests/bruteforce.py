@@ -3,7 +3,7 @@
 None of these use leaves as segments, the segment group action, or the
 oracle's code: they evaluate the defining integrals directly.
 
-* ``ray_integral``: Eq. 2.13 of the paper along a whole ray,
+* ``ray_integral``: Eq. 2.12 of the paper along a whole ray,
   A = exp(-int kappa), B = int q(x) exp(-int_x^{x2} kappa), by the composite
   trapezoid rule on a fine grid, with the medium found by point location.
 * ``leaves_along_ray``: the leaves a ray passes, found by point location at

@@ -26,7 +26,7 @@ def rand_seg(rng=RNG):
 # ---------------------------------------------------------------- Sec. 2.4 --
 def test_combine_matches_sequential_application():
     """Eq. 2.14 with 2 = nearer: applying the far segment first and then the
-    near one to an intensity (Eq. 2.10) equals applying their combination."""
+    near one to an intensity (Eq. 2.11) equals applying their combination."""
     for _ in range(50):
         n, f = rand_seg(), rand_seg()
         Ib = RNG.uniform(-1, 1, 3)
@@ -69,7 +69,7 @@ def test_identity_inverse_and_non_commutativity():
 
 # ---------------------------------------------------------------- Sec. 2.5 --
 def const_seg(beta, gamma, dx):
-    """Eq. 2.12 (constant medium) with its beta -> 0 limit."""
+    """Eq. 2.13 (constant medium) with its beta -> 0 limit."""
     A = math.exp(-beta * dx)
     B = gamma * dx if beta == 0.0 else gamma / beta * -math.expm1(-beta * dx)
     return np.array([A, B, B * 0.5, B * 2.0])
@@ -77,7 +77,7 @@ def const_seg(beta, gamma, dx):
 
 @pytest.mark.parametrize("beta", [0.0, 1e-9, 0.3, 2.0, 15.0])
 def test_cut_matches_constant_medium_and_recombines(beta):
-    """Eq. 2.17: a cut piece equals the closed form on the shorter length, and
+    """Eq. 2.20: a cut piece equals the closed form on the shorter length, and
     near piece (+) far piece gives the whole segment back."""
     dx, gamma = 0.7, 1.3
     s = const_seg(beta, gamma, dx)
@@ -90,13 +90,13 @@ def test_cut_matches_constant_medium_and_recombines(beta):
 
 
 def test_cut_transparent_special_case():
-    """Eq. 2.17, A = 1: B_i = B dx_i / dx."""
+    """Eq. 2.20, A = 1: B_i = B dx_i / dx."""
     s = np.array([1.0, 0.8, 0.2, 0.4])
     np.testing.assert_allclose(O.cut(s, 0.25), [1.0, 0.2, 0.05, 0.1], rtol=1e-15)
 
 
 def test_average_properties():
-    """Eq. 2.18: idempotent, symmetric, geometric mean of A, arithmetic mean of B;
+    """Eq. 2.21: idempotent, symmetric, geometric mean of A, arithmetic mean of B;
     for equal absorption it is the limit of finer and finer alternation of the
     two media (the construction in the proof of Sec. 2.5)."""
     for _ in range(10):
@@ -172,7 +172,7 @@ def test_ortho_rays_and_c1_rectangles():
 
 
 def test_perspective_ray_reprojects_to_its_pixel():
-    """Eq. 2.2 and Eq. 2.3 agree: the point o + r of pixel (i, j) lies on the
+    """Eq. 2.5 and Eq. 2.6 agree: the point o + r of pixel (i, j) lies on the
     projection plane (depth n) at pixel coordinates (i, j)."""
     cam = I.perspective_camera(7, 96, 54)
     t, u, v = (np.array(x) for x in (cam.t, cam.u, cam.v))
@@ -368,7 +368,7 @@ def _tiny(level, seed=1809):
 @pytest.mark.parametrize("level", [0, 1, 2])
 def test_render_matches_quadrature_of_the_closed_form(level):
     """Whole-image brute force on 1, 8 and 64 leaves: per ray, the closed-form
-    solution (Eq. 2.13) by trapezoid quadrature on 2e5 points with point
+    solution (Eq. 2.12) by trapezoid quadrature on 2e5 points with point
     location -- no segments, no sorting, no group action -- against the oracle
     with a fine discretisation; the configured RK4 x 4 stays within its
     truncation error.  Includes a non-zero background."""
