@@ -135,6 +135,37 @@ int ocr_set_camera(ocr_forest *F, const ocr_camera *cams, int ncams);
  * per pixel.  stats may be NULL. */
 int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats);
 
+/* Pruning for callers that cannot allocate device memory at the time they
+ * need it: an application that serves all device memory from a pool it
+ * reserved up front, a real-time loop that must not take the device-wide
+ * synchronisation an allocation implies, a plug-in living inside another
+ * program's memory budget.  The paper has no counterpart: it is the pruning
+ * step above (Sec. 3.1) packaged so that it allocates nothing.
+ *
+ * Inputs (device, caller-owned): d_leaf_geo [nleaves * 4] int32, per leaf
+ * {x, y, z, level} with anchors in units of 2^-max_level, Morton order;
+ * 16-byte aligned.  cam: host struct, read as float32 exactly like
+ * ocr_set_camera.  Outputs (device, caller-owned): d_rects [nleaves * 4]
+ * int32, the same rectangles ocr_render reports in ocr_stats.d_rects (may be
+ * NULL; 16-byte aligned); d_visible_idx [nleaves] int32, the indices of the
+ * visible leaves in increasing order (entries past the count are left
+ * untouched).  *h_nvisible (host) receives the number of visible leaves.
+ *
+ * It calls no allocation routine.  Its only scratch is a fixed array of
+ * OCR_NOALLOC_MAX_LEAVES / 1024 + 2 eight-byte words (512 KiB) compiled into
+ * the library, which every device that loads the library keeps until the
+ * process exits.  nleaves above OCR_NOALLOC_MAX_LEAVES returns
+ * OCR_ERR_INVALID.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress, with the device current), so make the first
+ * call before any stream capture.  All calls share the one array and reset
+ * it at their start: calls that overlap on the GPU (different streams,
+ * different host threads on one device) race and must be serialised by the
+ * caller.  Blocks the host until the result is ready. */
+#define OCR_NOALLOC_MAX_LEAVES (1 << 26)
+int ocr_prune_noalloc(const int32_t *d_leaf_geo, int64_t nleaves, int max_level,
+                      const ocr_camera *cam, int32_t *d_rects, int32_t *d_visible_idx,
+                      int64_t *h_nvisible, void *stream);
+
 /* Device memory held by the library for this forest (topology + scratch). */
 int64_t ocr_device_bytes(const ocr_forest *F);
 

@@ -156,3 +156,22 @@ def device_bytes(h) -> int:
 def destroy(h):
     if h:
         lib().ocr_destroy(h)
+
+
+def prune_noalloc(d_leaf_geo, nleaves: int, max_level: int, cam, d_rects, d_visible_idx,
+                  stream=None) -> int:
+    """ocr_prune_noalloc: pruning without any device allocation (for callers
+    that cannot allocate when they need the result).  Returns the number of
+    visible leaves; d_visible_idx[:n] holds their indices in Morton order."""
+    L = lib()
+    fn = L.ocr_prune_noalloc
+    fn.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.POINTER(Camera), C.c_void_p, C.c_void_p,
+                   C.POINTER(C.c_int64), C.c_void_p]
+    c = Camera()
+    c.o[:], c.v[:], c.t[:], c.u[:] = cam.o, cam.v, cam.t, cam.u
+    c.ell, c.near_, c.far_ = float(cam.ell), float(cam.near), float(cam.far)
+    c.w, c.h, c.ortho = int(cam.w), int(cam.h), int(bool(cam.ortho))
+    n = C.c_int64(-1)
+    _check(fn(_ptr(d_leaf_geo), int(nleaves), int(max_level), C.byref(c), _ptr(d_rects),
+              _ptr(d_visible_idx), C.byref(n), _ptr(stream)), "ocr_prune_noalloc")
+    return int(n.value)

@@ -939,3 +939,183 @@ cudaError_t launch_coarsen(const Topo &T, const Field &Fd, const Cam &C, const I
 }
 
 }  // namespace ocr
+
+// ==========================================================================
+// Pruning without device allocation (ocr_prune_noalloc).
+//
+// Some callers cannot allocate device memory when they need a result: an
+// application that hands out all device memory from a pool it reserved up
+// front, a real-time loop that must not take the device-wide synchronisation
+// cudaMalloc implies, or a plug-in that runs inside another program's memory
+// budget.  For them this entry point computes the pruning step -- every
+// leaf's pixel rectangle, exactly as cull_leaves_kernel does, plus the list of
+// visible leaves in Morton order -- using only caller-provided inputs and
+// outputs and one fixed scratch array that lives in the library's image on
+// each device.  The scratch holds the tile ticket, an error word and one
+// status word per tile of the single-pass (decoupled look-back) compaction.
+// ==========================================================================
+#include "../../include/ocraycast.h"
+
+#include <mutex>
+
+namespace ocr {
+namespace {
+
+constexpr int kNoAllocThreads = 256, kNoAllocItems = 4;
+constexpr int kNoAllocTile = kNoAllocThreads * kNoAllocItems;
+constexpr long long kNoAllocMaxTiles = (long long)OCR_NOALLOC_MAX_LEAVES / kNoAllocTile;
+constexpr unsigned long long kTileAggregate = 1ull << 62, kTilePrefix = 2ull << 62;
+constexpr unsigned long long kTileValue = (1ull << 62) - 1;
+constexpr int kLookbackSpins = 1 << 20;
+constexpr int kNoAllocMaxDevices = 64;
+
+// [0] tile ticket, [1] error word, [2 + t] status of tile t (flag << 62 | count).
+// 2 + 65536 words = 512 KiB on every device that loads the library.
+static __device__ __align__(256) unsigned long long g_prune_scratch[2 + kNoAllocMaxTiles];
+
+__global__ void __launch_bounds__(kNoAllocThreads)
+    prune_compact_kernel(const int4 *__restrict__ geo, int n, int L, Cam c, int4 *rects,
+                         int *vis_idx, unsigned long long *scratch) {
+  __shared__ int s_tile, s_wsum[kNoAllocThreads / 32];
+  __shared__ long long s_excl;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // tiles are numbered in the order CTAs start, so every predecessor a CTA
+  // waits for is already running
+  if (tid == 0) s_tile = (int)atomicAdd(scratch, 1ull);
+  __syncthreads();
+  const int tile = s_tile;
+  const int base = tile * kNoAllocTile + tid * kNoAllocItems;
+  const float scale = ldexpf(1.f, -L);
+  bool vis[kNoAllocItems];
+  int cnt = 0;
+#pragma unroll
+  for (int q = 0; q < kNoAllocItems; ++q) {
+    const int k = base + q;
+    vis[q] = false;
+    if (k < n) {
+      const int4 g = geo[k];
+      const int4 r = box_rect(c, node_lo(g, scale), ldexpf(1.f, -g.w));
+      if (rects) rects[k] = r;
+      vis[q] = r.x <= r.y;
+      cnt += vis[q];
+    }
+  }
+  int x = cnt;  // inclusive prefix within the warp
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_wsum[wid] = x;
+  __syncthreads();
+  int before = 0, total = 0;
+  for (int w = 0; w < kNoAllocThreads / 32; ++w) {
+    if (w < wid) before += s_wsum[w];
+    total += s_wsum[w];
+  }
+  if (tid == 0) {
+    unsigned long long *st = scratch + 2;
+    long long excl = 0;
+    if (tile == 0) {
+      atomicExch(st, kTilePrefix | (unsigned long long)total);
+    } else {
+      atomicExch(st + tile, kTileAggregate | (unsigned long long)total);
+      for (int p = tile - 1; p >= 0; --p) {
+        unsigned long long w = 0;
+        int spins = 0;
+        while (((w = atomicAdd(st + p, 0ull)) >> 62) == 0ull) {
+          if (++spins > kLookbackSpins) {  // never expected: give up, flag, return
+            atomicExch(scratch + 1, 1ull);
+            break;
+          }
+          __nanosleep(64);
+        }
+        excl += (long long)(w & kTileValue);
+        if ((w >> 62) != 1ull) break;  // an inclusive prefix (or a timeout) ends the walk
+      }
+      atomicExch(st + tile, kTilePrefix | (unsigned long long)(excl + total));
+    }
+    s_excl = excl;
+  }
+  __syncthreads();
+  long long pos = s_excl + before + x - cnt;
+#pragma unroll
+  for (int q = 0; q < kNoAllocItems; ++q)
+    if (vis[q]) vis_idx[pos++] = base + q;
+}
+
+}  // namespace
+}  // namespace ocr
+
+extern "C" int ocr_prune_noalloc(const int32_t *d_leaf_geo, int64_t nleaves, int max_level,
+                                 const ocr_camera *cam, int32_t *d_rects, int32_t *d_visible_idx,
+                                 int64_t *h_nvisible, void *stream) {
+  using namespace ocr;
+  if (!d_leaf_geo || !cam || !d_visible_idx || !h_nvisible) return OCR_ERR_INVALID;
+  if (nleaves < 1 || nleaves > OCR_NOALLOC_MAX_LEAVES) return OCR_ERR_INVALID;
+  if (max_level < 0 || max_level > 20) return OCR_ERR_INVALID;
+  if (((uintptr_t)d_leaf_geo & 15) || ((uintptr_t)d_rects & 15)) return OCR_ERR_INVALID;
+  const ocr_camera &cc = *cam;
+  if (cc.w < 1 || cc.h < 1 || (int64_t)cc.w * cc.h > (1ll << 31) - 1 || !(cc.near_ > 0.0) ||
+      !(cc.far_ > cc.near_) || !(cc.ell > 0.0))
+    return OCR_ERR_INVALID;
+  // the same float32 camera constants as ocr_set_camera
+  Cam k{};
+  for (int a = 0; a < 3; ++a) {
+    k.o[a] = (float)cc.o[a];
+    k.v[a] = (float)(cc.ortho ? cc.v[a] / cc.near_ : cc.v[a]);
+    k.lt[a] = (float)(cc.ell * cc.t[a]);
+    k.lu[a] = (float)(cc.ell * cc.u[a]);
+    k.t[a] = (float)cc.t[a];
+    k.u[a] = (float)cc.u[a];
+    k.vn[a] = (float)(cc.v[a] / cc.near_);
+  }
+  k.n = (float)cc.near_;
+  k.f = (float)cc.far_;
+  k.ell = (float)cc.ell;
+  k.cw = 0.5f * (float)(cc.w - 1);
+  k.ch = 0.5f * (float)(cc.h - 1);
+  k.w = cc.w;
+  k.h = cc.h;
+  k.ortho = cc.ortho ? 1 : 0;
+  k.amin = cc.ortho ? 0.f : 1.f;
+  k.amax = (float)(cc.ortho ? cc.far_ : cc.far_ / cc.near_);
+
+  // device address of the scratch array: looked up once per device, with that
+  // device current (the array's name is only a stand-in in host code)
+  static std::mutex mu;
+  static void *addr[kNoAllocMaxDevices] = {};
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return OCR_ERR_CUDA;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return OCR_ERR_UNSUPPORTED;
+  unsigned long long *scratch;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+      void *p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_prune_scratch) != cudaSuccess || !p) return OCR_ERR_CUDA;
+      addr[dev] = p;
+    }
+    scratch = static_cast<unsigned long long *>(addr[dev]);
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int ntiles = (int)((nleaves + kNoAllocTile - 1) / kNoAllocTile);
+  // the ticket, the error word and the tiles' status words must start at zero
+  if (cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * (2 + (size_t)ntiles), st) !=
+      cudaSuccess)
+    return OCR_ERR_CUDA;
+  prune_compact_kernel<<<ntiles, kNoAllocThreads, 0, st>>>(
+      reinterpret_cast<const int4 *>(d_leaf_geo), (int)nleaves, max_level, k,
+      reinterpret_cast<int4 *>(d_rects), d_visible_idx, scratch);
+  if (cudaGetLastError() != cudaSuccess) return OCR_ERR_CUDA;
+  unsigned long long h_err = 0, h_last = 0;
+  if (cudaMemcpyAsync(&h_err, scratch + 1, sizeof h_err, cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(&h_last, scratch + 2 + (ntiles - 1), sizeof h_last,
+                      cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return OCR_ERR_CUDA;
+  if (h_err) return OCR_ERR_DEVICE;
+  *h_nvisible = (int64_t)(h_last & kTileValue);
+  return OCR_OK;
+}
