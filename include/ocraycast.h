@@ -45,8 +45,10 @@ extern "C" {
 
 #define OCR_GEOM_CUBE 0
 
-#define OCR_RK4 0    /* nsteps equal classical RK4 steps per segment */
-#define OCR_DOPRI5 1 /* Dormand-Prince 5(4) inside the bisection of Algorithm 1 */
+#define OCR_RK4 0     /* nsteps equal classical RK4 steps per segment */
+#define OCR_DOPRI5 1  /* Dormand-Prince 5(4) inside the bisection of Algorithm 1 */
+#define OCR_GAUSS2 2  /* implicit 2-stage Gauss closed form (Eqs. 2.32-2.33), Algorithm 1 */
+#define OCR_SIMPSON 3 /* Simpson quadrature of the closed form (Eq. 2.34), Algorithm 1 */
 
 typedef struct ocr_forest ocr_forest;
 
@@ -74,10 +76,12 @@ typedef struct {
 } ocr_camera;
 
 /* Per-segment integrator.  RK4: nsteps equal steps from the far end, each
- * combined by Eq. 2.14.  DOPRI5: a step over [x1, x2] is replaced by its two
- * halves, combined near (+) far, while dx * kappa(xi) > c_rk at a stage
- * point or the embedded error estimate exceeds tol, up to max_depth halvings
- * (Algorithm 1).  bg is the background intensity I_b per channel. */
+ * combined by Eq. 2.14.  DOPRI5, GAUSS2, SIMPSON: a step over [x1, x2] is
+ * replaced by its two halves, combined near (+) far, while
+ * dx * kappa(xi) > c_rk at a node of the step (or, for DOPRI5, the embedded
+ * error estimate exceeds tol), up to max_depth halvings (Algorithm 1).  The
+ * Gauss nodes are x1 + (1/2 -+ sqrt(3)/6) dx, x1 the far end.  bg is the
+ * background intensity I_b per channel. */
 typedef struct {
   int method;
   int nsteps;

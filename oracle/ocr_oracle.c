@@ -325,12 +325,53 @@ static void dopri_step(const seg_ctx *S, double x1, double x2, double *y5, doubl
   *err = e;
 }
 
-/* Algorithm 1: if a stage sees dx kappa > c_RK (or the embedded error exceeds
- * tol), split at the midpoint and return segeval(mid, x2) (+) segeval(x1, mid). */
+/* Eqs. 2.32-2.33: the implicit two-stage Gauss method solved in closed form.
+ * With x measured from the far end x1, the formula is the Gauss-Legendre
+ * method when xi_0 = x1 + (1/2 - sqrt(3)/6) dx and xi_1 = x1 + (1/2 + sqrt(3)/6) dx. */
+static void gauss2_step(const seg_ctx *S, double x1, double x2, double *y, double *kmax) {
+  double dx = x2 - x1, r3 = sqrt(3.0);
+  double k0[4], k1[4];
+  medium_at(S, x1 + (0.5 - r3 / 6.0) * dx, k0);
+  medium_at(S, x1 + (0.5 + r3 / 6.0) * dx, k1);
+  double a1 = dx * (k0[0] + k1[0]) / 4.0;
+  double a2 = dx * dx * k0[0] * k1[0] / 12.0;
+  double den = 1.0 + a1 + a2;
+  y[0] = (1.0 - a1 + a2) / den;
+  for (int c = 1; c < 4; ++c) {
+    double b1 = dx * (k0[c] + k1[c]) / 2.0;
+    double b2 = dx * dx * (k0[0] * k1[c] - k1[0] * k0[c]) * r3 / 12.0;
+    y[c] = (b1 + b2) / den;
+  }
+  *kmax = dx * (k0[0] > k1[0] ? k0[0] : k1[0]);
+}
+
+/* Eq. 2.34: Simpson's rule on the closed form Eq. 2.12, nodes at the far end,
+ * the midpoint and the near end. */
+static void simpson_step(const seg_ctx *S, double x1, double x2, double *y, double *kmax) {
+  double dx = x2 - x1;
+  double k0[4], kh[4], k2[4];
+  medium_at(S, x1, k0);
+  medium_at(S, 0.5 * (x1 + x2), kh);
+  medium_at(S, x2, k2);
+  y[0] = exp(-dx * (k0[0] + 4.0 * kh[0] + k2[0]) / 6.0);
+  double sa = sqrt(y[0]);
+  for (int c = 1; c < 4; ++c) y[c] = dx * (y[0] * k0[c] + 4.0 * sa * kh[c] + k2[c]) / 6.0;
+  double m = k0[0] > kh[0] ? k0[0] : kh[0];
+  *kmax = dx * (m > k2[0] ? m : k2[0]);
+}
+
+/* Algorithm 1: if a stage sees dx kappa > c_RK (or, for DOPRI5, the embedded
+ * error exceeds tol), split at the midpoint and return
+ * segeval(mid, x2) (+) segeval(x1, mid). */
 static void segeval(const seg_ctx *S, const orc_integrator *I, double x1, double x2, int depth,
                     double *out, int64_t *nsteps) {
-  double y5[4], kmax, err;
-  dopri_step(S, x1, x2, y5, &kmax, &err);
+  double y5[4], kmax, err = 0.0;
+  if (I->method == ORC_GAUSS2)
+    gauss2_step(S, x1, x2, y5, &kmax);
+  else if (I->method == ORC_SIMPSON)
+    simpson_step(S, x1, x2, y5, &kmax);
+  else
+    dopri_step(S, x1, x2, y5, &kmax, &err);
   ++*nsteps;
   if (depth < I->max_depth && (kmax > I->c_rk || err > I->tol)) {
     double xm = 0.5 * (x1 + x2), near_s[4], far_s[4];

@@ -41,11 +41,13 @@ typedef struct {
   int w, h, ortho;
 } orc_camera;
 
-enum { ORC_RK4 = 0, ORC_DOPRI5 = 1 };
+enum { ORC_RK4 = 0, ORC_DOPRI5 = 1, ORC_GAUSS2 = 2, ORC_SIMPSON = 3 };
 typedef struct {
-  int method;      /* ORC_RK4: nsteps equal classical RK4 steps; ORC_DOPRI5: Algorithm 1 */
+  int method;      /* ORC_RK4: nsteps equal classical RK4 steps; the others inside Algorithm 1:
+                      ORC_DOPRI5 Dormand-Prince 5(4), ORC_GAUSS2 the implicit 2-stage Gauss
+                      closed form (Eqs. 2.32-2.33), ORC_SIMPSON quadrature (Eq. 2.34) */
   int nsteps;
-  double tol;      /* DOPRI5: split when the embedded error estimate exceeds tol */
+  double tol;      /* DOPRI5 only: split when the embedded error estimate exceeds tol */
   double c_rk;     /* split when dx * kappa(xi_j) > c_rk at any stage point */
   int max_depth;   /* bisection depth cap */
   double bg[3];    /* background intensity I_b per channel */

@@ -192,6 +192,54 @@ __device__ float4 integrate_segment(const Cubic &cu, const TF &tf, float dx, con
   unsigned idx = 0;
   float4 kq0 = medium(cu, tf, 0.f);
   const float4 one = seg_identity();
+  if (I.method != 1) {  // Gauss-2 (Eqs. 2.32-2.33) or Simpson (Eq. 2.34) inside Algorithm 1
+    for (;;) {
+      const float dtau = ldexpf(1.f, -depth);
+      const float t0 = (float)idx * dtau;
+      const float H = dx * dtau;
+      float4 S, kq1 = kq0;
+      float kmax;
+      if (I.method == 2) {
+        // Gauss points c = 1/2 -+ sqrt(3)/6, measured from the step's far end
+        const float4 g0 = medium(cu, tf, fmaf(0.21132486540518713f, dtau, t0));
+        const float4 g1 = medium(cu, tf, fmaf(0.78867513459481287f, dtau, t0));
+        const float a1 = 0.25f * H * (g0.x + g1.x), a2 = (H * H / 12.f) * g0.x * g1.x;
+        const float inv = 1.f / (1.f + a1 + a2);
+        const float h2 = H * H * 0.14433756729740644f;  // H^2 sqrt(3) / 12
+        S.x = (1.f - a1 + a2) * inv;
+        S.y = (0.5f * H * (g0.y + g1.y) + h2 * (g0.x * g1.y - g1.x * g0.y)) * inv;
+        S.z = (0.5f * H * (g0.z + g1.z) + h2 * (g0.x * g1.z - g1.x * g0.z)) * inv;
+        S.w = (0.5f * H * (g0.w + g1.w) + h2 * (g0.x * g1.w - g1.x * g0.w)) * inv;
+        kmax = H * fmaxf(g0.x, g1.x);
+      } else {
+        // Simpson nodes: far end, midpoint, near end
+        const float4 kh = medium(cu, tf, t0 + 0.5f * dtau);
+        kq1 = medium(cu, tf, t0 + dtau);
+        const float e = -(H / 6.f) * (kq0.x + 4.f * kh.x + kq1.x);
+        const float sa = __expf(0.5f * e), A = sa * sa;
+        const float w0 = (H / 6.f) * A, wh = (H / 6.f) * 4.f * sa, w1 = H / 6.f;
+        S = make_float4(A, fmaf(w0, kq0.y, fmaf(wh, kh.y, w1 * kq1.y)),
+                        fmaf(w0, kq0.z, fmaf(wh, kh.z, w1 * kq1.z)),
+                        fmaf(w0, kq0.w, fmaf(wh, kh.w, w1 * kq1.w)));
+        kmax = H * fmaxf(fmaxf(kq0.x, kh.x), kq1.x);
+      }
+      ++steps;
+      if (depth < I.max_depth && kmax > I.c_rk) {
+        ++depth;  // far half first
+        idx <<= 1;
+        continue;
+      }
+      acc = seg_combine(S, acc);
+      kq0 = kq1;  // Simpson: the next step starts where this one ended (unused by Gauss)
+      ++idx;
+      while (depth > 0 && !(idx & 1u)) {
+        idx >>= 1;
+        --depth;
+      }
+      if (depth == 0) break;
+    }
+    return acc;
+  }
   for (;;) {
     const float dtau = ldexpf(1.f, -depth);
     const float t0 = (float)idx * dtau;

@@ -462,3 +462,98 @@ def test_overlapping_segments_are_cut_and_averaged():
         tot = O.combine(near, O.cut(big, 1.0 - fr))
         np.testing.assert_allclose(r["rgba"][j, i], np.concatenate([tot[1:], [1 - tot[0]]]),
                                    rtol=1e-12)
+
+
+# ------------------------------------------------ Sec. 2.7: Gauss-2, Simpson --
+@pytest.mark.parametrize("kappa", [0.5, 7.0, 19.0])
+def test_gauss2_constant_medium_is_pade22(kappa):
+    """Eqs. 2.32-2.33 on a constant medium: A is the (2,2) Pade approximant of
+    exp(-z), z = k dx, and B = (q/k)(1 - A)."""
+    q = np.array([0.25, 0.5, 0.75])
+    f, tf = _one_leaf(np.full(8, 3.0), np.tile(np.concatenate([[kappa], q]), (8, 1)))
+    of = O.OracleForest(f, tf)
+    org, d = np.array([0.5, 0.5, -1.0]), np.array([0.0, 0.0, 1.0])
+    seg, st = O.segment_ab(of, {"method": "gauss2", "c_rk": 1e9, "max_depth": 0}, 0, org, d,
+                           1.0, 2.0)
+    z = kappa
+    A = (1 - z / 2 + z * z / 12) / (1 + z / 2 + z * z / 12)
+    assert st == 1
+    np.testing.assert_allclose(seg, np.concatenate([[A], q / kappa * (1 - A)]), rtol=1e-13)
+
+
+def test_gauss2_equals_direct_gauss_legendre_solve():
+    """On a varying medium one Gauss-2 step equals the two-stage Gauss-Legendre
+    method (c = 1/2 -+ sqrt(3)/6 from the far end, A = [[1/4, 1/4 - sqrt(3)/6],
+    [1/4 + sqrt(3)/6, 1/4]], b = (1/2, 1/2)) solved as a linear system."""
+    vals = RNG.uniform(0.5, 6.5, 8)
+    knots = np.column_stack([RNG.uniform(0, 8, 8), RNG.uniform(0, 1, (8, 3))])
+    f, tf = _one_leaf(vals, knots)
+    of = O.OracleForest(f, tf)
+    d = np.array([0.3, -0.4, 0.85])
+    org = np.array([0.5, 0.5, 0.5]) - 2.0 * d
+    hit, a0, a1 = O.ray_leaf(of, 0, org, d, 0, 1e9)
+    seg, _ = O.segment_ab(of, {"method": "gauss2", "c_rk": 1e9, "max_depth": 0}, 0, org, d, a0, a1)
+    r3 = math.sqrt(3.0)
+    c = np.array([0.5 - r3 / 6, 0.5 + r3 / 6])
+    Ag = np.array([[0.25, 0.25 - r3 / 6], [0.25 + r3 / 6, 0.25]])
+    rl = np.linalg.norm(d)
+    H = (a1 - a0) * rl
+    al = a1 - c * H / rl  # x = c H from the far end
+    s, _ = BF.field_at(f, org[None, :] + al[:, None] * d[None, :])
+    kq = BF.tf_numpy(tf, s)
+    beta, gam = kq[:, 0], kq[:, 1:]
+    # stages k_i = g_i - beta_i (y0 + H sum_j A_ij k_j): (I + H diag(beta) A) k = g - beta y0
+    M = np.eye(2) + H * beta[:, None] * Ag
+    kA = np.linalg.solve(M, -beta * 1.0)
+    ref = [1.0 + H * kA.sum() / 2]
+    for ch in range(3):
+        kB = np.linalg.solve(M, gam[:, ch])
+        ref.append(H * kB.sum() / 2)
+    np.testing.assert_allclose(seg, ref, rtol=1e-12, atol=1e-14)
+
+
+def test_simpson_exact_for_cubic_media():
+    """Eq. 2.34: Simpson's rule integrates cubics exactly, so with kappa and q
+    linear in the trilinear field (cubic along the ray) A = exp(-int kappa)
+    exactly, and with kappa = 0, B = int q exactly (Gauss-Legendre reference)."""
+    vals = RNG.uniform(0.5, 6.5, 8)
+    xg, wg = np.polynomial.legendre.leggauss(8)
+    d = np.array([0.35, 0.2, -0.9])
+    org = np.array([0.5, 0.45, 0.5]) - 2.0 * d
+    for kap_knots, q_r in [(np.arange(8) / 4.0, np.full(8, 0.5)),
+                           (np.zeros(8), np.arange(8) / 8.0)]:
+        knots = np.column_stack([kap_knots, q_r, np.full(8, 0.25), np.full(8, 0.125)])
+        f, tf = _one_leaf(vals, knots)
+        of = O.OracleForest(f, tf)
+        hit, a0, a1 = O.ray_leaf(of, 0, org, d, 0, 1e9)
+        seg, _ = O.segment_ab(of, {"method": "simpson", "c_rk": 1e9, "max_depth": 0}, 0, org, d,
+                              a0, a1)
+        al = 0.5 * (a0 + a1) + 0.5 * (a1 - a0) * xg
+        s, _ = BF.field_at(f, org[None, :] + al[:, None] * d[None, :])
+        kq = BF.tf_numpy(tf, s)
+        L = (a1 - a0) * np.linalg.norm(d)
+        tau = (wg * kq[:, 0]).sum() * 0.5 * L
+        np.testing.assert_allclose(seg[0], math.exp(-tau), rtol=1e-13)
+        if not kap_knots.any():
+            np.testing.assert_allclose(seg[1], (wg * kq[:, 1]).sum() * 0.5 * L, rtol=1e-13)
+
+
+@pytest.mark.parametrize("method", ["gauss2", "simpson"])
+def test_gauss2_simpson_converge_inside_algorithm1(method):
+    """Inside Algorithm 1 both converge to the closed form of a constant medium
+    as c_RK shrinks (Gauss at rate c_RK^4, Simpson's B at c_RK^2 or better),
+    and split uniformly into 2^(d+1) - 1 evaluated steps."""
+    kappa, q = 12.0, np.array([0.25, 0.5, 0.875])
+    f, tf = _one_leaf(np.full(8, 2.0), np.tile(np.concatenate([[kappa], q]), (8, 1)))
+    of = O.OracleForest(f, tf)
+    org, d = np.array([0.5, 0.5, -1.0]), np.array([0.0, 0.0, 1.0])
+    exact = np.concatenate([[math.exp(-kappa)], q / kappa * -math.expm1(-kappa)])
+    errs = []
+    for c_rk in (0.5, 0.25, 0.125):
+        seg, st = O.segment_ab(of, {"method": method, "c_rk": c_rk, "max_depth": 30}, 0, org, d,
+                               1.0, 2.0)
+        depth = math.ceil(math.log2(kappa / c_rk))
+        assert st == 2 ** (depth + 1) - 1
+        errs.append(np.abs(seg - exact).max())
+    assert errs[2] < errs[1] < errs[0]
+    assert errs[1] / errs[2] > (12 if method == "gauss2" else 3.5)
