@@ -83,6 +83,8 @@ def lib():
                                     d, P(C.c_int32), P(C.c_uint8), C.c_double, C.c_double,
                                     C.c_int, P(C.c_int64)]
         _lib.orc_render.restype = C.c_int64
+        _lib.orc_render_grad.argtypes = [P(Forest_), P(Camera_), P(Integrator_), d, d, d, C.c_int]
+        _lib.orc_render_grad.restype = C.c_int
     return _lib
 
 
@@ -239,3 +241,19 @@ def render(forest, tf, cam, integ: dict, rows=None, bg=(0.0, 0.0, 0.0), nthreads
         raise MemoryError("oracle render: allocation failed")
     return {"rgba": rgba, "counts": counts, "uncertain": unc.astype(bool),
             "segments": int(total), "steps": int(steps.value), "rows": rows_arr}
+
+
+def render_grad(forest, tf, cam, integ: dict, dL_drgba, bg=(0.0, 0.0, 0.0), nthreads: int = 0):
+    """FP64 gradient of L with respect to nodal values [N, 8] and knots [8, 4],
+    given dL/d(rgba) [h, w, 4]."""
+    of = OracleForest(forest, tf)
+    cs = camera_struct(cam)
+    ist = integrator_struct(integ, bg)
+    gb = np.ascontiguousarray(dL_drgba, dtype=np.float64).reshape(cam.h, cam.w, 4)
+    gn = np.zeros((forest.nleaves, 8))
+    gt = np.zeros((8, 4))
+    rc = lib().orc_render_grad(C.byref(of.s), C.byref(cs), C.byref(ist), _ptr(gb, C.c_double),
+                               _ptr(gn, C.c_double), _ptr(gt, C.c_double), int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle gradient: only RK4 and DOPRI5 are differentiated")
+    return gn, gt

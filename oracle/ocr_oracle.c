@@ -254,6 +254,11 @@ static void medium_at(const seg_ctx *S, double x, double *kq) {
   orc_tf_eval(S->F, s, kq);
 }
 
+/* One classical RK4 step of length hs starting at distance x0 from the far
+ * end, from the state y0 (NULL: from (1, 0)). */
+static void rk4_segment_from(const seg_ctx *S, double x0, double hs, const double *y0,
+                             double *out);
+
 /* Classical RK4 on A' = -kappa A, B' = q - kappa B (Eq. 2.29), x from the far
  * end, state continued across nsteps equal steps starting from (1, 0). */
 static void rk4_segment(const seg_ctx *S, double dx, int nsteps, double *y) {
@@ -278,6 +283,24 @@ static void rk4_segment(const seg_ctx *S, double dx, int nsteps, double *y) {
     RHS(kq2, yt, k4);
     for (int c = 0; c < 4; ++c) y[c] += hs / 6.0 * (k1[c] + 2.0 * k2[c] + 2.0 * k3[c] + k4[c]);
   }
+}
+
+static void rk4_segment_from(const seg_ctx *S, double x0, double hs, const double *y0,
+                             double *out) {
+  double y[4] = {1.0, 0.0, 0.0, 0.0};
+  if (y0) memcpy(y, y0, sizeof y);
+  double kq0[4], kq1[4], kq2[4], k1[4], k2[4], k3[4], k4[4], yt[4];
+  medium_at(S, x0, kq0);
+  medium_at(S, x0 + 0.5 * hs, kq1);
+  medium_at(S, x0 + hs, kq2);
+  RHS(kq0, y, k1);
+  for (int c = 0; c < 4; ++c) yt[c] = y[c] + 0.5 * hs * k1[c];
+  RHS(kq1, yt, k2);
+  for (int c = 0; c < 4; ++c) yt[c] = y[c] + 0.5 * hs * k2[c];
+  RHS(kq1, yt, k3);
+  for (int c = 0; c < 4; ++c) yt[c] = y[c] + hs * k3[c];
+  RHS(kq2, yt, k4);
+  for (int c = 0; c < 4; ++c) out[c] = y[c] + hs / 6.0 * (k1[c] + 2.0 * k2[c] + 2.0 * k3[c] + k4[c]);
 }
 
 /* Dormand-Prince 5(4) tableau (Dormand & Prince, J. Comput. Appl. Math. 6,
@@ -610,4 +633,237 @@ int64_t orc_render(const orc_forest *F, const orc_camera *C, const orc_integrato
   free(rect); free(vis); free(pext); free(rowpos); free(rstart); free(rleaf); free(fill);
   if (nsteps_total) *nsteps_total = steps;
   return total;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gradient (reverse mode, FP64)                                             */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  double *g_nodal; /* [N*8] */
+  double *g_tf;    /* [32] */
+} grad_acc;
+
+/* Adjoint of the medium at distance x from the far end: vbar = dL/d(kappa,
+ * q_r, q_g, q_b) there; accumulates into the knot values and, through the
+ * transfer function's slope and the trilinear weights, into the leaf's 8
+ * nodal values. */
+static void medium_bwd(const seg_ctx *S, int leaf, double x, const double *vbar, grad_acc *G) {
+  const orc_forest *F = S->F;
+  double alpha = S->a_out - x / S->rlen;
+  double u[3];
+  for (int a = 0; a < 3; ++a) u[a] = (S->org[a] + alpha * S->dir[a] - S->lo[a]) / S->h;
+  double s = orc_trilinear(S->nodal, u[0], u[1], u[2]);
+  double zr = (s - F->s_min) / (F->s_max - F->s_min) * 7.0;
+  int inside = zr > 0.0 && zr < 7.0;
+  double z = zr < 0.0 ? 0.0 : (zr > 7.0 ? 7.0 : zr);
+  int k = (int)floor(z);
+  if (k > 6) k = 6;
+  double w = z - k, sbar = 0.0;
+  for (int c = 0; c < 4; ++c) {
+#pragma omp atomic
+    G->g_tf[4 * k + c] += (1.0 - w) * vbar[c];
+#pragma omp atomic
+    G->g_tf[4 * (k + 1) + c] += w * vbar[c];
+    if (inside)
+      sbar += vbar[c] * ((double)F->tf[4 * (k + 1) + c] - (double)F->tf[4 * k + c]) * 7.0 /
+              (F->s_max - F->s_min);
+  }
+  for (int c = 0; c < 8; ++c) {
+    double wx = (c & 1) ? u[0] : 1.0 - u[0];
+    double wy = (c & 2) ? u[1] : 1.0 - u[1];
+    double wz = (c & 4) ? u[2] : 1.0 - u[2];
+#pragma omp atomic
+    G->g_nodal[8 * (size_t)leaf + c] += sbar * wx * wy * wz;
+  }
+}
+
+/* Adjoint of one explicit RK step from (1, 0) over [x1, x1 + dx] with nodes
+ * c[i], coefficients a[i][j] and weights b[i] (Eq. 2.31): given ybar =
+ * dL/d(output), accumulates dL/d(kappa, q) at every node. */
+static void rk_step_bwd(const seg_ctx *S, int leaf, double x1, double dx, int ns, const double *c,
+                        const double *a, int lda, const double *b, const double *ybar,
+                        grad_acc *G) {
+  double kq[7][4], Y[7][4], K[7][4], Kb[7][4];
+  for (int i = 0; i < ns; ++i) {
+    for (int q = 0; q < 4; ++q) Y[i][q] = (q == 0) ? 1.0 : 0.0;
+    for (int j = 0; j < i; ++j)
+      for (int q = 0; q < 4; ++q) Y[i][q] += dx * a[i * lda + j] * K[j][q];
+    medium_at(S, x1 + c[i] * dx, kq[i]);
+    RHS(kq[i], Y[i], K[i]);
+  }
+  for (int i = 0; i < ns; ++i)
+    for (int q = 0; q < 4; ++q) Kb[i][q] = dx * b[i] * ybar[q];
+  for (int i = ns - 1; i >= 0; --i) {
+    double vbar[4];
+    /* K_i = (-kappa Y_A, q_c - kappa Y_c) */
+    vbar[0] = 0.0;
+    for (int q = 0; q < 4; ++q) vbar[0] -= Kb[i][q] * Y[i][q];
+    for (int q = 1; q < 4; ++q) vbar[q] = Kb[i][q];
+    medium_bwd(S, leaf, x1 + c[i] * dx, vbar, G);
+    double Yb[4];
+    for (int q = 0; q < 4; ++q) Yb[q] = -kq[i][0] * Kb[i][q];
+    for (int j = 0; j < i; ++j)
+      for (int q = 0; q < 4; ++q) Kb[j][q] += dx * a[i * lda + j] * Yb[q];
+  }
+}
+
+static const double RK4_C[4] = {0.0, 0.5, 0.5, 1.0};
+static const double RK4_A[4][4] = {{0}, {0.5}, {0.0, 0.5}, {0.0, 0.0, 1.0}};
+static const double RK4_B[4] = {1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6};
+
+/* Adjoint of a near (+) far combination: result (A, B) = (An Af, Bn + An Bf). */
+static void combine_bwd(const double *nr, const double *fr, const double *ybar, double *nbar,
+                        double *fbar) {
+  nbar[0] = ybar[0] * fr[0];
+  for (int c = 1; c < 4; ++c) {
+    nbar[0] += ybar[c] * fr[c];
+    nbar[c] = ybar[c];
+    fbar[c] = nr[0] * ybar[c];
+  }
+  fbar[0] = ybar[0] * nr[0];
+}
+
+/* Adjoint of Algorithm 1 (the step tree is re-derived with the same tests). */
+static void segeval_bwd(const seg_ctx *S, const orc_integrator *I, int leaf, double x1, double x2,
+                        int depth, const double *ybar, grad_acc *G) {
+  double y5[4], kmax, err;
+  dopri_step(S, x1, x2, y5, &kmax, &err);
+  if (depth < I->max_depth && (kmax > I->c_rk || err > I->tol)) {
+    double xm = 0.5 * (x1 + x2), nr[4], fr[4], nb[4], fb[4];
+    int64_t dummy = 0;
+    segeval(S, I, x1, xm, depth + 1, fr, &dummy);
+    segeval(S, I, xm, x2, depth + 1, nr, &dummy);
+    combine_bwd(nr, fr, ybar, nb, fb);
+    segeval_bwd(S, I, leaf, x1, xm, depth + 1, fb, G);
+    segeval_bwd(S, I, leaf, xm, x2, depth + 1, nb, G);
+    return;
+  }
+  rk_step_bwd(S, leaf, x1, x2 - x1, 6, DP_C, &DP_A[0][0], 6, DP_B, ybar, G);
+}
+
+/* Adjoint of orc_segment_ab (RK4 and DOPRI5). */
+static void segment_bwd(const orc_forest *F, const orc_integrator *I, int leaf, const double *org,
+                        const double *dir, double a_in, double a_out, const double *ybar,
+                        grad_acc *G) {
+  seg_ctx S;
+  S.F = F;
+  S.nodal = F->nodal + 8 * (size_t)leaf;
+  leaf_box(F, leaf, S.lo, &S.h);
+  memcpy(S.org, org, sizeof S.org);
+  memcpy(S.dir, dir, sizeof S.dir);
+  S.a_out = a_out;
+  S.rlen = sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+  double dx = S.rlen * (a_out - a_in);
+  if (I->method == ORC_RK4) {
+    /* y_{n+1} = step_n(y_n) = R_n y_n + G_n: keep every y_n, then sweep back */
+    int n = I->nsteps;
+    double hs = dx / n;
+    double *ys = (double *)malloc(sizeof(double) * 4 * (size_t)(n + 1));
+    ys[0] = 1.0; ys[1] = ys[2] = ys[3] = 0.0;
+    for (int m = 0; m < n; ++m) { /* step from the state y_m: the same as rk4_segment */
+      double st[4];
+      rk4_segment_from(&S, m * hs, hs, ys + 4 * m, st);
+      memcpy(ys + 4 * (m + 1), st, sizeof st);
+    }
+    double yb[4];
+    memcpy(yb, ybar, sizeof yb);
+    for (int m = n - 1; m >= 0; --m) {
+      /* step m maps y_m to y_{m+1} = S_m (+) y_m with S_m the step from (1, 0):
+       * adjoint of the step's own value, then of the carried state */
+      double sm[4], sb[4], yprev_b[4];
+      rk4_segment_from(&S, m * hs, hs, NULL, sm);
+      combine_bwd(sm, ys + 4 * m, yb, sb, yprev_b);
+      rk_step_bwd(&S, leaf, m * hs, hs, 4, RK4_C, &RK4_A[0][0], 4, RK4_B, sb, G);
+      memcpy(yb, yprev_b, sizeof yb);
+    }
+    free(ys);
+  } else {
+    segeval_bwd(&S, I, leaf, 0.0, dx, 0, ybar, G);
+  }
+}
+
+int orc_render_grad(const orc_forest *F, const orc_camera *C, const orc_integrator *I,
+                    const double *dL_drgba, double *g_nodal, double *g_tf, int nthreads) {
+  if (I->method != ORC_RK4 && I->method != ORC_DOPRI5) return -2;
+  const int W = C->w, H = C->h;
+  int32_t *rect = (int32_t *)malloc(sizeof(int32_t) * 4 * (size_t)F->nleaves);
+  if (!rect) return -1;
+  for (int l = 0; l < F->nleaves; ++l) {
+    int unc = 0;
+    orc_leaf_rect(F, C, l, rect + 4 * (size_t)l, NULL, 0.0, &unc);
+  }
+  memset(g_nodal, 0, sizeof(double) * 8 * (size_t)F->nleaves);
+  memset(g_tf, 0, sizeof(double) * 32);
+  grad_acc G = {g_nodal, g_tf};
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel
+  {
+    int cap = 256;
+    orc_seg *sg = (orc_seg *)malloc(sizeof(orc_seg) * cap);
+    int *sl = (int *)malloc(sizeof(int) * cap);
+#pragma omp for schedule(dynamic, 16)
+    for (int p = 0; p < W * H; ++p) {
+      int i = p % W, j = p / W;
+      const double *gb = dL_drgba + 4 * (size_t)p;
+      if (gb[0] == 0.0 && gb[1] == 0.0 && gb[2] == 0.0 && gb[3] == 0.0) continue;
+      double org[3], dir[3], amin, amax;
+      orc_pixel_ray(C, i, j, org, dir, &amin, &amax);
+      int ns = 0;
+      for (int l = 0; l < F->nleaves; ++l) {
+        const int32_t *rc = rect + 4 * (size_t)l;
+        if (i < rc[0] - 1 || i > rc[1] + 1 || j < rc[2] - 1 || j > rc[3] + 1) continue;
+        double a0, a1;
+        if (!orc_ray_leaf(F, l, org, dir, amin, amax, &a0, &a1)) continue;
+        if (ns == cap) {
+          cap *= 2;
+          sg = (orc_seg *)realloc(sg, sizeof(orc_seg) * cap);
+          sl = (int *)realloc(sl, sizeof(int) * cap);
+        }
+        sg[ns].a_in = a0;
+        sg[ns].a_out = a1;
+        orc_segment_ab(F, I, l, org, dir, a0, a1, sg[ns].s, NULL);
+        sl[ns] = l;
+        ++ns;
+      }
+      /* order near to far by alpha (an index sort carrying the leaf ids) */
+      for (int a = 1; a < ns; ++a) {
+        orc_seg v = sg[a];
+        int vl = sl[a], b = a - 1;
+        while (b >= 0 && sg[b].a_in > v.a_in) {
+          sg[b + 1] = sg[b];
+          sl[b + 1] = sl[b];
+          --b;
+        }
+        sg[b + 1] = v;
+        sl[b + 1] = vl;
+      }
+      /* near transmittance T_k and far aggregate G_k of every segment */
+      double far[4] = {1.0, 0.0, 0.0, 0.0};
+      double *Gk = (double *)malloc(sizeof(double) * 4 * (size_t)(ns > 0 ? ns : 1));
+      for (int k = ns - 1; k >= 0; --k) {
+        memcpy(Gk + 4 * k, far, sizeof far);
+        orc_combine(sg[k].s, far, far);
+      }
+      double T = 1.0;
+      for (int k = 0; k < ns; ++k) {
+        const double *g = Gk + 4 * k;
+        double ybar[4];
+        /* I_c = near.B + T (B_k + A_k (g.B_c + g.A bg_c)), alpha = 1 - T A_k g.A */
+        ybar[0] = 0.0;
+        for (int c = 0; c < 3; ++c) ybar[0] += T * gb[c] * (g[1 + c] + g[0] * I->bg[c]);
+        ybar[0] -= T * gb[3] * g[0];
+        for (int c = 0; c < 3; ++c) ybar[1 + c] = T * gb[c];
+        segment_bwd(F, I, sl[k], org, dir, sg[k].a_in, sg[k].a_out, ybar, &G);
+        T *= sg[k].s[0];
+      }
+      free(Gk);
+    }
+    free(sg);
+    free(sl);
+  }
+  free(rect);
+  return 0;
 }

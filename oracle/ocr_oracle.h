@@ -98,6 +98,18 @@ int64_t orc_render(const orc_forest *F, const orc_camera *C, const orc_integrato
                    uint8_t *uncertain, double band_px, double band_rel, int nthreads,
                    int64_t *nsteps_total);
 
+/* Gradient of L with respect to the nodal values and the transfer-function
+ * knots, given dL/d(rgba) per pixel [h*w*4] (row-major).  FP64 reverse mode:
+ * per pixel the segments are ordered by alpha, each one's adjoint follows
+ * from the transmittance of the nearer ones and the aggregate of the farther
+ * ones (with the background), and is carried back through the integrator
+ * (RK4 or Algorithm 1 with DOPRI5; the step tree is re-derived with the same
+ * tests), the transfer function and the trilinear interpolation.  g_nodal
+ * [nleaves*8], g_tf [32] are overwritten.  Every pixel is tested against
+ * every leaf: for small cases.  Returns 0, or -2 for other integrators. */
+int orc_render_grad(const orc_forest *F, const orc_camera *C, const orc_integrator *I,
+                    const double *dL_drgba, double *g_nodal, double *g_tf, int nthreads);
+
 #ifdef __cplusplus
 }
 #endif

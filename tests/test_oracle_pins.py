@@ -557,3 +557,58 @@ def test_gauss2_simpson_converge_inside_algorithm1(method):
         errs.append(np.abs(seg - exact).max())
     assert errs[2] < errs[1] < errs[0]
     assert errs[1] / errs[2] > (12 if method == "gauss2" else 3.5)
+
+
+# ------------------------------------------------------- gradient (reverse) --
+def _loss(forest, tf, cam, integ, W, bg):
+    r = O.render(forest, tf, cam, integ, bg=bg)
+    return float((r["rgba"] * W).sum()), r["steps"]
+
+
+@pytest.mark.parametrize("integ", [{"method": "rk4", "nsteps": 4},
+                                   {"method": "dopri5", "tol": 1e-6, "c_rk": 0.5, "max_depth": 16}])
+@pytest.mark.parametrize("part", ["knots", "nodal"])
+def test_oracle_gradient_matches_central_differences(integ, part):
+    """The FP64 reverse-mode gradient of L = sum(W * rgba) equals central
+    differences of the (pinned) forward oracle.  Knots: all 32 knot values with
+    the seeded transfer function (L is smooth in them).  Nodal values: with a
+    transfer function linear in s (a piecewise-linear one makes L only
+    piecewise smooth in s, which central differences cannot resolve).
+    Perturbations are applied to the float32 inputs, the step is the exactly
+    representable difference, and a coordinate whose perturbation changes the
+    adaptive step tree is skipped (the gradient is that of the fixed tree)."""
+    fld = I.gaussian_field(4, 7)
+    f = I.uniform_cube_forest(1, fld)
+    tf = I.transfer_function(f.nodal, 3, kappa_max=8.0)
+    if part == "nodal":
+        k = np.arange(8)
+        tf.knots[:] = np.column_stack([0.5 + k, 0.1 + 0.1 * k, 0.8 - 0.1 * k, 0.3 + 0.05 * k])
+        span = float(f.nodal.max() - f.nodal.min())  # keep every s inside the knot range
+        tf.s_min, tf.s_max = float(f.nodal.min()) - 0.5 * span, float(f.nodal.max()) + 0.5 * span
+    cam = I.perspective_camera(5, 8, 6, dist=(1.8, 2.2))
+    bg = (0.2, 0.1, 0.05)
+    rng = np.random.default_rng(11)
+    W = rng.uniform(-1, 1, (cam.h, cam.w, 4))
+    gn, gt = O.render_grad(f, tf, cam, integ, W, bg=bg)
+    assert np.abs(gn).max() > 0 and np.abs(gt).max() > 0
+    if part == "knots":
+        coords, arr, g = range(32), tf.knots.reshape(-1), gt.reshape(-1)
+    else:
+        coords, arr, g = rng.choice(f.nodal.size, 24, replace=False), f.nodal.reshape(-1), gn.reshape(-1)
+    scale = np.abs(g).max()
+    checked = 0
+    for k in coords:
+        v = float(arr[k])
+        h = 1e-3 * max(1.0, abs(v))
+        vp, vm = np.float32(v + h), np.float32(v - h)
+        arr[k] = vp
+        lp, sp = _loss(f, tf, cam, integ, W, bg)
+        arr[k] = vm
+        lm, sm = _loss(f, tf, cam, integ, W, bg)
+        arr[k] = np.float32(v)
+        if sp != sm:
+            continue
+        fd = (lp - lm) / (float(vp) - float(vm))
+        assert abs(g[k] - fd) <= 2e-5 * abs(fd) + 1e-6 * scale, (part, k, g[k], fd)
+        checked += 1
+    assert checked >= (28 if part == "knots" else 20)
