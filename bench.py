@@ -55,6 +55,7 @@ def parse_args():
     p.add_argument("--cpu-row-stride", type=int, default=1,
                    help="CPU baseline renders every n-th image row")
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    p.add_argument("--no-backward", action="store_true", help="skip the adjoint measurement")
     p.add_argument("--image", default="1920x1080",
                    help="image size WxH (smaller sizes only for profiling captures)")
     return p.parse_args()
@@ -257,6 +258,26 @@ def main():
     if world > 1:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
 
+    # differentiation: dL/d(nodal, knots) of an L2 loss against a target rendered
+    # from a seeded 5% perturbation of the nodal data (segments recomputed)
+    bwd_ms = []
+    if not args.no_backward:
+        pert = forest.nodal * (1 + 0.05 * np.random.default_rng(5).uniform(-1, 1, forest.nodal.shape))
+        r.set_data(torch.from_numpy(pert.astype(np.float32)).to(dev), r.tf)
+        target = r.render(out)[0].clone()
+        r.set_data(torch.from_numpy(np.ascontiguousarray(forest.nodal, np.float32)).to(dev), r.tf)
+        img = r.render(out)[0]
+        grad_img = (2.0 * (img - target)).contiguous()
+        for k in range(args.warmup + max(3, args.steps // 4)):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r.backward(grad_img)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            if k >= args.warmup:
+                bwd_ms.append(a.elapsed_time(b))
+
     if rank == 0:
         peaks, src = measured_peaks()
         mm = sum(merge_ms) / len(merge_ms)
@@ -295,6 +316,12 @@ def main():
                          "ms_merge": mm, "ms_prune": sum(prune_ms) / len(prune_ms)},
             "clocks": clk.summary(),
         }
+        if bwd_ms:
+            mb = sum(bwd_ms) / len(bwd_ms)
+            line["backward"] = {"ms_backward": mb, "ms_forward": ms_max,
+                                "fwd_bwd_over_fwd": (ms_max + mb) / ms_max,
+                                "loss": "L2 against a render of a seeded 5% nodal perturbation",
+                                "grads": "nodal values and transfer-function knots"}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(forest, tf, cam, integ, args.cpu_row_stride)
         print(json.dumps(line), flush=True)

@@ -11,7 +11,9 @@
  *             the piece (Sec. 2.3, Eqs. 2.29 and 2.31, Algorithm 1);
  *   merge   - aggregate the segments of each ray up the octree with the
  *             segment group action (Eq. 2.14, Sec. 3.3) into its pixel,
- *             I_v = A I_b + B (Sec. 2.4), without a global depth sort.
+ *             I_v = A I_b + B (Sec. 2.4), without a global depth sort;
+ *   adjoint - the gradient of a loss on the image with respect to the nodal
+ *             data and the transfer function (ocr_render_backward).
  *
  * Conventions
  *  - Every entry point returns OCR_OK (0) or a negative OCR_ERR_* code and
@@ -169,6 +171,21 @@ int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats);
 int ocr_prune_noalloc(const int32_t *d_leaf_geo, int64_t nleaves, int max_level,
                       const ocr_camera *cam, int32_t *d_rects, int32_t *d_visible_idx,
                       int64_t *h_nvisible, void *stream);
+
+/* Gradient of a loss L(rgba) with respect to the nodal values and the
+ * transfer-function knots (Sec. 2.3-2.4, Eqs. 2.14 and 2.29-2.31 in reverse
+ * mode), for the forest, data, integrator and camera last set.
+ * d_dL_drgba [h*w*4] float32 (device): dL/d(I_r, I_g, I_b, alpha) per pixel;
+ * rays whose four entries are zero are skipped.  d_grad_nodal [nleaves*8] and
+ * d_grad_tf [8*4] float32 (device) are overwritten with dL/d(nodal) and
+ * dL/d(knots).  Segments are recomputed, not taken from a previous render;
+ * each ray's segments are put in front-to-back order by their mirrored Morton
+ * key.  RK4 and DOPRI5 only (OCR_ERR_UNSUPPORTED otherwise); a ray with more
+ * than 512 segments is skipped and reported as OCR_ERR_DEVICE.  Blocks the
+ * host three times (sizes of the pair space and of the hit lists, the error
+ * word). */
+int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_nodal,
+                        float *d_grad_tf, void *stream);
 
 /* Device memory held by the library for this forest (topology + scratch). */
 int64_t ocr_device_bytes(const ocr_forest *F);

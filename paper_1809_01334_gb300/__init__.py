@@ -10,13 +10,13 @@ and cameras.
 """
 from __future__ import annotations
 
-__all__ = ["Renderer", "capi", "inputs"]
+__all__ = ["Renderer", "RenderFunction", "capi", "inputs"]
 
 
 def __getattr__(name):
-    if name == "Renderer":
-        from .renderer import Renderer
-        return Renderer
+    if name in ("Renderer", "RenderFunction"):
+        from . import renderer
+        return getattr(renderer, name)
     if name in ("capi", "inputs"):
         import importlib
         return importlib.import_module(f".{name}", __name__)

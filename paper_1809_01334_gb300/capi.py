@@ -18,7 +18,8 @@ GEOM_CUBE = 0
 RK4, DOPRI5, GAUSS2, SIMPSON = 0, 1, 2, 3
 
 EXPORTS = ["ocr_build_forest", "ocr_forest_set_data", "ocr_set_integrator", "ocr_set_camera",
-           "ocr_render", "ocr_device_bytes", "ocr_destroy", "ocr_strerror"]
+           "ocr_render", "ocr_render_backward", "ocr_device_bytes", "ocr_destroy",
+           "ocr_strerror"]
 
 
 class ForestDesc(C.Structure):
@@ -175,3 +176,11 @@ def prune_noalloc(d_leaf_geo, nleaves: int, max_level: int, cam, d_rects, d_visi
     _check(fn(_ptr(d_leaf_geo), int(nleaves), int(max_level), C.byref(c), _ptr(d_rects),
               _ptr(d_visible_idx), C.byref(n), _ptr(stream)), "ocr_prune_noalloc")
     return int(n.value)
+
+
+def render_backward(h, d_dL_drgba, d_grad_nodal, d_grad_tf, stream=None):
+    """ocr_render_backward: dL/d(nodal) and dL/d(knots) given dL/d(rgba)."""
+    fn = lib().ocr_render_backward
+    fn.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    _check(fn(h, _ptr(d_dL_drgba), _ptr(d_grad_nodal), _ptr(d_grad_tf), _ptr(stream)),
+           "ocr_render_backward")

@@ -1,0 +1,647 @@
+// Adjoint of the render (ocr_render_backward), sm_103a.
+//
+// The gradient of a loss L(rgba) with respect to the nodal values and the
+// transfer-function knots, given dL/d(rgba).  Segments are recomputed, not
+// stored by the forward pass:
+//   pair_hits<false> - over the (visible leaf, pixel) pairs of the leaves'
+//                      rectangles in Morton order (a prefix sum of rectangle
+//                      areas splits them into equal CTA chunks): slab tests,
+//                      hits counted per ray;
+//   (scan)           - per-ray offsets of the hit lists;
+//   pair_hits<true>  - the same traversal, writing each hit's leaf and its
+//                      mirrored Morton key (the ray's front-to-back order);
+//   ray_backward     - one warp per ray: sort the hits by key, recompute every
+//                      segment, form the transmittance of the nearer segments
+//                      (prefix product) and the aggregate of the farther ones
+//                      with the background (suffix fold with Eq. 2.14) by warp
+//                      scans -- no group inverse -- and carry each segment's
+//                      adjoint back through the integrator (RK4, or the
+//                      Dormand-Prince steps of Algorithm 1 with the same step
+//                      tree), the transfer function and the trilinear weights.
+#include "ocr_common.h"
+#include "ocr_device.cuh"
+
+namespace ocr {
+namespace {
+
+constexpr int kPairThreads = 256;
+
+__device__ __forceinline__ long long area_of(int4 r) {
+  return r.x > r.y ? 0ll : (long long)(r.y - r.x + 1) * (long long)(r.w - r.z + 1);
+}
+
+// ------------------------------------------------------------------ scans --
+constexpr int kBScanThreads = 256, kBScanItems = 4, kBScanTile = kBScanThreads * kBScanItems;
+
+struct LeafArea {
+  const int4 *rect;
+  __device__ long long operator()(long long k) const { return area_of(rect[k]); }
+};
+struct RayCount {
+  const int *cnt;
+  __device__ long long operator()(long long k) const { return (long long)cnt[k]; }
+};
+
+__device__ long long block_excl_scan(long long v, long long *wt, long long &total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wt[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    long long w = lane < (int)(blockDim.x >> 5) ? wt[lane] : 0ll;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    wt[lane] = w;
+  }
+  __syncthreads();
+  total = wt[(blockDim.x >> 5) - 1];
+  const long long r = (wid ? wt[wid - 1] : 0ll) + x - v;
+  __syncthreads();
+  return r;
+}
+
+template <class G>
+__global__ void __launch_bounds__(kBScanThreads) bscan_reduce_kernel(G get, long long n,
+                                                                      long long *bs) {
+  __shared__ long long wt[32];
+  const long long base = (long long)blockIdx.x * kBScanTile + threadIdx.x * kBScanItems;
+  long long s = 0;
+#pragma unroll
+  for (int q = 0; q < kBScanItems; ++q)
+    if (base + q < n) s += get(base + q);
+  long long tot;
+  block_excl_scan(s, wt, tot);
+  if (threadIdx.x == 0) bs[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) bscan_sums_kernel(long long *bs, int nblk) {
+  __shared__ long long wt[32];
+  long long carry = 0;
+  for (int b = 0; b < nblk; b += blockDim.x) {
+    const int k = b + threadIdx.x;
+    const long long v = k < nblk ? bs[k] : 0ll;
+    long long tot;
+    const long long ex = block_excl_scan(v, wt, tot);
+    if (k < nblk) bs[k] = carry + ex;
+    carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bs[nblk] = carry;
+}
+
+template <class G>
+__global__ void __launch_bounds__(kBScanThreads) bscan_down_kernel(G get, long long n,
+                                                                    const long long *bs, int nblk,
+                                                                    long long *out) {
+  __shared__ long long wt[32];
+  const long long base = (long long)blockIdx.x * kBScanTile + threadIdx.x * kBScanItems;
+  long long a[kBScanItems], s = 0;
+#pragma unroll
+  for (int q = 0; q < kBScanItems; ++q) {
+    a[q] = base + q < n ? get(base + q) : 0ll;
+    s += a[q];
+  }
+  long long tot;
+  long long run = bs[blockIdx.x] + block_excl_scan(s, wt, tot);
+#pragma unroll
+  for (int q = 0; q < kBScanItems; ++q) {
+    if (base + q < n) out[base + q] = run;
+    run += a[q];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = bs[nblk];
+}
+
+template <class G>
+cudaError_t exclusive_scan(G get, long long n, long long *bs, long long bs_cap, long long *out,
+                           cudaStream_t st) {
+  const long long nblk = (n + kBScanTile - 1) / kBScanTile;
+  if (nblk + 1 > bs_cap || nblk > 0x7fffffffll) return cudaErrorInvalidValue;
+  if (nblk == 0) return cudaMemsetAsync(out, 0, sizeof(long long), st);
+  bscan_reduce_kernel<<<(unsigned)nblk, kBScanThreads, 0, st>>>(get, n, bs);
+  bscan_sums_kernel<<<1, 1024, 0, st>>>(bs, (int)nblk);
+  bscan_down_kernel<<<(unsigned)nblk, kBScanThreads, 0, st>>>(get, n, bs, (int)nblk, out);
+  return cudaGetLastError();
+}
+
+// chunk_leaf[c] = the leaf whose pairs hold pair c * kPairThreads
+__global__ void pair_chunk_map_kernel(const long long *off, int N, int *chunk_leaf) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    const long long a = off[k], b = off[k + 1];
+    if (b <= a) continue;
+    for (long long c = (a + kPairThreads - 1) / kPairThreads; c * kPairThreads < b; ++c)
+      chunk_leaf[c] = k;
+  }
+}
+
+// ----------------------------------------------------------- hit lists --
+template <bool FILL>
+__global__ void __launch_bounds__(kPairThreads)
+    pair_hits_kernel(Topo T, Cam c, const int4 *rect, const long long *leaf_off,
+                     const int *chunk_leaf, long long npairs, const float4 *dL, int *counts,
+                     const long long *ray_off, int *cursor, const unsigned long long *mkey,
+                     unsigned long long fx, unsigned long long *keys, int *hleaf) {
+  const long long p = (long long)blockIdx.x * kPairThreads + threadIdx.x;
+  if (p >= npairs) return;
+  const long long nch = (npairs + kPairThreads - 1) / kPairThreads;
+  int lo = chunk_leaf[blockIdx.x];
+  int hi = (blockIdx.x + 1 < nch) ? chunk_leaf[blockIdx.x + 1] + 1 : T.N;
+  while (lo + 1 < hi) {  // last leaf whose offset is <= p
+    const int mid = (lo + hi) >> 1;
+    if (leaf_off[mid] <= p) lo = mid; else hi = mid;
+  }
+  const int leaf = lo;
+  const int4 r = rect[leaf];
+  const long long local = p - leaf_off[leaf];
+  const int rw = r.y - r.x + 1;
+  const int i = r.x + (int)(local % rw), j = r.z + (int)(local / rw);
+  const long long pix = (long long)j * c.w + i;
+  const float4 g = dL[pix];
+  if (g.x == 0.f && g.y == 0.f && g.z == 0.f && g.w == 0.f) return;  // no gradient on this ray
+  float3 org, dir;
+  pixel_ray(c, i, j, org, dir);
+  const float3 inv = make_float3(recip_or_zero(dir.x), recip_or_zero(dir.y), recip_or_zero(dir.z));
+  const int4 gl = T.geo[leaf];
+  float a0, a1;
+  if (!slab(org, dir, inv, node_lo(gl, ldexpf(1.f, -T.L)), ldexpf(1.f, -gl.w), c.amin, c.amax, a0,
+            a1))
+    return;
+  if (!FILL) {
+    atomicAdd(counts + pix, 1);
+  } else {
+    const long long at = ray_off[pix] + atomicAdd(cursor + pix, 1);
+    const unsigned long long flip =
+        (dir.x < 0.f ? fx : 0ull) | (dir.y < 0.f ? fx << 1 : 0ull) | (dir.z < 0.f ? fx << 2 : 0ull);
+    keys[at] = mkey[leaf] ^ flip;
+    hleaf[at] = leaf;
+  }
+}
+
+// -------------------------------------------------------- segment adjoint --
+// Accumulates the adjoint of the transfer-function knots of consecutive
+// evaluations that fall in the same knot interval before touching shared memory.
+struct TfGrad {
+  int k = -1;
+  float4 a0, a1;  // knot k, knot k + 1
+  float *s_g;     // [32] in shared memory
+  __device__ void flush() {
+    if (k < 0) return;
+    atomicAdd(s_g + 4 * k + 0, a0.x); atomicAdd(s_g + 4 * k + 1, a0.y);
+    atomicAdd(s_g + 4 * k + 2, a0.z); atomicAdd(s_g + 4 * k + 3, a0.w);
+    atomicAdd(s_g + 4 * k + 4, a1.x); atomicAdd(s_g + 4 * k + 5, a1.y);
+    atomicAdd(s_g + 4 * k + 6, a1.z); atomicAdd(s_g + 4 * k + 7, a1.w);
+    k = -1;
+  }
+  __device__ void add(int kk, float w, float4 v) {
+    if (kk != k) {
+      flush();
+      k = kk;
+      a0 = a1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float w0 = 1.f - w;
+    a0.x = fmaf(w0, v.x, a0.x); a0.y = fmaf(w0, v.y, a0.y);
+    a0.z = fmaf(w0, v.z, a0.z); a0.w = fmaf(w0, v.w, a0.w);
+    a1.x = fmaf(w, v.x, a1.x); a1.y = fmaf(w, v.y, a1.y);
+    a1.z = fmaf(w, v.z, a1.z); a1.w = fmaf(w, v.w, a1.w);
+  }
+};
+
+struct SegAdj {
+  Cubic cu;
+  float3 uf, du;    // reference coordinates at the far end, change to the near end
+  float g8[8];      // adjoint of the 8 nodal values
+};
+
+// adjoint of the medium at tau: vbar = dL/d(kappa, q) there
+__device__ __forceinline__ void medium_bwd(SegAdj &S, const TF &tf, float tau, float4 vbar,
+                                           TfGrad &tg) {
+  const float s = fmaf(fmaf(fmaf(S.cu.p3, tau, S.cu.p2), tau, S.cu.p1), tau, S.cu.p0);
+  const float zr = (s - tf.s_min) * tf.inv;
+  const bool inside = zr > 0.f && zr < 7.f;
+  const float z = fminf(fmaxf(zr, 0.f), 7.f);
+  const int k = min((int)z, 6);
+  const float w = z - (float)k;
+  tg.add(k, w, vbar);
+  if (!inside) return;
+  const float4 d = tf.s[k];
+  const float sb = (vbar.x * d.x + vbar.y * d.y + vbar.z * d.z + vbar.w * d.w) * tf.inv;
+  const float u = fmaf(tau, S.du.x, S.uf.x), v = fmaf(tau, S.du.y, S.uf.y),
+              ww = fmaf(tau, S.du.z, S.uf.z);
+  const float u0 = 1.f - u, v0 = 1.f - v, w0 = 1.f - ww;
+  S.g8[0] = fmaf(sb, u0 * v0 * w0, S.g8[0]);
+  S.g8[1] = fmaf(sb, u * v0 * w0, S.g8[1]);
+  S.g8[2] = fmaf(sb, u0 * v * w0, S.g8[2]);
+  S.g8[3] = fmaf(sb, u * v * w0, S.g8[3]);
+  S.g8[4] = fmaf(sb, u0 * v0 * ww, S.g8[4]);
+  S.g8[5] = fmaf(sb, u * v0 * ww, S.g8[5]);
+  S.g8[6] = fmaf(sb, u0 * v * ww, S.g8[6]);
+  S.g8[7] = fmaf(sb, u * v * ww, S.g8[7]);
+}
+
+__device__ __forceinline__ float dot4(float4 a, float4 b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+}
+
+// dL/d(kappa, q) at a node from the stage derivative adjoint Kb and stage value Y
+__device__ __forceinline__ float4 node_vbar(float4 Kb, float4 Y) {
+  return make_float4(-dot4(Kb, Y), Kb.y, Kb.z, Kb.w);
+}
+
+__device__ __forceinline__ float4 scale4(float a, float4 x) {
+  return make_float4(a * x.x, a * x.y, a * x.z, a * x.w);
+}
+
+// adjoint of one RK4 step from (1, 0) with nodes at t0, t0 + dt/2, t0 + dt
+__device__ void rk4_step_bwd(SegAdj &S, const TF &tf, float t0, float dt, float H, float4 ybar,
+                             TfGrad &tg) {
+  const float4 one = seg_identity();
+  const float4 k0 = medium(S.cu, tf, t0), kh = medium(S.cu, tf, t0 + 0.5f * dt),
+               k1 = medium(S.cu, tf, t0 + dt);
+  const float4 Y1 = one, K1 = rhs(k0, Y1);
+  const float4 Y2 = axpy(0.5f * H, K1, one), K2 = rhs(kh, Y2);
+  const float4 Y3 = axpy(0.5f * H, K2, one), K3 = rhs(kh, Y3);
+  const float4 Y4 = axpy(H, K3, one);
+  float4 K4b = scale4(H / 6.f, ybar), K3b = scale4(H / 3.f, ybar), K2b = scale4(H / 3.f, ybar),
+         K1b = scale4(H / 6.f, ybar);
+  medium_bwd(S, tf, t0 + dt, node_vbar(K4b, Y4), tg);
+  K3b = axpy(H, scale4(-k1.x, K4b), K3b);
+  float4 vh = node_vbar(K3b, Y3);
+  K2b = axpy(0.5f * H, scale4(-kh.x, K3b), K2b);
+  const float4 v2 = node_vbar(K2b, Y2);
+  vh = make_float4(vh.x + v2.x, vh.y + v2.y, vh.z + v2.z, vh.w + v2.w);
+  medium_bwd(S, tf, t0 + 0.5f * dt, vh, tg);
+  K1b = axpy(0.5f * H, scale4(-kh.x, K2b), K1b);
+  medium_bwd(S, tf, t0, node_vbar(K1b, Y1), tg);
+}
+
+// adjoint of one Dormand-Prince step from (1, 0) (stages 1..6; the seventh
+// stage only feeds the error estimate)
+__device__ void dopri_step_bwd(SegAdj &S, const TF &tf, float t0, float dtau, float H,
+                               float4 ybar, TfGrad &tg) {
+  const float4 one = seg_identity();
+  const float tt[6] = {t0, fmaf(dp::c2, dtau, t0), fmaf(dp::c3, dtau, t0),
+                       fmaf(dp::c4, dtau, t0), fmaf(dp::c5, dtau, t0), t0 + dtau};
+  float4 kq[6], Y[6], K[6];
+  for (int i = 0; i < 6; ++i) kq[i] = medium(S.cu, tf, tt[i]);
+  Y[0] = one;
+  K[0] = rhs(kq[0], Y[0]);
+  Y[1] = axpy(H * dp::a21, K[0], one);
+  K[1] = rhs(kq[1], Y[1]);
+  Y[2] = axpy(H, lin4(dp::a31, K[0], dp::a32, K[1]), one);
+  K[2] = rhs(kq[2], Y[2]);
+  float4 t = lin4(dp::a41, K[0], dp::a42, K[1]);
+  t = axpy(dp::a43, K[2], t);
+  Y[3] = axpy(H, t, one);
+  K[3] = rhs(kq[3], Y[3]);
+  t = lin4(dp::a51, K[0], dp::a52, K[1]);
+  t = axpy(dp::a53, K[2], t);
+  t = axpy(dp::a54, K[3], t);
+  Y[4] = axpy(H, t, one);
+  K[4] = rhs(kq[4], Y[4]);
+  t = lin4(dp::a61, K[0], dp::a62, K[1]);
+  t = axpy(dp::a63, K[2], t);
+  t = axpy(dp::a64, K[3], t);
+  t = axpy(dp::a65, K[4], t);
+  Y[5] = axpy(H, t, one);
+  const float b[6] = {dp::b1, 0.f, dp::b3, dp::b4, dp::b5, dp::b6};
+  const float a[6][5] = {{0, 0, 0, 0, 0},
+                         {dp::a21, 0, 0, 0, 0},
+                         {dp::a31, dp::a32, 0, 0, 0},
+                         {dp::a41, dp::a42, dp::a43, 0, 0},
+                         {dp::a51, dp::a52, dp::a53, dp::a54, 0},
+                         {dp::a61, dp::a62, dp::a63, dp::a64, dp::a65}};
+  float4 Kb[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) Kb[i] = scale4(H * b[i], ybar);
+#pragma unroll
+  for (int i = 5; i >= 0; --i) {
+    medium_bwd(S, tf, tt[i], node_vbar(Kb[i], Y[i]), tg);
+    const float4 Yb = scale4(-kq[i].x, Kb[i]);
+#pragma unroll
+    for (int j = 0; j < i; ++j) Kb[j] = axpy(H * a[i][j], Yb, Kb[j]);
+  }
+}
+
+// adjoint of one step with value Sm, near transmittance Tm and far aggregate
+// Gm (background folded in through bg): dL/d(A, B) of the step
+__device__ __forceinline__ float4 step_adjoint(float Tm, float4 Gm, float4 Ib, float ab,
+                                               const float *bg) {
+  const float F0 = fmaf(Gm.x, bg[0], Gm.y), F1 = fmaf(Gm.x, bg[1], Gm.z),
+              F2 = fmaf(Gm.x, bg[2], Gm.w);
+  return make_float4(Tm * (Ib.x * F0 + Ib.y * F1 + Ib.z * F2 - ab * Gm.x), Tm * Ib.x, Tm * Ib.y,
+                     Tm * Ib.z);
+}
+
+// Adjoint of one segment: near transmittance T, far aggregate G, its value
+// A_seg; the steps are revisited far to near with the forward's step tree.
+__device__ void segment_bwd(const Topo &T, const Field &Fd, const Cam &c, const Integ &I,
+                            const TF &tf, int leaf, float3 org, float3 dir, float3 inv,
+                            float scale, float Tn, float4 G, float Aseg, float4 Ib, float ab,
+                            float *g_nodal, TfGrad &tg) {
+  const int4 g = __ldg(T.geo + leaf);
+  const float ih = ldexpf(1.f, g.w);
+  const float3 lo = node_lo(g, scale);
+  float a_in, a_out;
+  slab(org, dir, inv, lo, ldexpf(1.f, -g.w), c.amin, c.amax, a_in, a_out);
+  SegAdj S;
+  S.uf = make_float3((fmaf(a_out, dir.x, org.x) - lo.x) * ih,
+                     (fmaf(a_out, dir.y, org.y) - lo.y) * ih,
+                     (fmaf(a_out, dir.z, org.z) - lo.z) * ih);
+  const float da = a_in - a_out;
+  S.du = make_float3(da * dir.x * ih, da * dir.y * ih, da * dir.z * ih);
+  const float dx =
+      fmaxf(a_out - a_in, 0.f) * sqrtf(dir.x * dir.x + dir.y * dir.y + dir.z * dir.z);
+  S.cu = field_cubic(Fd.nodal + 8 * (size_t)leaf, S.uf, S.du);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) S.g8[q] = 0.f;
+  float4 acc = seg_identity();  // steps farther than the current one
+  if (I.method == 0) {
+    const int n = I.nsteps;
+    const float H = dx / (float)n, dt = 1.f / (float)n;
+    for (int s = 0; s < n; ++s) {
+      const float t0 = (float)s * dt, dts = (s + 1 == n) ? 1.f - t0 : dt;
+      const float4 Sm = rk4_step(H, medium(S.cu, tf, t0), medium(S.cu, tf, t0 + 0.5f * dts),
+                                 medium(S.cu, tf, t0 + dts));
+      const float4 accn = seg_combine(Sm, acc);
+      const float Tm = Tn * (Aseg / accn.x);
+      const float4 Gm = seg_combine(acc, G);
+      rk4_step_bwd(S, tf, t0, dts, H, step_adjoint(Tm, Gm, Ib, ab, I.bg), tg);
+      acc = accn;
+    }
+  } else {
+    int depth = 0;
+    unsigned idx = 0;
+    float4 kq0 = medium(S.cu, tf, 0.f);
+    const float4 one = seg_identity();
+    for (;;) {
+      const float dtau = ldexpf(1.f, -depth);
+      const float t0 = (float)idx * dtau;
+      const float H = dx * dtau;
+      // the forward step (value, split test) exactly as integrate_segment
+      const float4 kq2 = medium(S.cu, tf, fmaf(dp::c2, dtau, t0));
+      const float4 kq3 = medium(S.cu, tf, fmaf(dp::c3, dtau, t0));
+      const float4 kq4 = medium(S.cu, tf, fmaf(dp::c4, dtau, t0));
+      const float4 kq5 = medium(S.cu, tf, fmaf(dp::c5, dtau, t0));
+      const float4 kq6 = medium(S.cu, tf, t0 + dtau);
+      const float4 K1 = rhs(kq0, one);
+      const float4 K2 = rhs(kq2, axpy(H * dp::a21, K1, one));
+      const float4 K3 = rhs(kq3, axpy(H, lin4(dp::a31, K1, dp::a32, K2), one));
+      float4 t = lin4(dp::a41, K1, dp::a42, K2);
+      t = axpy(dp::a43, K3, t);
+      const float4 K4 = rhs(kq4, axpy(H, t, one));
+      t = lin4(dp::a51, K1, dp::a52, K2);
+      t = axpy(dp::a53, K3, t);
+      t = axpy(dp::a54, K4, t);
+      const float4 K5 = rhs(kq5, axpy(H, t, one));
+      t = lin4(dp::a61, K1, dp::a62, K2);
+      t = axpy(dp::a63, K3, t);
+      t = axpy(dp::a64, K4, t);
+      t = axpy(dp::a65, K5, t);
+      const float4 K6 = rhs(kq6, axpy(H, t, one));
+      t = lin4(dp::b1, K1, dp::b3, K3);
+      t = axpy(dp::b4, K4, t);
+      t = axpy(dp::b5, K5, t);
+      t = axpy(dp::b6, K6, t);
+      const float4 Y5 = axpy(H, t, one);
+      const float4 K7 = rhs(kq6, Y5);
+      float4 e = lin4(dp::e1, K1, dp::e3, K3);
+      e = axpy(dp::e4, K4, e);
+      e = axpy(dp::e5, K5, e);
+      e = axpy(dp::e6, K6, e);
+      e = axpy(dp::e7, K7, e);
+      const float err = H * fmaxf(fmaxf(fabsf(e.x), fabsf(e.y)), fmaxf(fabsf(e.z), fabsf(e.w)));
+      const float kmax =
+          fmaxf(fmaxf(fmaxf(kq0.x, kq2.x), fmaxf(kq3.x, kq4.x)), fmaxf(kq5.x, kq6.x));
+      if (depth < I.max_depth && (H * kmax > I.c_rk || err > I.tol)) {
+        ++depth;
+        idx <<= 1;
+        continue;
+      }
+      const float4 accn = seg_combine(Y5, acc);
+      const float Tm = Tn * (Aseg / accn.x);
+      const float4 Gm = seg_combine(acc, G);
+      dopri_step_bwd(S, tf, t0, dtau, H, step_adjoint(Tm, Gm, Ib, ab, I.bg), tg);
+      acc = accn;
+      kq0 = kq6;
+      ++idx;
+      while (depth > 0 && !(idx & 1u)) {
+        idx >>= 1;
+        --depth;
+      }
+      if (depth == 0) break;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    if (S.g8[q] != 0.f) atomicAdd(g_nodal + 8 * (size_t)leaf + q, S.g8[q]);
+}
+
+// ------------------------------------------------------------ ray adjoint --
+constexpr int kBwdWarps = 4;
+
+__global__ void __launch_bounds__(kBwdWarps * 32)
+    ray_backward_kernel(Topo T, Field Fd, Cam c, Integ I, const float4 *dL,
+                        const long long *ray_off, const unsigned long long *keys,
+                        const int *hleaf, float *g_nodal, float *g_tf, unsigned long long *err) {
+  extern __shared__ unsigned char s_raw[];
+  // per warp: keys (later T and A_seg), leaves, segment values (later far aggregates)
+  unsigned long long *s_key = reinterpret_cast<unsigned long long *>(s_raw);
+  int *s_leaf = reinterpret_cast<int *>(s_key + kBwdWarps * kMaxRayHits);
+  float4 *s_val = reinterpret_cast<float4 *>(s_leaf + kBwdWarps * kMaxRayHits);
+  __shared__ float4 s_tfv[8], s_tfs[8];
+  __shared__ float s_g[32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid < 8) {
+    const float4 v = Fd.tf[tid];
+    const float4 w = Fd.tf[tid < 7 ? tid + 1 : 7];
+    s_tfv[tid] = v;
+    s_tfs[tid] = make_float4(w.x - v.x, w.y - v.y, w.z - v.z, w.w - v.w);
+  }
+  if (tid < 32) s_g[tid] = 0.f;
+  __syncthreads();
+  unsigned long long *key = s_key + wid * kMaxRayHits;
+  int *lf = s_leaf + wid * kMaxRayHits;
+  float4 *val = s_val + wid * kMaxRayHits;
+  float *Tk = reinterpret_cast<float *>(key);           // reuses the key array after sorting
+  float *Ak = reinterpret_cast<float *>(key) + kMaxRayHits;
+  TF tf{s_tfv, s_tfs, Fd.s_min, Fd.inv_ds7};
+  TfGrad tg;
+  tg.s_g = s_g;
+  const float scale = ldexpf(1.f, -T.L);
+  const long long npix = (long long)c.w * c.h;
+  const long long nwarp = (long long)gridDim.x * kBwdWarps;
+  for (long long pix = (long long)blockIdx.x * kBwdWarps + wid; pix < npix; pix += nwarp) {
+    const long long h0 = ray_off[pix];
+    const int n = (int)(ray_off[pix + 1] - h0);
+    if (n == 0) continue;
+    if (n > kMaxRayHits) {
+      if (lane == 0) atomicAdd(err, 1ull);
+      continue;
+    }
+    int P = 32;
+    while (P < n) P <<= 1;
+    for (int k = lane; k < P; k += 32) {
+      key[k] = k < n ? keys[h0 + k] : ~0ull;
+      lf[k] = k < n ? hleaf[h0 + k] : -1;
+    }
+    __syncwarp();
+    // bitonic sort of (key, leaf) by key: nearest first
+    for (int sz = 2; sz <= P; sz <<= 1)
+      for (int st = sz >> 1; st > 0; st >>= 1) {
+        for (int k = lane; k < P; k += 32) {
+          const int m = k ^ st;
+          if (m > k) {
+            const bool up = (k & sz) == 0;
+            const unsigned long long a = key[k], b = key[m];
+            if ((a > b) == up) {
+              key[k] = b;
+              key[m] = a;
+              const int t = lf[k];
+              lf[k] = lf[m];
+              lf[m] = t;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    const int i = (int)(pix % c.w), j = (int)(pix / c.w);
+    float3 org, dir;
+    pixel_ray(c, i, j, org, dir);
+    const float3 inv =
+        make_float3(recip_or_zero(dir.x), recip_or_zero(dir.y), recip_or_zero(dir.z));
+    // segment values
+    int steps = 0;
+    for (int k = lane; k < n; k += 32)
+      val[k] = leaf_segment(T, Fd, c, I, tf, lf[k], org, dir, inv, scale, steps);
+    __syncwarp();
+    // near transmittance: exclusive product of A, nearest first
+    float carry = 1.f;
+    const int nb = (n + 31) / 32;
+    for (int b = 0; b < nb; ++b) {
+      const int k = b * 32 + lane;
+      const float a = k < n ? val[k].x : 1.f;
+      float x = a;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x *= y;
+      }
+      float ex = __shfl_up_sync(0xffffffffu, x, 1);
+      if (lane == 0) ex = 1.f;
+      if (k < n) {
+        Tk[k] = carry * ex;
+        Ak[k] = a;
+      }
+      carry *= __shfl_sync(0xffffffffu, x, 31);
+    }
+    __syncwarp();
+    // far aggregate of the segments behind each one: suffix fold, farthest first
+    float4 fc = seg_identity();
+    for (int b = nb - 1; b >= 0; --b) {
+      const int k = b * 32 + lane;
+      float4 x = k < n ? val[k] : seg_identity();
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        float4 y;
+        y.x = __shfl_down_sync(0xffffffffu, x.x, o);
+        y.y = __shfl_down_sync(0xffffffffu, x.y, o);
+        y.z = __shfl_down_sync(0xffffffffu, x.z, o);
+        y.w = __shfl_down_sync(0xffffffffu, x.w, o);
+        if (lane + o < 32) x = seg_combine(x, y);
+      }
+      float4 nx;
+      nx.x = __shfl_down_sync(0xffffffffu, x.x, 1);
+      nx.y = __shfl_down_sync(0xffffffffu, x.y, 1);
+      nx.z = __shfl_down_sync(0xffffffffu, x.z, 1);
+      nx.w = __shfl_down_sync(0xffffffffu, x.w, 1);
+      if (lane == 31) nx = seg_identity();
+      const float4 Gk = seg_combine(nx, fc);
+      float4 x0;
+      x0.x = __shfl_sync(0xffffffffu, x.x, 0);
+      x0.y = __shfl_sync(0xffffffffu, x.y, 0);
+      x0.z = __shfl_sync(0xffffffffu, x.z, 0);
+      x0.w = __shfl_sync(0xffffffffu, x.w, 0);
+      __syncwarp();
+      if (k < n) val[k] = Gk;
+      fc = seg_combine(x0, fc);
+    }
+    __syncwarp();
+    // adjoint of every segment
+    const float4 gp = dL[pix];
+    const float4 Ib = make_float4(gp.x, gp.y, gp.z, 0.f);
+    for (int k = lane; k < n; k += 32)
+      segment_bwd(T, Fd, c, I, tf, lf[k], org, dir, inv, scale, Tk[k], val[k], Ak[k], Ib, gp.w,
+                  g_nodal, tg);
+    __syncwarp();
+  }
+  tg.flush();
+  __syncthreads();
+  if (tid < 32 && s_g[tid] != 0.f) atomicAdd(g_tf + tid, s_g[tid]);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- launchers --
+cudaError_t bwd_leaf_scan(const Topo &T, const int4 *rect, long long *bs, long long bs_cap,
+                          long long *leaf_off, cudaStream_t st) {
+  return exclusive_scan(LeafArea{rect}, (long long)T.N, bs, bs_cap, leaf_off, st);
+}
+
+cudaError_t bwd_count_scan(const int *counts, long long n, long long *bs, long long bs_cap,
+                           long long *ray_off, cudaStream_t st) {
+  return exclusive_scan(RayCount{counts}, n, bs, bs_cap, ray_off, st);
+}
+
+long long bwd_scan_blocks(long long n) { return (n + kBScanTile - 1) / kBScanTile; }
+
+cudaError_t bwd_chunk_map(const long long *leaf_off, int N, int *chunk_leaf, cudaStream_t st) {
+  const int grid = (int)((N + 255) / 256 > 4096 ? 4096 : (N + 255) / 256);
+  pair_chunk_map_kernel<<<grid > 0 ? grid : 1, 256, 0, st>>>(leaf_off, N, chunk_leaf);
+  return cudaGetLastError();
+}
+
+cudaError_t bwd_pair_hits(bool fill, const Topo &T, const Cam &C, const int4 *rect,
+                          const long long *leaf_off, const int *chunk_leaf, long long npairs,
+                          const float4 *dL, int *counts, const long long *ray_off, int *cursor,
+                          const unsigned long long *mkey, unsigned long long fx,
+                          unsigned long long *keys, int *hleaf, cudaStream_t st) {
+  if (npairs <= 0) return cudaSuccess;
+  const long long nblk = (npairs + kPairThreads - 1) / kPairThreads;
+  if (nblk > 0x7fffffffll) return cudaErrorInvalidValue;
+  if (fill)
+    pair_hits_kernel<true><<<(unsigned)nblk, kPairThreads, 0, st>>>(
+        T, C, rect, leaf_off, chunk_leaf, npairs, dL, counts, ray_off, cursor, mkey, fx, keys,
+        hleaf);
+  else
+    pair_hits_kernel<false><<<(unsigned)nblk, kPairThreads, 0, st>>>(
+        T, C, rect, leaf_off, chunk_leaf, npairs, dL, counts, ray_off, cursor, mkey, fx, keys,
+        hleaf);
+  return cudaGetLastError();
+}
+
+cudaError_t bwd_rays(const Topo &T, const Field &Fd, const Cam &C, const Integ &I,
+                     const float4 *dL, const long long *ray_off, const unsigned long long *keys,
+                     const int *hleaf, float *g_nodal, float *g_tf, unsigned long long *err,
+                     int nsm, cudaStream_t st) {
+  const size_t smem = (size_t)kBwdWarps * kMaxRayHits * (sizeof(unsigned long long) + sizeof(int) +
+                                                          sizeof(float4));
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(ray_backward_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  ray_backward_kernel<<<nsm * 4, kBwdWarps * 32, smem, st>>>(T, Fd, C, I, dL, ray_off, keys, hleaf,
+                                                            g_nodal, g_tf, err);
+  return cudaGetLastError();
+}
+
+}  // namespace ocr

@@ -50,6 +50,22 @@ struct ocr_forest {
   long long entries_cap = 0;
   int *d_chunk_node = nullptr;        // [chunk_cap]
   long long chunk_cap = 0;
+  // adjoint
+  unsigned long long *d_mkey = nullptr;  // [N] Morton key of each leaf
+  unsigned long long fx = 0;             // Morton bit positions of x
+  long long *d_leaf_off = nullptr;       // [N + 1]
+  long long *d_bsums = nullptr;          // scan block sums
+  long long bsums_cap = 0;
+  int *d_pchunk = nullptr;               // pair chunk -> leaf
+  long long pchunk_cap = 0;
+  int *d_rcount = nullptr, *d_rcursor = nullptr;  // [npix]
+  long long *d_ray_off = nullptr;        // [npix + 1]
+  long long ray_cap = 0;
+  unsigned long long *d_hkey = nullptr;  // [hits]
+  int *d_hleaf = nullptr;
+  long long hit_cap = 0;
+  unsigned long long *d_err = nullptr;
+  int nsm = 0;
   int64_t bytes = 0;
 };
 
@@ -111,6 +127,16 @@ void free_all(ocr_forest *F) {
   cudaFree(F->d_stats);
   cudaFree(F->d_entries);
   cudaFree(F->d_chunk_node);
+  cudaFree(F->d_mkey);
+  cudaFree(F->d_leaf_off);
+  cudaFree(F->d_bsums);
+  cudaFree(F->d_pchunk);
+  cudaFree(F->d_rcount);
+  cudaFree(F->d_rcursor);
+  cudaFree(F->d_ray_off);
+  cudaFree(F->d_hkey);
+  cudaFree(F->d_hleaf);
+  cudaFree(F->d_err);
   if (F->h_group_slots) cudaFreeHost(F->h_group_slots);
   for (cudaEvent_t &e : F->ev)
     if (e) cudaEventDestroy(e);
@@ -268,7 +294,10 @@ int ocr_build_forest(const ocr_forest_desc *desc, void *stream, ocr_forest **out
       (rc = dev_alloc(&F->d_rect, (size_t)N + M + 1, F->bytes)) ||
       (rc = dev_alloc(&F->d_off, (size_t)M + 1, F->bytes)) ||
       (rc = dev_alloc(&F->d_group_slots, F->h_group_nodes.size(), F->bytes)) ||
-      (rc = dev_alloc(&F->d_stats, kStats, F->bytes))) {
+      (rc = dev_alloc(&F->d_stats, kStats, F->bytes)) ||
+      (rc = dev_alloc(&F->d_mkey, (size_t)N, F->bytes)) ||
+      (rc = dev_alloc(&F->d_leaf_off, (size_t)N + 1, F->bytes)) ||
+      (rc = dev_alloc(&F->d_err, 1, F->bytes))) {
     free_all(F);
     delete F;
     return rc;
@@ -295,6 +324,10 @@ int ocr_build_forest(const ocr_forest_desc *desc, void *stream, ocr_forest **out
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(F->d_leaves, lrange.data(), lrange.size() * sizeof(int2),
                         cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(F->d_mkey, key.data(), key.size() * sizeof(uint64_t),
+                        cudaMemcpyHostToDevice, st);
+  for (int l = 0; l < L; ++l) F->fx |= 1ull << (3 * l);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(F->d_group_nodes, F->h_group_nodes.data(),
                         F->h_group_nodes.size() * sizeof(int), cudaMemcpyHostToDevice, st);
@@ -495,6 +528,107 @@ int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats) {
       if (h[kStatErrors]) return OCR_ERR_DEVICE;
     }
   }
+  return OCR_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// (re)allocate a scratch buffer to hold at least n elements
+template <typename T>
+int grow(ocr_forest *F, T **p, long long &cap, long long n) {
+  if (n <= cap) return OCR_OK;
+  cudaFree(*p);
+  *p = nullptr;
+  F->bytes -= cap * (int64_t)sizeof(T);
+  cap = 0;
+  const long long want = n + n / 8 + 64;
+  int rc = dev_alloc(p, (size_t)want, F->bytes);
+  if (rc) return rc;
+  cap = want;
+  return OCR_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_nodal,
+                        float *d_grad_tf, void *stream) {
+  if (!F || !d_dL_drgba || !d_grad_nodal || !d_grad_tf) return OCR_ERR_INVALID;
+  if (!F->has_data || !F->has_cam || !F->has_integ) return OCR_ERR_STATE;
+  if (F->integ.method != OCR_RK4 && F->integ.method != OCR_DOPRI5) return OCR_ERR_UNSUPPORTED;
+  if ((uintptr_t)d_dL_drgba & 15) return OCR_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long npix = (long long)F->cam.w * F->cam.h;
+  Topo T{F->d_geo, F->d_child, F->d_leaves, F->N, F->M, F->L, F->lt};
+  Field Fd{F->d_nodal, reinterpret_cast<const float4 *>(F->d_tf), F->s_min,
+           7.f / (F->s_max - F->s_min)};
+  Scratch S{F->d_rect, F->d_off, F->d_entries, F->d_stats, nullptr, nullptr, nullptr};
+  if (!F->nsm) {
+    int dev = 0;
+    OCR_CUDA(cudaGetDevice(&dev));
+    OCR_CUDA(cudaDeviceGetAttribute(&F->nsm, cudaDevAttrMultiProcessorCount, dev));
+  }
+  int rc;
+  const long long nb = std::max(bwd_scan_blocks(F->N), bwd_scan_blocks(npix)) + 2;
+  if ((rc = grow(F, &F->d_bsums, F->bsums_cap, nb))) return rc;
+  {
+    const long long c0 = F->ray_cap;
+    if ((rc = grow(F, &F->d_rcount, F->ray_cap, npix))) return rc;
+    if (F->ray_cap != c0 || !F->d_rcursor || !F->d_ray_off) {  // same capacity for all three
+      cudaFree(F->d_rcursor);
+      cudaFree(F->d_ray_off);
+      F->d_rcursor = nullptr;
+      F->d_ray_off = nullptr;
+      if ((rc = dev_alloc(&F->d_rcursor, (size_t)F->ray_cap, F->bytes)) ||
+          (rc = dev_alloc(&F->d_ray_off, (size_t)F->ray_cap + 1, F->bytes)))
+        return rc;
+    }
+  }
+  OCR_CUDA(cudaMemsetAsync(d_grad_nodal, 0, sizeof(float) * 8 * (size_t)F->N, st));
+  OCR_CUDA(cudaMemsetAsync(d_grad_tf, 0, sizeof(float) * 32, st));
+  OCR_CUDA(cudaMemsetAsync(F->d_stats, 0, kStats * sizeof(unsigned long long), st));
+
+  // leaf rectangles, then the (leaf, pixel) pair space in Morton order
+  OCR_CUDA(launch_cull_leaves(T, F->cam, S, st));
+  OCR_CUDA(bwd_leaf_scan(T, F->d_rect, F->d_bsums, F->bsums_cap, F->d_leaf_off, st));
+  long long *h = F->h_group_slots + F->h_group_nodes.size();  // pinned scratch
+  OCR_CUDA(cudaMemcpyAsync(h, F->d_leaf_off + F->N, sizeof(long long), cudaMemcpyDeviceToHost, st));
+  OCR_CUDA(cudaStreamSynchronize(st));
+  const long long npairs = h[0];
+  if ((rc = grow(F, &F->d_pchunk, F->pchunk_cap, npairs / 256 + 2))) return rc;
+  OCR_CUDA(bwd_chunk_map(F->d_leaf_off, F->N, F->d_pchunk, st));
+  const float4 *dL = reinterpret_cast<const float4 *>(d_dL_drgba);
+
+  // hits per ray, their offsets, then the hit lists (leaf, mirrored Morton key)
+  OCR_CUDA(cudaMemsetAsync(F->d_rcount, 0, sizeof(int) * (size_t)npix, st));
+  OCR_CUDA(bwd_pair_hits(false, T, F->cam, F->d_rect, F->d_leaf_off, F->d_pchunk, npairs, dL,
+                         F->d_rcount, nullptr, nullptr, F->d_mkey, F->fx, nullptr, nullptr, st));
+  OCR_CUDA(bwd_count_scan(F->d_rcount, npix, F->d_bsums, F->bsums_cap, F->d_ray_off, st));
+  OCR_CUDA(cudaMemcpyAsync(h, F->d_ray_off + npix, sizeof(long long), cudaMemcpyDeviceToHost, st));
+  OCR_CUDA(cudaStreamSynchronize(st));
+  const long long nh = h[0];
+  {
+    long long c0 = F->hit_cap;
+    if ((rc = grow(F, &F->d_hkey, F->hit_cap, nh))) return rc;
+    if (F->hit_cap != c0 || !F->d_hleaf) {
+      cudaFree(F->d_hleaf);
+      F->d_hleaf = nullptr;
+      if ((rc = dev_alloc(&F->d_hleaf, (size_t)F->hit_cap, F->bytes))) return rc;
+    }
+  }
+  OCR_CUDA(cudaMemsetAsync(F->d_rcursor, 0, sizeof(int) * (size_t)npix, st));
+  OCR_CUDA(bwd_pair_hits(true, T, F->cam, F->d_rect, F->d_leaf_off, F->d_pchunk, npairs, dL,
+                         nullptr, F->d_ray_off, F->d_rcursor, F->d_mkey, F->fx, F->d_hkey,
+                         F->d_hleaf, st));
+
+  // one warp per ray: order, recompute, prefix/suffix, adjoint
+  OCR_CUDA(cudaMemsetAsync(F->d_err, 0, sizeof(unsigned long long), st));
+  OCR_CUDA(bwd_rays(T, Fd, F->cam, F->integ, dL, F->d_ray_off, F->d_hkey, F->d_hleaf,
+                    d_grad_nodal, d_grad_tf, F->d_err, F->nsm, st));
+  OCR_CUDA(cudaMemcpyAsync(h, F->d_err, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  OCR_CUDA(cudaStreamSynchronize(st));
+  if (h[0]) return OCR_ERR_DEVICE;
   return OCR_OK;
 }
 

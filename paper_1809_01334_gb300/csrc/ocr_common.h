@@ -70,6 +70,10 @@ constexpr int kStats = 16;
 constexpr int kStatSegments = 0, kStatSteps = 1, kStatTests = 2, kStatSlots = 3;
 constexpr int kStatCoarse = 8, kStatErrors = 4, kStatVisible = 5;
 
+// Adjoint: at most kMaxRayHits segments per ray (larger rays are skipped and
+// counted as device errors).
+constexpr int kMaxRayHits = 512;
+
 // Slots are processed in chunks of kChunk consecutive slots, one chunk per CTA.
 constexpr int kChunk = 128;
 
@@ -89,5 +93,22 @@ cudaError_t launch_subtree(const Topo &T, const Field &Fd, const Cam &C, const I
 cudaError_t launch_coarsen(const Topo &T, const Field &Fd, const Cam &C, const Integ &I, Scratch S,
                            int node_begin, int node_end, long long slot_begin, long long slot_end,
                            float4 *rgba, cudaStream_t stream);
+
+// Adjoint (ocr_backward.cu)
+cudaError_t bwd_leaf_scan(const Topo &T, const int4 *rect, long long *bs, long long bs_cap,
+                          long long *leaf_off, cudaStream_t st);
+cudaError_t bwd_count_scan(const int *counts, long long n, long long *bs, long long bs_cap,
+                           long long *ray_off, cudaStream_t st);
+long long bwd_scan_blocks(long long n);
+cudaError_t bwd_chunk_map(const long long *leaf_off, int N, int *chunk_leaf, cudaStream_t st);
+cudaError_t bwd_pair_hits(bool fill, const Topo &T, const Cam &C, const int4 *rect,
+                          const long long *leaf_off, const int *chunk_leaf, long long npairs,
+                          const float4 *dL, int *counts, const long long *ray_off, int *cursor,
+                          const unsigned long long *mkey, unsigned long long fx,
+                          unsigned long long *keys, int *hleaf, cudaStream_t st);
+cudaError_t bwd_rays(const Topo &T, const Field &Fd, const Cam &C, const Integ &I,
+                     const float4 *dL, const long long *ray_off, const unsigned long long *keys,
+                     const int *hleaf, float *g_nodal, float *g_tf, unsigned long long *err,
+                     int nsm, cudaStream_t st);
 
 }  // namespace ocr

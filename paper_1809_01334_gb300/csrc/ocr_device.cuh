@@ -1,0 +1,352 @@
+// Device helpers shared by the render kernels (ocr_kernels.cu) and the
+// adjoint (ocr_backward.cu): camera rays, slab test, the field along a
+// segment, the transfer function, the integrators and the pixel rectangle.
+#pragma once
+#include "ocr_common.h"
+
+namespace ocr {
+namespace {
+
+constexpr float kOne = 1.0f;
+
+__device__ __forceinline__ float4 seg_identity() { return make_float4(1.f, 0.f, 0.f, 0.f); }
+
+// Eq. 2.14: (A2, B2) (+) (A1, B1) = (A2 A1, B2 + A2 B1), n = nearer, f = farther.
+__device__ __forceinline__ float4 seg_combine(float4 n, float4 f) {
+  return make_float4(n.x * f.x, fmaf(n.x, f.y, n.y), fmaf(n.x, f.z, n.z), fmaf(n.x, f.w, n.w));
+}
+
+__device__ __forceinline__ void pixel_ray(const Cam &c, int i, int j, float3 &org, float3 &dir) {
+  float di = (float)i - c.cw, dj = (float)j - c.ch;
+  float ox = fmaf(dj, c.lu[0], fmaf(di, c.lt[0], 0.f));
+  float oy = fmaf(dj, c.lu[1], fmaf(di, c.lt[1], 0.f));
+  float oz = fmaf(dj, c.lu[2], fmaf(di, c.lt[2], 0.f));
+  if (c.ortho) {
+    org = make_float3(c.o[0] + ox, c.o[1] + oy, c.o[2] + oz);
+    dir = make_float3(c.v[0], c.v[1], c.v[2]);
+  } else {
+    org = make_float3(c.o[0], c.o[1], c.o[2]);
+    dir = make_float3(c.v[0] + ox, c.v[1] + oy, c.v[2] + oz);
+  }
+}
+
+__device__ __forceinline__ float recip_or_zero(float d) { return d != 0.f ? 1.f / d : 0.f; }
+
+// Slab test of the ray against the axis-aligned box [lo, lo + h]^3, clipped to
+// [amin, amax].  A zero direction component keeps the ray inside the slab or
+// misses it entirely.
+__device__ __forceinline__ bool slab(float3 org, float3 dir, float3 inv, float3 lo, float h,
+                                     float amin, float amax, float &a_in, float &a_out) {
+  float t0 = amin, t1 = amax;
+  const float o[3] = {org.x, org.y, org.z}, d[3] = {dir.x, dir.y, dir.z};
+  const float iv[3] = {inv.x, inv.y, inv.z}, l[3] = {lo.x, lo.y, lo.z};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float b0 = l[a], b1 = l[a] + h;
+    if (d[a] == 0.f) {
+      if (o[a] < b0 || o[a] > b1) return false;
+    } else {
+      float s0 = (b0 - o[a]) * iv[a], s1 = (b1 - o[a]) * iv[a];
+      t0 = fmaxf(t0, fminf(s0, s1));
+      t1 = fminf(t1, fmaxf(s0, s1));
+    }
+  }
+  a_in = t0;
+  a_out = t1;
+  return t1 > t0;
+}
+
+__device__ __forceinline__ float3 node_lo(int4 g, float scale) {
+  return make_float3((float)g.x * scale, (float)g.y * scale, (float)g.z * scale);
+}
+
+// ------------------------------------------------------------------ medium --
+// The trilinear field along a straight segment is a cubic in the segment
+// parameter tau (tau = 0 at the far end, 1 at the near end): its four
+// coefficients are formed once per segment and each evaluation is three FMAs.
+struct Cubic {
+  float p0, p1, p2, p3;
+};
+
+__device__ __forceinline__ Cubic field_cubic(const float *__restrict__ nd, float3 a, float3 d) {
+  const float4 lo = __ldg(reinterpret_cast<const float4 *>(nd));
+  const float4 hi = __ldg(reinterpret_cast<const float4 *>(nd) + 1);
+  const float n0 = lo.x, n1 = lo.y, n2 = lo.z, n3 = lo.w, n4 = hi.x, n5 = hi.y, n6 = hi.z,
+              n7 = hi.w;
+  // monomial form of the trilinear interpolant in (U, V, W)
+  const float c0 = n0, cu = n1 - n0, cv = n2 - n0, cw = n4 - n0;
+  const float cuv = (n3 - n2) - (n1 - n0), cuw = (n5 - n4) - (n1 - n0),
+              cvw = (n6 - n4) - (n2 - n0);
+  const float cuvw = ((n7 - n6) - (n5 - n4)) - ((n3 - n2) - (n1 - n0));
+  // substitute U = a.x + tau d.x, V = a.y + tau d.y, W = a.z + tau d.z
+  Cubic c;
+  const float ab = a.x * a.y, ac = a.x * a.z, bc = a.y * a.z;
+  c.p0 = c0 + cu * a.x + cv * a.y + cw * a.z + cuv * ab + cuw * ac + cvw * bc + cuvw * ab * a.z;
+  c.p1 = cu * d.x + cv * d.y + cw * d.z + cuv * (a.x * d.y + a.y * d.x) +
+         cuw * (a.x * d.z + a.z * d.x) + cvw * (a.y * d.z + a.z * d.y) +
+         cuvw * (ab * d.z + ac * d.y + bc * d.x);
+  c.p2 = cuv * d.x * d.y + cuw * d.x * d.z + cvw * d.y * d.z +
+         cuvw * (a.x * d.y * d.z + a.y * d.x * d.z + a.z * d.x * d.y);
+  c.p3 = cuvw * d.x * d.y * d.z;
+  return c;
+}
+
+struct TF {
+  const float4 *v, *s;  // knot values and slopes (shared memory)
+  float s_min, inv;
+};
+
+// (kappa, q_r, q_g, q_b) at parameter tau: piecewise-linear transfer function
+// of the field value, constant outside the knot range.
+__device__ __forceinline__ float4 medium(const Cubic &c, const TF &tf, float tau) {
+  const float s = fmaf(fmaf(fmaf(c.p3, tau, c.p2), tau, c.p1), tau, c.p0);
+  float z = (s - tf.s_min) * tf.inv;
+  z = fminf(fmaxf(z, 0.f), 7.f);
+  const int k = min((int)z, 6);
+  const float w = z - (float)k;
+  const float4 a = tf.v[k], d = tf.s[k];
+  return make_float4(fmaf(w, d.x, a.x), fmaf(w, d.y, a.y), fmaf(w, d.z, a.z), fmaf(w, d.w, a.w));
+}
+
+// Right-hand side of Eq. 2.29 for the state Y = (A, B_r, B_g, B_b).
+__device__ __forceinline__ float4 rhs(float4 kq, float4 Y) {
+  return make_float4(-kq.x * Y.x, fmaf(-kq.x, Y.y, kq.y), fmaf(-kq.x, Y.z, kq.z),
+                     fmaf(-kq.x, Y.w, kq.w));
+}
+
+__device__ __forceinline__ float4 axpy(float a, float4 x, float4 y) {
+  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+
+// Classical RK4 from (1, 0) over one step of length H with the medium at the
+// step's far end (k0), midpoint (kh) and near end (k1).
+__device__ __forceinline__ float4 rk4_step(float H, float4 k0, float4 kh, float4 k1) {
+  const float4 one = seg_identity();
+  const float4 K1 = rhs(k0, one);
+  const float4 K2 = rhs(kh, axpy(0.5f * H, K1, one));
+  const float4 K3 = rhs(kh, axpy(0.5f * H, K2, one));
+  const float4 K4 = rhs(k1, axpy(H, K3, one));
+  float4 s = axpy(2.f, K2, K1);
+  s = axpy(2.f, K3, s);
+  s.x += K4.x; s.y += K4.y; s.z += K4.z; s.w += K4.w;
+  return axpy(H * (1.f / 6.f), s, one);
+}
+
+// Dormand & Prince (1980) 5(4) tableau.
+namespace dp {
+constexpr float c2 = 1.f / 5, c3 = 3.f / 10, c4 = 4.f / 5, c5 = 8.f / 9;
+constexpr float a21 = 1.f / 5;
+constexpr float a31 = 3.f / 40, a32 = 9.f / 40;
+constexpr float a41 = 44.f / 45, a42 = -56.f / 15, a43 = 32.f / 9;
+constexpr float a51 = 19372.f / 6561, a52 = -25360.f / 2187, a53 = 64448.f / 6561,
+                a54 = -212.f / 729;
+constexpr float a61 = 9017.f / 3168, a62 = -355.f / 33, a63 = 46732.f / 5247, a64 = 49.f / 176,
+                a65 = -5103.f / 18656;
+constexpr float b1 = 35.f / 384, b3 = 500.f / 1113, b4 = 125.f / 192, b5 = -2187.f / 6784,
+                b6 = 11.f / 84;
+// e = b - b* (fifth- minus fourth-order weights), seventh stage at the end point
+constexpr float e1 = 71.f / 57600, e3 = -71.f / 16695, e4 = 71.f / 1920, e5 = -17253.f / 339200,
+                e6 = 22.f / 525, e7 = -1.f / 40;
+}  // namespace dp
+
+__device__ __forceinline__ float4 lin4(float a, float4 x, float b, float4 y) {
+  return make_float4(fmaf(a, x.x, b * y.x), fmaf(a, x.y, b * y.y), fmaf(a, x.z, b * y.z),
+                     fmaf(a, x.w, b * y.w));
+}
+
+// (A, B) of one segment of world length dx: RK4 x nsteps, or DOPRI5 inside
+// the midpoint bisection of Algorithm 1, walked far half first so that each
+// accepted piece is nearer than everything accumulated so far.
+__device__ float4 integrate_segment(const Cubic &cu, const TF &tf, float dx, const Integ &I,
+                                    int &steps) {
+  float4 acc = seg_identity();
+  if (I.method == 0) {
+    const int n = I.nsteps;
+    const float H = dx / (float)n, dt = 1.f / (float)n;
+    float4 k0 = medium(cu, tf, 0.f);
+    for (int s = 0; s < n; ++s) {
+      const float t0 = (float)s * dt;
+      const float4 kh = medium(cu, tf, t0 + 0.5f * dt);
+      const float4 k1 = medium(cu, tf, (s + 1 == n) ? 1.f : t0 + dt);
+      acc = seg_combine(rk4_step(H, k0, kh, k1), acc);
+      k0 = k1;
+    }
+    steps += n;
+    return acc;
+  }
+  int depth = 0;
+  unsigned idx = 0;
+  float4 kq0 = medium(cu, tf, 0.f);
+  const float4 one = seg_identity();
+  if (I.method != 1) {  // Gauss-2 (Eqs. 2.32-2.33) or Simpson (Eq. 2.34) inside Algorithm 1
+    for (;;) {
+      const float dtau = ldexpf(1.f, -depth);
+      const float t0 = (float)idx * dtau;
+      const float H = dx * dtau;
+      float4 S, kq1 = kq0;
+      float kmax;
+      if (I.method == 2) {
+        // Gauss points c = 1/2 -+ sqrt(3)/6, measured from the step's far end
+        const float4 g0 = medium(cu, tf, fmaf(0.21132486540518713f, dtau, t0));
+        const float4 g1 = medium(cu, tf, fmaf(0.78867513459481287f, dtau, t0));
+        const float a1 = 0.25f * H * (g0.x + g1.x), a2 = (H * H / 12.f) * g0.x * g1.x;
+        const float inv = 1.f / (1.f + a1 + a2);
+        const float h2 = H * H * 0.14433756729740644f;  // H^2 sqrt(3) / 12
+        S.x = (1.f - a1 + a2) * inv;
+        S.y = (0.5f * H * (g0.y + g1.y) + h2 * (g0.x * g1.y - g1.x * g0.y)) * inv;
+        S.z = (0.5f * H * (g0.z + g1.z) + h2 * (g0.x * g1.z - g1.x * g0.z)) * inv;
+        S.w = (0.5f * H * (g0.w + g1.w) + h2 * (g0.x * g1.w - g1.x * g0.w)) * inv;
+        kmax = H * fmaxf(g0.x, g1.x);
+      } else {
+        // Simpson nodes: far end, midpoint, near end
+        const float4 kh = medium(cu, tf, t0 + 0.5f * dtau);
+        kq1 = medium(cu, tf, t0 + dtau);
+        const float e = -(H / 6.f) * (kq0.x + 4.f * kh.x + kq1.x);
+        const float sa = __expf(0.5f * e), A = sa * sa;
+        const float w0 = (H / 6.f) * A, wh = (H / 6.f) * 4.f * sa, w1 = H / 6.f;
+        S = make_float4(A, fmaf(w0, kq0.y, fmaf(wh, kh.y, w1 * kq1.y)),
+                        fmaf(w0, kq0.z, fmaf(wh, kh.z, w1 * kq1.z)),
+                        fmaf(w0, kq0.w, fmaf(wh, kh.w, w1 * kq1.w)));
+        kmax = H * fmaxf(fmaxf(kq0.x, kh.x), kq1.x);
+      }
+      ++steps;
+      if (depth < I.max_depth && kmax > I.c_rk) {
+        ++depth;  // far half first
+        idx <<= 1;
+        continue;
+      }
+      acc = seg_combine(S, acc);
+      kq0 = kq1;  // Simpson: the next step starts where this one ended (unused by Gauss)
+      ++idx;
+      while (depth > 0 && !(idx & 1u)) {
+        idx >>= 1;
+        --depth;
+      }
+      if (depth == 0) break;
+    }
+    return acc;
+  }
+  for (;;) {
+    const float dtau = ldexpf(1.f, -depth);
+    const float t0 = (float)idx * dtau;
+    const float H = dx * dtau;
+    const float4 kq2 = medium(cu, tf, fmaf(dp::c2, dtau, t0));
+    const float4 kq3 = medium(cu, tf, fmaf(dp::c3, dtau, t0));
+    const float4 kq4 = medium(cu, tf, fmaf(dp::c4, dtau, t0));
+    const float4 kq5 = medium(cu, tf, fmaf(dp::c5, dtau, t0));
+    const float4 kq6 = medium(cu, tf, t0 + dtau);
+    const float4 K1 = rhs(kq0, one);
+    const float4 K2 = rhs(kq2, axpy(H * dp::a21, K1, one));
+    const float4 K3 = rhs(kq3, axpy(H, lin4(dp::a31, K1, dp::a32, K2), one));
+    float4 t = lin4(dp::a41, K1, dp::a42, K2);
+    t = axpy(dp::a43, K3, t);
+    const float4 K4 = rhs(kq4, axpy(H, t, one));
+    t = lin4(dp::a51, K1, dp::a52, K2);
+    t = axpy(dp::a53, K3, t);
+    t = axpy(dp::a54, K4, t);
+    const float4 K5 = rhs(kq5, axpy(H, t, one));
+    t = lin4(dp::a61, K1, dp::a62, K2);
+    t = axpy(dp::a63, K3, t);
+    t = axpy(dp::a64, K4, t);
+    t = axpy(dp::a65, K5, t);
+    const float4 K6 = rhs(kq6, axpy(H, t, one));
+    t = lin4(dp::b1, K1, dp::b3, K3);
+    t = axpy(dp::b4, K4, t);
+    t = axpy(dp::b5, K5, t);
+    t = axpy(dp::b6, K6, t);
+    const float4 Y5 = axpy(H, t, one);
+    const float4 K7 = rhs(kq6, Y5);
+    float4 e = lin4(dp::e1, K1, dp::e3, K3);
+    e = axpy(dp::e4, K4, e);
+    e = axpy(dp::e5, K5, e);
+    e = axpy(dp::e6, K6, e);
+    e = axpy(dp::e7, K7, e);
+    const float err = H * fmaxf(fmaxf(fabsf(e.x), fabsf(e.y)), fmaxf(fabsf(e.z), fabsf(e.w)));
+    const float kmax =
+        fmaxf(fmaxf(fmaxf(kq0.x, kq2.x), fmaxf(kq3.x, kq4.x)), fmaxf(kq5.x, kq6.x));
+    ++steps;
+    if (depth < I.max_depth && (H * kmax > I.c_rk || err > I.tol)) {
+      ++depth;  // far half first; it starts where this step started
+      idx <<= 1;
+      continue;
+    }
+    acc = seg_combine(Y5, acc);
+    kq0 = kq6;
+    ++idx;
+    while (depth > 0 && !(idx & 1u)) {
+      idx >>= 1;
+      --depth;
+    }
+    if (depth == 0) break;
+  }
+  return acc;
+}
+
+// ----------------------------------------------------------------- culling --
+__device__ __forceinline__ int4 empty_rect() { return make_int4(0, -1, 0, -1); }
+
+// Pixel rectangle of the camera-space bounding box of the cube [lo, lo+h]^3:
+// the box is mapped by X = (t, u, v/n)^T (x - o) (an affine map, so its AABB is
+// centre +- half-extent), clipped to the visible depth range, and projected.
+__device__ int4 box_rect(const Cam &c, float3 lo, float h) {
+  const float hh = 0.5f * h;
+  const float cx = lo.x + hh - c.o[0], cy = lo.y + hh - c.o[1], cz = lo.z + hh - c.o[2];
+  float X[3], E[3];
+  const float *rows[3] = {c.t, c.u, c.vn};
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const float *R = rows[r];
+    X[r] = fmaf(R[0], cx, fmaf(R[1], cy, R[2] * cz));
+    E[r] = hh * (fabsf(R[0]) + fabsf(R[1]) + fabsf(R[2]));
+  }
+  const float zlo = fmaxf(X[2] - E[2], c.ortho ? 0.f : c.n);
+  const float zhi = fminf(X[2] + E[2], c.f);
+  if (!(zlo <= zhi)) return empty_rect();
+  float pmin[2], pmax[2];
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const float x0 = X[a] - E[a], x1 = X[a] + E[a];
+    float lo_p, hi_p;
+    if (c.ortho) {
+      lo_p = x0 / c.ell;
+      hi_p = x1 / c.ell;
+    } else {
+      const float sl = c.n / (zlo * c.ell), sh = c.n / (zhi * c.ell);
+      lo_p = fminf(fminf(x0 * sl, x0 * sh), fminf(x1 * sl, x1 * sh));
+      hi_p = fmaxf(fmaxf(x0 * sl, x0 * sh), fmaxf(x1 * sl, x1 * sh));
+    }
+    const float cen = a == 0 ? c.cw : c.ch;
+    pmin[a] = lo_p + cen;
+    pmax[a] = hi_p + cen;
+  }
+  const float wl = (float)(c.w - 1), hl = (float)(c.h - 1);
+  const float i0 = fmaxf(ceilf(pmin[0]), 0.f), i1 = fminf(floorf(pmax[0]), wl);
+  const float j0 = fmaxf(ceilf(pmin[1]), 0.f), j1 = fminf(floorf(pmax[1]), hl);
+  if (!(i0 <= i1 && j0 <= j1)) return empty_rect();
+  return make_int4((int)i0, (int)i1, (int)j0, (int)j1);
+}
+
+
+// The segment of one leaf along one ray: slab interval, reference coordinates
+// of its far end and their change to the near end, field cubic, integration.
+__device__ __forceinline__ float4 leaf_segment(const Topo &T, const Field &Fd, const Cam &c,
+                                               const Integ &I, const TF &tf, int leaf, float3 org,
+                                               float3 dir, float3 inv, float scale, int &steps) {
+  const int4 g = __ldg(T.geo + leaf);
+  const float ih = ldexpf(1.f, g.w);  // 1 / edge length
+  const float3 lo = node_lo(g, scale);
+  float a_in, a_out;
+  slab(org, dir, inv, lo, ldexpf(1.f, -g.w), c.amin, c.amax, a_in, a_out);
+  const float3 ufar = make_float3((fmaf(a_out, dir.x, org.x) - lo.x) * ih,
+                                  (fmaf(a_out, dir.y, org.y) - lo.y) * ih,
+                                  (fmaf(a_out, dir.z, org.z) - lo.z) * ih);
+  const float da = a_in - a_out;
+  const float3 du = make_float3(da * dir.x * ih, da * dir.y * ih, da * dir.z * ih);
+  const float dx =
+      fmaxf(a_out - a_in, 0.f) * sqrtf(dir.x * dir.x + dir.y * dir.y + dir.z * dir.z);
+  const Cubic cu = field_cubic(Fd.nodal + 8 * (size_t)leaf, ufar, du);
+  return integrate_segment(cu, tf, dx, I, steps);
+}
+
+}  // namespace
+}  // namespace ocr

@@ -84,6 +84,15 @@ class Renderer:
         st.update(extra)
         return out, st
 
+    def backward(self, grad_rgba: torch.Tensor, stream=None):
+        """dL/d(nodal) [N, 8] and dL/d(knots) [8, 4] for the data, camera and
+        integrator last set, given dL/d(rgba) [h, w, 4] on the device."""
+        g = grad_rgba.detach().to(self.device, torch.float32).contiguous()
+        gn = torch.empty_like(self.nodal)
+        gt = torch.empty_like(self.tf)
+        capi.render_backward(self.h, g, gn, gt, _stream_ptr(stream))
+        return gn, gt
+
     def device_bytes(self) -> int:
         return capi.device_bytes(self.h)
 
@@ -97,3 +106,27 @@ class Renderer:
             self.close()
         except Exception:
             pass
+
+
+class RenderFunction(torch.autograd.Function):
+    """image = render(nodal, knots) with the CUDA adjoint as its backward.
+
+    ``RenderFunction.apply(nodal, knots, renderer)`` renders with the
+    renderer's forest, camera and integrator; the backward pass calls
+    ``ocr_render_backward`` (segments recomputed, not stored)."""
+
+    @staticmethod
+    def forward(ctx, nodal, knots, renderer):
+        renderer.set_data(nodal.detach().contiguous(), knots.detach().contiguous())
+        img, _ = renderer.render()
+        ctx.renderer = renderer
+        ctx.save_for_backward(nodal, knots)
+        return img
+
+    @staticmethod
+    def backward(ctx, grad_img):
+        nodal, knots = ctx.saved_tensors
+        r = ctx.renderer
+        r.set_data(nodal.detach().contiguous(), knots.detach().contiguous())
+        gn, gt = r.backward(grad_img)
+        return gn, gt, None
