@@ -56,6 +56,8 @@ def parse_args():
                    help="CPU baseline renders every n-th image row")
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     p.add_argument("--no-backward", action="store_true", help="skip the adjoint measurement")
+    p.add_argument("--batch-cameras", type=int, default=64,
+                   help="cameras of the batched (CUDA graph) measurement; 0 skips it")
     p.add_argument("--image", default="1920x1080",
                    help="image size WxH (smaller sizes only for profiling captures)")
     return p.parse_args()
@@ -141,6 +143,65 @@ def cpu_baseline(forest, tf, cam, integ, stride: int):
     return {"value": r["segments"] / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"every {stride}th row of the 1920x1080 image ({len(rows)} rows, "
                       f"{r['segments']} segments, {dt:.1f} s)"}
+
+
+def run_batch(args, forest, tf, integ, dev, flush):
+    """Many cameras of uneven sizes (log-uniform 256^2 .. 2048^2) rendered by one
+    CUDA-graph launch, against the same cameras rendered one view at a time
+    (each: set the camera, render, as a single-view user would)."""
+    import torch
+    from paper_1809_01334_gb300 import Renderer
+    from paper_1809_01334_gb300 import inputs as I
+    cams = I.batch_cameras(args.batch_cameras)
+    npix = sum(c.w * c.h for c in cams)
+    r = Renderer(forest, tf, integ, device=dev)
+    r.set_cameras(cams)
+    out = torch.empty((npix, 4), dtype=torch.float32, device=dev)
+    _, _, st = r.render_batch(out, with_index=True)
+    segments = st["segments"]
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(s):
+        r.render_batch(out, stream=s)
+    torch.cuda.current_stream(dev).wait_stream(s)
+    torch.cuda.synchronize(dev)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        r.render_batch(out, stream=torch.cuda.current_stream(dev))
+    stream = torch.cuda.current_stream(dev)
+    reps = 3
+    gms = []
+    for k in range(1 + reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.replay()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        if k:
+            gms.append(a.elapsed_time(b))
+    del g
+    r.close()
+    # one view at a time
+    one = Renderer(forest, tf, integ, device=dev)
+    seq = []
+    for k in range(2):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for cam in cams:
+            one.set_camera(cam)
+            img, _ = one.render()
+        torch.cuda.synchronize(dev)
+        if k:
+            seq.append((time.perf_counter() - t0) * 1e3)
+    one.close()
+    gm = sum(gms) / len(gms)
+    sq = sum(seq) / len(seq)
+    return {"cameras": len(cams), "pixels": npix, "segments": segments,
+            "graph_ms": gm, "sequential_ms": sq, "speedup_vs_sequential": sq / gm,
+            "segments_per_s": segments / (gm * 1e-3), "mpixel_per_s": npix / (gm * 1e-3) / 1e6,
+            "sequential": "one Renderer: set_camera + render per view, wall time",
+            "sizes": "square, side round(256 * 8**u), u ~ U[0,1], seeded"}
 
 
 def run_reference(args, world, rank):
@@ -278,6 +339,8 @@ def main():
             if k >= args.warmup:
                 bwd_ms.append(a.elapsed_time(b))
 
+    batch = run_batch(args, forest, tf, integ, dev, flush) if args.batch_cameras > 0 else None
+
     if rank == 0:
         peaks, src = measured_peaks()
         mm = sum(merge_ms) / len(merge_ms)
@@ -316,6 +379,8 @@ def main():
                          "ms_merge": mm, "ms_prune": sum(prune_ms) / len(prune_ms)},
             "clocks": clk.summary(),
         }
+        if batch:
+            line["batch"] = batch
         if bwd_ms:
             mb = sum(bwd_ms) / len(bwd_ms)
             line["backward"] = {"ms_backward": mb, "ms_forward": ms_max,

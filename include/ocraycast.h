@@ -23,8 +23,8 @@
  *    internal copies of the forest topology and a scratch arena, both freed
  *    by ocr_destroy().
  *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default
- *    stream).  Work is enqueued on it; ocr_render blocks the host once per
- *    call, after pruning, to size its scratch memory.
+ *    stream).  Work is enqueued on it; ocr_render returns without waiting
+ *    for the device unless counters or phase times are requested.
  *  - Only the single unit-cube tree with the identity map is implemented in
  *    this version (OCR_GEOM_CUBE); other geometries return
  *    OCR_ERR_UNSUPPORTED.
@@ -106,7 +106,7 @@ typedef struct {
   int32_t *d_rects;
   int fill_counters;
   int time_phases;
-  int64_t visible_leaves; /* leaves that survived pruning */
+  int64_t visible_leaves; /* (camera, leaf) pairs that survived pruning */
   int64_t segments;       /* ray segments integrated (sum of d_counts) */
   int64_t rk_steps;       /* Runge-Kutta steps taken over all segments */
   int64_t leaf_tests;     /* (leaf, ray) slab tests performed */
@@ -134,11 +134,21 @@ int ocr_forest_set_data(ocr_forest *F, const float *d_nodal, const float *d_tf, 
 
 int ocr_set_integrator(ocr_forest *F, const ocr_integrator *integ);
 
-/* Set the camera (host struct, copied).  ncams must be 1 in this version. */
+/* Set the cameras (host structs, copied), 1 <= ncams <= 4096.  Plans every
+ * camera once: its pruning and slot layout run on the device (legacy default
+ * stream, blocking) to size its scratch, which is allocated here.  Rendering
+ * then never waits for the host, so ocr_render without counters can be
+ * captured in a CUDA graph.  Several cameras are rendered by one ocr_render
+ * call (batching: the paper's multiple image instances, Sec. 3). */
 int ocr_set_camera(ocr_forest *F, const ocr_camera *cams, int ncams);
 
-/* Render one image: d_rgba [h*w*4] float32, row-major, (I_r, I_g, I_b, 1 - A)
- * per pixel.  stats may be NULL. */
+/* Render the images of all cameras: d_rgba float32, the cameras' images
+ * concatenated in order, each [h*w*4] row-major, (I_r, I_g, I_b, 1 - A) per
+ * pixel.  With several cameras the work is spread over internal streams that
+ * fork from and join back into `stream`.  stats may be NULL; its d_counts is
+ * indexed like the concatenated image, d_visible is the union over cameras,
+ * d_rects belongs to the first camera, time_phases applies to single-camera
+ * renders only. */
 int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats);
 
 /* Pruning for callers that cannot allocate device memory at the time they

@@ -137,6 +137,16 @@ def set_camera(h, o, v, t, u, ell, near, far, w, h_px, ortho=False):
     _check(lib().ocr_set_camera(h, C.byref(c), 1), "ocr_set_camera")
 
 
+def set_cameras(h, cams):
+    """ocr_set_camera with several cameras (inputs.Camera objects)."""
+    arr = (Camera * len(cams))()
+    for c, cam in zip(arr, cams):
+        c.o[:], c.v[:], c.t[:], c.u[:] = cam.o, cam.v, cam.t, cam.u
+        c.ell, c.near_, c.far_ = float(cam.ell), float(cam.near), float(cam.far)
+        c.w, c.h, c.ortho = int(cam.w), int(cam.h), int(bool(cam.ortho))
+    _check(lib().ocr_set_camera(h, arr, len(cams)), "ocr_set_camera")
+
+
 def render(h, d_rgba, stream=None, d_counts=None, d_visible=None, d_rects=None,
            fill_counters: bool = False, time_phases: bool = False) -> dict:
     s = Stats(_ptr(d_counts), _ptr(d_visible), _ptr(d_rects), int(bool(fill_counters)),

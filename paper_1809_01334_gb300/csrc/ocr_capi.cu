@@ -19,6 +19,25 @@
 
 using namespace ocr;
 
+// Per-camera plan: the float32 camera, its pixel range in the concatenated
+// image, the slot layout found when the camera was set (the render recomputes
+// it on the device and launches with these sizes, so it never waits for the
+// host), and the camera's own scratch.
+struct CamPlan {
+  Cam cam{};
+  long long npix = 0, pix_off = 0;
+  std::vector<long long> gslots;      // [L + 1] slot boundaries of the level groups
+  int4 *d_rect = nullptr;             // [N + M + 1]
+  long long *d_off = nullptr;         // [M + 1]
+  long long *d_bsums = nullptr;       // [area_scan_blocks(M) + 1]
+  long long *d_gslots = nullptr;      // [L + 1]
+  int *d_chunk = nullptr;             // [total / kChunk + 2]
+  float4 *d_entries = nullptr;        // [total slots]
+};
+
+constexpr int kRenderStreams = 4;   // cameras of a batch are spread over these
+constexpr int kMaxCameras = 4096;
+
 struct ocr_forest {
   int N = 0, M = 0, L = 0;
   int root = 0;                       // unified id of the tree root
@@ -26,6 +45,7 @@ struct ocr_forest {
   std::vector<int> level_count;       // number of internal nodes at level l
   std::vector<int> h_group_nodes;     // [L + 1] group boundaries, deepest level first, then M
   int4 *d_geo = nullptr;              // [N + M + 1]
+  int bsums_blocks = 0;               // area_scan_blocks(M) + 1
   int *d_child = nullptr;             // [(M + 1) * 8]
   int2 *d_leaves = nullptr;           // [M] leaf range of each internal node
   int lt = 0;                         // tile level: deepest level with stored aggregates
@@ -36,20 +56,13 @@ struct ocr_forest {
   float s_min = 0.f, s_max = 1.f;
   bool has_data = false, has_cam = false, has_integ = false;
   Integ integ{};
-  Cam cam{};
-  // scratch
-  int4 *d_rect = nullptr;             // [N + M + 1]
-  long long *d_off = nullptr;         // [M + 1]
-  long long *d_block_sums = nullptr;  // [nblk + 1]
-  int block_sums_cap = 0;
-  long long *d_group_slots = nullptr; // [L + 1]
-  long long *h_group_slots = nullptr; // pinned [L + 1 + 8]
+  std::vector<CamPlan> plans;         // one per camera of the last ocr_set_camera
+  long long total_pix = 0;
+  cudaStream_t sub[kRenderStreams] = {};
+  cudaEvent_t fork = nullptr, join[kRenderStreams] = {};
+  long long *h_group_slots = nullptr; // pinned [L + 1 + kStats]
   unsigned long long *d_stats = nullptr;  // [kStats]
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // start, layout, subtree, end
-  float4 *d_entries = nullptr;
-  long long entries_cap = 0;
-  int *d_chunk_node = nullptr;        // [chunk_cap]
-  long long chunk_cap = 0;
   // adjoint
   unsigned long long *d_mkey = nullptr;  // [N] Morton key of each leaf
   unsigned long long fx = 0;             // Morton bit positions of x
@@ -115,18 +128,30 @@ int dev_alloc(T **p, size_t n, int64_t &bytes) {
   return OCR_OK;
 }
 
+void free_plans(ocr_forest *F) {
+  for (CamPlan &P : F->plans) {
+    cudaFree(P.d_rect);
+    cudaFree(P.d_off);
+    cudaFree(P.d_bsums);
+    cudaFree(P.d_gslots);
+    cudaFree(P.d_chunk);
+    cudaFree(P.d_entries);
+  }
+  F->plans.clear();
+}
+
 void free_all(ocr_forest *F) {
   cudaFree(F->d_geo);
   cudaFree(F->d_child);
   cudaFree(F->d_leaves);
   cudaFree(F->d_group_nodes);
-  cudaFree(F->d_rect);
-  cudaFree(F->d_off);
-  cudaFree(F->d_block_sums);
-  cudaFree(F->d_group_slots);
+  free_plans(F);
+  for (int q = 0; q < kRenderStreams; ++q) {
+    if (F->sub[q]) cudaStreamDestroy(F->sub[q]);
+    if (F->join[q]) cudaEventDestroy(F->join[q]);
+  }
+  if (F->fork) cudaEventDestroy(F->fork);
   cudaFree(F->d_stats);
-  cudaFree(F->d_entries);
-  cudaFree(F->d_chunk_node);
   cudaFree(F->d_mkey);
   cudaFree(F->d_leaf_off);
   cudaFree(F->d_bsums);
@@ -140,6 +165,35 @@ void free_all(ocr_forest *F) {
   if (F->h_group_slots) cudaFreeHost(F->h_group_slots);
   for (cudaEvent_t &e : F->ev)
     if (e) cudaEventDestroy(e);
+}
+
+bool valid_camera(const ocr_camera &c) {
+  return c.w >= 1 && c.h >= 1 && (int64_t)c.w * c.h <= (1ll << 31) - 1 && c.near_ > 0.0 &&
+         c.far_ > c.near_ && c.ell > 0.0;
+}
+
+// float32 camera constants (both the render and ocr_prune_noalloc read these
+// exact roundings)
+void to_cam(const ocr_camera &c, Cam &k) {
+  for (int a = 0; a < 3; ++a) {
+    k.o[a] = (float)c.o[a];
+    k.v[a] = (float)(c.ortho ? c.v[a] / c.near_ : c.v[a]);
+    k.lt[a] = (float)(c.ell * c.t[a]);
+    k.lu[a] = (float)(c.ell * c.u[a]);
+    k.t[a] = (float)c.t[a];
+    k.u[a] = (float)c.u[a];
+    k.vn[a] = (float)(c.v[a] / c.near_);
+  }
+  k.n = (float)c.near_;
+  k.f = (float)c.far_;
+  k.ell = (float)c.ell;
+  k.cw = 0.5f * (float)(c.w - 1);
+  k.ch = 0.5f * (float)(c.h - 1);
+  k.w = c.w;
+  k.h = c.h;
+  k.ortho = c.ortho ? 1 : 0;
+  k.amin = c.ortho ? 0.f : 1.f;
+  k.amax = (float)(c.ortho ? c.far_ : c.far_ / c.near_);
 }
 
 }  // namespace
@@ -291,9 +345,6 @@ int ocr_build_forest(const ocr_forest_desc *desc, void *stream, ocr_forest **out
       (rc = dev_alloc(&F->d_child, child.size(), F->bytes)) ||
       (rc = dev_alloc(&F->d_leaves, lrange.size(), F->bytes)) ||
       (rc = dev_alloc(&F->d_group_nodes, F->h_group_nodes.size(), F->bytes)) ||
-      (rc = dev_alloc(&F->d_rect, (size_t)N + M + 1, F->bytes)) ||
-      (rc = dev_alloc(&F->d_off, (size_t)M + 1, F->bytes)) ||
-      (rc = dev_alloc(&F->d_group_slots, F->h_group_nodes.size(), F->bytes)) ||
       (rc = dev_alloc(&F->d_stats, kStats, F->bytes)) ||
       (rc = dev_alloc(&F->d_mkey, (size_t)N, F->bytes)) ||
       (rc = dev_alloc(&F->d_leaf_off, (size_t)N + 1, F->bytes)) ||
@@ -302,12 +353,7 @@ int ocr_build_forest(const ocr_forest_desc *desc, void *stream, ocr_forest **out
     delete F;
     return rc;
   }
-  F->block_sums_cap = area_scan_blocks(M) + 1;
-  if ((rc = dev_alloc(&F->d_block_sums, F->block_sums_cap, F->bytes))) {
-    free_all(F);
-    delete F;
-    return rc;
-  }
+  F->bsums_blocks = area_scan_blocks(M) + 1;
   if (cudaMallocHost((void **)&F->h_group_slots,
                      sizeof(long long) * (F->h_group_nodes.size() + kStats)) !=
       cudaSuccess) {
@@ -379,130 +425,158 @@ int ocr_set_integrator(ocr_forest *F, const ocr_integrator *I) {
 }
 
 int ocr_set_camera(ocr_forest *F, const ocr_camera *cams, int ncams) {
-  if (!F || !cams) return OCR_ERR_INVALID;
-  if (ncams != 1) return OCR_ERR_UNSUPPORTED;
-  const ocr_camera &c = cams[0];
-  if (c.w < 1 || c.h < 1 || (int64_t)c.w * c.h > (1ll << 31) - 1 || !(c.near_ > 0.0) ||
-      !(c.far_ > c.near_) || !(c.ell > 0.0))
-    return OCR_ERR_INVALID;
-  Cam &k = F->cam;
-  for (int a = 0; a < 3; ++a) {
-    k.o[a] = (float)c.o[a];
-    k.v[a] = (float)(c.ortho ? c.v[a] / c.near_ : c.v[a]);
-    k.lt[a] = (float)(c.ell * c.t[a]);
-    k.lu[a] = (float)(c.ell * c.u[a]);
-    k.t[a] = (float)c.t[a];
-    k.u[a] = (float)c.u[a];
-    k.vn[a] = (float)(c.v[a] / c.near_);
+  if (!F || !cams || ncams < 1) return OCR_ERR_INVALID;
+  if (ncams > kMaxCameras) return OCR_ERR_UNSUPPORTED;
+  for (int k = 0; k < ncams; ++k)
+    if (!valid_camera(cams[k])) return OCR_ERR_INVALID;
+  free_plans(F);
+  F->has_cam = false;
+  F->plans.resize(ncams);
+  long long pix = 0;
+  for (int k = 0; k < ncams; ++k) {
+    CamPlan &P = F->plans[k];
+    to_cam(cams[k], P.cam);
+    P.npix = (long long)cams[k].w * cams[k].h;
+    P.pix_off = pix;
+    pix += P.npix;
   }
-  k.n = (float)c.near_;
-  k.f = (float)c.far_;
-  k.ell = (float)c.ell;
-  k.cw = 0.5f * (float)(c.w - 1);
-  k.ch = 0.5f * (float)(c.h - 1);
-  k.w = c.w;
-  k.h = c.h;
-  k.ortho = c.ortho ? 1 : 0;
-  k.amin = c.ortho ? 0.f : 1.f;
-  k.amax = (float)(c.ortho ? c.far_ : c.far_ / c.near_);
+  F->total_pix = pix;
+  if (ncams > 1 && !F->fork) {
+    OCR_CUDA(cudaEventCreateWithFlags(&F->fork, cudaEventDisableTiming));
+    for (int q = 0; q < kRenderStreams; ++q) {
+      OCR_CUDA(cudaStreamCreateWithFlags(&F->sub[q], cudaStreamNonBlocking));
+      OCR_CUDA(cudaEventCreateWithFlags(&F->join[q], cudaEventDisableTiming));
+    }
+  }
+  // plan every camera: run its pruning and slot layout once and keep the sizes
+  const int G = (int)F->h_group_nodes.size();
+  Topo T{F->d_geo, F->d_child, F->d_leaves, F->N, F->M, F->L, F->lt};
+  for (CamPlan &P : F->plans) {
+    int rc;
+    if ((rc = dev_alloc(&P.d_rect, (size_t)F->N + F->M + 1, F->bytes)) ||
+        (rc = dev_alloc(&P.d_off, (size_t)F->M + 1, F->bytes)) ||
+        (rc = dev_alloc(&P.d_bsums, (size_t)F->bsums_blocks, F->bytes)) ||
+        (rc = dev_alloc(&P.d_gslots, (size_t)G, F->bytes)))
+      return rc;
+    Scratch S{P.d_rect, P.d_off, nullptr, F->d_stats, nullptr, nullptr, nullptr};
+    OCR_CUDA(launch_cull_leaves(T, P.cam, S, 0));
+    for (int l = F->L - 1; l >= 0; --l)
+      OCR_CUDA(launch_union_level(T, F->level_base[l], F->level_base[l] + F->level_count[l], P.cam,
+                                  S, 0));
+    OCR_CUDA(launch_area_scan(T, S, P.d_bsums, F->bsums_blocks, P.d_gslots, F->d_group_nodes, G,
+                              0));
+    OCR_CUDA(cudaMemcpyAsync(F->h_group_slots, P.d_gslots, sizeof(long long) * G,
+                             cudaMemcpyDeviceToHost, 0));
+    OCR_CUDA(cudaStreamSynchronize(0));
+    P.gslots.assign(F->h_group_slots, F->h_group_slots + G);
+    const long long total = P.gslots[G - 1];
+    if ((rc = dev_alloc(&P.d_chunk, (size_t)(total / kChunk + 2), F->bytes)) ||
+        (rc = dev_alloc(&P.d_entries, (size_t)(total > 0 ? total : 1), F->bytes)))
+      return rc;
+  }
   F->has_cam = true;
   return OCR_OK;
 }
+
+}  // extern "C"
+
+namespace {
+
+// Enqueue one camera's render on stream st: pruning, rectangle unions, slot
+// layout (recomputed; equal to the plan), subtree pass, coarsening passes and
+// the pixel pass into rgba.  No host synchronisation.
+int enqueue_camera(ocr_forest *F, CamPlan &P, float4 *rgba, int *counts, unsigned char *visible,
+                   cudaStream_t st, bool timed, bool &subtree_ran, int64_t &launches) {
+  const int G = (int)F->h_group_nodes.size();
+  Topo T{F->d_geo, F->d_child, F->d_leaves, F->N, F->M, F->L, F->lt};
+  Field Fd{F->d_nodal, reinterpret_cast<const float4 *>(F->d_tf), F->s_min,
+           7.f / (F->s_max - F->s_min)};
+  Scratch S{P.d_rect, P.d_off, P.d_entries, F->d_stats, counts, visible, P.d_chunk};
+  OCR_CUDA(launch_cull_leaves(T, P.cam, S, st));
+  ++launches;
+  for (int l = F->L - 1; l >= 0; --l) {
+    OCR_CUDA(launch_union_level(T, F->level_base[l], F->level_base[l] + F->level_count[l], P.cam,
+                                S, st));
+    launches += F->level_count[l] > 0;
+  }
+  OCR_CUDA(launch_area_scan(T, S, P.d_bsums, F->bsums_blocks, P.d_gslots, F->d_group_nodes, G,
+                            st));
+  launches += area_scan_blocks(F->M) > 0 ? 4 : 1;
+  OCR_CUDA(launch_chunk_map(T, S, st));
+  launches += F->M > 0;
+  if (timed) OCR_CUDA(cudaEventRecord(F->ev[1], st));
+  // group g covers level L - 1 - g: the tile level runs the subtree pass, the
+  // levels above it the coarsening passes, deepest first
+  for (int g = 0; g + 1 < G; ++g) {
+    const int level = F->L - 1 - g;
+    const long long a = P.gslots[g], b = P.gslots[g + 1];
+    if (b <= a) continue;
+    if (level == F->lt) {
+      if (timed) OCR_CUDA(cudaEventRecord(F->ev[2], st));
+      OCR_CUDA(launch_subtree(T, Fd, P.cam, F->integ, S, F->h_group_nodes[g],
+                              F->h_group_nodes[g + 1], a, b, st));
+      if (timed) OCR_CUDA(cudaEventRecord(F->ev[3], st));
+      subtree_ran = true;
+    } else {
+      OCR_CUDA(launch_coarsen(T, Fd, P.cam, F->integ, S, F->h_group_nodes[g],
+                              F->h_group_nodes[g + 1], a, b, nullptr, st));
+    }
+    ++launches;
+  }
+  // the super-root pass writes every pixel
+  OCR_CUDA(launch_coarsen(T, Fd, P.cam, F->integ, S, F->M, F->M, 0, P.npix, rgba, st));
+  ++launches;
+  return OCR_OK;
+}
+
+}  // namespace
+
+extern "C" {
 
 int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats) {
   if (!F || !d_rgba) return OCR_ERR_INVALID;
   if (!F->has_data || !F->has_cam || !F->has_integ) return OCR_ERR_STATE;
   if ((uintptr_t)d_rgba & 15) return OCR_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
-  const int G = (int)F->h_group_nodes.size();  // L + 1
-  Topo T{F->d_geo, F->d_child, F->d_leaves, F->N, F->M, F->L, F->lt};
-  Field Fd{F->d_nodal, reinterpret_cast<const float4 *>(F->d_tf), F->s_min,
-           7.f / (F->s_max - F->s_min)};
-  Scratch S{F->d_rect, F->d_off, F->d_entries, F->d_stats, nullptr, nullptr, nullptr};
-  if (stats) {
-    S.counts = stats->d_counts;
-    S.visible = stats->d_visible;
-    if (S.counts)
-      OCR_CUDA(cudaMemsetAsync(S.counts, 0, sizeof(int) * (size_t)F->cam.w * F->cam.h, st));
-  }
-  const bool timed = stats && stats->time_phases;
+  const int K = (int)F->plans.size();
+  const int G = (int)F->h_group_nodes.size();
+  int *counts = stats ? stats->d_counts : nullptr;
+  unsigned char *visible = stats ? stats->d_visible : nullptr;
+  if (counts) OCR_CUDA(cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)F->total_pix, st));
+  if (visible) OCR_CUDA(cudaMemsetAsync(visible, 0, (size_t)F->N, st));
+  const bool timed = stats && stats->time_phases && K == 1;
   if (timed && !F->ev[0])
     for (cudaEvent_t &e : F->ev) OCR_CUDA(cudaEventCreate(&e));
   int64_t launches = 0;
-  OCR_CUDA(cudaMemsetAsync(F->d_stats, 0, kStats * sizeof(unsigned long long), st));
-  if (timed) OCR_CUDA(cudaEventRecord(F->ev[0], st));
-
-  // prune: leaf rectangles; internal rectangles bottom-up; slot layout
-  OCR_CUDA(launch_cull_leaves(T, F->cam, S, st));
-  ++launches;
-  for (int l = F->L - 1; l >= 0; --l) {
-    OCR_CUDA(launch_union_level(T, F->level_base[l], F->level_base[l] + F->level_count[l], F->cam,
-                                S, st));
-    launches += F->level_count[l] > 0;
-  }
-  OCR_CUDA(launch_area_scan(T, S, F->d_block_sums, F->block_sums_cap, F->d_group_slots,
-                            F->d_group_nodes, G, st));
-  launches += area_scan_blocks(F->M) > 0 ? 4 : 1;
-  OCR_CUDA(cudaMemcpyAsync(F->h_group_slots, F->d_group_slots, sizeof(long long) * G,
-                           cudaMemcpyDeviceToHost, st));
-  OCR_CUDA(cudaStreamSynchronize(st));
-  const long long total = F->h_group_slots[G - 1];
-  if (total > F->entries_cap) {
-    cudaFree(F->d_entries);
-    F->d_entries = nullptr;
-    F->bytes -= F->entries_cap * (int64_t)sizeof(float4);
-    F->entries_cap = 0;
-    const long long cap = total + total / 8 + 1024;
-    int rc = dev_alloc(&F->d_entries, (size_t)cap, F->bytes);
-    if (rc) return rc;
-    F->entries_cap = cap;
-  }
-  S.entries = F->d_entries;
-  const long long nchunks = (total + kChunk - 1) / kChunk + 1;
-  if (nchunks > F->chunk_cap) {
-    cudaFree(F->d_chunk_node);
-    F->d_chunk_node = nullptr;
-    F->bytes -= F->chunk_cap * (int64_t)sizeof(int);
-    F->chunk_cap = 0;
-    const long long cap = nchunks + nchunks / 8 + 64;
-    int rc = dev_alloc(&F->d_chunk_node, (size_t)cap, F->bytes);
-    if (rc) return rc;
-    F->chunk_cap = cap;
-  }
-  S.chunk_node = F->d_chunk_node;
-  OCR_CUDA(launch_chunk_map(T, S, st));
-  launches += F->M > 0;
-  if (timed) OCR_CUDA(cudaEventRecord(F->ev[1], st));
-
-  // group g covers level L - 1 - g.  Levels below the tile level hold no
-  // slots; the tile level runs the subtree pass, the levels above it the
-  // coarsening passes, deepest first.
   bool subtree_ran = false;
-  for (int g = 0; g + 1 < G; ++g) {
-    const int level = F->L - 1 - g;
-    const long long a = F->h_group_slots[g], b = F->h_group_slots[g + 1];
-    if (b <= a) continue;
-    if (level == F->lt) {
-      if (timed) OCR_CUDA(cudaEventRecord(F->ev[2], st));
-      OCR_CUDA(launch_subtree(T, Fd, F->cam, F->integ, S, F->h_group_nodes[g],
-                              F->h_group_nodes[g + 1], a, b, st));
-      if (timed) OCR_CUDA(cudaEventRecord(F->ev[3], st));
-      subtree_ran = true;
-    } else
-      OCR_CUDA(launch_coarsen(T, Fd, F->cam, F->integ, S, F->h_group_nodes[g],
-                              F->h_group_nodes[g + 1], a, b, nullptr, st));
-    ++launches;
+  OCR_CUDA(cudaMemsetAsync(F->d_stats, 0, kStats * sizeof(unsigned long long), st));
+  float4 *rgba = reinterpret_cast<float4 *>(d_rgba);
+  if (K == 1) {
+    if (timed) OCR_CUDA(cudaEventRecord(F->ev[0], st));
+    int rc = enqueue_camera(F, F->plans[0], rgba, counts, visible, st, timed, subtree_ran,
+                            launches);
+    if (rc) return rc;
+    if (timed) OCR_CUDA(cudaEventRecord(F->ev[4], st));
+  } else {
+    // fan the cameras out over the internal streams and join them back
+    OCR_CUDA(cudaEventRecord(F->fork, st));
+    for (int q = 0; q < kRenderStreams; ++q) OCR_CUDA(cudaStreamWaitEvent(F->sub[q], F->fork, 0));
+    for (int k = 0; k < K; ++k) {
+      CamPlan &P = F->plans[k];
+      int rc = enqueue_camera(F, P, rgba + P.pix_off, counts ? counts + P.pix_off : nullptr,
+                              visible, F->sub[k % kRenderStreams], false, subtree_ran, launches);
+      if (rc) return rc;
+    }
+    for (int q = 0; q < kRenderStreams; ++q) {
+      OCR_CUDA(cudaEventRecord(F->join[q], F->sub[q]));
+      OCR_CUDA(cudaStreamWaitEvent(st, F->join[q], 0));
+    }
   }
-  // the super-root pass writes every pixel
-  OCR_CUDA(launch_coarsen(T, Fd, F->cam, F->integ, S, F->M, F->M, 0,
-                          (long long)F->cam.w * F->cam.h, reinterpret_cast<float4 *>(d_rgba), st));
-  ++launches;
-  if (timed) OCR_CUDA(cudaEventRecord(F->ev[4], st));
 
   if (stats) {
     stats->launches = launches;
     if (stats->d_rects)
-      OCR_CUDA(cudaMemcpyAsync(stats->d_rects, F->d_rect, sizeof(int4) * (size_t)F->N,
+      OCR_CUDA(cudaMemcpyAsync(stats->d_rects, F->plans[0].d_rect, sizeof(int4) * (size_t)F->N,
                                cudaMemcpyDeviceToDevice, st));
     if (timed) {
       OCR_CUDA(cudaEventSynchronize(F->ev[4]));
@@ -559,11 +633,13 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
   if (F->integ.method != OCR_RK4 && F->integ.method != OCR_DOPRI5) return OCR_ERR_UNSUPPORTED;
   if ((uintptr_t)d_dL_drgba & 15) return OCR_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
-  const long long npix = (long long)F->cam.w * F->cam.h;
+  CamPlan &P0 = F->plans[0];
+  const Cam &cam = P0.cam;
+  const long long npix = P0.npix;
   Topo T{F->d_geo, F->d_child, F->d_leaves, F->N, F->M, F->L, F->lt};
   Field Fd{F->d_nodal, reinterpret_cast<const float4 *>(F->d_tf), F->s_min,
            7.f / (F->s_max - F->s_min)};
-  Scratch S{F->d_rect, F->d_off, F->d_entries, F->d_stats, nullptr, nullptr, nullptr};
+  Scratch S{P0.d_rect, P0.d_off, nullptr, F->d_stats, nullptr, nullptr, nullptr};
   if (!F->nsm) {
     int dev = 0;
     OCR_CUDA(cudaGetDevice(&dev));
@@ -590,8 +666,8 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
   OCR_CUDA(cudaMemsetAsync(F->d_stats, 0, kStats * sizeof(unsigned long long), st));
 
   // leaf rectangles, then the (leaf, pixel) pair space in Morton order
-  OCR_CUDA(launch_cull_leaves(T, F->cam, S, st));
-  OCR_CUDA(bwd_leaf_scan(T, F->d_rect, F->d_bsums, F->bsums_cap, F->d_leaf_off, st));
+  OCR_CUDA(launch_cull_leaves(T, cam, S, st));
+  OCR_CUDA(bwd_leaf_scan(T, P0.d_rect, F->d_bsums, F->bsums_cap, F->d_leaf_off, st));
   long long *h = F->h_group_slots + F->h_group_nodes.size();  // pinned scratch
   OCR_CUDA(cudaMemcpyAsync(h, F->d_leaf_off + F->N, sizeof(long long), cudaMemcpyDeviceToHost, st));
   OCR_CUDA(cudaStreamSynchronize(st));
@@ -602,7 +678,7 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
 
   // hits per ray, their offsets, then the hit lists (leaf, mirrored Morton key)
   OCR_CUDA(cudaMemsetAsync(F->d_rcount, 0, sizeof(int) * (size_t)npix, st));
-  OCR_CUDA(bwd_pair_hits(false, T, F->cam, F->d_rect, F->d_leaf_off, F->d_pchunk, npairs, dL,
+  OCR_CUDA(bwd_pair_hits(false, T, cam, P0.d_rect, F->d_leaf_off, F->d_pchunk, npairs, dL,
                          F->d_rcount, nullptr, nullptr, F->d_mkey, F->fx, nullptr, nullptr, st));
   OCR_CUDA(bwd_count_scan(F->d_rcount, npix, F->d_bsums, F->bsums_cap, F->d_ray_off, st));
   OCR_CUDA(cudaMemcpyAsync(h, F->d_ray_off + npix, sizeof(long long), cudaMemcpyDeviceToHost, st));
@@ -618,13 +694,13 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
     }
   }
   OCR_CUDA(cudaMemsetAsync(F->d_rcursor, 0, sizeof(int) * (size_t)npix, st));
-  OCR_CUDA(bwd_pair_hits(true, T, F->cam, F->d_rect, F->d_leaf_off, F->d_pchunk, npairs, dL,
+  OCR_CUDA(bwd_pair_hits(true, T, cam, P0.d_rect, F->d_leaf_off, F->d_pchunk, npairs, dL,
                          nullptr, F->d_ray_off, F->d_rcursor, F->d_mkey, F->fx, F->d_hkey,
                          F->d_hleaf, st));
 
   // one warp per ray: order, recompute, prefix/suffix, adjoint
   OCR_CUDA(cudaMemsetAsync(F->d_err, 0, sizeof(unsigned long long), st));
-  OCR_CUDA(bwd_rays(T, Fd, F->cam, F->integ, dL, F->d_ray_off, F->d_hkey, F->d_hleaf,
+  OCR_CUDA(bwd_rays(T, Fd, cam, F->integ, dL, F->d_ray_off, F->d_hkey, F->d_hleaf,
                     d_grad_nodal, d_grad_tf, F->d_err, F->nsm, st));
   OCR_CUDA(cudaMemcpyAsync(h, F->d_err, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
   OCR_CUDA(cudaStreamSynchronize(st));

@@ -35,7 +35,7 @@ __global__ void cull_leaves_kernel(Topo T, Cam c, Scratch S) {
       const int4 r = box_rect(c, node_lo(g, scale), ldexpf(1.f, -g.w));
       S.rect[k] = r;
       vis = r.x <= r.y;
-      if (S.visible) S.visible[k] = (unsigned char)vis;
+      if (S.visible && vis) S.visible[k] = 1;  // zeroed by the host; OR over cameras
     }
     nvis += __popc(__ballot_sync(0xffffffffu, vis));
   }

@@ -34,7 +34,7 @@ __all__ = [
     "SplitMix64", "GaussianField", "Forest", "TransferFunction", "Camera",
     "gaussian_field", "uniform_cube_forest", "adaptive_cube_forest",
     "transfer_function", "ortho_camera_c1", "perspective_camera", "morton_keys",
-    "preset_c1", "preset_c2", "preset_small",
+    "preset_c1", "preset_c2", "preset_c4", "preset_small", "batch_cameras",
 ]
 
 _M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
@@ -365,6 +365,22 @@ def preset_c2(w: int = 1920, h: int = 1080, theta: float = C2_THETA, max_level: 
     cam = perspective_camera(7, w, h)
     integ = {"method": "dopri5", "tol": 1e-6, "c_rk": 0.5, "max_depth": 16}
     return forest, tf, cam, integ
+
+
+def batch_cameras(n: int = 64, seed: int = 7, lo: int = 256, ratio: float = 8.0):
+    """n square perspective cameras with sides round(lo * ratio**u), u ~ U[0, 1]
+    (log-uniform sizes), each at its own seeded position."""
+    rng = SplitMix64(seed)
+    u = rng.uniform(n)
+    return [perspective_camera(seed * 1000 + k, int(round(lo * ratio ** u[k])),
+                               int(round(lo * ratio ** u[k]))) for k in range(n)]
+
+
+def preset_c4(n: int = 64):
+    """The C2 forest, field and transfer function seen by n cameras of
+    log-uniform sizes 256^2 .. 2048^2."""
+    forest, tf, _, integ = preset_c2()
+    return forest, tf, batch_cameras(n), integ
 
 
 def preset_small(kind: str = "adaptive", seed: int = 1809, w: int = 48, h: int = 40,

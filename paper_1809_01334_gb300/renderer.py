@@ -63,6 +63,37 @@ class Renderer:
         capi.set_camera(self.h, cam.o, cam.v, cam.t, cam.u, cam.ell, cam.near, cam.far, cam.w,
                         cam.h, cam.ortho)
         self.cam = cam
+        self.cams = [cam]
+
+    def set_cameras(self, cams):
+        """Several cameras rendered together by render_batch (one call, no host
+        synchronisation; capturable in a CUDA graph)."""
+        capi.set_cameras(self.h, cams)
+        self.cam = cams[0]
+        self.cams = list(cams)
+
+    def batch_pixels(self) -> int:
+        return sum(c.w * c.h for c in self.cams)
+
+    def render_batch(self, out: torch.Tensor | None = None, stream=None, with_index=False):
+        """Render every camera into one flat buffer [sum(w*h), 4]; returns it,
+        the per-camera [h, w, 4] views and the stats."""
+        n = self.batch_pixels()
+        if out is None:
+            out = torch.empty((n, 4), dtype=torch.float32, device=self.device)
+        extra = {}
+        if with_index:
+            extra["counts"] = torch.empty(n, dtype=torch.int32, device=self.device)
+            extra["visible"] = torch.empty(self.forest.nleaves, dtype=torch.uint8,
+                                           device=self.device)
+        st = capi.render(self.h, out, _stream_ptr(stream), d_counts=extra.get("counts"),
+                         d_visible=extra.get("visible"), fill_counters=with_index)
+        st.update(extra)
+        views, at = [], 0
+        for c in self.cams:
+            views.append(out[at:at + c.w * c.h].view(c.h, c.w, 4))
+            at += c.w * c.h
+        return out, views, st
 
     def render(self, out: torch.Tensor | None = None, stream=None, with_index=False,
                fill_counters=False, time_phases=False):
