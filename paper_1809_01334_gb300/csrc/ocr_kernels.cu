@@ -202,7 +202,7 @@ __device__ __forceinline__ unsigned spread3_9(unsigned v) {  // 3 bits -> positi
 constexpr int kCand = 128;     // candidate leaves per round of phase A
 constexpr int kWarpBatch = 64; // hits per warp batch of phase C
 
-__global__ void __launch_bounds__(kChunk, 6)
+__global__ void __launch_bounds__(kChunk, 8)
     subtree_kernel(Topo T, Field Fd, Cam c, Integ I, Scratch S, int nb, int ne, long long s0,
                    long long s1) {
   constexpr int NT = kChunk, NW = NT / 32;
@@ -218,7 +218,6 @@ __global__ void __launch_bounds__(kChunk, 6)
   __shared__ unsigned s_list[kMaxSubtreeHits][NT];       // (mirrored key << 22) | leaf - base
   __shared__ float4 s_res[NW][kWarpBatch];
   __shared__ int s_wcnt[NW], s_nn, s_leaf_base;
-  __shared__ unsigned long long s_acc[4];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid < 8) {
     const float4 v = Fd.tf[tid];
@@ -226,7 +225,6 @@ __global__ void __launch_bounds__(kChunk, 6)
     s_tfv[tid] = v;
     s_tfs[tid] = make_float4(w.x - v.x, w.y - v.y, w.z - v.z, w.w - v.w);
   }
-  if (tid < 4) s_acc[tid] = 0ull;
 
   // slot -> node, pixel, ray; rays that miss the node's box skip all leaves
   const long long chunk = s0 / NT + blockIdx.x, cs = chunk * NT;
@@ -404,16 +402,15 @@ __global__ void __launch_bounds__(kChunk, 6)
     if (nhit > (unsigned)kMaxSubtreeHits) atomicAdd(S.stats + kStatErrors, 1ull);
     if (nhit && S.counts) atomicAdd(S.counts + (size_t)j * c.w + i, (int)nhit);
   }
+  // counters: one atomic per warp and counter, no CTA-wide barrier at the end
   unsigned long long v[4] = {nhit, (unsigned long long)steps, ntest, active ? 1ull : 0ull};
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     unsigned long long x = v[q];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if (lane == 0 && x) atomicAdd(&s_acc[q], x);
+    if (lane == 0 && x) atomicAdd(S.stats + q, x);
   }
-  __syncthreads();
-  if (tid < 4 && s_acc[tid]) atomicAdd(S.stats + tid, s_acc[tid]);
 }
 
 template <bool FINAL>
