@@ -394,3 +394,181 @@ def preset_small(kind: str = "adaptive", seed: int = 1809, w: int = 48, h: int =
     tf = transfer_function(forest.nodal, 1334)
     cam = perspective_camera(cam_seed, w, h)
     return forest, tf, cam
+
+
+# --------------------------------------------------------------------------
+# Cubed-sphere shell: six trees, the equiangular map, degree-2 nodal data.
+# --------------------------------------------------------------------------
+SHELL_R0, SHELL_R1 = 0.55, 1.0
+
+# tree k: (face normal, first tangent, second tangent); reference coordinates
+# (xi, eta, zeta) map to r(zeta) * normalize(n + tan(pi/4 (2 xi - 1)) e1 +
+# tan(pi/4 (2 eta - 1)) e2), r(zeta) = R0 + (R1 - R0) zeta
+SHELL_FRAMES = np.array([
+    [[1, 0, 0], [0, 1, 0], [0, 0, 1]],
+    [[-1, 0, 0], [0, 0, 1], [0, 1, 0]],
+    [[0, 1, 0], [0, 0, 1], [1, 0, 0]],
+    [[0, -1, 0], [1, 0, 0], [0, 0, 1]],
+    [[0, 0, 1], [1, 0, 0], [0, 1, 0]],
+    [[0, 0, -1], [0, 1, 0], [1, 0, 0]]], dtype=np.float64)
+
+
+def shell_map(tree, xi, eta, zeta):
+    """Equiangular cubed-sphere map of tree reference coordinates to space."""
+    fr = SHELL_FRAMES[np.asarray(tree)]
+    a = np.tan(np.pi / 4 * (2 * np.asarray(xi) - 1))[..., None]
+    b = np.tan(np.pi / 4 * (2 * np.asarray(eta) - 1))[..., None]
+    d = fr[..., 0, :] + a * fr[..., 1, :] + b * fr[..., 2, :]
+    d /= np.linalg.norm(d, axis=-1, keepdims=True)
+    return (SHELL_R0 + (SHELL_R1 - SHELL_R0) * np.asarray(zeta))[..., None] * d
+
+
+@dataclass
+class ShellNoise:
+    """f(x) = sum_{l<=lmax} sum_m c_lm Y_lm(x/|x|) (1 + sin(2 pi l zeta)/2),
+    c_lm ~ N(0, 1/(l+1)), real spherical harmonics, zeta the normalised radius."""
+    coef: dict
+    lmax: int
+
+    def direction_terms(self, d):
+        """A_l(d) = sum_m c_lm Y_lm(d) for l = 0..lmax; d unit vectors [..., 3]."""
+        ct = np.clip(d[..., 2], -1.0, 1.0)
+        st = np.sqrt(np.maximum(0.0, 1.0 - ct * ct))
+        phi = np.arctan2(d[..., 1], d[..., 0])
+        out = np.zeros((self.lmax + 1,) + ct.shape)
+        pmm = np.ones_like(ct)
+        for m in range(self.lmax + 1):
+            if m > 0:
+                pmm = pmm * (2 * m - 1) * st
+            pl2, pl1 = None, pmm
+            for l in range(m, self.lmax + 1):
+                if l == m:
+                    p = pmm
+                elif l == m + 1:
+                    p = ct * (2 * m + 1) * pmm
+                else:
+                    p = ((2 * l - 1) * ct * pl1 - (l + m - 1) * pl2) / (l - m)
+                if l > m:
+                    pl2, pl1 = pl1, p
+                k = math.sqrt((2 * l + 1) / (4 * math.pi) * math.factorial(l - m) /
+                              math.factorial(l + m))
+                if m == 0:
+                    out[l] += self.coef[(l, 0)] * k * p
+                else:
+                    out[l] += math.sqrt(2.0) * k * p * (self.coef[(l, m)] * np.cos(m * phi) +
+                                                        self.coef[(l, -m)] * np.sin(m * phi))
+        return out
+
+    @staticmethod
+    def radial_terms(zeta, lmax):
+        return np.stack([1.0 + 0.5 * np.sin(2 * np.pi * l * np.asarray(zeta))
+                         for l in range(lmax + 1)])
+
+    def value(self, pts):
+        pts = np.asarray(pts, dtype=np.float64)
+        r = np.linalg.norm(pts, axis=-1)
+        A = self.direction_terms(pts / r[..., None])
+        R = self.radial_terms((r - SHELL_R0) / (SHELL_R1 - SHELL_R0), self.lmax)
+        return (A * R).sum(axis=0)
+
+
+def shell_noise(seed: int = 1809, lmax: int = 8) -> ShellNoise:
+    rng = SplitMix64(seed)
+    coef = {}
+    for l in range(lmax + 1):
+        for m in range(-l, l + 1):
+            u1, u2 = rng.uniform(2)
+            g = math.sqrt(-2.0 * math.log(max(u1, 1e-300))) * math.cos(2 * math.pi * u2)
+            coef[(l, m)] = g / math.sqrt(l + 1.0)
+    return ShellNoise(coef, lmax)
+
+
+def shell_forest(noise: ShellNoise, min_level: int, max_level: int, theta: float) -> Forest:
+    """Six trees refined from min_level while the noise varies by more than
+    theta over a node (its 8 corners and centre), not balanced.  Nodal data:
+    27 values per leaf at the leaf's local nodes (a, b, c)/2, node index
+    a + 3 b + 9 c (the degree-2 Gauss-Lobatto nodes 0, 1/2, 1)."""
+    L = max_level
+    n2 = 1 << (L + 1)                      # the finest node grid: level L + 1
+    g = np.arange(n2 + 1) / n2
+    XI, ETA = np.meshgrid(g, g, indexing="ij")
+    A = np.empty((6, noise.lmax + 1, n2 + 1, n2 + 1))
+    for t in range(6):
+        d = shell_map(np.full(XI.shape, t), XI, ETA, np.zeros(XI.shape))
+        A[t] = noise.direction_terms(d / np.linalg.norm(d, axis=-1, keepdims=True))
+    R = ShellNoise.radial_terms(g, noise.lmax)  # [lmax + 1, n2 + 1]
+
+    ls = np.arange(noise.lmax + 1)[None, :]
+
+    def f_at(t, ix, iy, iz):  # f at points of the level-(L + 1) node grid
+        return (A[t[:, None], ls, ix[:, None], iy[:, None]] * R[:, iz].T).sum(axis=1)
+
+    levs, anchors, trees = [], [], []
+    for t in range(6):
+        refined = [np.zeros((1 << l,) * 3, bool) for l in range(L)]
+        for l in range(min_level):
+            refined[l][...] = True
+        for l in range(min_level, L):
+            n1 = 1 << l
+            exists = np.ones((n1,) * 3, bool) if l == 0 else _upsample(refined[l - 1])
+            idx = np.argwhere(exists)
+            if idx.shape[0] == 0:
+                continue
+            step = 1 << (L + 1 - l)  # node-grid units per level-l cell
+            vals = []
+            for c in range(9):
+                off = np.array([1, 1, 1]) if c == 8 else np.array([c & 1, (c >> 1) & 1, (c >> 2) & 1]) * 2
+                p = idx * step + off * (step // 2)
+                vals.append(f_at(np.full(idx.shape[0], t), p[:, 0], p[:, 1], p[:, 2]))
+            vals = np.stack(vals)
+            ref = (vals.max(axis=0) - vals.min(axis=0)) > theta
+            refined[l][tuple(idx[ref].T)] = True
+        for l in range(0, L + 1):
+            n1 = 1 << l
+            exists = np.ones((n1,) * 3, bool) if l == 0 else _upsample(refined[l - 1])
+            leaf = exists & ~refined[l] if l < L else exists
+            idx = np.argwhere(leaf)
+            if idx.shape[0]:
+                anchors.append((idx << (L - l)).astype(np.int32))
+                levs.append(np.full(idx.shape[0], l, dtype=np.uint8))
+                trees.append(np.full(idx.shape[0], t, dtype=np.int32))
+    lev = np.concatenate(levs)
+    anchor = np.concatenate(anchors)
+    tree = np.concatenate(trees)
+    lev, anchor, tree = _sort_forest(lev, anchor, tree)
+    nodal = np.empty((lev.shape[0], 27), dtype=np.float32)
+    step = (1 << (L + 1 - lev.astype(np.int64))) // 2  # node-grid units per half leaf
+    for c in range(27):
+        a, b, cc = c % 3, (c // 3) % 3, c // 9
+        ix = 2 * anchor[:, 0].astype(np.int64) + a * step
+        iy = 2 * anchor[:, 1].astype(np.int64) + b * step
+        iz = 2 * anchor[:, 2].astype(np.int64) + cc * step
+        nodal[:, c] = f_at(tree, ix, iy, iz).astype(np.float32)
+    return Forest("shell", L, lev, anchor, tree, nodal,
+                  {"kind": "shell", "min_level": min_level, "max_level": max_level,
+                   "theta": theta, "r0": SHELL_R0, "r1": SHELL_R1,
+                   "frames": SHELL_FRAMES.tolist()})
+
+
+C3_THETA = 0.4  # calibrated once (bisection) for the 4..7 shell
+
+
+def preset_c3(w: int = 2048, h: int = 2048, theta: float = C3_THETA, min_level: int = 4,
+              max_level: int = 7):
+    """Cubed-sphere shell, levels 4..7, degree-2 data from SH noise (degree 8),
+    perspective 45 deg at 2048^2, DOPRI5 tol 1e-5."""
+    noise = shell_noise(1809, 8)
+    forest = shell_forest(noise, min_level, max_level, theta)
+    tf = transfer_function(forest.nodal, 1334)
+    cam = perspective_camera(7, w, h, target=(0.0, 0.0, 0.0))
+    integ = {"method": "dopri5", "tol": 1e-5, "c_rk": 0.5, "max_depth": 16}
+    return forest, tf, cam, integ
+
+
+def preset_shell_small(w: int = 40, h: int = 32, min_level: int = 1, max_level: int = 3,
+                       theta: float = 2.0, cam_seed: int = 7):
+    noise = shell_noise(1809, 8)
+    forest = shell_forest(noise, min_level, max_level, theta)
+    tf = transfer_function(forest.nodal, 1334)
+    cam = perspective_camera(cam_seed, w, h, dist=(2.2, 2.6), target=(0.0, 0.0, 0.0))
+    return forest, tf, cam
