@@ -42,7 +42,9 @@ class Forest_(C.Structure):
     _fields_ = [("nleaves", C.c_int), ("max_level", C.c_int),
                 ("anchor", C.POINTER(C.c_int32)), ("level", C.POINTER(C.c_uint8)),
                 ("nodal", C.POINTER(C.c_float)), ("tf", C.POINTER(C.c_float)),
-                ("s_min", C.c_double), ("s_max", C.c_double)]
+                ("s_min", C.c_double), ("s_max", C.c_double), ("geometry", C.c_int),
+                ("tree", C.POINTER(C.c_int32)), ("frames", C.c_double * 9 * 6),
+                ("r0", C.c_double), ("r1", C.c_double)]
 
 
 class Camera_(C.Structure):
@@ -75,6 +77,13 @@ def lib():
         _lib.orc_leaf_rect.restype = C.c_int
         _lib.orc_ray_leaf.argtypes = [P(Forest_), C.c_int, d, d, C.c_double, C.c_double, d, d]
         _lib.orc_ray_leaf.restype = C.c_int
+        _lib.orc_ray_leaf_tie.argtypes = [P(Forest_), C.c_int, d, d, C.c_double, C.c_double, d,
+                                          d, C.c_double, P(C.c_int)]
+        _lib.orc_ray_leaf_tie.restype = C.c_int
+        _lib.orc_triquadratic.argtypes = [P(C.c_float), C.c_double, C.c_double, C.c_double]
+        _lib.orc_triquadratic.restype = C.c_double
+        _lib.orc_shell_map.argtypes = [P(Forest_), C.c_int, d, d]
+        _lib.orc_shell_inverse.argtypes = [P(Forest_), C.c_int, d, d]
         _lib.orc_segment_ab.argtypes = [P(Forest_), P(Integrator_), C.c_int, d, d, C.c_double,
                                         C.c_double, d, P(C.c_int64)]
         _lib.orc_cull.argtypes = [P(Forest_), P(Camera_), P(C.c_int32), P(C.c_uint8),
@@ -96,15 +105,24 @@ class OracleForest:
     """Keeps the numpy arrays alive while the C struct points into them."""
 
     def __init__(self, forest, tf):
-        if forest.geometry != "cube":
-            raise ValueError("oracle forest: only the unit-cube geometry is implemented")
+        if forest.geometry not in ("cube", "shell"):
+            raise ValueError(f"oracle forest: unknown geometry {forest.geometry!r}")
         self.anchor = np.ascontiguousarray(forest.anchor, dtype=np.int32)
         self.level = np.ascontiguousarray(forest.level, dtype=np.uint8)
         self.nodal = np.ascontiguousarray(forest.nodal, dtype=np.float32)
+        self.tree = np.ascontiguousarray(forest.tree, dtype=np.int32)
         self.tf = np.ascontiguousarray(tf.knots, dtype=np.float32).reshape(-1)
         self.s = Forest_(forest.nleaves, forest.max_level, _ptr(self.anchor, C.c_int32),
                          _ptr(self.level, C.c_uint8), _ptr(self.nodal, C.c_float),
                          _ptr(self.tf, C.c_float), float(tf.s_min), float(tf.s_max))
+        self.s.tree = _ptr(self.tree, C.c_int32)
+        if forest.geometry == "shell":
+            self.s.geometry = 1
+            fr = np.asarray(forest.meta["frames"], dtype=np.float64).reshape(-1)
+            for k in range(54):
+                self.s.frames[k // 9][k % 9] = fr[k]
+            self.s.r0, self.s.r1 = float(forest.meta["r0"]), float(forest.meta["r1"])
+        self.stride = 27 if forest.geometry == "shell" else 8
 
 
 def camera_struct(cam) -> Camera_:
@@ -177,6 +195,25 @@ def trilinear(nodal8, u, v, w):
     return lib().orc_trilinear(_ptr(a, C.c_float), float(u), float(v), float(w))
 
 
+def triquadratic(nodal27, u, v, w):
+    a = np.ascontiguousarray(nodal27, dtype=np.float32)
+    return lib().orc_triquadratic(_ptr(a, C.c_float), float(u), float(v), float(w))
+
+
+def shell_map(of: OracleForest, tree, ref):
+    x = np.zeros(3)
+    lib().orc_shell_map(C.byref(of.s), int(tree), _ptr(np.ascontiguousarray(ref, float),
+                                                       C.c_double), _ptr(x, C.c_double))
+    return x
+
+
+def shell_inverse(of: OracleForest, tree, x):
+    ref = np.zeros(3)
+    lib().orc_shell_inverse(C.byref(of.s), int(tree), _ptr(np.ascontiguousarray(x, float),
+                                                           C.c_double), _ptr(ref, C.c_double))
+    return ref
+
+
 def pixel_ray(cam, i, j):
     org, d, lims = np.zeros(3), np.zeros(3), np.zeros(2)
     cs = camera_struct(cam)
@@ -186,11 +223,24 @@ def pixel_ray(cam, i, j):
 
 
 def ray_leaf(of: OracleForest, leaf, org, d, amin, amax):
-    a = np.zeros(2)
+    """Cube leaf: (hit, alpha_in, alpha_out) of the slab interval."""
+    a, b = np.zeros(2), np.zeros(2)
     hit = lib().orc_ray_leaf(C.byref(of.s), int(leaf), _ptr(np.asarray(org, float), C.c_double),
                              _ptr(np.asarray(d, float), C.c_double), float(amin), float(amax),
-                             _ptr(a[0:1], C.c_double), _ptr(a[1:2], C.c_double))
-    return bool(hit), float(a[0]), float(a[1])
+                             _ptr(a, C.c_double), _ptr(b, C.c_double))
+    return bool(hit), float(a[0]), float(b[0])
+
+
+def ray_leaf_intervals(of: OracleForest, leaf, org, d, amin, amax, band_rel: float = 0.0):
+    """All intervals of the ray inside the leaf (at most two), nearest first,
+    and the tie flag."""
+    a, b = np.zeros(2), np.zeros(2)
+    tie = C.c_int(0)
+    n = lib().orc_ray_leaf_tie(C.byref(of.s), int(leaf), _ptr(np.asarray(org, float), C.c_double),
+                               _ptr(np.asarray(d, float), C.c_double), float(amin), float(amax),
+                               _ptr(a, C.c_double), _ptr(b, C.c_double), float(band_rel),
+                               C.byref(tie))
+    return [(float(a[k]), float(b[k])) for k in range(n)], bool(tie.value)
 
 
 def segment_ab(of: OracleForest, integ: dict, leaf, org, d, a_in, a_out):
@@ -202,6 +252,18 @@ def segment_ab(of: OracleForest, integ: dict, leaf, org, d, a_in, a_out):
                          _ptr(np.ascontiguousarray(d, float), C.c_double), float(a_in),
                          float(a_out), _ptr(out, C.c_double), C.byref(st))
     return out, int(st.value)
+
+
+def leaf_rect(of: OracleForest, cam, leaf, band_px: float = 0.0):
+    """(visible, rect {i0,i1,j0,j1}, projected extents {i_min,i_max,j_min,j_max},
+    tie flag) of one leaf."""
+    cs = camera_struct(cam)
+    rect = np.zeros(4, dtype=np.int32)
+    pext = np.zeros(4)
+    unc = C.c_int(0)
+    vis = lib().orc_leaf_rect(C.byref(of.s), C.byref(cs), int(leaf), _ptr(rect, C.c_int32),
+                              _ptr(pext, C.c_double), float(band_px), C.byref(unc))
+    return bool(vis), rect, pext, bool(unc.value)
 
 
 def cull(forest, tf, cam, band_px: float = 4e-3):
@@ -244,13 +306,13 @@ def render(forest, tf, cam, integ: dict, rows=None, bg=(0.0, 0.0, 0.0), nthreads
 
 
 def render_grad(forest, tf, cam, integ: dict, dL_drgba, bg=(0.0, 0.0, 0.0), nthreads: int = 0):
-    """FP64 gradient of L with respect to nodal values [N, 8] and knots [8, 4],
-    given dL/d(rgba) [h, w, 4]."""
+    """FP64 gradient of L with respect to nodal values [N, 8] (cube) or
+    [N, 27] (shell) and knots [8, 4], given dL/d(rgba) [h, w, 4]."""
     of = OracleForest(forest, tf)
     cs = camera_struct(cam)
     ist = integrator_struct(integ, bg)
     gb = np.ascontiguousarray(dL_drgba, dtype=np.float64).reshape(cam.h, cam.w, 4)
-    gn = np.zeros((forest.nleaves, 8))
+    gn = np.zeros((forest.nleaves, of.stride))
     gt = np.zeros((8, 4))
     rc = lib().orc_render_grad(C.byref(of.s), C.byref(cs), C.byref(ist), _ptr(gb, C.c_double),
                                _ptr(gn, C.c_double), _ptr(gt, C.c_double), int(nthreads))

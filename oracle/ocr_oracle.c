@@ -86,10 +86,107 @@ double orc_trilinear(const float *nd, double u, double v, double w) {
   return s;
 }
 
+/* The leaf's box in the reference coordinates of its tree (for the cube, the
+ * identity map, in space). */
 static void leaf_box(const orc_forest *F, int leaf, double *lo, double *h) {
   double scale = ldexp(1.0, -F->max_level);
   *h = ldexp(1.0, -(int)F->level[leaf]);
   for (int a = 0; a < 3; ++a) lo[a] = F->anchor[3 * leaf + a] * scale;
+}
+
+static int nodal_stride(const orc_forest *F) { return F->geometry == 1 ? 27 : 8; }
+
+/* Degree-2 Lagrange basis on {0, 1/2, 1} at t. */
+static void quad_basis(double t, double *l) {
+  l[0] = 2.0 * (t - 0.5) * (t - 1.0);
+  l[1] = -4.0 * t * (t - 1.0);
+  l[2] = 2.0 * t * (t - 0.5);
+}
+
+double orc_triquadratic(const float *nd, double u, double v, double w) {
+  double lu[3], lv[3], lw[3], s = 0.0;
+  quad_basis(u, lu);
+  quad_basis(v, lv);
+  quad_basis(w, lw);
+  for (int c = 0; c < 27; ++c) s += (double)nd[c] * lu[c % 3] * lv[(c / 3) % 3] * lw[c / 9];
+  return s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cubed-sphere shell: the equiangular map (the paper's tree-to-space map of  */
+/* Sec. 2.1 taken as the six-tree cubed sphere)                               */
+/* ------------------------------------------------------------------------ */
+
+static const double ORC_PI = 3.14159265358979323846;
+
+static double dot3(const double *a, const double *b) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+/* tan(pi/4 (2 xi - 1)): the tangent-plane coordinate of reference xi */
+static double eq_tan(double xi) { return tan(0.25 * ORC_PI * (2.0 * xi - 1.0)); }
+
+static double shell_radius(const orc_forest *F, double zeta) {
+  return F->r0 + (F->r1 - F->r0) * zeta;
+}
+
+/* unit direction of reference (xi, eta) in tree k */
+static void shell_dir(const orc_forest *F, int k, double xi, double eta, double *d) {
+  double a = eq_tan(xi), b = eq_tan(eta);
+  for (int c = 0; c < 3; ++c) d[c] = F->frames[k][0][c] + a * F->frames[k][1][c] + b * F->frames[k][2][c];
+  double nn = sqrt(dot3(d, d));
+  for (int c = 0; c < 3; ++c) d[c] /= nn;
+}
+
+void orc_shell_map(const orc_forest *F, int tree, const double *ref, double *x) {
+  double d[3], r = shell_radius(F, ref[2]);
+  shell_dir(F, tree, ref[0], ref[1], d);
+  for (int c = 0; c < 3; ++c) x[c] = r * d[c];
+}
+
+/* xi = atan(x.e1 / x.n) 2/pi + 1/2, eta likewise with e2, zeta from |x| */
+void orc_shell_inverse(const orc_forest *F, int tree, const double *x, double *ref) {
+  double pn = dot3(x, F->frames[tree][0]);
+  ref[0] = atan2(dot3(x, F->frames[tree][1]), pn) * 2.0 / ORC_PI + 0.5;
+  ref[1] = atan2(dot3(x, F->frames[tree][2]), pn) * 2.0 / ORC_PI + 0.5;
+  ref[2] = (sqrt(dot3(x, x)) - F->r0) / (F->r1 - F->r0);
+}
+
+/* The 8 mapped corners of a leaf and a distance delta such that every point
+ * of the leaf lies within delta of their convex hull.  Cube: delta = 0.
+ * Shell: a point r d of the leaf has d = p / |p| with p a convex combination
+ * of the 4 unit corner directions d_i, and r p lies in the hull of the 8
+ * corners; |r d - r p| = r (1 - |p|) <= r_out (1 - min_i d_i . c) for any
+ * unit c, here c = normalize(sum_i d_i). */
+static void leaf_corners(const orc_forest *F, int leaf, double x[8][3], double *delta) {
+  double lo[3], h;
+  leaf_box(F, leaf, lo, &h);
+  *delta = 0.0;
+  if (F->geometry != 1) {
+    for (int c = 0; c < 8; ++c) {
+      x[c][0] = lo[0] + ((c & 1) ? h : 0.0);
+      x[c][1] = lo[1] + ((c & 2) ? h : 0.0);
+      x[c][2] = lo[2] + ((c & 4) ? h : 0.0);
+    }
+    return;
+  }
+  int k = F->tree[leaf];
+  double d[4][3], csum[3] = {0.0, 0.0, 0.0};
+  for (int c = 0; c < 4; ++c) {
+    shell_dir(F, k, lo[0] + ((c & 1) ? h : 0.0), lo[1] + ((c & 2) ? h : 0.0), d[c]);
+    for (int a = 0; a < 3; ++a) csum[a] += d[c][a];
+  }
+  double cn = sqrt(dot3(csum, csum)), cmin = 1.0;
+  for (int c = 0; c < 4; ++c) {
+    double cc = dot3(d[c], csum) / cn;
+    if (cc < cmin) cmin = cc;
+  }
+  double rin = shell_radius(F, lo[2]), rout = shell_radius(F, lo[2] + h);
+  for (int c = 0; c < 8; ++c) {
+    double r = (c & 4) ? rout : rin;
+    for (int a = 0; a < 3; ++a) x[c][a] = r * d[c & 3][a];
+  }
+  *delta = rout * (1.0 - cmin);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -145,17 +242,23 @@ static int axis_visible(double pmin, double pmax, int lim) {
  * visibility decision. */
 int orc_leaf_rect(const orc_forest *F, const orc_camera *C, int leaf, int32_t *rect,
                   double *pext, double band_px, int *vis_unc) {
-  double lo[3], h;
-  leaf_box(F, leaf, lo, &h);
+  double xc[8][3], delta;
+  leaf_corners(F, leaf, xc, &delta);
   double bmin[3] = {INFINITY, INFINITY, INFINITY}, bmax[3] = {-INFINITY, -INFINITY, -INFINITY};
   for (int c = 0; c < 8; ++c) {
-    double x[3] = {lo[0] + ((c & 1) ? h : 0.0), lo[1] + ((c & 2) ? h : 0.0),
-                   lo[2] + ((c & 4) ? h : 0.0)};
     double X[3];
-    camera_transform(C, x, X);
+    camera_transform(C, xc[c], X);
     for (int a = 0; a < 3; ++a) {
       if (X[a] < bmin[a]) bmin[a] = X[a];
       if (X[a] > bmax[a]) bmax[a] = X[a];
+    }
+  }
+  if (delta > 0.0) { /* widen by delta along each camera axis (t, u, v / n) */
+    double ext[3] = {delta * sqrt(dot3(C->t, C->t)), delta * sqrt(dot3(C->u, C->u)),
+                     delta * sqrt(dot3(C->v, C->v)) / C->near_};
+    for (int a = 0; a < 3; ++a) {
+      bmin[a] -= ext[a];
+      bmax[a] += ext[a];
     }
   }
   double zlo_lim = C->ortho ? 0.0 : C->near_;
@@ -208,8 +311,9 @@ int orc_leaf_rect(const orc_forest *F, const orc_camera *C, int leaf, int32_t *r
 }
 
 /* Slab test: the ray's parameter interval inside the axis-aligned leaf box. */
-int orc_ray_leaf(const orc_forest *F, int leaf, const double *org, const double *dir, double amin,
-                 double amax, double *a_in, double *a_out) {
+static int ray_cube_leaf(const orc_forest *F, int leaf, const double *org, const double *dir,
+                         double amin, double amax, double *a_in, double *a_out, double band_rel,
+                         int *tie) {
   double lo[3], h;
   leaf_box(F, leaf, lo, &h);
   double t0 = amin, t1 = amax;
@@ -217,8 +321,8 @@ int orc_ray_leaf(const orc_forest *F, int leaf, const double *org, const double 
     double b0 = lo[a], b1 = lo[a] + h;
     if (dir[a] == 0.0) {
       if (org[a] < b0 || org[a] > b1) { /* parallel to the slab and outside it */
-        *a_in = INFINITY;
-        *a_out = -INFINITY;
+        a_in[0] = INFINITY;
+        a_out[0] = -INFINITY;
         return 0;
       }
       continue;
@@ -228,9 +332,88 @@ int orc_ray_leaf(const orc_forest *F, int leaf, const double *org, const double 
     if (s0 > t0) t0 = s0;
     if (s1 < t1) t1 = s1;
   }
-  *a_in = t0;
-  *a_out = t1;
+  a_in[0] = t0;
+  a_out[0] = t1;
+  if (tie && isfinite(t0) && isfinite(t1)) {
+    double scale = fabs(t1) > fabs(t0) ? fabs(t1) : fabs(t0);
+    if (fabs(t1 - t0) <= band_rel * scale) *tie = 1;
+  }
   return t1 > t0;
+}
+
+/* Shell leaf: its angular extent is the cone of the four half-spaces
+ * x . (e1 - tan0 n) >= 0, x . (tan1 n - e1) >= 0 (and the same with e2), whose
+ * boundary planes pass through the origin; its radial extent is the shell
+ * R_in <= |x| <= R_out.  The ray meets the cone in one interval, the outer
+ * ball in one interval, and leaves out the inner ball's interval: at most two
+ * pieces.  The sphere crossings are alpha = -b +- sqrt((R^2 - |p|^2) / |r|^2)
+ * with b = (o . r) / |r|^2 and p = o - b r the ray's point nearest the centre. */
+static int ray_shell_leaf(const orc_forest *F, int leaf, const double *org, const double *dir,
+                          double amin, double amax, double *a_in, double *a_out, double band_rel,
+                          int *tie) {
+  double lo[3], h;
+  leaf_box(F, leaf, lo, &h);
+  const double(*fr)[3] = F->frames[F->tree[leaf]];
+  double t0 = amin, t1 = amax;
+  for (int s = 0; s < 4; ++s) {
+    const double *e = fr[1 + s / 2];
+    double tn = eq_tan(lo[s / 2] + ((s & 1) ? h : 0.0)), sg = (s & 1) ? -1.0 : 1.0, m[3];
+    for (int c = 0; c < 3; ++c) m[c] = sg * (e[c] - tn * fr[0][c]);
+    double g0 = dot3(org, m), g1 = dot3(dir, m);
+    if (g1 == 0.0) {
+      if (g0 < 0.0) return 0;
+      continue;
+    }
+    double a = -g0 / g1;
+    if (g1 > 0.0) {
+      if (a > t0) t0 = a;
+    } else if (a < t1) {
+      t1 = a;
+    }
+  }
+  double rr = dot3(dir, dir), b = dot3(org, dir) / rr, p[3];
+  for (int c = 0; c < 3; ++c) p[c] = org[c] - b * dir[c];
+  double pp = dot3(p, p);
+  double rin = shell_radius(F, lo[2]), rout = shell_radius(F, lo[2] + h);
+  double hout = rout * rout - pp, hin = rin * rin - pp;
+  if (tie && (fabs(hout) <= band_rel * rout * rout || fabs(hin) <= band_rel * rin * rin)) *tie = 1;
+  if (!(hout > 0.0)) return 0;
+  double so = sqrt(hout / rr);
+  if (-b - so > t0) t0 = -b - so;
+  if (-b + so < t1) t1 = -b + so;
+  double lo_p[2] = {t0, t0}, hi_p[2] = {t1, t1};
+  int npieces = 1;
+  if (hin > 0.0) {
+    double si = sqrt(hin / rr);
+    if (-b - si < hi_p[0]) hi_p[0] = -b - si;
+    if (-b + si > lo_p[1]) lo_p[1] = -b + si;
+    npieces = 2;
+  }
+  int n = 0;
+  for (int k = 0; k < npieces; ++k) {
+    if (tie && isfinite(lo_p[k]) && isfinite(hi_p[k])) {
+      double scale = fabs(hi_p[k]) > fabs(lo_p[k]) ? fabs(hi_p[k]) : fabs(lo_p[k]);
+      if (fabs(hi_p[k] - lo_p[k]) <= band_rel * scale) *tie = 1;
+    }
+    if (hi_p[k] > lo_p[k]) {
+      a_in[n] = lo_p[k];
+      a_out[n] = hi_p[k];
+      ++n;
+    }
+  }
+  return n;
+}
+
+int orc_ray_leaf_tie(const orc_forest *F, int leaf, const double *org, const double *dir,
+                     double amin, double amax, double *a_in, double *a_out, double band_rel,
+                     int *tie) {
+  if (F->geometry == 1) return ray_shell_leaf(F, leaf, org, dir, amin, amax, a_in, a_out, band_rel, tie);
+  return ray_cube_leaf(F, leaf, org, dir, amin, amax, a_in, a_out, band_rel, tie);
+}
+
+int orc_ray_leaf(const orc_forest *F, int leaf, const double *org, const double *dir, double amin,
+                 double amax, double *a_in, double *a_out) {
+  return orc_ray_leaf_tie(F, leaf, org, dir, amin, amax, a_in, a_out, 0.0, NULL);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -240,18 +423,47 @@ int orc_ray_leaf(const orc_forest *F, int leaf, const double *org, const double 
 typedef struct {
   const orc_forest *F;
   const float *nodal;
+  int tree;
   double lo[3], h;
   double org[3], dir[3];
   double a_out, rlen; /* x runs from the far end: alpha(x) = a_out - x / |r| */
 } seg_ctx;
 
+/* Local coordinates in [0, 1]^3 of the leaf at distance x from the far end of
+ * the segment (the shell goes through the inverse map). */
+static void local_coords(const seg_ctx *S, double x, double *u) {
+  double alpha = S->a_out - x / S->rlen, p[3];
+  for (int a = 0; a < 3; ++a) p[a] = S->org[a] + alpha * S->dir[a];
+  if (S->F->geometry == 1) {
+    double ref[3];
+    orc_shell_inverse(S->F, S->tree, p, ref);
+    memcpy(p, ref, sizeof ref);
+  }
+  for (int a = 0; a < 3; ++a) u[a] = (p[a] - S->lo[a]) / S->h;
+}
+
+static double field_at(const seg_ctx *S, const double *u) {
+  if (S->F->geometry == 1) return orc_triquadratic(S->nodal, u[0], u[1], u[2]);
+  return orc_trilinear(S->nodal, u[0], u[1], u[2]);
+}
+
 /* kappa and q at distance x from the far end of the segment. */
 static void medium_at(const seg_ctx *S, double x, double *kq) {
-  double alpha = S->a_out - x / S->rlen;
   double u[3];
-  for (int a = 0; a < 3; ++a) u[a] = (S->org[a] + alpha * S->dir[a] - S->lo[a]) / S->h;
-  double s = orc_trilinear(S->nodal, u[0], u[1], u[2]);
-  orc_tf_eval(S->F, s, kq);
+  local_coords(S, x, u);
+  orc_tf_eval(S->F, field_at(S, u), kq);
+}
+
+static void seg_init(seg_ctx *S, const orc_forest *F, int leaf, const double *org,
+                     const double *dir, double a_out) {
+  S->F = F;
+  S->nodal = F->nodal + (size_t)nodal_stride(F) * (size_t)leaf;
+  S->tree = F->geometry == 1 ? F->tree[leaf] : 0;
+  leaf_box(F, leaf, S->lo, &S->h);
+  memcpy(S->org, org, sizeof S->org);
+  memcpy(S->dir, dir, sizeof S->dir);
+  S->a_out = a_out;
+  S->rlen = sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
 }
 
 /* One classical RK4 step of length hs starting at distance x0 from the far
@@ -409,13 +621,7 @@ static void segeval(const seg_ctx *S, const orc_integrator *I, double x1, double
 void orc_segment_ab(const orc_forest *F, const orc_integrator *I, int leaf, const double *org,
                     const double *dir, double a_in, double a_out, double *seg4, int64_t *nsteps) {
   seg_ctx S;
-  S.F = F;
-  S.nodal = F->nodal + 8 * (size_t)leaf;
-  leaf_box(F, leaf, S.lo, &S.h);
-  memcpy(S.org, org, sizeof S.org);
-  memcpy(S.dir, dir, sizeof S.dir);
-  S.a_out = a_out;
-  S.rlen = sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+  seg_init(&S, F, leaf, org, dir, a_out);
   double dx = S.rlen * (a_out - a_in);
   int64_t dummy = 0;
   if (!nsteps) nsteps = &dummy;
@@ -596,13 +802,9 @@ int64_t orc_render(const orc_forest *F, const orc_camera *C, const orc_integrato
         int ns = 0, unc = 0;
         for (int q = cstart[i]; q < cstart[i + 1]; ++q) {
           int l = pl[pord[q]];
-          double a_in, a_out;
-          int hit = orc_ray_leaf(F, l, org, dir, amin, amax, &a_in, &a_out);
-          if (isfinite(a_in) && isfinite(a_out)) {
-            double scale = fabs(a_out) > fabs(a_in) ? fabs(a_out) : fabs(a_in);
-            if (fabs(a_out - a_in) <= band_rel * scale) unc = 1;
-          }
-          if (!hit) continue;
+          double a_in[2], a_out[2];
+          int nhit = orc_ray_leaf_tie(F, l, org, dir, amin, amax, a_in, a_out, band_rel, &unc);
+          if (!nhit) continue;
           /* a hit outside the leaf's own rectangle, or within band_px of its edge */
           {
             const double *pe = pext + 4 * (size_t)l;
@@ -610,16 +812,18 @@ int64_t orc_render(const orc_forest *F, const orc_camera *C, const orc_integrato
                 j > pe[3] - band_px)
               unc = 1;
           }
-          if (ns == cap_seg) {
-            cap_seg *= 2;
-            sg = (orc_seg *)realloc(sg, sizeof(orc_seg) * cap_seg);
+          for (int k = 0; k < nhit; ++k) {
+            if (ns == cap_seg) {
+              cap_seg *= 2;
+              sg = (orc_seg *)realloc(sg, sizeof(orc_seg) * cap_seg);
+            }
+            sg[ns].a_in = a_in[k];
+            sg[ns].a_out = a_out[k];
+            int64_t st = 0;
+            orc_segment_ab(F, I, l, org, dir, a_in[k], a_out[k], sg[ns].s, &st);
+            steps += st;
+            ++ns;
           }
-          sg[ns].a_in = a_in;
-          sg[ns].a_out = a_out;
-          int64_t st = 0;
-          orc_segment_ab(F, I, l, org, dir, a_in, a_out, sg[ns].s, &st);
-          steps += st;
-          ++ns;
         }
         size_t pix = (size_t)r * W + i;
         composite(sg, ns, I->bg, rgba + 4 * pix);
@@ -650,10 +854,9 @@ typedef struct {
  * nodal values. */
 static void medium_bwd(const seg_ctx *S, int leaf, double x, const double *vbar, grad_acc *G) {
   const orc_forest *F = S->F;
-  double alpha = S->a_out - x / S->rlen;
   double u[3];
-  for (int a = 0; a < 3; ++a) u[a] = (S->org[a] + alpha * S->dir[a] - S->lo[a]) / S->h;
-  double s = orc_trilinear(S->nodal, u[0], u[1], u[2]);
+  local_coords(S, x, u);
+  double s = field_at(S, u);
   double zr = (s - F->s_min) / (F->s_max - F->s_min) * 7.0;
   int inside = zr > 0.0 && zr < 7.0;
   double z = zr < 0.0 ? 0.0 : (zr > 7.0 ? 7.0 : zr);
@@ -668,6 +871,17 @@ static void medium_bwd(const seg_ctx *S, int leaf, double x, const double *vbar,
     if (inside)
       sbar += vbar[c] * ((double)F->tf[4 * (k + 1) + c] - (double)F->tf[4 * k + c]) * 7.0 /
               (F->s_max - F->s_min);
+  }
+  if (F->geometry == 1) {
+    double lu[3], lv[3], lw[3];
+    quad_basis(u[0], lu);
+    quad_basis(u[1], lv);
+    quad_basis(u[2], lw);
+    for (int c = 0; c < 27; ++c) {
+#pragma omp atomic
+      G->g_nodal[27 * (size_t)leaf + c] += sbar * lu[c % 3] * lv[(c / 3) % 3] * lw[c / 9];
+    }
+    return;
   }
   for (int c = 0; c < 8; ++c) {
     double wx = (c & 1) ? u[0] : 1.0 - u[0];
@@ -747,13 +961,7 @@ static void segment_bwd(const orc_forest *F, const orc_integrator *I, int leaf, 
                         const double *dir, double a_in, double a_out, const double *ybar,
                         grad_acc *G) {
   seg_ctx S;
-  S.F = F;
-  S.nodal = F->nodal + 8 * (size_t)leaf;
-  leaf_box(F, leaf, S.lo, &S.h);
-  memcpy(S.org, org, sizeof S.org);
-  memcpy(S.dir, dir, sizeof S.dir);
-  S.a_out = a_out;
-  S.rlen = sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+  seg_init(&S, F, leaf, org, dir, a_out);
   double dx = S.rlen * (a_out - a_in);
   if (I->method == ORC_RK4) {
     /* y_{n+1} = step_n(y_n) = R_n y_n + G_n: keep every y_n, then sweep back */
@@ -793,7 +1001,7 @@ int orc_render_grad(const orc_forest *F, const orc_camera *C, const orc_integrat
     int unc = 0;
     orc_leaf_rect(F, C, l, rect + 4 * (size_t)l, NULL, 0.0, &unc);
   }
-  memset(g_nodal, 0, sizeof(double) * 8 * (size_t)F->nleaves);
+  memset(g_nodal, 0, sizeof(double) * (size_t)nodal_stride(F) * (size_t)F->nleaves);
   memset(g_tf, 0, sizeof(double) * 32);
   grad_acc G = {g_nodal, g_tf};
 #ifdef _OPENMP
@@ -815,18 +1023,20 @@ int orc_render_grad(const orc_forest *F, const orc_camera *C, const orc_integrat
       for (int l = 0; l < F->nleaves; ++l) {
         const int32_t *rc = rect + 4 * (size_t)l;
         if (i < rc[0] - 1 || i > rc[1] + 1 || j < rc[2] - 1 || j > rc[3] + 1) continue;
-        double a0, a1;
-        if (!orc_ray_leaf(F, l, org, dir, amin, amax, &a0, &a1)) continue;
-        if (ns == cap) {
-          cap *= 2;
-          sg = (orc_seg *)realloc(sg, sizeof(orc_seg) * cap);
-          sl = (int *)realloc(sl, sizeof(int) * cap);
+        double a0[2], a1[2];
+        int nhit = orc_ray_leaf(F, l, org, dir, amin, amax, a0, a1);
+        for (int k = 0; k < nhit; ++k) {
+          if (ns == cap) {
+            cap *= 2;
+            sg = (orc_seg *)realloc(sg, sizeof(orc_seg) * cap);
+            sl = (int *)realloc(sl, sizeof(int) * cap);
+          }
+          sg[ns].a_in = a0[k];
+          sg[ns].a_out = a1[k];
+          orc_segment_ab(F, I, l, org, dir, a0[k], a1[k], sg[ns].s, NULL);
+          sl[ns] = l;
+          ++ns;
         }
-        sg[ns].a_in = a0;
-        sg[ns].a_out = a1;
-        orc_segment_ab(F, I, l, org, dir, a0, a1, sg[ns].s, NULL);
-        sl[ns] = l;
-        ++ns;
       }
       /* order near to far by alpha (an index sort carrying the leaf ids) */
       for (int a = 1; a < ns; ++a) {

@@ -24,15 +24,24 @@
 extern "C" {
 #endif
 
-/* Forest of one unit-cube tree with the identity map. */
+/* A forest: one unit-cube tree with the identity map (geometry 0), or the six
+ * trees of a cubed-sphere shell (geometry 1).  Shell tree k maps reference
+ * (xi, eta, zeta) to r(zeta) normalize(n + tan(pi/4 (2 xi - 1)) e1 +
+ * tan(pi/4 (2 eta - 1)) e2), r(zeta) = r0 + (r1 - r0) zeta, with (n, e1, e2)
+ * = frames[k]. */
 typedef struct {
   int nleaves;
   int max_level;            /* anchors are integers in units of 2^-max_level */
   const int32_t *anchor;    /* [nleaves*3] */
   const uint8_t *level;     /* [nleaves] */
-  const float *nodal;       /* [nleaves*8], corner c = bx + 2 by + 4 bz */
+  const float *nodal;       /* [nleaves*stride]: cube, 8 corners c = bx + 2 by + 4 bz;
+                               shell, 27 nodes a + 3 b + 9 c at (a, b, c)/2 */
   const float *tf;          /* [8*4]: kappa, q_r, q_g, q_b at the 8 knots */
   double s_min, s_max;      /* knot k sits at s_min + k (s_max - s_min) / 7 */
+  int geometry;             /* 0 cube, 1 shell */
+  const int32_t *tree;      /* [nleaves] (shell) */
+  double frames[6][3][3];
+  double r0, r1;
 } orc_forest;
 
 typedef struct {
@@ -75,10 +84,30 @@ void orc_pixel_ray(const orc_camera *C, int i, int j, double *org, double *dir,
 int orc_leaf_rect(const orc_forest *F, const orc_camera *C, int leaf, int32_t *rect,
                   double *pext, double band_px, int *vis_unc);
 
-/* Slab intersection of a ray with a leaf; returns 1 and [a_in, a_out] if the
- * clipped interval is non-empty. */
+/* Intersection of a ray with a leaf, clipped to [amin, amax]: a slab test
+ * for the cube; for a shell leaf the four half-spaces through the origin
+ * bounding its angular extent and the spherical shell between its two radii
+ * (at most two intervals).  Returns the number of non-empty intervals and
+ * fills a_in[k], a_out[k] (arrays of 2), nearest first. */
 int orc_ray_leaf(const orc_forest *F, int leaf, const double *org, const double *dir,
                  double amin, double amax, double *a_in, double *a_out);
+
+/* The same, also raising *tie (when tie is not NULL) for a decision within
+ * band_rel of flipping: an interval of relative length <= band_rel, or a ray
+ * whose squared distance from the shell's centre is within band_rel of a
+ * leaf's squared radius.  For the cube, a_in[0], a_out[0] receive the slab
+ * interval even when it is empty. */
+int orc_ray_leaf_tie(const orc_forest *F, int leaf, const double *org, const double *dir,
+                     double amin, double amax, double *a_in, double *a_out, double band_rel,
+                     int *tie);
+
+/* The equiangular map of tree reference coordinates to space and its inverse
+ * (shell forests). */
+void orc_shell_map(const orc_forest *F, int tree, const double *ref, double *x);
+void orc_shell_inverse(const orc_forest *F, int tree, const double *x, double *ref);
+
+/* Degree-2 Lagrange interpolation on the nodes {0, 1/2, 1}^3. */
+double orc_triquadratic(const float *nodal27, double u, double v, double w);
 
 /* (A, B) of the segment [a_in, a_out] of the ray inside the leaf. */
 void orc_segment_ab(const orc_forest *F, const orc_integrator *I, int leaf,
@@ -104,8 +133,9 @@ int64_t orc_render(const orc_forest *F, const orc_camera *C, const orc_integrato
  * from the transmittance of the nearer ones and the aggregate of the farther
  * ones (with the background), and is carried back through the integrator
  * (RK4 or Algorithm 1 with DOPRI5; the step tree is re-derived with the same
- * tests), the transfer function and the trilinear interpolation.  g_nodal
- * [nleaves*8], g_tf [32] are overwritten.  Every pixel is tested against
+ * tests), the transfer function and the trilinear (cube) or triquadratic
+ * (shell) interpolation.  g_nodal [nleaves*8 or *27], g_tf [32] are
+ * overwritten.  Every pixel is tested against
  * every leaf: for small cases.  Returns 0, or -2 for other integrators. */
 int orc_render_grad(const orc_forest *F, const orc_camera *C, const orc_integrator *I,
                     const double *dL_drgba, double *g_nodal, double *g_tf, int nthreads);
