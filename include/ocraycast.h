@@ -25,9 +25,10 @@
  *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default
  *    stream).  Work is enqueued on it; ocr_render returns without waiting
  *    for the device unless counters or phase times are requested.
- *  - Only the single unit-cube tree with the identity map is implemented in
- *    this version (OCR_GEOM_CUBE); other geometries return
- *    OCR_ERR_UNSUPPORTED.
+ *  - Two geometries: one unit-cube tree with the identity map
+ *    (OCR_GEOM_CUBE) and the six-tree cubed-sphere shell with the equiangular
+ *    map (OCR_GEOM_SHELL, the paper's forest of octrees with a curved tree
+ *    map, Sec. 2.1).
  */
 #ifndef OCRAYCAST_H
 #define OCRAYCAST_H
@@ -46,6 +47,7 @@ extern "C" {
 #define OCR_ERR_STATE (-6)       /* call order violated (no data / no camera set) */
 
 #define OCR_GEOM_CUBE 0
+#define OCR_GEOM_SHELL 1
 
 #define OCR_RK4 0     /* nsteps equal classical RK4 steps per segment */
 #define OCR_DOPRI5 1  /* Dormand-Prince 5(4) inside the bisection of Algorithm 1 */
@@ -54,16 +56,29 @@ extern "C" {
 
 typedef struct ocr_forest ocr_forest;
 
-/* Linear forest of one octree over the unit cube (Sec. 2.1, Sec. 3).
- * Leaves are listed in Morton order of their anchors and tile the cube.
- * anchor[3*k + a] is leaf k's lower corner along axis a in integer units of
- * 2^-max_level; level[k] its level (edge length 2^-level).  max_level <= 20. */
+/* Linear forest of octrees (Sec. 2.1, Sec. 3).  anchor[3*k + a] is leaf k's
+ * lower corner along axis a of its tree's reference cube in integer units of
+ * 2^-max_level; level[k] its level (edge length 2^-level).  max_level <= 20.
+ *
+ * OCR_GEOM_CUBE: one tree, the identity map onto the unit cube; leaves in
+ * Morton order of their anchors, tiling the cube.  h_tree, frames, r0, r1 are
+ * ignored.
+ *
+ * OCR_GEOM_SHELL: six trees; leaves sorted by (h_tree[k], Morton key), each
+ * tree's leaves tiling its reference cube.  Tree t maps reference
+ * (xi, eta, zeta) to r(zeta) normalize(n + tan(pi/4 (2 xi - 1)) e1 +
+ * tan(pi/4 (2 eta - 1)) e2) with (n, e1, e2) = frames[t] (orthonormal rows),
+ * r(zeta) = r0 + (r1 - r0) zeta, 0 < r0 < r1: the equiangular cubed sphere,
+ * whose six normals n must be the +-x, +-y, +-z axes, one per tree. */
 typedef struct {
-  int geometry;          /* OCR_GEOM_CUBE */
+  int geometry;          /* OCR_GEOM_CUBE or OCR_GEOM_SHELL */
   int max_level;
   int64_t nleaves;
   const int32_t *h_anchor; /* [nleaves * 3] */
   const uint8_t *h_level;  /* [nleaves] */
+  const int32_t *h_tree;   /* [nleaves] tree 0..5 (shell) */
+  double frames[6][3][3];  /* shell: rows n, e1, e2 of each tree */
+  double r0, r1;           /* shell radii */
 } ocr_forest_desc;
 
 /* Pinhole camera of Sec. 2.2, Eq. 2.5: ray (i, j) is o + alpha r with
@@ -126,8 +141,9 @@ typedef struct {
 int ocr_build_forest(const ocr_forest_desc *desc, void *stream, ocr_forest **out);
 
 /* Attach the field and the transfer function (not copied, not owned):
- * d_nodal [nleaves*8] float32, corner c = bx + 2 by + 4 bz of each leaf
- * (trilinear data); d_tf [8*4] float32, (kappa, q_r, q_g, q_b) at 8 knots
+ * d_nodal float32, cube: [nleaves*8], corner c = bx + 2 by + 4 bz of each
+ * leaf (trilinear data); shell: [nleaves*27], node c = a + 3 b + 9 c' at local
+ * coordinates (a, b, c')/2 (degree-2 Lagrange data); d_tf [8*4] float32, (kappa, q_r, q_g, q_b) at 8 knots
  * spaced uniformly over [s_min, s_max], piecewise linear, constant outside. */
 int ocr_forest_set_data(ocr_forest *F, const float *d_nodal, const float *d_tf, float s_min,
                         float s_max, void *stream);
@@ -139,7 +155,9 @@ int ocr_set_integrator(ocr_forest *F, const ocr_integrator *integ);
  * stream, blocking) to size its scratch, which is allocated here.  Rendering
  * then never waits for the host, so ocr_render without counters can be
  * captured in a CUDA graph.  Several cameras are rendered by one ocr_render
- * call (batching: the paper's multiple image instances, Sec. 3). */
+ * call (batching: the paper's multiple image instances, Sec. 3).  Shell
+ * forests also size each camera's segment lists here; a ray with more than
+ * 4096 segments returns OCR_ERR_UNSUPPORTED. */
 int ocr_set_camera(ocr_forest *F, const ocr_camera *cams, int ncams);
 
 /* Render the images of all cameras: d_rgba float32, the cameras' images
@@ -148,7 +166,14 @@ int ocr_set_camera(ocr_forest *F, const ocr_camera *cams, int ncams);
  * fork from and join back into `stream`.  stats may be NULL; its d_counts is
  * indexed like the concatenated image, d_visible is the union over cameras,
  * d_rects belongs to the first camera, time_phases applies to single-camera
- * renders only. */
+ * renders only.
+ * Shell forests: a ray meets a leaf in up to two intervals and the Morton
+ * order is not the order along a ray, so each ray's segments are listed over
+ * the leaves' pixel rectangles, ordered by entry depth (ties by tree and
+ * Morton key), integrated, and merged nearest first with Eq. 2.14; overlapping
+ * neighbours are cut (Eq. 2.20) and averaged (Eq. 2.21).  A ray with more
+ * segments than ocr_set_camera found on any ray is left at the background
+ * and counted as a device error (OCR_ERR_DEVICE when counters are filled). */
 int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats);
 
 /* Pruning for callers that cannot allocate device memory at the time they

@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libocraycast.so")
-SOURCES = ["ocr_capi.cu", "ocr_kernels.cu", "ocr_backward.cu"]
+SOURCES = ["ocr_capi.cu", "ocr_kernels.cu", "ocr_backward.cu", "ocr_shell.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--use_fast_math",
          "-Xptxas", "-v"]

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libocraycast.so")
 
 OK, ERR_INVALID, ERR_CUDA, ERR_OOM, ERR_UNSUPPORTED, ERR_DEVICE, ERR_STATE = 0, -1, -2, -3, -4, -5, -6
-GEOM_CUBE = 0
+GEOM_CUBE, GEOM_SHELL = 0, 1
 RK4, DOPRI5, GAUSS2, SIMPSON = 0, 1, 2, 3
 
 EXPORTS = ["ocr_build_forest", "ocr_forest_set_data", "ocr_set_integrator", "ocr_set_camera",
@@ -24,7 +24,9 @@ EXPORTS = ["ocr_build_forest", "ocr_forest_set_data", "ocr_set_integrator", "ocr
 
 class ForestDesc(C.Structure):
     _fields_ = [("geometry", C.c_int), ("max_level", C.c_int), ("nleaves", C.c_int64),
-                ("h_anchor", C.POINTER(C.c_int32)), ("h_level", C.POINTER(C.c_uint8))]
+                ("h_anchor", C.POINTER(C.c_int32)), ("h_level", C.POINTER(C.c_uint8)),
+                ("h_tree", C.POINTER(C.c_int32)), ("frames", C.c_double * 9 * 6),
+                ("r0", C.c_double), ("r1", C.c_double)]
 
 
 class Camera(C.Structure):
@@ -105,13 +107,23 @@ def _ptr(x):
     return x.ctypes.data
 
 
-def build_forest(level, anchor, max_level: int, stream=None, geometry: int = GEOM_CUBE):
-    """ocr_build_forest.  level: uint8 [N], anchor: int32 [N, 3] (host numpy)."""
+def build_forest(level, anchor, max_level: int, stream=None, geometry: int = GEOM_CUBE,
+                 tree=None, frames=None, r0: float = 0.0, r1: float = 0.0):
+    """ocr_build_forest.  level: uint8 [N], anchor: int32 [N, 3] (host numpy);
+    shell forests also tree: int32 [N], frames: [6, 3, 3] (rows n, e1, e2), r0, r1."""
     import numpy as np
     lv = np.ascontiguousarray(level, dtype=np.uint8)
     an = np.ascontiguousarray(anchor, dtype=np.int32)
     d = ForestDesc(geometry, int(max_level), int(lv.shape[0]),
                    an.ctypes.data_as(C.POINTER(C.c_int32)), lv.ctypes.data_as(C.POINTER(C.c_uint8)))
+    if geometry == GEOM_SHELL:
+        tr = np.ascontiguousarray(tree, dtype=np.int32)
+        d.h_tree = tr.ctypes.data_as(C.POINTER(C.c_int32))
+        fr = np.asarray(frames, dtype=np.float64).reshape(6, 9)
+        for t in range(6):
+            for k in range(9):
+                d.frames[t][k] = float(fr[t, k])
+        d.r0, d.r1 = float(r0), float(r1)
     h = C.c_void_p()
     _check(lib().ocr_build_forest(C.byref(d), _ptr(stream), C.byref(h)), "ocr_build_forest")
     return h

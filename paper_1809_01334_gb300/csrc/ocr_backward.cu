@@ -24,7 +24,7 @@
 namespace ocr {
 namespace {
 
-constexpr int kPairThreads = 256;
+constexpr int kPairThreads = kPairChunk;
 
 __device__ __forceinline__ long long area_of(int4 r) {
   return r.x > r.y ? 0ll : (long long)(r.y - r.x + 1) * (long long)(r.w - r.z + 1);

@@ -33,12 +33,24 @@ struct CamPlan {
   long long *d_gslots = nullptr;      // [L + 1]
   int *d_chunk = nullptr;             // [total / kChunk + 2]
   float4 *d_entries = nullptr;        // [total slots]
+  // shell forests: the (leaf, pixel) pair space and the per-ray segment lists
+  long long npairs = 0, nhits = 0, bs_cap = 0;
+  int cap = 0;                        // longest list found, rounded up to a power of two
+  long long *d_leaf_off = nullptr;    // [N + 1]
+  long long *d_sbsums = nullptr;      // [bs_cap]
+  int *d_pchunk = nullptr;            // [npairs / kPairChunk + 2]
+  int *d_rcount = nullptr, *d_rcursor = nullptr;  // [npix]
+  long long *d_ray_off = nullptr;     // [npix + 1]
+  unsigned long long *d_keys = nullptr;  // [nhits]
 };
 
 constexpr int kRenderStreams = 4;   // cameras of a batch are spread over these
 constexpr int kMaxCameras = 4096;
 
 struct ocr_forest {
+  int geometry = OCR_GEOM_CUBE;
+  Shell shell{};                      // shell: frames and tables (in d_shell_tabs)
+  float *d_shell_tabs = nullptr;      // [54 + 2 (2^L + 1)]
   int N = 0, M = 0, L = 0;
   int root = 0;                       // unified id of the tree root
   std::vector<int> level_base;        // internal index of the first node of level l
@@ -136,11 +148,19 @@ void free_plans(ocr_forest *F) {
     cudaFree(P.d_gslots);
     cudaFree(P.d_chunk);
     cudaFree(P.d_entries);
+    cudaFree(P.d_leaf_off);
+    cudaFree(P.d_sbsums);
+    cudaFree(P.d_pchunk);
+    cudaFree(P.d_rcount);
+    cudaFree(P.d_rcursor);
+    cudaFree(P.d_ray_off);
+    cudaFree(P.d_keys);
   }
   F->plans.clear();
 }
 
 void free_all(ocr_forest *F) {
+  cudaFree(F->d_shell_tabs);
   cudaFree(F->d_geo);
   cudaFree(F->d_child);
   cudaFree(F->d_leaves);
@@ -196,6 +216,193 @@ void to_cam(const ocr_camera &c, Cam &k) {
   k.amax = (float)(c.ortho ? c.far_ : c.far_ / c.near_);
 }
 
+// A signed unit axis vector: the index of its non-zero entry, or -1.
+int axis_of(const double *v) {
+  int ax = -1;
+  for (int a = 0; a < 3; ++a) {
+    if (v[a] == 0.0) continue;
+    if ((v[a] != 1.0 && v[a] != -1.0) || ax >= 0) return -1;
+    ax = a;
+  }
+  return ax;
+}
+
+// Shell forest: validate the six trees and their leaves, upload the leaf
+// records {x, y, z, level | tree << 8} and the tables of plane tangents and
+// sphere radii every kernel reads.
+int build_shell(const ocr_forest_desc *desc, cudaStream_t st, ocr_forest **out) {
+  const int L = desc->max_level;
+  const int64_t N64 = desc->nleaves;
+  if (L < 0 || L > 20 || N64 < 6 || N64 > (1ll << 30) || !desc->h_anchor || !desc->h_level ||
+      !desc->h_tree)
+    return OCR_ERR_INVALID;
+  if (!(desc->r0 > 0.0) || !(desc->r1 > desc->r0) || !std::isfinite(desc->r1))
+    return OCR_ERR_INVALID;
+  int seen = 0;
+  for (int t = 0; t < 6; ++t) {
+    int ax[3];
+    for (int r = 0; r < 3; ++r)
+      if ((ax[r] = axis_of(desc->frames[t][r])) < 0) return OCR_ERR_INVALID;
+    if (ax[0] == ax[1] || ax[0] == ax[2] || ax[1] == ax[2]) return OCR_ERR_INVALID;
+    const int id = 2 * ax[0] + (desc->frames[t][0][ax[0]] < 0.0);
+    if (seen & (1 << id)) return OCR_ERR_INVALID;  // two trees around one axis direction
+    seen |= 1 << id;
+  }
+  const int N = (int)N64;
+  const uint64_t full = 1ull << (3 * L);
+  uint64_t expect = 0;
+  int tree = 0;
+  std::vector<int4> geo((size_t)N + 1);
+  for (int k = 0; k < N; ++k) {
+    const int t = desc->h_tree[k], lv = desc->h_level[k];
+    if (t < 0 || t > 5 || lv > L) return OCR_ERR_INVALID;
+    if (t != tree) {  // the previous tree must be complete, trees in order 0..5
+      if (t != tree + 1 || expect != full) return OCR_ERR_INVALID;
+      tree = t;
+      expect = 0;
+    }
+    const int32_t *a = desc->h_anchor + 3 * (size_t)k;
+    const int32_t mask = (1 << (L - lv)) - 1;
+    for (int d = 0; d < 3; ++d)
+      if (a[d] < 0 || a[d] >= (1 << L) || (a[d] & mask)) return OCR_ERR_INVALID;
+    if (morton(a[0], a[1], a[2]) != expect) return OCR_ERR_INVALID;
+    expect += 1ull << (3 * (L - lv));
+    geo[k] = make_int4(a[0], a[1], a[2], lv | t << 8);
+  }
+  if (tree != 5 || expect != full) return OCR_ERR_INVALID;
+  geo[N] = make_int4(0, 0, 0, -1);
+
+  const int nt = (1 << L) + 1;
+  std::vector<float> tabs(54 + 2 * (size_t)nt);
+  for (int t = 0; t < 6; ++t)
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) tabs[9 * t + 3 * r + c] = (float)desc->frames[t][r][c];
+  const double pi = 3.14159265358979323846;
+  for (int k = 0; k < nt; ++k) {
+    // tan(pi/4 (2 k 2^-L - 1)): odd about the tree centre, exactly -+1 at its edges
+    const double x = std::ldexp(2.0 * k, -L) - 1.0, ax = std::fabs(x);
+    const double v = ax == 1.0 ? 1.0 : std::tan(0.25 * pi * ax);
+    tabs[54 + k] = (float)(x < 0.0 ? -v : v);
+    tabs[54 + nt + k] = (float)(desc->r0 + (desc->r1 - desc->r0) * std::ldexp((double)k, -L));
+  }
+
+  ocr_forest *F = new (std::nothrow) ocr_forest();
+  if (!F) return OCR_ERR_OOM;
+  F->geometry = OCR_GEOM_SHELL;
+  F->N = N;
+  F->L = L;
+  F->M = 0;
+  int rc;
+  if ((rc = dev_alloc(&F->d_geo, geo.size(), F->bytes)) ||
+      (rc = dev_alloc(&F->d_shell_tabs, tabs.size(), F->bytes)) ||
+      (rc = dev_alloc(&F->d_stats, kStats, F->bytes)) ||
+      (rc = dev_alloc(&F->d_err, 1, F->bytes))) {
+    free_all(F);
+    delete F;
+    return rc;
+  }
+  if (cudaMallocHost((void **)&F->h_group_slots, sizeof(long long) * (kStats + 2)) !=
+      cudaSuccess) {
+    F->h_group_slots = nullptr;
+    free_all(F);
+    delete F;
+    return OCR_ERR_OOM;
+  }
+  F->shell.frames = F->d_shell_tabs;
+  F->shell.tan_tab = F->d_shell_tabs + 54;
+  F->shell.rad_tab = F->d_shell_tabs + 54 + nt;
+  F->shell.L = L;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&F->nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(F->d_geo, geo.data(), geo.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                        st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(F->d_shell_tabs, tabs.data(), tabs.size() * sizeof(float),
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    free_all(F);
+    delete F;
+    return cuda_fail(e);
+  }
+  *out = F;
+  return OCR_OK;
+}
+
+// Plan one camera of a shell forest: its pruning and pair space, the segment
+// count of every ray, the size of the lists and the longest one.  Blocks the
+// host (legacy default stream).
+int plan_shell(ocr_forest *F, CamPlan &P) {
+  const long long npix = P.npix;
+  const Topo T{F->d_geo, nullptr, nullptr, F->N, 0, F->L, 0};
+  int rc;
+  P.bs_cap = std::max(bwd_scan_blocks(F->N), bwd_scan_blocks(npix)) + 2;
+  if ((rc = dev_alloc(&P.d_rect, (size_t)F->N + 1, F->bytes)) ||
+      (rc = dev_alloc(&P.d_leaf_off, (size_t)F->N + 1, F->bytes)) ||
+      (rc = dev_alloc(&P.d_sbsums, (size_t)P.bs_cap, F->bytes)) ||
+      (rc = dev_alloc(&P.d_rcount, (size_t)npix, F->bytes)) ||
+      (rc = dev_alloc(&P.d_rcursor, (size_t)npix, F->bytes)) ||
+      (rc = dev_alloc(&P.d_ray_off, (size_t)npix + 1, F->bytes)))
+    return rc;
+  long long *h = F->h_group_slots;
+  OCR_CUDA(cudaMemsetAsync(F->d_stats, 0, kStats * sizeof(unsigned long long), 0));
+  OCR_CUDA(shell_cull(F->d_geo, F->N, F->shell, P.cam, P.d_rect, nullptr, F->d_stats, 0));
+  OCR_CUDA(bwd_leaf_scan(T, P.d_rect, P.d_sbsums, P.bs_cap, P.d_leaf_off, 0));
+  OCR_CUDA(cudaMemcpyAsync(h, P.d_leaf_off + F->N, sizeof(long long), cudaMemcpyDeviceToHost, 0));
+  OCR_CUDA(cudaStreamSynchronize(0));
+  P.npairs = h[0];
+  if ((rc = dev_alloc(&P.d_pchunk, (size_t)(P.npairs / kPairChunk + 2), F->bytes))) return rc;
+  OCR_CUDA(bwd_chunk_map(P.d_leaf_off, F->N, P.d_pchunk, 0));
+  OCR_CUDA(cudaMemsetAsync(P.d_rcount, 0, sizeof(int) * (size_t)npix, 0));
+  OCR_CUDA(shell_pairs(false, F->d_geo, F->N, F->shell, P.cam, P.d_rect, P.d_leaf_off,
+                       P.d_pchunk, P.npairs, P.d_rcount, nullptr, nullptr, nullptr, 0,
+                       F->d_stats, 0));
+  OCR_CUDA(bwd_count_scan(P.d_rcount, npix, P.d_sbsums, P.bs_cap, P.d_ray_off, 0));
+  OCR_CUDA(cudaMemcpyAsync(h, P.d_ray_off + npix, sizeof(long long), cudaMemcpyDeviceToHost, 0));
+  OCR_CUDA(cudaMemcpyAsync(h + 1, F->d_stats + kStatMaxHits, sizeof(long long),
+                           cudaMemcpyDeviceToHost, 0));
+  OCR_CUDA(cudaStreamSynchronize(0));
+  P.nhits = h[0];
+  const long long longest = h[1];
+  if (longest > kShellMaxCap) return OCR_ERR_UNSUPPORTED;
+  P.cap = 32;
+  while (P.cap < longest) P.cap <<= 1;
+  return dev_alloc(&P.d_keys, (size_t)(P.nhits > 0 ? P.nhits : 1), F->bytes);
+}
+
+// Enqueue one camera's render of a shell forest on st: pruning, pair space,
+// counts, list offsets, lists, then one warp per ray.  No host synchronisation.
+int enqueue_shell(ocr_forest *F, CamPlan &P, float4 *rgba, int *counts, unsigned char *visible,
+                  cudaStream_t st, bool timed, int64_t &launches) {
+  const long long npix = P.npix;
+  const Topo T{F->d_geo, nullptr, nullptr, F->N, 0, F->L, 0};
+  const Field Fd{F->d_nodal, reinterpret_cast<const float4 *>(F->d_tf), F->s_min,
+                 7.f / (F->s_max - F->s_min)};
+  OCR_CUDA(shell_cull(F->d_geo, F->N, F->shell, P.cam, P.d_rect, visible, F->d_stats, st));
+  OCR_CUDA(bwd_leaf_scan(T, P.d_rect, P.d_sbsums, P.bs_cap, P.d_leaf_off, st));
+  OCR_CUDA(bwd_chunk_map(P.d_leaf_off, F->N, P.d_pchunk, st));
+  OCR_CUDA(cudaMemsetAsync(P.d_rcount, 0, sizeof(int) * (size_t)npix, st));
+  OCR_CUDA(shell_pairs(false, F->d_geo, F->N, F->shell, P.cam, P.d_rect, P.d_leaf_off,
+                       P.d_pchunk, P.npairs, P.d_rcount, nullptr, nullptr, nullptr, 0, nullptr,
+                       st));
+  OCR_CUDA(bwd_count_scan(P.d_rcount, npix, P.d_sbsums, P.bs_cap, P.d_ray_off, st));
+  OCR_CUDA(cudaMemsetAsync(P.d_rcursor, 0, sizeof(int) * (size_t)npix, st));
+  OCR_CUDA(shell_pairs(true, F->d_geo, F->N, F->shell, P.cam, P.d_rect, P.d_leaf_off, P.d_pchunk,
+                       P.npairs, nullptr, P.d_ray_off, P.d_rcursor, P.d_keys, P.nhits,
+                       F->d_stats, st));
+  if (timed) OCR_CUDA(cudaEventRecord(F->ev[1], st));
+  if (timed) OCR_CUDA(cudaEventRecord(F->ev[2], st));
+  OCR_CUDA(shell_rays(F->d_geo, F->N, F->shell, Fd, P.cam, F->integ, P.d_ray_off, npix, P.d_keys,
+                      P.nhits, P.cap, rgba, counts, F->d_stats, F->nsm, st));
+  if (timed) OCR_CUDA(cudaEventRecord(F->ev[3], st));
+  // cull, 2 scans of 3 kernels (1 when empty), chunk map, 2 pair passes, rays
+  launches += 1 + (bwd_scan_blocks(F->N) > 0 ? 3 : 0) + 1 + (P.npairs > 0 ? 2 : 0) +
+              (bwd_scan_blocks(npix) > 0 ? 3 : 0) + 1;
+  return OCR_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -216,6 +423,7 @@ const char *ocr_strerror(int code) {
 int ocr_build_forest(const ocr_forest_desc *desc, void *stream, ocr_forest **out) {
   if (!desc || !out) return OCR_ERR_INVALID;
   *out = nullptr;
+  if (desc->geometry == OCR_GEOM_SHELL) return build_shell(desc, (cudaStream_t)stream, out);
   if (desc->geometry != OCR_GEOM_CUBE) return OCR_ERR_UNSUPPORTED;
   const int L = desc->max_level;
   const int64_t N64 = desc->nleaves;
@@ -448,6 +656,15 @@ int ocr_set_camera(ocr_forest *F, const ocr_camera *cams, int ncams) {
       OCR_CUDA(cudaEventCreateWithFlags(&F->join[q], cudaEventDisableTiming));
     }
   }
+  if (F->geometry == OCR_GEOM_SHELL) {
+    for (CamPlan &P : F->plans) {
+      const int rc = plan_shell(F, P);
+      if (rc) return rc;
+    }
+    OCR_CUDA(shell_rays_prepare());
+    F->has_cam = true;
+    return OCR_OK;
+  }
   // plan every camera: run its pruning and slot layout once and keep the sizes
   const int G = (int)F->h_group_nodes.size();
   Topo T{F->d_geo, F->d_child, F->d_leaves, F->N, F->M, F->L, F->lt};
@@ -553,8 +770,11 @@ int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats) {
   float4 *rgba = reinterpret_cast<float4 *>(d_rgba);
   if (K == 1) {
     if (timed) OCR_CUDA(cudaEventRecord(F->ev[0], st));
-    int rc = enqueue_camera(F, F->plans[0], rgba, counts, visible, st, timed, subtree_ran,
-                            launches);
+    int rc = F->geometry == OCR_GEOM_SHELL
+                 ? enqueue_shell(F, F->plans[0], rgba, counts, visible, st, timed, launches)
+                 : enqueue_camera(F, F->plans[0], rgba, counts, visible, st, timed, subtree_ran,
+                                  launches);
+    subtree_ran |= F->geometry == OCR_GEOM_SHELL;
     if (rc) return rc;
     if (timed) OCR_CUDA(cudaEventRecord(F->ev[4], st));
   } else {
@@ -563,8 +783,12 @@ int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats) {
     for (int q = 0; q < kRenderStreams; ++q) OCR_CUDA(cudaStreamWaitEvent(F->sub[q], F->fork, 0));
     for (int k = 0; k < K; ++k) {
       CamPlan &P = F->plans[k];
-      int rc = enqueue_camera(F, P, rgba + P.pix_off, counts ? counts + P.pix_off : nullptr,
-                              visible, F->sub[k % kRenderStreams], false, subtree_ran, launches);
+      int *cnt = counts ? counts + P.pix_off : nullptr;
+      int rc = F->geometry == OCR_GEOM_SHELL
+                   ? enqueue_shell(F, P, rgba + P.pix_off, cnt, visible,
+                                   F->sub[k % kRenderStreams], false, launches)
+                   : enqueue_camera(F, P, rgba + P.pix_off, cnt, visible,
+                                    F->sub[k % kRenderStreams], false, subtree_ran, launches);
       if (rc) return rc;
     }
     for (int q = 0; q < kRenderStreams; ++q) {
@@ -599,6 +823,12 @@ int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats) {
       stats->subtree_rk_steps = (int64_t)h[kStatSteps];
       stats->subtree_leaf_tests = (int64_t)h[kStatTests];
       stats->visible_leaves = (int64_t)h[kStatVisible];
+      if (F->geometry == OCR_GEOM_SHELL) {  // two passes over every (leaf, pixel) pair
+        int64_t pairs = 0;
+        for (const CamPlan &P : F->plans) pairs += 2 * P.npairs;
+        stats->leaf_tests = stats->subtree_leaf_tests = pairs;
+        stats->slots = 0;
+      }
       if (h[kStatErrors]) return OCR_ERR_DEVICE;
     }
   }
@@ -631,6 +861,7 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
   if (!F || !d_dL_drgba || !d_grad_nodal || !d_grad_tf) return OCR_ERR_INVALID;
   if (!F->has_data || !F->has_cam || !F->has_integ) return OCR_ERR_STATE;
   if (F->integ.method != OCR_RK4 && F->integ.method != OCR_DOPRI5) return OCR_ERR_UNSUPPORTED;
+  if (F->geometry != OCR_GEOM_CUBE) return OCR_ERR_UNSUPPORTED;
   if ((uintptr_t)d_dL_drgba & 15) return OCR_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   CamPlan &P0 = F->plans[0];

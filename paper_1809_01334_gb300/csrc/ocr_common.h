@@ -77,6 +77,23 @@ constexpr int kMaxRayHits = 512;
 // Slots are processed in chunks of kChunk consecutive slots, one chunk per CTA.
 constexpr int kChunk = 128;
 
+// (leaf, pixel) pair spaces (the adjoint, the shell) are cut into chunks of
+// kPairChunk pairs, one CTA each.
+constexpr int kPairChunk = 256;
+
+// Cubed-sphere shell (geometry 1).  Leaf geo = {x, y, z, level | tree << 8},
+// anchors in units of 2^-L of the tree's reference cube.  The tangents of the
+// equiangular planes and the radii of the spherical faces come from tables
+// rounded once on the host, so that two leaves sharing a face compute
+// bit-identical crossings of a ray with it.
+struct Shell {
+  const float *frames;   // [6 * 9] per tree: n, e1, e2
+  const float *tan_tab;  // [2^L + 1] tan(pi/4 (2 k 2^-L - 1))
+  const float *rad_tab;  // [2^L + 1] r0 + (r1 - r0) k 2^-L
+  int L;
+};
+constexpr int kStatMaxHits = 6;  // shell: the most segments on one ray (atomicMax)
+
 // Launch wrappers (ocr_kernels.cu).  All enqueue on `stream` and return the
 // launch error.
 cudaError_t launch_cull_leaves(const Topo &T, const Cam &C, Scratch S, cudaStream_t stream);
@@ -110,5 +127,29 @@ cudaError_t bwd_rays(const Topo &T, const Field &Fd, const Cam &C, const Integ &
                      const float4 *dL, const long long *ray_off, const unsigned long long *keys,
                      const int *hleaf, float *g_nodal, float *g_tf, unsigned long long *err,
                      int nsm, cudaStream_t st);
+
+// Cubed-sphere shell (ocr_shell.cu)
+cudaError_t shell_cull(const int4 *geo, int N, const Shell &S, const Cam &C, int4 *rect,
+                       unsigned char *visible, unsigned long long *stats, cudaStream_t st);
+// count pass (fill = false): segments per ray into counts, and, when stats is
+// given, the longest list into stats[kStatMaxHits]; fill pass: the keys, at
+// most key_cap of them (a list that would pass key_cap is a device error)
+cudaError_t shell_pairs(bool fill, const int4 *geo, int N, const Shell &S, const Cam &C,
+                        const int4 *rect, const long long *leaf_off, const int *chunk_leaf,
+                        long long npairs, int *counts, const long long *ray_off, int *cursor,
+                        unsigned long long *keys, long long key_cap, unsigned long long *stats,
+                        cudaStream_t st);
+// per-CTA warps and dynamic shared memory of shell_rays for rays of up to cap
+// segments (cap a power of two, 32..kShellMaxCap); shell_rays_prepare raises the
+// kernel's shared-memory limit to the largest of these and must run before the
+// first launch
+constexpr int kShellMaxCap = 4096;
+int shell_ray_warps(int cap);
+size_t shell_ray_smem(int cap);
+cudaError_t shell_rays_prepare();
+cudaError_t shell_rays(const int4 *geo, int N, const Shell &S, const Field &Fd, const Cam &C,
+                       const Integ &I, const long long *ray_off, long long npix,
+                       const unsigned long long *keys, long long key_cap, int cap, float4 *rgba,
+                       int *counts, unsigned long long *stats, int nsm, cudaStream_t st);
 
 }  // namespace ocr

@@ -96,16 +96,20 @@ struct TF {
   float s_min, inv;
 };
 
-// (kappa, q_r, q_g, q_b) at parameter tau: piecewise-linear transfer function
-// of the field value, constant outside the knot range.
-__device__ __forceinline__ float4 medium(const Cubic &c, const TF &tf, float tau) {
-  const float s = fmaf(fmaf(fmaf(c.p3, tau, c.p2), tau, c.p1), tau, c.p0);
+// (kappa, q_r, q_g, q_b) of the field value s: piecewise-linear transfer
+// function, constant outside the knot range.
+__device__ __forceinline__ float4 tf_lookup(const TF &tf, float s) {
   float z = (s - tf.s_min) * tf.inv;
   z = fminf(fmaxf(z, 0.f), 7.f);
   const int k = min((int)z, 6);
   const float w = z - (float)k;
   const float4 a = tf.v[k], d = tf.s[k];
   return make_float4(fmaf(w, d.x, a.x), fmaf(w, d.y, a.y), fmaf(w, d.z, a.z), fmaf(w, d.w, a.w));
+}
+
+// The medium at parameter tau of a segment through a cube leaf.
+__device__ __forceinline__ float4 medium(const Cubic &c, const TF &tf, float tau) {
+  return tf_lookup(tf, fmaf(fmaf(fmaf(c.p3, tau, c.p2), tau, c.p1), tau, c.p0));
 }
 
 // Right-hand side of Eq. 2.29 for the state Y = (A, B_r, B_g, B_b).
@@ -157,7 +161,8 @@ __device__ __forceinline__ float4 lin4(float a, float4 x, float b, float4 y) {
 // (A, B) of one segment of world length dx: RK4 x nsteps, or DOPRI5 inside
 // the midpoint bisection of Algorithm 1, walked far half first so that each
 // accepted piece is nearer than everything accumulated so far.
-__device__ float4 integrate_segment(const Cubic &cu, const TF &tf, float dx, const Integ &I,
+template <class Fld>
+__device__ float4 integrate_segment(const Fld &cu, const TF &tf, float dx, const Integ &I,
                                     int &steps) {
   float4 acc = seg_identity();
   if (I.method == 0) {
@@ -288,24 +293,16 @@ __device__ __forceinline__ int4 empty_rect() { return make_int4(0, -1, 0, -1); }
 // Pixel rectangle of the camera-space bounding box of the cube [lo, lo+h]^3:
 // the box is mapped by X = (t, u, v/n)^T (x - o) (an affine map, so its AABB is
 // centre +- half-extent), clipped to the visible depth range, and projected.
-__device__ int4 box_rect(const Cam &c, float3 lo, float h) {
-  const float hh = 0.5f * h;
-  const float cx = lo.x + hh - c.o[0], cy = lo.y + hh - c.o[1], cz = lo.z + hh - c.o[2];
-  float X[3], E[3];
-  const float *rows[3] = {c.t, c.u, c.vn};
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    const float *R = rows[r];
-    X[r] = fmaf(R[0], cx, fmaf(R[1], cy, R[2] * cz));
-    E[r] = hh * (fabsf(R[0]) + fabsf(R[1]) + fabsf(R[2]));
-  }
-  const float zlo = fmaxf(X[2] - E[2], c.ortho ? 0.f : c.n);
-  const float zhi = fminf(X[2] + E[2], c.f);
+// Pixel rectangle of the camera-space box [blo, bhi]: clipped to the visible
+// depth range, its corners projected, the pixel centres inside kept.
+__device__ int4 project_box(const Cam &c, const float *blo, const float *bhi) {
+  const float zlo = fmaxf(blo[2], c.ortho ? 0.f : c.n);
+  const float zhi = fminf(bhi[2], c.f);
   if (!(zlo <= zhi)) return empty_rect();
   float pmin[2], pmax[2];
 #pragma unroll
   for (int a = 0; a < 2; ++a) {
-    const float x0 = X[a] - E[a], x1 = X[a] + E[a];
+    const float x0 = blo[a], x1 = bhi[a];
     float lo_p, hi_p;
     if (c.ortho) {
       lo_p = x0 / c.ell;
@@ -324,6 +321,22 @@ __device__ int4 box_rect(const Cam &c, float3 lo, float h) {
   const float j0 = fmaxf(ceilf(pmin[1]), 0.f), j1 = fminf(floorf(pmax[1]), hl);
   if (!(i0 <= i1 && j0 <= j1)) return empty_rect();
   return make_int4((int)i0, (int)i1, (int)j0, (int)j1);
+}
+
+__device__ int4 box_rect(const Cam &c, float3 lo, float h) {
+  const float hh = 0.5f * h;
+  const float cx = lo.x + hh - c.o[0], cy = lo.y + hh - c.o[1], cz = lo.z + hh - c.o[2];
+  float blo[3], bhi[3];
+  const float *rows[3] = {c.t, c.u, c.vn};
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const float *R = rows[r];
+    const float X = fmaf(R[0], cx, fmaf(R[1], cy, R[2] * cz));
+    const float E = hh * (fabsf(R[0]) + fabsf(R[1]) + fabsf(R[2]));
+    blo[r] = X - E;
+    bhi[r] = X + E;
+  }
+  return project_box(c, blo, bhi);
 }
 
 

@@ -1,0 +1,529 @@
+// Cubed-sphere shell forests (six trees, the equiangular map, degree-2 data)
+// on sm_103a.
+//
+// A shell leaf is bounded by four planes through the centre (constant xi or
+// eta of its tree) and two spheres (constant zeta), so a ray meets it in at
+// most two intervals and the Morton order of the leaves is no longer the
+// order along a ray.  The render therefore builds per-ray segment lists:
+//   shell_cull    - per leaf: the camera-space AABB of its 8 mapped corners,
+//                   widened by r_out (1 - cos phi) (every point of the leaf
+//                   lies that close to the corners' hull), projected to its
+//                   pixel rectangle (Sec. 3.1, Sec. 2.2);
+//   shell_pairs   - over the (leaf, pixel) pairs of the rectangles (the prefix
+//                   sum of rectangle areas cuts them into equal CTA chunks):
+//                   ray / leaf intersection, segments counted per ray, then,
+//                   after a scan, written to the ray's list with the entry
+//                   depth alpha_in as the sort key (ties by (tree, Morton
+//                   key) through the leaf index);
+//   shell_rays    - one warp per ray: sort the list (bitonic, in shared
+//                   memory), integrate every segment (RK4 or Algorithm 1 with
+//                   DOPRI5 / Gauss-2 / Simpson, the field through the inverse
+//                   map and the degree-2 interpolation), resolve overlaps by
+//                   cut (Eq. 2.20) and average (Eq. 2.21), and merge nearest
+//                   first with Eq. 2.14 into the pixel I = A I_b + B.
+#include "ocr_common.h"
+#include "ocr_device.cuh"
+
+namespace ocr {
+namespace {
+
+// One leaf's geometry, float32: its tree frame, the tangents of its four
+// planes and its two radii (read from the shared tables).
+struct LeafShell {
+  float n[3], e1[3], e2[3];
+  float ta0, ta1, tb0, tb1;
+  float rin, rout;
+  int level;
+};
+
+__device__ __forceinline__ LeafShell leaf_shell(const Shell &S, int4 g) {
+  LeafShell q;
+  q.level = g.w & 255;
+  const int tree = g.w >> 8, sz = 1 << (S.L - q.level);
+  const float *fr = S.frames + 9 * tree;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    q.n[c] = __ldg(fr + c);
+    q.e1[c] = __ldg(fr + 3 + c);
+    q.e2[c] = __ldg(fr + 6 + c);
+  }
+  q.ta0 = __ldg(S.tan_tab + g.x);
+  q.ta1 = __ldg(S.tan_tab + g.x + sz);
+  q.tb0 = __ldg(S.tan_tab + g.y);
+  q.tb1 = __ldg(S.tan_tab + g.y + sz);
+  q.rin = __ldg(S.rad_tab + g.z);
+  q.rout = __ldg(S.rad_tab + g.z + sz);
+  return q;
+}
+
+__device__ __forceinline__ float dot3(const float *a, float3 b) {
+  return fmaf(a[0], b.x, fmaf(a[1], b.y, a[2] * b.z));
+}
+
+// Intervals of the ray o + alpha r inside the leaf, clipped to [amin, amax],
+// nearest first; returns their number (0..2).  The cone: x . m >= 0 for the
+// lower planes and <= 0 for the upper ones, m = e - T n; each crossing is
+// -(o . m) / (r . m) computed from (T, e, n) alone, so neighbours agree bit
+// for bit.  The spheres: alpha = -b -+ sqrt((R^2 - |p|^2) / |r|^2), b = o.r / |r|^2,
+// p = o - b r.
+__device__ __forceinline__ int shell_ray_leaf(const LeafShell &q, float3 org, float3 dir,
+                                              float amin, float amax, float *a_in, float *a_out) {
+  float t0 = amin, t1 = amax;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const float *e = s < 2 ? q.e1 : q.e2;
+    const float T = s == 0 ? q.ta0 : s == 1 ? q.ta1 : s == 2 ? q.tb0 : q.tb1;
+    const float m[3] = {fmaf(-T, q.n[0], e[0]), fmaf(-T, q.n[1], e[1]), fmaf(-T, q.n[2], e[2])};
+    const float g0 = dot3(m, org), g1 = dot3(m, dir);
+    const bool upper = (s & 1) != 0;
+    if (g1 == 0.f) {
+      if ((upper ? -g0 : g0) < 0.f) return 0;  // parallel to the plane and outside
+      continue;
+    }
+    const float a = -g0 / g1;
+    if ((upper ? -g1 : g1) > 0.f)
+      t0 = fmaxf(t0, a);
+    else
+      t1 = fminf(t1, a);
+  }
+  const float rr = fmaf(dir.x, dir.x, fmaf(dir.y, dir.y, dir.z * dir.z));
+  const float b = fmaf(org.x, dir.x, fmaf(org.y, dir.y, org.z * dir.z)) / rr;
+  const float px = fmaf(-b, dir.x, org.x), py = fmaf(-b, dir.y, org.y), pz = fmaf(-b, dir.z, org.z);
+  const float pp = fmaf(px, px, fmaf(py, py, pz * pz));
+  const float hout = fmaf(q.rout, q.rout, -pp);
+  if (!(hout > 0.f)) return 0;
+  const float so = sqrtf(hout / rr);
+  t0 = fmaxf(t0, -b - so);
+  t1 = fminf(t1, -b + so);
+  const float hin = fmaf(q.rin, q.rin, -pp);
+  int n = 0;
+  if (hin > 0.f) {
+    const float si = sqrtf(hin / rr);
+    const float c0 = fminf(t1, -b - si), c1 = fmaxf(t0, -b + si);
+    if (c0 > t0) {
+      a_in[n] = t0;
+      a_out[n] = c0;
+      ++n;
+    }
+    if (t1 > c1) {
+      a_in[n] = c1;
+      a_out[n] = t1;
+      ++n;
+    }
+  } else if (t1 > t0) {
+    a_in[0] = t0;
+    a_out[0] = t1;
+    n = 1;
+  }
+  return n;
+}
+
+// ----------------------------------------------------------------- culling --
+__global__ void __launch_bounds__(256)
+    shell_cull_kernel(const int4 *__restrict__ geo, int N, Shell S, Cam c, int4 *rect,
+                      unsigned char *visible, unsigned long long *stats) {
+  int nvis = 0;
+  const float tn = sqrtf(c.t[0] * c.t[0] + c.t[1] * c.t[1] + c.t[2] * c.t[2]);
+  const float un = sqrtf(c.u[0] * c.u[0] + c.u[1] * c.u[1] + c.u[2] * c.u[2]);
+  const float vn = sqrtf(c.vn[0] * c.vn[0] + c.vn[1] * c.vn[1] + c.vn[2] * c.vn[2]);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    const LeafShell q = leaf_shell(S, __ldg(geo + k));
+    float d[4][3], cs[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      const float ta = (cc & 1) ? q.ta1 : q.ta0, tb = (cc & 2) ? q.tb1 : q.tb0;
+      float nn = 0.f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        d[cc][a] = fmaf(tb, q.e2[a], fmaf(ta, q.e1[a], q.n[a]));
+        nn = fmaf(d[cc][a], d[cc][a], nn);
+      }
+      const float inv = 1.f / sqrtf(nn);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        d[cc][a] *= inv;
+        cs[a] += d[cc][a];
+      }
+    }
+    const float csn = 1.f / sqrtf(cs[0] * cs[0] + cs[1] * cs[1] + cs[2] * cs[2]);
+    float cmin = 1.f;
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc)
+      cmin = fminf(cmin, (d[cc][0] * cs[0] + d[cc][1] * cs[1] + d[cc][2] * cs[2]) * csn);
+    const float delta = q.rout * (1.f - cmin);
+    float blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    const float *rows[3] = {c.t, c.u, c.vn};
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) {
+      const float r = (cc & 4) ? q.rout : q.rin;
+      const float x = fmaf(r, d[cc & 3][0], -c.o[0]), y = fmaf(r, d[cc & 3][1], -c.o[1]),
+                  z = fmaf(r, d[cc & 3][2], -c.o[2]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float X = fmaf(rows[a][0], x, fmaf(rows[a][1], y, rows[a][2] * z));
+        blo[a] = fminf(blo[a], X);
+        bhi[a] = fmaxf(bhi[a], X);
+      }
+    }
+    const float ext[3] = {delta * tn, delta * un, delta * vn};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      blo[a] -= ext[a];
+      bhi[a] += ext[a];
+    }
+    const int4 r = project_box(c, blo, bhi);
+    rect[k] = r;
+    const bool vis = r.x <= r.y;
+    if (vis && visible) visible[k] = 1;
+    nvis += vis;
+  }
+  // one counter update per warp
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nvis += __shfl_down_sync(0xffffffffu, nvis, o);
+  if ((threadIdx.x & 31) == 0 && nvis) atomicAdd(stats + kStatVisible, (unsigned long long)nvis);
+}
+
+// ------------------------------------------------------- segment lists --
+template <bool FILL>
+__global__ void __launch_bounds__(kPairChunk)
+    shell_pairs_kernel(const int4 *__restrict__ geo, int N, Shell S, Cam c,
+                       const int4 *__restrict__ rect, const long long *__restrict__ leaf_off,
+                       const int *__restrict__ chunk_leaf, long long npairs, int *counts,
+                       const long long *__restrict__ ray_off, int *cursor,
+                       unsigned long long *keys, long long key_cap, unsigned long long *stats) {
+  const long long p = (long long)blockIdx.x * kPairChunk + threadIdx.x;
+  if (p >= npairs) return;
+  const long long nch = (npairs + kPairChunk - 1) / kPairChunk;
+  int lo = chunk_leaf[blockIdx.x];
+  int hi = (blockIdx.x + 1 < nch) ? chunk_leaf[blockIdx.x + 1] + 1 : N;
+  while (lo + 1 < hi) {  // the last leaf whose offset is <= p
+    const int mid = (lo + hi) >> 1;
+    if (leaf_off[mid] <= p) lo = mid; else hi = mid;
+  }
+  const int leaf = lo;
+  const int4 r = rect[leaf];
+  const long long local = p - leaf_off[leaf];
+  const int rw = r.y - r.x + 1;
+  const int i = r.x + (int)(local % rw), j = r.z + (int)(local / rw);
+  const long long pix = (long long)j * c.w + i;
+  float3 org, dir;
+  pixel_ray(c, i, j, org, dir);
+  float ai[2], ao[2];
+  const int n = shell_ray_leaf(leaf_shell(S, __ldg(geo + leaf)), org, dir, c.amin, c.amax, ai, ao);
+  if (!n) return;
+  if (!FILL) {
+    atomicAdd(counts + pix, n);
+  } else {
+    const long long at = ray_off[pix] + atomicAdd(cursor + pix, n);
+    if (at + n > key_cap || at + n > ray_off[pix + 1]) {  // more than counted and planned
+      atomicAdd(stats + kStatErrors, 1ull);
+      return;
+    }
+    for (int t = 0; t < n; ++t)  // alpha_in >= 0: its bits sort like the value
+      keys[at + t] = (unsigned long long)__float_as_uint(ai[t]) << 32 |
+                     (unsigned)(2 * leaf + t);
+  }
+}
+
+__global__ void __launch_bounds__(256) max_count_kernel(const int *counts, long long n,
+                                                        unsigned long long *stats) {
+  int m = 0;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x)
+    m = max(m, counts[k]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(stats + kStatMaxHits, (unsigned long long)m);
+}
+
+// -------------------------------------------------------------- the field --
+// The field along one segment, tau in [0, 1] from the far end to the near end:
+// the point's coordinates in the tree frame (x.n, x.e1, x.e2) are affine in
+// tau; the local coordinates follow from the inverse map,
+//   u = (2/pi) (atan(x.e1 / x.n) - atan(ta)) / h
+//     = (2/pi) atan2(x.e1 - ta x.n, x.n + ta x.e1) / h,
+//   w = (|x| - r_in) / (r_out - r_in),
+// then the degree-2 Lagrange interpolation of the 27 nodal values.
+struct ShellSeg {
+  float pf[3], dp[3];
+  float ta, tb, ka, rin, kr;
+  float nd[27];
+};
+
+__device__ __forceinline__ void quad_basis(float t, float *l) {
+  l[0] = 2.f * (t - 0.5f) * (t - 1.f);
+  l[1] = -4.f * t * (t - 1.f);
+  l[2] = 2.f * t * (t - 0.5f);
+}
+
+__device__ __forceinline__ float4 medium(const ShellSeg &g, const TF &tf, float tau) {
+  const float pn = fmaf(tau, g.dp[0], g.pf[0]), p1 = fmaf(tau, g.dp[1], g.pf[1]),
+              p2 = fmaf(tau, g.dp[2], g.pf[2]);
+  const float u = atan2f(fmaf(-g.ta, pn, p1), fmaf(g.ta, p1, pn)) * g.ka;
+  const float v = atan2f(fmaf(-g.tb, pn, p2), fmaf(g.tb, p2, pn)) * g.ka;
+  const float w = (sqrtf(fmaf(pn, pn, fmaf(p1, p1, p2 * p2))) - g.rin) * g.kr;
+  float lu[3], lv[3], lw[3];
+  quad_basis(u, lu);
+  quad_basis(v, lv);
+  quad_basis(w, lw);
+  float s = 0.f;
+#pragma unroll
+  for (int cz = 0; cz < 3; ++cz) {
+    float sz = 0.f;
+#pragma unroll
+    for (int by = 0; by < 3; ++by) {
+      const float *r = g.nd + 9 * cz + 3 * by;
+      sz = fmaf(lv[by], fmaf(lu[0], r[0], fmaf(lu[1], r[1], lu[2] * r[2])), sz);
+    }
+    s = fmaf(lw[cz], sz, s);
+  }
+  return tf_lookup(tf, s);
+}
+
+// ---------------------------------------------------------- one ray, one warp --
+// Eq. 2.20 (1 - A^f formed as -expm1(f ln A)) and Eq. 2.21.
+__device__ __forceinline__ float4 seg_cut(float4 s, float f) {
+  const float la = logf(s.x);
+  const float ratio = la == 0.f ? f : expm1f(f * la) / expm1f(la);
+  return make_float4(expf(f * la), s.y * ratio, s.z * ratio, s.w * ratio);
+}
+
+__device__ __forceinline__ float4 seg_average(float4 a, float4 b) {
+  return make_float4(sqrtf(a.x * b.x), 0.5f * (a.y + b.y), 0.5f * (a.z + b.z), 0.5f * (a.w + b.w));
+}
+
+// near segment N on [a0, a1] and far segment F on [b0, b1] with b0 < a1: the
+// pieces before, inside and after the overlap, the overlapped ones averaged
+__device__ float4 resolve_overlap(float4 N, float2 in, float4 F, float2 iF) {
+  const float e = fminf(in.y, iF.y), LN = in.y - in.x, LF = iF.y - iF.x;
+  float4 r = seg_identity();
+  if (iF.x > in.x) r = seg_cut(N, (iF.x - in.x) / LN);
+  r = seg_combine(r, seg_average(seg_cut(N, (e - iF.x) / LN), seg_cut(F, (e - iF.x) / LF)));
+  if (in.y > e)
+    r = seg_combine(r, seg_cut(N, (in.y - e) / LN));
+  else if (iF.y > e)
+    r = seg_combine(r, seg_cut(F, (iF.y - e) / LF));
+  return r;
+}
+
+__global__ void shell_rays_kernel(const int4 *__restrict__ geo, int N, Shell S, Field Fd, Cam c,
+                                  Integ I,
+                                  const long long *__restrict__ ray_off, long long npix,
+                                  const unsigned long long *__restrict__ keys, long long key_cap,
+                                  int cap, float4 *rgba, int *counts,
+                                  unsigned long long *stats) {
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  __shared__ float4 s_tfv[8], s_tfs[8];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  if (tid < 8) {
+    const float4 v = Fd.tf[tid];
+    const float4 w = Fd.tf[tid < 7 ? tid + 1 : 7];
+    s_tfv[tid] = v;
+    s_tfs[tid] = make_float4(w.x - v.x, w.y - v.y, w.z - v.z, w.w - v.w);
+  }
+  __syncthreads();
+  const TF tf{s_tfv, s_tfs, Fd.s_min, Fd.inv_ds7};
+  float4 *val = reinterpret_cast<float4 *>(s_raw) + (size_t)wid * cap;
+  unsigned long long *key =
+      reinterpret_cast<unsigned long long *>(reinterpret_cast<float4 *>(s_raw) + (size_t)nw * cap) +
+      (size_t)wid * cap;
+  float2 *iv = reinterpret_cast<float2 *>(key);  // the intervals replace the keys once sorted
+  const float bg[3] = {I.bg[0], I.bg[1], I.bg[2]};
+  int steps = 0, segs = 0, errs = 0;
+  const long long nwarp = (long long)gridDim.x * nw;
+  for (long long pix = (long long)blockIdx.x * nw + wid; pix < npix; pix += nwarp) {
+    const long long h0 = ray_off[pix];
+    const int n = (int)(ray_off[pix + 1] - h0);
+    if (counts && lane == 0) counts[pix] = n;
+    if (n == 0) {
+      if (lane == 0) rgba[pix] = make_float4(bg[0], bg[1], bg[2], 0.f);
+      continue;
+    }
+    if (n > cap || h0 + n > key_cap) {  // larger than planned: not rendered
+      if (lane == 0) {
+        ++errs;
+        rgba[pix] = make_float4(bg[0], bg[1], bg[2], 0.f);
+      }
+      continue;
+    }
+    int P = 32;
+    while (P < n) P <<= 1;
+    for (int k = lane; k < P; k += 32) key[k] = k < n ? keys[h0 + k] : ~0ull;
+    __syncwarp();
+    for (int sz = 2; sz <= P; sz <<= 1)  // bitonic sort, nearest first
+      for (int st = sz >> 1; st > 0; st >>= 1) {
+        for (int k = lane; k < P; k += 32) {
+          const int m = k ^ st;
+          if (m > k) {
+            const bool up = (k & sz) == 0;
+            const unsigned long long a = key[k], b = key[m];
+            if ((a > b) == up) {
+              key[k] = b;
+              key[m] = a;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    const int i = (int)(pix % c.w), j = (int)(pix / c.w);
+    float3 org, dir;
+    pixel_ray(c, i, j, org, dir);
+    const float rl = sqrtf(fmaf(dir.x, dir.x, fmaf(dir.y, dir.y, dir.z * dir.z)));
+    for (int k = lane; k < n; k += 32) {
+      const unsigned lp = (unsigned)(key[k] & 0xffffffffu);
+      const int leaf = (int)(lp >> 1), piece = (int)(lp & 1u);
+      if (leaf >= N) {  // not a list entry written by the fill pass
+        ++errs;
+        val[k] = seg_identity();
+        iv[k] = make_float2(0.f, 0.f);
+        continue;
+      }
+      const LeafShell q = leaf_shell(S, __ldg(geo + leaf));
+      float ai[2], ao[2];
+      if (shell_ray_leaf(q, org, dir, c.amin, c.amax, ai, ao) <= piece) {
+        ++errs;
+        val[k] = seg_identity();
+        iv[k] = make_float2(0.f, 0.f);
+        continue;
+      }
+      const float a_in = ai[piece], a_out = ao[piece];
+      ShellSeg g;
+      const float3 pf = make_float3(fmaf(a_out, dir.x, org.x), fmaf(a_out, dir.y, org.y),
+                                    fmaf(a_out, dir.z, org.z));
+      const float da = a_in - a_out;
+      const float3 dv = make_float3(da * dir.x, da * dir.y, da * dir.z);
+      g.pf[0] = dot3(q.n, pf);
+      g.pf[1] = dot3(q.e1, pf);
+      g.pf[2] = dot3(q.e2, pf);
+      g.dp[0] = dot3(q.n, dv);
+      g.dp[1] = dot3(q.e1, dv);
+      g.dp[2] = dot3(q.e2, dv);
+      g.ta = q.ta0;
+      g.tb = q.tb0;
+      g.ka = ldexpf(0.63661977236758134f, q.level);  // (2 / pi) / h
+      g.rin = q.rin;
+      g.kr = 1.f / (q.rout - q.rin);
+      const float *nd = Fd.nodal + 27 * (size_t)leaf;
+#pragma unroll
+      for (int a = 0; a < 27; ++a) g.nd[a] = __ldg(nd + a);
+      val[k] = integrate_segment(g, tf, (a_out - a_in) * rl, I, steps);
+      iv[k] = make_float2(a_in, a_out);
+    }
+    segs += n;
+    __syncwarp();
+    // overlaps of consecutive segments are rounding slivers, if any
+    bool ov = false;
+    for (int k = lane; k + 1 < n; k += 32) ov |= iv[k + 1].x < iv[k].y;
+    float4 acc = seg_identity();
+    if (!__any_sync(0xffffffffu, ov)) {
+      // lane l folds a contiguous run, then the runs are combined in order
+      const int q = (n + 31) >> 5, k0 = lane * q, k1 = min(k0 + q, n);
+      for (int k = k0; k < k1; ++k) acc = seg_combine(acc, val[k]);
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        float4 y;
+        y.x = __shfl_down_sync(0xffffffffu, acc.x, o);
+        y.y = __shfl_down_sync(0xffffffffu, acc.y, o);
+        y.z = __shfl_down_sync(0xffffffffu, acc.z, o);
+        y.w = __shfl_down_sync(0xffffffffu, acc.w, o);
+        if ((lane & (2 * o - 1)) == 0) acc = seg_combine(acc, y);
+      }
+    } else if (lane == 0) {
+      float4 cur = val[0];
+      float2 ci = iv[0];
+      for (int k = 1; k < n; ++k) {
+        const float4 nv = val[k];
+        const float2 ni = iv[k];
+        if (ni.x < ci.y) {
+          cur = resolve_overlap(cur, ci, nv, ni);
+          ci = make_float2(ci.x, fmaxf(ci.y, ni.y));
+        } else {
+          acc = seg_combine(acc, cur);
+          cur = nv;
+          ci = ni;
+        }
+      }
+      acc = seg_combine(acc, cur);
+    }
+    if (lane == 0)
+      rgba[pix] = make_float4(fmaf(acc.x, bg[0], acc.y), fmaf(acc.x, bg[1], acc.z),
+                              fmaf(acc.x, bg[2], acc.w), 1.f - acc.x);
+    __syncwarp();
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xffffffffu, steps, o);
+  if (lane == 0) {
+    atomicAdd(stats + kStatSegments, (unsigned long long)segs);
+    atomicAdd(stats + kStatSteps, (unsigned long long)steps);
+    if (errs) atomicAdd(stats + kStatErrors, (unsigned long long)errs);
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- launchers --
+cudaError_t shell_cull(const int4 *geo, int N, const Shell &S, const Cam &C, int4 *rect,
+                       unsigned char *visible, unsigned long long *stats, cudaStream_t st) {
+  const int grid = (N + 255) / 256 > 8192 ? 8192 : (N + 255) / 256;
+  shell_cull_kernel<<<grid > 0 ? grid : 1, 256, 0, st>>>(geo, N, S, C, rect, visible, stats);
+  return cudaGetLastError();
+}
+
+cudaError_t shell_pairs(bool fill, const int4 *geo, int N, const Shell &S, const Cam &C,
+                        const int4 *rect, const long long *leaf_off, const int *chunk_leaf,
+                        long long npairs, int *counts, const long long *ray_off, int *cursor,
+                        unsigned long long *keys, long long key_cap, unsigned long long *stats,
+                        cudaStream_t st) {
+  if (npairs > 0) {
+    const long long nblk = (npairs + kPairChunk - 1) / kPairChunk;
+    if (nblk > 0x7fffffffll) return cudaErrorInvalidValue;
+    if (fill)
+      shell_pairs_kernel<true><<<(unsigned)nblk, kPairChunk, 0, st>>>(
+          geo, N, S, C, rect, leaf_off, chunk_leaf, npairs, counts, ray_off, cursor, keys,
+          key_cap, stats);
+    else
+      shell_pairs_kernel<false><<<(unsigned)nblk, kPairChunk, 0, st>>>(
+          geo, N, S, C, rect, leaf_off, chunk_leaf, npairs, counts, ray_off, cursor, keys,
+          key_cap, stats);
+  }
+  if (!fill && stats) {  // the longest list, for planning
+    const long long npix = (long long)C.w * C.h;
+    const long long g = (npix + 255) / 256;
+    max_count_kernel<<<(unsigned)(g > 4096 ? 4096 : (g > 0 ? g : 1)), 256, 0, st>>>(counts, npix,
+                                                                                 stats);
+  }
+  return cudaGetLastError();
+}
+
+int shell_ray_warps(int cap) {
+  const size_t per = (size_t)cap * (sizeof(float4) + sizeof(unsigned long long));
+  int w = (int)((96u << 10) / per);
+  return w < 1 ? 1 : (w > 8 ? 8 : w);
+}
+
+size_t shell_ray_smem(int cap) {
+  return (size_t)shell_ray_warps(cap) * cap * (sizeof(float4) + sizeof(unsigned long long));
+}
+
+cudaError_t shell_rays_prepare() {
+  size_t most = 0;  // the largest launch any list capacity asks for
+  for (int cap = 32; cap <= kShellMaxCap; cap <<= 1) most = most > shell_ray_smem(cap) ? most : shell_ray_smem(cap);
+  return cudaFuncSetAttribute(shell_rays_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)most);
+}
+
+cudaError_t shell_rays(const int4 *geo, int N, const Shell &S, const Field &Fd, const Cam &C,
+                       const Integ &I, const long long *ray_off, long long npix,
+                       const unsigned long long *keys, long long key_cap, int cap, float4 *rgba,
+                       int *counts, unsigned long long *stats, int nsm, cudaStream_t st) {
+  if (cap < 32 || cap > kShellMaxCap || (cap & (cap - 1))) return cudaErrorInvalidValue;
+  const size_t smem = shell_ray_smem(cap);
+  const int warps = shell_ray_warps(cap);
+  const long long need = (npix + warps - 1) / warps;
+  const long long grid = need < (long long)nsm * 8 ? need : (long long)nsm * 8;
+  shell_rays_kernel<<<(unsigned)(grid > 0 ? grid : 1), warps * 32, smem, st>>>(
+      geo, N, S, Fd, C, I, ray_off, npix, keys, key_cap, cap, rgba, counts, stats);
+  return cudaGetLastError();
+}
+
+}  // namespace ocr

@@ -28,7 +28,13 @@ class Renderer:
         self.device = torch.device(device)
         self.forest = forest
         s = _stream_ptr(None)
-        self.h = capi.build_forest(forest.level, forest.anchor, forest.max_level, stream=s)
+        if forest.geometry == "shell":
+            self.h = capi.build_forest(forest.level, forest.anchor, forest.max_level, stream=s,
+                                       geometry=capi.GEOM_SHELL, tree=forest.tree,
+                                       frames=forest.meta["frames"], r0=forest.meta["r0"],
+                                       r1=forest.meta["r1"])
+        else:
+            self.h = capi.build_forest(forest.level, forest.anchor, forest.max_level, stream=s)
         self.nodal = torch.from_numpy(np.ascontiguousarray(forest.nodal, np.float32)).to(self.device)
         self.tf = torch.from_numpy(np.ascontiguousarray(tf.knots, np.float32)).to(self.device)
         self.s_min, self.s_max = float(tf.s_min), float(tf.s_max)
@@ -116,7 +122,7 @@ class Renderer:
         return out, st
 
     def backward(self, grad_rgba: torch.Tensor, stream=None):
-        """dL/d(nodal) [N, 8] and dL/d(knots) [8, 4] for the data, camera and
+        """dL/d(nodal) [N, 8] and dL/d(knots) [8, 4] (cube forests) for the data, camera and
         integrator last set, given dL/d(rgba) [h, w, 4] on the device."""
         g = grad_rgba.detach().to(self.device, torch.float32).contiguous()
         gn = torch.empty_like(self.nodal)
