@@ -282,7 +282,8 @@ def cull(forest, tf, cam, band_px: float = 4e-3):
 def render(forest, tf, cam, integ: dict, rows=None, bg=(0.0, 0.0, 0.0), nthreads: int = 0,
            band_px: float = 4e-3, band_rel: float = 1e-5):
     """Render the listed rows (default: all).  Returns rgba [nrows, w, 4] (FP64),
-    per-ray segment counts, per-ray tie flags, total segments and RK steps."""
+    per-ray segment counts, per-ray tie flags and tie counts (leaves of the ray
+    with a decision inside the tie band), total segments and RK steps."""
     of = OracleForest(forest, tf)
     cs = camera_struct(cam)
     ist = integrator_struct(integ, bg)
@@ -301,7 +302,7 @@ def render(forest, tf, cam, integ: dict, rows=None, bg=(0.0, 0.0, 0.0), nthreads
                              int(nthreads), C.byref(steps))
     if total < 0:
         raise MemoryError("oracle render: allocation failed")
-    return {"rgba": rgba, "counts": counts, "uncertain": unc.astype(bool),
+    return {"rgba": rgba, "counts": counts, "uncertain": unc.astype(bool), "ties": unc.astype(int),
             "segments": int(total), "steps": int(steps.value), "rows": rows_arr}
 
 

@@ -799,19 +799,21 @@ int64_t orc_render(const orc_forest *F, const orc_camera *C, const orc_integrato
       for (int i = 0; i < W; ++i) {
         double org[3], dir[3], amin, amax;
         orc_pixel_ray(C, i, j, org, dir, &amin, &amax);
-        int ns = 0, unc = 0;
+        int ns = 0, nties = 0;
         for (int q = cstart[i]; q < cstart[i + 1]; ++q) {
           int l = pl[pord[q]];
           double a_in[2], a_out[2];
-          int nhit = orc_ray_leaf_tie(F, l, org, dir, amin, amax, a_in, a_out, band_rel, &unc);
-          if (!nhit) continue;
+          int tie = 0;
+          int nhit = orc_ray_leaf_tie(F, l, org, dir, amin, amax, a_in, a_out, band_rel, &tie);
           /* a hit outside the leaf's own rectangle, or within band_px of its edge */
-          {
+          if (nhit) {
             const double *pe = pext + 4 * (size_t)l;
             if (i < pe[0] + band_px || i > pe[1] - band_px || j < pe[2] + band_px ||
                 j > pe[3] - band_px)
-              unc = 1;
+              tie = 1;
           }
+          nties += tie;
+          if (!nhit) continue;
           for (int k = 0; k < nhit; ++k) {
             if (ns == cap_seg) {
               cap_seg *= 2;
@@ -828,7 +830,7 @@ int64_t orc_render(const orc_forest *F, const orc_camera *C, const orc_integrato
         size_t pix = (size_t)r * W + i;
         composite(sg, ns, I->bg, rgba + 4 * pix);
         if (counts) counts[pix] = ns;
-        if (uncertain) uncertain[pix] = (uint8_t)unc;
+        if (uncertain) uncertain[pix] = (uint8_t)(nties < 255 ? nties : 255);
         total += ns;
       }
     }

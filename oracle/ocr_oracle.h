@@ -119,8 +119,9 @@ void orc_cull(const orc_forest *F, const orc_camera *C, int32_t *rect, uint8_t *
               uint8_t *uncertain, double band_px);
 
 /* Render the listed image rows (rows == NULL: all rows).  rgba[nrows*w*4],
- * counts[nrows*w] (segments per ray), uncertain[nrows*w] (a decision of this
- * ray fell within the tie band).  Returns the total number of segments, or a
+ * counts[nrows*w] (segments per ray), uncertain[nrows*w] (the number of this
+ * ray's leaves, saturating at 255, with a decision within the tie band; each
+ * such leaf can change the ray's segment count by at most two).  Returns the total number of segments, or a
  * negative number on allocation failure. */
 int64_t orc_render(const orc_forest *F, const orc_camera *C, const orc_integrator *I,
                    const int *rows, int nrows, double *rgba, int32_t *counts,

@@ -40,6 +40,8 @@ def _compare(forest, tf, cam, integ, rows=None, bg=(0.0, 0.0, 0.0), max_unc_frac
     assert unc.mean() <= max_unc_frac, f"tie-band rays {unc.mean():.3%}"
     bad = (counts != ref["counts"]) & ~unc
     assert not bad.any(), f"{bad.sum()} rays with different segment counts"
+    # on a tie-band ray, each tie-band leaf changes the count by at most two
+    assert (np.abs(counts - ref["counts"]) <= 2 * ref["ties"]).all()
     cull = O.cull(forest, tf, cam, band_px=BAND_PX)
     vis = st["visible"].cpu().numpy().astype(bool)
     assert not ((vis != cull["visible"]) & ~cull["uncertain"]).any()
