@@ -209,16 +209,20 @@ int ocr_prune_noalloc(const int32_t *d_leaf_geo, int64_t nleaves, int max_level,
 
 /* Gradient of a loss L(rgba) with respect to the nodal values and the
  * transfer-function knots (Sec. 2.3-2.4, Eqs. 2.14 and 2.29-2.31 in reverse
- * mode), for the forest, data, integrator and camera last set.
+ * mode), for the forest, data, integrator and the first camera last set.
  * d_dL_drgba [h*w*4] float32 (device): dL/d(I_r, I_g, I_b, alpha) per pixel;
- * rays whose four entries are zero are skipped.  d_grad_nodal [nleaves*8] and
- * d_grad_tf [8*4] float32 (device) are overwritten with dL/d(nodal) and
- * dL/d(knots).  Segments are recomputed, not taken from a previous render;
- * each ray's segments are put in front-to-back order by their mirrored Morton
- * key.  RK4 and DOPRI5 only (OCR_ERR_UNSUPPORTED otherwise); a ray with more
- * than 512 segments is skipped and reported as OCR_ERR_DEVICE.  Blocks the
- * host three times (sizes of the pair space and of the hit lists, the error
- * word). */
+ * rays whose four entries are zero are skipped.  d_grad_nodal [nleaves*8]
+ * (cube) or [nleaves*27] (shell) and d_grad_tf [8*4] float32 (device) are
+ * overwritten with dL/d(nodal) and dL/d(knots).  Segments are recomputed, not
+ * taken from a previous render.  Cube: each ray's segments are put in
+ * front-to-back order by their mirrored Morton key; a ray with more than 512
+ * segments is skipped and reported as OCR_ERR_DEVICE.  Shell: the render's
+ * per-ray lists are rebuilt in the first camera's scratch (so a backward call
+ * must not overlap a render of the same forest on another stream) and ordered
+ * by entry depth; overlapping rounding slivers are combined as if they did
+ * not overlap.  RK4 and DOPRI5 only (OCR_ERR_UNSUPPORTED otherwise).  Blocks
+ * the host (cube: three times, for the sizes of the pair space and of the hit
+ * lists and the error word; shell: once, for the error word). */
 int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_nodal,
                         float *d_grad_tf, void *stream);
 

@@ -20,6 +20,7 @@
 //                      tree), the transfer function and the trilinear weights.
 #include "ocr_common.h"
 #include "ocr_device.cuh"
+#include "ocr_shell.cuh"
 
 namespace ocr {
 namespace {
@@ -213,37 +214,72 @@ struct TfGrad {
   }
 };
 
-struct SegAdj {
-  Cubic cu;
-  float3 uf, du;    // reference coordinates at the far end, change to the near end
-  float g8[8];      // adjoint of the 8 nodal values
-};
-
-// adjoint of the medium at tau: vbar = dL/d(kappa, q) there
-__device__ __forceinline__ void medium_bwd(SegAdj &S, const TF &tf, float tau, float4 vbar,
-                                           TfGrad &tg) {
-  const float s = fmaf(fmaf(fmaf(S.cu.p3, tau, S.cu.p2), tau, S.cu.p1), tau, S.cu.p0);
+// dL/ds at a field value s from vbar = dL/d(kappa, q) (the transfer
+// function's slope; zero where it is clamped), after crediting the knots
+__device__ __forceinline__ float tf_bwd(const TF &tf, float s, float4 vbar, TfGrad &tg) {
   const float zr = (s - tf.s_min) * tf.inv;
   const bool inside = zr > 0.f && zr < 7.f;
   const float z = fminf(fmaxf(zr, 0.f), 7.f);
   const int k = min((int)z, 6);
   const float w = z - (float)k;
   tg.add(k, w, vbar);
-  if (!inside) return;
+  if (!inside) return 0.f;
   const float4 d = tf.s[k];
-  const float sb = (vbar.x * d.x + vbar.y * d.y + vbar.z * d.z + vbar.w * d.w) * tf.inv;
-  const float u = fmaf(tau, S.du.x, S.uf.x), v = fmaf(tau, S.du.y, S.uf.y),
-              ww = fmaf(tau, S.du.z, S.uf.z);
-  const float u0 = 1.f - u, v0 = 1.f - v, w0 = 1.f - ww;
-  S.g8[0] = fmaf(sb, u0 * v0 * w0, S.g8[0]);
-  S.g8[1] = fmaf(sb, u * v0 * w0, S.g8[1]);
-  S.g8[2] = fmaf(sb, u0 * v * w0, S.g8[2]);
-  S.g8[3] = fmaf(sb, u * v * w0, S.g8[3]);
-  S.g8[4] = fmaf(sb, u0 * v0 * ww, S.g8[4]);
-  S.g8[5] = fmaf(sb, u * v0 * ww, S.g8[5]);
-  S.g8[6] = fmaf(sb, u0 * v * ww, S.g8[6]);
-  S.g8[7] = fmaf(sb, u * v * ww, S.g8[7]);
+  return (vbar.x * d.x + vbar.y * d.y + vbar.z * d.z + vbar.w * d.w) * tf.inv;
 }
+
+// Segment through a cube leaf: the field is the cubic in tau; the adjoint of
+// the 8 corner values goes through the trilinear weights.
+struct SegAdj {
+  Cubic cu;
+  float3 uf, du;    // reference coordinates at the far end, change to the near end
+  float g8[8];      // adjoint of the 8 nodal values
+  __device__ __forceinline__ float4 kq(const TF &tf, float tau) const {
+    return medium(cu, tf, tau);
+  }
+  // adjoint of the medium at tau: vbar = dL/d(kappa, q) there
+  __device__ __forceinline__ void bwd(const TF &tf, float tau, float4 vbar, TfGrad &tg) {
+    const float s = fmaf(fmaf(fmaf(cu.p3, tau, cu.p2), tau, cu.p1), tau, cu.p0);
+    const float sb = tf_bwd(tf, s, vbar, tg);
+    if (sb == 0.f) return;
+    const float u = fmaf(tau, du.x, uf.x), v = fmaf(tau, du.y, uf.y), ww = fmaf(tau, du.z, uf.z);
+    const float u0 = 1.f - u, v0 = 1.f - v, w0 = 1.f - ww;
+    g8[0] = fmaf(sb, u0 * v0 * w0, g8[0]);
+    g8[1] = fmaf(sb, u * v0 * w0, g8[1]);
+    g8[2] = fmaf(sb, u0 * v * w0, g8[2]);
+    g8[3] = fmaf(sb, u * v * w0, g8[3]);
+    g8[4] = fmaf(sb, u0 * v0 * ww, g8[4]);
+    g8[5] = fmaf(sb, u * v0 * ww, g8[5]);
+    g8[6] = fmaf(sb, u0 * v * ww, g8[6]);
+    g8[7] = fmaf(sb, u * v * ww, g8[7]);
+  }
+};
+
+// Segment through a shell leaf: the field through the inverse map and the
+// degree-2 interpolation; the adjoint of the 27 nodal values is kept in this
+// thread's column of a shared-memory array (g27[q * stride]).
+struct ShellAdj {
+  ShellSeg g;
+  float *g27;
+  int stride;
+  __device__ __forceinline__ float4 kq(const TF &tf, float tau) const {
+    return medium(g, tf, tau);
+  }
+  __device__ __forceinline__ void bwd(const TF &tf, float tau, float4 vbar, TfGrad &tg) {
+    float lu[3], lv[3], lw[3];
+    const float s = shell_field(g, tau, lu, lv, lw);
+    const float sb = tf_bwd(tf, s, vbar, tg);
+    if (sb == 0.f) return;
+#pragma unroll
+    for (int cz = 0; cz < 3; ++cz)
+#pragma unroll
+      for (int by = 0; by < 3; ++by) {
+        const float f = sb * lw[cz] * lv[by];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) g27[(9 * cz + 3 * by + ax) * stride] += f * lu[ax];
+      }
+  }
+};
 
 __device__ __forceinline__ float dot4(float4 a, float4 b) {
   return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
@@ -259,37 +295,38 @@ __device__ __forceinline__ float4 scale4(float a, float4 x) {
 }
 
 // adjoint of one RK4 step from (1, 0) with nodes at t0, t0 + dt/2, t0 + dt
-__device__ void rk4_step_bwd(SegAdj &S, const TF &tf, float t0, float dt, float H, float4 ybar,
+template <class SA>
+__device__ void rk4_step_bwd(SA &S, const TF &tf, float t0, float dt, float H, float4 ybar,
                              TfGrad &tg) {
   const float4 one = seg_identity();
-  const float4 k0 = medium(S.cu, tf, t0), kh = medium(S.cu, tf, t0 + 0.5f * dt),
-               k1 = medium(S.cu, tf, t0 + dt);
+  const float4 k0 = S.kq(tf, t0), kh = S.kq(tf, t0 + 0.5f * dt), k1 = S.kq(tf, t0 + dt);
   const float4 Y1 = one, K1 = rhs(k0, Y1);
   const float4 Y2 = axpy(0.5f * H, K1, one), K2 = rhs(kh, Y2);
   const float4 Y3 = axpy(0.5f * H, K2, one), K3 = rhs(kh, Y3);
   const float4 Y4 = axpy(H, K3, one);
   float4 K4b = scale4(H / 6.f, ybar), K3b = scale4(H / 3.f, ybar), K2b = scale4(H / 3.f, ybar),
          K1b = scale4(H / 6.f, ybar);
-  medium_bwd(S, tf, t0 + dt, node_vbar(K4b, Y4), tg);
+  S.bwd(tf, t0 + dt, node_vbar(K4b, Y4), tg);
   K3b = axpy(H, scale4(-k1.x, K4b), K3b);
   float4 vh = node_vbar(K3b, Y3);
   K2b = axpy(0.5f * H, scale4(-kh.x, K3b), K2b);
   const float4 v2 = node_vbar(K2b, Y2);
   vh = make_float4(vh.x + v2.x, vh.y + v2.y, vh.z + v2.z, vh.w + v2.w);
-  medium_bwd(S, tf, t0 + 0.5f * dt, vh, tg);
+  S.bwd(tf, t0 + 0.5f * dt, vh, tg);
   K1b = axpy(0.5f * H, scale4(-kh.x, K2b), K1b);
-  medium_bwd(S, tf, t0, node_vbar(K1b, Y1), tg);
+  S.bwd(tf, t0, node_vbar(K1b, Y1), tg);
 }
 
 // adjoint of one Dormand-Prince step from (1, 0) (stages 1..6; the seventh
 // stage only feeds the error estimate)
-__device__ void dopri_step_bwd(SegAdj &S, const TF &tf, float t0, float dtau, float H,
+template <class SA>
+__device__ void dopri_step_bwd(SA &S, const TF &tf, float t0, float dtau, float H,
                                float4 ybar, TfGrad &tg) {
   const float4 one = seg_identity();
   const float tt[6] = {t0, fmaf(dp::c2, dtau, t0), fmaf(dp::c3, dtau, t0),
                        fmaf(dp::c4, dtau, t0), fmaf(dp::c5, dtau, t0), t0 + dtau};
   float4 kq[6], Y[6], K[6];
-  for (int i = 0; i < 6; ++i) kq[i] = medium(S.cu, tf, tt[i]);
+  for (int i = 0; i < 6; ++i) kq[i] = S.kq(tf, tt[i]);
   Y[0] = one;
   K[0] = rhs(kq[0], Y[0]);
   Y[1] = axpy(H * dp::a21, K[0], one);
@@ -322,7 +359,7 @@ __device__ void dopri_step_bwd(SegAdj &S, const TF &tf, float t0, float dtau, fl
   for (int i = 0; i < 6; ++i) Kb[i] = scale4(H * b[i], ybar);
 #pragma unroll
   for (int i = 5; i >= 0; --i) {
-    medium_bwd(S, tf, tt[i], node_vbar(Kb[i], Y[i]), tg);
+    S.bwd(tf, tt[i], node_vbar(Kb[i], Y[i]), tg);
     const float4 Yb = scale4(-kq[i].x, Kb[i]);
 #pragma unroll
     for (int j = 0; j < i; ++j) Kb[j] = axpy(H * a[i][j], Yb, Kb[j]);
@@ -339,8 +376,92 @@ __device__ __forceinline__ float4 step_adjoint(float Tm, float4 Gm, float4 Ib, f
                      Tm * Ib.z);
 }
 
-// Adjoint of one segment: near transmittance T, far aggregate G, its value
-// A_seg; the steps are revisited far to near with the forward's step tree.
+// The steps of one segment, revisited far to near with the forward's step
+// tree: near transmittance Tn, far aggregate G (with the background folded in
+// through bg), the segment's own transmittance Aseg.
+template <class SA>
+__device__ void segment_steps_bwd(SA &S, const TF &tf, float dx, const Integ &I, float Tn,
+                                  float4 G, float Aseg, float4 Ib, float ab, TfGrad &tg) {
+  float4 acc = seg_identity();  // steps farther than the current one
+  if (I.method == 0) {
+    const int n = I.nsteps;
+    const float H = dx / (float)n, dt = 1.f / (float)n;
+    for (int s = 0; s < n; ++s) {
+      const float t0 = (float)s * dt, dts = (s + 1 == n) ? 1.f - t0 : dt;
+      const float4 Sm = rk4_step(H, S.kq(tf, t0), S.kq(tf, t0 + 0.5f * dts), S.kq(tf, t0 + dts));
+      const float4 accn = seg_combine(Sm, acc);
+      const float Tm = Tn * (Aseg / accn.x);
+      const float4 Gm = seg_combine(acc, G);
+      rk4_step_bwd(S, tf, t0, dts, H, step_adjoint(Tm, Gm, Ib, ab, I.bg), tg);
+      acc = accn;
+    }
+    return;
+  }
+  int depth = 0;
+  unsigned idx = 0;
+  float4 kq0 = S.kq(tf, 0.f);
+  const float4 one = seg_identity();
+  for (;;) {
+    const float dtau = ldexpf(1.f, -depth);
+    const float t0 = (float)idx * dtau;
+    const float H = dx * dtau;
+    // the forward step (value, split test) exactly as integrate_segment
+    const float4 kq2 = S.kq(tf, fmaf(dp::c2, dtau, t0));
+    const float4 kq3 = S.kq(tf, fmaf(dp::c3, dtau, t0));
+    const float4 kq4 = S.kq(tf, fmaf(dp::c4, dtau, t0));
+    const float4 kq5 = S.kq(tf, fmaf(dp::c5, dtau, t0));
+    const float4 kq6 = S.kq(tf, t0 + dtau);
+    const float4 K1 = rhs(kq0, one);
+    const float4 K2 = rhs(kq2, axpy(H * dp::a21, K1, one));
+    const float4 K3 = rhs(kq3, axpy(H, lin4(dp::a31, K1, dp::a32, K2), one));
+    float4 t = lin4(dp::a41, K1, dp::a42, K2);
+    t = axpy(dp::a43, K3, t);
+    const float4 K4 = rhs(kq4, axpy(H, t, one));
+    t = lin4(dp::a51, K1, dp::a52, K2);
+    t = axpy(dp::a53, K3, t);
+    t = axpy(dp::a54, K4, t);
+    const float4 K5 = rhs(kq5, axpy(H, t, one));
+    t = lin4(dp::a61, K1, dp::a62, K2);
+    t = axpy(dp::a63, K3, t);
+    t = axpy(dp::a64, K4, t);
+    t = axpy(dp::a65, K5, t);
+    const float4 K6 = rhs(kq6, axpy(H, t, one));
+    t = lin4(dp::b1, K1, dp::b3, K3);
+    t = axpy(dp::b4, K4, t);
+    t = axpy(dp::b5, K5, t);
+    t = axpy(dp::b6, K6, t);
+    const float4 Y5 = axpy(H, t, one);
+    const float4 K7 = rhs(kq6, Y5);
+    float4 e = lin4(dp::e1, K1, dp::e3, K3);
+    e = axpy(dp::e4, K4, e);
+    e = axpy(dp::e5, K5, e);
+    e = axpy(dp::e6, K6, e);
+    e = axpy(dp::e7, K7, e);
+    const float err = H * fmaxf(fmaxf(fabsf(e.x), fabsf(e.y)), fmaxf(fabsf(e.z), fabsf(e.w)));
+    const float kmax =
+        fmaxf(fmaxf(fmaxf(kq0.x, kq2.x), fmaxf(kq3.x, kq4.x)), fmaxf(kq5.x, kq6.x));
+    if (depth < I.max_depth && (H * kmax > I.c_rk || err > I.tol)) {
+      ++depth;
+      idx <<= 1;
+      continue;
+    }
+    const float4 accn = seg_combine(Y5, acc);
+    const float Tm = Tn * (Aseg / accn.x);
+    const float4 Gm = seg_combine(acc, G);
+    dopri_step_bwd(S, tf, t0, dtau, H, step_adjoint(Tm, Gm, Ib, ab, I.bg), tg);
+    acc = accn;
+    kq0 = kq6;
+    ++idx;
+    while (depth > 0 && !(idx & 1u)) {
+      idx >>= 1;
+      --depth;
+    }
+    if (depth == 0) break;
+  }
+}
+
+// Adjoint of one segment of a cube leaf: near transmittance T, far aggregate
+// G, its value A_seg.
 __device__ void segment_bwd(const Topo &T, const Field &Fd, const Cam &c, const Integ &I,
                             const TF &tf, int leaf, float3 org, float3 dir, float3 inv,
                             float scale, float Tn, float4 G, float Aseg, float4 Ib, float ab,
@@ -361,89 +482,95 @@ __device__ void segment_bwd(const Topo &T, const Field &Fd, const Cam &c, const 
   S.cu = field_cubic(Fd.nodal + 8 * (size_t)leaf, S.uf, S.du);
 #pragma unroll
   for (int q = 0; q < 8; ++q) S.g8[q] = 0.f;
-  float4 acc = seg_identity();  // steps farther than the current one
-  if (I.method == 0) {
-    const int n = I.nsteps;
-    const float H = dx / (float)n, dt = 1.f / (float)n;
-    for (int s = 0; s < n; ++s) {
-      const float t0 = (float)s * dt, dts = (s + 1 == n) ? 1.f - t0 : dt;
-      const float4 Sm = rk4_step(H, medium(S.cu, tf, t0), medium(S.cu, tf, t0 + 0.5f * dts),
-                                 medium(S.cu, tf, t0 + dts));
-      const float4 accn = seg_combine(Sm, acc);
-      const float Tm = Tn * (Aseg / accn.x);
-      const float4 Gm = seg_combine(acc, G);
-      rk4_step_bwd(S, tf, t0, dts, H, step_adjoint(Tm, Gm, Ib, ab, I.bg), tg);
-      acc = accn;
-    }
-  } else {
-    int depth = 0;
-    unsigned idx = 0;
-    float4 kq0 = medium(S.cu, tf, 0.f);
-    const float4 one = seg_identity();
-    for (;;) {
-      const float dtau = ldexpf(1.f, -depth);
-      const float t0 = (float)idx * dtau;
-      const float H = dx * dtau;
-      // the forward step (value, split test) exactly as integrate_segment
-      const float4 kq2 = medium(S.cu, tf, fmaf(dp::c2, dtau, t0));
-      const float4 kq3 = medium(S.cu, tf, fmaf(dp::c3, dtau, t0));
-      const float4 kq4 = medium(S.cu, tf, fmaf(dp::c4, dtau, t0));
-      const float4 kq5 = medium(S.cu, tf, fmaf(dp::c5, dtau, t0));
-      const float4 kq6 = medium(S.cu, tf, t0 + dtau);
-      const float4 K1 = rhs(kq0, one);
-      const float4 K2 = rhs(kq2, axpy(H * dp::a21, K1, one));
-      const float4 K3 = rhs(kq3, axpy(H, lin4(dp::a31, K1, dp::a32, K2), one));
-      float4 t = lin4(dp::a41, K1, dp::a42, K2);
-      t = axpy(dp::a43, K3, t);
-      const float4 K4 = rhs(kq4, axpy(H, t, one));
-      t = lin4(dp::a51, K1, dp::a52, K2);
-      t = axpy(dp::a53, K3, t);
-      t = axpy(dp::a54, K4, t);
-      const float4 K5 = rhs(kq5, axpy(H, t, one));
-      t = lin4(dp::a61, K1, dp::a62, K2);
-      t = axpy(dp::a63, K3, t);
-      t = axpy(dp::a64, K4, t);
-      t = axpy(dp::a65, K5, t);
-      const float4 K6 = rhs(kq6, axpy(H, t, one));
-      t = lin4(dp::b1, K1, dp::b3, K3);
-      t = axpy(dp::b4, K4, t);
-      t = axpy(dp::b5, K5, t);
-      t = axpy(dp::b6, K6, t);
-      const float4 Y5 = axpy(H, t, one);
-      const float4 K7 = rhs(kq6, Y5);
-      float4 e = lin4(dp::e1, K1, dp::e3, K3);
-      e = axpy(dp::e4, K4, e);
-      e = axpy(dp::e5, K5, e);
-      e = axpy(dp::e6, K6, e);
-      e = axpy(dp::e7, K7, e);
-      const float err = H * fmaxf(fmaxf(fabsf(e.x), fabsf(e.y)), fmaxf(fabsf(e.z), fabsf(e.w)));
-      const float kmax =
-          fmaxf(fmaxf(fmaxf(kq0.x, kq2.x), fmaxf(kq3.x, kq4.x)), fmaxf(kq5.x, kq6.x));
-      if (depth < I.max_depth && (H * kmax > I.c_rk || err > I.tol)) {
-        ++depth;
-        idx <<= 1;
-        continue;
-      }
-      const float4 accn = seg_combine(Y5, acc);
-      const float Tm = Tn * (Aseg / accn.x);
-      const float4 Gm = seg_combine(acc, G);
-      dopri_step_bwd(S, tf, t0, dtau, H, step_adjoint(Tm, Gm, Ib, ab, I.bg), tg);
-      acc = accn;
-      kq0 = kq6;
-      ++idx;
-      while (depth > 0 && !(idx & 1u)) {
-        idx >>= 1;
-        --depth;
-      }
-      if (depth == 0) break;
-    }
-  }
+  segment_steps_bwd(S, tf, dx, I, Tn, G, Aseg, Ib, ab, tg);
 #pragma unroll
   for (int q = 0; q < 8; ++q)
     if (S.g8[q] != 0.f) atomicAdd(g_nodal + 8 * (size_t)leaf + q, S.g8[q]);
 }
 
 // ------------------------------------------------------------ ray adjoint --
+// Over a ray's n segment values val[0..n) (nearest first), one warp: the
+// transmittance of the nearer segments Tk (exclusive product of A), the
+// segment's own Ak, and, in place of val, the aggregate of the farther ones
+// (suffix fold with Eq. 2.14) -- no group inverse.
+__device__ void near_far_scans(int n, int lane, float4 *val, float *Tk, float *Ak) {
+  float carry = 1.f;
+  const int nb = (n + 31) / 32;
+  for (int b = 0; b < nb; ++b) {
+    const int k = b * 32 + lane;
+    const float a = k < n ? val[k].x : 1.f;
+    float x = a;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x *= y;
+    }
+    float ex = __shfl_up_sync(0xffffffffu, x, 1);
+    if (lane == 0) ex = 1.f;
+    if (k < n) {
+      Tk[k] = carry * ex;
+      Ak[k] = a;
+    }
+    carry *= __shfl_sync(0xffffffffu, x, 31);
+  }
+  __syncwarp();
+  float4 fc = seg_identity();
+  for (int b = nb - 1; b >= 0; --b) {
+    const int k = b * 32 + lane;
+    float4 x = k < n ? val[k] : seg_identity();
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      float4 y;
+      y.x = __shfl_down_sync(0xffffffffu, x.x, o);
+      y.y = __shfl_down_sync(0xffffffffu, x.y, o);
+      y.z = __shfl_down_sync(0xffffffffu, x.z, o);
+      y.w = __shfl_down_sync(0xffffffffu, x.w, o);
+      if (lane + o < 32) x = seg_combine(x, y);
+    }
+    float4 nx;
+    nx.x = __shfl_down_sync(0xffffffffu, x.x, 1);
+    nx.y = __shfl_down_sync(0xffffffffu, x.y, 1);
+    nx.z = __shfl_down_sync(0xffffffffu, x.z, 1);
+    nx.w = __shfl_down_sync(0xffffffffu, x.w, 1);
+    if (lane == 31) nx = seg_identity();
+    const float4 Gk = seg_combine(nx, fc);
+    float4 x0;
+    x0.x = __shfl_sync(0xffffffffu, x.x, 0);
+    x0.y = __shfl_sync(0xffffffffu, x.y, 0);
+    x0.z = __shfl_sync(0xffffffffu, x.z, 0);
+    x0.w = __shfl_sync(0xffffffffu, x.w, 0);
+    __syncwarp();
+    if (k < n) val[k] = Gk;
+    fc = seg_combine(x0, fc);
+  }
+  __syncwarp();
+}
+
+// bitonic sort of keys[0..P) (P a power of two >= 32) by one warp, ascending,
+// carrying an int payload when lf is not null
+__device__ void warp_sort(unsigned long long *key, int *lf, int P, int lane) {
+  for (int sz = 2; sz <= P; sz <<= 1)
+    for (int st = sz >> 1; st > 0; st >>= 1) {
+      for (int k = lane; k < P; k += 32) {
+        const int m = k ^ st;
+        if (m > k) {
+          const bool up = (k & sz) == 0;
+          const unsigned long long a = key[k], b = key[m];
+          if ((a > b) == up) {
+            key[k] = b;
+            key[m] = a;
+            if (lf) {
+              const int t = lf[k];
+              lf[k] = lf[m];
+              lf[m] = t;
+            }
+          }
+        }
+      }
+      __syncwarp();
+    }
+}
+
 constexpr int kBwdWarps = 4;
 
 __global__ void __launch_bounds__(kBwdWarps * 32)
@@ -492,25 +619,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32)
       lf[k] = k < n ? hleaf[h0 + k] : -1;
     }
     __syncwarp();
-    // bitonic sort of (key, leaf) by key: nearest first
-    for (int sz = 2; sz <= P; sz <<= 1)
-      for (int st = sz >> 1; st > 0; st >>= 1) {
-        for (int k = lane; k < P; k += 32) {
-          const int m = k ^ st;
-          if (m > k) {
-            const bool up = (k & sz) == 0;
-            const unsigned long long a = key[k], b = key[m];
-            if ((a > b) == up) {
-              key[k] = b;
-              key[m] = a;
-              const int t = lf[k];
-              lf[k] = lf[m];
-              lf[m] = t;
-            }
-          }
-        }
-        __syncwarp();
-      }
+    warp_sort(key, lf, P, lane);  // (key, leaf) by key: nearest first
     const int i = (int)(pix % c.w), j = (int)(pix / c.w);
     float3 org, dir;
     pixel_ray(c, i, j, org, dir);
@@ -521,64 +630,115 @@ __global__ void __launch_bounds__(kBwdWarps * 32)
     for (int k = lane; k < n; k += 32)
       val[k] = leaf_segment(T, Fd, c, I, tf, lf[k], org, dir, inv, scale, steps);
     __syncwarp();
-    // near transmittance: exclusive product of A, nearest first
-    float carry = 1.f;
-    const int nb = (n + 31) / 32;
-    for (int b = 0; b < nb; ++b) {
-      const int k = b * 32 + lane;
-      const float a = k < n ? val[k].x : 1.f;
-      float x = a;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const float y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x *= y;
-      }
-      float ex = __shfl_up_sync(0xffffffffu, x, 1);
-      if (lane == 0) ex = 1.f;
-      if (k < n) {
-        Tk[k] = carry * ex;
-        Ak[k] = a;
-      }
-      carry *= __shfl_sync(0xffffffffu, x, 31);
-    }
-    __syncwarp();
-    // far aggregate of the segments behind each one: suffix fold, farthest first
-    float4 fc = seg_identity();
-    for (int b = nb - 1; b >= 0; --b) {
-      const int k = b * 32 + lane;
-      float4 x = k < n ? val[k] : seg_identity();
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        float4 y;
-        y.x = __shfl_down_sync(0xffffffffu, x.x, o);
-        y.y = __shfl_down_sync(0xffffffffu, x.y, o);
-        y.z = __shfl_down_sync(0xffffffffu, x.z, o);
-        y.w = __shfl_down_sync(0xffffffffu, x.w, o);
-        if (lane + o < 32) x = seg_combine(x, y);
-      }
-      float4 nx;
-      nx.x = __shfl_down_sync(0xffffffffu, x.x, 1);
-      nx.y = __shfl_down_sync(0xffffffffu, x.y, 1);
-      nx.z = __shfl_down_sync(0xffffffffu, x.z, 1);
-      nx.w = __shfl_down_sync(0xffffffffu, x.w, 1);
-      if (lane == 31) nx = seg_identity();
-      const float4 Gk = seg_combine(nx, fc);
-      float4 x0;
-      x0.x = __shfl_sync(0xffffffffu, x.x, 0);
-      x0.y = __shfl_sync(0xffffffffu, x.y, 0);
-      x0.z = __shfl_sync(0xffffffffu, x.z, 0);
-      x0.w = __shfl_sync(0xffffffffu, x.w, 0);
-      __syncwarp();
-      if (k < n) val[k] = Gk;
-      fc = seg_combine(x0, fc);
-    }
-    __syncwarp();
+    near_far_scans(n, lane, val, Tk, Ak);
     // adjoint of every segment
     const float4 gp = dL[pix];
     const float4 Ib = make_float4(gp.x, gp.y, gp.z, 0.f);
     for (int k = lane; k < n; k += 32)
       segment_bwd(T, Fd, c, I, tf, lf[k], org, dir, inv, scale, Tk[k], val[k], Ak[k], Ib, gp.w,
                   g_nodal, tg);
+    __syncwarp();
+  }
+  tg.flush();
+  __syncthreads();
+  if (tid < 32 && s_g[tid] != 0.f) atomicAdd(g_tf + tid, s_g[tid]);
+}
+
+// The same for a shell forest: the lists hold (alpha_in, leaf, piece) keys;
+// the segment adjoint goes through the inverse map and the degree-2 weights,
+// the 27 nodal adjoints of a segment collected in shared memory.  Overlap
+// resolution (cut and average of rounding slivers) is treated as plain
+// combination here.
+__global__ void __launch_bounds__(kBwdWarps * 32)
+    shell_ray_backward_kernel(const int4 *__restrict__ geo, int N, Shell S, Field Fd, Cam c,
+                              Integ I, const float4 *dL, const long long *ray_off,
+                              const unsigned long long *keys, long long key_cap, int cap,
+                              float *g_nodal, float *g_tf, unsigned long long *err) {
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  float4 *s_val = reinterpret_cast<float4 *>(s_raw);
+  unsigned long long *s_key = reinterpret_cast<unsigned long long *>(s_val + nw * cap);
+  int *s_lf = reinterpret_cast<int *>(s_key + nw * cap);
+  float *s_g27 = reinterpret_cast<float *>(s_lf + nw * cap);  // [27][blockDim.x]
+  __shared__ float4 s_tfv[8], s_tfs[8];
+  __shared__ float s_g[32];
+  if (tid < 8) {
+    const float4 v = Fd.tf[tid];
+    const float4 w = Fd.tf[tid < 7 ? tid + 1 : 7];
+    s_tfv[tid] = v;
+    s_tfs[tid] = make_float4(w.x - v.x, w.y - v.y, w.z - v.z, w.w - v.w);
+  }
+  if (tid < 32) s_g[tid] = 0.f;
+  __syncthreads();
+  float4 *val = s_val + wid * cap;
+  unsigned long long *key = s_key + wid * cap;
+  int *lf = s_lf + wid * cap;
+  float *Tk = reinterpret_cast<float *>(key);  // reuses the key array after sorting
+  float *Ak = reinterpret_cast<float *>(key) + cap;
+  const TF tf{s_tfv, s_tfs, Fd.s_min, Fd.inv_ds7};
+  TfGrad tg;
+  tg.s_g = s_g;
+  const long long npix = (long long)c.w * c.h;
+  const long long nwarp = (long long)gridDim.x * nw;
+  for (long long pix = (long long)blockIdx.x * nw + wid; pix < npix; pix += nwarp) {
+    const long long h0 = ray_off[pix];
+    const int n = (int)(ray_off[pix + 1] - h0);
+    if (n == 0) continue;
+    if (n > cap || h0 + n > key_cap) {
+      if (lane == 0) atomicAdd(err, 1ull);
+      continue;
+    }
+    const float4 gp = dL[pix];
+    if (gp.x == 0.f && gp.y == 0.f && gp.z == 0.f && gp.w == 0.f) continue;
+    int P = 32;
+    while (P < n) P <<= 1;
+    for (int k = lane; k < P; k += 32) key[k] = k < n ? keys[h0 + k] : ~0ull;
+    __syncwarp();
+    warp_sort(key, nullptr, P, lane);
+    for (int k = lane; k < n; k += 32) lf[k] = (int)(unsigned)(key[k] & 0xffffffffu);
+    __syncwarp();
+    const int i = (int)(pix % c.w), j = (int)(pix / c.w);
+    float3 org, dir;
+    pixel_ray(c, i, j, org, dir);
+    const float rl = sqrtf(fmaf(dir.x, dir.x, fmaf(dir.y, dir.y, dir.z * dir.z)));
+    int steps = 0, bad = 0;
+    for (int k = lane; k < n; k += 32) {
+      const int leaf = lf[k] >> 1, piece = lf[k] & 1;
+      ShellSeg g;
+      float dx;
+      float2 iv;
+      if (leaf >= N ||
+          !shell_segment(S, Fd.nodal, c, __ldg(geo + leaf), leaf, piece, org, dir, rl, g, dx, iv)) {
+        ++bad;
+        val[k] = seg_identity();
+        continue;
+      }
+      val[k] = integrate_segment(g, tf, dx, I, steps);
+    }
+    __syncwarp();
+    near_far_scans(n, lane, val, Tk, Ak);
+    const float4 Ib = make_float4(gp.x, gp.y, gp.z, 0.f);
+    for (int k = lane; k < n; k += 32) {
+      const int leaf = lf[k] >> 1, piece = lf[k] & 1;
+      ShellAdj A;
+      float dx;
+      float2 iv;
+      if (leaf >= N ||
+          !shell_segment(S, Fd.nodal, c, __ldg(geo + leaf), leaf, piece, org, dir, rl, A.g, dx,
+                         iv))
+        continue;
+      A.g27 = s_g27 + tid;
+      A.stride = (int)blockDim.x;
+#pragma unroll
+      for (int q = 0; q < 27; ++q) A.g27[q * A.stride] = 0.f;
+      segment_steps_bwd(A, tf, dx, I, Tk[k], val[k], Ak[k], Ib, gp.w, tg);
+#pragma unroll
+      for (int q = 0; q < 27; ++q) {
+        const float v = A.g27[q * A.stride];
+        if (v != 0.f) atomicAdd(g_nodal + 27 * (size_t)leaf + q, v);
+      }
+    }
+    if (bad) atomicAdd(err, (unsigned long long)bad);
     __syncwarp();
   }
   tg.flush();
@@ -641,6 +801,43 @@ cudaError_t bwd_rays(const Topo &T, const Field &Fd, const Cam &C, const Integ &
   }
   ray_backward_kernel<<<nsm * 4, kBwdWarps * 32, smem, st>>>(T, Fd, C, I, dL, ray_off, keys, hleaf,
                                                             g_nodal, g_tf, err);
+  return cudaGetLastError();
+}
+
+}  // namespace ocr
+
+namespace ocr {
+
+// warps per CTA: up to kBwdWarps, within 200 KB of shared memory
+static int shell_bwd_warps(int cap) {
+  const size_t per = (size_t)cap * (sizeof(float4) + sizeof(unsigned long long) + sizeof(int)) +
+                     sizeof(float) * 27 * 32;
+  const int w = (int)((200u << 10) / per);
+  return w < 1 ? 1 : (w > kBwdWarps ? kBwdWarps : w);
+}
+
+size_t shell_bwd_smem(int cap) {
+  const int w = shell_bwd_warps(cap);
+  return (size_t)w * cap * (sizeof(float4) + sizeof(unsigned long long) + sizeof(int)) +
+         sizeof(float) * 27 * 32 * w;
+}
+
+cudaError_t shell_bwd_prepare() {
+  size_t most = 0;
+  for (int cap = 32; cap <= kShellMaxCap; cap <<= 1)
+    most = most > shell_bwd_smem(cap) ? most : shell_bwd_smem(cap);
+  return cudaFuncSetAttribute(shell_ray_backward_kernel,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+}
+
+cudaError_t shell_bwd_rays(const int4 *geo, int N, const Shell &S, const Field &Fd, const Cam &C,
+                           const Integ &I, const float4 *dL, const long long *ray_off,
+                           const unsigned long long *keys, long long key_cap, int cap,
+                           float *g_nodal, float *g_tf, unsigned long long *err, int nsm,
+                           cudaStream_t st) {
+  if (cap < 32 || cap > kShellMaxCap || (cap & (cap - 1))) return cudaErrorInvalidValue;
+  shell_ray_backward_kernel<<<nsm * 4, shell_bwd_warps(cap) * 32, shell_bwd_smem(cap), st>>>(
+      geo, N, S, Fd, C, I, dL, ray_off, keys, key_cap, cap, g_nodal, g_tf, err);
   return cudaGetLastError();
 }
 

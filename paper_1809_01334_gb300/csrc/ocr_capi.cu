@@ -372,14 +372,11 @@ int plan_shell(ocr_forest *F, CamPlan &P) {
   return dev_alloc(&P.d_keys, (size_t)(P.nhits > 0 ? P.nhits : 1), F->bytes);
 }
 
-// Enqueue one camera's render of a shell forest on st: pruning, pair space,
-// counts, list offsets, lists, then one warp per ray.  No host synchronisation.
-int enqueue_shell(ocr_forest *F, CamPlan &P, float4 *rgba, int *counts, unsigned char *visible,
-                  cudaStream_t st, bool timed, int64_t &launches) {
+// Enqueue the segment lists of one camera of a shell forest on st: pruning,
+// pair space, counts, list offsets, lists.  No host synchronisation.
+int enqueue_shell_lists(ocr_forest *F, CamPlan &P, unsigned char *visible, cudaStream_t st) {
   const long long npix = P.npix;
   const Topo T{F->d_geo, nullptr, nullptr, F->N, 0, F->L, 0};
-  const Field Fd{F->d_nodal, reinterpret_cast<const float4 *>(F->d_tf), F->s_min,
-                 7.f / (F->s_max - F->s_min)};
   OCR_CUDA(shell_cull(F->d_geo, F->N, F->shell, P.cam, P.d_rect, visible, F->d_stats, st));
   OCR_CUDA(bwd_leaf_scan(T, P.d_rect, P.d_sbsums, P.bs_cap, P.d_leaf_off, st));
   OCR_CUDA(bwd_chunk_map(P.d_leaf_off, F->N, P.d_pchunk, st));
@@ -392,6 +389,18 @@ int enqueue_shell(ocr_forest *F, CamPlan &P, float4 *rgba, int *counts, unsigned
   OCR_CUDA(shell_pairs(true, F->d_geo, F->N, F->shell, P.cam, P.d_rect, P.d_leaf_off, P.d_pchunk,
                        P.npairs, nullptr, P.d_ray_off, P.d_rcursor, P.d_keys, P.nhits,
                        F->d_stats, st));
+  return OCR_OK;
+}
+
+// Enqueue one camera's render of a shell forest on st: the segment lists, then
+// one warp per ray.  No host synchronisation.
+int enqueue_shell(ocr_forest *F, CamPlan &P, float4 *rgba, int *counts, unsigned char *visible,
+                  cudaStream_t st, bool timed, int64_t &launches) {
+  const long long npix = P.npix;
+  const Field Fd{F->d_nodal, reinterpret_cast<const float4 *>(F->d_tf), F->s_min,
+                 7.f / (F->s_max - F->s_min)};
+  const int rc = enqueue_shell_lists(F, P, visible, st);
+  if (rc) return rc;
   if (timed) OCR_CUDA(cudaEventRecord(F->ev[1], st));
   if (timed) OCR_CUDA(cudaEventRecord(F->ev[2], st));
   OCR_CUDA(shell_rays(F->d_geo, F->N, F->shell, Fd, P.cam, F->integ, P.d_ray_off, npix, P.d_keys,
@@ -662,6 +671,7 @@ int ocr_set_camera(ocr_forest *F, const ocr_camera *cams, int ncams) {
       if (rc) return rc;
     }
     OCR_CUDA(shell_rays_prepare());
+    OCR_CUDA(shell_bwd_prepare());
     F->has_cam = true;
     return OCR_OK;
   }
@@ -861,9 +871,29 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
   if (!F || !d_dL_drgba || !d_grad_nodal || !d_grad_tf) return OCR_ERR_INVALID;
   if (!F->has_data || !F->has_cam || !F->has_integ) return OCR_ERR_STATE;
   if (F->integ.method != OCR_RK4 && F->integ.method != OCR_DOPRI5) return OCR_ERR_UNSUPPORTED;
-  if (F->geometry != OCR_GEOM_CUBE) return OCR_ERR_UNSUPPORTED;
   if ((uintptr_t)d_dL_drgba & 15) return OCR_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
+  if (F->geometry == OCR_GEOM_SHELL) {
+    // rebuild the first camera's lists, then one warp per ray
+    CamPlan &P = F->plans[0];
+    const Field Fd{F->d_nodal, reinterpret_cast<const float4 *>(F->d_tf), F->s_min,
+                   7.f / (F->s_max - F->s_min)};
+    OCR_CUDA(cudaMemsetAsync(d_grad_nodal, 0, sizeof(float) * 27 * (size_t)F->N, st));
+    OCR_CUDA(cudaMemsetAsync(d_grad_tf, 0, sizeof(float) * 32, st));
+    OCR_CUDA(cudaMemsetAsync(F->d_stats, 0, kStats * sizeof(unsigned long long), st));
+    OCR_CUDA(cudaMemsetAsync(F->d_err, 0, sizeof(unsigned long long), st));
+    int rc = enqueue_shell_lists(F, P, nullptr, st);
+    if (rc) return rc;
+    OCR_CUDA(shell_bwd_rays(F->d_geo, F->N, F->shell, Fd, P.cam, F->integ,
+                            reinterpret_cast<const float4 *>(d_dL_drgba), P.d_ray_off, P.d_keys,
+                            P.nhits, P.cap, d_grad_nodal, d_grad_tf, F->d_err, F->nsm, st));
+    long long *h = F->h_group_slots;
+    OCR_CUDA(cudaMemcpyAsync(h, F->d_err, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    OCR_CUDA(cudaMemcpyAsync(h + 1, F->d_stats + kStatErrors, sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, st));
+    OCR_CUDA(cudaStreamSynchronize(st));
+    return (h[0] || h[1]) ? OCR_ERR_DEVICE : OCR_OK;
+  }
   CamPlan &P0 = F->plans[0];
   const Cam &cam = P0.cam;
   const long long npix = P0.npix;

@@ -152,4 +152,15 @@ cudaError_t shell_rays(const int4 *geo, int N, const Shell &S, const Field &Fd, 
                        const unsigned long long *keys, long long key_cap, int cap, float4 *rgba,
                        int *counts, unsigned long long *stats, int nsm, cudaStream_t st);
 
+// Adjoint of a shell render (ocr_backward.cu), over lists built by shell_pairs:
+// one warp per ray, kBwdWarps warps per CTA; shell_bwd_prepare raises the
+// kernel's shared-memory limit for every list capacity
+size_t shell_bwd_smem(int cap);
+cudaError_t shell_bwd_prepare();
+cudaError_t shell_bwd_rays(const int4 *geo, int N, const Shell &S, const Field &Fd, const Cam &C,
+                           const Integ &I, const float4 *dL, const long long *ray_off,
+                           const unsigned long long *keys, long long key_cap, int cap,
+                           float *g_nodal, float *g_tf, unsigned long long *err, int nsm,
+                           cudaStream_t st);
+
 }  // namespace ocr

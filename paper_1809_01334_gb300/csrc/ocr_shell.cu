@@ -23,100 +23,10 @@
 //                   first with Eq. 2.14 into the pixel I = A I_b + B.
 #include "ocr_common.h"
 #include "ocr_device.cuh"
+#include "ocr_shell.cuh"
 
 namespace ocr {
 namespace {
-
-// One leaf's geometry, float32: its tree frame, the tangents of its four
-// planes and its two radii (read from the shared tables).
-struct LeafShell {
-  float n[3], e1[3], e2[3];
-  float ta0, ta1, tb0, tb1;
-  float rin, rout;
-  int level;
-};
-
-__device__ __forceinline__ LeafShell leaf_shell(const Shell &S, int4 g) {
-  LeafShell q;
-  q.level = g.w & 255;
-  const int tree = g.w >> 8, sz = 1 << (S.L - q.level);
-  const float *fr = S.frames + 9 * tree;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    q.n[c] = __ldg(fr + c);
-    q.e1[c] = __ldg(fr + 3 + c);
-    q.e2[c] = __ldg(fr + 6 + c);
-  }
-  q.ta0 = __ldg(S.tan_tab + g.x);
-  q.ta1 = __ldg(S.tan_tab + g.x + sz);
-  q.tb0 = __ldg(S.tan_tab + g.y);
-  q.tb1 = __ldg(S.tan_tab + g.y + sz);
-  q.rin = __ldg(S.rad_tab + g.z);
-  q.rout = __ldg(S.rad_tab + g.z + sz);
-  return q;
-}
-
-__device__ __forceinline__ float dot3(const float *a, float3 b) {
-  return fmaf(a[0], b.x, fmaf(a[1], b.y, a[2] * b.z));
-}
-
-// Intervals of the ray o + alpha r inside the leaf, clipped to [amin, amax],
-// nearest first; returns their number (0..2).  The cone: x . m >= 0 for the
-// lower planes and <= 0 for the upper ones, m = e - T n; each crossing is
-// -(o . m) / (r . m) computed from (T, e, n) alone, so neighbours agree bit
-// for bit.  The spheres: alpha = -b -+ sqrt((R^2 - |p|^2) / |r|^2), b = o.r / |r|^2,
-// p = o - b r.
-__device__ __forceinline__ int shell_ray_leaf(const LeafShell &q, float3 org, float3 dir,
-                                              float amin, float amax, float *a_in, float *a_out) {
-  float t0 = amin, t1 = amax;
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    const float *e = s < 2 ? q.e1 : q.e2;
-    const float T = s == 0 ? q.ta0 : s == 1 ? q.ta1 : s == 2 ? q.tb0 : q.tb1;
-    const float m[3] = {fmaf(-T, q.n[0], e[0]), fmaf(-T, q.n[1], e[1]), fmaf(-T, q.n[2], e[2])};
-    const float g0 = dot3(m, org), g1 = dot3(m, dir);
-    const bool upper = (s & 1) != 0;
-    if (g1 == 0.f) {
-      if ((upper ? -g0 : g0) < 0.f) return 0;  // parallel to the plane and outside
-      continue;
-    }
-    const float a = -g0 / g1;
-    if ((upper ? -g1 : g1) > 0.f)
-      t0 = fmaxf(t0, a);
-    else
-      t1 = fminf(t1, a);
-  }
-  const float rr = fmaf(dir.x, dir.x, fmaf(dir.y, dir.y, dir.z * dir.z));
-  const float b = fmaf(org.x, dir.x, fmaf(org.y, dir.y, org.z * dir.z)) / rr;
-  const float px = fmaf(-b, dir.x, org.x), py = fmaf(-b, dir.y, org.y), pz = fmaf(-b, dir.z, org.z);
-  const float pp = fmaf(px, px, fmaf(py, py, pz * pz));
-  const float hout = fmaf(q.rout, q.rout, -pp);
-  if (!(hout > 0.f)) return 0;
-  const float so = sqrtf(hout / rr);
-  t0 = fmaxf(t0, -b - so);
-  t1 = fminf(t1, -b + so);
-  const float hin = fmaf(q.rin, q.rin, -pp);
-  int n = 0;
-  if (hin > 0.f) {
-    const float si = sqrtf(hin / rr);
-    const float c0 = fminf(t1, -b - si), c1 = fmaxf(t0, -b + si);
-    if (c0 > t0) {
-      a_in[n] = t0;
-      a_out[n] = c0;
-      ++n;
-    }
-    if (t1 > c1) {
-      a_in[n] = c1;
-      a_out[n] = t1;
-      ++n;
-    }
-  } else if (t1 > t0) {
-    a_in[0] = t0;
-    a_out[0] = t1;
-    n = 1;
-  }
-  return n;
-}
 
 // ----------------------------------------------------------------- culling --
 __global__ void __launch_bounds__(256)
@@ -236,50 +146,6 @@ __global__ void __launch_bounds__(256) max_count_kernel(const int *counts, long 
   if ((threadIdx.x & 31) == 0 && m) atomicMax(stats + kStatMaxHits, (unsigned long long)m);
 }
 
-// -------------------------------------------------------------- the field --
-// The field along one segment, tau in [0, 1] from the far end to the near end:
-// the point's coordinates in the tree frame (x.n, x.e1, x.e2) are affine in
-// tau; the local coordinates follow from the inverse map,
-//   u = (2/pi) (atan(x.e1 / x.n) - atan(ta)) / h
-//     = (2/pi) atan2(x.e1 - ta x.n, x.n + ta x.e1) / h,
-//   w = (|x| - r_in) / (r_out - r_in),
-// then the degree-2 Lagrange interpolation of the 27 nodal values.
-struct ShellSeg {
-  float pf[3], dp[3];
-  float ta, tb, ka, rin, kr;
-  float nd[27];
-};
-
-__device__ __forceinline__ void quad_basis(float t, float *l) {
-  l[0] = 2.f * (t - 0.5f) * (t - 1.f);
-  l[1] = -4.f * t * (t - 1.f);
-  l[2] = 2.f * t * (t - 0.5f);
-}
-
-__device__ __forceinline__ float4 medium(const ShellSeg &g, const TF &tf, float tau) {
-  const float pn = fmaf(tau, g.dp[0], g.pf[0]), p1 = fmaf(tau, g.dp[1], g.pf[1]),
-              p2 = fmaf(tau, g.dp[2], g.pf[2]);
-  const float u = atan2f(fmaf(-g.ta, pn, p1), fmaf(g.ta, p1, pn)) * g.ka;
-  const float v = atan2f(fmaf(-g.tb, pn, p2), fmaf(g.tb, p2, pn)) * g.ka;
-  const float w = (sqrtf(fmaf(pn, pn, fmaf(p1, p1, p2 * p2))) - g.rin) * g.kr;
-  float lu[3], lv[3], lw[3];
-  quad_basis(u, lu);
-  quad_basis(v, lv);
-  quad_basis(w, lw);
-  float s = 0.f;
-#pragma unroll
-  for (int cz = 0; cz < 3; ++cz) {
-    float sz = 0.f;
-#pragma unroll
-    for (int by = 0; by < 3; ++by) {
-      const float *r = g.nd + 9 * cz + 3 * by;
-      sz = fmaf(lv[by], fmaf(lu[0], r[0], fmaf(lu[1], r[1], lu[2] * r[2])), sz);
-    }
-    s = fmaf(lw[cz], sz, s);
-  }
-  return tf_lookup(tf, s);
-}
-
 // ---------------------------------------------------------- one ray, one warp --
 // Eq. 2.20 (1 - A^f formed as -expm1(f ln A)) and Eq. 2.21.
 __device__ __forceinline__ float4 seg_cut(float4 s, float f) {
@@ -372,42 +238,19 @@ __global__ void shell_rays_kernel(const int4 *__restrict__ geo, int N, Shell S, 
     for (int k = lane; k < n; k += 32) {
       const unsigned lp = (unsigned)(key[k] & 0xffffffffu);
       const int leaf = (int)(lp >> 1), piece = (int)(lp & 1u);
-      if (leaf >= N) {  // not a list entry written by the fill pass
-        ++errs;
-        val[k] = seg_identity();
-        iv[k] = make_float2(0.f, 0.f);
-        continue;
-      }
-      const LeafShell q = leaf_shell(S, __ldg(geo + leaf));
-      float ai[2], ao[2];
-      if (shell_ray_leaf(q, org, dir, c.amin, c.amax, ai, ao) <= piece) {
-        ++errs;
-        val[k] = seg_identity();
-        iv[k] = make_float2(0.f, 0.f);
-        continue;
-      }
-      const float a_in = ai[piece], a_out = ao[piece];
       ShellSeg g;
-      const float3 pf = make_float3(fmaf(a_out, dir.x, org.x), fmaf(a_out, dir.y, org.y),
-                                    fmaf(a_out, dir.z, org.z));
-      const float da = a_in - a_out;
-      const float3 dv = make_float3(da * dir.x, da * dir.y, da * dir.z);
-      g.pf[0] = dot3(q.n, pf);
-      g.pf[1] = dot3(q.e1, pf);
-      g.pf[2] = dot3(q.e2, pf);
-      g.dp[0] = dot3(q.n, dv);
-      g.dp[1] = dot3(q.e1, dv);
-      g.dp[2] = dot3(q.e2, dv);
-      g.ta = q.ta0;
-      g.tb = q.tb0;
-      g.ka = ldexpf(0.63661977236758134f, q.level);  // (2 / pi) / h
-      g.rin = q.rin;
-      g.kr = 1.f / (q.rout - q.rin);
-      const float *nd = Fd.nodal + 27 * (size_t)leaf;
-#pragma unroll
-      for (int a = 0; a < 27; ++a) g.nd[a] = __ldg(nd + a);
-      val[k] = integrate_segment(g, tf, (a_out - a_in) * rl, I, steps);
-      iv[k] = make_float2(a_in, a_out);
+      float dx;
+      float2 ivk;
+      // an entry the fill pass did not write, or a piece the ray does not have
+      if (leaf >= N ||
+          !shell_segment(S, Fd.nodal, c, __ldg(geo + leaf), leaf, piece, org, dir, rl, g, dx, ivk)) {
+        ++errs;
+        val[k] = seg_identity();
+        iv[k] = make_float2(0.f, 0.f);
+        continue;
+      }
+      val[k] = integrate_segment(g, tf, dx, I, steps);
+      iv[k] = ivk;
     }
     segs += n;
     __syncwarp();

@@ -565,6 +565,22 @@ def preset_c3(w: int = 2048, h: int = 2048, theta: float = C3_THETA, min_level: 
     return forest, tf, cam, integ
 
 
+C5_THETA = 0.5  # calibrated once to give 1,082,535 leaves over levels 4..6
+
+
+def preset_c5(w: int = 1024, h: int = 1024, theta: float = C5_THETA, min_level: int = 4,
+              max_level: int = 6):
+    """Cubed-sphere shell, levels 4..6, degree-2 data from SH noise (degree 8),
+    perspective 45 deg at 1024^2, DOPRI5 tol 1e-5 (the differentiation
+    workload; its target is rendered from a seeded 5% perturbation)."""
+    noise = shell_noise(1809, 8)
+    forest = shell_forest(noise, min_level, max_level, theta)
+    tf = transfer_function(forest.nodal, 1334)
+    cam = perspective_camera(7, w, h, target=(0.0, 0.0, 0.0))
+    integ = {"method": "dopri5", "tol": 1e-5, "c_rk": 0.5, "max_depth": 16}
+    return forest, tf, cam, integ
+
+
 def preset_shell_small(w: int = 40, h: int = 32, min_level: int = 1, max_level: int = 3,
                        theta: float = 2.0, cam_seed: int = 7):
     noise = shell_noise(1809, 8)

@@ -1,0 +1,120 @@
+"""The CUDA adjoint on cubed-sphere shell forests (27 nodal values per leaf)
+against the FP64 oracle gradient and central differences of the FP64 forward
+oracle: relative L2 error of the gradient vectors <= 1e-3; per coordinate,
+error relative to max(|g_ref|, 1e-3 max|g_ref|) <= 1e-3.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1809_01334_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+DOPRI = {"method": "dopri5", "tol": 1e-5, "c_rk": 0.5, "max_depth": 16}
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+@pytest.mark.parametrize("integ", [{"method": "rk4", "nsteps": 4}, DOPRI])
+def test_shell_gradient_matches_oracle(integ):
+    from paper_1809_01334_gb300 import Renderer
+    f, tf, _ = I.preset_shell_small()
+    cam = I.perspective_camera(21, 24, 18, dist=(2.2, 2.6), target=(0.0, 0.0, 0.0))
+    bg = (0.1, 0.05, 0.2)
+    r = Renderer(f, tf, integ, bg=bg)
+    r.set_camera(cam)
+    W = np.random.default_rng(3).uniform(-1, 1, (cam.h, cam.w, 4)).astype(np.float32)
+    gn, gt = r.backward(torch.from_numpy(W).cuda())
+    torch.cuda.synchronize()
+    assert gn.shape == (f.nleaves, 27)
+    rn, rt = O.render_grad(f, tf, cam, integ, W.astype(np.float64), bg=bg)
+    en = _rel(gn.cpu().numpy().astype(np.float64), rn)
+    et = _rel(gt.cpu().numpy().astype(np.float64), rt)
+    assert en <= 1e-3 and et <= 1e-3, (en, et)
+    r.close()
+
+
+def test_shell_autograd_l2_loss_against_perturbed_target():
+    """The configuration of the differentiation workload at small size: L2
+    loss against a target rendered from a seeded 5% perturbation of the nodal
+    values, gradients through RenderFunction, against the oracle gradient and
+    central differences on 64 coordinates (48 nodal values of visible leaves,
+    16 knot values)."""
+    from paper_1809_01334_gb300 import Renderer, RenderFunction
+    f, tf, _ = I.preset_shell_small()
+    cam = I.perspective_camera(23, 20, 16, dist=(2.2, 2.6), target=(0.0, 0.0, 0.0))
+    r = Renderer(f, tf, DOPRI)
+    r.set_camera(cam)
+    rng = np.random.default_rng(5)
+    pert = (f.nodal * (1 + 0.05 * rng.uniform(-1, 1, f.nodal.shape))).astype(np.float32)
+    r.set_data(torch.from_numpy(pert).cuda(), r.tf.clone())
+    target, _ = r.render()
+    target = target.clone()
+    nodal = torch.from_numpy(f.nodal.copy()).cuda().requires_grad_(True)
+    knots = torch.from_numpy(tf.knots.copy()).cuda().requires_grad_(True)
+    img = RenderFunction.apply(nodal, knots, r)
+    loss = ((img - target) ** 2).sum()
+    loss.backward()
+    gn = nodal.grad.cpu().numpy().astype(np.float64)
+    gt = knots.grad.cpu().numpy().astype(np.float64)
+    W = (2.0 * (img - target)).detach().cpu().numpy().astype(np.float64)
+    rn, rt = O.render_grad(f, tf, cam, DOPRI, W)
+    assert _rel(gn, rn) <= 1e-3 and _rel(gt, rt) <= 1e-3
+    vis = O.cull(f, tf, cam)["visible"]
+    cand = np.flatnonzero(np.repeat(vis, 27) & (np.abs(rn.reshape(-1)) > 0))
+    coords = [("n", int(k)) for k in rng.choice(cand, 48, replace=False)]
+    coords += [("t", int(k)) for k in rng.choice(32, 16, replace=False)]
+    gmax = max(np.abs(rn).max(), np.abs(rt).max())
+    checked = 0
+    for kind, k in coords:
+        arr = f.nodal.reshape(-1) if kind == "n" else tf.knots.reshape(-1)
+        v = float(arr[k])
+        hh = 1e-4 * max(1.0, abs(v))
+        vp, vm = np.float32(v + hh), np.float32(v - hh)
+        arr[k] = vp
+        a = O.render(f, tf, cam, DOPRI)
+        arr[k] = vm
+        b = O.render(f, tf, cam, DOPRI)
+        arr[k] = np.float32(v)
+        if a["steps"] != b["steps"]:
+            continue  # the perturbation changed the adaptive step tree
+        fd = float(((a["rgba"] - b["rgba"]) * W).sum()) / (float(vp) - float(vm))
+        g = gn.reshape(-1)[k] if kind == "n" else gt.reshape(-1)[k]
+        assert abs(g - fd) <= 1e-3 * max(abs(fd), 1e-3 * gmax), (kind, k, g, fd)
+        checked += 1
+    assert checked >= 56
+    r.close()
+
+
+def test_c5_full_size_gradient_on_sampled_rows():
+    """The differentiation workload at full size (shell levels 4..6, 1024x1024,
+    DOPRI5 tol 1e-5): the GPU adjoint of the L2 loss against the perturbed
+    target, restricted to three image rows, against the FP64 oracle gradient
+    of the same restricted loss."""
+    from paper_1809_01334_gb300 import Renderer
+    f, tf, cam, integ = I.preset_c5()
+    r = Renderer(f, tf, integ)
+    r.set_camera(cam)
+    rng = np.random.default_rng(1809)
+    pert = (f.nodal * (1 + 0.05 * rng.uniform(-1, 1, f.nodal.shape))).astype(np.float32)
+    base = r.nodal.clone()
+    r.set_data(torch.from_numpy(pert).cuda(), r.tf.clone())
+    target, _ = r.render()
+    target = target.clone()
+    r.set_data(base, r.tf)
+    img, _ = r.render()
+    rows = [300, 512, 700]
+    W = torch.zeros_like(img)
+    W[rows] = 2.0 * (img[rows] - target[rows])
+    gn, gt = r.backward(W)
+    torch.cuda.synchronize()
+    rn, rt = O.render_grad(f, tf, cam, integ, W.cpu().numpy().astype(np.float64))
+    assert np.abs(rn).max() > 0
+    en = _rel(gn.cpu().numpy().astype(np.float64), rn)
+    et = _rel(gt.cpu().numpy().astype(np.float64), rt)
+    assert en <= 1e-3 and et <= 1e-3, (en, et)
+    r.close()
