@@ -58,6 +58,8 @@ def parse_args():
     p.add_argument("--no-backward", action="store_true", help="skip the adjoint measurement")
     p.add_argument("--batch-cameras", type=int, default=64,
                    help="cameras of the batched (CUDA graph) measurement; 0 skips it")
+    p.add_argument("--no-shell", action="store_true",
+                   help="skip the cubed-sphere shell measurements (render and adjoint)")
     p.add_argument("--image", default="1920x1080",
                    help="image size WxH (smaller sizes only for profiling captures)")
     return p.parse_args()
@@ -204,6 +206,75 @@ def run_batch(args, forest, tf, integ, dev, flush):
             "sizes": "square, side round(256 * 8**u), u ~ U[0,1], seeded"}
 
 
+def _timed(fn, stream, flush, warmup, steps):
+    """Mean device time (ms) of fn() over steps runs after warmup runs, L2
+    flushed before each (outside the timed interval)."""
+    import torch
+    ms = []
+    for k in range(warmup + steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        if k >= warmup:
+            ms.append(a.elapsed_time(b))
+    return sum(ms) / len(ms)
+
+
+def run_shell(args, dev, flush):
+    """Cubed-sphere shell render: 6 trees, levels 4-7 (5,001,233 leaves),
+    degree-2 data, 2048x2048, DOPRI5 tol 1e-5; and the adjoint of an L2 loss
+    on the levels 4-6 shell (1,082,535 leaves) at 1024x1024."""
+    import numpy as np
+    import torch
+    from paper_1809_01334_gb300 import Renderer
+    from paper_1809_01334_gb300 import inputs as I
+    stream = torch.cuda.current_stream(dev)
+    forest, tf, cam, integ = I.preset_c3()
+    r = Renderer(forest, tf, integ, device=dev)
+    r.set_camera(cam)
+    out = torch.empty((cam.h, cam.w, 4), dtype=torch.float32, device=dev)
+    _, st = r.render(out, fill_counters=True)
+    phases = []
+
+    def fwd():
+        phases.append(r.render(out, time_phases=True)[1])
+    ms = _timed(fwd, stream, flush, 2, 5)
+    rays_ms = sum(p["ms_subtree"] for p in phases[2:]) / len(phases[2:])
+    c3 = {"workload": "cubed-sphere shell, 6 trees, levels 4-7 (%d leaves, degree-2 FP32 "
+                      "data), perspective 45deg 2048x2048, DOPRI5 tol 1e-5" % forest.nleaves,
+          "ms_per_render": ms, "segments": st["segments"], "rk_steps": st["rk_steps"],
+          "pair_tests": st["leaf_tests"], "segments_per_s": st["segments"] / (ms * 1e-3),
+          "mpixel_per_s": cam.w * cam.h / (ms * 1e-3) / 1e6, "ms_rays_kernel": rays_ms,
+          "launches": st["launches"]}
+    r.close()
+    del out
+    # differentiation on the levels 4-6 shell
+    forest, tf, cam, integ = I.preset_c5()
+    r = Renderer(forest, tf, integ, device=dev)
+    r.set_camera(cam)
+    out = torch.empty((cam.h, cam.w, 4), dtype=torch.float32, device=dev)
+    pert = forest.nodal * (1 + 0.05 * np.random.default_rng(1809).uniform(-1, 1, forest.nodal.shape))
+    base = r.nodal
+    r.set_data(torch.from_numpy(pert.astype(np.float32)).to(dev), r.tf)
+    target = r.render(out)[0].clone()
+    r.set_data(base, r.tf)
+    img = r.render(out)[0]
+    grad_img = (2.0 * (img - target)).contiguous()
+    _, st = r.render(out, fill_counters=True)
+    fms = _timed(lambda: r.render(out), stream, flush, 2, 5)
+    bms = _timed(lambda: r.backward(grad_img), stream, flush, 2, 5)
+    c5 = {"workload": "cubed-sphere shell, levels 4-6 (%d leaves, degree-2 FP32 data), "
+                      "1024x1024, DOPRI5 tol 1e-5; L2 loss against a render of a seeded 5%% "
+                      "nodal perturbation" % forest.nleaves,
+          "ms_forward": fms, "ms_backward": bms, "fwd_bwd_over_fwd": (fms + bms) / fms,
+          "segments": st["segments"], "grads": "27 nodal values per leaf and the 32 knot values"}
+    r.close()
+    return c3, c5
+
+
 def run_reference(args, world, rank):
     """The oracle as the reference arm: each step renders a bounded sample of rows."""
     if rank != 0:
@@ -340,6 +411,7 @@ def main():
                 bwd_ms.append(a.elapsed_time(b))
 
     batch = run_batch(args, forest, tf, integ, dev, flush) if args.batch_cameras > 0 else None
+    shell = run_shell(args, dev, flush) if not args.no_shell else None
 
     if rank == 0:
         peaks, src = measured_peaks()
@@ -381,6 +453,8 @@ def main():
         }
         if batch:
             line["batch"] = batch
+        if shell:
+            line["shell_render"], line["shell_backward"] = shell
         if bwd_ms:
             mb = sum(bwd_ms) / len(bwd_ms)
             line["backward"] = {"ms_backward": mb, "ms_forward": ms_max,
