@@ -177,10 +177,11 @@ __device__ __forceinline__ void slot_lookup(const Topo &T, const Scratch &S, int
   }
   node = lo - 1;
   const int4 r = S.rect[T.N + node];
-  const long long local = slot - S.off[node];
-  const int rw = r.y - r.x + 1;
-  i = r.x + (int)(local % rw);
-  j = r.z + (int)(local / rw);
+  const unsigned local = (unsigned)(slot - S.off[node]);  // < w * h < 2^31
+  const unsigned rw = (unsigned)(r.y - r.x + 1);
+  const unsigned row = local / rw;
+  i = r.x + (int)(local - row * rw);
+  j = r.z + (int)row;
 }
 
 __device__ __forceinline__ unsigned spread3_9(unsigned v) {  // 3 bits -> positions 0, 3, 6
@@ -190,34 +191,42 @@ __device__ __forceinline__ unsigned spread3_9(unsigned v) {  // 3 bits -> positi
 // Subtree pass (Sec. 3.2 + Sec. 3.3 for the deepest levels).  A CTA owns a
 // chunk of kChunk consecutive (tile-level node, ray) slots, one thread each.
 //  A. per node of the chunk, the leaves of its subtree whose pixel rectangle
-//     meets the chunk's rows are gathered in shared memory (Morton order);
-//     every ray scans that list, slab-tests the leaves whose rectangle holds
-//     its pixel and appends the hits to its own list;
+//     meets the node's rows in the chunk are compacted into a shared table
+//     (Morton order): each with its box (rectangle within those rows), its
+//     anchor relative to the node and its level.  The table's (candidate,
+//     pixel) pairs are spread evenly over the CTA by a prefix sum of the box
+//     areas; every pair whose pixel is a live ray of the candidate's node is
+//     slab-tested and a hit appended to that ray's list;
 //  B. each ray sorts its hits by their Morton key inside the tile node with
 //     every axis mirrored where the ray runs towards negative coordinates:
 //     the ray's front-to-back order for disjoint cells;
 //  C. each warp integrates the hits of its 32 rays, one hit per lane, in
 //     batches, and
 //  D. every lane folds its own ray's results nearest-first with Eq. 2.14.
-constexpr int kCand = 128;     // candidate leaves per round of phase A
-constexpr int kWarpBatch = 64; // hits per warp batch of phase C
+constexpr int kSubtreeThreads = kChunk;  // one chunk per CTA
+constexpr int kCand = kSubtreeThreads;  // candidate table of phase A
+constexpr int kWarpBatch = 32; // hits per warp batch of phase C
 
-__global__ void __launch_bounds__(kChunk, 8)
+__global__ void __launch_bounds__(kSubtreeThreads, 1024 / kSubtreeThreads)
     subtree_kernel(Topo T, Field Fd, Cam c, Integ I, Scratch S, int nb, int ne, long long s0,
                    long long s1) {
-  constexpr int NT = kChunk, NW = NT / 32;
+  constexpr int NT = kSubtreeThreads, NW = NT / 32;
+  static_assert(kCand == NT, "one table entry per thread in the prefix sum");
   __shared__ float4 s_tfv[8], s_tfs[8];
-  __shared__ float4 s_ro[NT], s_rd[NT], s_ri[NT];        // ray origin, direction, 1/direction
+  __shared__ float s_ray[6][NT];                         // ray origin and direction, by component
   __shared__ int s_node[NT];                             // node of each slot, -1 inactive
   __shared__ int s_tnode[NT];                            // distinct nodes of the chunk
-  __shared__ int4 s_cbox[kCand];                         // candidate leaf: rectangle ∩ chunk band
-  __shared__ int s_cl[kCand], s_cpre[kCand];             // candidate leaf index, pair prefix
+  __shared__ int s_liveq[NT];                            // live ray: index of its node, else -1
+  __shared__ int4 s_qinfo[NT];                           // node: {rect x0, rect y0, width, off - cs}
+  __shared__ unsigned long long s_qgeo[NT];              // node: anchor x | y << 21 | z << 42
+  __shared__ int4 s_cbox[kCand];                         // candidate: rectangle within the rows
+  __shared__ int s_cpre[kCand + 1];                      // candidate: pair count, then prefix
+  __shared__ unsigned s_crel[kCand];                     // candidate: anchor in the node, level
+  __shared__ int s_cl[kCand];                            // candidate: (node index << 22) | leaf - base
   __shared__ int s_cnt[NT];                              // hits of each ray
-  __shared__ unsigned char s_live[NT];
-  __shared__ unsigned s_flip[NT];
   __shared__ unsigned s_list[kMaxSubtreeHits][NT];       // (mirrored key << 22) | leaf - base
   __shared__ float4 s_res[NW][kWarpBatch];
-  __shared__ int s_wcnt[NW], s_nn, s_leaf_base;
+  __shared__ int s_wcnt[NW], s_nn, s_leaf_base, s_ncand;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid < 8) {
     const float4 v = Fd.tf[tid];
@@ -227,11 +236,11 @@ __global__ void __launch_bounds__(kChunk, 8)
   }
 
   // slot -> node, pixel, ray; rays that miss the node's box skip all leaves
-  const long long chunk = s0 / NT + blockIdx.x, cs = chunk * NT;
+  const long long cs = (s0 / kChunk) * kChunk + (long long)blockIdx.x * NT;
   const long long slot = cs + tid;
   const bool active = slot >= s0 && slot < s1;
   int node = -1, i = 0, j = 0;
-  if (active) slot_lookup(T, S, nb, ne, chunk, slot, node, i, j);
+  if (active) slot_lookup(T, S, nb, ne, slot / kChunk, slot, node, i, j);
   float3 org, dir;
   pixel_ray(c, i, j, org, dir);
   const float3 inv = make_float3(recip_or_zero(dir.x), recip_or_zero(dir.y), recip_or_zero(dir.z));
@@ -242,17 +251,17 @@ __global__ void __launch_bounds__(kChunk, 8)
     float a0, a1;
     live = slab(org, dir, inv, node_lo(gn, scale), ldexpf(1.f, -gn.w), c.amin, c.amax, a0, a1);
   }
-  const unsigned flip =
-      (dir.x < 0.f ? 0x49u : 0u) | (dir.y < 0.f ? 0x92u : 0u) | (dir.z < 0.f ? 0x124u : 0u);
-  s_ro[tid] = make_float4(org.x, org.y, org.z, 0.f);
-  s_rd[tid] = make_float4(dir.x, dir.y, dir.z, 0.f);
-  s_ri[tid] = make_float4(inv.x, inv.y, inv.z, 0.f);
+  s_ray[0][tid] = org.x;
+  s_ray[1][tid] = org.y;
+  s_ray[2][tid] = org.z;
+  s_ray[3][tid] = dir.x;
+  s_ray[4][tid] = dir.y;
+  s_ray[5][tid] = dir.z;
   s_node[tid] = active ? node : -1;
-  s_live[tid] = live;
-  s_flip[tid] = flip;
   __syncthreads();
 
-  // distinct nodes of the chunk (a node's slots are contiguous)
+  // distinct nodes of the chunk (a node's slots are contiguous), this slot's
+  // node index among them, and each node's layout in the chunk
   {
     const bool head = active && (tid == 0 || s_node[tid - 1] != node);
     const unsigned bal = __ballot_sync(0xffffffffu, head);
@@ -260,90 +269,131 @@ __global__ void __launch_bounds__(kChunk, 8)
     __syncthreads();
     int base = 0;
     for (int w = 0; w < wid; ++w) base += s_wcnt[w];
-    if (head) s_tnode[base + __popc(bal & ((1u << lane) - 1u))] = node;
+    const int myq = base + __popc(bal & (0xffffffffu >> (31 - lane))) - 1;
+    if (head) {
+      s_tnode[myq] = node;
+      const int4 rn = __ldg(S.rect + T.N + node);
+      s_qinfo[myq] = make_int4(rn.x, rn.z, rn.y - rn.x + 1, (int)(__ldg(S.off + node) - cs));
+      const int4 gq = __ldg(T.geo + T.N + node);
+      s_qgeo[myq] = (unsigned long long)gq.x | (unsigned long long)gq.y << 21 |
+                    (unsigned long long)gq.z << 42;
+    }
+    s_liveq[tid] = live ? myq : -1;
     if (tid == NT - 1) {
       int tot = 0;
       for (int w = 0; w < NW; ++w) tot += s_wcnt[w];
       s_nn = tot;
+      s_ncand = 0;
     }
     __syncthreads();
     if (tid == 0) s_leaf_base = s_nn ? __ldg(T.leaves + s_tnode[0]).x : 0;
   }
   __syncthreads();
 
-  // A. candidates and hits: (candidate leaf, pixel) pairs, spread evenly
-  // over the CTA by a prefix sum of their counts
+  // A. candidates and hits
   unsigned ntest = 0;
   const int nn = s_nn, leaf_base = s_leaf_base;
   s_cnt[tid] = 0;
+  // the table's pairs: prefix of the pair counts, then one pair per thread at a time
+  auto flush = [&]() {
+    __syncthreads();
+    const int nc = s_ncand;
+    const int n0 = tid < nc ? s_cpre[tid] : 0;
+    int x = n0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wcnt[wid] = x;
+    __syncthreads();
+    int base = 0, tot = 0;
+    for (int w = 0; w < NW; ++w) {
+      if (w < wid) base += s_wcnt[w];
+      tot += s_wcnt[w];
+    }
+    if (tid < nc) s_cpre[tid] = base + x - n0;
+    if (tid == 0) s_cpre[nc] = tot;
+    __syncthreads();
+    for (int pq = tid; pq < tot; pq += NT) {
+      int lo = 0, hi = nc;  // candidate: last k with s_cpre[k] <= pq
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_cpre[mid] <= pq) lo = mid; else hi = mid;
+      }
+      const int4 b = s_cbox[lo];
+      const int loc = pq - s_cpre[lo];
+      // row = floor(loc / width) from the rounded reciprocal: exact, as the
+      // quotient of (loc + 1/2) stays 1/(2 width) away from an integer
+      const int bw = b.y - b.x + 1;
+      const int row = (int)(((float)loc + 0.5f) * (1.f / (float)bw));
+      const int ii = b.x + loc - row * bw, jj = b.z + row;
+      const int tl = s_cl[lo];
+      const int q = tl >> 22;
+      const int4 qi = s_qinfo[q];
+      const int t = qi.w + (jj - qi.y) * qi.z + (ii - qi.x);
+      if (t < 0 || t >= NT || s_liveq[t] != q) continue;
+      ++ntest;
+      const unsigned rel = s_crel[lo];
+      const unsigned rx = rel & 255u, ry = (rel >> 8) & 255u, rz = (rel >> 16) & 255u;
+      const unsigned long long gq = s_qgeo[q];
+      const int4 g = make_int4((int)(gq & 0x1fffffu) + (int)rx, (int)((gq >> 21) & 0x1fffffu) + (int)ry,
+                               (int)(gq >> 42) + (int)rz, (int)(rel >> 24));
+      const float3 ro = make_float3(s_ray[0][t], s_ray[1][t], s_ray[2][t]);
+      const float3 rd = make_float3(s_ray[3][t], s_ray[4][t], s_ray[5][t]);
+      const float3 ri = make_float3(recip_or_zero(rd.x), recip_or_zero(rd.y), recip_or_zero(rd.z));
+      float b0, b1;
+      if (!slab(ro, rd, ri, node_lo(g, scale), ldexpf(1.f, -g.w), c.amin, c.amax, b0, b1))
+        continue;
+      const unsigned key = spread3_9(rx) | (spread3_9(ry) << 1) | (spread3_9(rz) << 2);
+      const unsigned flip =
+          (rd.x < 0.f ? 0x49u : 0u) | (rd.y < 0.f ? 0x92u : 0u) | (rd.z < 0.f ? 0x124u : 0u);
+      const int k = atomicAdd(&s_cnt[t], 1);
+      if (k < kMaxSubtreeHits) s_list[k][t] = ((key ^ flip) << 22) | (unsigned)(tl & 0x3fffff);
+    }
+    __syncthreads();
+    if (tid == 0) s_ncand = 0;
+  };
   for (int q = 0; q < nn; ++q) {
     const int nd = s_tnode[q];
     const int2 lr = __ldg(T.leaves + nd);
-    const int4 rn = __ldg(S.rect + T.N + nd);
-    const long long off = __ldg(S.off + nd);
-    const int rw = rn.y - rn.x + 1;
-    const long long la = max(cs, off) - off;  // node-local slots inside the chunk
-    const long long lb = min(min(cs + NT, s1), __ldg(S.off + nd + 1)) - off;
-    const int jr0 = rn.z + (int)(la / rw), jr1 = rn.z + (int)((lb - 1) / rw);
-    const unsigned dm = (1u << (T.L - __ldg(T.geo + T.N + nd).w)) - 1u;
-    for (int l0 = lr.x; l0 < lr.y; l0 += kCand) {
+    const int4 qi = s_qinfo[q];
+    const unsigned long long gq = s_qgeo[q];
+    // the node's rows in the chunk: its slots [la, lb) within the node
+    const int la = max(0, -qi.w), lb = min(NT, (int)min(s1 - cs, (long long)__ldg(S.off + nd + 1) - cs)) - qi.w;
+    const int jr0 = qi.y + la / qi.z, jr1 = qi.y + (lb - 1) / qi.z;
+    const int x0 = qi.x, x1 = qi.x + qi.z - 1;
+    for (int l0 = lr.x; l0 < lr.y; l0 += NT) {
+      __syncthreads();
+      if (s_ncand + NT > kCand) flush();
       const int l = l0 + tid;
+      int4 box = empty_rect();
       int cnt = 0;
-      int4 box = empty_rect();  // overlap of the leaf's rectangle with the chunk band
-      if (tid < kCand && l < lr.y) {
+      if (l < lr.y) {
         const int4 r = __ldg(S.rect + l);
-        box = make_int4(max(r.x, rn.x), min(r.y, rn.y), max(r.z, jr0), min(r.w, jr1));
+        box = make_int4(max(r.x, x0), min(r.y, x1), max(r.z, jr0), min(r.w, jr1));
         if (box.x <= box.y && box.z <= box.w) cnt = (box.y - box.x + 1) * (box.w - box.z + 1);
       }
-      // exclusive prefix of the pair counts over the CTA
-      int x = cnt;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-      }
-      __syncthreads();  // previous round's pair table fully consumed
-      if (lane == 31) s_wcnt[wid] = x;
+      const unsigned bal = __ballot_sync(0xffffffffu, cnt > 0);
+      if (lane == 0) s_wcnt[wid] = __popc(bal);
       __syncthreads();
-      int base = 0, tot = 0;
-      for (int w = 0; w < NW; ++w) {
-        if (w < wid) base += s_wcnt[w];
-        tot += s_wcnt[w];
+      int base = s_ncand;
+      for (int w = 0; w < wid; ++w) base += s_wcnt[w];
+      if (cnt > 0) {
+        const int at = base + __popc(bal & ((1u << lane) - 1u));
+        const int4 g = __ldg(T.geo + l);
+        s_cbox[at] = box;
+        s_cpre[at] = cnt;
+        s_crel[at] = (unsigned)(g.x - (int)(gq & 0x1fffffu)) |
+                     (unsigned)(g.y - (int)((gq >> 21) & 0x1fffffu)) << 8 |
+                     (unsigned)(g.z - (int)(gq >> 42)) << 16 | (unsigned)g.w << 24;
+        s_cl[at] = (q << 22) | (l - leaf_base);
       }
-      s_cpre[tid] = base + x - cnt;
-      s_cbox[tid] = box;
-      s_cl[tid] = l;
       __syncthreads();
-      for (int pq = tid; pq < tot; pq += NT) {
-        int lo = 0, hi = kCand;  // candidate: last k with s_cpre[k] <= pq
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (s_cpre[mid] <= pq) lo = mid; else hi = mid;
-        }
-        const int4 b = s_cbox[lo];
-        const int loc = pq - s_cpre[lo], bw = b.y - b.x + 1;
-        const int jj = b.z + loc / bw, ii = b.x + loc % bw;
-        const long long ls = (long long)(jj - rn.z) * rw + (ii - rn.x);
-        if (ls < la || ls >= lb) continue;
-        const int t = (int)(off + ls - cs);
-        if (!s_live[t]) continue;
-        ++ntest;
-        const int lf = s_cl[lo];
-        const int4 g = __ldg(T.geo + lf);
-        const float4 ro = s_ro[t], rd = s_rd[t], ri = s_ri[t];
-        float b0, b1;
-        if (!slab(make_float3(ro.x, ro.y, ro.z), make_float3(rd.x, rd.y, rd.z),
-                  make_float3(ri.x, ri.y, ri.z), node_lo(g, scale), ldexpf(1.f, -g.w), c.amin,
-                  c.amax, b0, b1))
-          continue;
-        const unsigned key = spread3_9((unsigned)g.x & dm) | (spread3_9((unsigned)g.y & dm) << 1) |
-                             (spread3_9((unsigned)g.z & dm) << 2);
-        const int k = atomicAdd(&s_cnt[t], 1);
-        if (k < kMaxSubtreeHits)
-          s_list[k][t] = ((key ^ s_flip[t]) << 22) | (unsigned)(lf - leaf_base);
-      }
+      if (tid == NT - 1) s_ncand = base + __popc(bal);
     }
   }
+  flush();
   __syncthreads();
   const unsigned nhit = (unsigned)s_cnt[tid];
 
@@ -382,15 +432,17 @@ __global__ void __launch_bounds__(kChunk, 8)
         const int p = __shfl_sync(0xffffffffu, pre, lo + st - 1);
         if (p <= h) lo += st;
       }
-      const int ow = lo;
-      const int owpre = __shfl_sync(0xffffffffu, my0, ow & 31);
+      const int ow = lo & 31;
+      const int owpre = __shfl_sync(0xffffffffu, my0, ow);
       if (h < b1) {
         const int t = wid * 32 + ow;
         const int leaf = leaf_base + (int)(s_list[h - owpre][t] & 0x3fffffu);
-        const float4 ro = s_ro[t], rd = s_rd[t], ri = s_ri[t];
-        s_res[wid][h - b0] = leaf_segment(T, Fd, c, I, tf, leaf, make_float3(ro.x, ro.y, ro.z),
-                                          make_float3(rd.x, rd.y, rd.z),
-                                          make_float3(ri.x, ri.y, ri.z), scale, steps);
+        const float3 ro = make_float3(s_ray[0][t], s_ray[1][t], s_ray[2][t]);
+        const float3 rd = make_float3(s_ray[3][t], s_ray[4][t], s_ray[5][t]);
+        s_res[wid][h - b0] = leaf_segment(T, Fd, c, I, tf, leaf, ro, rd,
+                                          make_float3(recip_or_zero(rd.x), recip_or_zero(rd.y),
+                                                      recip_or_zero(rd.z)),
+                                          scale, steps);
       }
     }
     __syncwarp();
@@ -519,25 +571,27 @@ __global__ void __launch_bounds__(kCoarsenThreads, 8)
   // same sequence is formed by combining along x, then y, then z, each pair
   // nearer-first (Eq. 2.14 is associative), with every index static.
   if (active) {
+    // the internal children's slots of this pixel: rectangles and offsets in
+    // one round of independent loads, then the aggregates in another
+    long long e[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int id = ch[q];
+      e[q] = -1;
+      if (live && id >= T.N) {
+        const int4 r = __ldg(S.rect + id);
+        const long long o = __ldg(S.off + id - T.N);
+        if (i >= r.x && i <= r.y && j >= r.z && j <= r.w)
+          e[q] = o + (long long)(j - r.z) * (r.y - r.x + 1) + (i - r.x);
+      }
+    }
     float4 cs[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      if (!live) {
-        cs[q] = seg_identity();
-        continue;
-      }
       const int id = ch[q];
       float4 s = seg_identity();
-      if (id >= 0 && id < T.N) {
-        s = s_seg[q][tid];
-      } else if (id >= T.N) {
-        const int4 r = S.rect[id];
-        if (i >= r.x && i <= r.y && j >= r.z && j <= r.w) {
-          const long long e =
-              S.off[id - T.N] + (long long)(j - r.z) * (r.y - r.x + 1) + (i - r.x);
-          s = S.entries[e];
-        }
-      }
+      if (live && id >= 0 && id < T.N) s = s_seg[q][tid];
+      else if (e[q] >= 0) s = S.entries[e[q]];
       cs[q] = s;
     }
     const bool fx = dir.x < 0.f, fy = dir.y < 0.f, fz = dir.z < 0.f;
@@ -622,9 +676,10 @@ cudaError_t launch_subtree(const Topo &T, const Field &Fd, const Cam &C, const I
                            Scratch S, int nb, int ne, long long s0, long long s1,
                            cudaStream_t stream) {
   if (s1 <= s0) return cudaSuccess;
-  const long long nblk = (s1 - 1) / kChunk - s0 / kChunk + 1;
+  const long long per = kSubtreeThreads / kChunk;  // chunks per CTA
+  const long long nblk = ((s1 - 1) / kChunk - s0 / kChunk + per) / per;
   if (nblk > 0x7fffffffll) return cudaErrorInvalidValue;
-  subtree_kernel<<<(unsigned)nblk, kChunk, 0, stream>>>(T, Fd, C, I, S, nb, ne, s0, s1);
+  subtree_kernel<<<(unsigned)nblk, kSubtreeThreads, 0, stream>>>(T, Fd, C, I, S, nb, ne, s0, s1);
   return cudaGetLastError();
 }
 
