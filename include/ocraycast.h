@@ -53,6 +53,7 @@ extern "C" {
 #define OCR_DOPRI5 1  /* Dormand-Prince 5(4) inside the bisection of Algorithm 1 */
 #define OCR_GAUSS2 2  /* implicit 2-stage Gauss closed form (Eqs. 2.32-2.33), Algorithm 1 */
 #define OCR_SIMPSON 3 /* Simpson quadrature of the closed form (Eq. 2.34), Algorithm 1 */
+#define OCR_EQUILIBRIUM 4 /* intensity interface of Eq. 2.18, Algorithm 1 (see ocr_integrator) */
 
 typedef struct ocr_forest ocr_forest;
 
@@ -97,8 +98,12 @@ typedef struct {
  * replaced by its two halves, combined near (+) far, while
  * dx * kappa(xi) > c_rk at a node of the step (or, for DOPRI5, the embedded
  * error estimate exceeds tol), up to max_depth halvings (Algorithm 1).  The
- * Gauss nodes are x1 + (1/2 -+ sqrt(3)/6) dx, x1 the far end.  bg is the
- * background intensity I_b per channel. */
+ * Gauss nodes are x1 + (1/2 -+ sqrt(3)/6) dx, x1 the far end.  EQUILIBRIUM
+ * (the interface of Eq. 2.18, Sec. 2.5): the transfer function's colour
+ * channels are read as the intensity I the application wants to see, not as
+ * an emission density; a step's A = exp(-dx (kappa_far + 4 kappa_mid +
+ * kappa_near) / 6) and B = I_mid (1 - A), split by the c_rk test of
+ * Algorithm 1.  bg is the background intensity I_b per channel. */
 typedef struct {
   int method;
   int nsteps;

@@ -22,7 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "_build", "libocr_oracle.so")
 _lib = None
 
-RK4, DOPRI5, GAUSS2, SIMPSON = 0, 1, 2, 3
+RK4, DOPRI5, GAUSS2, SIMPSON, EQUILIBRIUM = 0, 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:
@@ -145,8 +145,8 @@ def integrator_struct(integ: dict, bg=(0.0, 0.0, 0.0)) -> Integrator_:
         s.tol = float(integ.get("tol", 1e-6))
         s.c_rk = float(integ.get("c_rk", 0.5))
         s.max_depth = int(integ.get("max_depth", 16))
-    elif integ["method"] in ("gauss2", "simpson"):
-        s.method = GAUSS2 if integ["method"] == "gauss2" else SIMPSON
+    elif integ["method"] in ("gauss2", "simpson", "equilibrium"):
+        s.method = {"gauss2": GAUSS2, "simpson": SIMPSON, "equilibrium": EQUILIBRIUM}[integ["method"]]
         s.nsteps, s.tol = 0, 0.0
         s.c_rk = float(integ.get("c_rk", 0.5))
         s.max_depth = int(integ.get("max_depth", 16))

@@ -595,6 +595,25 @@ static void simpson_step(const seg_ctx *S, double x1, double x2, double *y, doub
   *kmax = dx * (m > k2[0] ? m : k2[0]);
 }
 
+/* Eq. 2.18 as an interface (Sec. 2.5): the application supplies the
+ * absorption kappa and the intensity I it wants to see; A follows from the
+ * absorption (Simpson's rule on the optical depth, nodes far end, midpoint,
+ * near end) and B = I (1 - A), 1 - A formed as -expm1.  For constant
+ * coefficients this is exactly Eq. 2.13 with q = kappa I. */
+static void equilibrium_step(const seg_ctx *S, double x1, double x2, double *y, double *kmax) {
+  double dx = x2 - x1;
+  double k0[4], kh[4], k2[4];
+  medium_at(S, x1, k0);
+  medium_at(S, 0.5 * (x1 + x2), kh);
+  medium_at(S, x2, k2);
+  double e = -dx * (k0[0] + 4.0 * kh[0] + k2[0]) / 6.0;
+  double om = -expm1(e);
+  y[0] = exp(e);
+  for (int c = 1; c < 4; ++c) y[c] = kh[c] * om;
+  double m = k0[0] > kh[0] ? k0[0] : kh[0];
+  *kmax = dx * (m > k2[0] ? m : k2[0]);
+}
+
 /* Algorithm 1: if a stage sees dx kappa > c_RK (or, for DOPRI5, the embedded
  * error exceeds tol), split at the midpoint and return
  * segeval(mid, x2) (+) segeval(x1, mid). */
@@ -605,6 +624,8 @@ static void segeval(const seg_ctx *S, const orc_integrator *I, double x1, double
     gauss2_step(S, x1, x2, y5, &kmax);
   else if (I->method == ORC_SIMPSON)
     simpson_step(S, x1, x2, y5, &kmax);
+  else if (I->method == ORC_EQUILIBRIUM)
+    equilibrium_step(S, x1, x2, y5, &kmax);
   else
     dopri_step(S, x1, x2, y5, &kmax, &err);
   ++*nsteps;

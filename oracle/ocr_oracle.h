@@ -50,11 +50,15 @@ typedef struct {
   int w, h, ortho;
 } orc_camera;
 
-enum { ORC_RK4 = 0, ORC_DOPRI5 = 1, ORC_GAUSS2 = 2, ORC_SIMPSON = 3 };
+enum { ORC_RK4 = 0, ORC_DOPRI5 = 1, ORC_GAUSS2 = 2, ORC_SIMPSON = 3, ORC_EQUILIBRIUM = 4 };
 typedef struct {
   int method;      /* ORC_RK4: nsteps equal classical RK4 steps; the others inside Algorithm 1:
                       ORC_DOPRI5 Dormand-Prince 5(4), ORC_GAUSS2 the implicit 2-stage Gauss
-                      closed form (Eqs. 2.32-2.33), ORC_SIMPSON quadrature (Eq. 2.34) */
+                      closed form (Eqs. 2.32-2.33), ORC_SIMPSON quadrature (Eq. 2.34),
+                      ORC_EQUILIBRIUM the intensity interface of Eq. 2.18: the transfer
+                      function's colour channels are the desired intensity I, a step's A is
+                      exp(-Simpson integral of kappa) and its B = I(1 - A), I taken at the
+                      step's midpoint */
   int nsteps;
   double tol;      /* DOPRI5 only: split when the embedded error estimate exceeds tol */
   double c_rk;     /* split when dx * kappa(xi_j) > c_rk at any stage point */

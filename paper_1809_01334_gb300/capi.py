@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libocraycast.so")
 
 OK, ERR_INVALID, ERR_CUDA, ERR_OOM, ERR_UNSUPPORTED, ERR_DEVICE, ERR_STATE = 0, -1, -2, -3, -4, -5, -6
 GEOM_CUBE, GEOM_SHELL = 0, 1
-RK4, DOPRI5, GAUSS2, SIMPSON = 0, 1, 2, 3
+RK4, DOPRI5, GAUSS2, SIMPSON, EQUILIBRIUM = 0, 1, 2, 3, 4
 
 EXPORTS = ["ocr_build_forest", "ocr_forest_set_data", "ocr_set_integrator", "ocr_set_camera",
            "ocr_render", "ocr_render_backward", "ocr_device_bytes", "ocr_destroy",

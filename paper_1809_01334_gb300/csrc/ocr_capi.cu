@@ -626,7 +626,8 @@ int ocr_set_integrator(ocr_forest *F, const ocr_integrator *I) {
   } else if (I->method == OCR_DOPRI5) {
     if (!(I->tol > 0.f) || !(I->c_rk > 0.f) || I->max_depth < 0 || I->max_depth > 24)
       return OCR_ERR_INVALID;
-  } else if (I->method == OCR_GAUSS2 || I->method == OCR_SIMPSON) {
+  } else if (I->method == OCR_GAUSS2 || I->method == OCR_SIMPSON ||
+             I->method == OCR_EQUILIBRIUM) {
     if (!(I->c_rk > 0.f) || I->max_depth < 0 || I->max_depth > 24) return OCR_ERR_INVALID;
   } else {
     return OCR_ERR_UNSUPPORTED;

@@ -183,7 +183,7 @@ __device__ float4 integrate_segment(const Fld &cu, const TF &tf, float dx, const
   unsigned idx = 0;
   float4 kq0 = medium(cu, tf, 0.f);
   const float4 one = seg_identity();
-  if (I.method != 1) {  // Gauss-2 (Eqs. 2.32-2.33) or Simpson (Eq. 2.34) inside Algorithm 1
+  if (I.method != 1) {  // Gauss-2 (Eqs. 2.32-2.33), Simpson (Eq. 2.34) or Eq. 2.18, Algorithm 1
     for (;;) {
       const float dtau = ldexpf(1.f, -depth);
       const float t0 = (float)idx * dtau;
@@ -202,6 +202,15 @@ __device__ float4 integrate_segment(const Fld &cu, const TF &tf, float dx, const
         S.z = (0.5f * H * (g0.z + g1.z) + h2 * (g0.x * g1.z - g1.x * g0.z)) * inv;
         S.w = (0.5f * H * (g0.w + g1.w) + h2 * (g0.x * g1.w - g1.x * g0.w)) * inv;
         kmax = H * fmaxf(g0.x, g1.x);
+      } else if (I.method == 4) {
+        // Eq. 2.18 as an interface: the colour channels are the intensity I;
+        // A from Simpson's rule on the optical depth, B = I_mid (1 - A)
+        const float4 kh = medium(cu, tf, t0 + 0.5f * dtau);
+        kq1 = medium(cu, tf, t0 + dtau);
+        const float e = -(H / 6.f) * (kq0.x + 4.f * kh.x + kq1.x);
+        const float om = -expm1f(e);
+        S = make_float4(1.f - om, kh.y * om, kh.z * om, kh.w * om);
+        kmax = H * fmaxf(fmaxf(kq0.x, kh.x), kq1.x);
       } else {
         // Simpson nodes: far end, midpoint, near end
         const float4 kh = medium(cu, tf, t0 + 0.5f * dtau);

@@ -58,9 +58,10 @@ class Renderer:
             capi.set_integrator(self.h, capi.DOPRI5, tol=integ.get("tol", 1e-6),
                                 c_rk=integ.get("c_rk", 0.5), max_depth=integ.get("max_depth", 16),
                                 bg=bg)
-        elif integ["method"] in ("gauss2", "simpson"):
-            capi.set_integrator(self.h, capi.GAUSS2 if integ["method"] == "gauss2" else
-                                capi.SIMPSON, c_rk=integ.get("c_rk", 0.5),
+        elif integ["method"] in ("gauss2", "simpson", "equilibrium"):
+            method = {"gauss2": capi.GAUSS2, "simpson": capi.SIMPSON,
+                      "equilibrium": capi.EQUILIBRIUM}[integ["method"]]
+            capi.set_integrator(self.h, method, c_rk=integ.get("c_rk", 0.5),
                                 max_depth=integ.get("max_depth", 16), bg=bg)
         else:
             raise ValueError(integ["method"])

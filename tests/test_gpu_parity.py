@@ -72,10 +72,12 @@ def test_small_adaptive_perspective(integ):
 
 
 @pytest.mark.parametrize("integ", [{"method": "gauss2", "c_rk": 0.05, "max_depth": 16},
-                                   {"method": "simpson", "c_rk": 0.2, "max_depth": 16}])
+                                   {"method": "simpson", "c_rk": 0.2, "max_depth": 16},
+                                   {"method": "equilibrium", "c_rk": 0.2, "max_depth": 16}])
 def test_gauss2_and_simpson_integrators(integ):
-    """Sec. 2.7's implicit Gauss closed form and Simpson quadrature inside
-    Algorithm 1, on the adaptive mesh with a non-zero background."""
+    """Sec. 2.7's implicit Gauss closed form and Simpson quadrature, and the
+    intensity interface of Eq. 2.18, inside Algorithm 1, on the adaptive mesh
+    with a non-zero background."""
     f, tf, cam = I.preset_small(w=64, h=48)
     _compare(f, tf, cam, integ, bg=(0.1, 0.2, 0.3))
 

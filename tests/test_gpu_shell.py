@@ -28,7 +28,7 @@ def test_small_adaptive_shell_dopri5():
     assert st["segments"] > 0 and (ref["counts"] >= 2).mean() > 0.3
 
 
-@pytest.mark.parametrize("method", ["rk4", "gauss2", "simpson"])
+@pytest.mark.parametrize("method", ["rk4", "gauss2", "simpson", "equilibrium"])
 def test_uniform_shell_integrators(method):
     """Uniform level-2 shell (384 leaves) with every integrator and a
     background."""
@@ -36,7 +36,8 @@ def test_uniform_shell_integrators(method):
     cam = I.perspective_camera(5, 33, 27, dist=(2.2, 2.6), target=(0.0, 0.0, 0.0))
     integ = {"rk4": {"method": "rk4", "nsteps": 4},
              "gauss2": {"method": "gauss2", "c_rk": 0.05, "max_depth": 16},
-             "simpson": {"method": "simpson", "c_rk": 0.2, "max_depth": 16}}[method]
+             "simpson": {"method": "simpson", "c_rk": 0.2, "max_depth": 16},
+             "equilibrium": {"method": "equilibrium", "c_rk": 0.2, "max_depth": 16}}[method]
     _compare(f, tf, cam, integ, bg=(0.3, 0.2, 0.1))
 
 

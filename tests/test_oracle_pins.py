@@ -559,6 +559,59 @@ def test_gauss2_simpson_converge_inside_algorithm1(method):
     assert errs[1] / errs[2] > (12 if method == "gauss2" else 3.5)
 
 
+# ------------------------------------------------- Eq. 2.18 as an interface --
+def test_equilibrium_interface_constant_medium_is_exact():
+    """Eq. 2.18: with constant kappa and intensity I the step is exactly the
+    equilibrium solution, A = exp(-kappa L), B = I (1 - A), whatever the
+    splitting (Eq. 2.13 with q = kappa I); every split gives the same value."""
+    kappa, inten = 7.0, np.array([0.25, 0.5, 0.875])
+    f, tf = _one_leaf(np.full(8, 2.0), np.tile(np.concatenate([[kappa], inten]), (8, 1)))
+    of = O.OracleForest(f, tf)
+    org, d = np.array([0.5, 0.5, -1.0]), np.array([0.0, 0.0, 1.0])
+    L = 1.0
+    exact = np.concatenate([[math.exp(-kappa * L)], inten * -math.expm1(-kappa * L)])
+    for c_rk, depth in [(1e9, 0), (0.5, 30), (0.01, 30)]:
+        seg, st = O.segment_ab(of, {"method": "equilibrium", "c_rk": c_rk, "max_depth": depth},
+                               0, org, d, 1.0, 2.0)
+        np.testing.assert_allclose(seg, exact, rtol=1e-12, atol=1e-15)
+    # the same as the ODE of Eq. 2.29 with emission q = kappa I (fine DOPRI5)
+    f2, tf2 = _one_leaf(np.full(8, 2.0), np.tile(np.concatenate([[kappa], kappa * inten]), (8, 1)))
+    ode, _ = O.segment_ab(O.OracleForest(f2, tf2), {"method": "dopri5", "tol": 1e-12, "c_rk": 0.05,
+                                                     "max_depth": 30}, 0, org, d, 1.0, 2.0)
+    np.testing.assert_allclose(ode, exact, rtol=1e-10, atol=1e-12)
+
+
+def test_equilibrium_interface_converges_to_the_ode_with_emission_kappa_times_intensity():
+    """With varying data, Algorithm 1 with the Eq. 2.18 step converges, as
+    c_RK shrinks, to Eq. 2.12 with q(x) = kappa(x) I(x): trapezoid quadrature
+    of the closed form with point location (no segments) along the ray."""
+    vals = RNG.uniform(0.5, 6.5, 8)
+    knots = np.column_stack([1.0 + np.arange(8), 0.1 + 0.1 * np.arange(8),
+                             0.9 - 0.1 * np.arange(8), np.full(8, 0.4)])
+    f, tf = _one_leaf(vals, knots)
+    of = O.OracleForest(f, tf)
+    d = np.array([0.35, 0.2, -0.9])
+    org = np.array([0.5, 0.45, 0.5]) - 2.0 * d
+    hit, a0, a1 = O.ray_leaf(of, 0, org, d, 0, 1e9)
+    rl = np.linalg.norm(d)
+    xs = np.linspace(0.0, (a1 - a0) * rl, 400001)
+    pts = org[None, :] + (a1 - xs / rl)[:, None] * d[None, :]
+    s, _ = BF.field_at(f, pts)
+    kq = BF.tf_numpy(tf, s)
+    kap, q = kq[:, 0], kq[:, :1] * kq[:, 1:]
+    dx = xs[1] - xs[0]
+    tau = np.concatenate([[0.0], np.cumsum(0.5 * (kap[1:] + kap[:-1]) * dx)])
+    fB = q * np.exp(-(tau[-1] - tau))[:, None]
+    ref = np.concatenate([[math.exp(-tau[-1])], (0.5 * (fB[1:] + fB[:-1]) * dx).sum(axis=0)])
+    errs = []
+    for c_rk in (0.2, 0.05, 0.0125):
+        seg, _ = O.segment_ab(of, {"method": "equilibrium", "c_rk": c_rk, "max_depth": 30}, 0,
+                              org, d, a0, a1)
+        errs.append(np.abs(seg - ref).max())
+    # second order (I at the step midpoint): each 4x finer c_RK divides the error by ~16
+    assert errs[2] < errs[1] < errs[0] and errs[2] < 2e-7 and errs[1] / errs[2] > 10, errs
+
+
 # ------------------------------------------------------- gradient (reverse) --
 def _loss(forest, tf, cam, integ, W, bg):
     r = O.render(forest, tf, cam, integ, bg=bg)
