@@ -158,6 +158,7 @@ def run_batch(args, forest, tf, integ, dev, flush):
     npix = sum(c.w * c.h for c in cams)
     r = Renderer(forest, tf, integ, device=dev)
     r.set_cameras(cams)
+    tune = r.autotune(reps=2)
     out = torch.empty((npix, 4), dtype=torch.float32, device=dev)
     _, _, st = r.render_batch(out, with_index=True)
     segments = st["segments"]
@@ -202,6 +203,7 @@ def run_batch(args, forest, tf, integ, dev, flush):
     return {"cameras": len(cams), "pixels": npix, "segments": segments,
             "graph_ms": gm, "sequential_ms": sq, "speedup_vs_sequential": sq / gm,
             "segments_per_s": segments / (gm * 1e-3), "mpixel_per_s": npix / (gm * 1e-3) / 1e6,
+            "autotune": {"best": tune["best"], "tried": tune["tried"]},
             "sequential": "one Renderer: set_camera + render per view, wall time",
             "sizes": "square, side round(256 * 8**u), u ~ U[0,1], seeded"}
 

@@ -231,6 +231,41 @@ int ocr_prune_noalloc(const int32_t *d_leaf_geo, int64_t nleaves, int max_level,
 int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_nodal,
                         float *d_grad_tf, void *stream);
 
+/* Tuning of the render's decomposition (the batching autotuner's knobs):
+ *   tile_depth  cube forests: how many octree levels (1..3) one CTA merges in
+ *               shared memory before per-(node, ray) aggregates go to HBM; the
+ *               levels above are merged by one pass per level.  Deeper tiles
+ *               mean fewer passes and more candidate leaves per CTA.
+ *   streams     internal streams (1..8) over which the cameras of a
+ *               multi-camera render are spread.
+ *   shell_warps shell forests: warps per CTA of the per-ray kernel (1..8;
+ *               0 = as many as fit in 96 KB of shared memory).
+ *   ms          ocr_autotune: the measured device time of one ocr_render.
+ * Defaults: tile_depth 3, streams 4, shell_warps 0. */
+typedef struct {
+  int tile_depth;
+  int streams;
+  int shell_warps;
+  float ms;
+} ocr_tuning;
+
+/* Apply a tuning.  Changing tile_depth of a cube forest re-plans the cameras
+ * (blocking, like ocr_set_camera).  OCR_ERR_INVALID for values out of range. */
+int ocr_set_tuning(ocr_forest *F, const ocr_tuning *t);
+int ocr_get_tuning(const ocr_forest *F, ocr_tuning *t);
+
+/* Autotuner: render the cameras, data and integrator last set under every
+ * candidate tuning (cube: tile_depth 1..3 x streams {1, 2, 4, 8}; shell:
+ * shell_warps {1, 2, 4, 8} x streams; streams only with several cameras),
+ * one warm-up and `reps` timed renders each (CUDA events on an internal
+ * stream, 1 <= reps <= 100), and keep the fastest, returned in *best.  The
+ * candidates and their times go to tried[0 .. max_tried) (may be NULL when
+ * max_tried is 0) and their number to *ntried (may be NULL).  Allocates a
+ * scratch image for the duration of the call; blocks the host.  On error the
+ * previous tuning is restored. */
+int ocr_autotune(ocr_forest *F, int reps, ocr_tuning *best, ocr_tuning *tried, int max_tried,
+                 int *ntried);
+
 /* Device memory held by the library for this forest (topology + scratch). */
 int64_t ocr_device_bytes(const ocr_forest *F);
 

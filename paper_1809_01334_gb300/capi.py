@@ -18,8 +18,8 @@ GEOM_CUBE, GEOM_SHELL = 0, 1
 RK4, DOPRI5, GAUSS2, SIMPSON, EQUILIBRIUM = 0, 1, 2, 3, 4
 
 EXPORTS = ["ocr_build_forest", "ocr_forest_set_data", "ocr_set_integrator", "ocr_set_camera",
-           "ocr_render", "ocr_render_backward", "ocr_device_bytes", "ocr_destroy",
-           "ocr_strerror"]
+           "ocr_render", "ocr_render_backward", "ocr_set_tuning", "ocr_get_tuning",
+           "ocr_autotune", "ocr_device_bytes", "ocr_destroy", "ocr_strerror"]
 
 
 class ForestDesc(C.Structure):
@@ -49,6 +49,11 @@ class Stats(C.Structure):
                 ("subtree_leaf_tests", C.c_int64),
                 ("launches", C.c_int64), ("ms_prune", C.c_float), ("ms_merge", C.c_float),
                 ("ms_subtree", C.c_float)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("tile_depth", C.c_int), ("streams", C.c_int), ("shell_warps", C.c_int),
+                ("ms", C.c_float)]
 
 
 class OcrError(RuntimeError):
@@ -170,6 +175,40 @@ def render(h, d_rgba, stream=None, d_counts=None, d_visible=None, d_rects=None,
             "subtree_leaf_tests": s.subtree_leaf_tests,
             "launches": s.launches, "ms_prune": s.ms_prune, "ms_merge": s.ms_merge,
             "ms_subtree": s.ms_subtree}
+
+
+def _tuning_dict(t: Tuning) -> dict:
+    return {"tile_depth": t.tile_depth, "streams": t.streams, "shell_warps": t.shell_warps,
+            "ms": float(t.ms)}
+
+
+def set_tuning(h, tile_depth: int = 3, streams: int = 4, shell_warps: int = 0):
+    """ocr_set_tuning (a cube forest re-plans its cameras when tile_depth changes)."""
+    t = Tuning(int(tile_depth), int(streams), int(shell_warps), 0.0)
+    L = lib()
+    L.ocr_set_tuning.argtypes = [C.c_void_p, C.POINTER(Tuning)]
+    _check(L.ocr_set_tuning(h, C.byref(t)), "ocr_set_tuning")
+
+
+def get_tuning(h) -> dict:
+    t = Tuning()
+    L = lib()
+    L.ocr_get_tuning.argtypes = [C.c_void_p, C.POINTER(Tuning)]
+    _check(L.ocr_get_tuning(h, C.byref(t)), "ocr_get_tuning")
+    return _tuning_dict(t)
+
+
+def autotune(h, reps: int = 3) -> dict:
+    """ocr_autotune: times every candidate tuning on the current cameras and
+    keeps the fastest.  Returns {"best": ..., "tried": [...]}."""
+    best = Tuning()
+    tried = (Tuning * 64)()
+    n = C.c_int(0)
+    L = lib()
+    L.ocr_autotune.argtypes = [C.c_void_p, C.c_int, C.POINTER(Tuning), C.POINTER(Tuning), C.c_int,
+                               C.POINTER(C.c_int)]
+    _check(L.ocr_autotune(h, int(reps), C.byref(best), tried, 64, C.byref(n)), "ocr_autotune")
+    return {"best": _tuning_dict(best), "tried": [_tuning_dict(tried[k]) for k in range(n.value)]}
 
 
 def device_bytes(h) -> int:

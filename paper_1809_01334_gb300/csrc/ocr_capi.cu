@@ -44,7 +44,7 @@ struct CamPlan {
   unsigned long long *d_keys = nullptr;  // [nhits]
 };
 
-constexpr int kRenderStreams = 4;   // cameras of a batch are spread over these
+constexpr int kMaxStreams = 8;      // cameras of a batch are spread over up to this many
 constexpr int kMaxCameras = 4096;
 
 struct ocr_forest {
@@ -70,8 +70,12 @@ struct ocr_forest {
   Integ integ{};
   std::vector<CamPlan> plans;         // one per camera of the last ocr_set_camera
   long long total_pix = 0;
-  cudaStream_t sub[kRenderStreams] = {};
-  cudaEvent_t fork = nullptr, join[kRenderStreams] = {};
+  cudaStream_t sub[kMaxStreams] = {};
+  cudaEvent_t fork = nullptr, join[kMaxStreams] = {};
+  // tuning (ocr_set_tuning / ocr_autotune)
+  int tile_depth = kSubtreeDepth;     // cube: octree levels aggregated inside one CTA
+  int nstreams = 4;                   // internal streams of multi-camera renders
+  int shell_warps = 0;                // shell: warps per CTA of the per-ray kernel (0: most)
   long long *h_group_slots = nullptr; // pinned [L + 1 + kStats]
   unsigned long long *d_stats = nullptr;  // [kStats]
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // start, layout, subtree, end
@@ -140,22 +144,29 @@ int dev_alloc(T **p, size_t n, int64_t &bytes) {
   return OCR_OK;
 }
 
+// free one plan's device scratch (its camera and sizes stay)
+void free_plan_buffers(ocr_forest *F, CamPlan &P) {
+  void *bufs[] = {P.d_rect, P.d_off, P.d_bsums, P.d_gslots, P.d_chunk, P.d_entries, P.d_leaf_off,
+                  P.d_sbsums, P.d_pchunk, P.d_rcount, P.d_rcursor, P.d_ray_off, P.d_keys};
+  for (void *b : bufs) cudaFree(b);
+  P.d_rect = nullptr;
+  P.d_off = nullptr;
+  P.d_bsums = nullptr;
+  P.d_gslots = nullptr;
+  P.d_chunk = nullptr;
+  P.d_entries = nullptr;
+  P.d_leaf_off = nullptr;
+  P.d_sbsums = nullptr;
+  P.d_pchunk = nullptr;
+  P.d_rcount = nullptr;
+  P.d_rcursor = nullptr;
+  P.d_ray_off = nullptr;
+  P.d_keys = nullptr;
+  (void)F;
+}
+
 void free_plans(ocr_forest *F) {
-  for (CamPlan &P : F->plans) {
-    cudaFree(P.d_rect);
-    cudaFree(P.d_off);
-    cudaFree(P.d_bsums);
-    cudaFree(P.d_gslots);
-    cudaFree(P.d_chunk);
-    cudaFree(P.d_entries);
-    cudaFree(P.d_leaf_off);
-    cudaFree(P.d_sbsums);
-    cudaFree(P.d_pchunk);
-    cudaFree(P.d_rcount);
-    cudaFree(P.d_rcursor);
-    cudaFree(P.d_ray_off);
-    cudaFree(P.d_keys);
-  }
+  for (CamPlan &P : F->plans) free_plan_buffers(F, P);
   F->plans.clear();
 }
 
@@ -166,7 +177,7 @@ void free_all(ocr_forest *F) {
   cudaFree(F->d_leaves);
   cudaFree(F->d_group_nodes);
   free_plans(F);
-  for (int q = 0; q < kRenderStreams; ++q) {
+  for (int q = 0; q < kMaxStreams; ++q) {
     if (F->sub[q]) cudaStreamDestroy(F->sub[q]);
     if (F->join[q]) cudaEventDestroy(F->join[q]);
   }
@@ -331,6 +342,8 @@ int build_shell(const ocr_forest_desc *desc, cudaStream_t st, ocr_forest **out) 
   return OCR_OK;
 }
 
+int plan_cameras(ocr_forest *F);
+
 // Plan one camera of a shell forest: its pruning and pair space, the segment
 // count of every ray, the size of the lists and the longest one.  Blocks the
 // host (legacy default stream).
@@ -404,7 +417,7 @@ int enqueue_shell(ocr_forest *F, CamPlan &P, float4 *rgba, int *counts, unsigned
   if (timed) OCR_CUDA(cudaEventRecord(F->ev[1], st));
   if (timed) OCR_CUDA(cudaEventRecord(F->ev[2], st));
   OCR_CUDA(shell_rays(F->d_geo, F->N, F->shell, Fd, P.cam, F->integ, P.d_ray_off, npix, P.d_keys,
-                      P.nhits, P.cap, rgba, counts, F->d_stats, F->nsm, st));
+                      P.nhits, P.cap, rgba, counts, F->d_stats, F->nsm, F->shell_warps, st));
   if (timed) OCR_CUDA(cudaEventRecord(F->ev[3], st));
   // cull, 2 scans of 3 kernels (1 when empty), chunk map, 2 pair passes, rays
   launches += 1 + (bwd_scan_blocks(F->N) > 0 ? 3 : 0) + 1 + (P.npairs > 0 ? 2 : 0) +
@@ -661,11 +674,25 @@ int ocr_set_camera(ocr_forest *F, const ocr_camera *cams, int ncams) {
   F->total_pix = pix;
   if (ncams > 1 && !F->fork) {
     OCR_CUDA(cudaEventCreateWithFlags(&F->fork, cudaEventDisableTiming));
-    for (int q = 0; q < kRenderStreams; ++q) {
+    for (int q = 0; q < kMaxStreams; ++q) {
       OCR_CUDA(cudaStreamCreateWithFlags(&F->sub[q], cudaStreamNonBlocking));
       OCR_CUDA(cudaEventCreateWithFlags(&F->join[q], cudaEventDisableTiming));
     }
   }
+  const int rc = plan_cameras(F);
+  if (rc) return rc;
+  F->has_cam = true;
+  return OCR_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Plan every camera of the last ocr_set_camera: run its pruning and layout
+// once on the device (legacy default stream, blocking) and size its scratch.
+int plan_cameras(ocr_forest *F) {
+  for (CamPlan &P : F->plans) free_plan_buffers(F, P);
   if (F->geometry == OCR_GEOM_SHELL) {
     for (CamPlan &P : F->plans) {
       const int rc = plan_shell(F, P);
@@ -673,10 +700,8 @@ int ocr_set_camera(ocr_forest *F, const ocr_camera *cams, int ncams) {
     }
     OCR_CUDA(shell_rays_prepare());
     OCR_CUDA(shell_bwd_prepare());
-    F->has_cam = true;
     return OCR_OK;
   }
-  // plan every camera: run its pruning and slot layout once and keep the sizes
   const int G = (int)F->h_group_nodes.size();
   Topo T{F->d_geo, F->d_child, F->d_leaves, F->N, F->M, F->L, F->lt};
   for (CamPlan &P : F->plans) {
@@ -702,11 +727,10 @@ int ocr_set_camera(ocr_forest *F, const ocr_camera *cams, int ncams) {
         (rc = dev_alloc(&P.d_entries, (size_t)(total > 0 ? total : 1), F->bytes)))
       return rc;
   }
-  F->has_cam = true;
   return OCR_OK;
 }
 
-}  // extern "C"
+}  // namespace
 
 namespace {
 
@@ -791,18 +815,19 @@ int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats) {
   } else {
     // fan the cameras out over the internal streams and join them back
     OCR_CUDA(cudaEventRecord(F->fork, st));
-    for (int q = 0; q < kRenderStreams; ++q) OCR_CUDA(cudaStreamWaitEvent(F->sub[q], F->fork, 0));
+    const int ns = std::min(F->nstreams, K);
+    for (int q = 0; q < ns; ++q) OCR_CUDA(cudaStreamWaitEvent(F->sub[q], F->fork, 0));
     for (int k = 0; k < K; ++k) {
       CamPlan &P = F->plans[k];
       int *cnt = counts ? counts + P.pix_off : nullptr;
       int rc = F->geometry == OCR_GEOM_SHELL
-                   ? enqueue_shell(F, P, rgba + P.pix_off, cnt, visible,
-                                   F->sub[k % kRenderStreams], false, launches)
-                   : enqueue_camera(F, P, rgba + P.pix_off, cnt, visible,
-                                    F->sub[k % kRenderStreams], false, subtree_ran, launches);
+                   ? enqueue_shell(F, P, rgba + P.pix_off, cnt, visible, F->sub[k % ns], false,
+                                   launches)
+                   : enqueue_camera(F, P, rgba + P.pix_off, cnt, visible, F->sub[k % ns], false,
+                                    subtree_ran, launches);
       if (rc) return rc;
     }
-    for (int q = 0; q < kRenderStreams; ++q) {
+    for (int q = 0; q < ns; ++q) {
       OCR_CUDA(cudaEventRecord(F->join[q], F->sub[q]));
       OCR_CUDA(cudaStreamWaitEvent(st, F->join[q], 0));
     }
@@ -967,6 +992,98 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
   OCR_CUDA(cudaMemcpyAsync(h, F->d_err, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
   OCR_CUDA(cudaStreamSynchronize(st));
   if (h[0]) return OCR_ERR_DEVICE;
+  return OCR_OK;
+}
+
+int ocr_set_tuning(ocr_forest *F, const ocr_tuning *t) {
+  if (!F || !t) return OCR_ERR_INVALID;
+  if (t->tile_depth < 1 || t->tile_depth > kSubtreeDepth || t->streams < 1 ||
+      t->streams > kMaxStreams || t->shell_warps < 0 || t->shell_warps > 8)
+    return OCR_ERR_INVALID;
+  F->nstreams = t->streams;
+  F->shell_warps = t->shell_warps;
+  if (t->tile_depth != F->tile_depth) {
+    F->tile_depth = t->tile_depth;
+    F->lt = F->L > F->tile_depth ? F->L - F->tile_depth : 0;
+    if (F->has_cam && F->geometry == OCR_GEOM_CUBE) {
+      F->has_cam = false;
+      const int rc = plan_cameras(F);
+      if (rc) return rc;
+      F->has_cam = true;
+    }
+  }
+  return OCR_OK;
+}
+
+int ocr_get_tuning(const ocr_forest *F, ocr_tuning *t) {
+  if (!F || !t) return OCR_ERR_INVALID;
+  t->tile_depth = F->tile_depth;
+  t->streams = F->nstreams;
+  t->shell_warps = F->shell_warps;
+  t->ms = 0.f;
+  return OCR_OK;
+}
+
+int ocr_autotune(ocr_forest *F, int reps, ocr_tuning *best, ocr_tuning *tried, int max_tried,
+                 int *ntried) {
+  if (!F || !best || reps < 1 || reps > 100 || max_tried < 0 || (max_tried > 0 && !tried))
+    return OCR_ERR_INVALID;
+  if (!F->has_data || !F->has_cam || !F->has_integ) return OCR_ERR_STATE;
+  const int K = (int)F->plans.size();
+  std::vector<ocr_tuning> cand;
+  const int streams[] = {1, 2, 4, 8};
+  const int warps[] = {1, 2, 4, 8};
+  for (int si = 0; si < 4; ++si) {
+    if (K == 1 && streams[si] != F->nstreams) continue;  // one camera: streams are unused
+    if (F->geometry == OCR_GEOM_SHELL) {
+      for (int w : warps) cand.push_back({F->tile_depth, streams[si], w, 0.f});
+    } else {
+      for (int d = 1; d <= kSubtreeDepth; ++d)
+        if (d <= F->L || d == kSubtreeDepth) cand.push_back({d, streams[si], 0, 0.f});
+    }
+  }
+  float4 *rgba = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = OCR_OK;
+  ocr_tuning keep;
+  ocr_get_tuning(F, &keep);
+  ocr_tuning win = keep;
+  win.ms = INFINITY;
+  int n = 0;
+  cudaError_t ce = cudaMalloc((void **)&rgba, sizeof(float4) * (size_t)F->total_pix);
+  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) rc = cuda_fail(ce);
+  for (size_t c = 0; c < cand.size() && rc == OCR_OK; ++c) {
+    if ((rc = ocr_set_tuning(F, &cand[c]))) break;
+    if ((rc = ocr_render(F, reinterpret_cast<float *>(rgba), st, nullptr))) break;  // warm-up
+    ce = cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && ce == cudaSuccess && rc == OCR_OK; ++r)
+      rc = ocr_render(F, reinterpret_cast<float *>(rgba), st, nullptr);
+    if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
+    if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+    if (ce != cudaSuccess) rc = cuda_fail(ce);
+    if (rc) break;
+    cand[c].ms = ms / (float)reps;
+    if (n < max_tried) tried[n] = cand[c];
+    ++n;
+    if (cand[c].ms < win.ms) win = cand[c];
+  }
+  if (rgba) cudaFree(rgba);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  if (ntried) *ntried = n;
+  if (rc) {
+    ocr_set_tuning(F, &keep);
+    return rc;
+  }
+  if ((rc = ocr_set_tuning(F, &win))) return rc;
+  *best = win;
   return OCR_OK;
 }
 

@@ -144,13 +144,14 @@ cudaError_t shell_pairs(bool fill, const int4 *geo, int N, const Shell &S, const
 // kernel's shared-memory limit to the largest of these and must run before the
 // first launch
 constexpr int kShellMaxCap = 4096;
-int shell_ray_warps(int cap);
-size_t shell_ray_smem(int cap);
+int shell_ray_warps(int cap, int want);
+size_t shell_ray_smem(int cap, int want);
 cudaError_t shell_rays_prepare();
 cudaError_t shell_rays(const int4 *geo, int N, const Shell &S, const Field &Fd, const Cam &C,
                        const Integ &I, const long long *ray_off, long long npix,
                        const unsigned long long *keys, long long key_cap, int cap, float4 *rgba,
-                       int *counts, unsigned long long *stats, int nsm, cudaStream_t st);
+                       int *counts, unsigned long long *stats, int nsm, int want_warps,
+                       cudaStream_t st);
 
 // Adjoint of a shell render (ocr_backward.cu), over lists built by shell_pairs:
 // one warp per ray, kBwdWarps warps per CTA; shell_bwd_prepare raises the

@@ -338,19 +338,23 @@ cudaError_t shell_pairs(bool fill, const int4 *geo, int N, const Shell &S, const
   return cudaGetLastError();
 }
 
-int shell_ray_warps(int cap) {
+// Warps per CTA of shell_rays: `want` if given (0: as many as fit), within
+// 96 KB of shared memory (one warp at least).
+int shell_ray_warps(int cap, int want) {
   const size_t per = (size_t)cap * (sizeof(float4) + sizeof(unsigned long long));
   int w = (int)((96u << 10) / per);
-  return w < 1 ? 1 : (w > 8 ? 8 : w);
+  w = w < 1 ? 1 : (w > 8 ? 8 : w);
+  return (want > 0 && want < w) ? want : w;
 }
 
-size_t shell_ray_smem(int cap) {
-  return (size_t)shell_ray_warps(cap) * cap * (sizeof(float4) + sizeof(unsigned long long));
+size_t shell_ray_smem(int cap, int want) {
+  return (size_t)shell_ray_warps(cap, want) * cap * (sizeof(float4) + sizeof(unsigned long long));
 }
 
 cudaError_t shell_rays_prepare() {
   size_t most = 0;  // the largest launch any list capacity asks for
-  for (int cap = 32; cap <= kShellMaxCap; cap <<= 1) most = most > shell_ray_smem(cap) ? most : shell_ray_smem(cap);
+  for (int cap = 32; cap <= kShellMaxCap; cap <<= 1)
+    most = most > shell_ray_smem(cap, 0) ? most : shell_ray_smem(cap, 0);
   return cudaFuncSetAttribute(shell_rays_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)most);
 }
@@ -358,10 +362,11 @@ cudaError_t shell_rays_prepare() {
 cudaError_t shell_rays(const int4 *geo, int N, const Shell &S, const Field &Fd, const Cam &C,
                        const Integ &I, const long long *ray_off, long long npix,
                        const unsigned long long *keys, long long key_cap, int cap, float4 *rgba,
-                       int *counts, unsigned long long *stats, int nsm, cudaStream_t st) {
+                       int *counts, unsigned long long *stats, int nsm, int want_warps,
+                       cudaStream_t st) {
   if (cap < 32 || cap > kShellMaxCap || (cap & (cap - 1))) return cudaErrorInvalidValue;
-  const size_t smem = shell_ray_smem(cap);
-  const int warps = shell_ray_warps(cap);
+  const size_t smem = shell_ray_smem(cap, want_warps);
+  const int warps = shell_ray_warps(cap, want_warps);
   const long long need = (npix + warps - 1) / warps;
   const long long grid = need < (long long)nsm * 8 ? need : (long long)nsm * 8;
   shell_rays_kernel<<<(unsigned)(grid > 0 ? grid : 1), warps * 32, smem, st>>>(

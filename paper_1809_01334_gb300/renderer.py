@@ -131,6 +131,17 @@ class Renderer:
         capi.render_backward(self.h, g, gn, gt, _stream_ptr(stream))
         return gn, gt
 
+    def autotune(self, reps: int = 3) -> dict:
+        """Time the candidate decompositions on the current cameras and keep
+        the fastest (ocr_autotune)."""
+        return capi.autotune(self.h, reps)
+
+    def set_tuning(self, tile_depth: int = 3, streams: int = 4, shell_warps: int = 0):
+        capi.set_tuning(self.h, tile_depth, streams, shell_warps)
+
+    def get_tuning(self) -> dict:
+        return capi.get_tuning(self.h)
+
     def device_bytes(self) -> int:
         return capi.device_bytes(self.h)
 

@@ -86,6 +86,53 @@ def test_malformed_forests_are_rejected_on_the_host(lib):
     assert _build_rc(lib, lv, an, 25) == capi.ERR_INVALID
 
 
+def _shell_rc(lib, f, tree=None, frames=None, r0=None, r1=None, level=None, anchor=None):
+    lv = np.ascontiguousarray(f.level if level is None else level, np.uint8)
+    an = np.ascontiguousarray(f.anchor if anchor is None else anchor, np.int32)
+    tr = np.ascontiguousarray(f.tree if tree is None else tree, np.int32)
+    d = capi.ForestDesc(capi.GEOM_SHELL, f.max_level, lv.shape[0],
+                        an.ctypes.data_as(C.POINTER(C.c_int32)),
+                        lv.ctypes.data_as(C.POINTER(C.c_uint8)))
+    d.h_tree = tr.ctypes.data_as(C.POINTER(C.c_int32))
+    fr = np.asarray(f.meta["frames"] if frames is None else frames, np.float64).reshape(6, 9)
+    for t in range(6):
+        for k in range(9):
+            d.frames[t][k] = float(fr[t, k])
+    d.r0 = f.meta["r0"] if r0 is None else r0
+    d.r1 = f.meta["r1"] if r1 is None else r1
+    h = C.c_void_p()
+    rc = lib.ocr_build_forest(C.byref(d), None, C.byref(h))
+    if rc == 0:
+        lib.ocr_destroy(h)
+    return rc
+
+
+def test_malformed_shell_forests_are_rejected_on_the_host(lib):
+    f = I.shell_forest(I.shell_noise(1809, 8), 1, 2, 2.0)
+    fr = np.asarray(f.meta["frames"], np.float64)
+    # frames: a tilted normal, two trees around the same axis direction, a repeated axis
+    bad = fr.copy(); bad[0, 0] = [0.6, 0.8, 0.0]
+    assert _shell_rc(lib, f, frames=bad) == capi.ERR_INVALID
+    bad = fr.copy(); bad[1] = bad[0]
+    assert _shell_rc(lib, f, frames=bad) == capi.ERR_INVALID
+    bad = fr.copy(); bad[2, 1] = bad[2, 0]
+    assert _shell_rc(lib, f, frames=bad) == capi.ERR_INVALID
+    # radii, tree ids out of range or out of order, a tree left incomplete
+    assert _shell_rc(lib, f, r0=0.0) == capi.ERR_INVALID
+    assert _shell_rc(lib, f, r0=1.2, r1=1.0) == capi.ERR_INVALID
+    tr = f.tree.copy(); tr[0] = 6
+    assert _shell_rc(lib, f, tree=tr) == capi.ERR_INVALID
+    tr = f.tree.copy(); tr[-1] = 4
+    assert _shell_rc(lib, f, tree=tr) == capi.ERR_INVALID
+    keep = f.tree != 3
+    assert _shell_rc(lib, f, tree=f.tree[keep], level=f.level[keep],
+                     anchor=f.anchor[keep]) == capi.ERR_INVALID
+    # a gap inside a tree
+    drop = np.ones(f.nleaves, bool); drop[np.flatnonzero(f.tree == 2)[3]] = False
+    assert _shell_rc(lib, f, tree=f.tree[drop], level=f.level[drop],
+                     anchor=f.anchor[drop]) == capi.ERR_INVALID
+
+
 def test_null_handles_are_rejected(lib):
     integ = capi.Integrator(0, 4, 1e-6, 0.5, 16)
     assert lib.ocr_set_integrator(None, C.byref(integ)) == capi.ERR_INVALID
@@ -94,4 +141,10 @@ def test_null_handles_are_rejected(lib):
     assert lib.ocr_render(None, None, None, None) == capi.ERR_INVALID
     assert lib.ocr_forest_set_data(None, None, None, 0.0, 1.0, None) == capi.ERR_INVALID
     assert lib.ocr_device_bytes(None) == 0
+    t = capi.Tuning(3, 4, 0, 0.0)
+    lib.ocr_set_tuning.argtypes = [C.c_void_p, C.POINTER(capi.Tuning)]
+    assert lib.ocr_set_tuning(None, C.byref(t)) == capi.ERR_INVALID
+    lib.ocr_autotune.argtypes = [C.c_void_p, C.c_int, C.POINTER(capi.Tuning),
+                                 C.POINTER(capi.Tuning), C.c_int, C.POINTER(C.c_int)]
+    assert lib.ocr_autotune(None, 3, C.byref(t), None, 0, None) == capi.ERR_INVALID
     lib.ocr_destroy(None)

@@ -70,3 +70,51 @@ def test_batch_in_a_cuda_graph():
         torch.cuda.synchronize()
         assert torch.equal(out, ref)
     r.close()
+
+
+@pytest.mark.parametrize("depth", [1, 2, 3])
+def test_every_tile_depth_matches_the_oracle(depth):
+    """The autotuner's tile depths (octree levels merged inside one CTA) all
+    give the oracle's images and segment counts, on several cameras at once
+    with 1, 2 and 8 internal streams."""
+    from paper_1809_01334_gb300 import Renderer
+    f, tf, _ = I.preset_small()
+    cams = _cams()
+    r = Renderer(f, tf, INTEG)
+    r.set_cameras(cams)
+    for streams in (1, 2, 8):
+        r.set_tuning(tile_depth=depth, streams=streams)
+        assert r.get_tuning()["tile_depth"] == depth
+        flat, views, st = r.render_batch(with_index=True)
+        torch.cuda.synchronize()
+        for k in (0, 2):
+            ref = O.render(f, tf, cams[k], INTEG, band_px=4e-3, band_rel=2e-6)
+            assert np.abs(views[k].cpu().numpy() - ref["rgba"]).max() <= 1e-4
+            at = sum(c.w * c.h for c in cams[:k])
+            cnt = st["counts"][at:at + cams[k].w * cams[k].h].cpu().numpy().reshape(ref["counts"].shape)
+            assert not ((cnt != ref["counts"]) & ~ref["uncertain"]).any()
+    r.close()
+
+
+@pytest.mark.parametrize("kind", ["cube", "shell"])
+def test_autotune_keeps_the_fastest_valid_setting(kind):
+    from paper_1809_01334_gb300 import Renderer
+    if kind == "cube":
+        f, tf, _ = I.preset_small()
+        cams = _cams()
+    else:
+        f, tf, _ = I.preset_shell_small()
+        cams = [I.perspective_camera(41 + k, 24 + 7 * k, 20, dist=(2.2, 2.6), target=(0.0, 0.0, 0.0))
+                for k in range(3)]
+    r = Renderer(f, tf, INTEG)
+    r.set_cameras(cams)
+    res = r.autotune(reps=2)
+    tried, best = res["tried"], res["best"]
+    assert len(tried) >= 4 and all(t["ms"] > 0 for t in tried)
+    assert best["ms"] == min(t["ms"] for t in tried)
+    assert r.get_tuning() == {**best, "ms": 0.0}
+    flat, views, st = r.render_batch()
+    torch.cuda.synchronize()
+    ref = O.render(f, tf, cams[1], INTEG)
+    assert np.abs(views[1].cpu().numpy() - ref["rgba"]).max() <= 1e-4
+    r.close()
