@@ -55,7 +55,9 @@ class Camera_(C.Structure):
 
 class Integrator_(C.Structure):
     _fields_ = [("method", C.c_int), ("nsteps", C.c_int), ("tol", C.c_double),
-                ("c_rk", C.c_double), ("max_depth", C.c_int), ("bg", C.c_double * 3)]
+                ("c_rk", C.c_double), ("max_depth", C.c_int), ("bg", C.c_double * 3),
+                ("surface", C.c_int), ("s_iso", C.c_double), ("a_s", C.c_double),
+                ("i_s", C.c_double * 3)]
 
 
 def lib():
@@ -92,6 +94,10 @@ def lib():
                                     d, P(C.c_int32), P(C.c_uint8), C.c_double, C.c_double,
                                     C.c_int, P(C.c_int64)]
         _lib.orc_render.restype = C.c_int64
+        _lib.orc_render_ex.argtypes = [P(Forest_), P(Camera_), P(Integrator_), P(C.c_int),
+                                       C.c_int, d, P(C.c_int32), P(C.c_int32), P(C.c_uint8),
+                                       C.c_double, C.c_double, C.c_int, P(C.c_int64)]
+        _lib.orc_render_ex.restype = C.c_int64
         _lib.orc_render_grad.argtypes = [P(Forest_), P(Camera_), P(Integrator_), d, d, d, C.c_int]
         _lib.orc_render_grad.restype = C.c_int
     return _lib
@@ -153,6 +159,11 @@ def integrator_struct(integ: dict, bg=(0.0, 0.0, 0.0)) -> Integrator_:
     else:
         raise ValueError(integ["method"])
     s.bg[:] = bg
+    surf = integ.get("surface")
+    if surf:  # Sec. 2.8 on the isosurface s = s_iso: {"s_iso", "a_s", "i_s"}
+        s.surface = 1
+        s.s_iso, s.a_s = float(surf["s_iso"]), float(surf["a_s"])
+        s.i_s[:] = [float(x) for x in surf["i_s"]]
     return s
 
 
@@ -294,15 +305,17 @@ def render(forest, tf, cam, integ: dict, rows=None, bg=(0.0, 0.0, 0.0), nthreads
     nr = int(rows_arr.shape[0])
     rgba = np.zeros((nr, cam.w, 4), dtype=np.float64)
     counts = np.zeros((nr, cam.w), dtype=np.int32)
+    cross = np.zeros((nr, cam.w), dtype=np.int32)
     unc = np.zeros((nr, cam.w), dtype=np.uint8)
     steps = C.c_int64(0)
-    total = lib().orc_render(C.byref(of.s), C.byref(cs), C.byref(ist), _ptr(rows_arr, C.c_int),
-                             nr, _ptr(rgba, C.c_double), _ptr(counts, C.c_int32),
-                             _ptr(unc, C.c_uint8), float(band_px), float(band_rel),
-                             int(nthreads), C.byref(steps))
+    total = lib().orc_render_ex(C.byref(of.s), C.byref(cs), C.byref(ist), _ptr(rows_arr, C.c_int),
+                                nr, _ptr(rgba, C.c_double), _ptr(counts, C.c_int32),
+                                _ptr(cross, C.c_int32), _ptr(unc, C.c_uint8), float(band_px),
+                                float(band_rel), int(nthreads), C.byref(steps))
     if total < 0:
         raise MemoryError("oracle render: allocation failed")
-    return {"rgba": rgba, "counts": counts, "uncertain": unc.astype(bool), "ties": unc.astype(int),
+    return {"rgba": rgba, "counts": counts, "crossings": cross, "uncertain": unc.astype(bool),
+            "ties": unc.astype(int),
             "segments": int(total), "steps": int(steps.value), "rows": rows_arr}
 
 

@@ -466,37 +466,12 @@ static void seg_init(seg_ctx *S, const orc_forest *F, int leaf, const double *or
   S->rlen = sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
 }
 
-/* One classical RK4 step of length hs starting at distance x0 from the far
- * end, from the state y0 (NULL: from (1, 0)). */
-static void rk4_segment_from(const seg_ctx *S, double x0, double hs, const double *y0,
-                             double *out);
-
-/* Classical RK4 on A' = -kappa A, B' = q - kappa B (Eq. 2.29), x from the far
- * end, state continued across nsteps equal steps starting from (1, 0). */
-static void rk4_segment(const seg_ctx *S, double dx, int nsteps, double *y) {
-  y[0] = 1.0; y[1] = y[2] = y[3] = 0.0;
-  double hs = dx / nsteps;
-  for (int n = 0; n < nsteps; ++n) {
-    double x0 = n * hs;
-    double kq0[4], kq1[4], kq2[4];
-    medium_at(S, x0, kq0);
-    medium_at(S, x0 + 0.5 * hs, kq1);
-    medium_at(S, x0 + hs, kq2);
-    double k1[4], k2[4], k3[4], k4[4], yt[4];
-    /* f(x, Y) = (-kappa A, q - kappa B) */
+/* f(x, Y) = (-kappa A, q - kappa B) of Eq. 2.29 */
 #define RHS(kq, Y, K) do { (K)[0] = -(kq)[0] * (Y)[0]; \
       for (int c = 1; c < 4; ++c) (K)[c] = (kq)[c] - (kq)[0] * (Y)[c]; } while (0)
-    RHS(kq0, y, k1);
-    for (int c = 0; c < 4; ++c) yt[c] = y[c] + 0.5 * hs * k1[c];
-    RHS(kq1, yt, k2);
-    for (int c = 0; c < 4; ++c) yt[c] = y[c] + 0.5 * hs * k2[c];
-    RHS(kq1, yt, k3);
-    for (int c = 0; c < 4; ++c) yt[c] = y[c] + hs * k3[c];
-    RHS(kq2, yt, k4);
-    for (int c = 0; c < 4; ++c) y[c] += hs / 6.0 * (k1[c] + 2.0 * k2[c] + 2.0 * k3[c] + k4[c]);
-  }
-}
 
+/* Classical RK4 on A' = -kappa A, B' = q - kappa B (Eq. 2.29), x from the far
+ * end: one step of length hs from x0, from the state y0 (NULL: from (1, 0)). */
 static void rk4_segment_from(const seg_ctx *S, double x0, double hs, const double *y0,
                              double *out) {
   double y[4] = {1.0, 0.0, 0.0, 0.0};
@@ -639,19 +614,113 @@ static void segeval(const seg_ctx *S, const orc_integrator *I, double x1, double
   memcpy(out, y5, sizeof y5);
 }
 
-void orc_segment_ab(const orc_forest *F, const orc_integrator *I, int leaf, const double *org,
-                    const double *dir, double a_in, double a_out, double *seg4, int64_t *nsteps) {
+/* The volume between distances x1 < x2 from the far end: RK4 with nsteps
+ * equal steps over the piece, or Algorithm 1 on it. */
+static void volume_piece(const seg_ctx *S, const orc_integrator *I, double x1, double x2,
+                         double *seg4, int64_t *nsteps) {
+  if (I->method == ORC_RK4) {
+    double y[4] = {1.0, 0.0, 0.0, 0.0}, hs = (x2 - x1) / I->nsteps;
+    for (int n = 0; n < I->nsteps; ++n) rk4_segment_from(S, x1 + n * hs, hs, y, y);
+    memcpy(seg4, y, sizeof y);
+    *nsteps += I->nsteps;
+  } else {
+    segeval(S, I, x1, x2, 0, seg4, nsteps);
+  }
+}
+
+/* Trilinear gradient of the field in space at distance x from the far end. */
+static void field_grad(const seg_ctx *S, double x, double *g) {
+  double u[3], d[3] = {0.0, 0.0, 0.0};
+  local_coords(S, x, u);
+  for (int c = 0; c < 8; ++c) {
+    double w[3], dw[3];
+    for (int a = 0; a < 3; ++a) {
+      int b = (c >> a) & 1;
+      w[a] = b ? u[a] : 1.0 - u[a];
+      dw[a] = b ? 1.0 : -1.0;
+    }
+    d[0] += (double)S->nodal[c] * dw[0] * w[1] * w[2];
+    d[1] += (double)S->nodal[c] * w[0] * dw[1] * w[2];
+    d[2] += (double)S->nodal[c] * w[0] * w[1] * dw[2];
+  }
+  for (int a = 0; a < 3; ++a) g[a] = d[a] / S->h;
+}
+
+/* Crossings of the isosurface inside a segment of length dx: sign changes of
+ * s - s_iso between the samples x_k = k dx / 8, each located by bisection.
+ * Returns their number (far to near) in xs; *tie is raised when a sample lies
+ * within band of s_iso. */
+static int iso_crossings(const seg_ctx *S, const orc_integrator *I, double dx, double *xs,
+                         double band, int *tie) {
+  double g[9];
+  for (int k = 0; k <= 8; ++k) {
+    double u[3];
+    local_coords(S, dx * k / 8.0, u);
+    g[k] = field_at(S, u) - I->s_iso;
+    if (tie && fabs(g[k]) <= band) *tie = 1;
+  }
+  int n = 0;
+  for (int k = 0; k < 8; ++k) {
+    if (!((g[k] < 0.0 && g[k + 1] > 0.0) || (g[k] > 0.0 && g[k + 1] < 0.0))) continue;
+    double lo = dx * k / 8.0, hi = dx * (k + 1) / 8.0, glo = g[k];
+    for (int it = 0; it < 60; ++it) {
+      double mid = 0.5 * (lo + hi), u[3];
+      local_coords(S, mid, u);
+      double gm = field_at(S, u) - I->s_iso;
+      if ((gm < 0.0) == (glo < 0.0)) {
+        lo = mid;
+        glo = gm;
+      } else {
+        hi = mid;
+      }
+    }
+    xs[n++] = 0.5 * (lo + hi);
+  }
+  return n;
+}
+
+/* Eqs. 2.18 and 2.35: the surface segment at distance x from the far end. */
+static void iso_segment(const seg_ctx *S, const orc_integrator *I, double x, double *seg4) {
+  double g[3];
+  field_grad(S, x, g);
+  double gn = sqrt(dot3(g, g));
+  double cphi = gn > 0.0 ? fabs(dot3(g, S->dir)) / (gn * S->rlen) : 1.0;
+  double A = I->a_s >= 1.0 ? 1.0 : (cphi <= 0.0 ? 0.0 : pow(I->a_s, 1.0 / cphi));
+  seg4[0] = A;
+  for (int c = 0; c < 3; ++c) seg4[1 + c] = I->i_s[c] * (1.0 - A);
+}
+
+static void segment_value(const orc_forest *F, const orc_integrator *I, int leaf,
+                          const double *org, const double *dir, double a_in, double a_out,
+                          double *seg4, int64_t *nsteps, int *ncross, double band, int *tie) {
   seg_ctx S;
   seg_init(&S, F, leaf, org, dir, a_out);
   double dx = S.rlen * (a_out - a_in);
   int64_t dummy = 0;
   if (!nsteps) nsteps = &dummy;
-  if (I->method == ORC_RK4) {
-    rk4_segment(&S, dx, I->nsteps, seg4);
-    *nsteps += I->nsteps;
-  } else {
-    segeval(&S, I, 0.0, dx, 0, seg4, nsteps);
+  if (!I->surface || F->geometry != 0) {
+    volume_piece(&S, I, 0.0, dx, seg4, nsteps);
+    return;
   }
+  double xs[8], acc[4] = {1.0, 0.0, 0.0, 0.0}, piece[4], x1 = 0.0;
+  int m = iso_crossings(&S, I, dx, xs, band, tie);
+  if (ncross) *ncross += m;
+  for (int k = 0; k <= m; ++k) {  /* far to near: volume, surface, volume, ... */
+    double x2 = k < m ? xs[k] : dx;
+    volume_piece(&S, I, x1, x2, piece, nsteps);
+    orc_combine(piece, acc, acc);
+    if (k < m) {
+      iso_segment(&S, I, x2, piece);
+      orc_combine(piece, acc, acc);
+    }
+    x1 = x2;
+  }
+  memcpy(seg4, acc, sizeof acc);
+}
+
+void orc_segment_ab(const orc_forest *F, const orc_integrator *I, int leaf, const double *org,
+                    const double *dir, double a_in, double a_out, double *seg4, int64_t *nsteps) {
+  segment_value(F, I, leaf, org, dir, a_in, a_out, seg4, nsteps, NULL, 0.0, NULL);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -735,7 +804,19 @@ int64_t orc_render(const orc_forest *F, const orc_camera *C, const orc_integrato
                    const int *rows, int nrows, double *rgba, int32_t *counts,
                    uint8_t *uncertain, double band_px, double band_rel, int nthreads,
                    int64_t *nsteps_total) {
+  return orc_render_ex(F, C, I, rows, nrows, rgba, counts, NULL, uncertain, band_px, band_rel,
+                       nthreads, nsteps_total);
+}
+
+int64_t orc_render_ex(const orc_forest *F, const orc_camera *C, const orc_integrator *I,
+                      const int *rows, int nrows, double *rgba, int32_t *counts,
+                      int32_t *crossings, uint8_t *uncertain, double band_px, double band_rel,
+                      int nthreads, int64_t *nsteps_total) {
   const int W = C->w, H = C->h;
+  /* isosurface ties: a sample within this of s_iso (FP32 field values carry
+   * relative errors of a few 1e-7 of the data's magnitude) */
+  const double smag = fabs(F->s_max) > fabs(F->s_min) ? fabs(F->s_max) : fabs(F->s_min);
+  const double sband = 10.0 * band_rel * (smag > 0.0 ? smag : 1.0);
   if (!rows) nrows = H;
   /* candidate rectangle of every leaf: its pixel rectangle widened by one
    * pixel, so that a ray hitting the leaf is never missed through rounding */
@@ -820,7 +901,7 @@ int64_t orc_render(const orc_forest *F, const orc_camera *C, const orc_integrato
       for (int i = 0; i < W; ++i) {
         double org[3], dir[3], amin, amax;
         orc_pixel_ray(C, i, j, org, dir, &amin, &amax);
-        int ns = 0, nties = 0;
+        int ns = 0, nties = 0, ncross = 0;
         for (int q = cstart[i]; q < cstart[i + 1]; ++q) {
           int l = pl[pord[q]];
           double a_in[2], a_out[2];
@@ -843,7 +924,10 @@ int64_t orc_render(const orc_forest *F, const orc_camera *C, const orc_integrato
             sg[ns].a_in = a_in[k];
             sg[ns].a_out = a_out[k];
             int64_t st = 0;
-            orc_segment_ab(F, I, l, org, dir, a_in[k], a_out[k], sg[ns].s, &st);
+            int stie = 0;
+            segment_value(F, I, l, org, dir, a_in[k], a_out[k], sg[ns].s, &st, &ncross, sband,
+                          &stie);
+            nties += stie;
             steps += st;
             ++ns;
           }
@@ -851,6 +935,7 @@ int64_t orc_render(const orc_forest *F, const orc_camera *C, const orc_integrato
         size_t pix = (size_t)r * W + i;
         composite(sg, ns, I->bg, rgba + 4 * pix);
         if (counts) counts[pix] = ns;
+        if (crossings) crossings[pix] = ncross;
         if (uncertain) uncertain[pix] = (uint8_t)(nties < 255 ? nties : 255);
         total += ns;
       }

@@ -64,6 +64,14 @@ typedef struct {
   double c_rk;     /* split when dx * kappa(xi_j) > c_rk at any stage point */
   int max_depth;   /* bisection depth cap */
   double bg[3];    /* background intensity I_b per channel */
+  /* Sec. 2.8 on the isosurface s = s_iso of the field (cube forests): where a
+   * segment's field crosses s_iso, the segment is cut there and a surface
+   * segment A_phi = a_s^(1 / cos phi), B_phi = i_s (1 - A_phi) (Eqs. 2.18,
+   * 2.35) inserted, phi the angle between the ray and the field gradient.
+   * Crossings are the sign changes of s - s_iso between 9 equally spaced
+   * samples of the segment (far end to near end), located by bisection. */
+  int surface;
+  double s_iso, a_s, i_s[3];
 } orc_integrator;
 
 /* Segment algebra on (A, B_r, B_g, B_b). */
@@ -131,6 +139,14 @@ int64_t orc_render(const orc_forest *F, const orc_camera *C, const orc_integrato
                    const int *rows, int nrows, double *rgba, int32_t *counts,
                    uint8_t *uncertain, double band_px, double band_rel, int nthreads,
                    int64_t *nsteps_total);
+
+/* The same, also writing crossings[nrows*w] (isosurface crossings per ray;
+ * may be NULL); a ray with a sample within the tie band of s_iso counts as a
+ * tie in uncertain. */
+int64_t orc_render_ex(const orc_forest *F, const orc_camera *C, const orc_integrator *I,
+                      const int *rows, int nrows, double *rgba, int32_t *counts,
+                      int32_t *crossings, uint8_t *uncertain, double band_px, double band_rel,
+                      int nthreads, int64_t *nsteps_total);
 
 /* Gradient of L with respect to the nodal values and the transfer-function
  * knots, given dL/d(rgba) per pixel [h*w*4] (row-major).  FP64 reverse mode:

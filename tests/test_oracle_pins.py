@@ -612,6 +612,97 @@ def test_equilibrium_interface_converges_to_the_ode_with_emission_kappa_times_in
     assert errs[2] < errs[1] < errs[0] and errs[2] < 2e-7 and errs[1] / errs[2] > 10, errs
 
 
+# ------------------------------------------------------- Sec. 2.8 surfaces --
+def _surface_case(a_s, nodal, kappa=3.0, inten=(0.2, 0.5, 0.9), c=(1, 2, 0.5), s_iso=0.5):
+    f, tf = _one_leaf(nodal, np.tile(np.concatenate([[kappa], inten]), (8, 1)))
+    of = O.OracleForest(f, tf)
+    d = np.array(c, float)
+    d /= np.linalg.norm(d) * 2.0
+    org = np.array([0.43, 0.52, 0.55]) - 4.0 * d  # off the leaf's centre: no sample on the plane
+    hit, a0, a1 = O.ray_leaf(of, 0, org, d, 0.0, 1e9)
+    assert hit
+    integ = {"method": "equilibrium", "c_rk": 1e9, "max_depth": 0,
+             "surface": {"s_iso": s_iso, "a_s": a_s, "i_s": (0.7, 0.1, 0.3)}}
+    seg, _ = O.segment_ab(of, integ, 0, org, d, a0, a1)
+    return seg, org, d, a0, a1, kappa, np.asarray(inten, np.float32).astype(np.float64)
+
+
+def _const_piece(kappa, inten, L):
+    A = math.exp(-kappa * L)
+    return np.concatenate([[A], inten * (1.0 - A)])
+
+
+@pytest.mark.parametrize("plane", ["x", "y+2z"])
+def test_planar_isosurface_closed_form(plane):
+    """Eq. 2.35 on a plane (the isosurface 1/2 of the field s = x, or of
+    s = (y + 2z)/4 at 3/8, whose normal is (0, 1, 2)/sqrt 5) inside a constant medium:
+    the segment is near piece (+) surface (+) far piece, the surface with
+    A = a_s^(1/cos phi), phi between the ray and the normal, and B = I_s (1 - A)
+    (Eq. 2.18)."""
+    if plane == "x":
+        nodal = [float(c & 1) for c in range(8)]  # s = u_x
+        nrm, iso = np.array([1.0, 0.0, 0.0]), 0.5
+    else:
+        nodal = [(((c >> 1) & 1) + 2.0 * ((c >> 2) & 1)) / 4.0 for c in range(8)]  # exact in float32
+        nrm, iso = np.array([0.0, 1.0, 2.0]) / math.sqrt(5.0), 0.375
+    for a_s in (0.0, 0.35, 0.9):
+        seg, org, d, a0, a1, kappa, inten = _surface_case(a_s, nodal, s_iso=iso)
+        rl = np.linalg.norm(d)
+        # crossing of the plane n . x = n . (1/2, 1/2, 1/2)
+        ac = (nrm @ np.full(3, 0.5) - nrm @ org) / (nrm @ d)
+        assert a0 < ac < a1
+        near = _const_piece(kappa, inten, (ac - a0) * rl)
+        far = _const_piece(kappa, inten, (a1 - ac) * rl)
+        cphi = abs(nrm @ d) / rl
+        A = a_s ** (1.0 / cphi)
+        surf = np.concatenate([[A], np.array([0.7, 0.1, 0.3]) * (1.0 - A)])
+        exp = O.combine(near, O.combine(surf, far))
+        np.testing.assert_allclose(seg, exp, rtol=1e-10, atol=1e-12)
+
+
+def test_transparent_surface_is_invisible_and_opaque_surface_hides_the_rest():
+    """a_s = 1 leaves the segment unchanged (B_s = I_s (1 - 1) = 0); a_s = 0
+    makes everything behind the surface invisible."""
+    nodal = [float(c & 1) for c in range(8)]
+    seg1, org, d, a0, a1, kappa, inten = _surface_case(1.0, nodal)
+    rl = np.linalg.norm(d)
+    np.testing.assert_allclose(seg1, _const_piece(kappa, inten, (a1 - a0) * rl), rtol=1e-12)
+    seg0, *_ = _surface_case(0.0, nodal)
+    ac = (0.5 - org[0]) / d[0]
+    near = _const_piece(kappa, inten, (ac - a0) * rl)
+    assert seg0[0] == 0.0
+    np.testing.assert_allclose(seg0[1:], near[1:] + near[0] * np.array([0.7, 0.1, 0.3]),
+                               rtol=1e-12)
+
+
+def test_two_crossings_and_none():
+    """s = (2x - 1)(2y - 1) vanishes on the planes x = 1/2 and y = 1/2: a ray
+    crossing both inside the leaf meets the isosurface s = 0 twice, in order;
+    a ray through a region where s keeps its sign meets it never."""
+    nodal = [(2 * (c & 1) - 1) * (2 * ((c >> 1) & 1) - 1) * 1.0 for c in range(8)]
+    f, tf = _one_leaf(nodal, np.tile([2.0, 0.2, 0.5, 0.9], (8, 1)))
+    tf.s_min, tf.s_max = -1.0, 1.0
+    cam = I.Camera(o=(0.37, 0.61, 3.0), v=(0.0, 0.0, -1.0), t=(1.0, 0.0, 0.0), u=(0.0, 1.0, 0.0),
+                   ell=0.125, near=1.0, far=1e30, w=4, h=4, ortho=True)
+    surf = {"method": "equilibrium", "c_rk": 1e9, "max_depth": 0,
+            "surface": {"s_iso": 0.0, "a_s": 0.5, "i_s": (1.0, 1.0, 1.0)}}
+    r = O.render(f, tf, cam, surf)
+    # orthographic rays along -z never cross the planes x = 1/2, y = 1/2
+    assert (r["crossings"] == 0).all()
+    of = O.OracleForest(f, tf)
+    d = np.array([0.8, 0.9, 0.1])
+    org = np.array([0.05, 0.1, 0.45])
+    hit, a0, a1 = O.ray_leaf(of, 0, org - d, d, 0.0, 1e9)
+    seg, _ = O.segment_ab(of, dict(surf, surface=dict(surf["surface"], a_s=0.0)), 0, org - d, d,
+                          a0, a1)
+    # an opaque surface: only the volume before the first crossing (x = 1/2 at
+    # alpha 1 + 0.45/0.8, y = 1/2 at 1 + 0.4/0.9) and the surface's intensity
+    first = 1.0 + min(0.45 / 0.8, 0.4 / 0.9)
+    near = _const_piece(2.0, np.array([0.2, 0.5, 0.9], np.float32).astype(float),
+                        (first - a0) * np.linalg.norm(d))
+    np.testing.assert_allclose(seg, [0.0, *(near[1:] + near[0])], rtol=1e-10)
+
+
 # ------------------------------------------------------- gradient (reverse) --
 def _loss(forest, tf, cam, integ, W, bg):
     r = O.render(forest, tf, cam, integ, bg=bg)
