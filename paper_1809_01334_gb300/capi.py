@@ -37,7 +37,8 @@ class Camera(C.Structure):
 
 class Integrator(C.Structure):
     _fields_ = [("method", C.c_int), ("nsteps", C.c_int), ("tol", C.c_float), ("c_rk", C.c_float),
-                ("max_depth", C.c_int), ("bg", C.c_float * 3)]
+                ("max_depth", C.c_int), ("bg", C.c_float * 3), ("surface", C.c_int),
+                ("s_iso", C.c_float), ("a_s", C.c_float), ("i_s", C.c_float * 3)]
 
 
 class Stats(C.Structure):
@@ -140,9 +141,14 @@ def forest_set_data(h, d_nodal, d_tf, s_min: float, s_max: float, stream=None):
 
 
 def set_integrator(h, method: int, nsteps: int = 4, tol: float = 1e-6, c_rk: float = 0.5,
-                   max_depth: int = 16, bg=(0.0, 0.0, 0.0)):
+                   max_depth: int = 16, bg=(0.0, 0.0, 0.0), surface=None):
+    """surface: None, or {"s_iso", "a_s", "i_s"} for the isosurface of Sec. 2.8."""
     s = Integrator(int(method), int(nsteps), float(tol), float(c_rk), int(max_depth))
     s.bg[:] = bg
+    if surface:
+        s.surface = 1
+        s.s_iso, s.a_s = float(surface["s_iso"]), float(surface["a_s"])
+        s.i_s[:] = [float(x) for x in surface["i_s"]]
     _check(lib().ocr_set_integrator(h, C.byref(s)), "ocr_set_integrator")
 
 

@@ -645,12 +645,20 @@ int ocr_set_integrator(ocr_forest *F, const ocr_integrator *I) {
   } else {
     return OCR_ERR_UNSUPPORTED;
   }
+  if (I->surface) {
+    if (F->geometry != OCR_GEOM_CUBE) return OCR_ERR_UNSUPPORTED;
+    if (!(I->a_s >= 0.f && I->a_s <= 1.f) || !std::isfinite(I->s_iso)) return OCR_ERR_INVALID;
+  }
   F->integ.method = I->method;
   F->integ.nsteps = I->nsteps;
   F->integ.tol = I->tol;
   F->integ.c_rk = I->c_rk;
   F->integ.max_depth = I->max_depth;
   for (int c = 0; c < 3; ++c) F->integ.bg[c] = I->bg[c];
+  F->integ.surface = I->surface ? 1 : 0;
+  F->integ.s_iso = I->s_iso;
+  F->integ.a_s = I->a_s;
+  for (int c = 0; c < 3; ++c) F->integ.i_s[c] = I->i_s[c];
   F->has_integ = true;
   return OCR_OK;
 }
@@ -897,6 +905,7 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
   if (!F || !d_dL_drgba || !d_grad_nodal || !d_grad_tf) return OCR_ERR_INVALID;
   if (!F->has_data || !F->has_cam || !F->has_integ) return OCR_ERR_STATE;
   if (F->integ.method != OCR_RK4 && F->integ.method != OCR_DOPRI5) return OCR_ERR_UNSUPPORTED;
+  if (F->integ.surface) return OCR_ERR_UNSUPPORTED;
   if ((uintptr_t)d_dL_drgba & 15) return OCR_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   if (F->geometry == OCR_GEOM_SHELL) {

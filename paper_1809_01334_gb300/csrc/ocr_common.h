@@ -19,11 +19,13 @@ struct Cam {
 };
 
 struct Integ {
-  int method;  // 0 = RK4 x nsteps, 1 = DOPRI5 inside Algorithm 1
+  int method;  // 0 RK4 x nsteps; inside Algorithm 1: 1 DOPRI5, 2 Gauss-2, 3 Simpson, 4 Eq. 2.18
   int nsteps;
   float tol, c_rk;
   int max_depth;
   float bg[3];
+  int surface;           // isosurface s = s_iso rendered with (a_s, i_s) (Sec. 2.8)
+  float s_iso, a_s, i_s[3];
 };
 
 // Unified node numbering: [0, N) leaves in Morton order, [N, N + M) internal

@@ -107,6 +107,10 @@ __device__ __forceinline__ float4 tf_lookup(const TF &tf, float s) {
   return make_float4(fmaf(w, d.x, a.x), fmaf(w, d.y, a.y), fmaf(w, d.z, a.z), fmaf(w, d.w, a.w));
 }
 
+__device__ __forceinline__ float cubic_at(const Cubic &c, float tau) {
+  return fmaf(fmaf(fmaf(c.p3, tau, c.p2), tau, c.p1), tau, c.p0);
+}
+
 // The medium at parameter tau of a segment through a cube leaf.
 __device__ __forceinline__ float4 medium(const Cubic &c, const TF &tf, float tau) {
   return tf_lookup(tf, fmaf(fmaf(fmaf(c.p3, tau, c.p2), tau, c.p1), tau, c.p0));
@@ -349,8 +353,81 @@ __device__ int4 box_rect(const Cam &c, float3 lo, float h) {
 }
 
 
+// ----------------------------------------------------------- surfaces --
+// The cubic on [ta, tb], reparametrised to [0, 1].
+__device__ __forceinline__ Cubic sub_cubic(const Cubic &c, float ta, float tb) {
+  const float L = tb - ta;
+  Cubic r;
+  r.p0 = fmaf(fmaf(fmaf(c.p3, ta, c.p2), ta, c.p1), ta, c.p0);
+  r.p1 = L * fmaf(fmaf(3.f * c.p3, ta, 2.f * c.p2), ta, c.p1);
+  r.p2 = L * L * fmaf(3.f * c.p3, ta, c.p2);
+  r.p3 = L * L * L * c.p3;
+  return r;
+}
+
+// Sec. 2.8 on the isosurface s = s_iso: the sign changes of s - s_iso between
+// 9 equally spaced samples (far end to near end) are located by bisection;
+// the segment is cut there and, at each crossing, the surface segment of
+// Eqs. 2.18 and 2.35 (A = a_s^(1 / cos phi), B = i_s (1 - A), phi between the
+// ray and the field gradient) goes between the two pieces.
+__device__ float4 iso_split_segment(const Cubic &cu, const float *__restrict__ nd,
+                                                 float3 uf, float3 du, float3 dir, const TF &tf,
+                                                 float dx, const Integ &I, int &steps) {
+  float4 acc = seg_identity();
+  float t1 = 0.f;
+  float gp = cubic_at(cu, 0.f) - I.s_iso;
+  for (int k = 0; k < 8; ++k) {
+    const float tk1 = (float)(k + 1) * 0.125f;
+    const float gn = cubic_at(cu, tk1) - I.s_iso;
+    if ((gp < 0.f && gn > 0.f) || (gp > 0.f && gn < 0.f)) {
+      float lo = (float)k * 0.125f, hi = tk1, glo = gp;
+      for (int it = 0; it < 24; ++it) {
+        const float mid = 0.5f * (lo + hi), gm = cubic_at(cu, mid) - I.s_iso;
+        if ((gm < 0.f) == (glo < 0.f)) {
+          lo = mid;
+          glo = gm;
+        } else {
+          hi = mid;
+        }
+      }
+      const float tc = 0.5f * (lo + hi);
+      acc = seg_combine(integrate_segment(sub_cubic(cu, t1, tc), tf, dx * (tc - t1), I, steps),
+                        acc);
+      // gradient of the trilinear interpolant (its direction is all that counts)
+      const float u = fmaf(tc, du.x, uf.x), v = fmaf(tc, du.y, uf.y), w = fmaf(tc, du.z, uf.z);
+      float g[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const float n = __ldg(nd + c);
+        const float wx = (c & 1) ? u : 1.f - u, wy = (c & 2) ? v : 1.f - v,
+                    wz = (c & 4) ? w : 1.f - w;
+        const float sx = (c & 1) ? 1.f : -1.f, sy = (c & 2) ? 1.f : -1.f,
+                    sz = (c & 4) ? 1.f : -1.f;
+        g[0] = fmaf(n * sx, wy * wz, g[0]);
+        g[1] = fmaf(n * sy, wx * wz, g[1]);
+        g[2] = fmaf(n * sz, wx * wy, g[2]);
+      }
+      const float gn2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+      const float rl = sqrtf(dir.x * dir.x + dir.y * dir.y + dir.z * dir.z);
+      const float cphi = gn2 > 0.f ? fabsf(g[0] * dir.x + g[1] * dir.y + g[2] * dir.z) /
+                                         (sqrtf(gn2) * rl)
+                                   : 1.f;
+      const float A = I.a_s >= 1.f ? 1.f
+                      : (I.a_s <= 0.f || cphi <= 0.f) ? 0.f
+                                                      : exp2f(log2f(I.a_s) / cphi);
+      const float om = 1.f - A;
+      acc = seg_combine(make_float4(A, I.i_s[0] * om, I.i_s[1] * om, I.i_s[2] * om), acc);
+      t1 = tc;
+    }
+    gp = gn;
+  }
+  return seg_combine(integrate_segment(sub_cubic(cu, t1, 1.f), tf, dx * (1.f - t1), I, steps),
+                     acc);
+}
+
 // The segment of one leaf along one ray: slab interval, reference coordinates
 // of its far end and their change to the near end, field cubic, integration.
+template <bool SURF = false>
 __device__ __forceinline__ float4 leaf_segment(const Topo &T, const Field &Fd, const Cam &c,
                                                const Integ &I, const TF &tf, int leaf, float3 org,
                                                float3 dir, float3 inv, float scale, int &steps) {
@@ -367,6 +444,8 @@ __device__ __forceinline__ float4 leaf_segment(const Topo &T, const Field &Fd, c
   const float dx =
       fmaxf(a_out - a_in, 0.f) * sqrtf(dir.x * dir.x + dir.y * dir.y + dir.z * dir.z);
   const Cubic cu = field_cubic(Fd.nodal + 8 * (size_t)leaf, ufar, du);
+  if (SURF)
+    return iso_split_segment(cu, Fd.nodal + 8 * (size_t)leaf, ufar, du, dir, tf, dx, I, steps);
   return integrate_segment(cu, tf, dx, I, steps);
 }
 

@@ -207,6 +207,7 @@ constexpr int kSubtreeThreads = kChunk;  // one chunk per CTA
 constexpr int kCand = kSubtreeThreads;  // candidate table of phase A
 constexpr int kWarpBatch = 32; // hits per warp batch of phase C
 
+template <bool SURF>
 __global__ void __launch_bounds__(kSubtreeThreads, 1024 / kSubtreeThreads)
     subtree_kernel(Topo T, Field Fd, Cam c, Integ I, Scratch S, int nb, int ne, long long s0,
                    long long s1) {
@@ -439,7 +440,7 @@ __global__ void __launch_bounds__(kSubtreeThreads, 1024 / kSubtreeThreads)
         const int leaf = leaf_base + (int)(s_list[h - owpre][t] & 0x3fffffu);
         const float3 ro = make_float3(s_ray[0][t], s_ray[1][t], s_ray[2][t]);
         const float3 rd = make_float3(s_ray[3][t], s_ray[4][t], s_ray[5][t]);
-        s_res[wid][h - b0] = leaf_segment(T, Fd, c, I, tf, leaf, ro, rd,
+        s_res[wid][h - b0] = leaf_segment<SURF>(T, Fd, c, I, tf, leaf, ro, rd,
                                           make_float3(recip_or_zero(rd.x), recip_or_zero(rd.y),
                                                       recip_or_zero(rd.z)),
                                           scale, steps);
@@ -465,7 +466,7 @@ __global__ void __launch_bounds__(kSubtreeThreads, 1024 / kSubtreeThreads)
   }
 }
 
-template <bool FINAL>
+template <bool FINAL, bool SURF>
 __global__ void __launch_bounds__(kCoarsenThreads, 8)
     coarsen_kernel(Topo T, Field Fd, Cam c, Integ I, Scratch S, int nb, int ne, long long s0,
                    long long s1, float4 *rgba) {
@@ -562,7 +563,7 @@ __global__ void __launch_bounds__(kCoarsenThreads, 8)
     float3 o2, d2;
     pixel_ray(c, p.x, p.y, o2, d2);
     const float3 iv2 = make_float3(recip_or_zero(d2.x), recip_or_zero(d2.y), recip_or_zero(d2.z));
-    s_seg[q][st] = leaf_segment(T, Fd, c, I, tf, leaf, o2, d2, iv2, scale, steps);
+    s_seg[q][st] = leaf_segment<SURF>(T, Fd, c, I, tf, leaf, o2, d2, iv2, scale, steps);
   }
   __syncthreads();
 
@@ -679,7 +680,12 @@ cudaError_t launch_subtree(const Topo &T, const Field &Fd, const Cam &C, const I
   const long long per = kSubtreeThreads / kChunk;  // chunks per CTA
   const long long nblk = ((s1 - 1) / kChunk - s0 / kChunk + per) / per;
   if (nblk > 0x7fffffffll) return cudaErrorInvalidValue;
-  subtree_kernel<<<(unsigned)nblk, kSubtreeThreads, 0, stream>>>(T, Fd, C, I, S, nb, ne, s0, s1);
+  if (I.surface)  // isosurface segments (Sec. 2.8): a separate instantiation
+    subtree_kernel<true><<<(unsigned)nblk, kSubtreeThreads, 0, stream>>>(T, Fd, C, I, S, nb, ne,
+                                                                         s0, s1);
+  else
+    subtree_kernel<false><<<(unsigned)nblk, kSubtreeThreads, 0, stream>>>(T, Fd, C, I, S, nb, ne,
+                                                                          s0, s1);
   return cudaGetLastError();
 }
 
@@ -690,12 +696,19 @@ cudaError_t launch_coarsen(const Topo &T, const Field &Fd, const Cam &C, const I
   const long long nblk = rgba ? (s1 - s0 + kCoarsenThreads - 1) / kCoarsenThreads
                               : (s1 - 1) / kCoarsenThreads - s0 / kCoarsenThreads + 1;
   if (nblk > 0x7fffffffll) return cudaErrorInvalidValue;
-  if (rgba)
-    coarsen_kernel<true><<<(unsigned)nblk, kCoarsenThreads, 0, stream>>>(T, Fd, C, I, S, nb, ne,
-                                                                          s0, s1, rgba);
+  const unsigned g = (unsigned)nblk;
+  if (rgba && I.surface)
+    coarsen_kernel<true, true><<<g, kCoarsenThreads, 0, stream>>>(T, Fd, C, I, S, nb, ne, s0, s1,
+                                                                   rgba);
+  else if (rgba)
+    coarsen_kernel<true, false><<<g, kCoarsenThreads, 0, stream>>>(T, Fd, C, I, S, nb, ne, s0, s1,
+                                                                    rgba);
+  else if (I.surface)
+    coarsen_kernel<false, true><<<g, kCoarsenThreads, 0, stream>>>(T, Fd, C, I, S, nb, ne, s0, s1,
+                                                                    nullptr);
   else
-    coarsen_kernel<false><<<(unsigned)nblk, kCoarsenThreads, 0, stream>>>(T, Fd, C, I, S, nb, ne,
-                                                                           s0, s1, nullptr);
+    coarsen_kernel<false, false><<<g, kCoarsenThreads, 0, stream>>>(T, Fd, C, I, S, nb, ne, s0,
+                                                                     s1, nullptr);
   return cudaGetLastError();
 }
 

@@ -52,17 +52,21 @@ class Renderer:
                              _stream_ptr(None))
 
     def set_integrator(self, integ: dict, bg=(0.0, 0.0, 0.0)):
+        """integ["surface"] (optional): {"s_iso", "a_s", "i_s"}, the isosurface
+        rendered as a surface (Sec. 2.8)."""
+        surf = integ.get("surface")
         if integ["method"] == "rk4":
-            capi.set_integrator(self.h, capi.RK4, nsteps=integ.get("nsteps", 4), bg=bg)
+            capi.set_integrator(self.h, capi.RK4, nsteps=integ.get("nsteps", 4), bg=bg,
+                                surface=surf)
         elif integ["method"] == "dopri5":
             capi.set_integrator(self.h, capi.DOPRI5, tol=integ.get("tol", 1e-6),
                                 c_rk=integ.get("c_rk", 0.5), max_depth=integ.get("max_depth", 16),
-                                bg=bg)
+                                bg=bg, surface=surf)
         elif integ["method"] in ("gauss2", "simpson", "equilibrium"):
             method = {"gauss2": capi.GAUSS2, "simpson": capi.SIMPSON,
                       "equilibrium": capi.EQUILIBRIUM}[integ["method"]]
             capi.set_integrator(self.h, method, c_rk=integ.get("c_rk", 0.5),
-                                max_depth=integ.get("max_depth", 16), bg=bg)
+                                max_depth=integ.get("max_depth", 16), bg=bg, surface=surf)
         else:
             raise ValueError(integ["method"])
 
