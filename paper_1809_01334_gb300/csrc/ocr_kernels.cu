@@ -205,6 +205,8 @@ __device__ __forceinline__ unsigned spread3_9(unsigned v) {  // 3 bits -> positi
 //  D. every lane folds its own ray's results nearest-first with Eq. 2.14.
 constexpr int kSubtreeThreads = kChunk;  // one chunk per CTA
 constexpr int kCand = kSubtreeThreads;  // candidate table of phase A
+constexpr int kPairWin = 1024;          // (candidate, pixel) pairs resolved per window
+static_assert(kCand <= 256, "candidate indices are stored in one byte");
 constexpr int kWarpBatch = 32; // hits per warp batch of phase C
 
 template <bool SURF>
@@ -224,6 +226,7 @@ __global__ void __launch_bounds__(kSubtreeThreads, 1024 / kSubtreeThreads)
   __shared__ int s_cpre[kCand + 1];                      // candidate: pair count, then prefix
   __shared__ unsigned s_crel[kCand];                     // candidate: anchor in the node, level
   __shared__ int s_cl[kCand];                            // candidate: (node index << 22) | leaf - base
+  __shared__ unsigned char s_pc[kPairWin];               // candidate of each pair in the window
   __shared__ int s_cnt[NT];                              // hits of each ray
   __shared__ unsigned s_list[kMaxSubtreeHits][NT];       // (mirrored key << 22) | leaf - base
   __shared__ float4 s_res[NW][kWarpBatch];
@@ -316,12 +319,15 @@ __global__ void __launch_bounds__(kSubtreeThreads, 1024 / kSubtreeThreads)
     if (tid < nc) s_cpre[tid] = base + x - n0;
     if (tid == 0) s_cpre[nc] = tot;
     __syncthreads();
-    for (int pq = tid; pq < tot; pq += NT) {
-      int lo = 0, hi = nc;  // candidate: last k with s_cpre[k] <= pq
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (s_cpre[mid] <= pq) lo = mid; else hi = mid;
-      }
+    // pairs in windows of kPairWin: each candidate marks its pairs in the
+    // window with its index, then every pair finds its candidate in one load
+    const int my_pre = tid < nc ? s_cpre[tid] : 0, my_end = my_pre + n0;
+    for (int w0 = 0; w0 < tot; w0 += kPairWin) {
+      const int w1 = min(tot, w0 + kPairWin);
+      for (int p = max(my_pre, w0); p < min(my_end, w1); ++p) s_pc[p - w0] = (unsigned char)tid;
+      __syncthreads();
+    for (int pq = w0 + tid; pq < w1; pq += NT) {
+      const int lo = s_pc[pq - w0];
       const int4 b = s_cbox[lo];
       const int loc = pq - s_cpre[lo];
       // row = floor(loc / width) from the rounded reciprocal: exact, as the
@@ -352,7 +358,8 @@ __global__ void __launch_bounds__(kSubtreeThreads, 1024 / kSubtreeThreads)
       const int k = atomicAdd(&s_cnt[t], 1);
       if (k < kMaxSubtreeHits) s_list[k][t] = ((key ^ flip) << 22) | (unsigned)(tl & 0x3fffff);
     }
-    __syncthreads();
+      __syncthreads();
+    }
     if (tid == 0) s_ncand = 0;
   };
   for (int q = 0; q < nn; ++q) {
