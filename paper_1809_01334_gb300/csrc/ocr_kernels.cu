@@ -217,10 +217,10 @@ __global__ void __launch_bounds__(kSubtreeThreads, 1024 / kSubtreeThreads)
   static_assert(kCand == NT, "one table entry per thread in the prefix sum");
   __shared__ float4 s_tfv[8], s_tfs[8];
   __shared__ float s_ray[6][NT];                         // ray origin and direction, by component
-  __shared__ int s_node[NT];                             // node of each slot, -1 inactive
-  __shared__ int s_tnode[NT];                            // distinct nodes of the chunk
-  __shared__ int s_liveq[NT];                            // live ray: index of its node, else -1
+  __shared__ signed char s_liveq[NT];                    // live ray: index of its node, else -1
   __shared__ int4 s_qinfo[NT];                           // node: {rect x0, rect y0, width, off - cs}
+  __shared__ int2 s_qlr[NT];                             // node: its leaves [first, end)
+  __shared__ int2 s_qrows[NT];                           // node: its rows in the chunk
   __shared__ unsigned long long s_qgeo[NT];              // node: anchor x | y << 21 | z << 42
   __shared__ int4 s_cbox[kCand];                         // candidate: rectangle within the rows
   __shared__ int s_cpre[kCand + 1];                      // candidate: pair count, then prefix
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kSubtreeThreads, 1024 / kSubtreeThreads)
   __shared__ int s_cnt[NT];                              // hits of each ray
   __shared__ unsigned s_list[kMaxSubtreeHits][NT];       // (mirrored key << 22) | leaf - base
   __shared__ float4 s_res[NW][kWarpBatch];
-  __shared__ int s_wcnt[NW], s_nn, s_leaf_base, s_ncand;
+  __shared__ int s_wcnt[NW], s_nn, s_leaf_base, s_ncand, s_ltot;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid < 8) {
     const float4 v = Fd.tf[tid];
@@ -261,6 +261,7 @@ __global__ void __launch_bounds__(kSubtreeThreads, 1024 / kSubtreeThreads)
   s_ray[3][tid] = dir.x;
   s_ray[4][tid] = dir.y;
   s_ray[5][tid] = dir.z;
+  int *s_node = s_cnt;  // node of each slot (-1 inactive) until phase A
   s_node[tid] = active ? node : -1;
   __syncthreads();
 
@@ -275,14 +276,20 @@ __global__ void __launch_bounds__(kSubtreeThreads, 1024 / kSubtreeThreads)
     for (int w = 0; w < wid; ++w) base += s_wcnt[w];
     const int myq = base + __popc(bal & (0xffffffffu >> (31 - lane))) - 1;
     if (head) {
-      s_tnode[myq] = node;
       const int4 rn = __ldg(S.rect + T.N + node);
-      s_qinfo[myq] = make_int4(rn.x, rn.z, rn.y - rn.x + 1, (int)(__ldg(S.off + node) - cs));
+      const long long off = __ldg(S.off + node), off1 = __ldg(S.off + node + 1);
       const int4 gq = __ldg(T.geo + T.N + node);
+      const int2 lr = __ldg(T.leaves + node);
+      const int w = rn.y - rn.x + 1, ow = (int)(off - cs);
+      s_qinfo[myq] = make_int4(rn.x, rn.z, w, ow);
       s_qgeo[myq] = (unsigned long long)gq.x | (unsigned long long)gq.y << 21 |
                     (unsigned long long)gq.z << 42;
+      s_qlr[myq] = lr;
+      // the node's slots [la, lb) in the chunk, and their rows
+      const int la = max(0, -ow), lb = (int)(min(min(cs + NT, s1), off1) - off);
+      s_qrows[myq] = make_int2(rn.z + la / w, rn.z + (lb - 1) / w);
     }
-    s_liveq[tid] = live ? myq : -1;
+    s_liveq[tid] = (signed char)(live ? myq : -1);
     if (tid == NT - 1) {
       int tot = 0;
       for (int w = 0; w < NW; ++w) tot += s_wcnt[w];
@@ -290,7 +297,12 @@ __global__ void __launch_bounds__(kSubtreeThreads, 1024 / kSubtreeThreads)
       s_ncand = 0;
     }
     __syncthreads();
-    if (tid == 0) s_leaf_base = s_nn ? __ldg(T.leaves + s_tnode[0]).x : 0;
+    if (tid == 0) {
+      int lt = 0;
+      for (int q = 0; q < s_nn; ++q) lt += s_qlr[q].y - s_qlr[q].x;
+      s_ltot = lt;
+      s_leaf_base = s_nn ? s_qlr[0].x : 0;
+    }
   }
   __syncthreads();
 
@@ -362,43 +374,70 @@ __global__ void __launch_bounds__(kSubtreeThreads, 1024 / kSubtreeThreads)
     }
     if (tid == 0) s_ncand = 0;
   };
-  for (int q = 0; q < nn; ++q) {
-    const int nd = s_tnode[q];
-    const int2 lr = __ldg(T.leaves + nd);
-    const int4 qi = s_qinfo[q];
+  // the candidate leaf l of node q: kept if its rectangle meets the node's
+  // columns and its rows in the chunk
+  auto candidate = [&](int q, int l, bool in_range, int &cnt) -> int4 {
+    int4 box = empty_rect();
+    cnt = 0;
+    if (in_range) {
+      const int4 qi = s_qinfo[q];
+      const int2 rows = s_qrows[q];
+      const int4 r = __ldg(S.rect + l);
+      box = make_int4(max(r.x, qi.x), min(r.y, qi.x + qi.z - 1), max(r.z, rows.x), min(r.w, rows.y));
+      if (box.x <= box.y && box.z <= box.w) cnt = (box.y - box.x + 1) * (box.w - box.z + 1);
+    }
+    return box;
+  };
+  auto store = [&](int at, int q, int l, int4 box, int cnt) {
     const unsigned long long gq = s_qgeo[q];
-    // the node's rows in the chunk: its slots [la, lb) within the node
-    const int la = max(0, -qi.w), lb = min(NT, (int)min(s1 - cs, (long long)__ldg(S.off + nd + 1) - cs)) - qi.w;
-    const int jr0 = qi.y + la / qi.z, jr1 = qi.y + (lb - 1) / qi.z;
-    const int x0 = qi.x, x1 = qi.x + qi.z - 1;
-    for (int l0 = lr.x; l0 < lr.y; l0 += NT) {
-      __syncthreads();
-      if (s_ncand + NT > kCand) flush();
-      const int l = l0 + tid;
-      int4 box = empty_rect();
-      int cnt = 0;
-      if (l < lr.y) {
-        const int4 r = __ldg(S.rect + l);
-        box = make_int4(max(r.x, x0), min(r.y, x1), max(r.z, jr0), min(r.w, jr1));
-        if (box.x <= box.y && box.z <= box.w) cnt = (box.y - box.x + 1) * (box.w - box.z + 1);
+    const int4 g = __ldg(T.geo + l);
+    s_cbox[at] = box;
+    s_cpre[at] = cnt;
+    s_crel[at] = (unsigned)(g.x - (int)(gq & 0x1fffffu)) |
+                 (unsigned)(g.y - (int)((gq >> 21) & 0x1fffffu)) << 8 |
+                 (unsigned)(g.z - (int)(gq >> 42)) << 16 | (unsigned)g.w << 24;
+    s_cl[at] = (q << 22) | (l - leaf_base);
+  };
+  if (s_ltot <= kCand) {
+    // all the chunk's leaves fit the table: the warps take 32-leaf blocks in
+    // turn and append their candidates without CTA barriers
+    int q = 0, b = wid;  // this warp's block: the b-th 32-leaf block of node q
+    while (q < nn) {
+      const int2 lr = s_qlr[q];
+      const int nb32 = (lr.y - lr.x + 31) >> 5;
+      if (b >= nb32) {
+        b -= nb32;
+        ++q;
+        continue;
       }
+      const int l = lr.x + 32 * b + lane;
+      int cnt;
+      const int4 box = candidate(q, l, l < lr.y, cnt);
       const unsigned bal = __ballot_sync(0xffffffffu, cnt > 0);
-      if (lane == 0) s_wcnt[wid] = __popc(bal);
-      __syncthreads();
-      int base = s_ncand;
-      for (int w = 0; w < wid; ++w) base += s_wcnt[w];
-      if (cnt > 0) {
-        const int at = base + __popc(bal & ((1u << lane) - 1u));
-        const int4 g = __ldg(T.geo + l);
-        s_cbox[at] = box;
-        s_cpre[at] = cnt;
-        s_crel[at] = (unsigned)(g.x - (int)(gq & 0x1fffffu)) |
-                     (unsigned)(g.y - (int)((gq >> 21) & 0x1fffffu)) << 8 |
-                     (unsigned)(g.z - (int)(gq >> 42)) << 16 | (unsigned)g.w << 24;
-        s_cl[at] = (q << 22) | (l - leaf_base);
+      int base = 0;
+      if (lane == 0 && bal) base = atomicAdd(&s_ncand, __popc(bal));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (cnt > 0) store(base + __popc(bal & ((1u << lane) - 1u)), q, l, box, cnt);
+      b += NW;
+    }
+  } else {
+    for (int q = 0; q < nn; ++q) {
+      const int2 lr = s_qlr[q];
+      for (int l0 = lr.x; l0 < lr.y; l0 += NT) {
+        __syncthreads();
+        if (s_ncand + NT > kCand) flush();
+        const int l = l0 + tid;
+        int cnt;
+        const int4 box = candidate(q, l, l < lr.y, cnt);
+        const unsigned bal = __ballot_sync(0xffffffffu, cnt > 0);
+        if (lane == 0) s_wcnt[wid] = __popc(bal);
+        __syncthreads();
+        int base = s_ncand;
+        for (int w = 0; w < wid; ++w) base += s_wcnt[w];
+        if (cnt > 0) store(base + __popc(bal & ((1u << lane) - 1u)), q, l, box, cnt);
+        __syncthreads();
+        if (tid == NT - 1) s_ncand = base + __popc(bal);
       }
-      __syncthreads();
-      if (tid == NT - 1) s_ncand = base + __popc(bal);
     }
   }
   flush();
