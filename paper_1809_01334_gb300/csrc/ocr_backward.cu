@@ -573,15 +573,16 @@ __device__ void warp_sort(unsigned long long *key, int *lf, int P, int lane) {
 
 constexpr int kBwdWarps = 4;
 
-__global__ void __launch_bounds__(kBwdWarps * 32)
+__global__ void __launch_bounds__(kBwdWarps * 32, 4)
     ray_backward_kernel(Topo T, Field Fd, Cam c, Integ I, const float4 *dL,
                         const long long *ray_off, const unsigned long long *keys,
-                        const int *hleaf, float *g_nodal, float *g_tf, unsigned long long *err) {
+                        const int *hleaf, float *g_nodal, float *g_tf, unsigned long long *err,
+                        int cap) {
   extern __shared__ unsigned char s_raw[];
   // per warp: keys (later T and A_seg), leaves, segment values (later far aggregates)
   unsigned long long *s_key = reinterpret_cast<unsigned long long *>(s_raw);
-  int *s_leaf = reinterpret_cast<int *>(s_key + kBwdWarps * kMaxRayHits);
-  float4 *s_val = reinterpret_cast<float4 *>(s_leaf + kBwdWarps * kMaxRayHits);
+  float4 *s_val = reinterpret_cast<float4 *>(s_key + kBwdWarps * cap);
+  int *s_leaf = reinterpret_cast<int *>(s_val + kBwdWarps * cap);
   __shared__ float4 s_tfv[8], s_tfs[8];
   __shared__ float s_g[32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -593,11 +594,11 @@ __global__ void __launch_bounds__(kBwdWarps * 32)
   }
   if (tid < 32) s_g[tid] = 0.f;
   __syncthreads();
-  unsigned long long *key = s_key + wid * kMaxRayHits;
-  int *lf = s_leaf + wid * kMaxRayHits;
-  float4 *val = s_val + wid * kMaxRayHits;
+  unsigned long long *key = s_key + wid * cap;
+  int *lf = s_leaf + wid * cap;
+  float4 *val = s_val + wid * cap;
   float *Tk = reinterpret_cast<float *>(key);           // reuses the key array after sorting
-  float *Ak = reinterpret_cast<float *>(key) + kMaxRayHits;
+  float *Ak = reinterpret_cast<float *>(key) + cap;
   TF tf{s_tfv, s_tfs, Fd.s_min, Fd.inv_ds7};
   TfGrad tg;
   tg.s_g = s_g;
@@ -608,7 +609,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32)
     const long long h0 = ray_off[pix];
     const int n = (int)(ray_off[pix + 1] - h0);
     if (n == 0) continue;
-    if (n > kMaxRayHits) {
+    if (n > cap) {
       if (lane == 0) atomicAdd(err, 1ull);
       continue;
     }
@@ -786,21 +787,43 @@ cudaError_t bwd_pair_hits(bool fill, const Topo &T, const Cam &C, const int4 *re
   return cudaGetLastError();
 }
 
+__global__ void __launch_bounds__(256) hits_max_kernel(const int *counts, long long n,
+                                                       unsigned long long *out) {
+  int m = 0;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x)
+    m = max(m, counts[k]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, (unsigned long long)m);
+}
+
+cudaError_t bwd_max_hits(const int *counts, long long n, unsigned long long *out,
+                         cudaStream_t st) {
+  const long long g = (n + 255) / 256;
+  hits_max_kernel<<<(unsigned)(g > 4096 ? 4096 : (g > 0 ? g : 1)), 256, 0, st>>>(counts, n, out);
+  return cudaGetLastError();
+}
+
+size_t bwd_rays_smem(int cap) {
+  return (size_t)kBwdWarps * cap * (sizeof(unsigned long long) + sizeof(int) + sizeof(float4));
+}
+
 cudaError_t bwd_rays(const Topo &T, const Field &Fd, const Cam &C, const Integ &I,
                      const float4 *dL, const long long *ray_off, const unsigned long long *keys,
                      const int *hleaf, float *g_nodal, float *g_tf, unsigned long long *err,
-                     int nsm, cudaStream_t st) {
-  const size_t smem = (size_t)kBwdWarps * kMaxRayHits * (sizeof(unsigned long long) + sizeof(int) +
-                                                          sizeof(float4));
+                     int nsm, int cap, cudaStream_t st) {
+  if (cap < 32 || cap > kMaxRayHits || (cap & (cap - 1))) return cudaErrorInvalidValue;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(ray_backward_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bwd_rays_smem(kMaxRayHits));
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  ray_backward_kernel<<<nsm * 4, kBwdWarps * 32, smem, st>>>(T, Fd, C, I, dL, ray_off, keys, hleaf,
-                                                            g_nodal, g_tf, err);
+  ray_backward_kernel<<<nsm * 4, kBwdWarps * 32, bwd_rays_smem(cap), st>>>(
+      T, Fd, C, I, dL, ray_off, keys, hleaf, g_nodal, g_tf, err, cap);
   return cudaGetLastError();
 }
 

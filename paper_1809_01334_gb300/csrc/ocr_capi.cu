@@ -977,9 +977,14 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
   OCR_CUDA(bwd_pair_hits(false, T, cam, P0.d_rect, F->d_leaf_off, F->d_pchunk, npairs, dL,
                          F->d_rcount, nullptr, nullptr, F->d_mkey, F->fx, nullptr, nullptr, st));
   OCR_CUDA(bwd_count_scan(F->d_rcount, npix, F->d_bsums, F->bsums_cap, F->d_ray_off, st));
+  OCR_CUDA(bwd_max_hits(F->d_rcount, npix, F->d_stats + kStatMaxHits, st));
   OCR_CUDA(cudaMemcpyAsync(h, F->d_ray_off + npix, sizeof(long long), cudaMemcpyDeviceToHost, st));
+  OCR_CUDA(cudaMemcpyAsync(h + 1, F->d_stats + kStatMaxHits, sizeof(long long),
+                           cudaMemcpyDeviceToHost, st));
   OCR_CUDA(cudaStreamSynchronize(st));
   const long long nh = h[0];
+  int cap = 32;  // per-warp lists sized for the longest ray (longer than 512: skipped)
+  while (cap < h[1] && cap < kMaxRayHits) cap <<= 1;
   {
     long long c0 = F->hit_cap;
     if ((rc = grow(F, &F->d_hkey, F->hit_cap, nh))) return rc;
@@ -997,7 +1002,7 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
   // one warp per ray: order, recompute, prefix/suffix, adjoint
   OCR_CUDA(cudaMemsetAsync(F->d_err, 0, sizeof(unsigned long long), st));
   OCR_CUDA(bwd_rays(T, Fd, cam, F->integ, dL, F->d_ray_off, F->d_hkey, F->d_hleaf,
-                    d_grad_nodal, d_grad_tf, F->d_err, F->nsm, st));
+                    d_grad_nodal, d_grad_tf, F->d_err, F->nsm, cap, st));
   OCR_CUDA(cudaMemcpyAsync(h, F->d_err, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
   OCR_CUDA(cudaStreamSynchronize(st));
   if (h[0]) return OCR_ERR_DEVICE;

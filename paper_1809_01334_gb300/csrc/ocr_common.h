@@ -125,10 +125,15 @@ cudaError_t bwd_pair_hits(bool fill, const Topo &T, const Cam &C, const int4 *re
                           const float4 *dL, int *counts, const long long *ray_off, int *cursor,
                           const unsigned long long *mkey, unsigned long long fx,
                           unsigned long long *keys, int *hleaf, cudaStream_t st);
+// the most hits on one ray (atomicMax into *out, which the caller zeroes)
+cudaError_t bwd_max_hits(const int *counts, long long n, unsigned long long *out,
+                         cudaStream_t st);
+// one warp per ray; cap: a power of two, 32..kMaxRayHits, at least the most
+// hits on one ray (longer rays are skipped and counted in err)
 cudaError_t bwd_rays(const Topo &T, const Field &Fd, const Cam &C, const Integ &I,
                      const float4 *dL, const long long *ray_off, const unsigned long long *keys,
                      const int *hleaf, float *g_nodal, float *g_tf, unsigned long long *err,
-                     int nsm, cudaStream_t st);
+                     int nsm, int cap, cudaStream_t st);
 
 // Cubed-sphere shell (ocr_shell.cu)
 cudaError_t shell_cull(const int4 *geo, int N, const Shell &S, const Cam &C, int4 *rect,
