@@ -294,12 +294,12 @@ __device__ __forceinline__ float4 scale4(float a, float4 x) {
   return make_float4(a * x.x, a * x.y, a * x.z, a * x.w);
 }
 
-// adjoint of one RK4 step from (1, 0) with nodes at t0, t0 + dt/2, t0 + dt
+// adjoint of one RK4 step from (1, 0) with nodes at t0, t0 + dt/2, t0 + dt,
+// where the medium is k0, kh, k1 (as the forward step evaluated it)
 template <class SA>
 __device__ void rk4_step_bwd(SA &S, const TF &tf, float t0, float dt, float H, float4 ybar,
-                             TfGrad &tg) {
+                             TfGrad &tg, float4 k0, float4 kh, float4 k1) {
   const float4 one = seg_identity();
-  const float4 k0 = S.kq(tf, t0), kh = S.kq(tf, t0 + 0.5f * dt), k1 = S.kq(tf, t0 + dt);
   const float4 Y1 = one, K1 = rhs(k0, Y1);
   const float4 Y2 = axpy(0.5f * H, K1, one), K2 = rhs(kh, Y2);
   const float4 Y3 = axpy(0.5f * H, K2, one), K3 = rhs(kh, Y3);
@@ -319,14 +319,14 @@ __device__ void rk4_step_bwd(SA &S, const TF &tf, float t0, float dt, float H, f
 
 // adjoint of one Dormand-Prince step from (1, 0) (stages 1..6; the seventh
 // stage only feeds the error estimate)
+// (kq: the medium at the six nodes, as the forward step evaluated it)
 template <class SA>
 __device__ void dopri_step_bwd(SA &S, const TF &tf, float t0, float dtau, float H,
-                               float4 ybar, TfGrad &tg) {
+                               float4 ybar, TfGrad &tg, const float4 *kq) {
   const float4 one = seg_identity();
   const float tt[6] = {t0, fmaf(dp::c2, dtau, t0), fmaf(dp::c3, dtau, t0),
                        fmaf(dp::c4, dtau, t0), fmaf(dp::c5, dtau, t0), t0 + dtau};
-  float4 kq[6], Y[6], K[6];
-  for (int i = 0; i < 6; ++i) kq[i] = S.kq(tf, tt[i]);
+  float4 Y[6], K[6];
   Y[0] = one;
   K[0] = rhs(kq[0], Y[0]);
   Y[1] = axpy(H * dp::a21, K[0], one);
@@ -388,11 +388,12 @@ __device__ void segment_steps_bwd(SA &S, const TF &tf, float dx, const Integ &I,
     const float H = dx / (float)n, dt = 1.f / (float)n;
     for (int s = 0; s < n; ++s) {
       const float t0 = (float)s * dt, dts = (s + 1 == n) ? 1.f - t0 : dt;
-      const float4 Sm = rk4_step(H, S.kq(tf, t0), S.kq(tf, t0 + 0.5f * dts), S.kq(tf, t0 + dts));
+      const float4 k0 = S.kq(tf, t0), kh = S.kq(tf, t0 + 0.5f * dts), k1 = S.kq(tf, t0 + dts);
+      const float4 Sm = rk4_step(H, k0, kh, k1);
       const float4 accn = seg_combine(Sm, acc);
       const float Tm = Tn * (Aseg / accn.x);
       const float4 Gm = seg_combine(acc, G);
-      rk4_step_bwd(S, tf, t0, dts, H, step_adjoint(Tm, Gm, Ib, ab, I.bg), tg);
+      rk4_step_bwd(S, tf, t0, dts, H, step_adjoint(Tm, Gm, Ib, ab, I.bg), tg, k0, kh, k1);
       acc = accn;
     }
     return;
@@ -448,7 +449,8 @@ __device__ void segment_steps_bwd(SA &S, const TF &tf, float dx, const Integ &I,
     const float4 accn = seg_combine(Y5, acc);
     const float Tm = Tn * (Aseg / accn.x);
     const float4 Gm = seg_combine(acc, G);
-    dopri_step_bwd(S, tf, t0, dtau, H, step_adjoint(Tm, Gm, Ib, ab, I.bg), tg);
+    const float4 kq[6] = {kq0, kq2, kq3, kq4, kq5, kq6};
+    dopri_step_bwd(S, tf, t0, dtau, H, step_adjoint(Tm, Gm, Ib, ab, I.bg), tg, kq);
     acc = accn;
     kq0 = kq6;
     ++idx;
