@@ -60,6 +60,10 @@ def parse_args():
                    help="cameras of the batched (CUDA graph) measurement; 0 skips it")
     p.add_argument("--no-shell", action="store_true",
                    help="skip the cubed-sphere shell measurements (render and adjoint)")
+    p.add_argument("--only-shell", action="store_true",
+                   help="run the shell measurements alone (profiling captures)")
+    p.add_argument("--shell-image", default="2048x2048",
+                   help="image size WxH of the shell render (smaller sizes only for profiling)")
     p.add_argument("--image", default="1920x1080",
                    help="image size WxH (smaller sizes only for profiling captures)")
     return p.parse_args()
@@ -234,7 +238,8 @@ def run_shell(args, dev, flush):
     from paper_1809_01334_gb300 import Renderer
     from paper_1809_01334_gb300 import inputs as I
     stream = torch.cuda.current_stream(dev)
-    forest, tf, cam, integ = I.preset_c3()
+    sw, sh = (int(x) for x in args.shell_image.split("x"))
+    forest, tf, cam, integ = I.preset_c3(w=sw, h=sh)
     r = Renderer(forest, tf, integ, device=dev)
     r.set_camera(cam)
     out = torch.empty((cam.h, cam.w, 4), dtype=torch.float32, device=dev)
@@ -246,7 +251,7 @@ def run_shell(args, dev, flush):
     ms = _timed(fwd, stream, flush, 2, 5)
     rays_ms = sum(p["ms_subtree"] for p in phases[2:]) / len(phases[2:])
     c3 = {"workload": "cubed-sphere shell, 6 trees, levels 4-7 (%d leaves, degree-2 FP32 "
-                      "data), perspective 45deg 2048x2048, DOPRI5 tol 1e-5" % forest.nleaves,
+                      "data), perspective 45deg %dx%d, DOPRI5 tol 1e-5" % (forest.nleaves, sw, sh),
           "ms_per_render": ms, "segments": st["segments"], "rk_steps": st["rk_steps"],
           "pair_tests": st["leaf_tests"], "segments_per_s": st["segments"] / (ms * 1e-3),
           "mpixel_per_s": cam.w * cam.h / (ms * 1e-3) / 1e6, "ms_rays_kernel": rays_ms,
@@ -324,6 +329,13 @@ def main():
     from paper_1809_01334_gb300 import inputs as I
 
     torch.cuda.set_device(local)
+    if args.only_shell:
+        dev = torch.device("cuda", local)
+        flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+        c3, c5 = run_shell(args, dev, flush)
+        if rank == 0:
+            print(json.dumps({"shell_render": c3, "shell_backward": c5}), flush=True)
+        return
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
