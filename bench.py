@@ -136,6 +136,23 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def subtree_traffic():
+    """DRAM bytes per launch of the subtree pass from the committed ncu capture
+    (profiles/subtree_kernel_traffic.json), or None when the kernel's sources
+    have changed since the counters were taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "subtree_kernel_traffic.json")) as fh:
+            rec = json.load(fh)
+        h = hashlib.sha256()
+        for f in rec["sources"]:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+        return rec["dram_bytes_per_launch"] if h.hexdigest() == rec["sources_sha256"] else None
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def cpu_baseline(forest, tf, cam, integ, stride: int):
     """The FP64 oracle, as it stands, on this host's cores: every stride-th row."""
     import numpy as np
@@ -458,7 +475,8 @@ def main():
                     "d2h_bytes_per_step": int(out.numel() * 4)},
             "roofline": {"bound": "alu", "kernel": "subtree_kernel",
                          "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                         "unit": "TFP32op/s", "frac": achieved / peak_ops, "traffic": None,
+                         "unit": "TFP32op/s", "frac": achieved / peak_ops,
+                         "traffic": subtree_traffic(), "traffic_unit": "bytes per launch (ncu)",
                          "fp32_ops_per_launch": ops, "ms_per_launch": sm,
                          "peak_source": f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                         f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({src})",
