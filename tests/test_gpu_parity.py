@@ -139,3 +139,51 @@ def test_c2_full_size_sampled_rows():
     err, st, ref = _compare(f, tf, cam, integ, rows=rows)
     assert st["visible_leaves"] == f.nleaves
     assert st["segments"] > 20_000_000
+
+
+def _spike_forest(max_level, p=(0.3137, 0.5821, 0.4419), seed=5):
+    """A forest refined only around the point p, one cell per level, down to
+    max_level: 7 leaves per level and 8 at the finest (Morton order)."""
+    L = max_level
+    levels, anchors = [], []
+    cell = np.zeros(3, np.int64)  # anchor (units of 2^-L) of the refined cell at each level
+    for l in range(L):
+        half = 1 << (L - l - 1)
+        pc = np.floor(np.asarray(p) * (1 << (l + 1))).astype(np.int64) & 1  # child holding p
+        for o in range(8):
+            bits = np.array([o & 1, (o >> 1) & 1, (o >> 2) & 1])
+            a = cell + bits * half
+            if l + 1 < L and (bits == pc).all():
+                continue
+            levels.append(l + 1)
+            anchors.append(a)
+        cell = cell + pc * half
+    lv = np.array(levels, np.uint8)
+    an = np.array(anchors, np.int32)
+    lv, an, tr = I._sort_forest(lv, an, np.zeros(len(lv), np.int32))
+    fld = I.gaussian_field(4, seed)
+    nodal = I._sample_corners(fld, lv, an, L).astype(np.float32)
+    f = I.Forest("cube", L, lv, an, tr, nodal, {"kind": "spike"})
+    tf = I.transfer_function(f.nodal, 1334)
+    return f, tf
+
+
+@pytest.mark.parametrize("max_level", [12, 16])
+def test_deep_forest_zoomed_camera(max_level):
+    """Maximum depths: a forest refined around one point to level 12 and 16
+    (anchors up to 2^16), seen by a camera zoomed onto that point so that the
+    deep cells cover pixels; 13 coarsening passes above the tile level."""
+    f, tf = _spike_forest(max_level)
+    assert f.nleaves == 7 * max_level + 1
+    p = (0.3137, 0.5821, 0.4419)
+    cam = I.perspective_camera(13, 40, 32, dist=(2e-3, 2.5e-3), fov_deg=30.0, near=1e-4,
+                               target=p)
+    err, st, ref = _compare(f, tf, cam, {"method": "rk4", "nsteps": 4}, max_unc_frac=0.05)
+    assert (ref["counts"] > 0).all() and st["visible_leaves"] >= max_level
+
+
+def test_wide_image_index_arithmetic():
+    """A 4096 x 7 image: pixel and slot indices across a wide row."""
+    f, tf, _ = I.preset_small()
+    cam = I.perspective_camera(17, 4096, 7)
+    _compare(f, tf, cam, {"method": "rk4", "nsteps": 2}, max_unc_frac=0.05)

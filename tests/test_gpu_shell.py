@@ -124,3 +124,21 @@ def test_c3_full_size_sampled_rows():
     rows = np.linspace(200, 1850, 8).astype(int)
     err, st, ref = _compare(f, tf, cam, integ, rows=rows, max_unc_frac=0.2)
     assert st["segments"] > 1e8
+
+
+def test_shell_empty_view_is_background():
+    """A camera looking away from the shell: no leaf survives pruning, every
+    pixel is the background with alpha 0."""
+    from paper_1809_01334_gb300 import Renderer
+    f, tf, _ = I.preset_shell_small()
+    cam = I.Camera(o=(0.0, 0.0, 3.0), v=(0.0, 0.0, 0.1), t=(1.0, 0.0, 0.0), u=(0.0, 1.0, 0.0),
+                   ell=float(np.float32(1e-3)), near=float(np.float32(0.1)), far=100.0, w=17, h=9)
+    bg = (0.25, 0.5, 0.75)
+    r = Renderer(f, tf, DOPRI_C3, bg=bg)
+    r.set_camera(cam)
+    img, st = r.render(with_index=True)
+    torch.cuda.synchronize()
+    assert st["visible_leaves"] == 0 and st["segments"] == 0
+    exp = torch.tensor([bg[0], bg[1], bg[2], 0.0], device=img.device).expand_as(img)
+    assert torch.equal(img, exp)
+    r.close()
