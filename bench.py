@@ -128,6 +128,24 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest value of x over the ranks (the job's time is its slowest
+    rank's); world == 1 returns x."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput of independent replicas: every rank processes the
+    same number of units; the job takes as long as its slowest rank."""
+    return world * units_per_rank / (ms_max * 1e-3)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -393,10 +411,7 @@ def main():
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     ms = sum(step_ms) / len(step_ms)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, dev)
 
     # end to end through the public API from pinned host memory: nodal data in,
     # image out, every step
@@ -417,9 +432,7 @@ def main():
         if k >= args.warmup:
             e2e_ms.append(a.elapsed_time(b))
     e2e = sum(e2e_ms) / len(e2e_ms) if e2e_ms else float("nan")
-    te = torch.tensor([e2e], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_max = max_over_ranks(e2e, world, dev)
 
     # differentiation: dL/d(nodal, knots) of an L2 loss against a target rendered
     # from a seeded 5% perturbation of the nodal data (segments recomputed)
@@ -457,7 +470,7 @@ def main():
         peak_ops = nsm * FP32_LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6
         achieved = ops / (sm * 1e-3)
         line = {
-            "metric": METRIC, "value": world * segments / (ms_max * 1e-3), "unit": UNIT,
+            "metric": METRIC, "value": job_throughput(segments, world, ms_max), "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -470,7 +483,7 @@ def main():
                        "l2": "flushed (512 MB write) before every timed step",
                        "parallelism": f"replicas x{world}"},
             "gpu_launches": launches * args.steps,
-            "e2e": {"value": world * segments / (float(te.item()) * 1e-3), "unit": UNIT,
+            "e2e": {"value": job_throughput(segments, world, e2e_max), "unit": UNIT,
                     "h2d_bytes_per_step": int(forest.nodal.nbytes),
                     "d2h_bytes_per_step": int(out.numel() * 4)},
             "roofline": {"bound": "alu", "kernel": "subtree_kernel",
