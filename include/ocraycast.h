@@ -251,12 +251,18 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
  *               multi-camera render are spread.
  *   shell_warps shell forests: warps per CTA of the per-ray kernel (1..8;
  *               0 = as many as fit in 96 KB of shared memory).
+ *   merge       cube forests: the levels above the tile level are merged by
+ *               one pass per level over (node, ray) aggregates (0), or by one
+ *               pass in which each pixel's thread walks those levels top-down
+ *               in its front-to-back octant order (1).  Equal up to rounding
+ *               order (Eq. 2.14 is associative).
  *   ms          ocr_autotune: the measured device time of one ocr_render.
- * Defaults: tile_depth 3, streams 4, shell_warps 0. */
+ * Defaults: tile_depth 3, streams 4, shell_warps 0, merge 0. */
 typedef struct {
   int tile_depth;
   int streams;
   int shell_warps;
+  int merge;
   float ms;
 } ocr_tuning;
 
@@ -266,7 +272,7 @@ int ocr_set_tuning(ocr_forest *F, const ocr_tuning *t);
 int ocr_get_tuning(const ocr_forest *F, ocr_tuning *t);
 
 /* Autotuner: render the cameras, data and integrator last set under every
- * candidate tuning (cube: tile_depth 1..3 x streams {1, 2, 4, 8}; shell:
+ * candidate tuning (cube: tile_depth 1..3 x merge {0, 1} x streams {1, 2, 4, 8}; shell:
  * shell_warps {1, 2, 4, 8} x streams; streams only with several cameras),
  * one warm-up and `reps` timed renders each (CUDA events on an internal
  * stream, 1 <= reps <= 100), and keep the fastest, returned in *best.  The

@@ -54,7 +54,7 @@ class Stats(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("tile_depth", C.c_int), ("streams", C.c_int), ("shell_warps", C.c_int),
-                ("ms", C.c_float)]
+                ("merge", C.c_int), ("ms", C.c_float)]
 
 
 class OcrError(RuntimeError):
@@ -185,12 +185,12 @@ def render(h, d_rgba, stream=None, d_counts=None, d_visible=None, d_rects=None,
 
 def _tuning_dict(t: Tuning) -> dict:
     return {"tile_depth": t.tile_depth, "streams": t.streams, "shell_warps": t.shell_warps,
-            "ms": float(t.ms)}
+            "merge": t.merge, "ms": float(t.ms)}
 
 
-def set_tuning(h, tile_depth: int = 3, streams: int = 4, shell_warps: int = 0):
+def set_tuning(h, tile_depth: int = 3, streams: int = 4, shell_warps: int = 0, merge: int = 0):
     """ocr_set_tuning (a cube forest re-plans its cameras when tile_depth changes)."""
-    t = Tuning(int(tile_depth), int(streams), int(shell_warps), 0.0)
+    t = Tuning(int(tile_depth), int(streams), int(shell_warps), int(merge), 0.0)
     L = lib()
     L.ocr_set_tuning.argtypes = [C.c_void_p, C.POINTER(Tuning)]
     _check(L.ocr_set_tuning(h, C.byref(t)), "ocr_set_tuning")

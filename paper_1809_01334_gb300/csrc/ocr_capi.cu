@@ -76,6 +76,8 @@ struct ocr_forest {
   int tile_depth = kSubtreeDepth;     // cube: octree levels aggregated inside one CTA
   int nstreams = 4;                   // internal streams of multi-camera renders
   int shell_warps = 0;                // shell: warps per CTA of the per-ray kernel (0: most)
+  int merge = 0;                      // cube: levels above the tile level by per-level passes
+                                      // (0) or by one top-down pass per pixel (1)
   long long *h_group_slots = nullptr; // pinned [L + 1 + kStats]
   unsigned long long *d_stats = nullptr;  // [kStats]
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // start, layout, subtree, end
@@ -584,6 +586,16 @@ int ocr_build_forest(const ocr_forest_desc *desc, void *stream, ocr_forest **out
     return rc;
   }
   F->bsums_blocks = area_scan_blocks(M) + 1;
+  {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&F->nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+      free_all(F);
+      delete F;
+      return cuda_fail(e);
+    }
+  }
   if (cudaMallocHost((void **)&F->h_group_slots,
                      sizeof(long long) * (F->h_group_nodes.size() + kStats)) !=
       cudaSuccess) {
@@ -766,11 +778,12 @@ int enqueue_camera(ocr_forest *F, CamPlan &P, float4 *rgba, int *counts, unsigne
   launches += F->M > 0;
   if (timed) OCR_CUDA(cudaEventRecord(F->ev[1], st));
   // group g covers level L - 1 - g: the tile level runs the subtree pass, the
-  // levels above it the coarsening passes, deepest first
+  // levels above it the coarsening passes, deepest first (or the top-down pass)
   for (int g = 0; g + 1 < G; ++g) {
     const int level = F->L - 1 - g;
     const long long a = P.gslots[g], b = P.gslots[g + 1];
     if (b <= a) continue;
+    if (F->merge == 1 && level != F->lt) continue;
     if (level == F->lt) {
       if (timed) OCR_CUDA(cudaEventRecord(F->ev[2], st));
       OCR_CUDA(launch_subtree(T, Fd, P.cam, F->integ, S, F->h_group_nodes[g],
@@ -784,7 +797,10 @@ int enqueue_camera(ocr_forest *F, CamPlan &P, float4 *rgba, int *counts, unsigne
     ++launches;
   }
   // the super-root pass writes every pixel
-  OCR_CUDA(launch_coarsen(T, Fd, P.cam, F->integ, S, F->M, F->M, 0, P.npix, rgba, st));
+  if (F->merge == 1)
+    OCR_CUDA(launch_topdown(T, Fd, P.cam, F->integ, S, P.npix, rgba, F->nsm, st));
+  else
+    OCR_CUDA(launch_coarsen(T, Fd, P.cam, F->integ, S, F->M, F->M, 0, P.npix, rgba, st));
   ++launches;
   return OCR_OK;
 }
@@ -1012,10 +1028,12 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
 int ocr_set_tuning(ocr_forest *F, const ocr_tuning *t) {
   if (!F || !t) return OCR_ERR_INVALID;
   if (t->tile_depth < 1 || t->tile_depth > kSubtreeDepth || t->streams < 1 ||
-      t->streams > kMaxStreams || t->shell_warps < 0 || t->shell_warps > 8)
+      t->streams > kMaxStreams || t->shell_warps < 0 || t->shell_warps > 8 || t->merge < 0 ||
+      t->merge > 1)
     return OCR_ERR_INVALID;
   F->nstreams = t->streams;
   F->shell_warps = t->shell_warps;
+  F->merge = t->merge;
   if (t->tile_depth != F->tile_depth) {
     F->tile_depth = t->tile_depth;
     F->lt = F->L > F->tile_depth ? F->L - F->tile_depth : 0;
@@ -1034,6 +1052,7 @@ int ocr_get_tuning(const ocr_forest *F, ocr_tuning *t) {
   t->tile_depth = F->tile_depth;
   t->streams = F->nstreams;
   t->shell_warps = F->shell_warps;
+  t->merge = F->merge;
   t->ms = 0.f;
   return OCR_OK;
 }
@@ -1050,10 +1069,11 @@ int ocr_autotune(ocr_forest *F, int reps, ocr_tuning *best, ocr_tuning *tried, i
   for (int si = 0; si < 4; ++si) {
     if (K == 1 && streams[si] != F->nstreams) continue;  // one camera: streams are unused
     if (F->geometry == OCR_GEOM_SHELL) {
-      for (int w : warps) cand.push_back({F->tile_depth, streams[si], w, 0.f});
+      for (int w : warps) cand.push_back({F->tile_depth, streams[si], w, 0, 0.f});
     } else {
-      for (int d = 1; d <= kSubtreeDepth; ++d)
-        if (d <= F->L || d == kSubtreeDepth) cand.push_back({d, streams[si], 0, 0.f});
+      for (int m = 0; m <= 1; ++m)
+        for (int d = 1; d <= kSubtreeDepth; ++d)
+          if (d <= F->L || d == kSubtreeDepth) cand.push_back({d, streams[si], 0, m, 0.f});
     }
   }
   float4 *rgba = nullptr;

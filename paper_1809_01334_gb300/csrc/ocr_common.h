@@ -112,6 +112,10 @@ cudaError_t launch_subtree(const Topo &T, const Field &Fd, const Cam &C, const I
 cudaError_t launch_coarsen(const Topo &T, const Field &Fd, const Cam &C, const Integ &I, Scratch S,
                            int node_begin, int node_end, long long slot_begin, long long slot_end,
                            float4 *rgba, cudaStream_t stream);
+// the levels above the tile level and the pixels in one pass: one thread per
+// pixel walks the octree top-down (instead of the per-level coarsen passes)
+cudaError_t launch_topdown(const Topo &T, const Field &Fd, const Cam &C, const Integ &I, Scratch S,
+                           long long npix, float4 *rgba, int nsm, cudaStream_t stream);
 
 // Adjoint (ocr_backward.cu)
 cudaError_t bwd_leaf_scan(const Topo &T, const int4 *rect, long long *bs, long long bs_cap,

@@ -672,6 +672,99 @@ __global__ void __launch_bounds__(kCoarsenThreads, 8)
   if (tid < 4 && s_cnt[tid]) atomicAdd(S.stats + kStatCoarse + tid, s_cnt[tid]);
 }
 
+// Top-down merge of the levels above the tile level, one thread per pixel:
+// the octree is walked from the super-root in the ray's front-to-back order
+// of octants (q ^ mask, mask the direction's sign bits), descending into
+// internal nodes whose rectangle holds the pixel; a tile-level node
+// contributes its (node, ray) aggregate, a leaf above the tile level its
+// segment; the contributions are combined nearest first (Eq. 2.14).  The same
+// result as the per-level passes up to rounding order (Eq. 2.14 is
+// associative), in one launch and without intermediate aggregates in HBM.
+constexpr int kTopDownThreads = 128;
+constexpr int kMaxTopDownDepth = 24;
+
+template <bool SURF>
+__global__ void __launch_bounds__(kTopDownThreads)
+    topdown_kernel(Topo T, Field Fd, Cam c, Integ I, Scratch S, long long npix, float4 *rgba) {
+  __shared__ float4 s_tfv[8], s_tfs[8];
+  __shared__ unsigned long long s_cnt[3];
+  const int tid = threadIdx.x;
+  if (tid < 8) {
+    const float4 v = Fd.tf[tid];
+    const float4 w = Fd.tf[tid < 7 ? tid + 1 : 7];
+    s_tfv[tid] = v;
+    s_tfs[tid] = make_float4(w.x - v.x, w.y - v.y, w.z - v.z, w.w - v.w);
+  }
+  if (tid < 3) s_cnt[tid] = 0ull;
+  __syncthreads();
+  const TF tf{s_tfv, s_tfs, Fd.s_min, Fd.inv_ds7};
+  const float scale = ldexpf(1.f, -T.L);
+  unsigned hits = 0, tests = 0;
+  int steps = 0;
+  for (long long pix = (long long)blockIdx.x * kTopDownThreads + tid; pix < npix;
+       pix += (long long)gridDim.x * kTopDownThreads) {
+    const int i = (int)(pix % c.w), j = (int)(pix / c.w);
+    float3 org, dir;
+    pixel_ray(c, i, j, org, dir);
+    const float3 inv = make_float3(recip_or_zero(dir.x), recip_or_zero(dir.y), recip_or_zero(dir.z));
+    const int mask = (dir.x < 0.f ? 1 : 0) | (dir.y < 0.f ? 2 : 0) | (dir.z < 0.f ? 4 : 0);
+    float4 acc = seg_identity();
+    int nhit = 0;
+    int stk[kMaxTopDownDepth];  // internal index of the node and the next octant to visit
+    unsigned char sq[kMaxTopDownDepth];
+    int sp = 0;
+    stk[0] = T.M;  // the super-root
+    sq[0] = 0;
+    sp = 1;
+    while (sp > 0) {
+      const int nd = stk[sp - 1];
+      const int q = sq[sp - 1];
+      if (q == 8) {
+        --sp;
+        continue;
+      }
+      sq[sp - 1] = (unsigned char)(q + 1);
+      const int ch = __ldg(T.child + 8 * nd + (q ^ mask));
+      if (ch < 0) continue;
+      const int4 r = __ldg(S.rect + ch);
+      if (i < r.x || i > r.y || j < r.z || j > r.w) continue;
+      if (ch < T.N) {  // a leaf above the tile level
+        ++tests;
+        const int4 g = __ldg(T.geo + ch);
+        float a0, a1;
+        if (slab(org, dir, inv, node_lo(g, scale), ldexpf(1.f, -g.w), c.amin, c.amax, a0, a1)) {
+          acc = seg_combine(acc, leaf_segment<SURF>(T, Fd, c, I, tf, ch, org, dir, inv, scale,
+                                                    steps));
+          ++nhit;
+        }
+      } else if (__ldg(T.geo + ch).w == T.lt) {  // a tile-level node: its aggregate
+        const long long e = __ldg(S.off + ch - T.N) + (long long)(j - r.z) * (r.y - r.x + 1) +
+                            (i - r.x);
+        acc = seg_combine(acc, S.entries[e]);
+      } else if (sp < kMaxTopDownDepth) {
+        stk[sp] = ch - T.N;
+        sq[sp] = 0;
+        ++sp;
+      }
+    }
+    rgba[pix] = make_float4(fmaf(acc.x, I.bg[0], acc.y), fmaf(acc.x, I.bg[1], acc.z),
+                            fmaf(acc.x, I.bg[2], acc.w), kOne - acc.x);
+    if (nhit && S.counts) S.counts[pix] += nhit;  // after the subtree pass, in stream order
+    hits += nhit;
+  }
+  // counters: segments, RK steps and leaf tests of the levels above the tile level
+  unsigned long long v[3] = {hits, (unsigned long long)steps, tests};
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    unsigned long long x = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if ((tid & 31) == 0 && x) atomicAdd(&s_cnt[q], x);
+  }
+  __syncthreads();
+  if (tid < 3 && s_cnt[tid]) atomicAdd(S.stats + kStatCoarse + tid, s_cnt[tid]);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------- launchers --
@@ -755,6 +848,19 @@ cudaError_t launch_coarsen(const Topo &T, const Field &Fd, const Cam &C, const I
   else
     coarsen_kernel<false, false><<<g, kCoarsenThreads, 0, stream>>>(T, Fd, C, I, S, nb, ne, s0,
                                                                      s1, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_topdown(const Topo &T, const Field &Fd, const Cam &C, const Integ &I, Scratch S,
+                           long long npix, float4 *rgba, int nsm, cudaStream_t stream) {
+  if (npix <= 0) return cudaSuccess;
+  const long long need = (npix + kTopDownThreads - 1) / kTopDownThreads;
+  const long long cap = (long long)(nsm > 0 ? nsm : 1) * 16;
+  const unsigned g = (unsigned)(need < cap ? need : cap);
+  if (I.surface)
+    topdown_kernel<true><<<g, kTopDownThreads, 0, stream>>>(T, Fd, C, I, S, npix, rgba);
+  else
+    topdown_kernel<false><<<g, kTopDownThreads, 0, stream>>>(T, Fd, C, I, S, npix, rgba);
   return cudaGetLastError();
 }
 

@@ -140,8 +140,9 @@ class Renderer:
         the fastest (ocr_autotune)."""
         return capi.autotune(self.h, reps)
 
-    def set_tuning(self, tile_depth: int = 3, streams: int = 4, shell_warps: int = 0):
-        capi.set_tuning(self.h, tile_depth, streams, shell_warps)
+    def set_tuning(self, tile_depth: int = 3, streams: int = 4, shell_warps: int = 0,
+                   merge: int = 0):
+        capi.set_tuning(self.h, tile_depth, streams, shell_warps, merge)
 
     def get_tuning(self) -> dict:
         return capi.get_tuning(self.h)

@@ -72,9 +72,11 @@ def test_batch_in_a_cuda_graph():
     r.close()
 
 
+@pytest.mark.parametrize("merge", [0, 1])
 @pytest.mark.parametrize("depth", [1, 2, 3])
-def test_every_tile_depth_matches_the_oracle(depth):
-    """The autotuner's tile depths (octree levels merged inside one CTA) all
+def test_every_tile_depth_matches_the_oracle(depth, merge):
+    """The autotuner's tile depths (octree levels merged inside one CTA) and
+    both merges of the levels above (per-level passes, one top-down pass) all
     give the oracle's images and segment counts, on several cameras at once
     with 1, 2 and 8 internal streams."""
     from paper_1809_01334_gb300 import Renderer
@@ -83,7 +85,7 @@ def test_every_tile_depth_matches_the_oracle(depth):
     r = Renderer(f, tf, INTEG)
     r.set_cameras(cams)
     for streams in (1, 2, 8):
-        r.set_tuning(tile_depth=depth, streams=streams)
+        r.set_tuning(tile_depth=depth, streams=streams, merge=merge)
         assert r.get_tuning()["tile_depth"] == depth
         flat, views, st = r.render_batch(with_index=True)
         torch.cuda.synchronize()
