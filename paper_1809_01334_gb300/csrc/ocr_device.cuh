@@ -162,6 +162,80 @@ __device__ __forceinline__ float4 lin4(float a, float4 x, float b, float4 y) {
                      fmaf(a, x.w, b * y.w));
 }
 
+// One Dormand-Prince 5(4) step from (1, 0) over the dyadic interval
+// [idx, idx + 1] 2^-depth of tau (kq0: the medium at its far end): the
+// fifth-order value Y5, the medium at the near end kq6, the embedded error and
+// the largest H kappa at the nodes (the split tests of Algorithm 1).
+template <class Fld>
+__device__ __forceinline__ void dopri_eval(const Fld &cu, const TF &tf, float dx, int depth,
+                                           unsigned idx, float4 kq0, float4 &Y5, float4 &kq6,
+                                           float &err, float &hkmax) {
+  const float4 one = seg_identity();
+  const float dtau = ldexpf(1.f, -depth);
+  const float t0 = (float)idx * dtau;
+  const float H = dx * dtau;
+  const float4 kq2 = medium(cu, tf, fmaf(dp::c2, dtau, t0));
+  const float4 kq3 = medium(cu, tf, fmaf(dp::c3, dtau, t0));
+  const float4 kq4 = medium(cu, tf, fmaf(dp::c4, dtau, t0));
+  const float4 kq5 = medium(cu, tf, fmaf(dp::c5, dtau, t0));
+  kq6 = medium(cu, tf, t0 + dtau);
+  const float4 K1 = rhs(kq0, one);
+  const float4 K2 = rhs(kq2, axpy(H * dp::a21, K1, one));
+  const float4 K3 = rhs(kq3, axpy(H, lin4(dp::a31, K1, dp::a32, K2), one));
+  float4 t = lin4(dp::a41, K1, dp::a42, K2);
+  t = axpy(dp::a43, K3, t);
+  const float4 K4 = rhs(kq4, axpy(H, t, one));
+  t = lin4(dp::a51, K1, dp::a52, K2);
+  t = axpy(dp::a53, K3, t);
+  t = axpy(dp::a54, K4, t);
+  const float4 K5 = rhs(kq5, axpy(H, t, one));
+  t = lin4(dp::a61, K1, dp::a62, K2);
+  t = axpy(dp::a63, K3, t);
+  t = axpy(dp::a64, K4, t);
+  t = axpy(dp::a65, K5, t);
+  const float4 K6 = rhs(kq6, axpy(H, t, one));
+  t = lin4(dp::b1, K1, dp::b3, K3);
+  t = axpy(dp::b4, K4, t);
+  t = axpy(dp::b5, K5, t);
+  t = axpy(dp::b6, K6, t);
+  Y5 = axpy(H, t, one);
+  const float4 K7 = rhs(kq6, Y5);
+  float4 e = lin4(dp::e1, K1, dp::e3, K3);
+  e = axpy(dp::e4, K4, e);
+  e = axpy(dp::e5, K5, e);
+  e = axpy(dp::e6, K6, e);
+  e = axpy(dp::e7, K7, e);
+  err = H * fmaxf(fmaxf(fabsf(e.x), fabsf(e.y)), fmaxf(fabsf(e.z), fabsf(e.w)));
+  hkmax = H * fmaxf(fmaxf(fmaxf(kq0.x, kq2.x), fmaxf(kq3.x, kq4.x)), fmaxf(kq5.x, kq6.x));
+}
+
+// Algorithm 1's bisection with Dormand-Prince steps, one step per call, walked
+// far half first: the step at (depth, idx) is taken; if the split test fails
+// it is replaced by its halves (depth + 1), else its value is combined behind
+// acc (Eq. 2.14) and the walk moves on.  Returns true when the segment is done.
+template <class Fld>
+__device__ __forceinline__ bool dopri_advance(const Fld &cu, const TF &tf, float dx,
+                                              const Integ &I, int &depth, unsigned &idx,
+                                              float4 &kq0, float4 &acc, int &steps) {
+  float4 Y5, kq6;
+  float err, hkmax;
+  dopri_eval(cu, tf, dx, depth, idx, kq0, Y5, kq6, err, hkmax);
+  ++steps;
+  if (depth < I.max_depth && (hkmax > I.c_rk || err > I.tol)) {
+    ++depth;  // far half first; it starts where this step started
+    idx <<= 1;
+    return false;
+  }
+  acc = seg_combine(Y5, acc);
+  kq0 = kq6;
+  ++idx;
+  while (depth > 0 && !(idx & 1u)) {
+    idx >>= 1;
+    --depth;
+  }
+  return depth == 0;
+}
+
 // (A, B) of one segment of world length dx: RK4 x nsteps, or DOPRI5 inside
 // the midpoint bisection of Algorithm 1, walked far half first so that each
 // accepted piece is nearer than everything accumulated so far.
@@ -245,45 +319,11 @@ __device__ float4 integrate_segment(const Fld &cu, const TF &tf, float dx, const
     return acc;
   }
   for (;;) {
-    const float dtau = ldexpf(1.f, -depth);
-    const float t0 = (float)idx * dtau;
-    const float H = dx * dtau;
-    const float4 kq2 = medium(cu, tf, fmaf(dp::c2, dtau, t0));
-    const float4 kq3 = medium(cu, tf, fmaf(dp::c3, dtau, t0));
-    const float4 kq4 = medium(cu, tf, fmaf(dp::c4, dtau, t0));
-    const float4 kq5 = medium(cu, tf, fmaf(dp::c5, dtau, t0));
-    const float4 kq6 = medium(cu, tf, t0 + dtau);
-    const float4 K1 = rhs(kq0, one);
-    const float4 K2 = rhs(kq2, axpy(H * dp::a21, K1, one));
-    const float4 K3 = rhs(kq3, axpy(H, lin4(dp::a31, K1, dp::a32, K2), one));
-    float4 t = lin4(dp::a41, K1, dp::a42, K2);
-    t = axpy(dp::a43, K3, t);
-    const float4 K4 = rhs(kq4, axpy(H, t, one));
-    t = lin4(dp::a51, K1, dp::a52, K2);
-    t = axpy(dp::a53, K3, t);
-    t = axpy(dp::a54, K4, t);
-    const float4 K5 = rhs(kq5, axpy(H, t, one));
-    t = lin4(dp::a61, K1, dp::a62, K2);
-    t = axpy(dp::a63, K3, t);
-    t = axpy(dp::a64, K4, t);
-    t = axpy(dp::a65, K5, t);
-    const float4 K6 = rhs(kq6, axpy(H, t, one));
-    t = lin4(dp::b1, K1, dp::b3, K3);
-    t = axpy(dp::b4, K4, t);
-    t = axpy(dp::b5, K5, t);
-    t = axpy(dp::b6, K6, t);
-    const float4 Y5 = axpy(H, t, one);
-    const float4 K7 = rhs(kq6, Y5);
-    float4 e = lin4(dp::e1, K1, dp::e3, K3);
-    e = axpy(dp::e4, K4, e);
-    e = axpy(dp::e5, K5, e);
-    e = axpy(dp::e6, K6, e);
-    e = axpy(dp::e7, K7, e);
-    const float err = H * fmaxf(fmaxf(fabsf(e.x), fabsf(e.y)), fmaxf(fabsf(e.z), fabsf(e.w)));
-    const float kmax =
-        fmaxf(fmaxf(fmaxf(kq0.x, kq2.x), fmaxf(kq3.x, kq4.x)), fmaxf(kq5.x, kq6.x));
+    float4 Y5, kq6;
+    float err, hkmax;
+    dopri_eval(cu, tf, dx, depth, idx, kq0, Y5, kq6, err, hkmax);
     ++steps;
-    if (depth < I.max_depth && (H * kmax > I.c_rk || err > I.tol)) {
+    if (depth < I.max_depth && (hkmax > I.c_rk || err > I.tol)) {
       ++depth;  // far half first; it starts where this step started
       idx <<= 1;
       continue;

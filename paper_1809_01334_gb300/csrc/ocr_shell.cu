@@ -172,8 +172,8 @@ __device__ float4 resolve_overlap(float4 N, float2 in, float4 F, float2 iF) {
   return r;
 }
 
-__global__ void shell_rays_kernel(const int4 *__restrict__ geo, int N, Shell S, Field Fd, Cam c,
-                                  Integ I,
+__global__ void __launch_bounds__(256, 2)
+    shell_rays_kernel(const int4 *__restrict__ geo, int N, Shell S, Field Fd, Cam c, Integ I,
                                   const long long *__restrict__ ray_off, long long npix,
                                   const unsigned long long *__restrict__ keys, long long key_cap,
                                   int cap, float4 *rgba, int *counts,
@@ -235,22 +235,67 @@ __global__ void shell_rays_kernel(const int4 *__restrict__ geo, int N, Shell S, 
     float3 org, dir;
     pixel_ray(c, i, j, org, dir);
     const float rl = sqrtf(fmaf(dir.x, dir.x, fmaf(dir.y, dir.y, dir.z * dir.z)));
-    for (int k = lane; k < n; k += 32) {
-      const unsigned lp = (unsigned)(key[k] & 0xffffffffu);
-      const int leaf = (int)(lp >> 1), piece = (int)(lp & 1u);
+    if (I.method == 1) {
+      // Dormand-Prince inside Algorithm 1: every lane advances its segment one
+      // step at a time and takes the ray's next segment as soon as it is done,
+      // so the lanes stay busy while some of them bisect
+      int next = 0, k = 0, depth = 0;
+      unsigned idx = 0;
+      bool busy = false;
       ShellSeg g;
-      float dx;
-      float2 ivk;
-      // an entry the fill pass did not write, or a piece the ray does not have
-      if (leaf >= N ||
-          !shell_segment(S, Fd.nodal, c, __ldg(geo + leaf), leaf, piece, org, dir, rl, g, dx, ivk)) {
-        ++errs;
-        val[k] = seg_identity();
-        iv[k] = make_float2(0.f, 0.f);
-        continue;
+      float dx = 0.f;
+      float2 ivk = make_float2(0.f, 0.f);
+      float4 kq0 = seg_identity(), sacc = seg_identity();
+      for (;;) {
+        const unsigned idle = __ballot_sync(0xffffffffu, !busy);
+        const int kk = next + __popc(idle & ((1u << lane) - 1u));
+        next += __popc(idle);
+        if (!busy && kk < n) {
+          k = kk;
+          const unsigned lp = (unsigned)(key[k] & 0xffffffffu);
+          const int leaf = (int)(lp >> 1), piece = (int)(lp & 1u);
+          // an entry the fill pass did not write, or a piece the ray does not have
+          if (leaf >= N || !shell_segment(S, Fd.nodal, c, __ldg(geo + leaf), leaf, piece, org,
+                                          dir, rl, g, dx, ivk)) {
+            ++errs;
+            val[k] = seg_identity();
+            iv[k] = make_float2(0.f, 0.f);
+          } else {
+            busy = true;
+            depth = 0;
+            idx = 0;
+            sacc = seg_identity();
+            kq0 = medium(g, tf, 0.f);
+          }
+        }
+        if (!__any_sync(0xffffffffu, busy)) {
+          if (next >= n) break;
+          continue;
+        }
+        if (busy && dopri_advance(g, tf, dx, I, depth, idx, kq0, sacc, steps)) {
+          val[k] = sacc;
+          iv[k] = ivk;
+          busy = false;
+        }
       }
-      val[k] = integrate_segment(g, tf, dx, I, steps);
-      iv[k] = ivk;
+    } else {
+      for (int k = lane; k < n; k += 32) {
+        const unsigned lp = (unsigned)(key[k] & 0xffffffffu);
+        const int leaf = (int)(lp >> 1), piece = (int)(lp & 1u);
+        ShellSeg g;
+        float dx;
+        float2 ivk;
+        // an entry the fill pass did not write, or a piece the ray does not have
+        if (leaf >= N || !shell_segment(S, Fd.nodal, c, __ldg(geo + leaf), leaf, piece, org, dir,
+                                        rl, g, dx, ivk)) {
+          ++errs;
+          val[k] = seg_identity();
+          iv[k] = make_float2(0.f, 0.f);
+          continue;
+        }
+        val[k] = integrate_segment(g, tf, dx, I, steps);
+        iv[k] = ivk;
+      }
     }
     segs += n;
     __syncwarp();
