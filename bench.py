@@ -64,6 +64,8 @@ def parse_args():
                    help="run the shell measurements alone (profiling captures)")
     p.add_argument("--shell-image", default="2048x2048",
                    help="image size WxH of the shell render (smaller sizes only for profiling)")
+    p.add_argument("--shell-bwd-image", default="1024x1024",
+                   help="image size WxH of the shell adjoint (smaller sizes only for profiling)")
     p.add_argument("--image", default="1920x1080",
                    help="image size WxH (smaller sizes only for profiling captures)")
     return p.parse_args()
@@ -294,7 +296,8 @@ def run_shell(args, dev, flush):
     r.close()
     del out
     # differentiation on the levels 4-6 shell
-    forest, tf, cam, integ = I.preset_c5()
+    bw, bh = (int(x) for x in args.shell_bwd_image.split("x"))
+    forest, tf, cam, integ = I.preset_c5(w=bw, h=bh)
     r = Renderer(forest, tf, integ, device=dev)
     r.set_camera(cam)
     out = torch.empty((cam.h, cam.w, 4), dtype=torch.float32, device=dev)
@@ -309,8 +312,8 @@ def run_shell(args, dev, flush):
     fms = _timed(lambda: r.render(out), stream, flush, 2, 5)
     bms = _timed(lambda: r.backward(grad_img), stream, flush, 2, 5)
     c5 = {"workload": "cubed-sphere shell, levels 4-6 (%d leaves, degree-2 FP32 data), "
-                      "1024x1024, DOPRI5 tol 1e-5; L2 loss against a render of a seeded 5%% "
-                      "nodal perturbation" % forest.nleaves,
+                      "%dx%d, DOPRI5 tol 1e-5; L2 loss against a render of a seeded 5%% "
+                      "nodal perturbation" % (forest.nleaves, bw, bh),
           "ms_forward": fms, "ms_backward": bms, "fwd_bwd_over_fwd": (fms + bms) / fms,
           "segments": st["segments"], "grads": "27 nodal values per leaf and the 32 knot values"}
     r.close()
