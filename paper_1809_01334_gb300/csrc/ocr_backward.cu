@@ -357,7 +357,9 @@ __device__ void dopri_step_bwd(SA &S, const TF &tf, float t0, float dtau, float 
   float4 Kb[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) Kb[i] = scale4(H * b[i], ybar);
-#pragma unroll
+  // one copy of the node adjoint in the code (it inlines the field and its
+  // weights): the stages are walked by a loop
+#pragma unroll 1
   for (int i = 5; i >= 0; --i) {
     S.bwd(tf, tt[i], node_vbar(Kb[i], Y[i]), tg);
     const float4 Yb = scale4(-kq[i].x, Kb[i]);
@@ -647,24 +649,98 @@ __global__ void __launch_bounds__(kBwdWarps * 32, 4)
   if (tid < 32 && s_g[tid] != 0.f) atomicAdd(g_tf + tid, s_g[tid]);
 }
 
-// The same for a shell forest: the lists hold (alpha_in, leaf, piece) keys;
-// the segment adjoint goes through the inverse map and the degree-2 weights,
-// the 27 nodal adjoints of a segment collected in shared memory.  Overlap
-// resolution (cut and average of rounding slivers) is treated as plain
-// combination here.
-__global__ void __launch_bounds__(kBwdWarps * 32)
-    shell_ray_backward_kernel(const int4 *__restrict__ geo, int N, Shell S, Field Fd, Cam c,
-                              Integ I, const float4 *dL, const long long *ray_off,
-                              const unsigned long long *keys, long long key_cap, int cap,
-                              float *g_nodal, float *g_tf, unsigned long long *err) {
+// The same for a shell forest, in two passes over lists that hold
+// (alpha_in, leaf, piece) keys.  Overlap resolution (cut and average of
+// rounding slivers) is treated as plain combination here.
+//
+// Pass 1, one warp per ray: sort the ray's keys (carrying each segment's index
+// in the leaf-grouped list), integrate every segment, and store per segment,
+// at that index, the transmittance of the nearer segments and its own
+// (rec_ta) and the aggregate of the farther ones (rec_g).  Rays whose image
+// adjoint is zero are skipped (pass 2 skips their segments too).
+__global__ void __launch_bounds__(256)
+    shell_bwd_values_kernel(const int4 *__restrict__ geo, int N, Shell S, Field Fd, Cam c,
+                            Integ I, const float4 *dL, const long long *ray_off,
+                            const unsigned long long *keys, const unsigned *kpos,
+                            long long key_cap, int cap, float2 *rec_ta, float4 *rec_g,
+                            unsigned long long *err) {
   extern __shared__ __align__(16) unsigned char s_raw[];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   float4 *s_val = reinterpret_cast<float4 *>(s_raw);
   unsigned long long *s_key = reinterpret_cast<unsigned long long *>(s_val + nw * cap);
-  int *s_lf = reinterpret_cast<int *>(s_key + nw * cap);
-  float *s_g27 = reinterpret_cast<float *>(s_lf + nw * cap);  // [27][blockDim.x]
+  int *s_pos = reinterpret_cast<int *>(s_key + nw * cap);
+  __shared__ float4 s_tfv[8], s_tfs[8];
+  if (tid < 8) {
+    const float4 v = Fd.tf[tid];
+    const float4 w = Fd.tf[tid < 7 ? tid + 1 : 7];
+    s_tfv[tid] = v;
+    s_tfs[tid] = make_float4(w.x - v.x, w.y - v.y, w.z - v.z, w.w - v.w);
+  }
+  __syncthreads();
+  float4 *val = s_val + wid * cap;
+  unsigned long long *key = s_key + wid * cap;
+  int *pos = s_pos + wid * cap;
+  float *Tk = reinterpret_cast<float *>(key);  // reuses the key array after sorting
+  float *Ak = reinterpret_cast<float *>(key) + cap;
+  const TF tf{s_tfv, s_tfs, Fd.s_min, Fd.inv_ds7};
+  const long long npix = (long long)c.w * c.h;
+  const long long nwarp = (long long)gridDim.x * nw;
+  int bad = 0;
+  for (long long pix = (long long)blockIdx.x * nw + wid; pix < npix; pix += nwarp) {
+    const long long h0 = ray_off[pix];
+    const int n = (int)(ray_off[pix + 1] - h0);
+    if (n == 0) continue;
+    if (n > cap || h0 + n > key_cap) {
+      if (lane == 0) ++bad;
+      continue;
+    }
+    const float4 gp = dL[pix];
+    if (gp.x == 0.f && gp.y == 0.f && gp.z == 0.f && gp.w == 0.f) continue;
+    int P = 32;
+    while (P < n) P <<= 1;
+    for (int k = lane; k < P; k += 32) {
+      key[k] = k < n ? keys[h0 + k] : ~0ull;
+      pos[k] = k < n ? (int)kpos[h0 + k] : -1;
+    }
+    __syncwarp();
+    warp_sort(key, pos, P, lane);  // nearest first, the list index along
+    const int i = (int)(pix % c.w), j = (int)(pix / c.w);
+    float3 org, dir;
+    pixel_ray(c, i, j, org, dir);
+    const float rl = sqrtf(fmaf(dir.x, dir.x, fmaf(dir.y, dir.y, dir.z * dir.z)));
+    int steps = 0;
+    bad += shell_ray_values(geo, N, S, Fd.nodal, c, I, tf, key, n, org, dir, rl, val, nullptr,
+                            lane, steps);
+    __syncwarp();
+    near_far_scans(n, lane, val, Tk, Ak);
+    for (int k = lane; k < n; k += 32) {
+      const unsigned q = (unsigned)pos[k];
+      if ((long long)q < key_cap) {
+        rec_ta[q] = make_float2(Tk[k], Ak[k]);
+        rec_g[q] = val[k];
+      }
+    }
+    __syncwarp();
+  }
+  if (bad) atomicAdd(err, (unsigned long long)bad);
+}
+
+// Pass 2, one thread per segment of the leaf-grouped list: the ray, the
+// segment's field, its step adjoints with the near transmittance and far
+// aggregate of pass 1; the 27 nodal adjoints go to this thread's column of a
+// shared array and are summed over the warp's lanes of the same leaf (the list
+// keeps a leaf's segments together), one atomic per value and leaf.
+constexpr int kSegThreads = 128;
+constexpr int kSegStride = kSegThreads + 1;  // row stride: lanes summing rows hit distinct banks
+
+__global__ void __launch_bounds__(kSegThreads, 4)
+    shell_bwd_segments_kernel(const int4 *__restrict__ geo, int N, Shell S, Field Fd, Cam c,
+                              Integ I, const float4 *dL, const int2 *lm, const float2 *rec_ta,
+                              const float4 *rec_g, long long nseg, float *g_nodal, float *g_tf) {
+  __shared__ float s_g27[27 * kSegStride];
   __shared__ float4 s_tfv[8], s_tfs[8];
   __shared__ float s_g[32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid < 8) {
     const float4 v = Fd.tf[tid];
     const float4 w = Fd.tf[tid < 7 ? tid + 1 : 7];
@@ -673,75 +749,54 @@ __global__ void __launch_bounds__(kBwdWarps * 32)
   }
   if (tid < 32) s_g[tid] = 0.f;
   __syncthreads();
-  float4 *val = s_val + wid * cap;
-  unsigned long long *key = s_key + wid * cap;
-  int *lf = s_lf + wid * cap;
-  float *Tk = reinterpret_cast<float *>(key);  // reuses the key array after sorting
-  float *Ak = reinterpret_cast<float *>(key) + cap;
   const TF tf{s_tfv, s_tfs, Fd.s_min, Fd.inv_ds7};
   TfGrad tg;
   tg.s_g = s_g;
   const long long npix = (long long)c.w * c.h;
-  const long long nwarp = (long long)gridDim.x * nw;
-  for (long long pix = (long long)blockIdx.x * nw + wid; pix < npix; pix += nwarp) {
-    const long long h0 = ray_off[pix];
-    const int n = (int)(ray_off[pix + 1] - h0);
-    if (n == 0) continue;
-    if (n > cap || h0 + n > key_cap) {
-      if (lane == 0) atomicAdd(err, 1ull);
-      continue;
-    }
-    const float4 gp = dL[pix];
-    if (gp.x == 0.f && gp.y == 0.f && gp.z == 0.f && gp.w == 0.f) continue;
-    int P = 32;
-    while (P < n) P <<= 1;
-    for (int k = lane; k < P; k += 32) key[k] = k < n ? keys[h0 + k] : ~0ull;
-    __syncwarp();
-    warp_sort(key, nullptr, P, lane);
-    for (int k = lane; k < n; k += 32) lf[k] = (int)(unsigned)(key[k] & 0xffffffffu);
-    __syncwarp();
-    const int i = (int)(pix % c.w), j = (int)(pix / c.w);
-    float3 org, dir;
-    pixel_ray(c, i, j, org, dir);
-    const float rl = sqrtf(fmaf(dir.x, dir.x, fmaf(dir.y, dir.y, dir.z * dir.z)));
-    int steps = 0, bad = 0;
-    for (int k = lane; k < n; k += 32) {
-      const int leaf = lf[k] >> 1, piece = lf[k] & 1;
-      ShellSeg g;
-      float dx;
-      float2 iv;
-      if (leaf >= N ||
-          !shell_segment(S, Fd.nodal, c, __ldg(geo + leaf), leaf, piece, org, dir, rl, g, dx, iv)) {
-        ++bad;
-        val[k] = seg_identity();
-        continue;
-      }
-      val[k] = integrate_segment(g, tf, dx, I, steps);
-    }
-    __syncwarp();
-    near_far_scans(n, lane, val, Tk, Ak);
-    const float4 Ib = make_float4(gp.x, gp.y, gp.z, 0.f);
-    for (int k = lane; k < n; k += 32) {
-      const int leaf = lf[k] >> 1, piece = lf[k] & 1;
-      ShellAdj A;
-      float dx;
-      float2 iv;
-      if (leaf >= N ||
-          !shell_segment(S, Fd.nodal, c, __ldg(geo + leaf), leaf, piece, org, dir, rl, A.g, dx,
-                         iv))
-        continue;
-      A.g27 = s_g27 + tid;
-      A.stride = (int)blockDim.x;
+  float *g27 = s_g27 + tid;
+  for (long long b = (long long)blockIdx.x * kSegThreads; b < nseg;
+       b += (long long)gridDim.x * kSegThreads) {
+    const long long e = b + tid;
 #pragma unroll
-      for (int q = 0; q < 27; ++q) A.g27[q * A.stride] = 0.f;
-      segment_steps_bwd(A, tf, dx, I, Tk[k], val[k], Ak[k], Ib, gp.w, tg);
-#pragma unroll
-      for (int q = 0; q < 27; ++q) {
-        const float v = A.g27[q * A.stride];
-        if (v != 0.f) atomicAdd(g_nodal + 27 * (size_t)leaf + q, v);
+    for (int q = 0; q < 27; ++q) g27[q * kSegStride] = 0.f;
+    int leaf = -1;
+    if (e < nseg) {
+      const int2 m = lm[e];
+      const int lf = m.y >> 1, piece = m.y & 1;
+      if (m.x >= 0 && (long long)m.x < npix && m.y >= 0 && lf < N) {
+        const float4 gp = dL[m.x];
+        if (gp.x != 0.f || gp.y != 0.f || gp.z != 0.f || gp.w != 0.f) {
+          float3 org, dir;
+          pixel_ray(c, m.x % c.w, m.x / c.w, org, dir);
+          const float rl = sqrtf(fmaf(dir.x, dir.x, fmaf(dir.y, dir.y, dir.z * dir.z)));
+          ShellAdj A;
+          float dx;
+          float2 iv;
+          if (shell_segment(S, Fd.nodal, c, __ldg(geo + lf), lf, piece, org, dir, rl, A.g, dx,
+                            iv)) {
+            A.g27 = g27;
+            A.stride = kSegStride;
+            const float2 ta = rec_ta[e];
+            segment_steps_bwd(A, tf, dx, I, ta.x, rec_g[e], ta.y,
+                              make_float4(gp.x, gp.y, gp.z, 0.f), gp.w, tg);
+            leaf = lf;
+          }
+        }
       }
     }
-    if (bad) atomicAdd(err, (unsigned long long)bad);
+    __syncwarp();
+    unsigned todo = __ballot_sync(0xffffffffu, leaf >= 0);
+    while (todo) {
+      const int lf = __shfl_sync(0xffffffffu, leaf, __ffs(todo) - 1);
+      const unsigned grp = __ballot_sync(0xffffffffu, leaf == lf);
+      todo &= ~grp;
+      if (lane < 27) {
+        const float *row = s_g27 + lane * kSegStride + (wid << 5);
+        float sum = 0.f;
+        for (unsigned mm = grp; mm; mm &= mm - 1) sum += row[__ffs(mm) - 1];
+        if (sum != 0.f) atomicAdd(g_nodal + 27 * (size_t)lf + lane, sum);
+      }
+    }
     __syncwarp();
   }
   tg.flush();
@@ -833,36 +888,51 @@ cudaError_t bwd_rays(const Topo &T, const Field &Fd, const Cam &C, const Integ &
 
 namespace ocr {
 
-// warps per CTA: up to kBwdWarps, within 200 KB of shared memory
+// warps per CTA of the values pass: up to 8, within 200 KB of shared memory
 static int shell_bwd_warps(int cap) {
-  const size_t per = (size_t)cap * (sizeof(float4) + sizeof(unsigned long long) + sizeof(int)) +
-                     sizeof(float) * 27 * 32;
+  const size_t per = (size_t)cap * (sizeof(float4) + sizeof(unsigned long long) + sizeof(int));
   const int w = (int)((200u << 10) / per);
-  return w < 1 ? 1 : (w > kBwdWarps ? kBwdWarps : w);
+  return w < 1 ? 1 : (w > 8 ? 8 : w);
 }
 
 size_t shell_bwd_smem(int cap) {
-  const int w = shell_bwd_warps(cap);
-  return (size_t)w * cap * (sizeof(float4) + sizeof(unsigned long long) + sizeof(int)) +
-         sizeof(float) * 27 * 32 * w;
+  return (size_t)shell_bwd_warps(cap) * cap *
+         (sizeof(float4) + sizeof(unsigned long long) + sizeof(int));
 }
 
 cudaError_t shell_bwd_prepare() {
   size_t most = 0;
   for (int cap = 32; cap <= kShellMaxCap; cap <<= 1)
     most = most > shell_bwd_smem(cap) ? most : shell_bwd_smem(cap);
-  return cudaFuncSetAttribute(shell_ray_backward_kernel,
+  return cudaFuncSetAttribute(shell_bwd_values_kernel,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
 }
 
-cudaError_t shell_bwd_rays(const int4 *geo, int N, const Shell &S, const Field &Fd, const Cam &C,
-                           const Integ &I, const float4 *dL, const long long *ray_off,
-                           const unsigned long long *keys, long long key_cap, int cap,
-                           float *g_nodal, float *g_tf, unsigned long long *err, int nsm,
-                           cudaStream_t st) {
+cudaError_t shell_bwd_values(const int4 *geo, int N, const Shell &S, const Field &Fd,
+                             const Cam &C, const Integ &I, const float4 *dL,
+                             const long long *ray_off, const unsigned long long *keys,
+                             const unsigned *kpos, long long key_cap, int cap, float2 *rec_ta,
+                             float4 *rec_g, unsigned long long *err, int nsm, cudaStream_t st) {
   if (cap < 32 || cap > kShellMaxCap || (cap & (cap - 1))) return cudaErrorInvalidValue;
-  shell_ray_backward_kernel<<<nsm * 4, shell_bwd_warps(cap) * 32, shell_bwd_smem(cap), st>>>(
-      geo, N, S, Fd, C, I, dL, ray_off, keys, key_cap, cap, g_nodal, g_tf, err);
+  const int warps = shell_bwd_warps(cap);
+  const long long npix = (long long)C.w * C.h;
+  const long long need = (npix + warps - 1) / warps;
+  const long long grid = need < (long long)nsm * 8 ? need : (long long)nsm * 8;
+  shell_bwd_values_kernel<<<(unsigned)(grid > 0 ? grid : 1), warps * 32, shell_bwd_smem(cap),
+                            st>>>(geo, N, S, Fd, C, I, dL, ray_off, keys, kpos, key_cap, cap,
+                                  rec_ta, rec_g, err);
+  return cudaGetLastError();
+}
+
+cudaError_t shell_bwd_segments(const int4 *geo, int N, const Shell &S, const Field &Fd,
+                               const Cam &C, const Integ &I, const float4 *dL, const int2 *lm,
+                               const float2 *rec_ta, const float4 *rec_g, long long nseg,
+                               float *g_nodal, float *g_tf, int nsm, cudaStream_t st) {
+  if (nseg <= 0) return cudaSuccess;
+  const long long need = (nseg + kSegThreads - 1) / kSegThreads;
+  const long long grid = need < (long long)nsm * 4 ? need : (long long)nsm * 4;
+  shell_bwd_segments_kernel<<<(unsigned)grid, kSegThreads, 0, st>>>(
+      geo, N, S, Fd, C, I, dL, lm, rec_ta, rec_g, nseg, g_nodal, g_tf);
   return cudaGetLastError();
 }
 

@@ -95,6 +95,15 @@ struct ocr_forest {
   unsigned long long *d_hkey = nullptr;  // [hits]
   int *d_hleaf = nullptr;
   long long hit_cap = 0;
+  // shell adjoint: per segment, its index in the leaf-grouped list (beside the
+  // key), the list itself, and the near transmittance / own transmittance / far
+  // aggregate per list entry
+  unsigned *d_skpos = nullptr;
+  int2 *d_slm = nullptr;
+  float2 *d_srta = nullptr;
+  float4 *d_srg = nullptr;
+  long long seg_cap = 0;
+  unsigned long long *d_lmcount = nullptr;
   unsigned long long *d_err = nullptr;
   int nsm = 0;
   int64_t bytes = 0;
@@ -194,6 +203,11 @@ void free_all(ocr_forest *F) {
   cudaFree(F->d_ray_off);
   cudaFree(F->d_hkey);
   cudaFree(F->d_hleaf);
+  cudaFree(F->d_skpos);
+  cudaFree(F->d_slm);
+  cudaFree(F->d_srta);
+  cudaFree(F->d_srg);
+  cudaFree(F->d_lmcount);
   cudaFree(F->d_err);
   if (F->h_group_slots) cudaFreeHost(F->h_group_slots);
   for (cudaEvent_t &e : F->ev)
@@ -371,7 +385,7 @@ int plan_shell(ocr_forest *F, CamPlan &P) {
   if ((rc = dev_alloc(&P.d_pchunk, (size_t)(P.npairs / kPairChunk + 2), F->bytes))) return rc;
   OCR_CUDA(bwd_chunk_map(P.d_leaf_off, F->N, P.d_pchunk, 0));
   OCR_CUDA(cudaMemsetAsync(P.d_rcount, 0, sizeof(int) * (size_t)npix, 0));
-  OCR_CUDA(shell_pairs(false, F->d_geo, F->N, F->shell, P.cam, P.d_rect, P.d_leaf_off,
+  OCR_CUDA(shell_pairs(0, F->d_geo, F->N, F->shell, P.cam, P.d_rect, P.d_leaf_off,
                        P.d_pchunk, P.npairs, P.d_rcount, nullptr, nullptr, nullptr, 0,
                        F->d_stats, 0));
   OCR_CUDA(bwd_count_scan(P.d_rcount, npix, P.d_sbsums, P.bs_cap, P.d_ray_off, 0));
@@ -388,22 +402,31 @@ int plan_shell(ocr_forest *F, CamPlan &P) {
 }
 
 // Enqueue the segment lists of one camera of a shell forest on st: pruning,
-// pair space, counts, list offsets, lists.  No host synchronisation.
-int enqueue_shell_lists(ocr_forest *F, CamPlan &P, unsigned char *visible, cudaStream_t st) {
+// pair space, counts, list offsets, lists (for the adjoint also the
+// leaf-grouped list, into F's adjoint buffers).  No host synchronisation.
+int enqueue_shell_lists(ocr_forest *F, CamPlan &P, unsigned char *visible, cudaStream_t st,
+                        bool adjoint = false) {
   const long long npix = P.npix;
   const Topo T{F->d_geo, nullptr, nullptr, F->N, 0, F->L, 0};
   OCR_CUDA(shell_cull(F->d_geo, F->N, F->shell, P.cam, P.d_rect, visible, F->d_stats, st));
   OCR_CUDA(bwd_leaf_scan(T, P.d_rect, P.d_sbsums, P.bs_cap, P.d_leaf_off, st));
   OCR_CUDA(bwd_chunk_map(P.d_leaf_off, F->N, P.d_pchunk, st));
   OCR_CUDA(cudaMemsetAsync(P.d_rcount, 0, sizeof(int) * (size_t)npix, st));
-  OCR_CUDA(shell_pairs(false, F->d_geo, F->N, F->shell, P.cam, P.d_rect, P.d_leaf_off,
+  OCR_CUDA(shell_pairs(0, F->d_geo, F->N, F->shell, P.cam, P.d_rect, P.d_leaf_off,
                        P.d_pchunk, P.npairs, P.d_rcount, nullptr, nullptr, nullptr, 0, nullptr,
                        st));
   OCR_CUDA(bwd_count_scan(P.d_rcount, npix, P.d_sbsums, P.bs_cap, P.d_ray_off, st));
   OCR_CUDA(cudaMemsetAsync(P.d_rcursor, 0, sizeof(int) * (size_t)npix, st));
-  OCR_CUDA(shell_pairs(true, F->d_geo, F->N, F->shell, P.cam, P.d_rect, P.d_leaf_off, P.d_pchunk,
-                       P.npairs, nullptr, P.d_ray_off, P.d_rcursor, P.d_keys, P.nhits,
-                       F->d_stats, st));
+  if (adjoint) {
+    OCR_CUDA(cudaMemsetAsync(F->d_lmcount, 0, sizeof(unsigned long long), st));
+    OCR_CUDA(shell_pairs(2, F->d_geo, F->N, F->shell, P.cam, P.d_rect, P.d_leaf_off,
+                         P.d_pchunk, P.npairs, nullptr, P.d_ray_off, P.d_rcursor, P.d_keys,
+                         P.nhits, F->d_stats, st, F->d_skpos, F->d_slm, F->d_lmcount));
+  } else {
+    OCR_CUDA(shell_pairs(1, F->d_geo, F->N, F->shell, P.cam, P.d_rect, P.d_leaf_off,
+                         P.d_pchunk, P.npairs, nullptr, P.d_ray_off, P.d_rcursor, P.d_keys,
+                         P.nhits, F->d_stats, st));
+  }
   return OCR_OK;
 }
 
@@ -925,19 +948,47 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
   if ((uintptr_t)d_dL_drgba & 15) return OCR_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   if (F->geometry == OCR_GEOM_SHELL) {
-    // rebuild the first camera's lists, then one warp per ray
+    // rebuild the first camera's lists with the leaf-grouped list, then the
+    // values pass (one warp per ray) and the segment pass (one thread each)
     CamPlan &P = F->plans[0];
     const Field Fd{F->d_nodal, reinterpret_cast<const float4 *>(F->d_tf), F->s_min,
                    7.f / (F->s_max - F->s_min)};
+    if (P.nhits >= 0xffffffffll) return OCR_ERR_UNSUPPORTED;  // list indices are 32-bit
+    if (F->seg_cap < P.nhits || !F->d_lmcount) {
+      cudaFree(F->d_skpos);
+      cudaFree(F->d_slm);
+      cudaFree(F->d_srta);
+      cudaFree(F->d_srg);
+      F->d_skpos = nullptr;
+      F->d_slm = nullptr;
+      F->d_srta = nullptr;
+      F->d_srg = nullptr;
+      F->bytes -= F->seg_cap * (int64_t)(sizeof(unsigned) + sizeof(int2) + sizeof(float2) +
+                                         sizeof(float4));
+      F->seg_cap = 0;
+      const long long want = std::min(P.nhits + P.nhits / 8 + 64, 0xffffffffll);
+      int rc;
+      if ((rc = dev_alloc(&F->d_skpos, (size_t)want, F->bytes)) ||
+          (rc = dev_alloc(&F->d_slm, (size_t)want, F->bytes)) ||
+          (rc = dev_alloc(&F->d_srta, (size_t)want, F->bytes)) ||
+          (rc = dev_alloc(&F->d_srg, (size_t)want, F->bytes)))
+        return rc;
+      F->seg_cap = want;
+      if (!F->d_lmcount && (rc = dev_alloc(&F->d_lmcount, 1, F->bytes))) return rc;
+    }
     OCR_CUDA(cudaMemsetAsync(d_grad_nodal, 0, sizeof(float) * 27 * (size_t)F->N, st));
     OCR_CUDA(cudaMemsetAsync(d_grad_tf, 0, sizeof(float) * 32, st));
     OCR_CUDA(cudaMemsetAsync(F->d_stats, 0, kStats * sizeof(unsigned long long), st));
     OCR_CUDA(cudaMemsetAsync(F->d_err, 0, sizeof(unsigned long long), st));
-    int rc = enqueue_shell_lists(F, P, nullptr, st);
+    int rc = enqueue_shell_lists(F, P, nullptr, st, true);
     if (rc) return rc;
-    OCR_CUDA(shell_bwd_rays(F->d_geo, F->N, F->shell, Fd, P.cam, F->integ,
-                            reinterpret_cast<const float4 *>(d_dL_drgba), P.d_ray_off, P.d_keys,
-                            P.nhits, P.cap, d_grad_nodal, d_grad_tf, F->d_err, F->nsm, st));
+    const float4 *dL = reinterpret_cast<const float4 *>(d_dL_drgba);
+    OCR_CUDA(shell_bwd_values(F->d_geo, F->N, F->shell, Fd, P.cam, F->integ, dL, P.d_ray_off,
+                              P.d_keys, F->d_skpos, P.nhits, P.cap, F->d_srta, F->d_srg,
+                              F->d_err, F->nsm, st));
+    OCR_CUDA(shell_bwd_segments(F->d_geo, F->N, F->shell, Fd, P.cam, F->integ, dL, F->d_slm,
+                                F->d_srta, F->d_srg, P.nhits, d_grad_nodal, d_grad_tf, F->nsm,
+                                st));
     long long *h = F->h_group_slots;
     OCR_CUDA(cudaMemcpyAsync(h, F->d_err, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     OCR_CUDA(cudaMemcpyAsync(h + 1, F->d_stats + kStatErrors, sizeof(unsigned long long),

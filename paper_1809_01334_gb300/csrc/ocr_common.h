@@ -142,14 +142,18 @@ cudaError_t bwd_rays(const Topo &T, const Field &Fd, const Cam &C, const Integ &
 // Cubed-sphere shell (ocr_shell.cu)
 cudaError_t shell_cull(const int4 *geo, int N, const Shell &S, const Cam &C, int4 *rect,
                        unsigned char *visible, unsigned long long *stats, cudaStream_t st);
-// count pass (fill = false): segments per ray into counts, and, when stats is
-// given, the longest list into stats[kStatMaxHits]; fill pass: the keys, at
-// most key_cap of them (a list that would pass key_cap is a device error)
-cudaError_t shell_pairs(bool fill, const int4 *geo, int N, const Shell &S, const Cam &C,
+// mode 0, the count pass: segments per ray into counts, and, when stats is
+// given, the longest list into stats[kStatMaxHits]; mode 1, the fill pass: the
+// keys, at most key_cap of them (a list that would pass key_cap is a device
+// error); mode 2: the fill pass that also appends every segment to the
+// leaf-grouped list lm (pixel, 2 leaf + piece) through the counter *lm_count
+// (zeroed by the caller) and stores its index there in kpos beside the key
+cudaError_t shell_pairs(int mode, const int4 *geo, int N, const Shell &S, const Cam &C,
                         const int4 *rect, const long long *leaf_off, const int *chunk_leaf,
                         long long npairs, int *counts, const long long *ray_off, int *cursor,
                         unsigned long long *keys, long long key_cap, unsigned long long *stats,
-                        cudaStream_t st);
+                        cudaStream_t st, unsigned *kpos = nullptr, int2 *lm = nullptr,
+                        unsigned long long *lm_count = nullptr);
 // per-CTA warps and dynamic shared memory of shell_rays for rays of up to cap
 // segments (cap a power of two, 32..kShellMaxCap); shell_rays_prepare raises the
 // kernel's shared-memory limit to the largest of these and must run before the
@@ -164,15 +168,24 @@ cudaError_t shell_rays(const int4 *geo, int N, const Shell &S, const Field &Fd, 
                        int *counts, unsigned long long *stats, int nsm, int want_warps,
                        cudaStream_t st);
 
-// Adjoint of a shell render (ocr_backward.cu), over lists built by shell_pairs:
-// one warp per ray, kBwdWarps warps per CTA; shell_bwd_prepare raises the
-// kernel's shared-memory limit for every list capacity
+// Adjoint of a shell render (ocr_backward.cu), over lists built by shell_pairs
+// in mode 2.  shell_bwd_values: one warp per ray (warps per CTA from the list
+// capacity cap) stores per segment, at its index in the leaf-grouped list, the
+// transmittance of the nearer segments and its own (rec_ta) and the aggregate
+// of the farther ones (rec_g); shell_bwd_segments: one thread per segment of
+// the leaf-grouped list, its adjoint, the 27 nodal adjoints summed over the
+// warp's lanes of the same leaf before the atomics.  shell_bwd_prepare raises
+// the first kernel's shared-memory limit for every list capacity.
 size_t shell_bwd_smem(int cap);
 cudaError_t shell_bwd_prepare();
-cudaError_t shell_bwd_rays(const int4 *geo, int N, const Shell &S, const Field &Fd, const Cam &C,
-                           const Integ &I, const float4 *dL, const long long *ray_off,
-                           const unsigned long long *keys, long long key_cap, int cap,
-                           float *g_nodal, float *g_tf, unsigned long long *err, int nsm,
-                           cudaStream_t st);
+cudaError_t shell_bwd_values(const int4 *geo, int N, const Shell &S, const Field &Fd,
+                             const Cam &C, const Integ &I, const float4 *dL,
+                             const long long *ray_off, const unsigned long long *keys,
+                             const unsigned *kpos, long long key_cap, int cap, float2 *rec_ta,
+                             float4 *rec_g, unsigned long long *err, int nsm, cudaStream_t st);
+cudaError_t shell_bwd_segments(const int4 *geo, int N, const Shell &S, const Field &Fd,
+                               const Cam &C, const Integ &I, const float4 *dL, const int2 *lm,
+                               const float2 *rec_ta, const float4 *rec_g, long long nseg,
+                               float *g_nodal, float *g_tf, int nsm, cudaStream_t st);
 
 }  // namespace ocr

@@ -94,44 +94,87 @@ __global__ void __launch_bounds__(256)
 }
 
 // ------------------------------------------------------- segment lists --
-template <bool FILL>
+// MODE 0 counts segments per ray; MODE 1 writes the keys; MODE 2 also appends
+// every segment to a list grouped by leaf (one global append per CTA, whose
+// pairs are consecutive in leaf order): lm[pos] = (pixel, 2 leaf + piece), and
+// kpos[at] = pos beside the key, for the adjoint.
+template <int MODE>
 __global__ void __launch_bounds__(kPairChunk)
     shell_pairs_kernel(const int4 *__restrict__ geo, int N, Shell S, Cam c,
                        const int4 *__restrict__ rect, const long long *__restrict__ leaf_off,
                        const int *__restrict__ chunk_leaf, long long npairs, int *counts,
                        const long long *__restrict__ ray_off, int *cursor,
-                       unsigned long long *keys, long long key_cap, unsigned long long *stats) {
+                       unsigned long long *keys, long long key_cap, unsigned long long *stats,
+                       unsigned *kpos, int2 *lm, unsigned long long *lm_count) {
   const long long p = (long long)blockIdx.x * kPairChunk + threadIdx.x;
-  if (p >= npairs) return;
-  const long long nch = (npairs + kPairChunk - 1) / kPairChunk;
-  int lo = chunk_leaf[blockIdx.x];
-  int hi = (blockIdx.x + 1 < nch) ? chunk_leaf[blockIdx.x + 1] + 1 : N;
-  while (lo + 1 < hi) {  // the last leaf whose offset is <= p
-    const int mid = (lo + hi) >> 1;
-    if (leaf_off[mid] <= p) lo = mid; else hi = mid;
-  }
-  const int leaf = lo;
-  const int4 r = rect[leaf];
-  const long long local = p - leaf_off[leaf];
-  const int rw = r.y - r.x + 1;
-  const int i = r.x + (int)(local % rw), j = r.z + (int)(local / rw);
-  const long long pix = (long long)j * c.w + i;
-  float3 org, dir;
-  pixel_ray(c, i, j, org, dir);
+  if (MODE != 2 && p >= npairs) return;
+  int n = 0, leaf = 0;
+  long long pix = 0;
   float ai[2], ao[2];
-  const int n = shell_ray_leaf(leaf_shell(S, __ldg(geo + leaf)), org, dir, c.amin, c.amax, ai, ao);
+  if (p < npairs) {
+    const long long nch = (npairs + kPairChunk - 1) / kPairChunk;
+    int lo = chunk_leaf[blockIdx.x];
+    int hi = (blockIdx.x + 1 < nch) ? chunk_leaf[blockIdx.x + 1] + 1 : N;
+    while (lo + 1 < hi) {  // the last leaf whose offset is <= p
+      const int mid = (lo + hi) >> 1;
+      if (leaf_off[mid] <= p) lo = mid; else hi = mid;
+    }
+    leaf = lo;
+    const int4 r = rect[leaf];
+    const long long local = p - leaf_off[leaf];
+    const int rw = r.y - r.x + 1;
+    const int i = r.x + (int)(local % rw), j = r.z + (int)(local / rw);
+    pix = (long long)j * c.w + i;
+    float3 org, dir;
+    pixel_ray(c, i, j, org, dir);
+    n = shell_ray_leaf(leaf_shell(S, __ldg(geo + leaf)), org, dir, c.amin, c.amax, ai, ao);
+  }
+  unsigned pos = 0;
+  if (MODE == 2) {  // this pair's place in the CTA's block of the leaf-grouped list
+    __shared__ unsigned s_w[kPairChunk / 32], s_base;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned x = (unsigned)n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[wid] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned tot = 0;
+      for (int w = 0; w < kPairChunk / 32; ++w) {
+        const unsigned t = s_w[w];
+        s_w[w] = tot;
+        tot += t;
+      }
+      s_base = tot ? (unsigned)atomicAdd(lm_count, (unsigned long long)tot) : 0u;
+    }
+    __syncthreads();
+    pos = s_base + s_w[wid] + x - (unsigned)n;
+  }
   if (!n) return;
-  if (!FILL) {
+  if (MODE == 0) {
     atomicAdd(counts + pix, n);
   } else {
     const long long at = ray_off[pix] + atomicAdd(cursor + pix, n);
-    if (at + n > key_cap || at + n > ray_off[pix + 1]) {  // more than counted and planned
+    const bool bad = at + n > key_cap || at + n > ray_off[pix + 1] ||
+                     (MODE == 2 && (long long)pos + n > key_cap);
+    if (bad) {  // more than counted and planned
       atomicAdd(stats + kStatErrors, 1ull);
+      if (MODE == 2)
+        for (int t = 0; t < n; ++t)
+          if ((long long)pos + t < key_cap) lm[pos + t] = make_int2(-1, -1);
       return;
     }
-    for (int t = 0; t < n; ++t)  // alpha_in >= 0: its bits sort like the value
+    for (int t = 0; t < n; ++t) {  // alpha_in >= 0: its bits sort like the value
       keys[at + t] = (unsigned long long)__float_as_uint(ai[t]) << 32 |
                      (unsigned)(2 * leaf + t);
+      if (MODE == 2) {
+        kpos[at + t] = pos + (unsigned)t;
+        lm[pos + t] = make_int2((int)pix, 2 * leaf + t);
+      }
+    }
   }
 }
 
@@ -235,68 +278,8 @@ __global__ void __launch_bounds__(256, 2)
     float3 org, dir;
     pixel_ray(c, i, j, org, dir);
     const float rl = sqrtf(fmaf(dir.x, dir.x, fmaf(dir.y, dir.y, dir.z * dir.z)));
-    if (I.method == 1) {
-      // Dormand-Prince inside Algorithm 1: every lane advances its segment one
-      // step at a time and takes the ray's next segment as soon as it is done,
-      // so the lanes stay busy while some of them bisect
-      int next = 0, k = 0, depth = 0;
-      unsigned idx = 0;
-      bool busy = false;
-      ShellSeg g;
-      float dx = 0.f;
-      float2 ivk = make_float2(0.f, 0.f);
-      float4 kq0 = seg_identity(), sacc = seg_identity();
-      for (;;) {
-        const unsigned idle = __ballot_sync(0xffffffffu, !busy);
-        const int kk = next + __popc(idle & ((1u << lane) - 1u));
-        next += __popc(idle);
-        if (!busy && kk < n) {
-          k = kk;
-          const unsigned lp = (unsigned)(key[k] & 0xffffffffu);
-          const int leaf = (int)(lp >> 1), piece = (int)(lp & 1u);
-          // an entry the fill pass did not write, or a piece the ray does not have
-          if (leaf >= N || !shell_segment(S, Fd.nodal, c, __ldg(geo + leaf), leaf, piece, org,
-                                          dir, rl, g, dx, ivk)) {
-            ++errs;
-            val[k] = seg_identity();
-            iv[k] = make_float2(0.f, 0.f);
-          } else {
-            busy = true;
-            depth = 0;
-            idx = 0;
-            sacc = seg_identity();
-            kq0 = medium(g, tf, 0.f);
-          }
-        }
-        if (!__any_sync(0xffffffffu, busy)) {
-          if (next >= n) break;
-          continue;
-        }
-        if (busy && dopri_advance(g, tf, dx, I, depth, idx, kq0, sacc, steps)) {
-          val[k] = sacc;
-          iv[k] = ivk;
-          busy = false;
-        }
-      }
-    } else {
-      for (int k = lane; k < n; k += 32) {
-        const unsigned lp = (unsigned)(key[k] & 0xffffffffu);
-        const int leaf = (int)(lp >> 1), piece = (int)(lp & 1u);
-        ShellSeg g;
-        float dx;
-        float2 ivk;
-        // an entry the fill pass did not write, or a piece the ray does not have
-        if (leaf >= N || !shell_segment(S, Fd.nodal, c, __ldg(geo + leaf), leaf, piece, org, dir,
-                                        rl, g, dx, ivk)) {
-          ++errs;
-          val[k] = seg_identity();
-          iv[k] = make_float2(0.f, 0.f);
-          continue;
-        }
-        val[k] = integrate_segment(g, tf, dx, I, steps);
-        iv[k] = ivk;
-      }
-    }
+    errs += shell_ray_values(geo, N, S, Fd.nodal, c, I, tf, key, n, org, dir, rl, val, iv,
+                             lane, steps);
     segs += n;
     __syncwarp();
     // overlaps of consecutive segments are rounding slivers, if any
@@ -357,24 +340,30 @@ cudaError_t shell_cull(const int4 *geo, int N, const Shell &S, const Cam &C, int
   return cudaGetLastError();
 }
 
-cudaError_t shell_pairs(bool fill, const int4 *geo, int N, const Shell &S, const Cam &C,
+cudaError_t shell_pairs(int mode, const int4 *geo, int N, const Shell &S, const Cam &C,
                         const int4 *rect, const long long *leaf_off, const int *chunk_leaf,
                         long long npairs, int *counts, const long long *ray_off, int *cursor,
                         unsigned long long *keys, long long key_cap, unsigned long long *stats,
-                        cudaStream_t st) {
+                        cudaStream_t st, unsigned *kpos, int2 *lm, unsigned long long *lm_count) {
+  if (mode < 0 || mode > 2 || (mode == 2 && (!kpos || !lm || !lm_count)))
+    return cudaErrorInvalidValue;
   if (npairs > 0) {
     const long long nblk = (npairs + kPairChunk - 1) / kPairChunk;
     if (nblk > 0x7fffffffll) return cudaErrorInvalidValue;
-    if (fill)
-      shell_pairs_kernel<true><<<(unsigned)nblk, kPairChunk, 0, st>>>(
+    if (mode == 0)
+      shell_pairs_kernel<0><<<(unsigned)nblk, kPairChunk, 0, st>>>(
           geo, N, S, C, rect, leaf_off, chunk_leaf, npairs, counts, ray_off, cursor, keys,
-          key_cap, stats);
+          key_cap, stats, kpos, lm, lm_count);
+    else if (mode == 1)
+      shell_pairs_kernel<1><<<(unsigned)nblk, kPairChunk, 0, st>>>(
+          geo, N, S, C, rect, leaf_off, chunk_leaf, npairs, counts, ray_off, cursor, keys,
+          key_cap, stats, kpos, lm, lm_count);
     else
-      shell_pairs_kernel<false><<<(unsigned)nblk, kPairChunk, 0, st>>>(
+      shell_pairs_kernel<2><<<(unsigned)nblk, kPairChunk, 0, st>>>(
           geo, N, S, C, rect, leaf_off, chunk_leaf, npairs, counts, ray_off, cursor, keys,
-          key_cap, stats);
+          key_cap, stats, kpos, lm, lm_count);
   }
-  if (!fill && stats) {  // the longest list, for planning
+  if (mode == 0 && stats) {  // the longest list, for planning
     const long long npix = (long long)C.w * C.h;
     const long long g = (npix + 255) / 256;
     max_count_kernel<<<(unsigned)(g > 4096 ? 4096 : (g > 0 ? g : 1)), 256, 0, st>>>(counts, npix,

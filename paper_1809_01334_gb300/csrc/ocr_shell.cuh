@@ -1,6 +1,7 @@
 // Device helpers of the cubed-sphere shell shared by the render
 // (ocr_shell.cu) and the adjoint (ocr_backward.cu): a leaf's geometry from the
-// shared tables, the ray / leaf intersection, and the field along a segment.
+// shared tables, the ray / leaf intersection, the field along a segment, and
+// the values of a ray's sorted segments.
 #pragma once
 #include "ocr_common.h"
 #include "ocr_device.cuh"
@@ -181,6 +182,80 @@ __device__ __forceinline__ bool shell_segment(const Shell &S, const float *__res
   dx = (a_out - a_in) * rl;
   iv = make_float2(a_in, a_out);
   return true;
+}
+
+// The values of the n segments of one ray, one warp: key[0..n) the ray's
+// sorted list, val[k] the k-th segment (A, B) and, when iv is given, its
+// interval (iv may alias key: entry k is read before it is written).  With
+// Dormand-Prince inside Algorithm 1 every lane advances its segment one step at
+// a time and takes the ray's next segment as soon as it is done, so the lanes
+// stay busy while some of them bisect.  Returns this lane's count of entries
+// that are not a segment of the ray (unwritten entries, missing pieces).
+__device__ __forceinline__ int shell_ray_values(const int4 *__restrict__ geo, int N,
+                                                const Shell &S, const float *__restrict__ nodal,
+                                                const Cam &c, const Integ &I, const TF &tf,
+                                                const unsigned long long *key, int n,
+                                                float3 org, float3 dir, float rl, float4 *val,
+                                                float2 *iv, int lane, int &steps) {
+  int errs = 0;
+  if (I.method == 1) {
+    int next = 0, k = 0, depth = 0;
+    unsigned idx = 0;
+    bool busy = false;
+    ShellSeg g;
+    float dx = 0.f;
+    float2 ivk = make_float2(0.f, 0.f);
+    float4 kq0 = seg_identity(), sacc = seg_identity();
+    for (;;) {
+      const unsigned idle = __ballot_sync(0xffffffffu, !busy);
+      const int kk = next + __popc(idle & ((1u << lane) - 1u));
+      next += __popc(idle);
+      if (!busy && kk < n) {
+        k = kk;
+        const unsigned lp = (unsigned)(key[k] & 0xffffffffu);
+        const int leaf = (int)(lp >> 1), piece = (int)(lp & 1u);
+        if (leaf >= N || !shell_segment(S, nodal, c, __ldg(geo + leaf), leaf, piece, org, dir,
+                                        rl, g, dx, ivk)) {
+          ++errs;
+          val[k] = seg_identity();
+          if (iv) iv[k] = make_float2(0.f, 0.f);
+        } else {
+          busy = true;
+          depth = 0;
+          idx = 0;
+          sacc = seg_identity();
+          kq0 = medium(g, tf, 0.f);
+        }
+      }
+      if (!__any_sync(0xffffffffu, busy)) {
+        if (next >= n) break;
+        continue;
+      }
+      if (busy && dopri_advance(g, tf, dx, I, depth, idx, kq0, sacc, steps)) {
+        val[k] = sacc;
+        if (iv) iv[k] = ivk;
+        busy = false;
+      }
+    }
+  } else {
+    for (int k = lane; k < n; k += 32) {
+      const unsigned lp = (unsigned)(key[k] & 0xffffffffu);
+      const int leaf = (int)(lp >> 1), piece = (int)(lp & 1u);
+      ShellSeg g;
+      float dx;
+      float2 ivk;
+      if (leaf >= N ||
+          !shell_segment(S, nodal, c, __ldg(geo + leaf), leaf, piece, org, dir, rl, g, dx, ivk)) {
+        ++errs;
+        val[k] = seg_identity();
+        if (iv) iv[k] = make_float2(0.f, 0.f);
+        continue;
+      }
+      val[k] = integrate_segment(g, tf, dx, I, steps);
+      if (iv) iv[k] = ivk;
+    }
+  }
+  return errs;
 }
 
 }  // namespace
