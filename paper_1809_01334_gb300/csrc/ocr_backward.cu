@@ -2,22 +2,32 @@
 //
 // The gradient of a loss L(rgba) with respect to the nodal values and the
 // transfer-function knots, given dL/d(rgba).  Segments are recomputed, not
-// stored by the forward pass:
-//   pair_hits<false> - over the (visible leaf, pixel) pairs of the leaves'
+// stored by the forward pass.  Cube forests:
+//   pair_hits<0>     - over the (visible leaf, pixel) pairs of the leaves'
 //                      rectangles in Morton order (a prefix sum of rectangle
 //                      areas splits them into equal CTA chunks): slab tests,
-//                      hits counted per ray;
+//                      hits counted per ray (rays without an image adjoint
+//                      are skipped);
 //   (scan)           - per-ray offsets of the hit lists;
-//   pair_hits<true>  - the same traversal, writing each hit's leaf and its
-//                      mirrored Morton key (the ray's front-to-back order);
-//   ray_backward     - one warp per ray: sort the hits by key, recompute every
-//                      segment, form the transmittance of the nearer segments
-//                      (prefix product) and the aggregate of the farther ones
-//                      with the background (suffix fold with Eq. 2.14) by warp
-//                      scans -- no group inverse -- and carry each segment's
-//                      adjoint back through the integrator (RK4, or the
-//                      Dormand-Prince steps of Algorithm 1 with the same step
-//                      tree), the transfer function and the trilinear weights.
+//   pair_hits<2>     - the same traversal, writing each hit's mirrored Morton
+//                      key (the ray's front-to-back order) to its ray's list,
+//                      and appending (pixel, leaf) to a list grouped by leaf
+//                      whose index goes beside the key;
+//   seg_values       - one thread per entry of the leaf-grouped list: the
+//                      segment's value (A, B);
+//   ray_scans        - one warp per ray: sort the keys, form the transmittance
+//                      of the nearer segments (prefix product) and the
+//                      aggregate of the farther ones with the background
+//                      (suffix fold with Eq. 2.14) by warp scans -- no group
+//                      inverse -- and store them per list entry;
+//   seg_adjoint      - one thread per entry: the segment's adjoint through the
+//                      integrator (RK4, or the Dormand-Prince steps of
+//                      Algorithm 1 with the same step tree), the transfer
+//                      function and the interpolation weights; the nodal
+//                      adjoints are summed over a warp's lanes of the same
+//                      leaf before the atomics.
+// Shell forests use the render's lists, built with the leaf-grouped list, and
+// the same three passes with the shell's geometry and field.
 #include "ocr_common.h"
 #include "ocr_device.cuh"
 #include "ocr_shell.cuh"
@@ -143,46 +153,81 @@ __global__ void pair_chunk_map_kernel(const long long *off, int N, int *chunk_le
 }
 
 // ----------------------------------------------------------- hit lists --
-template <bool FILL>
+// MODE 0 counts hits per ray; MODE 2 writes keys[at] and appends the hit to
+// the leaf-grouped list (one global append per CTA): lm[pos] = (pixel, leaf),
+// kpos[at] = pos.
+template <int MODE>
 __global__ void __launch_bounds__(kPairThreads)
     pair_hits_kernel(Topo T, Cam c, const int4 *rect, const long long *leaf_off,
                      const int *chunk_leaf, long long npairs, const float4 *dL, int *counts,
                      const long long *ray_off, int *cursor, const unsigned long long *mkey,
-                     unsigned long long fx, unsigned long long *keys, int *hleaf) {
+                     unsigned long long fx, unsigned long long *keys, unsigned *kpos, int2 *lm,
+                     unsigned long long *lm_count, long long key_cap, unsigned long long *err) {
   const long long p = (long long)blockIdx.x * kPairThreads + threadIdx.x;
-  if (p >= npairs) return;
-  const long long nch = (npairs + kPairThreads - 1) / kPairThreads;
-  int lo = chunk_leaf[blockIdx.x];
-  int hi = (blockIdx.x + 1 < nch) ? chunk_leaf[blockIdx.x + 1] + 1 : T.N;
-  while (lo + 1 < hi) {  // last leaf whose offset is <= p
-    const int mid = (lo + hi) >> 1;
-    if (leaf_off[mid] <= p) lo = mid; else hi = mid;
+  if (MODE == 0 && p >= npairs) return;
+  bool hit = false;
+  int leaf = 0;
+  long long pix = 0;
+  float3 dir = make_float3(0.f, 0.f, 0.f);
+  if (p < npairs) {
+    const long long nch = (npairs + kPairThreads - 1) / kPairThreads;
+    int lo = chunk_leaf[blockIdx.x];
+    int hi = (blockIdx.x + 1 < nch) ? chunk_leaf[blockIdx.x + 1] + 1 : T.N;
+    while (lo + 1 < hi) {  // last leaf whose offset is <= p
+      const int mid = (lo + hi) >> 1;
+      if (leaf_off[mid] <= p) lo = mid; else hi = mid;
+    }
+    leaf = lo;
+    const int4 r = rect[leaf];
+    const long long local = p - leaf_off[leaf];
+    const int rw = r.y - r.x + 1;
+    const int i = r.x + (int)(local % rw), j = r.z + (int)(local / rw);
+    pix = (long long)j * c.w + i;
+    const float4 g = dL[pix];
+    if (g.x != 0.f || g.y != 0.f || g.z != 0.f || g.w != 0.f) {  // else no gradient on this ray
+      float3 org;
+      pixel_ray(c, i, j, org, dir);
+      const float3 inv =
+          make_float3(recip_or_zero(dir.x), recip_or_zero(dir.y), recip_or_zero(dir.z));
+      const int4 gl = T.geo[leaf];
+      float a0, a1;
+      hit = slab(org, dir, inv, node_lo(gl, ldexpf(1.f, -T.L)), ldexpf(1.f, -gl.w), c.amin,
+                 c.amax, a0, a1);
+    }
   }
-  const int leaf = lo;
-  const int4 r = rect[leaf];
-  const long long local = p - leaf_off[leaf];
-  const int rw = r.y - r.x + 1;
-  const int i = r.x + (int)(local % rw), j = r.z + (int)(local / rw);
-  const long long pix = (long long)j * c.w + i;
-  const float4 g = dL[pix];
-  if (g.x == 0.f && g.y == 0.f && g.z == 0.f && g.w == 0.f) return;  // no gradient on this ray
-  float3 org, dir;
-  pixel_ray(c, i, j, org, dir);
-  const float3 inv = make_float3(recip_or_zero(dir.x), recip_or_zero(dir.y), recip_or_zero(dir.z));
-  const int4 gl = T.geo[leaf];
-  float a0, a1;
-  if (!slab(org, dir, inv, node_lo(gl, ldexpf(1.f, -T.L)), ldexpf(1.f, -gl.w), c.amin, c.amax, a0,
-            a1))
+  if (MODE == 0) {
+    if (hit) atomicAdd(counts + pix, 1);
     return;
-  if (!FILL) {
-    atomicAdd(counts + pix, 1);
-  } else {
-    const long long at = ray_off[pix] + atomicAdd(cursor + pix, 1);
-    const unsigned long long flip =
-        (dir.x < 0.f ? fx : 0ull) | (dir.y < 0.f ? fx << 1 : 0ull) | (dir.z < 0.f ? fx << 2 : 0ull);
-    keys[at] = mkey[leaf] ^ flip;
-    hleaf[at] = leaf;
   }
+  // this hit's place in the CTA's block of the leaf-grouped list
+  __shared__ unsigned s_w[kPairThreads / 32], s_base;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned bal = __ballot_sync(0xffffffffu, hit);
+  if (lane == 0) s_w[wid] = __popc(bal);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned tot = 0;
+    for (int w = 0; w < kPairThreads / 32; ++w) {
+      const unsigned t = s_w[w];
+      s_w[w] = tot;
+      tot += t;
+    }
+    s_base = tot ? (unsigned)atomicAdd(lm_count, (unsigned long long)tot) : 0u;
+  }
+  __syncthreads();
+  if (!hit) return;
+  const unsigned pos = s_base + s_w[wid] + __popc(bal & ((1u << lane) - 1u));
+  const long long at = ray_off[pix] + atomicAdd(cursor + pix, 1);
+  if (at >= key_cap || at >= ray_off[pix + 1] || (long long)pos >= key_cap) {
+    atomicAdd(err, 1ull);  // more hits than counted
+    if ((long long)pos < key_cap) lm[pos] = make_int2(-1, -1);
+    return;
+  }
+  const unsigned long long flip =
+      (dir.x < 0.f ? fx : 0ull) | (dir.y < 0.f ? fx << 1 : 0ull) | (dir.z < 0.f ? fx << 2 : 0ull);
+  keys[at] = mkey[leaf] ^ flip;
+  kpos[at] = pos;
+  lm[pos] = make_int2((int)pix, leaf);
 }
 
 // -------------------------------------------------------- segment adjoint --
@@ -231,6 +276,7 @@ __device__ __forceinline__ float tf_bwd(const TF &tf, float s, float4 vbar, TfGr
 // Segment through a cube leaf: the field is the cubic in tau; the adjoint of
 // the 8 corner values goes through the trilinear weights.
 struct SegAdj {
+  static constexpr int kUnroll = 6;
   Cubic cu;
   float3 uf, du;    // reference coordinates at the far end, change to the near end
   float g8[8];      // adjoint of the 8 nodal values
@@ -259,6 +305,7 @@ struct SegAdj {
 // degree-2 interpolation; the adjoint of the 27 nodal values is kept in this
 // thread's column of a shared-memory array (g27[q * stride]).
 struct ShellAdj {
+  static constexpr int kUnroll = 1;
   ShellSeg g;
   float *g27;
   int stride;
@@ -357,9 +404,9 @@ __device__ void dopri_step_bwd(SA &S, const TF &tf, float t0, float dtau, float 
   float4 Kb[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) Kb[i] = scale4(H * b[i], ybar);
-  // one copy of the node adjoint in the code (it inlines the field and its
-  // weights): the stages are walked by a loop
-#pragma unroll 1
+  // a shell node adjoint inlines the field and its 27 weights: one copy of it
+  // in the code, the stages walked by a loop (SA::kUnroll = 1)
+#pragma unroll SA::kUnroll
   for (int i = 5; i >= 0; --i) {
     S.bwd(tf, tt[i], node_vbar(Kb[i], Y[i]), tg);
     const float4 Yb = scale4(-kq[i].x, Kb[i]);
@@ -465,11 +512,11 @@ __device__ void segment_steps_bwd(SA &S, const TF &tf, float dx, const Integ &I,
 }
 
 // Adjoint of one segment of a cube leaf: near transmittance T, far aggregate
-// G, its value A_seg.
+// G, its value A_seg; the adjoints of the leaf's 8 nodal values into g8.
 __device__ void segment_bwd(const Topo &T, const Field &Fd, const Cam &c, const Integ &I,
                             const TF &tf, int leaf, float3 org, float3 dir, float3 inv,
                             float scale, float Tn, float4 G, float Aseg, float4 Ib, float ab,
-                            float *g_nodal, TfGrad &tg) {
+                            float *g8, TfGrad &tg) {
   const int4 g = __ldg(T.geo + leaf);
   const float ih = ldexpf(1.f, g.w);
   const float3 lo = node_lo(g, scale);
@@ -488,8 +535,7 @@ __device__ void segment_bwd(const Topo &T, const Field &Fd, const Cam &c, const 
   for (int q = 0; q < 8; ++q) S.g8[q] = 0.f;
   segment_steps_bwd(S, tf, dx, I, Tn, G, Aseg, Ib, ab, tg);
 #pragma unroll
-  for (int q = 0; q < 8; ++q)
-    if (S.g8[q] != 0.f) atomicAdd(g_nodal + 8 * (size_t)leaf + q, S.g8[q]);
+  for (int q = 0; q < 8; ++q) g8[q] = S.g8[q];
 }
 
 // ------------------------------------------------------------ ray adjoint --
@@ -575,114 +621,102 @@ __device__ void warp_sort(unsigned long long *key, int *lf, int P, int lane) {
     }
 }
 
-constexpr int kBwdWarps = 4;
-
-__global__ void __launch_bounds__(kBwdWarps * 32, 4)
-    ray_backward_kernel(Topo T, Field Fd, Cam c, Integ I, const float4 *dL,
-                        const long long *ray_off, const unsigned long long *keys,
-                        const int *hleaf, float *g_nodal, float *g_tf, unsigned long long *err,
-                        int cap) {
-  extern __shared__ unsigned char s_raw[];
-  // per warp: keys (later T and A_seg), leaves, segment values (later far aggregates)
-  unsigned long long *s_key = reinterpret_cast<unsigned long long *>(s_raw);
-  float4 *s_val = reinterpret_cast<float4 *>(s_key + kBwdWarps * cap);
-  int *s_leaf = reinterpret_cast<int *>(s_val + kBwdWarps * cap);
-  __shared__ float4 s_tfv[8], s_tfs[8];
-  __shared__ float s_g[32];
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+// The transfer-function table of a CTA in shared memory.
+__device__ __forceinline__ void load_tf(const Field &Fd, float4 *s_tfv, float4 *s_tfs) {
+  const int tid = threadIdx.x;
   if (tid < 8) {
     const float4 v = Fd.tf[tid];
     const float4 w = Fd.tf[tid < 7 ? tid + 1 : 7];
     s_tfv[tid] = v;
     s_tfs[tid] = make_float4(w.x - v.x, w.y - v.y, w.z - v.z, w.w - v.w);
   }
-  if (tid < 32) s_g[tid] = 0.f;
-  __syncthreads();
-  unsigned long long *key = s_key + wid * cap;
-  int *lf = s_leaf + wid * cap;
-  float4 *val = s_val + wid * cap;
-  float *Tk = reinterpret_cast<float *>(key);           // reuses the key array after sorting
-  float *Ak = reinterpret_cast<float *>(key) + cap;
-  TF tf{s_tfv, s_tfs, Fd.s_min, Fd.inv_ds7};
-  TfGrad tg;
-  tg.s_g = s_g;
-  const float scale = ldexpf(1.f, -T.L);
-  const long long npix = (long long)c.w * c.h;
-  const long long nwarp = (long long)gridDim.x * kBwdWarps;
-  for (long long pix = (long long)blockIdx.x * kBwdWarps + wid; pix < npix; pix += nwarp) {
-    const long long h0 = ray_off[pix];
-    const int n = (int)(ray_off[pix + 1] - h0);
-    if (n == 0) continue;
-    if (n > cap) {
-      if (lane == 0) atomicAdd(err, 1ull);
-      continue;
-    }
-    int P = 32;
-    while (P < n) P <<= 1;
-    for (int k = lane; k < P; k += 32) {
-      key[k] = k < n ? keys[h0 + k] : ~0ull;
-      lf[k] = k < n ? hleaf[h0 + k] : -1;
-    }
-    __syncwarp();
-    warp_sort(key, lf, P, lane);  // (key, leaf) by key: nearest first
-    const int i = (int)(pix % c.w), j = (int)(pix / c.w);
-    float3 org, dir;
-    pixel_ray(c, i, j, org, dir);
-    const float3 inv =
-        make_float3(recip_or_zero(dir.x), recip_or_zero(dir.y), recip_or_zero(dir.z));
-    // segment values
-    int steps = 0;
-    for (int k = lane; k < n; k += 32)
-      val[k] = leaf_segment(T, Fd, c, I, tf, lf[k], org, dir, inv, scale, steps);
-    __syncwarp();
-    near_far_scans(n, lane, val, Tk, Ak);
-    // adjoint of every segment
-    const float4 gp = dL[pix];
-    const float4 Ib = make_float4(gp.x, gp.y, gp.z, 0.f);
-    for (int k = lane; k < n; k += 32)
-      segment_bwd(T, Fd, c, I, tf, lf[k], org, dir, inv, scale, Tk[k], val[k], Ak[k], Ib, gp.w,
-                  g_nodal, tg);
-    __syncwarp();
-  }
-  tg.flush();
-  __syncthreads();
-  if (tid < 32 && s_g[tid] != 0.f) atomicAdd(g_tf + tid, s_g[tid]);
 }
 
-// The same for a shell forest, in two passes over lists that hold
-// (alpha_in, leaf, piece) keys.  Overlap resolution (cut and average of
-// rounding slivers) is treated as plain combination here.
-//
-// Pass 1, one warp per ray: sort the ray's keys (carrying each segment's index
-// in the leaf-grouped list), integrate every segment, and store per segment,
-// at that index, the transmittance of the nearer segments and its own
-// (rec_ta) and the aggregate of the farther ones (rec_g).  Rays whose image
-// adjoint is zero are skipped (pass 2 skips their segments too).
-__global__ void __launch_bounds__(256)
-    shell_bwd_values_kernel(const int4 *__restrict__ geo, int N, Shell S, Field Fd, Cam c,
-                            Integ I, const float4 *dL, const long long *ray_off,
-                            const unsigned long long *keys, const unsigned *kpos,
-                            long long key_cap, int cap, float2 *rec_ta, float4 *rec_g,
-                            unsigned long long *err) {
-  extern __shared__ __align__(16) unsigned char s_raw[];
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-  float4 *s_val = reinterpret_cast<float4 *>(s_raw);
-  unsigned long long *s_key = reinterpret_cast<unsigned long long *>(s_val + nw * cap);
-  int *s_pos = reinterpret_cast<int *>(s_key + nw * cap);
+__device__ __forceinline__ bool nonzero4(float4 g) {
+  return g.x != 0.f || g.y != 0.f || g.z != 0.f || g.w != 0.f;
+}
+
+constexpr int kSegThreads = 128;
+constexpr int kSegStride = kSegThreads + 1;  // row stride: lanes summing rows hit distinct banks
+
+// Pass 1, one thread per entry e of the leaf-grouped list (pixel, leaf): the
+// segment's value (A, B) into val[e].  Cube leaves.
+__global__ void __launch_bounds__(kSegThreads)
+    cube_seg_values_kernel(Topo T, Field Fd, Cam c, Integ I, const int2 *lm, long long nseg,
+                           float4 *val) {
   __shared__ float4 s_tfv[8], s_tfs[8];
-  if (tid < 8) {
-    const float4 v = Fd.tf[tid];
-    const float4 w = Fd.tf[tid < 7 ? tid + 1 : 7];
-    s_tfv[tid] = v;
-    s_tfs[tid] = make_float4(w.x - v.x, w.y - v.y, w.z - v.z, w.w - v.w);
-  }
+  load_tf(Fd, s_tfv, s_tfs);
   __syncthreads();
-  float4 *val = s_val + wid * cap;
-  unsigned long long *key = s_key + wid * cap;
-  int *pos = s_pos + wid * cap;
+  const TF tf{s_tfv, s_tfs, Fd.s_min, Fd.inv_ds7};
+  const float scale = ldexpf(1.f, -T.L);
+  const long long npix = (long long)c.w * c.h;
+  int steps = 0;
+  for (long long e = (long long)blockIdx.x * kSegThreads + threadIdx.x; e < nseg;
+       e += (long long)gridDim.x * kSegThreads) {
+    const int2 m = lm[e];
+    if (m.x < 0 || (long long)m.x >= npix || m.y < 0 || m.y >= T.N) continue;
+    float3 org, dir;
+    pixel_ray(c, m.x % c.w, m.x / c.w, org, dir);
+    const float3 inv =
+        make_float3(recip_or_zero(dir.x), recip_or_zero(dir.y), recip_or_zero(dir.z));
+    val[e] = leaf_segment(T, Fd, c, I, tf, m.y, org, dir, inv, scale, steps);
+  }
+}
+
+// The same for shell leaves: entries (pixel, 2 leaf + piece); rays without an
+// image adjoint are skipped.  A piece the ray does not have is counted in err.
+__global__ void __launch_bounds__(kSegThreads)
+    shell_seg_values_kernel(const int4 *__restrict__ geo, int N, Shell S, Field Fd, Cam c,
+                            Integ I, const float4 *dL, const int2 *lm, long long nseg,
+                            float4 *val, unsigned long long *err) {
+  __shared__ float4 s_tfv[8], s_tfs[8];
+  load_tf(Fd, s_tfv, s_tfs);
+  __syncthreads();
+  const TF tf{s_tfv, s_tfs, Fd.s_min, Fd.inv_ds7};
+  const long long npix = (long long)c.w * c.h;
+  int steps = 0, bad = 0;
+  for (long long e = (long long)blockIdx.x * kSegThreads + threadIdx.x; e < nseg;
+       e += (long long)gridDim.x * kSegThreads) {
+    const int2 m = lm[e];
+    const int lf = m.y >> 1, piece = m.y & 1;
+    if (m.x < 0 || (long long)m.x >= npix || m.y < 0 || lf >= N) continue;
+    if (!nonzero4(dL[m.x])) continue;
+    float3 org, dir;
+    pixel_ray(c, m.x % c.w, m.x / c.w, org, dir);
+    const float rl = sqrtf(fmaf(dir.x, dir.x, fmaf(dir.y, dir.y, dir.z * dir.z)));
+    ShellSeg g;
+    float dx;
+    float2 iv;
+    if (!shell_segment(S, Fd.nodal, c, __ldg(geo + lf), lf, piece, org, dir, rl, g, dx, iv)) {
+      ++bad;
+      val[e] = seg_identity();
+      continue;
+    }
+    val[e] = integrate_segment(g, tf, dx, I, steps);
+  }
+  if (bad) atomicAdd(err, (unsigned long long)bad);
+}
+
+// Pass 2, one warp per ray: sort the ray's keys (nearest first), carrying each
+// segment's index in the leaf-grouped list; gather the segment values there
+// (from rec_g), and store there the transmittance of the nearer segments and
+// the segment's own (rec_ta) and the aggregate of the farther ones (rec_g).
+// Rays without an image adjoint are skipped.  Geometry-free.
+__global__ void __launch_bounds__(256)
+    ray_scans_kernel(Cam c, const float4 *dL, const long long *ray_off,
+                     const unsigned long long *keys, const unsigned *kpos, long long key_cap,
+                     int cap, float2 *rec_ta, float4 *rec_g, unsigned long long *err) {
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  float4 *val = reinterpret_cast<float4 *>(s_raw) + (size_t)wid * cap;
+  unsigned long long *key =
+      reinterpret_cast<unsigned long long *>(reinterpret_cast<float4 *>(s_raw) + (size_t)nw * cap) +
+      (size_t)wid * cap;
+  int *pos = reinterpret_cast<int *>(reinterpret_cast<unsigned long long *>(
+                 reinterpret_cast<float4 *>(s_raw) + (size_t)nw * cap) + (size_t)nw * cap) +
+             (size_t)wid * cap;
   float *Tk = reinterpret_cast<float *>(key);  // reuses the key array after sorting
   float *Ak = reinterpret_cast<float *>(key) + cap;
-  const TF tf{s_tfv, s_tfs, Fd.s_min, Fd.inv_ds7};
   const long long npix = (long long)c.w * c.h;
   const long long nwarp = (long long)gridDim.x * nw;
   int bad = 0;
@@ -694,8 +728,7 @@ __global__ void __launch_bounds__(256)
       if (lane == 0) ++bad;
       continue;
     }
-    const float4 gp = dL[pix];
-    if (gp.x == 0.f && gp.y == 0.f && gp.z == 0.f && gp.w == 0.f) continue;
+    if (!nonzero4(dL[pix])) continue;
     int P = 32;
     while (P < n) P <<= 1;
     for (int k = lane; k < P; k += 32) {
@@ -703,14 +736,11 @@ __global__ void __launch_bounds__(256)
       pos[k] = k < n ? (int)kpos[h0 + k] : -1;
     }
     __syncwarp();
-    warp_sort(key, pos, P, lane);  // nearest first, the list index along
-    const int i = (int)(pix % c.w), j = (int)(pix / c.w);
-    float3 org, dir;
-    pixel_ray(c, i, j, org, dir);
-    const float rl = sqrtf(fmaf(dir.x, dir.x, fmaf(dir.y, dir.y, dir.z * dir.z)));
-    int steps = 0;
-    bad += shell_ray_values(geo, N, S, Fd.nodal, c, I, tf, key, n, org, dir, rl, val, nullptr,
-                            lane, steps);
+    warp_sort(key, pos, P, lane);
+    for (int k = lane; k < n; k += 32) {
+      const unsigned q = (unsigned)pos[k];
+      val[k] = (long long)q < key_cap ? rec_g[q] : seg_identity();
+    }
     __syncwarp();
     near_far_scans(n, lane, val, Tk, Ak);
     for (int k = lane; k < n; k += 32) {
@@ -725,28 +755,88 @@ __global__ void __launch_bounds__(256)
   if (bad) atomicAdd(err, (unsigned long long)bad);
 }
 
-// Pass 2, one thread per segment of the leaf-grouped list: the ray, the
-// segment's field, its step adjoints with the near transmittance and far
-// aggregate of pass 1; the 27 nodal adjoints go to this thread's column of a
-// shared array and are summed over the warp's lanes of the same leaf (the list
-// keeps a leaf's segments together), one atomic per value and leaf.
-constexpr int kSegThreads = 128;
-constexpr int kSegStride = kSegThreads + 1;  // row stride: lanes summing rows hit distinct banks
+// Sums the NV nodal adjoints in the shared columns (row stride kSegStride) of
+// the warp's lanes over the lanes that hold the same leaf (leaf < 0: nothing),
+// one atomic per value and leaf.
+template <int NV>
+__device__ __forceinline__ void leaf_group_flush(const float *s_rows, int leaf, int lane, int wid,
+                                                 float *g_nodal) {
+  unsigned todo = __ballot_sync(0xffffffffu, leaf >= 0);
+  while (todo) {
+    const int lf = __shfl_sync(0xffffffffu, leaf, __ffs(todo) - 1);
+    const unsigned grp = __ballot_sync(0xffffffffu, leaf == lf);
+    todo &= ~grp;
+    if (lane < NV) {
+      const float *row = s_rows + lane * kSegStride + (wid << 5);
+      float sum = 0.f;
+      for (unsigned mm = grp; mm; mm &= mm - 1) sum += row[__ffs(mm) - 1];
+      if (sum != 0.f) atomicAdd(g_nodal + NV * (size_t)lf + lane, sum);
+    }
+  }
+}
 
+// Pass 3, one thread per entry of the leaf-grouped list: the segment's step
+// adjoints with the near transmittance and far aggregate of pass 2, through
+// the trilinear weights; the 8 nodal adjoints summed over the warp's lanes of
+// the same leaf (the list keeps a leaf's segments together).  Cube leaves.
+__global__ void __launch_bounds__(kSegThreads)
+    cube_seg_adjoint_kernel(Topo T, Field Fd, Cam c, Integ I, const float4 *dL, const int2 *lm,
+                            const float2 *rec_ta, const float4 *rec_g, long long nseg,
+                            float *g_nodal, float *g_tf) {
+  __shared__ float s_g8[8 * kSegStride];
+  __shared__ float4 s_tfv[8], s_tfs[8];
+  __shared__ float s_g[32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  load_tf(Fd, s_tfv, s_tfs);
+  if (tid < 32) s_g[tid] = 0.f;
+  __syncthreads();
+  const TF tf{s_tfv, s_tfs, Fd.s_min, Fd.inv_ds7};
+  TfGrad tg;
+  tg.s_g = s_g;
+  const float scale = ldexpf(1.f, -T.L);
+  const long long npix = (long long)c.w * c.h;
+  for (long long b = (long long)blockIdx.x * kSegThreads; b < nseg;
+       b += (long long)gridDim.x * kSegThreads) {
+    const long long e = b + tid;
+    int leaf = -1;
+    if (e < nseg) {
+      const int2 m = lm[e];
+      if (m.x >= 0 && (long long)m.x < npix && m.y >= 0 && m.y < T.N) {
+        const float4 gp = dL[m.x];
+        float3 org, dir;
+        pixel_ray(c, m.x % c.w, m.x / c.w, org, dir);
+        const float3 inv =
+            make_float3(recip_or_zero(dir.x), recip_or_zero(dir.y), recip_or_zero(dir.z));
+        const float2 ta = rec_ta[e];
+        float g8[8];
+        segment_bwd(T, Fd, c, I, tf, m.y, org, dir, inv, scale, ta.x, rec_g[e], ta.y,
+                    make_float4(gp.x, gp.y, gp.z, 0.f), gp.w, g8, tg);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s_g8[q * kSegStride + tid] = g8[q];
+        leaf = m.y;
+      }
+    }
+    __syncwarp();
+    leaf_group_flush<8>(s_g8, leaf, lane, wid, g_nodal);
+    __syncwarp();
+  }
+  tg.flush();
+  __syncthreads();
+  if (tid < 32 && s_g[tid] != 0.f) atomicAdd(g_tf + tid, s_g[tid]);
+}
+
+// The same for shell leaves: the field through the inverse map and the
+// degree-2 weights; the 27 nodal adjoints go to this thread's column of the
+// shared array directly.  Rays without an image adjoint are skipped.
 __global__ void __launch_bounds__(kSegThreads, 4)
-    shell_bwd_segments_kernel(const int4 *__restrict__ geo, int N, Shell S, Field Fd, Cam c,
-                              Integ I, const float4 *dL, const int2 *lm, const float2 *rec_ta,
-                              const float4 *rec_g, long long nseg, float *g_nodal, float *g_tf) {
+    shell_seg_adjoint_kernel(const int4 *__restrict__ geo, int N, Shell S, Field Fd, Cam c,
+                             Integ I, const float4 *dL, const int2 *lm, const float2 *rec_ta,
+                             const float4 *rec_g, long long nseg, float *g_nodal, float *g_tf) {
   __shared__ float s_g27[27 * kSegStride];
   __shared__ float4 s_tfv[8], s_tfs[8];
   __shared__ float s_g[32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  if (tid < 8) {
-    const float4 v = Fd.tf[tid];
-    const float4 w = Fd.tf[tid < 7 ? tid + 1 : 7];
-    s_tfv[tid] = v;
-    s_tfs[tid] = make_float4(w.x - v.x, w.y - v.y, w.z - v.z, w.w - v.w);
-  }
+  load_tf(Fd, s_tfv, s_tfs);
   if (tid < 32) s_g[tid] = 0.f;
   __syncthreads();
   const TF tf{s_tfv, s_tfs, Fd.s_min, Fd.inv_ds7};
@@ -765,7 +855,7 @@ __global__ void __launch_bounds__(kSegThreads, 4)
       const int lf = m.y >> 1, piece = m.y & 1;
       if (m.x >= 0 && (long long)m.x < npix && m.y >= 0 && lf < N) {
         const float4 gp = dL[m.x];
-        if (gp.x != 0.f || gp.y != 0.f || gp.z != 0.f || gp.w != 0.f) {
+        if (nonzero4(gp)) {
           float3 org, dir;
           pixel_ray(c, m.x % c.w, m.x / c.w, org, dir);
           const float rl = sqrtf(fmaf(dir.x, dir.x, fmaf(dir.y, dir.y, dir.z * dir.z)));
@@ -785,18 +875,7 @@ __global__ void __launch_bounds__(kSegThreads, 4)
       }
     }
     __syncwarp();
-    unsigned todo = __ballot_sync(0xffffffffu, leaf >= 0);
-    while (todo) {
-      const int lf = __shfl_sync(0xffffffffu, leaf, __ffs(todo) - 1);
-      const unsigned grp = __ballot_sync(0xffffffffu, leaf == lf);
-      todo &= ~grp;
-      if (lane < 27) {
-        const float *row = s_g27 + lane * kSegStride + (wid << 5);
-        float sum = 0.f;
-        for (unsigned mm = grp; mm; mm &= mm - 1) sum += row[__ffs(mm) - 1];
-        if (sum != 0.f) atomicAdd(g_nodal + 27 * (size_t)lf + lane, sum);
-      }
-    }
+    leaf_group_flush<27>(s_g27, leaf, lane, wid, g_nodal);
     __syncwarp();
   }
   tg.flush();
@@ -825,22 +904,25 @@ cudaError_t bwd_chunk_map(const long long *leaf_off, int N, int *chunk_leaf, cud
   return cudaGetLastError();
 }
 
-cudaError_t bwd_pair_hits(bool fill, const Topo &T, const Cam &C, const int4 *rect,
+cudaError_t bwd_pair_hits(int mode, const Topo &T, const Cam &C, const int4 *rect,
                           const long long *leaf_off, const int *chunk_leaf, long long npairs,
                           const float4 *dL, int *counts, const long long *ray_off, int *cursor,
                           const unsigned long long *mkey, unsigned long long fx,
-                          unsigned long long *keys, int *hleaf, cudaStream_t st) {
+                          unsigned long long *keys, unsigned *kpos, int2 *lm,
+                          unsigned long long *lm_count, long long key_cap,
+                          unsigned long long *err, cudaStream_t st) {
+  if (mode != 0 && mode != 2) return cudaErrorInvalidValue;
   if (npairs <= 0) return cudaSuccess;
   const long long nblk = (npairs + kPairThreads - 1) / kPairThreads;
   if (nblk > 0x7fffffffll) return cudaErrorInvalidValue;
-  if (fill)
-    pair_hits_kernel<true><<<(unsigned)nblk, kPairThreads, 0, st>>>(
+  if (mode == 0)
+    pair_hits_kernel<0><<<(unsigned)nblk, kPairThreads, 0, st>>>(
         T, C, rect, leaf_off, chunk_leaf, npairs, dL, counts, ray_off, cursor, mkey, fx, keys,
-        hleaf);
+        kpos, lm, lm_count, key_cap, err);
   else
-    pair_hits_kernel<false><<<(unsigned)nblk, kPairThreads, 0, st>>>(
+    pair_hits_kernel<2><<<(unsigned)nblk, kPairThreads, 0, st>>>(
         T, C, rect, leaf_off, chunk_leaf, npairs, dL, counts, ray_off, cursor, mkey, fx, keys,
-        hleaf);
+        kpos, lm, lm_count, key_cap, err);
   return cudaGetLastError();
 }
 
@@ -862,76 +944,83 @@ cudaError_t bwd_max_hits(const int *counts, long long n, unsigned long long *out
   return cudaGetLastError();
 }
 
-size_t bwd_rays_smem(int cap) {
-  return (size_t)kBwdWarps * cap * (sizeof(unsigned long long) + sizeof(int) + sizeof(float4));
+// grid of the per-entry passes: one thread per entry, at most `per_sm` CTAs
+// per SM (grid-stride beyond)
+static unsigned seg_grid(long long nseg, int nsm, int per_sm) {
+  const long long need = (nseg + kSegThreads - 1) / kSegThreads;
+  const long long most = (long long)nsm * per_sm;
+  return (unsigned)(need < most ? need : most);
 }
 
-cudaError_t bwd_rays(const Topo &T, const Field &Fd, const Cam &C, const Integ &I,
-                     const float4 *dL, const long long *ray_off, const unsigned long long *keys,
-                     const int *hleaf, float *g_nodal, float *g_tf, unsigned long long *err,
-                     int nsm, int cap, cudaStream_t st) {
-  if (cap < 32 || cap > kMaxRayHits || (cap & (cap - 1))) return cudaErrorInvalidValue;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(ray_backward_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bwd_rays_smem(kMaxRayHits));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  ray_backward_kernel<<<nsm * 4, kBwdWarps * 32, bwd_rays_smem(cap), st>>>(
-      T, Fd, C, I, dL, ray_off, keys, hleaf, g_nodal, g_tf, err, cap);
+cudaError_t bwd_cube_values(const Topo &T, const Field &Fd, const Cam &C, const Integ &I,
+                            const int2 *lm, long long nseg, float4 *val, int nsm,
+                            cudaStream_t st) {
+  if (nseg <= 0) return cudaSuccess;
+  cube_seg_values_kernel<<<seg_grid(nseg, nsm, 16), kSegThreads, 0, st>>>(T, Fd, C, I, lm, nseg,
+                                                                          val);
   return cudaGetLastError();
 }
 
-}  // namespace ocr
+cudaError_t bwd_shell_values(const int4 *geo, int N, const Shell &S, const Field &Fd,
+                             const Cam &C, const Integ &I, const float4 *dL, const int2 *lm,
+                             long long nseg, float4 *val, unsigned long long *err, int nsm,
+                             cudaStream_t st) {
+  if (nseg <= 0) return cudaSuccess;
+  shell_seg_values_kernel<<<seg_grid(nseg, nsm, 16), kSegThreads, 0, st>>>(
+      geo, N, S, Fd, C, I, dL, lm, nseg, val, err);
+  return cudaGetLastError();
+}
 
-namespace ocr {
-
-// warps per CTA of the values pass: up to 8, within 200 KB of shared memory
-static int shell_bwd_warps(int cap) {
+// warps per CTA of the per-ray scans: up to 8, within 200 KB of shared memory
+static int scans_warps(int cap) {
   const size_t per = (size_t)cap * (sizeof(float4) + sizeof(unsigned long long) + sizeof(int));
   const int w = (int)((200u << 10) / per);
   return w < 1 ? 1 : (w > 8 ? 8 : w);
 }
 
-size_t shell_bwd_smem(int cap) {
-  return (size_t)shell_bwd_warps(cap) * cap *
+size_t bwd_scans_smem(int cap) {
+  return (size_t)scans_warps(cap) * cap *
          (sizeof(float4) + sizeof(unsigned long long) + sizeof(int));
 }
 
-cudaError_t shell_bwd_prepare() {
+cudaError_t bwd_scans_prepare() {
   size_t most = 0;
   for (int cap = 32; cap <= kShellMaxCap; cap <<= 1)
-    most = most > shell_bwd_smem(cap) ? most : shell_bwd_smem(cap);
-  return cudaFuncSetAttribute(shell_bwd_values_kernel,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+    most = most > bwd_scans_smem(cap) ? most : bwd_scans_smem(cap);
+  return cudaFuncSetAttribute(ray_scans_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)most);
 }
 
-cudaError_t shell_bwd_values(const int4 *geo, int N, const Shell &S, const Field &Fd,
-                             const Cam &C, const Integ &I, const float4 *dL,
-                             const long long *ray_off, const unsigned long long *keys,
-                             const unsigned *kpos, long long key_cap, int cap, float2 *rec_ta,
-                             float4 *rec_g, unsigned long long *err, int nsm, cudaStream_t st) {
+cudaError_t bwd_ray_scans(const Cam &C, const float4 *dL, const long long *ray_off,
+                          const unsigned long long *keys, const unsigned *kpos, long long key_cap,
+                          int cap, float2 *rec_ta, float4 *rec_g, unsigned long long *err,
+                          int nsm, cudaStream_t st) {
   if (cap < 32 || cap > kShellMaxCap || (cap & (cap - 1))) return cudaErrorInvalidValue;
-  const int warps = shell_bwd_warps(cap);
+  const int warps = scans_warps(cap);
   const long long npix = (long long)C.w * C.h;
   const long long need = (npix + warps - 1) / warps;
   const long long grid = need < (long long)nsm * 8 ? need : (long long)nsm * 8;
-  shell_bwd_values_kernel<<<(unsigned)(grid > 0 ? grid : 1), warps * 32, shell_bwd_smem(cap),
-                            st>>>(geo, N, S, Fd, C, I, dL, ray_off, keys, kpos, key_cap, cap,
-                                  rec_ta, rec_g, err);
+  ray_scans_kernel<<<(unsigned)(grid > 0 ? grid : 1), warps * 32, bwd_scans_smem(cap), st>>>(
+      C, dL, ray_off, keys, kpos, key_cap, cap, rec_ta, rec_g, err);
   return cudaGetLastError();
 }
 
-cudaError_t shell_bwd_segments(const int4 *geo, int N, const Shell &S, const Field &Fd,
-                               const Cam &C, const Integ &I, const float4 *dL, const int2 *lm,
-                               const float2 *rec_ta, const float4 *rec_g, long long nseg,
-                               float *g_nodal, float *g_tf, int nsm, cudaStream_t st) {
+cudaError_t bwd_cube_adjoint(const Topo &T, const Field &Fd, const Cam &C, const Integ &I,
+                             const float4 *dL, const int2 *lm, const float2 *rec_ta,
+                             const float4 *rec_g, long long nseg, float *g_nodal, float *g_tf,
+                             int nsm, cudaStream_t st) {
   if (nseg <= 0) return cudaSuccess;
-  const long long need = (nseg + kSegThreads - 1) / kSegThreads;
-  const long long grid = need < (long long)nsm * 4 ? need : (long long)nsm * 4;
-  shell_bwd_segments_kernel<<<(unsigned)grid, kSegThreads, 0, st>>>(
+  cube_seg_adjoint_kernel<<<seg_grid(nseg, nsm, 8), kSegThreads, 0, st>>>(
+      T, Fd, C, I, dL, lm, rec_ta, rec_g, nseg, g_nodal, g_tf);
+  return cudaGetLastError();
+}
+
+cudaError_t bwd_shell_adjoint(const int4 *geo, int N, const Shell &S, const Field &Fd,
+                              const Cam &C, const Integ &I, const float4 *dL, const int2 *lm,
+                              const float2 *rec_ta, const float4 *rec_g, long long nseg,
+                              float *g_nodal, float *g_tf, int nsm, cudaStream_t st) {
+  if (nseg <= 0) return cudaSuccess;
+  shell_seg_adjoint_kernel<<<seg_grid(nseg, nsm, 4), kSegThreads, 0, st>>>(
       geo, N, S, Fd, C, I, dL, lm, rec_ta, rec_g, nseg, g_nodal, g_tf);
   return cudaGetLastError();
 }

@@ -93,7 +93,6 @@ struct ocr_forest {
   long long *d_ray_off = nullptr;        // [npix + 1]
   long long ray_cap = 0;
   unsigned long long *d_hkey = nullptr;  // [hits]
-  int *d_hleaf = nullptr;
   long long hit_cap = 0;
   // shell adjoint: per segment, its index in the leaf-grouped list (beside the
   // key), the list itself, and the near transmittance / own transmittance / far
@@ -202,7 +201,6 @@ void free_all(ocr_forest *F) {
   cudaFree(F->d_rcursor);
   cudaFree(F->d_ray_off);
   cudaFree(F->d_hkey);
-  cudaFree(F->d_hleaf);
   cudaFree(F->d_skpos);
   cudaFree(F->d_slm);
   cudaFree(F->d_srta);
@@ -736,13 +734,13 @@ namespace {
 // once on the device (legacy default stream, blocking) and size its scratch.
 int plan_cameras(ocr_forest *F) {
   for (CamPlan &P : F->plans) free_plan_buffers(F, P);
+  OCR_CUDA(bwd_scans_prepare());
   if (F->geometry == OCR_GEOM_SHELL) {
     for (CamPlan &P : F->plans) {
       const int rc = plan_shell(F, P);
       if (rc) return rc;
     }
     OCR_CUDA(shell_rays_prepare());
-    OCR_CUDA(shell_bwd_prepare());
     return OCR_OK;
   }
   const int G = (int)F->h_group_nodes.size();
@@ -921,6 +919,33 @@ int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats) {
 }  // extern "C"
 
 namespace {
+// the adjoint's per-segment buffers (list index beside each key, leaf-grouped
+// list, records) for at least n segments, and the list's append counter
+int grow_adjoint(ocr_forest *F, long long n) {
+  if (F->seg_cap >= n && F->d_lmcount) return OCR_OK;
+  cudaFree(F->d_skpos);
+  cudaFree(F->d_slm);
+  cudaFree(F->d_srta);
+  cudaFree(F->d_srg);
+  F->d_skpos = nullptr;
+  F->d_slm = nullptr;
+  F->d_srta = nullptr;
+  F->d_srg = nullptr;
+  F->bytes -= F->seg_cap *
+              (int64_t)(sizeof(unsigned) + sizeof(int2) + sizeof(float2) + sizeof(float4));
+  F->seg_cap = 0;
+  const long long want = std::min(n + n / 8 + 64, 0xffffffffll);
+  int rc;
+  if ((rc = dev_alloc(&F->d_skpos, (size_t)want, F->bytes)) ||
+      (rc = dev_alloc(&F->d_slm, (size_t)want, F->bytes)) ||
+      (rc = dev_alloc(&F->d_srta, (size_t)want, F->bytes)) ||
+      (rc = dev_alloc(&F->d_srg, (size_t)want, F->bytes)))
+    return rc;
+  F->seg_cap = want;
+  if (!F->d_lmcount && (rc = dev_alloc(&F->d_lmcount, 1, F->bytes))) return rc;
+  return OCR_OK;
+}
+
 // (re)allocate a scratch buffer to hold at least n elements
 template <typename T>
 int grow(ocr_forest *F, T **p, long long &cap, long long n) {
@@ -954,41 +979,22 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
     const Field Fd{F->d_nodal, reinterpret_cast<const float4 *>(F->d_tf), F->s_min,
                    7.f / (F->s_max - F->s_min)};
     if (P.nhits >= 0xffffffffll) return OCR_ERR_UNSUPPORTED;  // list indices are 32-bit
-    if (F->seg_cap < P.nhits || !F->d_lmcount) {
-      cudaFree(F->d_skpos);
-      cudaFree(F->d_slm);
-      cudaFree(F->d_srta);
-      cudaFree(F->d_srg);
-      F->d_skpos = nullptr;
-      F->d_slm = nullptr;
-      F->d_srta = nullptr;
-      F->d_srg = nullptr;
-      F->bytes -= F->seg_cap * (int64_t)(sizeof(unsigned) + sizeof(int2) + sizeof(float2) +
-                                         sizeof(float4));
-      F->seg_cap = 0;
-      const long long want = std::min(P.nhits + P.nhits / 8 + 64, 0xffffffffll);
-      int rc;
-      if ((rc = dev_alloc(&F->d_skpos, (size_t)want, F->bytes)) ||
-          (rc = dev_alloc(&F->d_slm, (size_t)want, F->bytes)) ||
-          (rc = dev_alloc(&F->d_srta, (size_t)want, F->bytes)) ||
-          (rc = dev_alloc(&F->d_srg, (size_t)want, F->bytes)))
-        return rc;
-      F->seg_cap = want;
-      if (!F->d_lmcount && (rc = dev_alloc(&F->d_lmcount, 1, F->bytes))) return rc;
-    }
+    int rc = grow_adjoint(F, P.nhits);
+    if (rc) return rc;
     OCR_CUDA(cudaMemsetAsync(d_grad_nodal, 0, sizeof(float) * 27 * (size_t)F->N, st));
     OCR_CUDA(cudaMemsetAsync(d_grad_tf, 0, sizeof(float) * 32, st));
     OCR_CUDA(cudaMemsetAsync(F->d_stats, 0, kStats * sizeof(unsigned long long), st));
     OCR_CUDA(cudaMemsetAsync(F->d_err, 0, sizeof(unsigned long long), st));
-    int rc = enqueue_shell_lists(F, P, nullptr, st, true);
+    rc = enqueue_shell_lists(F, P, nullptr, st, true);
     if (rc) return rc;
     const float4 *dL = reinterpret_cast<const float4 *>(d_dL_drgba);
-    OCR_CUDA(shell_bwd_values(F->d_geo, F->N, F->shell, Fd, P.cam, F->integ, dL, P.d_ray_off,
-                              P.d_keys, F->d_skpos, P.nhits, P.cap, F->d_srta, F->d_srg,
-                              F->d_err, F->nsm, st));
-    OCR_CUDA(shell_bwd_segments(F->d_geo, F->N, F->shell, Fd, P.cam, F->integ, dL, F->d_slm,
-                                F->d_srta, F->d_srg, P.nhits, d_grad_nodal, d_grad_tf, F->nsm,
-                                st));
+    OCR_CUDA(bwd_shell_values(F->d_geo, F->N, F->shell, Fd, P.cam, F->integ, dL, F->d_slm,
+                              P.nhits, F->d_srg, F->d_err, F->nsm, st));
+    OCR_CUDA(bwd_ray_scans(P.cam, dL, P.d_ray_off, P.d_keys, F->d_skpos, P.nhits, P.cap,
+                           F->d_srta, F->d_srg, F->d_err, F->nsm, st));
+    OCR_CUDA(bwd_shell_adjoint(F->d_geo, F->N, F->shell, Fd, P.cam, F->integ, dL, F->d_slm,
+                               F->d_srta, F->d_srg, P.nhits, d_grad_nodal, d_grad_tf, F->nsm,
+                               st));
     long long *h = F->h_group_slots;
     OCR_CUDA(cudaMemcpyAsync(h, F->d_err, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     OCR_CUDA(cudaMemcpyAsync(h + 1, F->d_stats + kStatErrors, sizeof(unsigned long long),
@@ -1039,10 +1045,12 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
   OCR_CUDA(bwd_chunk_map(F->d_leaf_off, F->N, F->d_pchunk, st));
   const float4 *dL = reinterpret_cast<const float4 *>(d_dL_drgba);
 
-  // hits per ray, their offsets, then the hit lists (leaf, mirrored Morton key)
+  // hits per ray, their offsets, then the hit lists (mirrored Morton keys) and
+  // the leaf-grouped list
   OCR_CUDA(cudaMemsetAsync(F->d_rcount, 0, sizeof(int) * (size_t)npix, st));
-  OCR_CUDA(bwd_pair_hits(false, T, cam, P0.d_rect, F->d_leaf_off, F->d_pchunk, npairs, dL,
-                         F->d_rcount, nullptr, nullptr, F->d_mkey, F->fx, nullptr, nullptr, st));
+  OCR_CUDA(bwd_pair_hits(0, T, cam, P0.d_rect, F->d_leaf_off, F->d_pchunk, npairs, dL,
+                         F->d_rcount, nullptr, nullptr, F->d_mkey, F->fx, nullptr, nullptr,
+                         nullptr, nullptr, 0, nullptr, st));
   OCR_CUDA(bwd_count_scan(F->d_rcount, npix, F->d_bsums, F->bsums_cap, F->d_ray_off, st));
   OCR_CUDA(bwd_max_hits(F->d_rcount, npix, F->d_stats + kStatMaxHits, st));
   OCR_CUDA(cudaMemcpyAsync(h, F->d_ray_off + npix, sizeof(long long), cudaMemcpyDeviceToHost, st));
@@ -1050,26 +1058,23 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
                            cudaMemcpyDeviceToHost, st));
   OCR_CUDA(cudaStreamSynchronize(st));
   const long long nh = h[0];
-  int cap = 32;  // per-warp lists sized for the longest ray (longer than 512: skipped)
-  while (cap < h[1] && cap < kMaxRayHits) cap <<= 1;
-  {
-    long long c0 = F->hit_cap;
-    if ((rc = grow(F, &F->d_hkey, F->hit_cap, nh))) return rc;
-    if (F->hit_cap != c0 || !F->d_hleaf) {
-      cudaFree(F->d_hleaf);
-      F->d_hleaf = nullptr;
-      if ((rc = dev_alloc(&F->d_hleaf, (size_t)F->hit_cap, F->bytes))) return rc;
-    }
-  }
+  if (nh >= 0xffffffffll) return OCR_ERR_UNSUPPORTED;  // list indices are 32-bit
+  int cap = 32;  // per-warp lists sized for the longest ray (longer ones: device error)
+  while (cap < h[1] && cap < kShellMaxCap) cap <<= 1;
+  if ((rc = grow(F, &F->d_hkey, F->hit_cap, nh)) || (rc = grow_adjoint(F, nh))) return rc;
   OCR_CUDA(cudaMemsetAsync(F->d_rcursor, 0, sizeof(int) * (size_t)npix, st));
-  OCR_CUDA(bwd_pair_hits(true, T, cam, P0.d_rect, F->d_leaf_off, F->d_pchunk, npairs, dL,
-                         nullptr, F->d_ray_off, F->d_rcursor, F->d_mkey, F->fx, F->d_hkey,
-                         F->d_hleaf, st));
-
-  // one warp per ray: order, recompute, prefix/suffix, adjoint
+  OCR_CUDA(cudaMemsetAsync(F->d_lmcount, 0, sizeof(unsigned long long), st));
   OCR_CUDA(cudaMemsetAsync(F->d_err, 0, sizeof(unsigned long long), st));
-  OCR_CUDA(bwd_rays(T, Fd, cam, F->integ, dL, F->d_ray_off, F->d_hkey, F->d_hleaf,
-                    d_grad_nodal, d_grad_tf, F->d_err, F->nsm, cap, st));
+  OCR_CUDA(bwd_pair_hits(2, T, cam, P0.d_rect, F->d_leaf_off, F->d_pchunk, npairs, dL, nullptr,
+                         F->d_ray_off, F->d_rcursor, F->d_mkey, F->fx, F->d_hkey, F->d_skpos,
+                         F->d_slm, F->d_lmcount, nh, F->d_err, st));
+
+  // segment values, per-ray scans, segment adjoints
+  OCR_CUDA(bwd_cube_values(T, Fd, cam, F->integ, F->d_slm, nh, F->d_srg, F->nsm, st));
+  OCR_CUDA(bwd_ray_scans(cam, dL, F->d_ray_off, F->d_hkey, F->d_skpos, nh, cap, F->d_srta,
+                         F->d_srg, F->d_err, F->nsm, st));
+  OCR_CUDA(bwd_cube_adjoint(T, Fd, cam, F->integ, dL, F->d_slm, F->d_srta, F->d_srg, nh,
+                            d_grad_nodal, d_grad_tf, F->nsm, st));
   OCR_CUDA(cudaMemcpyAsync(h, F->d_err, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
   OCR_CUDA(cudaStreamSynchronize(st));
   if (h[0]) return OCR_ERR_DEVICE;

@@ -72,10 +72,6 @@ constexpr int kStats = 16;
 constexpr int kStatSegments = 0, kStatSteps = 1, kStatTests = 2, kStatSlots = 3;
 constexpr int kStatCoarse = 8, kStatErrors = 4, kStatVisible = 5;
 
-// Adjoint: at most kMaxRayHits segments per ray (larger rays are skipped and
-// counted as device errors).
-constexpr int kMaxRayHits = 512;
-
 // Slots are processed in chunks of kChunk consecutive slots, one chunk per CTA.
 constexpr int kChunk = 128;
 
@@ -124,20 +120,48 @@ cudaError_t bwd_count_scan(const int *counts, long long n, long long *bs, long l
                            long long *ray_off, cudaStream_t st);
 long long bwd_scan_blocks(long long n);
 cudaError_t bwd_chunk_map(const long long *leaf_off, int N, int *chunk_leaf, cudaStream_t st);
-cudaError_t bwd_pair_hits(bool fill, const Topo &T, const Cam &C, const int4 *rect,
+// mode 0: hits per ray into counts (rays with a zero image adjoint skipped);
+// mode 2: each hit's mirrored Morton key into its ray's list, and the hit
+// appended to the leaf-grouped list lm (pixel, leaf) through *lm_count (zeroed
+// by the caller), its index in kpos beside the key; more than key_cap hits
+// are counted in err
+cudaError_t bwd_pair_hits(int mode, const Topo &T, const Cam &C, const int4 *rect,
                           const long long *leaf_off, const int *chunk_leaf, long long npairs,
                           const float4 *dL, int *counts, const long long *ray_off, int *cursor,
                           const unsigned long long *mkey, unsigned long long fx,
-                          unsigned long long *keys, int *hleaf, cudaStream_t st);
+                          unsigned long long *keys, unsigned *kpos, int2 *lm,
+                          unsigned long long *lm_count, long long key_cap,
+                          unsigned long long *err, cudaStream_t st);
 // the most hits on one ray (atomicMax into *out, which the caller zeroes)
 cudaError_t bwd_max_hits(const int *counts, long long n, unsigned long long *out,
                          cudaStream_t st);
-// one warp per ray; cap: a power of two, 32..kMaxRayHits, at least the most
-// hits on one ray (longer rays are skipped and counted in err)
-cudaError_t bwd_rays(const Topo &T, const Field &Fd, const Cam &C, const Integ &I,
-                     const float4 *dL, const long long *ray_off, const unsigned long long *keys,
-                     const int *hleaf, float *g_nodal, float *g_tf, unsigned long long *err,
-                     int nsm, int cap, cudaStream_t st);
+// The three passes over a leaf-grouped list of nseg entries.  Values: one
+// thread per entry, the segment's (A, B) into val (shell: entries of rays with
+// a zero image adjoint are skipped; missing pieces counted in err).
+cudaError_t bwd_cube_values(const Topo &T, const Field &Fd, const Cam &C, const Integ &I,
+                            const int2 *lm, long long nseg, float4 *val, int nsm,
+                            cudaStream_t st);
+cudaError_t bwd_shell_values(const int4 *geo, int N, const Shell &S, const Field &Fd,
+                             const Cam &C, const Integ &I, const float4 *dL, const int2 *lm,
+                             long long nseg, float4 *val, unsigned long long *err, int nsm,
+                             cudaStream_t st);
+// Scans: one warp per ray, lists of up to cap entries (a power of two,
+// 32..kShellMaxCap; longer lists are counted in err): the values gathered from
+// rec_g by the list indices in kpos, then per entry the near transmittance and
+// own transmittance into rec_ta and the far aggregate into rec_g.
+// bwd_scans_prepare raises the kernel's shared-memory limit for every cap.
+size_t bwd_scans_smem(int cap);
+cudaError_t bwd_scans_prepare();
+cudaError_t bwd_ray_scans(const Cam &C, const float4 *dL, const long long *ray_off,
+                          const unsigned long long *keys, const unsigned *kpos, long long key_cap,
+                          int cap, float2 *rec_ta, float4 *rec_g, unsigned long long *err,
+                          int nsm, cudaStream_t st);
+// Adjoint: one thread per entry; nodal adjoints summed over a warp's lanes of
+// the same leaf, then accumulated into g_nodal, the knot adjoints into g_tf.
+cudaError_t bwd_cube_adjoint(const Topo &T, const Field &Fd, const Cam &C, const Integ &I,
+                             const float4 *dL, const int2 *lm, const float2 *rec_ta,
+                             const float4 *rec_g, long long nseg, float *g_nodal, float *g_tf,
+                             int nsm, cudaStream_t st);
 
 // Cubed-sphere shell (ocr_shell.cu)
 cudaError_t shell_cull(const int4 *geo, int N, const Shell &S, const Cam &C, int4 *rect,
@@ -168,24 +192,12 @@ cudaError_t shell_rays(const int4 *geo, int N, const Shell &S, const Field &Fd, 
                        int *counts, unsigned long long *stats, int nsm, int want_warps,
                        cudaStream_t st);
 
-// Adjoint of a shell render (ocr_backward.cu), over lists built by shell_pairs
-// in mode 2.  shell_bwd_values: one warp per ray (warps per CTA from the list
-// capacity cap) stores per segment, at its index in the leaf-grouped list, the
-// transmittance of the nearer segments and its own (rec_ta) and the aggregate
-// of the farther ones (rec_g); shell_bwd_segments: one thread per segment of
-// the leaf-grouped list, its adjoint, the 27 nodal adjoints summed over the
-// warp's lanes of the same leaf before the atomics.  shell_bwd_prepare raises
-// the first kernel's shared-memory limit for every list capacity.
-size_t shell_bwd_smem(int cap);
-cudaError_t shell_bwd_prepare();
-cudaError_t shell_bwd_values(const int4 *geo, int N, const Shell &S, const Field &Fd,
-                             const Cam &C, const Integ &I, const float4 *dL,
-                             const long long *ray_off, const unsigned long long *keys,
-                             const unsigned *kpos, long long key_cap, int cap, float2 *rec_ta,
-                             float4 *rec_g, unsigned long long *err, int nsm, cudaStream_t st);
-cudaError_t shell_bwd_segments(const int4 *geo, int N, const Shell &S, const Field &Fd,
-                               const Cam &C, const Integ &I, const float4 *dL, const int2 *lm,
-                               const float2 *rec_ta, const float4 *rec_g, long long nseg,
-                               float *g_nodal, float *g_tf, int nsm, cudaStream_t st);
+// Shell adjoint, the cube's three passes with the shell's geometry and field
+// (values by bwd_shell_values, scans by bwd_ray_scans) over lists built by
+// shell_pairs in mode 2.
+cudaError_t bwd_shell_adjoint(const int4 *geo, int N, const Shell &S, const Field &Fd,
+                              const Cam &C, const Integ &I, const float4 *dL, const int2 *lm,
+                              const float2 *rec_ta, const float4 *rec_g, long long nseg,
+                              float *g_nodal, float *g_tf, int nsm, cudaStream_t st);
 
 }  // namespace ocr
