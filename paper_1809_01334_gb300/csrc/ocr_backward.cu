@@ -232,17 +232,25 @@ __global__ void __launch_bounds__(kPairThreads)
 
 // -------------------------------------------------------- segment adjoint --
 // Accumulates the adjoint of the transfer-function knots of consecutive
-// evaluations that fall in the same knot interval before touching shared memory.
+// evaluations that fall in the same knot interval in registers; on a change of
+// interval they are added to this thread's own column of a shared [32][NT]
+// array (no atomics), which the CTA sums at its end (knot_grad_flush).
 struct TfGrad {
   int k = -1;
   float4 a0, a1;  // knot k, knot k + 1
-  float *s_g;     // [32] in shared memory
+  float *col;     // this thread's column: value v at col[v * stride]
+  int stride;
   __device__ void flush() {
     if (k < 0) return;
-    atomicAdd(s_g + 4 * k + 0, a0.x); atomicAdd(s_g + 4 * k + 1, a0.y);
-    atomicAdd(s_g + 4 * k + 2, a0.z); atomicAdd(s_g + 4 * k + 3, a0.w);
-    atomicAdd(s_g + 4 * k + 4, a1.x); atomicAdd(s_g + 4 * k + 5, a1.y);
-    atomicAdd(s_g + 4 * k + 6, a1.z); atomicAdd(s_g + 4 * k + 7, a1.w);
+    float *g = col + 4 * k * stride;
+    g[0] += a0.x;
+    g[stride] += a0.y;
+    g[2 * stride] += a0.z;
+    g[3 * stride] += a0.w;
+    g[4 * stride] += a1.x;
+    g[5 * stride] += a1.y;
+    g[6 * stride] += a1.z;
+    g[7 * stride] += a1.w;
     k = -1;
   }
   __device__ void add(int kk, float w, float4 v) {
@@ -258,6 +266,20 @@ struct TfGrad {
     a1.z = fmaf(w, v.z, a1.z); a1.w = fmaf(w, v.w, a1.w);
   }
 };
+
+// The CTA's knot adjoints: s_gt [32][NT] summed over the threads (each of the
+// first 32 threads one value, the columns visited in a rotated order so that
+// they hit distinct banks), one atomic per value.
+template <int NT>
+__device__ __forceinline__ void knot_grad_flush(const float *s_gt, float *g_tf) {
+  __syncthreads();
+  const int v = threadIdx.x;
+  if (v < 32) {
+    float sum = 0.f;
+    for (int t = 0; t < NT; ++t) sum += s_gt[v * NT + ((t + v) & (NT - 1))];
+    if (sum != 0.f) atomicAdd(g_tf + v, sum);
+  }
+}
 
 // dL/ds at a field value s from vbar = dL/d(kappa, q) (the transfer
 // function's slope; zero where it is clamped), after crediting the knots
@@ -638,6 +660,17 @@ __device__ __forceinline__ bool nonzero4(float4 g) {
 
 constexpr int kSegThreads = 128;
 constexpr int kSegStride = kSegThreads + 1;  // row stride: lanes summing rows hit distinct banks
+static_assert((kSegThreads & (kSegThreads - 1)) == 0, "rotated column order needs a power of two");
+
+// The CTA's contiguous range [b, end) of the nseg list entries, whole
+// multiples of kSegThreads: consecutive entries of a thread then belong to
+// nearby leaves (coherent knot intervals and nodal data).
+__device__ __forceinline__ void seg_range(long long nseg, long long &b, long long &end) {
+  const long long per =
+      ((nseg + gridDim.x - 1) / gridDim.x + kSegThreads - 1) / kSegThreads * kSegThreads;
+  b = (long long)blockIdx.x * per;
+  end = b + per < nseg ? b + per : nseg;
+}
 
 // Pass 1, one thread per entry e of the leaf-grouped list (pixel, leaf): the
 // segment's value (A, B) into val[e].  Cube leaves.
@@ -779,27 +812,30 @@ __device__ __forceinline__ void leaf_group_flush(const float *s_rows, int leaf, 
 // adjoints with the near transmittance and far aggregate of pass 2, through
 // the trilinear weights; the 8 nodal adjoints summed over the warp's lanes of
 // the same leaf (the list keeps a leaf's segments together).  Cube leaves.
-__global__ void __launch_bounds__(kSegThreads)
+__global__ void __launch_bounds__(kSegThreads, 4)
     cube_seg_adjoint_kernel(Topo T, Field Fd, Cam c, Integ I, const float4 *dL, const int2 *lm,
                             const float2 *rec_ta, const float4 *rec_g, long long nseg,
                             float *g_nodal, float *g_tf) {
   __shared__ float s_g8[8 * kSegStride];
+  __shared__ float s_gt[32 * kSegThreads];
   __shared__ float4 s_tfv[8], s_tfs[8];
-  __shared__ float s_g[32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   load_tf(Fd, s_tfv, s_tfs);
-  if (tid < 32) s_g[tid] = 0.f;
+#pragma unroll
+  for (int v = 0; v < 32; ++v) s_gt[v * kSegThreads + tid] = 0.f;
   __syncthreads();
   const TF tf{s_tfv, s_tfs, Fd.s_min, Fd.inv_ds7};
   TfGrad tg;
-  tg.s_g = s_g;
+  tg.col = s_gt + tid;
+  tg.stride = kSegThreads;
   const float scale = ldexpf(1.f, -T.L);
   const long long npix = (long long)c.w * c.h;
-  for (long long b = (long long)blockIdx.x * kSegThreads; b < nseg;
-       b += (long long)gridDim.x * kSegThreads) {
+  long long b, end;
+  seg_range(nseg, b, end);
+  for (; b < end; b += kSegThreads) {
     const long long e = b + tid;
     int leaf = -1;
-    if (e < nseg) {
+    if (e < end) {
       const int2 m = lm[e];
       if (m.x >= 0 && (long long)m.x < npix && m.y >= 0 && m.y < T.N) {
         const float4 gp = dL[m.x];
@@ -821,8 +857,7 @@ __global__ void __launch_bounds__(kSegThreads)
     __syncwarp();
   }
   tg.flush();
-  __syncthreads();
-  if (tid < 32 && s_g[tid] != 0.f) atomicAdd(g_tf + tid, s_g[tid]);
+  knot_grad_flush<kSegThreads>(s_gt, g_tf);
 }
 
 // The same for shell leaves: the field through the inverse map and the
@@ -833,24 +868,27 @@ __global__ void __launch_bounds__(kSegThreads, 4)
                              Integ I, const float4 *dL, const int2 *lm, const float2 *rec_ta,
                              const float4 *rec_g, long long nseg, float *g_nodal, float *g_tf) {
   __shared__ float s_g27[27 * kSegStride];
+  __shared__ float s_gt[32 * kSegThreads];
   __shared__ float4 s_tfv[8], s_tfs[8];
-  __shared__ float s_g[32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   load_tf(Fd, s_tfv, s_tfs);
-  if (tid < 32) s_g[tid] = 0.f;
+#pragma unroll
+  for (int v = 0; v < 32; ++v) s_gt[v * kSegThreads + tid] = 0.f;
   __syncthreads();
   const TF tf{s_tfv, s_tfs, Fd.s_min, Fd.inv_ds7};
   TfGrad tg;
-  tg.s_g = s_g;
+  tg.col = s_gt + tid;
+  tg.stride = kSegThreads;
   const long long npix = (long long)c.w * c.h;
   float *g27 = s_g27 + tid;
-  for (long long b = (long long)blockIdx.x * kSegThreads; b < nseg;
-       b += (long long)gridDim.x * kSegThreads) {
+  long long b, end;
+  seg_range(nseg, b, end);
+  for (; b < end; b += kSegThreads) {
     const long long e = b + tid;
 #pragma unroll
     for (int q = 0; q < 27; ++q) g27[q * kSegStride] = 0.f;
     int leaf = -1;
-    if (e < nseg) {
+    if (e < end) {
       const int2 m = lm[e];
       const int lf = m.y >> 1, piece = m.y & 1;
       if (m.x >= 0 && (long long)m.x < npix && m.y >= 0 && lf < N) {
@@ -879,8 +917,7 @@ __global__ void __launch_bounds__(kSegThreads, 4)
     __syncwarp();
   }
   tg.flush();
-  __syncthreads();
-  if (tid < 32 && s_g[tid] != 0.f) atomicAdd(g_tf + tid, s_g[tid]);
+  knot_grad_flush<kSegThreads>(s_gt, g_tf);
 }
 
 }  // namespace
@@ -1010,7 +1047,7 @@ cudaError_t bwd_cube_adjoint(const Topo &T, const Field &Fd, const Cam &C, const
                              const float4 *rec_g, long long nseg, float *g_nodal, float *g_tf,
                              int nsm, cudaStream_t st) {
   if (nseg <= 0) return cudaSuccess;
-  cube_seg_adjoint_kernel<<<seg_grid(nseg, nsm, 8), kSegThreads, 0, st>>>(
+  cube_seg_adjoint_kernel<<<seg_grid(nseg, nsm, 16), kSegThreads, 0, st>>>(
       T, Fd, C, I, dL, lm, rec_ta, rec_g, nseg, g_nodal, g_tf);
   return cudaGetLastError();
 }
@@ -1020,7 +1057,7 @@ cudaError_t bwd_shell_adjoint(const int4 *geo, int N, const Shell &S, const Fiel
                               const float2 *rec_ta, const float4 *rec_g, long long nseg,
                               float *g_nodal, float *g_tf, int nsm, cudaStream_t st) {
   if (nseg <= 0) return cudaSuccess;
-  shell_seg_adjoint_kernel<<<seg_grid(nseg, nsm, 4), kSegThreads, 0, st>>>(
+  shell_seg_adjoint_kernel<<<seg_grid(nseg, nsm, 16), kSegThreads, 0, st>>>(
       geo, N, S, Fd, C, I, dL, lm, rec_ta, rec_g, nseg, g_nodal, g_tf);
   return cudaGetLastError();
 }
