@@ -105,14 +105,33 @@ __device__ __forceinline__ int shell_ray_leaf(const LeafShell &q, float3 org, fl
 // the point's coordinates in the tree frame (x.n, x.e1, x.e2) are affine in
 // tau; the local coordinates follow from the inverse map,
 //   u = (2/pi) (atan(x.e1 / x.n) - atan(ta)) / h
-//     = (2/pi) atan2(x.e1 - ta x.n, x.n + ta x.e1) / h,
+//     = (2/pi) atan2(x.e1 - ta x.n, x.n + ta x.e1) / h
+// (for fine leaves the arctangent of the small ratio by its series),
 //   w = (|x| - r_in) / (r_out - r_in),
 // then the degree-2 Lagrange interpolation of the 27 nodal values.
 struct ShellSeg {
   float pf[3], dp[3];
   float ta, tb, ka, rin, kr;
+  int series;  // leaf level >= kSeriesLevel: the angles by atan_small
   float nd[27];
 };
+
+// Leaves of level >= kSeriesLevel span at most (pi/2) 2^-3 = pi/16 in each
+// angle, so the tangent of a point's angle from the leaf's lower plane stays
+// below tan(pi/16) = 0.199 (a little more for rounding at the faces).
+constexpr int kSeriesLevel = 3;
+
+// arctan(z) for |z| <= 0.2 by its Maclaurin series z - z^3/3 + z^5/5 - ... up
+// to z^11: the first omitted term, z^13/13, is below 3e-10 of z there.
+__device__ __forceinline__ float atan_small(float z) {
+  const float t = z * z;
+  float p = fmaf(t, -1.f / 11.f, 1.f / 9.f);
+  p = fmaf(p, t, -1.f / 7.f);
+  p = fmaf(p, t, 1.f / 5.f);
+  p = fmaf(p, t, -1.f / 3.f);
+  p = fmaf(p, t, 1.f);
+  return z * p;
+}
 
 __device__ __forceinline__ void quad_basis(float t, float *l) {
   l[0] = 2.f * (t - 0.5f) * (t - 1.f);
@@ -125,8 +144,16 @@ __device__ __forceinline__ float shell_field(const ShellSeg &g, float tau, float
                                              float *lw) {
   const float pn = fmaf(tau, g.dp[0], g.pf[0]), p1 = fmaf(tau, g.dp[1], g.pf[1]),
               p2 = fmaf(tau, g.dp[2], g.pf[2]);
-  const float u = atan2f(fmaf(-g.ta, pn, p1), fmaf(g.ta, p1, pn)) * g.ka;
-  const float v = atan2f(fmaf(-g.tb, pn, p2), fmaf(g.tb, p2, pn)) * g.ka;
+  const float ya = fmaf(-g.ta, pn, p1), xa = fmaf(g.ta, p1, pn);
+  const float yb = fmaf(-g.tb, pn, p2), xb = fmaf(g.tb, p2, pn);
+  float u, v;
+  if (g.series) {
+    u = atan_small(ya / xa) * g.ka;
+    v = atan_small(yb / xb) * g.ka;
+  } else {
+    u = atan2f(ya, xa) * g.ka;
+    v = atan2f(yb, xb) * g.ka;
+  }
   const float w = (sqrtf(fmaf(pn, pn, fmaf(p1, p1, p2 * p2))) - g.rin) * g.kr;
   quad_basis(u, lu);
   quad_basis(v, lv);
@@ -174,6 +201,7 @@ __device__ __forceinline__ bool shell_segment(const Shell &S, const float *__res
   g.ta = q.ta0;
   g.tb = q.tb0;
   g.ka = ldexpf(0.63661977236758134f, q.level);  // (2 / pi) / h
+  g.series = q.level >= kSeriesLevel;
   g.rin = q.rin;
   g.kr = 1.f / (q.rout - q.rin);
   const float *nd = nodal + 27 * (size_t)leaf;
