@@ -762,6 +762,51 @@ __global__ void __launch_bounds__(256)
       continue;
     }
     if (!nonzero4(dL[pix])) continue;
+    if (n <= 32) {  // one entry per lane: sort and scans in registers
+      unsigned long long kk = lane < n ? keys[h0 + lane] : ~0ull;
+      int q = lane < n ? (int)kpos[h0 + lane] : -1;
+      for (int sz = 2; sz <= 32; sz <<= 1)  // bitonic, ascending; keys are distinct
+        for (int st = sz >> 1; st > 0; st >>= 1) {
+          const unsigned long long ok = __shfl_xor_sync(0xffffffffu, kk, st);
+          const int oq = __shfl_xor_sync(0xffffffffu, q, st);
+          const bool low = (lane & st) == 0, up = (lane & sz) == 0;
+          if (low == up ? ok < kk : ok > kk) {
+            kk = ok;
+            q = oq;
+          }
+        }
+      const bool live = lane < n && (long long)(unsigned)q < key_cap;
+      const float4 v = live ? rec_g[(unsigned)q] : seg_identity();
+      float x = v.x;  // transmittance of this and the nearer segments
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x *= y;
+      }
+      float tn = __shfl_up_sync(0xffffffffu, x, 1);
+      if (lane == 0) tn = 1.f;
+      float4 f = v;  // this and the farther segments, Eq. 2.14
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        float4 y;
+        y.x = __shfl_down_sync(0xffffffffu, f.x, o);
+        y.y = __shfl_down_sync(0xffffffffu, f.y, o);
+        y.z = __shfl_down_sync(0xffffffffu, f.z, o);
+        y.w = __shfl_down_sync(0xffffffffu, f.w, o);
+        if (lane + o < 32) f = seg_combine(f, y);
+      }
+      float4 g;
+      g.x = __shfl_down_sync(0xffffffffu, f.x, 1);
+      g.y = __shfl_down_sync(0xffffffffu, f.y, 1);
+      g.z = __shfl_down_sync(0xffffffffu, f.z, 1);
+      g.w = __shfl_down_sync(0xffffffffu, f.w, 1);
+      if (lane == 31) g = seg_identity();
+      if (live) {
+        rec_ta[(unsigned)q] = make_float2(tn, v.x);
+        rec_g[(unsigned)q] = g;
+      }
+      continue;
+    }
     int P = 32;
     while (P < n) P <<= 1;
     for (int k = lane; k < P; k += 32) {
