@@ -807,14 +807,20 @@ __global__ void __launch_bounds__(256)
       }
       continue;
     }
-    int P = 32;
+    int P = 64;
     while (P < n) P <<= 1;
-    for (int k = lane; k < P; k += 32) {
-      key[k] = k < n ? keys[h0 + k] : ~0ull;
-      pos[k] = k < n ? (int)kpos[h0 + k] : -1;
+    if (P <= 256) {  // sorted in registers
+      if (P == 64) warp_sort_list<2, true>(keys + h0, kpos + h0, n, key, pos, P, lane);
+      else if (P == 128) warp_sort_list<4, true>(keys + h0, kpos + h0, n, key, pos, P, lane);
+      else warp_sort_list<8, true>(keys + h0, kpos + h0, n, key, pos, P, lane);
+    } else {
+      for (int k = lane; k < P; k += 32) {
+        key[k] = k < n ? keys[h0 + k] : ~0ull;
+        pos[k] = k < n ? (int)kpos[h0 + k] : -1;
+      }
+      __syncwarp();
+      warp_sort(key, pos, P, lane);
     }
-    __syncwarp();
-    warp_sort(key, pos, P, lane);
     for (int k = lane; k < n; k += 32) {
       const unsigned q = (unsigned)pos[k];
       val[k] = (long long)q < key_cap ? rec_g[q] : seg_identity();

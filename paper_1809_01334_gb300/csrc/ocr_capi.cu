@@ -442,9 +442,9 @@ int enqueue_shell(ocr_forest *F, CamPlan &P, float4 *rgba, int *counts, unsigned
   OCR_CUDA(shell_rays(F->d_geo, F->N, F->shell, Fd, P.cam, F->integ, P.d_ray_off, npix, P.d_keys,
                       P.nhits, P.cap, rgba, counts, F->d_stats, F->nsm, F->shell_warps, st));
   if (timed) OCR_CUDA(cudaEventRecord(F->ev[3], st));
-  // cull, 2 scans of 3 kernels (1 when empty), chunk map, 2 pair passes, rays
+  // cull, 2 scans of 3 kernels (1 when empty), chunk map, 2 pair passes, sort, rays
   launches += 1 + (bwd_scan_blocks(F->N) > 0 ? 3 : 0) + 1 + (P.npairs > 0 ? 2 : 0) +
-              (bwd_scan_blocks(npix) > 0 ? 3 : 0) + 1;
+              (bwd_scan_blocks(npix) > 0 ? 3 : 0) + 2;
   return OCR_OK;
 }
 

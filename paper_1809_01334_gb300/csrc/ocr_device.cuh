@@ -9,6 +9,93 @@ namespace {
 
 constexpr float kOne = 1.0f;
 
+// Ascending bitonic sort of P = 32 E keys (E <= 8) held by one warp in
+// registers: lane l holds the keys of indices j 32 + l (j < E).  Stages whose
+// partner index differs in bits >= 5 compare two of a lane's own registers;
+// the others swap with lane l ^ st by shuffles.  With PAY the int payload p
+// moves along.  The stage loops stay loops (small code); only the loops over
+// a lane's E registers are unrolled.
+template <int E, int JS, bool PAY>
+__device__ __forceinline__ void bitonic_in_lane(unsigned long long (&k)[E], int (&p)[E], int sz,
+                                                int lane) {
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    const int jp = j ^ JS;
+    if (jp > j && jp < E) {
+      const bool up = (((j << 5) | lane) & sz) == 0;
+      if ((k[j] > k[jp]) == up) {
+        const unsigned long long t = k[j];
+        k[j] = k[jp];
+        k[jp] = t;
+        if (PAY) {
+          const int u = p[j];
+          p[j] = p[jp];
+          p[jp] = u;
+        }
+      }
+    }
+  }
+}
+
+template <int E, bool PAY>
+__device__ __forceinline__ void warp_bitonic_regs(unsigned long long (&k)[E], int (&p)[E],
+                                                  int lane) {
+  static_assert(E == 1 || E == 2 || E == 4 || E == 8, "E: 1, 2, 4 or 8 keys per lane");
+#pragma unroll 1
+  for (int sz = 2; sz <= 32 * E; sz <<= 1) {
+#pragma unroll 1
+    for (int st = sz >> 1; st > 0; st >>= 1) {
+      if (st >= 128) {
+        bitonic_in_lane<E, 4, PAY>(k, p, sz, lane);
+      } else if (st == 64) {
+        bitonic_in_lane<E, 2, PAY>(k, p, sz, lane);
+      } else if (st == 32) {
+        bitonic_in_lane<E, 1, PAY>(k, p, sz, lane);
+      } else {
+        const bool low = (lane & st) == 0;
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+          const unsigned long long o = __shfl_xor_sync(0xffffffffu, k[j], st);
+          const int op = PAY ? __shfl_xor_sync(0xffffffffu, p[j], st) : 0;
+          const bool up = (((j << 5) | lane) & sz) == 0;
+          if (low == up ? o < k[j] : o > k[j]) {
+            k[j] = o;
+            if (PAY) p[j] = op;
+          }
+        }
+      }
+    }
+  }
+}
+
+// Loads the n <= 32 E keys src[0..n) (padded with ~0), sorts them in
+// registers and stores the first nst of them in order to dst (shared or
+// global memory); with PAY also the payloads (psrc, padded with -1) to pdst.
+template <int E, bool PAY>
+__device__ __forceinline__ void warp_sort_list(const unsigned long long *__restrict__ src,
+                                               const unsigned *__restrict__ psrc, int n,
+                                               unsigned long long *dst, int *pdst, int nst,
+                                               int lane) {
+  unsigned long long k[E];
+  int p[E];
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    const int i = (j << 5) | lane;
+    k[j] = i < n ? src[i] : ~0ull;
+    p[j] = (PAY && i < n) ? (int)psrc[i] : -1;
+  }
+  warp_bitonic_regs<E, PAY>(k, p, lane);
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    const int i = (j << 5) | lane;
+    if (i < nst) {
+      dst[i] = k[j];
+      if (PAY) pdst[i] = p[j];
+    }
+  }
+  __syncwarp();
+}
+
 __device__ __forceinline__ float4 seg_identity() { return make_float4(1.f, 0.f, 0.f, 0.f); }
 
 // Eq. 2.14: (A2, B2) (+) (A1, B1) = (A2 A1, B2 + A2 B1), n = nearer, f = farther.

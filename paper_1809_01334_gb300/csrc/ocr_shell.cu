@@ -215,6 +215,51 @@ __device__ float4 resolve_overlap(float4 N, float2 in, float4 F, float2 iF) {
   return r;
 }
 
+// Sorts every ray's list in place by its key (entry depth, then tree and
+// Morton key through the leaf index): one warp per ray, in registers for lists
+// of up to 256 keys, else bitonic in shared memory (cap keys per warp).
+__global__ void __launch_bounds__(256)
+    shell_sort_lists_kernel(const long long *__restrict__ ray_off, long long npix,
+                            unsigned long long *keys, long long key_cap, int cap) {
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned long long *key = reinterpret_cast<unsigned long long *>(s_raw) + (size_t)wid * cap;
+  const long long nwarp = (long long)gridDim.x * nw;
+  for (long long pix = (long long)blockIdx.x * nw + wid; pix < npix; pix += nwarp) {
+    const long long h0 = ray_off[pix];
+    const int n = (int)(ray_off[pix + 1] - h0);
+    if (n < 2 || n > cap || h0 + n > key_cap) continue;  // the render counts the bad ones
+    unsigned long long *lst = keys + h0;
+    if (n <= 32) warp_sort_list<1, false>(lst, nullptr, n, lst, nullptr, n, lane);
+    else if (n <= 64) warp_sort_list<2, false>(lst, nullptr, n, lst, nullptr, n, lane);
+    else if (n <= 128) warp_sort_list<4, false>(lst, nullptr, n, lst, nullptr, n, lane);
+    else if (n <= 256) warp_sort_list<8, false>(lst, nullptr, n, lst, nullptr, n, lane);
+    else {
+      int P = 512;
+      while (P < n) P <<= 1;
+      for (int k = lane; k < P; k += 32) key[k] = k < n ? lst[k] : ~0ull;
+      __syncwarp();
+      for (int sz = 2; sz <= P; sz <<= 1)
+        for (int st = sz >> 1; st > 0; st >>= 1) {
+          for (int k = lane; k < P; k += 32) {
+            const int m = k ^ st;
+            if (m > k) {
+              const bool up = (k & sz) == 0;
+              const unsigned long long a = key[k], b = key[m];
+              if ((a > b) == up) {
+                key[k] = b;
+                key[m] = a;
+              }
+            }
+          }
+          __syncwarp();
+        }
+      for (int k = lane; k < n; k += 32) lst[k] = key[k];
+      __syncwarp();
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256, 2)
     shell_rays_kernel(const int4 *__restrict__ geo, int N, Shell S, Field Fd, Cam c, Integ I,
                                   const long long *__restrict__ ray_off, long long npix,
@@ -255,25 +300,8 @@ __global__ void __launch_bounds__(256, 2)
       }
       continue;
     }
-    int P = 32;
-    while (P < n) P <<= 1;
-    for (int k = lane; k < P; k += 32) key[k] = k < n ? keys[h0 + k] : ~0ull;
+    for (int k = lane; k < n; k += 32) key[k] = keys[h0 + k];  // sorted by shell_sort_lists
     __syncwarp();
-    for (int sz = 2; sz <= P; sz <<= 1)  // bitonic sort, nearest first
-      for (int st = sz >> 1; st > 0; st >>= 1) {
-        for (int k = lane; k < P; k += 32) {
-          const int m = k ^ st;
-          if (m > k) {
-            const bool up = (k & sz) == 0;
-            const unsigned long long a = key[k], b = key[m];
-            if ((a > b) == up) {
-              key[k] = b;
-              key[m] = a;
-            }
-          }
-        }
-        __syncwarp();
-      }
     const int i = (int)(pix % c.w), j = (int)(pix / c.w);
     float3 org, dir;
     pixel_ray(c, i, j, org, dir);
@@ -385,20 +413,44 @@ size_t shell_ray_smem(int cap, int want) {
   return (size_t)shell_ray_warps(cap, want) * cap * (sizeof(float4) + sizeof(unsigned long long));
 }
 
+// warps per CTA of the sort kernel and its shared memory (only lists of more
+// than 256 keys use it): within 96 KB
+static int sort_warps(int cap) {
+  if (cap <= 256) return 8;
+  const int w = (int)((96u << 10) / ((size_t)cap * sizeof(unsigned long long)));
+  return w < 1 ? 1 : (w > 8 ? 8 : w);
+}
+
+static size_t sort_smem(int cap) {
+  return cap <= 256 ? 0 : (size_t)sort_warps(cap) * cap * sizeof(unsigned long long);
+}
+
 cudaError_t shell_rays_prepare() {
-  size_t most = 0;  // the largest launch any list capacity asks for
-  for (int cap = 32; cap <= kShellMaxCap; cap <<= 1)
+  size_t most = 0, most_sort = 0;  // the largest launch any list capacity asks for
+  for (int cap = 32; cap <= kShellMaxCap; cap <<= 1) {
     most = most > shell_ray_smem(cap, 0) ? most : shell_ray_smem(cap, 0);
-  return cudaFuncSetAttribute(shell_rays_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)most);
+    most_sort = most_sort > sort_smem(cap) ? most_sort : sort_smem(cap);
+  }
+  cudaError_t e = cudaFuncSetAttribute(shell_rays_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(shell_sort_lists_kernel,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most_sort);
 }
 
 cudaError_t shell_rays(const int4 *geo, int N, const Shell &S, const Field &Fd, const Cam &C,
                        const Integ &I, const long long *ray_off, long long npix,
-                       const unsigned long long *keys, long long key_cap, int cap, float4 *rgba,
+                       unsigned long long *keys, long long key_cap, int cap, float4 *rgba,
                        int *counts, unsigned long long *stats, int nsm, int want_warps,
                        cudaStream_t st) {
   if (cap < 32 || cap > kShellMaxCap || (cap & (cap - 1))) return cudaErrorInvalidValue;
+  {
+    const int warps = sort_warps(cap);
+    const long long need = (npix + warps - 1) / warps;
+    const long long grid = need < (long long)nsm * 16 ? need : (long long)nsm * 16;
+    shell_sort_lists_kernel<<<(unsigned)(grid > 0 ? grid : 1), warps * 32, sort_smem(cap), st>>>(
+        ray_off, npix, keys, key_cap, cap);
+  }
   const size_t smem = shell_ray_smem(cap, want_warps);
   const int warps = shell_ray_warps(cap, want_warps);
   const long long need = (npix + warps - 1) / warps;
