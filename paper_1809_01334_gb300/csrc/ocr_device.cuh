@@ -10,11 +10,11 @@ namespace {
 constexpr float kOne = 1.0f;
 
 // Ascending bitonic sort of P = 32 E keys (E <= 8) held by one warp in
-// registers: lane l holds the keys of indices j 32 + l (j < E).  Stages whose
-// partner index differs in bits >= 5 compare two of a lane's own registers;
-// the others swap with lane l ^ st by shuffles.  With PAY the int payload p
-// moves along.  The stage loops stay loops (small code); only the loops over
-// a lane's E registers are unrolled.
+// registers, blocked: lane l holds the keys of indices l E + j (j < E).
+// Stages whose partner index differs in a bit below E compare two of a lane's
+// own registers; the others swap with lane l ^ (st / E) by shuffles.  With
+// PAY the int payload p moves along.  The stage loops stay loops (small
+// code); only the loops over a lane's E registers are unrolled.
 template <int E, int JS, bool PAY>
 __device__ __forceinline__ void bitonic_in_lane(unsigned long long (&k)[E], int (&p)[E], int sz,
                                                 int lane) {
@@ -22,7 +22,7 @@ __device__ __forceinline__ void bitonic_in_lane(unsigned long long (&k)[E], int 
   for (int j = 0; j < E; ++j) {
     const int jp = j ^ JS;
     if (jp > j && jp < E) {
-      const bool up = (((j << 5) | lane) & sz) == 0;
+      const bool up = ((lane * E + j) & sz) == 0;
       if ((k[j] > k[jp]) == up) {
         const unsigned long long t = k[j];
         k[j] = k[jp];
@@ -45,19 +45,18 @@ __device__ __forceinline__ void warp_bitonic_regs(unsigned long long (&k)[E], in
   for (int sz = 2; sz <= 32 * E; sz <<= 1) {
 #pragma unroll 1
     for (int st = sz >> 1; st > 0; st >>= 1) {
-      if (st >= 128) {
-        bitonic_in_lane<E, 4, PAY>(k, p, sz, lane);
-      } else if (st == 64) {
-        bitonic_in_lane<E, 2, PAY>(k, p, sz, lane);
-      } else if (st == 32) {
-        bitonic_in_lane<E, 1, PAY>(k, p, sz, lane);
+      if (st < E) {
+        if (st == 4) bitonic_in_lane<E, 4, PAY>(k, p, sz, lane);
+        else if (st == 2) bitonic_in_lane<E, 2, PAY>(k, p, sz, lane);
+        else bitonic_in_lane<E, 1, PAY>(k, p, sz, lane);
       } else {
-        const bool low = (lane & st) == 0;
+        const int ls = st / E;
+        const bool low = (lane & ls) == 0;
 #pragma unroll
         for (int j = 0; j < E; ++j) {
-          const unsigned long long o = __shfl_xor_sync(0xffffffffu, k[j], st);
-          const int op = PAY ? __shfl_xor_sync(0xffffffffu, p[j], st) : 0;
-          const bool up = (((j << 5) | lane) & sz) == 0;
+          const unsigned long long o = __shfl_xor_sync(0xffffffffu, k[j], ls);
+          const int op = PAY ? __shfl_xor_sync(0xffffffffu, p[j], ls) : 0;
+          const bool up = ((lane * E + j) & sz) == 0;
           if (low == up ? o < k[j] : o > k[j]) {
             k[j] = o;
             if (PAY) p[j] = op;
@@ -80,14 +79,14 @@ __device__ __forceinline__ void warp_sort_list(const unsigned long long *__restr
   int p[E];
 #pragma unroll
   for (int j = 0; j < E; ++j) {
-    const int i = (j << 5) | lane;
+    const int i = lane * E + j;
     k[j] = i < n ? src[i] : ~0ull;
     p[j] = (PAY && i < n) ? (int)psrc[i] : -1;
   }
   warp_bitonic_regs<E, PAY>(k, p, lane);
 #pragma unroll
   for (int j = 0; j < E; ++j) {
-    const int i = (j << 5) | lane;
+    const int i = lane * E + j;
     if (i < nst) {
       dst[i] = k[j];
       if (PAY) pdst[i] = p[j];
