@@ -179,9 +179,10 @@ __global__ void __launch_bounds__(kPairThreads)
     }
     leaf = lo;
     const int4 r = rect[leaf];
-    const long long local = p - leaf_off[leaf];
-    const int rw = r.y - r.x + 1;
-    const int i = r.x + (int)(local % rw), j = r.z + (int)(local / rw);
+    // the pair's place in the rectangle: below w h < 2^31, 32-bit division
+    const unsigned local = (unsigned)(p - leaf_off[leaf]);
+    const unsigned rw = (unsigned)(r.y - r.x + 1), row = local / rw;
+    const int i = r.x + (int)(local - row * rw), j = r.z + (int)row;
     pix = (long long)j * c.w + i;
     const float4 g = dL[pix];
     if (g.x != 0.f || g.y != 0.f || g.z != 0.f || g.w != 0.f) {  // else no gradient on this ray

@@ -9,7 +9,7 @@ namespace {
 
 constexpr float kOne = 1.0f;
 
-// Ascending bitonic sort of P = 32 E keys (E <= 8) held by one warp in
+// Ascending bitonic sort of P = 32 E keys (E <= 16) held by one warp in
 // registers, blocked: lane l holds the keys of indices l E + j (j < E).
 // Stages whose partner index differs in a bit below E compare two of a lane's
 // own registers; the others swap with lane l ^ (st / E) by shuffles.  With
@@ -40,24 +40,27 @@ __device__ __forceinline__ void bitonic_in_lane(unsigned long long (&k)[E], int 
 template <int E, bool PAY>
 __device__ __forceinline__ void warp_bitonic_regs(unsigned long long (&k)[E], int (&p)[E],
                                                   int lane) {
-  static_assert(E == 1 || E == 2 || E == 4 || E == 8, "E: 1, 2, 4 or 8 keys per lane");
+  static_assert(E == 1 || E == 2 || E == 4 || E == 8 || E == 16, "E: 1 to 16 keys per lane");
 #pragma unroll 1
   for (int sz = 2; sz <= 32 * E; sz <<= 1) {
 #pragma unroll 1
     for (int st = sz >> 1; st > 0; st >>= 1) {
       if (st < E) {
-        if (st == 4) bitonic_in_lane<E, 4, PAY>(k, p, sz, lane);
+        if (st == 8) bitonic_in_lane<E, 8, PAY>(k, p, sz, lane);
+        else if (st == 4) bitonic_in_lane<E, 4, PAY>(k, p, sz, lane);
         else if (st == 2) bitonic_in_lane<E, 2, PAY>(k, p, sz, lane);
         else bitonic_in_lane<E, 1, PAY>(k, p, sz, lane);
       } else {
+        // sz >= 2 E here, so the direction is the same for all of a lane's
+        // registers; keys are distinct (padding aside, which may swap with
+        // itself), so "take the partner's key" is (o < k) == keep_min
         const int ls = st / E;
-        const bool low = (lane & ls) == 0;
+        const bool keep_min = ((lane & ls) == 0) == (((lane * E) & sz) == 0);
 #pragma unroll
         for (int j = 0; j < E; ++j) {
           const unsigned long long o = __shfl_xor_sync(0xffffffffu, k[j], ls);
           const int op = PAY ? __shfl_xor_sync(0xffffffffu, p[j], ls) : 0;
-          const bool up = ((lane * E + j) & sz) == 0;
-          if (low == up ? o < k[j] : o > k[j]) {
+          if ((o < k[j]) == keep_min) {
             k[j] = o;
             if (PAY) p[j] = op;
           }

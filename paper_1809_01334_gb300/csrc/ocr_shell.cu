@@ -121,9 +121,10 @@ __global__ void __launch_bounds__(kPairChunk)
     }
     leaf = lo;
     const int4 r = rect[leaf];
-    const long long local = p - leaf_off[leaf];
-    const int rw = r.y - r.x + 1;
-    const int i = r.x + (int)(local % rw), j = r.z + (int)(local / rw);
+    // the pair's place in the rectangle: below w h < 2^31, 32-bit division
+    const unsigned local = (unsigned)(p - leaf_off[leaf]);
+    const unsigned rw = (unsigned)(r.y - r.x + 1), row = local / rw;
+    const int i = r.x + (int)(local - row * rw), j = r.z + (int)row;
     pix = (long long)j * c.w + i;
     float3 org, dir;
     pixel_ray(c, i, j, org, dir);
@@ -217,7 +218,7 @@ __device__ float4 resolve_overlap(float4 N, float2 in, float4 F, float2 iF) {
 
 // Sorts every ray's list in place by its key (entry depth, then tree and
 // Morton key through the leaf index): one warp per ray, in registers for lists
-// of up to 256 keys, else bitonic in shared memory (cap keys per warp).
+// of up to 512 keys, else bitonic in shared memory (cap keys per warp).
 __global__ void __launch_bounds__(256)
     shell_sort_lists_kernel(const long long *__restrict__ ray_off, long long npix,
                             unsigned long long *keys, long long key_cap, int cap) {
@@ -234,8 +235,9 @@ __global__ void __launch_bounds__(256)
     else if (n <= 64) warp_sort_list<2, false>(lst, nullptr, n, lst, nullptr, n, lane);
     else if (n <= 128) warp_sort_list<4, false>(lst, nullptr, n, lst, nullptr, n, lane);
     else if (n <= 256) warp_sort_list<8, false>(lst, nullptr, n, lst, nullptr, n, lane);
+    else if (n <= 512) warp_sort_list<16, false>(lst, nullptr, n, lst, nullptr, n, lane);
     else {
-      int P = 512;
+      int P = 1024;
       while (P < n) P <<= 1;
       for (int k = lane; k < P; k += 32) key[k] = k < n ? lst[k] : ~0ull;
       __syncwarp();
@@ -414,15 +416,15 @@ size_t shell_ray_smem(int cap, int want) {
 }
 
 // warps per CTA of the sort kernel and its shared memory (only lists of more
-// than 256 keys use it): within 96 KB
+// than 512 keys use it): within 96 KB
 static int sort_warps(int cap) {
-  if (cap <= 256) return 8;
+  if (cap <= 512) return 8;
   const int w = (int)((96u << 10) / ((size_t)cap * sizeof(unsigned long long)));
   return w < 1 ? 1 : (w > 8 ? 8 : w);
 }
 
 static size_t sort_smem(int cap) {
-  return cap <= 256 ? 0 : (size_t)sort_warps(cap) * cap * sizeof(unsigned long long);
+  return cap <= 512 ? 0 : (size_t)sort_warps(cap) * cap * sizeof(unsigned long long);
 }
 
 cudaError_t shell_rays_prepare() {
