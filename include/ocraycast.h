@@ -231,14 +231,17 @@ int ocr_prune_noalloc(const int32_t *d_leaf_geo, int64_t nleaves, int max_level,
  * (cube) or [nleaves*27] (shell) and d_grad_tf [8*4] float32 (device) are
  * overwritten with dL/d(nodal) and dL/d(knots).  Segments are recomputed, not
  * taken from a previous render.  Cube: each ray's segments are put in
- * front-to-back order by their mirrored Morton key; a ray with more than 512
+ * front-to-back order by their mirrored Morton key; a ray with more than 4096
  * segments is skipped and reported as OCR_ERR_DEVICE.  Shell: the render's
  * per-ray lists are rebuilt in the first camera's scratch (so a backward call
  * must not overlap a render of the same forest on another stream) and ordered
  * by entry depth; overlapping rounding slivers are combined as if they did
- * not overlap.  RK4 and DOPRI5 only (OCR_ERR_UNSUPPORTED otherwise).  Blocks
- * the host (cube: three times, for the sizes of the pair space and of the hit
- * lists and the error word; shell: once, for the error word). */
+ * not overlap.  More than 2^32 - 2 segments in all: OCR_ERR_UNSUPPORTED.  The
+ * library keeps 32 B of scratch per segment for the adjoint (grown on demand,
+ * OCR_ERR_OOM if that fails).  RK4 and DOPRI5 only (OCR_ERR_UNSUPPORTED
+ * otherwise).  Blocks the host (cube: three times, for the sizes of the pair
+ * space and of the hit lists and the error word; shell: once, for the error
+ * word). */
 int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_nodal,
                         float *d_grad_tf, void *stream);
 

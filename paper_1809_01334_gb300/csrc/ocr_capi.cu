@@ -39,6 +39,7 @@ struct CamPlan {
   long long *d_leaf_off = nullptr;    // [N + 1]
   long long *d_sbsums = nullptr;      // [bs_cap]
   int *d_pchunk = nullptr;            // [npairs / kPairChunk + 2]
+  unsigned *d_pmask = nullptr;        // [npairs / kPairChunk + 1] x 8: pairs that hit
   int *d_rcount = nullptr, *d_rcursor = nullptr;  // [npix]
   long long *d_ray_off = nullptr;     // [npix + 1]
   unsigned long long *d_keys = nullptr;  // [nhits]
@@ -157,7 +158,8 @@ int dev_alloc(T **p, size_t n, int64_t &bytes) {
 // free one plan's device scratch (its camera and sizes stay)
 void free_plan_buffers(ocr_forest *F, CamPlan &P) {
   void *bufs[] = {P.d_rect, P.d_off, P.d_bsums, P.d_gslots, P.d_chunk, P.d_entries, P.d_leaf_off,
-                  P.d_sbsums, P.d_pchunk, P.d_rcount, P.d_rcursor, P.d_ray_off, P.d_keys};
+                  P.d_sbsums, P.d_pchunk, P.d_pmask, P.d_rcount, P.d_rcursor, P.d_ray_off,
+                  P.d_keys};
   for (void *b : bufs) cudaFree(b);
   P.d_rect = nullptr;
   P.d_off = nullptr;
@@ -168,6 +170,7 @@ void free_plan_buffers(ocr_forest *F, CamPlan &P) {
   P.d_leaf_off = nullptr;
   P.d_sbsums = nullptr;
   P.d_pchunk = nullptr;
+  P.d_pmask = nullptr;
   P.d_rcount = nullptr;
   P.d_rcursor = nullptr;
   P.d_ray_off = nullptr;
@@ -380,12 +383,15 @@ int plan_shell(ocr_forest *F, CamPlan &P) {
   OCR_CUDA(cudaMemcpyAsync(h, P.d_leaf_off + F->N, sizeof(long long), cudaMemcpyDeviceToHost, 0));
   OCR_CUDA(cudaStreamSynchronize(0));
   P.npairs = h[0];
-  if ((rc = dev_alloc(&P.d_pchunk, (size_t)(P.npairs / kPairChunk + 2), F->bytes))) return rc;
+  if ((rc = dev_alloc(&P.d_pchunk, (size_t)(P.npairs / kPairChunk + 2), F->bytes)) ||
+      (rc = dev_alloc(&P.d_pmask, (size_t)(P.npairs / kPairChunk + 1) * (kPairChunk / 32),
+                      F->bytes)))
+    return rc;
   OCR_CUDA(bwd_chunk_map(P.d_leaf_off, F->N, P.d_pchunk, 0));
   OCR_CUDA(cudaMemsetAsync(P.d_rcount, 0, sizeof(int) * (size_t)npix, 0));
   OCR_CUDA(shell_pairs(0, F->d_geo, F->N, F->shell, P.cam, P.d_rect, P.d_leaf_off,
                        P.d_pchunk, P.npairs, P.d_rcount, nullptr, nullptr, nullptr, 0,
-                       F->d_stats, 0));
+                       F->d_stats, P.d_pmask, 0));
   OCR_CUDA(bwd_count_scan(P.d_rcount, npix, P.d_sbsums, P.bs_cap, P.d_ray_off, 0));
   OCR_CUDA(cudaMemcpyAsync(h, P.d_ray_off + npix, sizeof(long long), cudaMemcpyDeviceToHost, 0));
   OCR_CUDA(cudaMemcpyAsync(h + 1, F->d_stats + kStatMaxHits, sizeof(long long),
@@ -412,18 +418,19 @@ int enqueue_shell_lists(ocr_forest *F, CamPlan &P, unsigned char *visible, cudaS
   OCR_CUDA(cudaMemsetAsync(P.d_rcount, 0, sizeof(int) * (size_t)npix, st));
   OCR_CUDA(shell_pairs(0, F->d_geo, F->N, F->shell, P.cam, P.d_rect, P.d_leaf_off,
                        P.d_pchunk, P.npairs, P.d_rcount, nullptr, nullptr, nullptr, 0, nullptr,
-                       st));
+                       P.d_pmask, st));
   OCR_CUDA(bwd_count_scan(P.d_rcount, npix, P.d_sbsums, P.bs_cap, P.d_ray_off, st));
   OCR_CUDA(cudaMemsetAsync(P.d_rcursor, 0, sizeof(int) * (size_t)npix, st));
   if (adjoint) {
     OCR_CUDA(cudaMemsetAsync(F->d_lmcount, 0, sizeof(unsigned long long), st));
     OCR_CUDA(shell_pairs(2, F->d_geo, F->N, F->shell, P.cam, P.d_rect, P.d_leaf_off,
                          P.d_pchunk, P.npairs, nullptr, P.d_ray_off, P.d_rcursor, P.d_keys,
-                         P.nhits, F->d_stats, st, F->d_skpos, F->d_slm, F->d_lmcount));
+                         P.nhits, F->d_stats, P.d_pmask, st, F->d_skpos, F->d_slm,
+                         F->d_lmcount));
   } else {
     OCR_CUDA(shell_pairs(1, F->d_geo, F->N, F->shell, P.cam, P.d_rect, P.d_leaf_off,
                          P.d_pchunk, P.npairs, nullptr, P.d_ray_off, P.d_rcursor, P.d_keys,
-                         P.nhits, F->d_stats, st));
+                         P.nhits, F->d_stats, P.d_pmask, st));
   }
   return OCR_OK;
 }

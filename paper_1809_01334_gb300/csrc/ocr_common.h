@@ -166,18 +166,21 @@ cudaError_t bwd_cube_adjoint(const Topo &T, const Field &Fd, const Cam &C, const
 // Cubed-sphere shell (ocr_shell.cu)
 cudaError_t shell_cull(const int4 *geo, int N, const Shell &S, const Cam &C, int4 *rect,
                        unsigned char *visible, unsigned long long *stats, cudaStream_t st);
-// mode 0, the count pass: segments per ray into counts, and, when stats is
-// given, the longest list into stats[kStatMaxHits]; mode 1, the fill pass: the
-// keys, at most key_cap of them (a list that would pass key_cap is a device
-// error); mode 2: the fill pass that also appends every segment to the
-// leaf-grouped list lm (pixel, 2 leaf + piece) through the counter *lm_count
-// (zeroed by the caller) and stores its index there in kpos beside the key
+// mode 0, the count pass: segments per ray into counts, which pairs hit into
+// hitmask (one bit per pair, [ceil(npairs / kPairChunk) * kPairChunk / 32]
+// words), and, when stats is given, the longest list into
+// stats[kStatMaxHits]; mode 1, the fill pass over the pairs that hit (the
+// count pass's mask): the keys, at most key_cap of them (a list that would
+// pass key_cap is a device error); mode 2: the fill pass that also appends
+// every segment to the leaf-grouped list lm (pixel, 2 leaf + piece) through
+// the counter *lm_count (zeroed by the caller) and stores its index there in
+// kpos beside the key
 cudaError_t shell_pairs(int mode, const int4 *geo, int N, const Shell &S, const Cam &C,
                         const int4 *rect, const long long *leaf_off, const int *chunk_leaf,
                         long long npairs, int *counts, const long long *ray_off, int *cursor,
                         unsigned long long *keys, long long key_cap, unsigned long long *stats,
-                        cudaStream_t st, unsigned *kpos = nullptr, int2 *lm = nullptr,
-                        unsigned long long *lm_count = nullptr);
+                        unsigned *hitmask, cudaStream_t st, unsigned *kpos = nullptr,
+                        int2 *lm = nullptr, unsigned long long *lm_count = nullptr);
 // per-CTA warps and dynamic shared memory of shell_rays for rays of up to cap
 // segments (cap a power of two, 32..kShellMaxCap); shell_rays_prepare raises the
 // kernel's shared-memory limit to the largest of these and must run before the

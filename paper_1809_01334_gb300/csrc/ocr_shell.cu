@@ -94,10 +94,12 @@ __global__ void __launch_bounds__(256)
 }
 
 // ------------------------------------------------------- segment lists --
-// MODE 0 counts segments per ray; MODE 1 writes the keys; MODE 2 also appends
-// every segment to a list grouped by leaf (one global append per CTA, whose
-// pairs are consecutive in leaf order): lm[pos] = (pixel, 2 leaf + piece), and
-// kpos[at] = pos beside the key, for the adjoint.
+// MODE 0 counts segments per ray and records which pairs hit (one ballot word
+// per warp in hitmask); MODE 1 writes the keys, intersecting only the pairs
+// that hit (packed to the CTA's first threads, in pair order); MODE 2 also
+// appends every segment to a list grouped by leaf (one global append per CTA,
+// whose pairs are consecutive in leaf order): lm[pos] = (pixel, 2 leaf +
+// piece), and kpos[at] = pos beside the key, for the adjoint.
 template <int MODE>
 __global__ void __launch_bounds__(kPairChunk)
     shell_pairs_kernel(const int4 *__restrict__ geo, int N, Shell S, Cam c,
@@ -105,13 +107,39 @@ __global__ void __launch_bounds__(kPairChunk)
                        const int *__restrict__ chunk_leaf, long long npairs, int *counts,
                        const long long *__restrict__ ray_off, int *cursor,
                        unsigned long long *keys, long long key_cap, unsigned long long *stats,
-                       unsigned *kpos, int2 *lm, unsigned long long *lm_count) {
-  const long long p = (long long)blockIdx.x * kPairChunk + threadIdx.x;
-  if (MODE != 2 && p >= npairs) return;
+                       unsigned *hitmask, unsigned *kpos, int2 *lm,
+                       unsigned long long *lm_count) {
+  constexpr int NW = kPairChunk / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int t = threadIdx.x;  // the chunk's pair this thread intersects
+  bool has = true;
+  if (MODE != 0) {
+    __shared__ unsigned short s_idx[kPairChunk];
+    __shared__ int s_h[NW + 1];
+    const unsigned word = hitmask[(size_t)blockIdx.x * NW + wid];
+    if (lane == 0) s_h[wid] = __popc(word);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int w = 0; w < NW; ++w) {
+        const int h = s_h[w];
+        s_h[w] = tot;
+        tot += h;
+      }
+      s_h[NW] = tot;
+    }
+    __syncthreads();
+    if ((word >> lane) & 1u)
+      s_idx[s_h[wid] + __popc(word & ((1u << lane) - 1u))] = (unsigned short)threadIdx.x;
+    __syncthreads();
+    has = (int)threadIdx.x < s_h[NW];
+    t = has ? s_idx[threadIdx.x] : 0;
+  }
+  const long long p = (long long)blockIdx.x * kPairChunk + t;
   int n = 0, leaf = 0;
   long long pix = 0;
   float ai[2], ao[2];
-  if (p < npairs) {
+  if (has && p < npairs) {
     const long long nch = (npairs + kPairChunk - 1) / kPairChunk;
     int lo = chunk_leaf[blockIdx.x];
     int hi = (blockIdx.x + 1 < nch) ? chunk_leaf[blockIdx.x + 1] + 1 : N;
@@ -130,10 +158,15 @@ __global__ void __launch_bounds__(kPairChunk)
     pixel_ray(c, i, j, org, dir);
     n = shell_ray_leaf(leaf_shell(S, __ldg(geo + leaf)), org, dir, c.amin, c.amax, ai, ao);
   }
+  if (MODE == 0) {
+    const unsigned bal = __ballot_sync(0xffffffffu, n > 0);
+    if (lane == 0) hitmask[(size_t)blockIdx.x * NW + wid] = bal;
+    if (n) atomicAdd(counts + pix, n);
+    return;
+  }
   unsigned pos = 0;
   if (MODE == 2) {  // this pair's place in the CTA's block of the leaf-grouped list
-    __shared__ unsigned s_w[kPairChunk / 32], s_base;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __shared__ unsigned s_w[NW], s_base;
     unsigned x = (unsigned)n;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -144,10 +177,10 @@ __global__ void __launch_bounds__(kPairChunk)
     __syncthreads();
     if (threadIdx.x == 0) {
       unsigned tot = 0;
-      for (int w = 0; w < kPairChunk / 32; ++w) {
-        const unsigned t = s_w[w];
+      for (int w = 0; w < NW; ++w) {
+        const unsigned u = s_w[w];
         s_w[w] = tot;
-        tot += t;
+        tot += u;
       }
       s_base = tot ? (unsigned)atomicAdd(lm_count, (unsigned long long)tot) : 0u;
     }
@@ -155,26 +188,21 @@ __global__ void __launch_bounds__(kPairChunk)
     pos = s_base + s_w[wid] + x - (unsigned)n;
   }
   if (!n) return;
-  if (MODE == 0) {
-    atomicAdd(counts + pix, n);
-  } else {
-    const long long at = ray_off[pix] + atomicAdd(cursor + pix, n);
-    const bool bad = at + n > key_cap || at + n > ray_off[pix + 1] ||
-                     (MODE == 2 && (long long)pos + n > key_cap);
-    if (bad) {  // more than counted and planned
-      atomicAdd(stats + kStatErrors, 1ull);
-      if (MODE == 2)
-        for (int t = 0; t < n; ++t)
-          if ((long long)pos + t < key_cap) lm[pos + t] = make_int2(-1, -1);
-      return;
-    }
-    for (int t = 0; t < n; ++t) {  // alpha_in >= 0: its bits sort like the value
-      keys[at + t] = (unsigned long long)__float_as_uint(ai[t]) << 32 |
-                     (unsigned)(2 * leaf + t);
-      if (MODE == 2) {
-        kpos[at + t] = pos + (unsigned)t;
-        lm[pos + t] = make_int2((int)pix, 2 * leaf + t);
-      }
+  const long long at = ray_off[pix] + atomicAdd(cursor + pix, n);
+  const bool bad = at + n > key_cap || at + n > ray_off[pix + 1] ||
+                   (MODE == 2 && (long long)pos + n > key_cap);
+  if (bad) {  // more than counted and planned
+    atomicAdd(stats + kStatErrors, 1ull);
+    if (MODE == 2)
+      for (int q = 0; q < n; ++q)
+        if ((long long)pos + q < key_cap) lm[pos + q] = make_int2(-1, -1);
+    return;
+  }
+  for (int q = 0; q < n; ++q) {  // alpha_in >= 0: its bits sort like the value
+    keys[at + q] = (unsigned long long)__float_as_uint(ai[q]) << 32 | (unsigned)(2 * leaf + q);
+    if (MODE == 2) {
+      kpos[at + q] = pos + (unsigned)q;
+      lm[pos + q] = make_int2((int)pix, 2 * leaf + q);
     }
   }
 }
@@ -374,8 +402,9 @@ cudaError_t shell_pairs(int mode, const int4 *geo, int N, const Shell &S, const 
                         const int4 *rect, const long long *leaf_off, const int *chunk_leaf,
                         long long npairs, int *counts, const long long *ray_off, int *cursor,
                         unsigned long long *keys, long long key_cap, unsigned long long *stats,
-                        cudaStream_t st, unsigned *kpos, int2 *lm, unsigned long long *lm_count) {
-  if (mode < 0 || mode > 2 || (mode == 2 && (!kpos || !lm || !lm_count)))
+                        unsigned *hitmask, cudaStream_t st, unsigned *kpos, int2 *lm,
+                        unsigned long long *lm_count) {
+  if (mode < 0 || mode > 2 || !hitmask || (mode == 2 && (!kpos || !lm || !lm_count)))
     return cudaErrorInvalidValue;
   if (npairs > 0) {
     const long long nblk = (npairs + kPairChunk - 1) / kPairChunk;
@@ -383,15 +412,15 @@ cudaError_t shell_pairs(int mode, const int4 *geo, int N, const Shell &S, const 
     if (mode == 0)
       shell_pairs_kernel<0><<<(unsigned)nblk, kPairChunk, 0, st>>>(
           geo, N, S, C, rect, leaf_off, chunk_leaf, npairs, counts, ray_off, cursor, keys,
-          key_cap, stats, kpos, lm, lm_count);
+          key_cap, stats, hitmask, kpos, lm, lm_count);
     else if (mode == 1)
       shell_pairs_kernel<1><<<(unsigned)nblk, kPairChunk, 0, st>>>(
           geo, N, S, C, rect, leaf_off, chunk_leaf, npairs, counts, ray_off, cursor, keys,
-          key_cap, stats, kpos, lm, lm_count);
+          key_cap, stats, hitmask, kpos, lm, lm_count);
     else
       shell_pairs_kernel<2><<<(unsigned)nblk, kPairChunk, 0, st>>>(
           geo, N, S, C, rect, leaf_off, chunk_leaf, npairs, counts, ray_off, cursor, keys,
-          key_cap, stats, kpos, lm, lm_count);
+          key_cap, stats, hitmask, kpos, lm, lm_count);
   }
   if (mode == 0 && stats) {  // the longest list, for planning
     const long long npix = (long long)C.w * C.h;

@@ -96,3 +96,45 @@ def test_autograd_l2_loss_against_perturbed_target():
         checked += 1
     assert checked >= 56
     r.close()
+
+
+def _diagonal_camera(w, h, fov_deg=12.0):
+    """Perspective camera on the cube's main diagonal, looking at its centre:
+    central rays cross about 3 x 2^L cells of a uniform level-L forest."""
+    d = np.array([1.0, 1.0, 1.0]) / np.sqrt(3.0)
+    o = np.array([0.5, 0.5, 0.5]) + 1.6 * d + np.array([0.013, -0.007, 0.004])
+    v = -d
+    up = np.array([0.0, 0.0, 1.0])
+    t = np.cross(v, up)
+    t /= np.linalg.norm(t)
+    u = np.cross(t, v)
+    near = float(np.float32(0.1))
+    ell = 2 * near * np.tan(np.radians(fov_deg / 2)) / h
+    return I.Camera(o=tuple(I._f32(o)), v=tuple(I._f32(v * near)), t=tuple(I._f32(t)),
+                    u=tuple(I._f32(u)), ell=float(np.float32(ell)), near=near, far=100.0,
+                    w=w, h=h)
+
+
+def test_long_rays_gradient():
+    """Rays with more than 256 segments (uniform level-7 cube seen along its
+    diagonal): the per-ray scans take their shared-memory sort; the gradient
+    of a loss on four rows against the oracle gradient."""
+    from paper_1809_01334_gb300 import Renderer
+    f = I.uniform_cube_forest(7, I.gaussian_field(4, 1809))
+    tf = I.transfer_function(f.nodal, 1334, kappa_max=3.0)
+    cam = _diagonal_camera(48, 36)
+    integ = {"method": "rk4", "nsteps": 2}
+    r = Renderer(f, tf, integ)
+    r.set_camera(cam)
+    _, st = r.render(with_index=True)
+    counts = st["counts"].cpu().numpy() if hasattr(st["counts"], "cpu") else np.asarray(st["counts"])
+    rows = [16, 17, 18, 19]
+    assert counts.reshape(cam.h, cam.w)[rows].max() > 256
+    W = np.zeros((cam.h, cam.w, 4), np.float32)
+    W[rows] = np.random.default_rng(11).uniform(-1, 1, (len(rows), cam.w, 4))
+    gn, gt = r.backward(torch.from_numpy(W).cuda())
+    torch.cuda.synchronize()
+    rn, rt = O.render_grad(f, tf, cam, integ, W.astype(np.float64))
+    en, et = _rel(gn.cpu().numpy().astype(np.float64), rn), _rel(gt.cpu().numpy().astype(np.float64), rt)
+    assert en <= 1e-3 and et <= 1e-3, (en, et)
+    r.close()
