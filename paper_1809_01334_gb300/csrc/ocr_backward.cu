@@ -325,8 +325,9 @@ struct SegAdj {
 };
 
 // Segment through a shell leaf: the field through the inverse map and the
-// degree-2 interpolation; the adjoint of the 27 nodal values is kept in this
-// thread's column of a shared-memory array (g27[q * stride]).
+// degree-2 polynomial (monomial coefficients); the adjoint of the 27 nodal
+// values goes through the Lagrange weights and is kept in this thread's column
+// of a shared-memory array (g27[q * stride]).
 struct ShellAdj {
   static constexpr int kUnroll = 1;
   ShellSeg g;
@@ -336,10 +337,14 @@ struct ShellAdj {
     return medium(g, tf, tau);
   }
   __device__ __forceinline__ void bwd(const TF &tf, float tau, float4 vbar, TfGrad &tg) {
-    float lu[3], lv[3], lw[3];
-    const float s = shell_field(g, tau, lu, lv, lw);
+    float u, v, w;
+    const float s = shell_field(g, tau, u, v, w);
     const float sb = tf_bwd(tf, s, vbar, tg);
     if (sb == 0.f) return;
+    float lu[3], lv[3], lw[3];  // d s / d(nodal value) = lu[a] lv[b] lw[c]
+    quad_basis(u, lu);
+    quad_basis(v, lv);
+    quad_basis(w, lw);
 #pragma unroll
     for (int cz = 0; cz < 3; ++cz)
 #pragma unroll

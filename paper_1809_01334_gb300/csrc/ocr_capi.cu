@@ -52,6 +52,7 @@ struct ocr_forest {
   int geometry = OCR_GEOM_CUBE;
   Shell shell{};                      // shell: frames and tables (in d_shell_tabs)
   float *d_shell_tabs = nullptr;      // [54 + 2 (2^L + 1)]
+  float *d_coef = nullptr;            // shell: [N * 27] the data in monomial form, per render
   int N = 0, M = 0, L = 0;
   int root = 0;                       // unified id of the tree root
   std::vector<int> level_base;        // internal index of the first node of level l
@@ -185,6 +186,7 @@ void free_plans(ocr_forest *F) {
 
 void free_all(ocr_forest *F) {
   cudaFree(F->d_shell_tabs);
+  cudaFree(F->d_coef);
   cudaFree(F->d_geo);
   cudaFree(F->d_child);
   cudaFree(F->d_leaves);
@@ -323,6 +325,7 @@ int build_shell(const ocr_forest_desc *desc, cudaStream_t st, ocr_forest **out) 
   int rc;
   if ((rc = dev_alloc(&F->d_geo, geo.size(), F->bytes)) ||
       (rc = dev_alloc(&F->d_shell_tabs, tabs.size(), F->bytes)) ||
+      (rc = dev_alloc(&F->d_coef, (size_t)F->N * 27, F->bytes)) ||
       (rc = dev_alloc(&F->d_stats, kStats, F->bytes)) ||
       (rc = dev_alloc(&F->d_err, 1, F->bytes))) {
     free_all(F);
@@ -440,7 +443,7 @@ int enqueue_shell_lists(ocr_forest *F, CamPlan &P, unsigned char *visible, cudaS
 int enqueue_shell(ocr_forest *F, CamPlan &P, float4 *rgba, int *counts, unsigned char *visible,
                   cudaStream_t st, bool timed, int64_t &launches) {
   const long long npix = P.npix;
-  const Field Fd{F->d_nodal, reinterpret_cast<const float4 *>(F->d_tf), F->s_min,
+  const Field Fd{F->d_coef, reinterpret_cast<const float4 *>(F->d_tf), F->s_min,
                  7.f / (F->s_max - F->s_min)};
   const int rc = enqueue_shell_lists(F, P, visible, st);
   if (rc) return rc;
@@ -855,8 +858,12 @@ int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats) {
   bool subtree_ran = false;
   OCR_CUDA(cudaMemsetAsync(F->d_stats, 0, kStats * sizeof(unsigned long long), st));
   float4 *rgba = reinterpret_cast<float4 *>(d_rgba);
+  if (timed) OCR_CUDA(cudaEventRecord(F->ev[0], st));
+  if (F->geometry == OCR_GEOM_SHELL) {  // this render's data in the kernels' monomial form
+    OCR_CUDA(shell_monomials(F->d_nodal, F->d_coef, F->N, st));
+    ++launches;
+  }
   if (K == 1) {
-    if (timed) OCR_CUDA(cudaEventRecord(F->ev[0], st));
     int rc = F->geometry == OCR_GEOM_SHELL
                  ? enqueue_shell(F, F->plans[0], rgba, counts, visible, st, timed, launches)
                  : enqueue_camera(F, F->plans[0], rgba, counts, visible, st, timed, subtree_ran,
@@ -983,7 +990,7 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
     // rebuild the first camera's lists with the leaf-grouped list, then the
     // values pass (one warp per ray) and the segment pass (one thread each)
     CamPlan &P = F->plans[0];
-    const Field Fd{F->d_nodal, reinterpret_cast<const float4 *>(F->d_tf), F->s_min,
+    const Field Fd{F->d_coef, reinterpret_cast<const float4 *>(F->d_tf), F->s_min,
                    7.f / (F->s_max - F->s_min)};
     if (P.nhits >= 0xffffffffll) return OCR_ERR_UNSUPPORTED;  // list indices are 32-bit
     int rc = grow_adjoint(F, P.nhits);
@@ -992,6 +999,7 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
     OCR_CUDA(cudaMemsetAsync(d_grad_tf, 0, sizeof(float) * 32, st));
     OCR_CUDA(cudaMemsetAsync(F->d_stats, 0, kStats * sizeof(unsigned long long), st));
     OCR_CUDA(cudaMemsetAsync(F->d_err, 0, sizeof(unsigned long long), st));
+    OCR_CUDA(shell_monomials(F->d_nodal, F->d_coef, F->N, st));
     rc = enqueue_shell_lists(F, P, nullptr, st, true);
     if (rc) return rc;
     const float4 *dL = reinterpret_cast<const float4 *>(d_dL_drgba);

@@ -164,6 +164,9 @@ cudaError_t bwd_cube_adjoint(const Topo &T, const Field &Fd, const Cam &C, const
                              int nsm, cudaStream_t st);
 
 // Cubed-sphere shell (ocr_shell.cu)
+// the leaves' degree-2 data (27 Lagrange nodal values each) in monomial form
+// (27 coefficients each, the polynomial the shell kernels evaluate)
+cudaError_t shell_monomials(const float *nodal, float *coef, int N, cudaStream_t st);
 cudaError_t shell_cull(const int4 *geo, int N, const Shell &S, const Cam &C, int4 *rect,
                        unsigned char *visible, unsigned long long *stats, cudaStream_t st);
 // mode 0, the count pass: segments per ray into counts, which pairs hit into

@@ -28,6 +28,38 @@
 namespace ocr {
 namespace {
 
+// ------------------------------------------------------ monomial form --
+// Per leaf: the 27 nodal values (Lagrange form on the nodes 0, 1/2, 1 per
+// axis, index 9 c + 3 b + a) to the coefficients of u^i v^j w^k at the same
+// index 9 k + 3 j + i.  Along one axis the values f0, f1, f2 at 0, 1/2, 1 give
+// p(t) = f0 + (-3 f0 + 4 f1 - f2) t + (2 f0 - 4 f1 + 2 f2) t^2.
+__device__ __forceinline__ void lagrange_to_monomial(float &f0, float &f1, float &f2) {
+  const float c1 = fmaf(-3.f, f0, fmaf(4.f, f1, -f2));
+  const float c2 = 2.f * (f0 + f2) - 4.f * f1;
+  f1 = c1;
+  f2 = c2;
+}
+
+__global__ void __launch_bounds__(256)
+    shell_monomial_kernel(const float *__restrict__ nodal, float *__restrict__ coef, int N) {
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < N; l += gridDim.x * blockDim.x) {
+    float f[27];
+#pragma unroll
+    for (int q = 0; q < 27; ++q) f[q] = __ldg(nodal + 27 * (size_t)l + q);
+#pragma unroll
+    for (int r = 0; r < 9; ++r) lagrange_to_monomial(f[3 * r], f[3 * r + 1], f[3 * r + 2]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        lagrange_to_monomial(f[9 * c + a], f[9 * c + 3 + a], f[9 * c + 6 + a]);
+#pragma unroll
+    for (int r = 0; r < 9; ++r) lagrange_to_monomial(f[r], f[9 + r], f[18 + r]);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) coef[27 * (size_t)l + q] = f[q];
+  }
+}
+
 // ----------------------------------------------------------------- culling --
 __global__ void __launch_bounds__(256)
     shell_cull_kernel(const int4 *__restrict__ geo, int N, Shell S, Cam c, int4 *rect,
@@ -391,6 +423,13 @@ __global__ void __launch_bounds__(256, 2)
 }  // namespace
 
 // ------------------------------------------------------------- launchers --
+cudaError_t shell_monomials(const float *nodal, float *coef, int N, cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  const int grid = (N + 255) / 256 > 8192 ? 8192 : (N + 255) / 256;
+  shell_monomial_kernel<<<grid, 256, 0, st>>>(nodal, coef, N);
+  return cudaGetLastError();
+}
+
 cudaError_t shell_cull(const int4 *geo, int N, const Shell &S, const Cam &C, int4 *rect,
                        unsigned char *visible, unsigned long long *stats, cudaStream_t st) {
   const int grid = (N + 255) / 256 > 8192 ? 8192 : (N + 255) / 256;

@@ -108,12 +108,15 @@ __device__ __forceinline__ int shell_ray_leaf(const LeafShell &q, float3 org, fl
 //     = (2/pi) atan2(x.e1 - ta x.n, x.n + ta x.e1) / h
 // (for fine leaves the arctangent of the small ratio by its series),
 //   w = (|x| - r_in) / (r_out - r_in),
-// then the degree-2 Lagrange interpolation of the 27 nodal values.
+// then the leaf's degree-2 tensor-product polynomial at (u, v, w).  The
+// kernels hold that polynomial in monomial form (shell_monomials converts the
+// 27 Lagrange nodal values once per render): cf[9 k + 3 j + i] multiplies
+// u^i v^j w^k, evaluated by nested Horner steps.
 struct ShellSeg {
   float pf[3], dp[3];
   float ta, tb, ka, rin, kr;
   int series;  // leaf level >= kSeriesLevel: the angles by atan_small
-  float nd[27];
+  float cf[27];
 };
 
 // Leaves of level >= kSeriesLevel span at most (pi/2) 2^-3 = pi/16 in each
@@ -133,20 +136,20 @@ __device__ __forceinline__ float atan_small(float z) {
   return z * p;
 }
 
+// Lagrange basis of degree 2 on the nodes 0, 1/2, 1 (the adjoint's weights).
 __device__ __forceinline__ void quad_basis(float t, float *l) {
   l[0] = 2.f * (t - 0.5f) * (t - 1.f);
   l[1] = -4.f * t * (t - 1.f);
   l[2] = 2.f * t * (t - 0.5f);
 }
 
-// The field value at tau and the basis values of the local coordinates.
-__device__ __forceinline__ float shell_field(const ShellSeg &g, float tau, float *lu, float *lv,
-                                             float *lw) {
+// The field value at tau and the local coordinates (u, v, w) there.
+__device__ __forceinline__ float shell_field(const ShellSeg &g, float tau, float &u, float &v,
+                                             float &w) {
   const float pn = fmaf(tau, g.dp[0], g.pf[0]), p1 = fmaf(tau, g.dp[1], g.pf[1]),
               p2 = fmaf(tau, g.dp[2], g.pf[2]);
   const float ya = fmaf(-g.ta, pn, p1), xa = fmaf(g.ta, p1, pn);
   const float yb = fmaf(-g.tb, pn, p2), xb = fmaf(g.tb, p2, pn);
-  float u, v;
   if (g.series) {
     u = atan_small(ya / xa) * g.ka;
     v = atan_small(yb / xb) * g.ka;
@@ -154,33 +157,31 @@ __device__ __forceinline__ float shell_field(const ShellSeg &g, float tau, float
     u = atan2f(ya, xa) * g.ka;
     v = atan2f(yb, xb) * g.ka;
   }
-  const float w = (sqrtf(fmaf(pn, pn, fmaf(p1, p1, p2 * p2))) - g.rin) * g.kr;
-  quad_basis(u, lu);
-  quad_basis(v, lv);
-  quad_basis(w, lw);
-  float s = 0.f;
+  w = (sqrtf(fmaf(pn, pn, fmaf(p1, p1, p2 * p2))) - g.rin) * g.kr;
+  float q[3];
 #pragma unroll
-  for (int cz = 0; cz < 3; ++cz) {
-    float sz = 0.f;
+  for (int k = 0; k < 3; ++k) {
+    float r[3];
 #pragma unroll
-    for (int by = 0; by < 3; ++by) {
-      const float *r = g.nd + 9 * cz + 3 * by;
-      sz = fmaf(lv[by], fmaf(lu[0], r[0], fmaf(lu[1], r[1], lu[2] * r[2])), sz);
+    for (int j = 0; j < 3; ++j) {
+      const float *c = g.cf + 9 * k + 3 * j;
+      r[j] = fmaf(fmaf(c[2], u, c[1]), u, c[0]);
     }
-    s = fmaf(lw[cz], sz, s);
+    q[k] = fmaf(fmaf(r[2], v, r[1]), v, r[0]);
   }
-  return s;
+  return fmaf(fmaf(q[2], w, q[1]), w, q[0]);
 }
 
 __device__ __forceinline__ float4 medium(const ShellSeg &g, const TF &tf, float tau) {
-  float lu[3], lv[3], lw[3];
-  return tf_lookup(tf, shell_field(g, tau, lu, lv, lw));
+  float u, v, w;
+  return tf_lookup(tf, shell_field(g, tau, u, v, w));
 }
 
 // The segment of the ray inside one leaf (the piece-th of its intervals):
-// its field, its world length, and the interval itself.  Returns false if the
+// its field (coef: the monomial coefficients of every leaf), its world length,
+// and the interval itself.  Returns false if the
 // ray does not have that piece.
-__device__ __forceinline__ bool shell_segment(const Shell &S, const float *__restrict__ nodal,
+__device__ __forceinline__ bool shell_segment(const Shell &S, const float *__restrict__ coef,
                                               const Cam &c, int4 geo, int leaf, int piece,
                                               float3 org, float3 dir, float rl, ShellSeg &g,
                                               float &dx, float2 &iv) {
@@ -204,9 +205,9 @@ __device__ __forceinline__ bool shell_segment(const Shell &S, const float *__res
   g.series = q.level >= kSeriesLevel;
   g.rin = q.rin;
   g.kr = 1.f / (q.rout - q.rin);
-  const float *nd = nodal + 27 * (size_t)leaf;
+  const float *cf = coef + 27 * (size_t)leaf;
 #pragma unroll
-  for (int a = 0; a < 27; ++a) g.nd[a] = __ldg(nd + a);
+  for (int a = 0; a < 27; ++a) g.cf[a] = __ldg(cf + a);
   dx = (a_out - a_in) * rl;
   iv = make_float2(a_in, a_out);
   return true;
