@@ -39,6 +39,15 @@ WORKLOAD = ("adaptive unit cube, levels 2-8 (2,053,451 leaves, 2:1 balanced, tri
 FP32_OPS_SLAB = 30
 FP32_OPS_SEGMENT = 128
 FP32_OPS_DOPRI_STEP = 234
+# The same for the shell's per-ray kernel: per segment the ray / leaf
+# intersection (four planes, two spheres), the field's set-up and its first
+# medium evaluation; per Dormand-Prince step five medium evaluations (each the
+# inverse map: two ratios and their arctangent series, the radius; 26 FMAs of
+# the monomial polynomial; the transfer function) and the same stage, error,
+# split and fold work as the cube.  Reciprocals and square roots (MUFU) are
+# not counted.
+FP32_OPS_SHELL_SEGMENT = 160
+FP32_OPS_SHELL_DOPRI_STEP = 499
 FP32_LANES_PER_SM = 128
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -287,12 +296,21 @@ def run_shell(args, dev, flush):
         phases.append(r.render(out, time_phases=True)[1])
     ms = _timed(fwd, stream, flush, 2, 5)
     rays_ms = sum(p["ms_subtree"] for p in phases[2:]) / len(phases[2:])
+    shell_ops = FP32_OPS_SHELL_SEGMENT * st["segments"] + FP32_OPS_SHELL_DOPRI_STEP * st["rk_steps"]
+    peaks, _ = measured_peaks()
+    shell_peak = (torch.cuda.get_device_properties(dev).multi_processor_count *
+                  FP32_LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12)
     c3 = {"workload": "cubed-sphere shell, 6 trees, levels 4-7 (%d leaves, degree-2 FP32 "
                       "data), perspective 45deg %dx%d, DOPRI5 tol 1e-5" % (forest.nleaves, sw, sh),
           "ms_per_render": ms, "segments": st["segments"], "rk_steps": st["rk_steps"],
           "pair_tests": st["leaf_tests"], "segments_per_s": st["segments"] / (ms * 1e-3),
           "mpixel_per_s": cam.w * cam.h / (ms * 1e-3) / 1e6, "ms_rays_kernel": rays_ms,
-          "launches": st["launches"]}
+          "launches": st["launches"],
+          "roofline": {"bound": "alu", "kernel": "shell_rays_kernel",
+                       "achieved": shell_ops / (rays_ms * 1e-3) / 1e12, "peak": shell_peak,
+                       "unit": "TFP32op/s",
+                       "frac": shell_ops / (rays_ms * 1e-3) / 1e12 / shell_peak,
+                       "fp32_ops_per_launch": shell_ops}}
     r.close()
     del out
     # differentiation on the levels 4-6 shell

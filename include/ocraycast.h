@@ -146,9 +146,11 @@ typedef struct {
   int64_t subtree_rk_steps; /* RK steps taken by the subtree pass */
   int64_t subtree_leaf_tests; /* (leaf, ray) slab tests of the subtree pass */
   int64_t launches;       /* kernels launched by this call */
-  float ms_prune;         /* pruning, rectangle unions, slot layout, host readback */
-  float ms_merge;         /* subtree pass + coarsening passes + pixel pass */
-  float ms_subtree;       /* the subtree pass alone */
+  float ms_prune;         /* cube: pruning, rectangle unions, slot layout, host readback;
+                             shell: the monomial form, pruning, the per-ray lists */
+  float ms_merge;         /* cube: subtree pass + coarsening passes + pixel pass;
+                             shell: sorting the lists + the per-ray kernel */
+  float ms_subtree;       /* cube: the subtree pass alone; shell: the per-ray kernel alone */
 } ocr_stats;
 
 /* Copy the forest topology to the device and derive its internal octree

@@ -448,6 +448,7 @@ int enqueue_shell(ocr_forest *F, CamPlan &P, float4 *rgba, int *counts, unsigned
   const int rc = enqueue_shell_lists(F, P, visible, st);
   if (rc) return rc;
   if (timed) OCR_CUDA(cudaEventRecord(F->ev[1], st));
+  OCR_CUDA(shell_sort_lists(P.d_ray_off, npix, P.d_keys, P.nhits, P.cap, F->nsm, st));
   if (timed) OCR_CUDA(cudaEventRecord(F->ev[2], st));
   OCR_CUDA(shell_rays(F->d_geo, F->N, F->shell, Fd, P.cam, F->integ, P.d_ray_off, npix, P.d_keys,
                       P.nhits, P.cap, rgba, counts, F->d_stats, F->nsm, F->shell_warps, st));

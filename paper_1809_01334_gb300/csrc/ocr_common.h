@@ -192,10 +192,12 @@ constexpr int kShellMaxCap = 4096;
 int shell_ray_warps(int cap, int want);
 size_t shell_ray_smem(int cap, int want);
 cudaError_t shell_rays_prepare();
-// (sorts every list in place, then renders: two launches)
+// every ray's list sorted in place by its key (before shell_rays)
+cudaError_t shell_sort_lists(const long long *ray_off, long long npix, unsigned long long *keys,
+                             long long key_cap, int cap, int nsm, cudaStream_t st);
 cudaError_t shell_rays(const int4 *geo, int N, const Shell &S, const Field &Fd, const Cam &C,
                        const Integ &I, const long long *ray_off, long long npix,
-                       unsigned long long *keys, long long key_cap, int cap, float4 *rgba,
+                       const unsigned long long *keys, long long key_cap, int cap, float4 *rgba,
                        int *counts, unsigned long long *stats, int nsm, int want_warps,
                        cudaStream_t st);
 

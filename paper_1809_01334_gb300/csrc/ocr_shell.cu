@@ -508,19 +508,23 @@ cudaError_t shell_rays_prepare() {
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most_sort);
 }
 
+cudaError_t shell_sort_lists(const long long *ray_off, long long npix, unsigned long long *keys,
+                             long long key_cap, int cap, int nsm, cudaStream_t st) {
+  if (cap < 32 || cap > kShellMaxCap || (cap & (cap - 1))) return cudaErrorInvalidValue;
+  const int warps = sort_warps(cap);
+  const long long need = (npix + warps - 1) / warps;
+  const long long grid = need < (long long)nsm * 16 ? need : (long long)nsm * 16;
+  shell_sort_lists_kernel<<<(unsigned)(grid > 0 ? grid : 1), warps * 32, sort_smem(cap), st>>>(
+      ray_off, npix, keys, key_cap, cap);
+  return cudaGetLastError();
+}
+
 cudaError_t shell_rays(const int4 *geo, int N, const Shell &S, const Field &Fd, const Cam &C,
                        const Integ &I, const long long *ray_off, long long npix,
-                       unsigned long long *keys, long long key_cap, int cap, float4 *rgba,
+                       const unsigned long long *keys, long long key_cap, int cap, float4 *rgba,
                        int *counts, unsigned long long *stats, int nsm, int want_warps,
                        cudaStream_t st) {
   if (cap < 32 || cap > kShellMaxCap || (cap & (cap - 1))) return cudaErrorInvalidValue;
-  {
-    const int warps = sort_warps(cap);
-    const long long need = (npix + warps - 1) / warps;
-    const long long grid = need < (long long)nsm * 16 ? need : (long long)nsm * 16;
-    shell_sort_lists_kernel<<<(unsigned)(grid > 0 ? grid : 1), warps * 32, sort_smem(cap), st>>>(
-        ray_off, npix, keys, key_cap, cap);
-  }
   const size_t smem = shell_ray_smem(cap, want_warps);
   const int warps = shell_ray_warps(cap, want_warps);
   const long long need = (npix + warps - 1) / warps;
