@@ -225,6 +225,20 @@ int ocr_prune_noalloc(const int32_t *d_leaf_geo, int64_t nleaves, int max_level,
                       const ocr_camera *cam, int32_t *d_rects, int32_t *d_visible_idx,
                       int64_t *h_nvisible, void *stream);
 
+/* Render from host memory: copy the field h_nodal (layout as in
+ * ocr_forest_set_data) and the knots h_tf [8*4] to device memory that the
+ * library owns, render every camera of the last ocr_set_camera into its own
+ * device image, copy that image to h_rgba (float32, sum of w*h*4) and return
+ * once it is there.  All work is ordered on `stream` after the caller's
+ * earlier work; the copy in overlaps the data-independent pruning and layout
+ * (cube forests).  Pinned host memory gives full copy speed; pageable memory
+ * works.  Afterwards the forest's data is the library's copy (a later
+ * ocr_forest_set_data replaces it).  s_min, s_max, stats and the error codes
+ * as in ocr_forest_set_data and ocr_render; OCR_ERR_OOM if the device copies
+ * cannot be allocated.  Blocks the host. */
+int ocr_render_host(ocr_forest *F, const float *h_nodal, const float *h_tf, float s_min,
+                    float s_max, float *h_rgba, void *stream, ocr_stats *stats);
+
 /* Gradient of a loss L(rgba) with respect to the nodal values and the
  * transfer-function knots (Sec. 2.3-2.4, Eqs. 2.14 and 2.29-2.31 in reverse
  * mode), for the forest, data, integrator and the first camera last set.

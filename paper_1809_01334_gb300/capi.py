@@ -18,7 +18,8 @@ GEOM_CUBE, GEOM_SHELL = 0, 1
 RK4, DOPRI5, GAUSS2, SIMPSON, EQUILIBRIUM = 0, 1, 2, 3, 4
 
 EXPORTS = ["ocr_build_forest", "ocr_forest_set_data", "ocr_set_integrator", "ocr_set_camera",
-           "ocr_render", "ocr_render_backward", "ocr_set_tuning", "ocr_get_tuning",
+           "ocr_render", "ocr_render_host", "ocr_render_backward", "ocr_set_tuning",
+           "ocr_get_tuning",
            "ocr_autotune", "ocr_device_bytes", "ocr_destroy", "ocr_strerror"]
 
 
@@ -80,6 +81,8 @@ def lib():
         L.ocr_set_integrator.argtypes = [vp, C.POINTER(Integrator)]
         L.ocr_set_camera.argtypes = [vp, C.POINTER(Camera), C.c_int]
         L.ocr_render.argtypes = [vp, vp, vp, C.POINTER(Stats)]
+        L.ocr_render_host.argtypes = [vp, vp, vp, C.c_float, C.c_float, vp, vp,
+                                      C.POINTER(Stats)]
         L.ocr_device_bytes.argtypes = [vp]
         L.ocr_device_bytes.restype = C.c_int64
         L.ocr_destroy.argtypes = [vp]
@@ -181,6 +184,17 @@ def render(h, d_rgba, stream=None, d_counts=None, d_visible=None, d_rects=None,
             "subtree_leaf_tests": s.subtree_leaf_tests,
             "launches": s.launches, "ms_prune": s.ms_prune, "ms_merge": s.ms_merge,
             "ms_subtree": s.ms_subtree}
+
+
+def render_host(h, h_nodal, h_tf, s_min: float, s_max: float, h_rgba, stream=None) -> dict:
+    """ocr_render_host: host field and knots in, host image out (blocks)."""
+    for a in (h_nodal, h_tf, h_rgba):
+        if hasattr(a, "device") and a.device.type != "cpu":
+            raise ValueError("ocr_render_host takes host buffers")
+    s = Stats()
+    _check(lib().ocr_render_host(h, _ptr(h_nodal), _ptr(h_tf), float(s_min), float(s_max),
+                                 _ptr(h_rgba), _ptr(stream), C.byref(s)), "ocr_render_host")
+    return {"segments": s.segments, "rk_steps": s.rk_steps, "launches": s.launches}
 
 
 def _tuning_dict(t: Tuning) -> dict:

@@ -106,6 +106,13 @@ struct ocr_forest {
   long long seg_cap = 0;
   unsigned long long *d_lmcount = nullptr;
   unsigned long long *d_err = nullptr;
+  // ocr_render_host: device copies of the caller's host data and image, the
+  // copy stream and the event that marks the data as arrived
+  float *d_hnodal = nullptr, *d_htf = nullptr, *d_hrgba = nullptr;
+  long long hnodal_cap = 0, hrgba_cap = 0;
+  cudaStream_t copy_st = nullptr;
+  cudaEvent_t copy_ev = nullptr;
+  cudaEvent_t data_ready = nullptr;  // set during ocr_render_host: kernels that read data wait
   int nsm = 0;
   int64_t bytes = 0;
 };
@@ -211,6 +218,11 @@ void free_all(ocr_forest *F) {
   cudaFree(F->d_srta);
   cudaFree(F->d_srg);
   cudaFree(F->d_lmcount);
+  cudaFree(F->d_hnodal);
+  cudaFree(F->d_htf);
+  cudaFree(F->d_hrgba);
+  if (F->copy_st) cudaStreamDestroy(F->copy_st);
+  if (F->copy_ev) cudaEventDestroy(F->copy_ev);
   cudaFree(F->d_err);
   if (F->h_group_slots) cudaFreeHost(F->h_group_slots);
   for (cudaEvent_t &e : F->ev)
@@ -808,6 +820,9 @@ int enqueue_camera(ocr_forest *F, CamPlan &P, float4 *rgba, int *counts, unsigne
   launches += area_scan_blocks(F->M) > 0 ? 4 : 1;
   OCR_CUDA(launch_chunk_map(T, S, st));
   launches += F->M > 0;
+  // the passes below read the field: with host data, wait for its copy here
+  // (the pruning and layout above overlap it)
+  if (F->data_ready) OCR_CUDA(cudaStreamWaitEvent(st, F->data_ready, 0));
   if (timed) OCR_CUDA(cudaEventRecord(F->ev[1], st));
   // group g covers level L - 1 - g: the tile level runs the subtree pass, the
   // levels above it the coarsening passes, deepest first (or the top-down pass)
@@ -861,6 +876,7 @@ int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats) {
   float4 *rgba = reinterpret_cast<float4 *>(d_rgba);
   if (timed) OCR_CUDA(cudaEventRecord(F->ev[0], st));
   if (F->geometry == OCR_GEOM_SHELL) {  // this render's data in the kernels' monomial form
+    if (F->data_ready) OCR_CUDA(cudaStreamWaitEvent(st, F->data_ready, 0));
     OCR_CUDA(shell_monomials(F->d_nodal, F->d_coef, F->N, st));
     ++launches;
   }
@@ -978,6 +994,44 @@ int grow(ocr_forest *F, T **p, long long &cap, long long n) {
 }  // namespace
 
 extern "C" {
+
+int ocr_render_host(ocr_forest *F, const float *h_nodal, const float *h_tf, float s_min,
+                    float s_max, float *h_rgba, void *stream, ocr_stats *stats) {
+  if (!F || !h_nodal || !h_tf || !h_rgba) return OCR_ERR_INVALID;
+  if (!F->has_cam || !F->has_integ) return OCR_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long nv = (F->geometry == OCR_GEOM_SHELL ? 27ll : 8ll) * F->N;
+  int rc;
+  const long long tf_at = (nv + 3) / 4 * 4;  // the 32 knot values after the data, 16 B aligned
+  if ((rc = grow(F, &F->d_hnodal, F->hnodal_cap, tf_at + 32))) return rc;
+  if ((rc = grow(F, &F->d_hrgba, F->hrgba_cap, 4 * F->total_pix))) return rc;
+  F->d_htf = F->d_hnodal + tf_at;
+  if (!F->copy_st) {
+    OCR_CUDA(cudaStreamCreateWithFlags(&F->copy_st, cudaStreamNonBlocking));
+    OCR_CUDA(cudaEventCreateWithFlags(&F->copy_ev, cudaEventDisableTiming));
+  }
+  // the copy in, ordered after the caller's earlier work on its stream
+  OCR_CUDA(cudaEventRecord(F->copy_ev, st));
+  OCR_CUDA(cudaStreamWaitEvent(F->copy_st, F->copy_ev, 0));
+  OCR_CUDA(cudaMemcpyAsync(F->d_hnodal, h_nodal, sizeof(float) * (size_t)nv,
+                           cudaMemcpyHostToDevice, F->copy_st));
+  OCR_CUDA(cudaMemcpyAsync(F->d_htf, h_tf, sizeof(float) * 32, cudaMemcpyHostToDevice,
+                           F->copy_st));
+  OCR_CUDA(cudaEventRecord(F->copy_ev, F->copy_st));
+  if ((rc = ocr_forest_set_data(F, F->d_hnodal, F->d_htf, s_min, s_max, stream))) {
+    OCR_CUDA(cudaStreamWaitEvent(st, F->copy_ev, 0));
+    return rc;
+  }
+  F->data_ready = F->copy_ev;
+  rc = ocr_render(F, reinterpret_cast<float *>(F->d_hrgba), stream, stats);
+  F->data_ready = nullptr;
+  OCR_CUDA(cudaStreamWaitEvent(st, F->copy_ev, 0));  // the copy is done before we return
+  if (rc) return rc;
+  OCR_CUDA(cudaMemcpyAsync(h_rgba, F->d_hrgba, sizeof(float) * 4 * (size_t)F->total_pix,
+                           cudaMemcpyDeviceToHost, st));
+  OCR_CUDA(cudaStreamSynchronize(st));
+  return OCR_OK;
+}
 
 int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_nodal,
                         float *d_grad_tf, void *stream) {

@@ -126,6 +126,23 @@ class Renderer:
         st.update(extra)
         return out, st
 
+    def render_host(self, nodal_h: torch.Tensor, tf_h: torch.Tensor, out_h: torch.Tensor,
+                    stream=None):
+        """Render from host memory (ocr_render_host): ``nodal_h`` ([N, 8] or
+        [N, 27]) and ``tf_h`` ([8, 4]) float32 on the host in, ``out_h`` (all
+        cameras' pixels x 4 float32 on the host, e.g. [h, w, 4] for one) out;
+        returns when ``out_h`` holds the image.  Afterwards the renderer's data
+        is the library's device copy."""
+        for t in (nodal_h, tf_h, out_h):
+            if t.device.type != "cpu" or t.dtype != torch.float32 or not t.is_contiguous():
+                raise ValueError("render_host takes contiguous float32 host tensors")
+        if nodal_h.numel() != self.nodal.numel() or tf_h.numel() != 32:
+            raise ValueError("render_host: nodal / knot sizes do not match the forest")
+        if out_h.numel() != self.batch_pixels() * 4:
+            raise ValueError("render_host: the image must hold 4 values per pixel of every camera")
+        return capi.render_host(self.h, nodal_h, tf_h, self.s_min, self.s_max, out_h,
+                                _stream_ptr(stream))
+
     def backward(self, grad_rgba: torch.Tensor, stream=None):
         """dL/d(nodal) [N, 8] and dL/d(knots) [8, 4] (cube forests) for the data, camera and
         integrator last set, given dL/d(rgba) [h, w, 4] on the device."""

@@ -187,3 +187,25 @@ def test_wide_image_index_arithmetic():
     f, tf, _ = I.preset_small()
     cam = I.perspective_camera(17, 4096, 7)
     _compare(f, tf, cam, {"method": "rk4", "nsteps": 2}, max_unc_frac=0.05)
+
+
+def test_render_host_equals_device_render():
+    """ocr_render_host (host data in, host image out, the copy overlapping the
+    pruning) gives the device render's pixels bit for bit, for a cube and a
+    shell forest, and leaves the library's copy as the renderer's data."""
+    from paper_1809_01334_gb300 import Renderer
+    integ = {"method": "dopri5", "tol": 1e-5, "c_rk": 0.5, "max_depth": 16}
+    for f, tf, cam in (I.preset_small("adaptive"), I.preset_shell_small()):
+        r = Renderer(f, tf, integ)
+        r.set_camera(cam)
+        ref, _ = r.render()
+        ref = ref.cpu()
+        nodal_h = torch.from_numpy(np.ascontiguousarray(f.nodal, np.float32)).pin_memory()
+        tf_h = torch.from_numpy(np.ascontiguousarray(tf.knots, np.float32)).pin_memory()
+        out_h = torch.empty((cam.h, cam.w, 4), dtype=torch.float32).pin_memory()
+        st = r.render_host(nodal_h, tf_h, out_h)
+        assert st["launches"] > 0
+        assert torch.equal(out_h, ref)
+        again, _ = r.render()  # now from the library's device copy
+        assert torch.equal(again.cpu(), ref)
+        r.close()
