@@ -138,3 +138,29 @@ def test_long_rays_gradient():
     en, et = _rel(gn.cpu().numpy().astype(np.float64), rn), _rel(gt.cpu().numpy().astype(np.float64), rt)
     assert en <= 1e-3 and et <= 1e-3, (en, et)
     r.close()
+
+
+@pytest.mark.parametrize("geometry", ["cube", "shell"])
+def test_empty_view_gradient_is_zero(geometry):
+    """A camera that sees no leaf: no pairs, no hits, no segments; the adjoint
+    returns zero gradients without an error."""
+    from paper_1809_01334_gb300 import Renderer
+    if geometry == "cube":
+        f, tf, _ = I.preset_small("adaptive")
+        cam = I.Camera(o=(0.5, 0.5, 3.0), v=(0.0, 0.0, 0.1), t=(1.0, 0.0, 0.0), u=(0.0, 1.0, 0.0),
+                       ell=float(np.float32(1e-3)), near=float(np.float32(0.1)), far=100.0,
+                       w=19, h=11)
+    else:
+        f, tf, _ = I.preset_shell_small()
+        cam = I.Camera(o=(0.0, 0.0, 3.0), v=(0.0, 0.0, 0.1), t=(1.0, 0.0, 0.0), u=(0.0, 1.0, 0.0),
+                       ell=float(np.float32(1e-3)), near=float(np.float32(0.1)), far=100.0,
+                       w=19, h=11)
+    r = Renderer(f, tf, {"method": "dopri5", "tol": 1e-5, "c_rk": 0.5, "max_depth": 16})
+    r.set_camera(cam)
+    img, st = r.render(with_index=True)
+    assert st["segments"] == 0
+    W = torch.ones((cam.h, cam.w, 4), dtype=torch.float32, device="cuda")
+    gn, gt = r.backward(W)
+    torch.cuda.synchronize()
+    assert float(gn.abs().max()) == 0.0 and float(gt.abs().max()) == 0.0
+    r.close()
