@@ -40,23 +40,41 @@ __device__ __forceinline__ void lagrange_to_monomial(float &f0, float &f1, float
   f2 = c2;
 }
 
-__global__ void __launch_bounds__(256)
+constexpr int kMonoLeaves = 256;  // leaves per CTA (one thread each)
+
+// The CTA's 256 leaves (27 x 256 consecutive floats) are staged through shared
+// memory with coalesced loads and stores; each thread converts one leaf
+// (row stride 27, odd: the threads' rows fall in distinct banks).
+__global__ void __launch_bounds__(kMonoLeaves)
     shell_monomial_kernel(const float *__restrict__ nodal, float *__restrict__ coef, int N) {
-  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < N; l += gridDim.x * blockDim.x) {
-    float f[27];
+  __shared__ float s_f[27 * kMonoLeaves];
+  for (long long l0 = (long long)blockIdx.x * kMonoLeaves; l0 < N;
+       l0 += (long long)gridDim.x * kMonoLeaves) {
+    const int nl = (int)(N - l0 < kMonoLeaves ? N - l0 : kMonoLeaves);
+    const float *src = nodal + 27 * l0;
+    for (int q = threadIdx.x; q < 27 * nl; q += kMonoLeaves) s_f[q] = __ldg(src + q);
+    __syncthreads();
+    if ((int)threadIdx.x < nl) {
+      float *f = s_f + 27 * threadIdx.x;
+      float g[27];
 #pragma unroll
-    for (int q = 0; q < 27; ++q) f[q] = __ldg(nodal + 27 * (size_t)l + q);
+      for (int q = 0; q < 27; ++q) g[q] = f[q];
 #pragma unroll
-    for (int r = 0; r < 9; ++r) lagrange_to_monomial(f[3 * r], f[3 * r + 1], f[3 * r + 2]);
+      for (int r = 0; r < 9; ++r) lagrange_to_monomial(g[3 * r], g[3 * r + 1], g[3 * r + 2]);
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
+      for (int c = 0; c < 3; ++c)
 #pragma unroll
-      for (int a = 0; a < 3; ++a)
-        lagrange_to_monomial(f[9 * c + a], f[9 * c + 3 + a], f[9 * c + 6 + a]);
+        for (int a = 0; a < 3; ++a)
+          lagrange_to_monomial(g[9 * c + a], g[9 * c + 3 + a], g[9 * c + 6 + a]);
 #pragma unroll
-    for (int r = 0; r < 9; ++r) lagrange_to_monomial(f[r], f[9 + r], f[18 + r]);
+      for (int r = 0; r < 9; ++r) lagrange_to_monomial(g[r], g[9 + r], g[18 + r]);
 #pragma unroll
-    for (int q = 0; q < 27; ++q) coef[27 * (size_t)l + q] = f[q];
+      for (int q = 0; q < 27; ++q) f[q] = g[q];
+    }
+    __syncthreads();
+    float *dst = coef + 27 * l0;
+    for (int q = threadIdx.x; q < 27 * nl; q += kMonoLeaves) dst[q] = s_f[q];
+    __syncthreads();
   }
 }
 
@@ -425,8 +443,8 @@ __global__ void __launch_bounds__(256, 2)
 // ------------------------------------------------------------- launchers --
 cudaError_t shell_monomials(const float *nodal, float *coef, int N, cudaStream_t st) {
   if (N <= 0) return cudaSuccess;
-  const int grid = (N + 255) / 256 > 8192 ? 8192 : (N + 255) / 256;
-  shell_monomial_kernel<<<grid, 256, 0, st>>>(nodal, coef, N);
+  const int need = (N + kMonoLeaves - 1) / kMonoLeaves;
+  shell_monomial_kernel<<<need > 8192 ? 8192 : need, kMonoLeaves, 0, st>>>(nodal, coef, N);
   return cudaGetLastError();
 }
 
