@@ -53,6 +53,7 @@ struct ocr_forest {
   Shell shell{};                      // shell: frames and tables (in d_shell_tabs)
   float *d_shell_tabs = nullptr;      // [54 + 2 (2^L + 1)]
   float *d_coef = nullptr;            // shell: [N * 27] the data in monomial form, per render
+  float4 *d_planes = nullptr;         // shell: [N * 4] per leaf its plane normals and radii
   int N = 0, M = 0, L = 0;
   int root = 0;                       // unified id of the tree root
   std::vector<int> level_base;        // internal index of the first node of level l
@@ -194,6 +195,7 @@ void free_plans(ocr_forest *F) {
 void free_all(ocr_forest *F) {
   cudaFree(F->d_shell_tabs);
   cudaFree(F->d_coef);
+  cudaFree(F->d_planes);
   cudaFree(F->d_geo);
   cudaFree(F->d_child);
   cudaFree(F->d_leaves);
@@ -338,6 +340,7 @@ int build_shell(const ocr_forest_desc *desc, cudaStream_t st, ocr_forest **out) 
   if ((rc = dev_alloc(&F->d_geo, geo.size(), F->bytes)) ||
       (rc = dev_alloc(&F->d_shell_tabs, tabs.size(), F->bytes)) ||
       (rc = dev_alloc(&F->d_coef, (size_t)F->N * 27, F->bytes)) ||
+      (rc = dev_alloc(&F->d_planes, (size_t)F->N * 4, F->bytes)) ||
       (rc = dev_alloc(&F->d_stats, kStats, F->bytes)) ||
       (rc = dev_alloc(&F->d_err, 1, F->bytes))) {
     free_all(F);
@@ -354,6 +357,7 @@ int build_shell(const ocr_forest_desc *desc, cudaStream_t st, ocr_forest **out) 
   F->shell.frames = F->d_shell_tabs;
   F->shell.tan_tab = F->d_shell_tabs + 54;
   F->shell.rad_tab = F->d_shell_tabs + 54 + nt;
+  F->shell.planes = F->d_planes;
   F->shell.L = L;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -364,6 +368,7 @@ int build_shell(const ocr_forest_desc *desc, cudaStream_t st, ocr_forest **out) 
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(F->d_shell_tabs, tabs.data(), tabs.size() * sizeof(float),
                         cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = shell_planes(F->d_geo, F->N, F->shell, F->d_planes, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     free_all(F);

@@ -88,6 +88,8 @@ struct Shell {
   const float *frames;   // [6 * 9] per tree: n, e1, e2
   const float *tan_tab;  // [2^L + 1] tan(pi/4 (2 k 2^-L - 1))
   const float *rad_tab;  // [2^L + 1] r0 + (r1 - r0) k 2^-L
+  const float4 *planes;  // [N * 4] per leaf the normals m = e - T n of its four planes
+                         // (xi low, xi high, eta low, eta high); w: r_in, r_out, 0, 0
   int L;
 };
 constexpr int kStatMaxHits = 6;  // shell: the most segments on one ray (atomicMax)
@@ -164,6 +166,10 @@ cudaError_t bwd_cube_adjoint(const Topo &T, const Field &Fd, const Cam &C, const
                              int nsm, cudaStream_t st);
 
 // Cubed-sphere shell (ocr_shell.cu)
+// the per-leaf plane table (Shell::planes) from the frames and tables, once
+// per forest
+cudaError_t shell_planes(const int4 *geo, int N, const Shell &S, float4 *planes,
+                         cudaStream_t st);
 // the leaves' degree-2 data (27 Lagrange nodal values each) in monomial form
 // (27 coefficients each, the polynomial the shell kernels evaluate)
 cudaError_t shell_monomials(const float *nodal, float *coef, int N, cudaStream_t st);

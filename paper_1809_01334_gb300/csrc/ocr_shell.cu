@@ -78,6 +78,19 @@ __global__ void __launch_bounds__(kMonoLeaves)
   }
 }
 
+// ------------------------------------------------------------ plane table --
+__global__ void __launch_bounds__(256)
+    shell_planes_kernel(const int4 *__restrict__ geo, int N, Shell S, float4 *planes) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    const LeafShell q = leaf_shell(S, __ldg(geo + k));
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const float3 m = plane_normal(q, s);
+      planes[4 * (size_t)k + s] = make_float4(m.x, m.y, m.z, s == 0 ? q.rin : s == 1 ? q.rout : 0.f);
+    }
+  }
+}
+
 // ----------------------------------------------------------------- culling --
 __global__ void __launch_bounds__(256)
     shell_cull_kernel(const int4 *__restrict__ geo, int N, Shell S, Cam c, int4 *rect,
@@ -206,7 +219,7 @@ __global__ void __launch_bounds__(kPairChunk)
     pix = (long long)j * c.w + i;
     float3 org, dir;
     pixel_ray(c, i, j, org, dir);
-    n = shell_ray_leaf(leaf_shell(S, __ldg(geo + leaf)), org, dir, c.amin, c.amax, ai, ao);
+    n = shell_ray_leaf(S.planes + 4 * (size_t)leaf, org, dir, c.amin, c.amax, ai, ao);
   }
   if (MODE == 0) {
     const unsigned bal = __ballot_sync(0xffffffffu, n > 0);
@@ -441,6 +454,14 @@ __global__ void __launch_bounds__(256, 2)
 }  // namespace
 
 // ------------------------------------------------------------- launchers --
+cudaError_t shell_planes(const int4 *geo, int N, const Shell &S, float4 *planes,
+                         cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  const int grid = (N + 255) / 256 > 8192 ? 8192 : (N + 255) / 256;
+  shell_planes_kernel<<<grid, 256, 0, st>>>(geo, N, S, planes);
+  return cudaGetLastError();
+}
+
 cudaError_t shell_monomials(const float *nodal, float *coef, int N, cudaStream_t st) {
   if (N <= 0) return cudaSuccess;
   const int need = (N + kMonoLeaves - 1) / kMonoLeaves;

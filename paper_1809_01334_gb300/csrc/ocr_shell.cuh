@@ -42,21 +42,30 @@ __device__ __forceinline__ float dot3(const float *a, float3 b) {
   return fmaf(a[0], b.x, fmaf(a[1], b.y, a[2] * b.z));
 }
 
+// The normal m = e - T n of one of the leaf's four planes (s: xi low, xi
+// high, eta low, eta high); the plane table holds exactly these values.
+__device__ __forceinline__ float3 plane_normal(const LeafShell &q, int s) {
+  const float *e = s < 2 ? q.e1 : q.e2;
+  const float T = s == 0 ? q.ta0 : s == 1 ? q.ta1 : s == 2 ? q.tb0 : q.tb1;
+  return make_float3(fmaf(-T, q.n[0], e[0]), fmaf(-T, q.n[1], e[1]), fmaf(-T, q.n[2], e[2]));
+}
+
 // Intervals of the ray o + alpha r inside the leaf, clipped to [amin, amax],
-// nearest first; returns their number (0..2).  The cone: x . m >= 0 for the
-// lower planes and <= 0 for the upper ones, m = e - T n; each crossing is
-// -(o . m) / (r . m) computed from (T, e, n) alone, so neighbours agree bit
-// for bit.  The spheres: alpha = -b -+ sqrt((R^2 - |p|^2) / |r|^2), b = o.r / |r|^2,
-// p = o - b r.
-__device__ __forceinline__ int shell_ray_leaf(const LeafShell &q, float3 org, float3 dir,
-                                              float amin, float amax, float *a_in, float *a_out) {
+// nearest first; returns their number (0..2).  m: the normals of the leaf's
+// four planes (xi low, xi high, eta low, eta high), r_in, r_out its radii.
+// The cone: x . m >= 0 for the lower planes and <= 0 for the upper ones; each
+// crossing is -(o . m) / (r . m) from m alone, so neighbours (whose shared
+// plane has the same T, e, n, or at a tree boundary an exactly negated m)
+// agree bit for bit.  The spheres: alpha = -b -+ sqrt((R^2 - |p|^2) / |r|^2),
+// b = o.r / |r|^2, p = o - b r.
+__device__ __forceinline__ int shell_ray_leaf_m(const float3 *m, float rin, float rout,
+                                                float3 org, float3 dir, float amin, float amax,
+                                                float *a_in, float *a_out) {
   float t0 = amin, t1 = amax;
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
-    const float *e = s < 2 ? q.e1 : q.e2;
-    const float T = s == 0 ? q.ta0 : s == 1 ? q.ta1 : s == 2 ? q.tb0 : q.tb1;
-    const float m[3] = {fmaf(-T, q.n[0], e[0]), fmaf(-T, q.n[1], e[1]), fmaf(-T, q.n[2], e[2])};
-    const float g0 = dot3(m, org), g1 = dot3(m, dir);
+    const float g0 = fmaf(m[s].x, org.x, fmaf(m[s].y, org.y, m[s].z * org.z));
+    const float g1 = fmaf(m[s].x, dir.x, fmaf(m[s].y, dir.y, m[s].z * dir.z));
     const bool upper = (s & 1) != 0;
     if (g1 == 0.f) {
       if ((upper ? -g0 : g0) < 0.f) return 0;  // parallel to the plane and outside
@@ -72,12 +81,12 @@ __device__ __forceinline__ int shell_ray_leaf(const LeafShell &q, float3 org, fl
   const float b = fmaf(org.x, dir.x, fmaf(org.y, dir.y, org.z * dir.z)) / rr;
   const float px = fmaf(-b, dir.x, org.x), py = fmaf(-b, dir.y, org.y), pz = fmaf(-b, dir.z, org.z);
   const float pp = fmaf(px, px, fmaf(py, py, pz * pz));
-  const float hout = fmaf(q.rout, q.rout, -pp);
+  const float hout = fmaf(rout, rout, -pp);
   if (!(hout > 0.f)) return 0;
   const float so = sqrtf(hout / rr);
   t0 = fmaxf(t0, -b - so);
   t1 = fminf(t1, -b + so);
-  const float hin = fmaf(q.rin, q.rin, -pp);
+  const float hin = fmaf(rin, rin, -pp);
   int n = 0;
   if (hin > 0.f) {
     const float si = sqrtf(hin / rr);
@@ -98,6 +107,32 @@ __device__ __forceinline__ int shell_ray_leaf(const LeafShell &q, float3 org, fl
     n = 1;
   }
   return n;
+}
+
+// The same with the normals formed from the leaf's frame and tangents (the
+// per-segment kernels, whose leaves change from lane to lane) ...
+__device__ __forceinline__ int shell_ray_leaf(const LeafShell &q, float3 org, float3 dir,
+                                              float amin, float amax, float *a_in, float *a_out) {
+  float3 m[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) m[s] = plane_normal(q, s);
+  return shell_ray_leaf_m(m, q.rin, q.rout, org, dir, amin, amax, a_in, a_out);
+}
+
+// ... or read from the per-leaf plane table, which holds the same values (the
+// pair passes, where consecutive threads share a leaf).
+__device__ __forceinline__ int shell_ray_leaf(const float4 *__restrict__ pl, float3 org,
+                                              float3 dir, float amin, float amax, float *a_in,
+                                              float *a_out) {
+  float3 m[4];
+  float w[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const float4 v = __ldg(pl + s);
+    m[s] = make_float3(v.x, v.y, v.z);
+    w[s] = v.w;
+  }
+  return shell_ray_leaf_m(m, w[0], w[1], org, dir, amin, amax, a_in, a_out);
 }
 
 // -------------------------------------------------------------- the field --
