@@ -109,7 +109,8 @@ struct ocr_forest {
   unsigned long long *d_err = nullptr;
   // ocr_render_host: device copies of the caller's host data and image, the
   // copy stream and the event that marks the data as arrived
-  float *d_hnodal = nullptr, *d_htf = nullptr, *d_hrgba = nullptr;
+  float *d_hnodal = nullptr, *d_hrgba = nullptr;
+  float *d_htf = nullptr;  // inside d_hnodal, after the field (not an allocation of its own)
   long long hnodal_cap = 0, hrgba_cap = 0;
   cudaStream_t copy_st = nullptr;
   cudaEvent_t copy_ev = nullptr;
@@ -220,8 +221,7 @@ void free_all(ocr_forest *F) {
   cudaFree(F->d_srta);
   cudaFree(F->d_srg);
   cudaFree(F->d_lmcount);
-  cudaFree(F->d_hnodal);
-  cudaFree(F->d_htf);
+  cudaFree(F->d_hnodal);  // d_htf points into it
   cudaFree(F->d_hrgba);
   if (F->copy_st) cudaStreamDestroy(F->copy_st);
   if (F->copy_ev) cudaEventDestroy(F->copy_ev);
