@@ -139,6 +139,10 @@ def test_null_handles_are_rejected(lib):
     cam = capi.Camera()
     assert lib.ocr_set_camera(None, C.byref(cam), 1) == capi.ERR_INVALID
     assert lib.ocr_render(None, None, None, None) == capi.ERR_INVALID
+    buf = np.zeros(64, np.float32)
+    assert lib.ocr_render_host(None, buf.ctypes.data, buf.ctypes.data, 0.0, 1.0,
+                               buf.ctypes.data, None, None) == capi.ERR_INVALID
+    assert lib.ocr_render_backward(None, None, None, None, None) == capi.ERR_INVALID
     assert lib.ocr_forest_set_data(None, None, None, 0.0, 1.0, None) == capi.ERR_INVALID
     assert lib.ocr_device_bytes(None) == 0
     t = capi.Tuning(3, 4, 0, 0, 0.0)
