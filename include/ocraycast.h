@@ -225,11 +225,13 @@ int ocr_prune_noalloc(const int32_t *d_leaf_geo, int64_t nleaves, int max_level,
                       const ocr_camera *cam, int32_t *d_rects, int32_t *d_visible_idx,
                       int64_t *h_nvisible, void *stream);
 
-/* Render from host memory: copy the field h_nodal (layout as in
+/* Render from host memory: the pipeline of ocr_render (pruning, Sec. 3.1;
+ * segments, Sec. 2.1-2.3; merging with Eq. 2.14, Sec. 2.4 and 3.3) with the
+ * inputs and the image in host memory.  Copy the field h_nodal (layout as in
  * ocr_forest_set_data) and the knots h_tf [8*4] to device memory that the
  * library owns, render every camera of the last ocr_set_camera into its own
- * device image, copy that image to h_rgba (float32, sum of w*h*4) and return
- * once it is there.  All work is ordered on `stream` after the caller's
+ * device image, copy that image to h_rgba (float32, sum of w*h*4, layout as
+ * in ocr_render) and return once it is there.  All work is ordered on `stream` after the caller's
  * earlier work; the copy in overlaps the data-independent pruning and layout
  * (cube forests).  Pinned host memory gives full copy speed; pageable memory
  * works.  Afterwards the forest's data is the library's copy (a later
