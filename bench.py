@@ -165,6 +165,32 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def fp32_fma_peak(local: int) -> dict:
+    """The FP32 FMA throughput of this GPU, measured: independent FFMA chains
+    (paper_1809_01334_gb300/csrc/ocr_fp32_peak.cu), seven launches of about
+    40 ms after a warm-up, CUDA events, SM clock sampled meanwhile.  The
+    rate counts lane-FMA instructions per second (one FMA = one operation,
+    as the kernels' algorithmic counts do)."""
+    import ctypes
+    from paper_1809_01334_gb300 import build as B
+    B.build()
+    lib = ctypes.CDLL(B.PEAK_LIB)
+    fn = lib.ocr_fp32_fma_peak
+    fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)]
+    best, med, ms = ctypes.c_double(), ctypes.c_double(), ctypes.c_float()
+    blocks_per_sm, trips, reps = 4, 60000, 7
+    with ClockSampler(local) as clk:
+        rc = fn(blocks_per_sm, trips, reps, ctypes.byref(best), ctypes.byref(med),
+                ctypes.byref(ms))
+    if rc != 0:
+        raise RuntimeError(f"FP32 FMA microbenchmark failed ({rc})")
+    return {"fma_per_s_best": best.value, "fma_per_s_median": med.value, "ms_best": ms.value,
+            "launch": f"{blocks_per_sm} CTAs of 256 threads per SM, 8 independent FFMA chains "
+                      f"per thread, {trips} x 16 steps each",
+            "clocks": clk.summary()}
+
+
 def subtree_traffic():
     """DRAM bytes per launch of the subtree pass from the committed ncu capture
     (profiles/subtree_kernel_traffic.json), or None when the kernel's sources
@@ -234,27 +260,30 @@ def run_batch(args, forest, tf, integ, dev, flush):
         if k:
             gms.append(a.elapsed_time(b))
     del g
-    r.close()
-    # one view at a time
-    one = Renderer(forest, tf, integ, device=dev)
+    # one view at a time: the same planned cameras (planning is outside the
+    # timed region for both arms), each view rendered alone on the stream
+    # after the previous one, device time
+    views = [torch.empty((c.h, c.w, 4), dtype=torch.float32, device=dev) for c in cams]
     seq = []
-    for k in range(2):
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        for cam in cams:
-            one.set_camera(cam)
-            img, _ = one.render()
+    for k in range(1 + reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for v in range(len(cams)):
+            r.render_view(v, views[v], stream=stream)
+        b.record(stream)
         torch.cuda.synchronize(dev)
         if k:
-            seq.append((time.perf_counter() - t0) * 1e3)
-    one.close()
+            seq.append(a.elapsed_time(b))
+    r.close()
     gm = sum(gms) / len(gms)
     sq = sum(seq) / len(seq)
     return {"cameras": len(cams), "pixels": npix, "segments": segments,
             "graph_ms": gm, "sequential_ms": sq, "speedup_vs_sequential": sq / gm,
             "segments_per_s": segments / (gm * 1e-3), "mpixel_per_s": npix / (gm * 1e-3) / 1e6,
             "autotune": {"best": tune["best"], "tried": tune["tried"]},
-            "sequential": "one Renderer: set_camera + render per view, wall time",
+            "sequential": "the same planned cameras, one ocr_render_view per view in "
+                          "order on one stream, device time (L2 flushed before each arm)",
             "sizes": "square, side round(256 * 8**u), u ~ U[0,1], seeded"}
 
 
@@ -297,9 +326,7 @@ def run_shell(args, dev, flush):
     ms = _timed(fwd, stream, flush, 2, 5)
     rays_ms = sum(p["ms_subtree"] for p in phases[2:]) / len(phases[2:])
     shell_ops = FP32_OPS_SHELL_SEGMENT * st["segments"] + FP32_OPS_SHELL_DOPRI_STEP * st["rk_steps"]
-    peaks, _ = measured_peaks()
-    shell_peak = (torch.cuda.get_device_properties(dev).multi_processor_count *
-                  FP32_LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12)
+    shell_peak = args.fp32_peak["fma_per_s_best"] / 1e12
     c3 = {"workload": "cubed-sphere shell, 6 trees, levels 4-7 (%d leaves, degree-2 FP32 "
                       "data), perspective 45deg %dx%d, DOPRI5 tol 1e-5" % (forest.nleaves, sw, sh),
           "ms_per_render": ms, "segments": st["segments"], "rk_steps": st["rk_steps"],
@@ -310,7 +337,8 @@ def run_shell(args, dev, flush):
                        "achieved": shell_ops / (rays_ms * 1e-3) / 1e12, "peak": shell_peak,
                        "unit": "TFP32op/s",
                        "frac": shell_ops / (rays_ms * 1e-3) / 1e12 / shell_peak,
-                       "fp32_ops_per_launch": shell_ops}}
+                       "fp32_ops_per_launch": shell_ops,
+                       "peak_source": "measured (FP32 FMA microbenchmark)"}}
     r.close()
     del out
     # differentiation on the levels 4-6 shell
@@ -385,6 +413,7 @@ def main():
     from paper_1809_01334_gb300 import inputs as I
 
     torch.cuda.set_device(local)
+    args.fp32_peak = fp32_fma_peak(local)
     if args.only_shell:
         dev = torch.device("cuda", local)
         flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
@@ -486,7 +515,8 @@ def main():
                FP32_OPS_SEGMENT * st0["subtree_segments"] +
                FP32_OPS_DOPRI_STEP * st0["subtree_rk_steps"])
         nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-        peak_ops = nsm * FP32_LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6
+        nominal = nsm * FP32_LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6
+        peak_ops = args.fp32_peak["fma_per_s_best"]
         achieved = ops / (sm * 1e-3)
         line = {
             "metric": METRIC, "value": job_throughput(segments, world, ms_max), "unit": UNIT,
@@ -511,8 +541,11 @@ def main():
                          "unit": "TFP32op/s", "frac": achieved / peak_ops,
                          "traffic": subtree_traffic(), "traffic_unit": "bytes per launch (ncu)",
                          "fp32_ops_per_launch": ops, "ms_per_launch": sm,
-                         "peak_source": f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
-                                        f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({src})",
+                         "peak_source": "measured (FP32 FMA microbenchmark, this run)",
+                         "peak_measurement": args.fp32_peak,
+                         "nominal_peak": nominal / 1e12,
+                         "nominal_source": f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                                           f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({src})",
                          "ms_merge": mm, "ms_prune": sum(prune_ms) / len(prune_ms)},
             "clocks": clk.summary(),
         }

@@ -169,8 +169,10 @@ int ocr_forest_set_data(ocr_forest *F, const float *d_nodal, const float *d_tf, 
 int ocr_set_integrator(ocr_forest *F, const ocr_integrator *integ);
 
 /* Set the cameras (host structs, copied), 1 <= ncams <= 4096.  Plans every
- * camera once: its pruning and slot layout run on the device (legacy default
- * stream, blocking) to size its scratch, which is allocated here.  Rendering
+ * camera once: its pruning and slot layout run on the device, on a stream the
+ * forest owns (nothing is ordered on the legacy default stream; the host
+ * blocks until the sizes are read back), to size its scratch, which is
+ * allocated here.  Must not overlap a render of the same forest.  Rendering
  * then never waits for the host, so ocr_render without counters can be
  * captured in a CUDA graph.  Several cameras are rendered by one ocr_render
  * call (batching: the paper's multiple image instances, Sec. 3).  Shell
@@ -194,16 +196,26 @@ int ocr_set_camera(ocr_forest *F, const ocr_camera *cams, int ncams);
  * and counted as a device error (OCR_ERR_DEVICE when counters are filled). */
 int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats);
 
+/* Render one camera of the last ocr_set_camera alone: camera `view`
+ * (0 <= view < ncams) into d_rgba [h*w*4] (its own image only), on `stream`,
+ * with the same pipeline as a single-camera ocr_render; stats as in
+ * ocr_render, for this camera.  Lets a caller render the views of a planned
+ * batch one at a time (the paper's image instances, Sec. 3, taken singly)
+ * without planning again.  OCR_ERR_INVALID for a view out of range. */
+int ocr_render_view(ocr_forest *F, int view, float *d_rgba, void *stream, ocr_stats *stats);
+
 /* Pruning for callers that cannot allocate device memory at the time they
  * need it: an application that serves all device memory from a pool it
  * reserved up front, a real-time loop that must not take the device-wide
  * synchronisation an allocation implies, a plug-in living inside another
- * program's memory budget.  The paper has no counterpart: it is the pruning
- * step above (Sec. 3.1) packaged so that it allocates nothing.
+ * program's memory budget.  The paper has no counterpart.
  *
- * Inputs (device, caller-owned): d_leaf_geo [nleaves * 4] int32, per leaf
- * {x, y, z, level} with anchors in units of 2^-max_level, Morton order;
- * 16-byte aligned.  cam: host struct, read as float32 exactly like
+ * Cube forests only (OCR_GEOM_CUBE leaf records).  Inputs (device,
+ * caller-owned): d_leaf_geo [nleaves * 4] int32, per leaf {x, y, z, level}
+ * with anchors in units of 2^-max_level, Morton order; 16-byte aligned.  A
+ * record whose level is negative or above max_level (a shell record, whose
+ * fourth word carries the tree in its upper bits, is one) returns
+ * OCR_ERR_INVALID after the kernel has run; the outputs are then undefined.  cam: host struct, read as float32 exactly like
  * ocr_set_camera.  Outputs (device, caller-owned): d_rects [nleaves * 4]
  * int32, the same rectangles ocr_render reports in ocr_stats.d_rects (may be
  * NULL; 16-byte aligned); d_visible_idx [nleaves] int32, the indices of the
@@ -216,7 +228,8 @@ int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats);
  * process exits.  nleaves above OCR_NOALLOC_MAX_LEAVES returns
  * OCR_ERR_INVALID.  The first call on a device looks up that array's device
  * address (cudaGetSymbolAddress, with the device current), so make the first
- * call before any stream capture.  All calls share the one array and reset
+ * call before any stream capture; the address is kept for the life of the
+ * process, so do not call this on a device after cudaDeviceReset.  All calls share the one array and reset
  * it at their start: calls that overlap on the GPU (different streams,
  * different host threads on one device) race and must be serialised by the
  * caller.  Blocks the host until the result is ready. */

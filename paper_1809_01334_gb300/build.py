@@ -1,7 +1,10 @@
 """Build the CUDA library in-tree with nvcc (sm_103a only).
 
 Produces ``paper_1809_01334_gb300/_build/libocraycast.so`` from the sources in
-``csrc/``.  Translation units compile in parallel; the link is one nvcc call.
+``csrc/``, and ``_build/libocrpeak.so`` (the FP32 FMA throughput
+microbenchmark that the benchmark's roofline is set against) from
+``csrc/ocr_fp32_peak.cu``.  Translation units compile in parallel; each
+library is linked by one nvcc call.
 """
 from __future__ import annotations
 
@@ -14,6 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libocraycast.so")
 SOURCES = ["ocr_capi.cu", "ocr_kernels.cu", "ocr_backward.cu", "ocr_shell.cu"]
+PEAK_SOURCE = "ocr_fp32_peak.cu"
+PEAK_LIB = os.path.join(OUT_DIR, "libocrpeak.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--use_fast_math",
          "-Xptxas", "-v"]
@@ -32,7 +37,9 @@ def _deps():
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
+    dep = _deps()
+    if (not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= dep
+            and os.path.exists(PEAK_LIB) and os.path.getmtime(PEAK_LIB) >= dep):
         return LIB
     nvcc = _nvcc()
     objs = []
@@ -45,17 +52,23 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
-        for obj, log in ex.map(compile_one, SOURCES):
-            objs.append(obj)
+    peak_obj = None
+    with cf.ThreadPoolExecutor(len(SOURCES) + 1) as ex:
+        for src, (obj, log) in zip(SOURCES + [PEAK_SOURCE],
+                                   ex.map(compile_one, SOURCES + [PEAK_SOURCE])):
+            if src == PEAK_SOURCE:
+                peak_obj = obj
+            else:
+                objs.append(obj)
             if verbose:
                 print(log)
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    for out, ins in ((LIB, objs), (PEAK_LIB, [peak_obj])):
+        tmp = out + f".tmp{os.getpid()}"
+        cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *ins]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, out)
     return LIB
 
 

@@ -18,9 +18,9 @@ GEOM_CUBE, GEOM_SHELL = 0, 1
 RK4, DOPRI5, GAUSS2, SIMPSON, EQUILIBRIUM = 0, 1, 2, 3, 4
 
 EXPORTS = ["ocr_build_forest", "ocr_forest_set_data", "ocr_set_integrator", "ocr_set_camera",
-           "ocr_render", "ocr_render_host", "ocr_render_backward", "ocr_set_tuning",
-           "ocr_get_tuning",
-           "ocr_autotune", "ocr_device_bytes", "ocr_destroy", "ocr_strerror"]
+           "ocr_render", "ocr_render_view", "ocr_render_host", "ocr_render_backward",
+           "ocr_set_tuning", "ocr_get_tuning", "ocr_autotune", "ocr_prune_noalloc",
+           "ocr_device_bytes", "ocr_destroy", "ocr_strerror"]
 
 
 class ForestDesc(C.Structure):
@@ -81,6 +81,7 @@ def lib():
         L.ocr_set_integrator.argtypes = [vp, C.POINTER(Integrator)]
         L.ocr_set_camera.argtypes = [vp, C.POINTER(Camera), C.c_int]
         L.ocr_render.argtypes = [vp, vp, vp, C.POINTER(Stats)]
+        L.ocr_render_view.argtypes = [vp, C.c_int, vp, vp, C.POINTER(Stats)]
         L.ocr_render_host.argtypes = [vp, vp, vp, C.c_float, C.c_float, vp, vp,
                                       C.POINTER(Stats)]
         L.ocr_device_bytes.argtypes = [vp]
@@ -184,6 +185,16 @@ def render(h, d_rgba, stream=None, d_counts=None, d_visible=None, d_rects=None,
             "subtree_leaf_tests": s.subtree_leaf_tests,
             "launches": s.launches, "ms_prune": s.ms_prune, "ms_merge": s.ms_merge,
             "ms_subtree": s.ms_subtree}
+
+
+def render_view(h, view: int, d_rgba, stream=None, d_counts=None, fill_counters: bool = False,
+                time_phases: bool = False) -> dict:
+    """ocr_render_view: one camera of the last set_cameras, alone, into its own image."""
+    s = Stats(_ptr(d_counts), None, None, int(bool(fill_counters)), int(bool(time_phases)))
+    _check(lib().ocr_render_view(h, int(view), _ptr(d_rgba), _ptr(stream), C.byref(s)),
+           "ocr_render_view")
+    return {"segments": s.segments, "rk_steps": s.rk_steps, "launches": s.launches,
+            "ms_prune": s.ms_prune, "ms_merge": s.ms_merge, "ms_subtree": s.ms_subtree}
 
 
 def render_host(h, h_nodal, h_tf, s_min: float, s_max: float, h_rgba, stream=None) -> dict:

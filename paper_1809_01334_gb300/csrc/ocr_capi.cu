@@ -74,6 +74,7 @@ struct ocr_forest {
   std::vector<CamPlan> plans;         // one per camera of the last ocr_set_camera
   long long total_pix = 0;
   cudaStream_t sub[kMaxStreams] = {};
+  cudaStream_t plan_st = nullptr;     // ocr_set_camera's planning (created on first use)
   cudaEvent_t fork = nullptr, join[kMaxStreams] = {};
   // tuning (ocr_set_tuning / ocr_autotune)
   int tile_depth = kSubtreeDepth;     // cube: octree levels aggregated inside one CTA
@@ -207,6 +208,7 @@ void free_all(ocr_forest *F) {
     if (F->join[q]) cudaEventDestroy(F->join[q]);
   }
   if (F->fork) cudaEventDestroy(F->fork);
+  if (F->plan_st) cudaStreamDestroy(F->plan_st);
   cudaFree(F->d_stats);
   cudaFree(F->d_mkey);
   cudaFree(F->d_leaf_off);
@@ -236,9 +238,11 @@ bool valid_camera(const ocr_camera &c) {
          c.far_ > c.near_ && c.ell > 0.0;
 }
 
+}  // namespace
+
 // float32 camera constants (both the render and ocr_prune_noalloc read these
 // exact roundings)
-void to_cam(const ocr_camera &c, Cam &k) {
+void ocr::to_cam(const ocr_camera &c, Cam &k) {
   for (int a = 0; a < 3; ++a) {
     k.o[a] = (float)c.o[a];
     k.v[a] = (float)(c.ortho ? c.v[a] / c.near_ : c.v[a]);
@@ -259,6 +263,8 @@ void to_cam(const ocr_camera &c, Cam &k) {
   k.amin = c.ortho ? 0.f : 1.f;
   k.amax = (float)(c.ortho ? c.far_ : c.far_ / c.near_);
 }
+
+namespace {
 
 // A signed unit axis vector: the index of its non-zero entry, or -1.
 int axis_of(const double *v) {
@@ -382,10 +388,11 @@ int build_shell(const ocr_forest_desc *desc, cudaStream_t st, ocr_forest **out) 
 int plan_cameras(ocr_forest *F);
 
 // Plan one camera of a shell forest: its pruning and pair space, the segment
-// count of every ray, the size of the lists and the longest one.  Blocks the
-// host (legacy default stream).
+// count of every ray, the size of the lists and the longest one.  Runs on the
+// forest's planning stream and blocks the host until the sizes are read back.
 int plan_shell(ocr_forest *F, CamPlan &P) {
   const long long npix = P.npix;
+  cudaStream_t ps = F->plan_st;
   const Topo T{F->d_geo, nullptr, nullptr, F->N, 0, F->L, 0};
   int rc;
   P.bs_cap = std::max(bwd_scan_blocks(F->N), bwd_scan_blocks(npix)) + 2;
@@ -397,26 +404,26 @@ int plan_shell(ocr_forest *F, CamPlan &P) {
       (rc = dev_alloc(&P.d_ray_off, (size_t)npix + 1, F->bytes)))
     return rc;
   long long *h = F->h_group_slots;
-  OCR_CUDA(cudaMemsetAsync(F->d_stats, 0, kStats * sizeof(unsigned long long), 0));
-  OCR_CUDA(shell_cull(F->d_geo, F->N, F->shell, P.cam, P.d_rect, nullptr, F->d_stats, 0));
-  OCR_CUDA(bwd_leaf_scan(T, P.d_rect, P.d_sbsums, P.bs_cap, P.d_leaf_off, 0));
-  OCR_CUDA(cudaMemcpyAsync(h, P.d_leaf_off + F->N, sizeof(long long), cudaMemcpyDeviceToHost, 0));
-  OCR_CUDA(cudaStreamSynchronize(0));
+  OCR_CUDA(cudaMemsetAsync(F->d_stats, 0, kStats * sizeof(unsigned long long), ps));
+  OCR_CUDA(shell_cull(F->d_geo, F->N, F->shell, P.cam, P.d_rect, nullptr, F->d_stats, ps));
+  OCR_CUDA(bwd_leaf_scan(T, P.d_rect, P.d_sbsums, P.bs_cap, P.d_leaf_off, ps));
+  OCR_CUDA(cudaMemcpyAsync(h, P.d_leaf_off + F->N, sizeof(long long), cudaMemcpyDeviceToHost, ps));
+  OCR_CUDA(cudaStreamSynchronize(ps));
   P.npairs = h[0];
   if ((rc = dev_alloc(&P.d_pchunk, (size_t)(P.npairs / kPairChunk + 2), F->bytes)) ||
       (rc = dev_alloc(&P.d_pmask, (size_t)(P.npairs / kPairChunk + 1) * (kPairChunk / 32),
                       F->bytes)))
     return rc;
-  OCR_CUDA(bwd_chunk_map(P.d_leaf_off, F->N, P.d_pchunk, 0));
-  OCR_CUDA(cudaMemsetAsync(P.d_rcount, 0, sizeof(int) * (size_t)npix, 0));
+  OCR_CUDA(bwd_chunk_map(P.d_leaf_off, F->N, P.d_pchunk, ps));
+  OCR_CUDA(cudaMemsetAsync(P.d_rcount, 0, sizeof(int) * (size_t)npix, ps));
   OCR_CUDA(shell_pairs(0, F->d_geo, F->N, F->shell, P.cam, P.d_rect, P.d_leaf_off,
                        P.d_pchunk, P.npairs, P.d_rcount, nullptr, nullptr, nullptr, 0,
-                       F->d_stats, P.d_pmask, 0));
-  OCR_CUDA(bwd_count_scan(P.d_rcount, npix, P.d_sbsums, P.bs_cap, P.d_ray_off, 0));
-  OCR_CUDA(cudaMemcpyAsync(h, P.d_ray_off + npix, sizeof(long long), cudaMemcpyDeviceToHost, 0));
+                       F->d_stats, P.d_pmask, ps));
+  OCR_CUDA(bwd_count_scan(P.d_rcount, npix, P.d_sbsums, P.bs_cap, P.d_ray_off, ps));
+  OCR_CUDA(cudaMemcpyAsync(h, P.d_ray_off + npix, sizeof(long long), cudaMemcpyDeviceToHost, ps));
   OCR_CUDA(cudaMemcpyAsync(h + 1, F->d_stats + kStatMaxHits, sizeof(long long),
-                           cudaMemcpyDeviceToHost, 0));
-  OCR_CUDA(cudaStreamSynchronize(0));
+                           cudaMemcpyDeviceToHost, ps));
+  OCR_CUDA(cudaStreamSynchronize(ps));
   P.nhits = h[0];
   const long long longest = h[1];
   if (longest > kShellMaxCap) return OCR_ERR_UNSUPPORTED;
@@ -759,9 +766,13 @@ int ocr_set_camera(ocr_forest *F, const ocr_camera *cams, int ncams) {
 namespace {
 
 // Plan every camera of the last ocr_set_camera: run its pruning and layout
-// once on the device (legacy default stream, blocking) and size its scratch.
+// once on the device (on the forest's own planning stream, so nothing waits
+// on the legacy default stream; the host blocks on that stream for the slot
+// totals) and size its scratch.
 int plan_cameras(ocr_forest *F) {
   for (CamPlan &P : F->plans) free_plan_buffers(F, P);
+  if (!F->plan_st) OCR_CUDA(cudaStreamCreateWithFlags(&F->plan_st, cudaStreamNonBlocking));
+  cudaStream_t ps = F->plan_st;
   OCR_CUDA(bwd_scans_prepare());
   if (F->geometry == OCR_GEOM_SHELL) {
     for (CamPlan &P : F->plans) {
@@ -781,15 +792,15 @@ int plan_cameras(ocr_forest *F) {
         (rc = dev_alloc(&P.d_gslots, (size_t)G, F->bytes)))
       return rc;
     Scratch S{P.d_rect, P.d_off, nullptr, F->d_stats, nullptr, nullptr, nullptr};
-    OCR_CUDA(launch_cull_leaves(T, P.cam, S, 0));
+    OCR_CUDA(launch_cull_leaves(T, P.cam, S, ps));
     for (int l = F->L - 1; l >= 0; --l)
       OCR_CUDA(launch_union_level(T, F->level_base[l], F->level_base[l] + F->level_count[l], P.cam,
-                                  S, 0));
+                                  S, ps));
     OCR_CUDA(launch_area_scan(T, S, P.d_bsums, F->bsums_blocks, P.d_gslots, F->d_group_nodes, G,
-                              0));
+                              ps));
     OCR_CUDA(cudaMemcpyAsync(F->h_group_slots, P.d_gslots, sizeof(long long) * G,
-                             cudaMemcpyDeviceToHost, 0));
-    OCR_CUDA(cudaStreamSynchronize(0));
+                             cudaMemcpyDeviceToHost, ps));
+    OCR_CUDA(cudaStreamSynchronize(ps));
     P.gslots.assign(F->h_group_slots, F->h_group_slots + G);
     const long long total = P.gslots[G - 1];
     if ((rc = dev_alloc(&P.d_chunk, (size_t)(total / kChunk + 2), F->bytes)) ||
@@ -861,16 +872,26 @@ int enqueue_camera(ocr_forest *F, CamPlan &P, float4 *rgba, int *counts, unsigne
 
 extern "C" {
 
-int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats) {
+}  // extern "C"
+
+namespace {
+
+// Render the cameras [first, first + K) of the last ocr_set_camera into
+// d_rgba (their images concatenated in order).
+int render_plans(ocr_forest *F, int first, int K, float *d_rgba, void *stream,
+                 ocr_stats *stats) {
   if (!F || !d_rgba) return OCR_ERR_INVALID;
   if (!F->has_data || !F->has_cam || !F->has_integ) return OCR_ERR_STATE;
   if ((uintptr_t)d_rgba & 15) return OCR_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
-  const int K = (int)F->plans.size();
   const int G = (int)F->h_group_nodes.size();
+  CamPlan *plans = F->plans.data() + first;
+  long long range_pix = 0;
+  for (int k = 0; k < K; ++k) range_pix += plans[k].npix;
+  const long long pix0 = plans[0].pix_off;
   int *counts = stats ? stats->d_counts : nullptr;
   unsigned char *visible = stats ? stats->d_visible : nullptr;
-  if (counts) OCR_CUDA(cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)F->total_pix, st));
+  if (counts) OCR_CUDA(cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)range_pix, st));
   if (visible) OCR_CUDA(cudaMemsetAsync(visible, 0, (size_t)F->N, st));
   const bool timed = stats && stats->time_phases && K == 1;
   if (timed && !F->ev[0])
@@ -887,8 +908,8 @@ int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats) {
   }
   if (K == 1) {
     int rc = F->geometry == OCR_GEOM_SHELL
-                 ? enqueue_shell(F, F->plans[0], rgba, counts, visible, st, timed, launches)
-                 : enqueue_camera(F, F->plans[0], rgba, counts, visible, st, timed, subtree_ran,
+                 ? enqueue_shell(F, plans[0], rgba, counts, visible, st, timed, launches)
+                 : enqueue_camera(F, plans[0], rgba, counts, visible, st, timed, subtree_ran,
                                   launches);
     subtree_ran |= F->geometry == OCR_GEOM_SHELL;
     if (rc) return rc;
@@ -899,12 +920,13 @@ int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats) {
     const int ns = std::min(F->nstreams, K);
     for (int q = 0; q < ns; ++q) OCR_CUDA(cudaStreamWaitEvent(F->sub[q], F->fork, 0));
     for (int k = 0; k < K; ++k) {
-      CamPlan &P = F->plans[k];
-      int *cnt = counts ? counts + P.pix_off : nullptr;
+      CamPlan &P = plans[k];
+      const long long at = P.pix_off - pix0;
+      int *cnt = counts ? counts + at : nullptr;
       int rc = F->geometry == OCR_GEOM_SHELL
-                   ? enqueue_shell(F, P, rgba + P.pix_off, cnt, visible, F->sub[k % ns], false,
+                   ? enqueue_shell(F, P, rgba + at, cnt, visible, F->sub[k % ns], false,
                                    launches)
-                   : enqueue_camera(F, P, rgba + P.pix_off, cnt, visible, F->sub[k % ns], false,
+                   : enqueue_camera(F, P, rgba + at, cnt, visible, F->sub[k % ns], false,
                                     subtree_ran, launches);
       if (rc) return rc;
     }
@@ -917,7 +939,7 @@ int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats) {
   if (stats) {
     stats->launches = launches;
     if (stats->d_rects)
-      OCR_CUDA(cudaMemcpyAsync(stats->d_rects, F->plans[0].d_rect, sizeof(int4) * (size_t)F->N,
+      OCR_CUDA(cudaMemcpyAsync(stats->d_rects, plans[0].d_rect, sizeof(int4) * (size_t)F->N,
                                cudaMemcpyDeviceToDevice, st));
     if (timed) {
       OCR_CUDA(cudaEventSynchronize(F->ev[4]));
@@ -942,7 +964,7 @@ int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats) {
       stats->visible_leaves = (int64_t)h[kStatVisible];
       if (F->geometry == OCR_GEOM_SHELL) {  // two passes over every (leaf, pixel) pair
         int64_t pairs = 0;
-        for (const CamPlan &P : F->plans) pairs += 2 * P.npairs;
+        for (int k = 0; k < K; ++k) pairs += 2 * plans[k].npairs;
         stats->leaf_tests = stats->subtree_leaf_tests = pairs;
         stats->slots = 0;
       }
@@ -950,6 +972,23 @@ int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats) {
     }
   }
   return OCR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ocr_render(ocr_forest *F, float *d_rgba, void *stream, ocr_stats *stats) {
+  if (!F) return OCR_ERR_INVALID;
+  if (!F->has_cam) return OCR_ERR_STATE;
+  return render_plans(F, 0, (int)F->plans.size(), d_rgba, stream, stats);
+}
+
+int ocr_render_view(ocr_forest *F, int view, float *d_rgba, void *stream, ocr_stats *stats) {
+  if (!F) return OCR_ERR_INVALID;
+  if (!F->has_cam) return OCR_ERR_STATE;
+  if (view < 0 || view >= (int)F->plans.size()) return OCR_ERR_INVALID;
+  return render_plans(F, view, 1, d_rgba, stream, stats);
 }
 
 }  // extern "C"

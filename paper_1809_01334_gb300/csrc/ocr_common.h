@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/ocraycast.h"
+
 namespace ocr {
 
 // Camera constants in float32, derived once per ocr_set_camera.
@@ -17,6 +19,10 @@ struct Cam {
   float amin, amax;
   int w, h, ortho;
 };
+
+// The float32 constants of a host camera: one routine for every entry point
+// that reads a camera (ocr_set_camera, ocr_prune_noalloc).
+void to_cam(const ocr_camera &c, Cam &k);
 
 struct Integ {
   int method;  // 0 RK4 x nsteps; inside Algorithm 1: 1 DOPRI5, 2 Gauss-2, 3 Simpson, 4 Eq. 2.18

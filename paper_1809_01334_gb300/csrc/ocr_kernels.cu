@@ -920,6 +920,13 @@ __global__ void __launch_bounds__(kNoAllocThreads)
     vis[q] = false;
     if (k < n) {
       const int4 g = geo[k];
+      if (g.w < 0 || g.w > L) {
+        // not a cube leaf record of this depth (e.g. a shell record, whose
+        // fourth word carries the tree above bit 8): flagged, never culled
+        atomicOr(scratch + 1, 2ull);
+        if (rects) rects[k] = empty_rect();
+        continue;
+      }
       const int4 r = box_rect(c, node_lo(g, scale), ldexpf(1.f, -g.w));
       if (rects) rects[k] = r;
       vis[q] = r.x <= r.y;
@@ -951,7 +958,7 @@ __global__ void __launch_bounds__(kNoAllocThreads)
         int spins = 0;
         while (((w = atomicAdd(st + p, 0ull)) >> 62) == 0ull) {
           if (++spins > kLookbackSpins) {  // never expected: give up, flag, return
-            atomicExch(scratch + 1, 1ull);
+            atomicOr(scratch + 1, 1ull);
             break;
           }
           __nanosleep(64);
@@ -985,30 +992,14 @@ extern "C" int ocr_prune_noalloc(const int32_t *d_leaf_geo, int64_t nleaves, int
   if (cc.w < 1 || cc.h < 1 || (int64_t)cc.w * cc.h > (1ll << 31) - 1 || !(cc.near_ > 0.0) ||
       !(cc.far_ > cc.near_) || !(cc.ell > 0.0))
     return OCR_ERR_INVALID;
-  // the same float32 camera constants as ocr_set_camera
+  // the same float32 camera constants as ocr_set_camera (one routine for both)
   Cam k{};
-  for (int a = 0; a < 3; ++a) {
-    k.o[a] = (float)cc.o[a];
-    k.v[a] = (float)(cc.ortho ? cc.v[a] / cc.near_ : cc.v[a]);
-    k.lt[a] = (float)(cc.ell * cc.t[a]);
-    k.lu[a] = (float)(cc.ell * cc.u[a]);
-    k.t[a] = (float)cc.t[a];
-    k.u[a] = (float)cc.u[a];
-    k.vn[a] = (float)(cc.v[a] / cc.near_);
-  }
-  k.n = (float)cc.near_;
-  k.f = (float)cc.far_;
-  k.ell = (float)cc.ell;
-  k.cw = 0.5f * (float)(cc.w - 1);
-  k.ch = 0.5f * (float)(cc.h - 1);
-  k.w = cc.w;
-  k.h = cc.h;
-  k.ortho = cc.ortho ? 1 : 0;
-  k.amin = cc.ortho ? 0.f : 1.f;
-  k.amax = (float)(cc.ortho ? cc.far_ : cc.far_ / cc.near_);
+  to_cam(cc, k);
 
   // device address of the scratch array: looked up once per device, with that
-  // device current (the array's name is only a stand-in in host code)
+  // device current (the array's name is only a stand-in in host code).  The
+  // address is kept for the life of the process, so the call must not be used
+  // on a device after cudaDeviceReset (which unloads the module holding it).
   static std::mutex mu;
   static void *addr[kNoAllocMaxDevices] = {};
   int dev = -1;
@@ -1041,7 +1032,8 @@ extern "C" int ocr_prune_noalloc(const int32_t *d_leaf_geo, int64_t nleaves, int
                       cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return OCR_ERR_CUDA;
-  if (h_err) return OCR_ERR_DEVICE;
+  if (h_err & 2ull) return OCR_ERR_INVALID;  // a record that is not a cube leaf of this depth
+  if (h_err) return OCR_ERR_DEVICE;          // a look-back wait that gave up
   *h_nvisible = (int64_t)(h_last & kTileValue);
   return OCR_OK;
 }

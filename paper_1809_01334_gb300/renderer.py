@@ -106,6 +106,21 @@ class Renderer:
             at += c.w * c.h
         return out, views, st
 
+    def render_view(self, view: int, out: torch.Tensor | None = None, stream=None,
+                    with_counts=False):
+        """Render camera ``view`` of the last ``set_cameras`` alone into ``out``
+        ([h, w, 4]), without planning again (ocr_render_view)."""
+        cam = self.cams[view]
+        if out is None:
+            out = torch.empty((cam.h, cam.w, 4), dtype=torch.float32, device=self.device)
+        counts = (torch.empty((cam.h, cam.w), dtype=torch.int32, device=self.device)
+                  if with_counts else None)
+        st = capi.render_view(self.h, view, out, _stream_ptr(stream), d_counts=counts,
+                              fill_counters=with_counts)
+        if with_counts:
+            st["counts"] = counts
+        return out, st
+
     def render(self, out: torch.Tensor | None = None, stream=None, with_index=False,
                fill_counters=False, time_phases=False):
         """Render into ``out`` ([h, w, 4] float32 on the device).  With

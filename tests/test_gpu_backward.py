@@ -29,6 +29,15 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
+def _per_element(g, g_ref, what):
+    """Every coordinate: |g - g_ref| <= 1e-3 max(|g_ref|, 1e-3 max|g_ref|)."""
+    g, g_ref = np.asarray(g).reshape(-1), np.asarray(g_ref).reshape(-1)
+    scale = np.maximum(np.abs(g_ref), 1e-3 * np.abs(g_ref).max())
+    bad = np.abs(g - g_ref) > 1e-3 * scale
+    assert not bad.any(), (f"{what}: {int(bad.sum())} of {g.size} coordinates off, worst "
+                           f"{float((np.abs(g - g_ref) / scale).max()):.3e}")
+
+
 @pytest.mark.parametrize("kind", ["uniform2", "adaptive"])
 @pytest.mark.parametrize("integ", [{"method": "rk4", "nsteps": 4},
                                    {"method": "dopri5", "tol": 1e-6, "c_rk": 0.5, "max_depth": 16}])
@@ -44,6 +53,8 @@ def test_gradient_matches_oracle(kind, integ):
     rn, rt = O.render_grad(f, tf, cam, integ, W.astype(np.float64), bg=bg)
     en, et = _rel(gn.cpu().numpy().astype(np.float64), rn), _rel(gt.cpu().numpy().astype(np.float64), rt)
     assert en <= 1e-3 and et <= 1e-3, (en, et)
+    _per_element(gn.cpu().numpy().astype(np.float64), rn, "nodal")
+    _per_element(gt.cpu().numpy().astype(np.float64), rt, "knots")
     r.close()
 
 
@@ -137,6 +148,8 @@ def test_long_rays_gradient():
     rn, rt = O.render_grad(f, tf, cam, integ, W.astype(np.float64))
     en, et = _rel(gn.cpu().numpy().astype(np.float64), rn), _rel(gt.cpu().numpy().astype(np.float64), rt)
     assert en <= 1e-3 and et <= 1e-3, (en, et)
+    _per_element(gn.cpu().numpy().astype(np.float64), rn, "nodal")
+    _per_element(gt.cpu().numpy().astype(np.float64), rt, "knots")
     r.close()
 
 

@@ -120,3 +120,38 @@ def test_autotune_keeps_the_fastest_valid_setting(kind):
     ref = O.render(f, tf, cams[1], INTEG)
     assert np.abs(views[1].cpu().numpy() - ref["rgba"]).max() <= 1e-4
     r.close()
+
+
+@pytest.mark.parametrize("kind", ["cube", "shell"])
+def test_render_view_equals_the_batch(kind):
+    """ocr_render_view renders one planned camera of a batch alone: the same
+    pixels and segment counts as that camera's part of the batch render, for
+    every view, in any order; a view out of range is rejected."""
+    from paper_1809_01334_gb300 import Renderer, capi
+    if kind == "cube":
+        f, tf, _ = I.preset_small()
+        cams = _cams()
+    else:
+        f, tf, _ = I.preset_shell_small()
+        cams = [I.perspective_camera(41 + k, 24 + 7 * k, 20, dist=(2.2, 2.6), target=(0.0, 0.0, 0.0))
+                for k in range(3)]
+    r = Renderer(f, tf, INTEG)
+    r.set_cameras(cams)
+    flat, views, st = r.render_batch(with_index=True)
+    torch.cuda.synchronize()
+    at = 0
+    starts = []
+    for c in cams:
+        starts.append(at)
+        at += c.w * c.h
+    for k in reversed(range(len(cams))):
+        img, s1 = r.render_view(k, with_counts=True)
+        torch.cuda.synchronize()
+        assert torch.equal(img, views[k])
+        cnt = st["counts"][starts[k]:starts[k] + cams[k].w * cams[k].h].view(cams[k].h, cams[k].w)
+        assert torch.equal(s1["counts"], cnt)
+        assert s1["segments"] == int(cnt.sum())
+    with pytest.raises(capi.OcrError) as e:
+        capi.render_view(r.h, len(cams), views[0])
+    assert e.value.code == capi.ERR_INVALID
+    r.close()

@@ -19,6 +19,15 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
+def _per_element(g, g_ref, what):
+    """Every coordinate: |g - g_ref| <= 1e-3 max(|g_ref|, 1e-3 max|g_ref|)."""
+    g, g_ref = np.asarray(g).reshape(-1), np.asarray(g_ref).reshape(-1)
+    scale = np.maximum(np.abs(g_ref), 1e-3 * np.abs(g_ref).max())
+    bad = np.abs(g - g_ref) > 1e-3 * scale
+    assert not bad.any(), (f"{what}: {int(bad.sum())} of {g.size} coordinates off, worst "
+                           f"{float((np.abs(g - g_ref) / scale).max()):.3e}")
+
+
 @pytest.mark.parametrize("integ", [{"method": "rk4", "nsteps": 4}, DOPRI])
 def test_shell_gradient_matches_oracle(integ):
     from paper_1809_01334_gb300 import Renderer
@@ -35,6 +44,8 @@ def test_shell_gradient_matches_oracle(integ):
     en = _rel(gn.cpu().numpy().astype(np.float64), rn)
     et = _rel(gt.cpu().numpy().astype(np.float64), rt)
     assert en <= 1e-3 and et <= 1e-3, (en, et)
+    _per_element(gn.cpu().numpy().astype(np.float64), rn, "nodal")
+    _per_element(gt.cpu().numpy().astype(np.float64), rt, "knots")
     r.close()
 
 
@@ -93,8 +104,9 @@ def test_shell_autograd_l2_loss_against_perturbed_target():
 def test_c5_full_size_gradient_on_sampled_rows():
     """The differentiation workload at full size (shell levels 4..6, 1024x1024,
     DOPRI5 tol 1e-5): the GPU adjoint of the L2 loss against the perturbed
-    target, restricted to three image rows, against the FP64 oracle gradient
-    of the same restricted loss."""
+    target, restricted to 32 image rows spread over the image, against the
+    FP64 oracle gradient of the same restricted loss: the vector norms and
+    every coordinate."""
     from paper_1809_01334_gb300 import Renderer
     f, tf, cam, integ = I.preset_c5()
     r = Renderer(f, tf, integ)
@@ -107,7 +119,7 @@ def test_c5_full_size_gradient_on_sampled_rows():
     target = target.clone()
     r.set_data(base, r.tf)
     img, _ = r.render()
-    rows = [300, 512, 700]
+    rows = np.linspace(0, cam.h - 1, 32).astype(int).tolist()
     W = torch.zeros_like(img)
     W[rows] = 2.0 * (img[rows] - target[rows])
     gn, gt = r.backward(W)
@@ -117,4 +129,6 @@ def test_c5_full_size_gradient_on_sampled_rows():
     en = _rel(gn.cpu().numpy().astype(np.float64), rn)
     et = _rel(gt.cpu().numpy().astype(np.float64), rt)
     assert en <= 1e-3 and et <= 1e-3, (en, et)
+    _per_element(gn.cpu().numpy().astype(np.float64), rn, "nodal")
+    _per_element(gt.cpu().numpy().astype(np.float64), rt, "knots")
     r.close()
