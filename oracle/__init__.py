@@ -32,8 +32,10 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
             os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "ocr_oracle.h"))):
         tmp = _SO + f".tmp{os.getpid()}"
+        # -ffp-contract=off: every operation rounds as written (no fused
+        # multiply-add the source does not spell out), in FP64 and FP32 alike
         subprocess.check_call(["gcc", "-O2", "-std=c99", "-D_DEFAULT_SOURCE", "-fopenmp", "-fPIC",
-                               "-shared", "-o", tmp, src, "-lm"])
+                               "-ffp-contract=off", "-shared", "-o", tmp, src, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -51,6 +53,14 @@ class Camera_(C.Structure):
     _fields_ = [("o", C.c_double * 3), ("v", C.c_double * 3), ("t", C.c_double * 3),
                 ("u", C.c_double * 3), ("ell", C.c_double), ("near_", C.c_double),
                 ("far_", C.c_double), ("w", C.c_int), ("h", C.c_int), ("ortho", C.c_int)]
+
+
+class Cam32_(C.Structure):
+    _fields_ = [("o", C.c_float * 3), ("v", C.c_float * 3), ("lt", C.c_float * 3),
+                ("lu", C.c_float * 3), ("t", C.c_float * 3), ("u", C.c_float * 3),
+                ("vn", C.c_float * 3), ("n", C.c_float), ("f", C.c_float), ("ell", C.c_float),
+                ("cw", C.c_float), ("ch", C.c_float), ("amin", C.c_float), ("amax", C.c_float),
+                ("w", C.c_int), ("h", C.c_int), ("ortho", C.c_int)]
 
 
 class Integrator_(C.Structure):
@@ -89,16 +99,26 @@ def lib():
         _lib.orc_segment_ab.argtypes = [P(Forest_), P(Integrator_), C.c_int, d, d, C.c_double,
                                         C.c_double, d, P(C.c_int64)]
         _lib.orc_cull.argtypes = [P(Forest_), P(Camera_), P(C.c_int32), P(C.c_uint8),
-                                  P(C.c_uint8), C.c_double]
+                                  P(C.c_uint8), C.c_double, C.c_int]
+        f = P(C.c_float)
+        _lib.orc_camera32.argtypes = [P(Camera_), P(Cam32_)]
+        _lib.orc_pixel_ray32.argtypes = [P(Cam32_), C.c_int, C.c_int, f, f]
+        _lib.orc_shell_tables32.argtypes = [P(Forest_), f, f]
+        _lib.orc_leaf_rect32.argtypes = [P(Forest_), P(Cam32_), f, f, C.c_int, P(C.c_int32)]
+        _lib.orc_leaf_rect32.restype = C.c_int
+        _lib.orc_ray_leaf32.argtypes = [P(Forest_), f, f, C.c_int, f, f, C.c_float, C.c_float,
+                                        f, f]
+        _lib.orc_ray_leaf32.restype = C.c_int
         _lib.orc_render.argtypes = [P(Forest_), P(Camera_), P(Integrator_), P(C.c_int), C.c_int,
                                     d, P(C.c_int32), P(C.c_uint8), C.c_double, C.c_double,
                                     C.c_int, P(C.c_int64)]
         _lib.orc_render.restype = C.c_int64
         _lib.orc_render_ex.argtypes = [P(Forest_), P(Camera_), P(Integrator_), P(C.c_int),
                                        C.c_int, d, P(C.c_int32), P(C.c_int32), P(C.c_uint8),
-                                       C.c_double, C.c_double, C.c_int, P(C.c_int64)]
+                                       C.c_double, C.c_double, C.c_int, P(C.c_int64), C.c_int]
         _lib.orc_render_ex.restype = C.c_int64
-        _lib.orc_render_grad.argtypes = [P(Forest_), P(Camera_), P(Integrator_), d, d, d, C.c_int]
+        _lib.orc_render_grad.argtypes = [P(Forest_), P(Camera_), P(Integrator_), d, d, d, C.c_int,
+                                         C.c_int]
         _lib.orc_render_grad.restype = C.c_int
     return _lib
 
@@ -277,8 +297,55 @@ def leaf_rect(of: OracleForest, cam, leaf, band_px: float = 0.0):
     return bool(vis), rect, pext, bool(unc.value)
 
 
-def cull(forest, tf, cam, band_px: float = 4e-3):
-    """Visible flag, pixel rectangle {i0,i1,j0,j1} and tie flag of every leaf."""
+def camera32(cam):
+    """The FP32 camera constants of the index decisions (orc_camera32)."""
+    k = Cam32_()
+    lib().orc_camera32(C.byref(camera_struct(cam)), C.byref(k))
+    return k
+
+
+def shell_tables32(of: OracleForest):
+    """FP32 plane tangents and radii of a shell forest (2^L + 1 each)."""
+    n = (1 << of.s.max_level) + 1
+    tt, rt = np.zeros(n, np.float32), np.zeros(n, np.float32)
+    lib().orc_shell_tables32(C.byref(of.s), _ptr(tt, C.c_float), _ptr(rt, C.c_float))
+    return tt, rt
+
+
+def pixel_ray32(k32, i, j):
+    org, d = np.zeros(3, np.float32), np.zeros(3, np.float32)
+    lib().orc_pixel_ray32(C.byref(k32), int(i), int(j), _ptr(org, C.c_float), _ptr(d, C.c_float))
+    return org, d
+
+
+def leaf_rect32(of: OracleForest, k32, leaf, tables=None):
+    """(visible, rect) of one leaf by the FP32 decision."""
+    rect = np.zeros(4, dtype=np.int32)
+    tt, rt = tables if tables is not None else (None, None)
+    vis = lib().orc_leaf_rect32(C.byref(of.s), C.byref(k32),
+                                None if tt is None else _ptr(tt, C.c_float),
+                                None if rt is None else _ptr(rt, C.c_float), int(leaf),
+                                _ptr(rect, C.c_int32))
+    return bool(vis), rect
+
+
+def ray_leaf32(of: OracleForest, leaf, org32, d32, amin, amax, tables=None):
+    """FP32 intervals [(a_in, a_out), ...] of the ray in the leaf."""
+    a, b = np.zeros(2, np.float32), np.zeros(2, np.float32)
+    tt, rt = tables if tables is not None else (None, None)
+    o = np.ascontiguousarray(org32, np.float32)
+    d = np.ascontiguousarray(d32, np.float32)
+    n = lib().orc_ray_leaf32(C.byref(of.s), None if tt is None else _ptr(tt, C.c_float),
+                             None if rt is None else _ptr(rt, C.c_float), int(leaf),
+                             _ptr(o, C.c_float), _ptr(d, C.c_float), float(amin), float(amax),
+                             _ptr(a, C.c_float), _ptr(b, C.c_float))
+    return [(float(a[k]), float(b[k])) for k in range(n)]
+
+
+def cull(forest, tf, cam, band_px: float = 4e-3, decide32: bool = True):
+    """Visible flag, pixel rectangle {i0,i1,j0,j1} and tie flag of every leaf.
+    decide32 (default): the FP32 decision (no ties flagged); else FP64 with the
+    leaves inside the band_px tie band flagged."""
     of = OracleForest(forest, tf)
     cs = camera_struct(cam)
     n = forest.nleaves
@@ -286,15 +353,18 @@ def cull(forest, tf, cam, band_px: float = 4e-3):
     vis = np.zeros(n, dtype=np.uint8)
     unc = np.zeros(n, dtype=np.uint8)
     lib().orc_cull(C.byref(of.s), C.byref(cs), _ptr(rect, C.c_int32), _ptr(vis, C.c_uint8),
-                   _ptr(unc, C.c_uint8), float(band_px))
+                   _ptr(unc, C.c_uint8), float(band_px), int(bool(decide32)))
     return {"rect": rect, "visible": vis.astype(bool), "uncertain": unc.astype(bool)}
 
 
 def render(forest, tf, cam, integ: dict, rows=None, bg=(0.0, 0.0, 0.0), nthreads: int = 0,
-           band_px: float = 4e-3, band_rel: float = 1e-5):
+           band_px: float = 4e-3, band_rel: float = 1e-5, decide32: bool = True):
     """Render the listed rows (default: all).  Returns rgba [nrows, w, 4] (FP64),
     per-ray segment counts, per-ray tie flags and tie counts (leaves of the ray
-    with a decision inside the tie band), total segments and RK steps."""
+    with a decision inside the tie band), total segments and RK steps.
+    decide32 (default): visibility, rays and intervals by the FP32 decisions,
+    values in FP64 (only isosurface sample ties are flagged); else everything
+    in FP64 with the geometric ties flagged."""
     of = OracleForest(forest, tf)
     cs = camera_struct(cam)
     ist = integrator_struct(integ, bg)
@@ -311,7 +381,8 @@ def render(forest, tf, cam, integ: dict, rows=None, bg=(0.0, 0.0, 0.0), nthreads
     total = lib().orc_render_ex(C.byref(of.s), C.byref(cs), C.byref(ist), _ptr(rows_arr, C.c_int),
                                 nr, _ptr(rgba, C.c_double), _ptr(counts, C.c_int32),
                                 _ptr(cross, C.c_int32), _ptr(unc, C.c_uint8), float(band_px),
-                                float(band_rel), int(nthreads), C.byref(steps))
+                                float(band_rel), int(nthreads), C.byref(steps),
+                                int(bool(decide32)))
     if total < 0:
         raise MemoryError("oracle render: allocation failed")
     return {"rgba": rgba, "counts": counts, "crossings": cross, "uncertain": unc.astype(bool),
@@ -319,7 +390,8 @@ def render(forest, tf, cam, integ: dict, rows=None, bg=(0.0, 0.0, 0.0), nthreads
             "segments": int(total), "steps": int(steps.value), "rows": rows_arr}
 
 
-def render_grad(forest, tf, cam, integ: dict, dL_drgba, bg=(0.0, 0.0, 0.0), nthreads: int = 0):
+def render_grad(forest, tf, cam, integ: dict, dL_drgba, bg=(0.0, 0.0, 0.0), nthreads: int = 0,
+                decide32: bool = True):
     """FP64 gradient of L with respect to nodal values [N, 8] (cube) or
     [N, 27] (shell) and knots [8, 4], given dL/d(rgba) [h, w, 4]."""
     of = OracleForest(forest, tf)
@@ -329,7 +401,10 @@ def render_grad(forest, tf, cam, integ: dict, dL_drgba, bg=(0.0, 0.0, 0.0), nthr
     gn = np.zeros((forest.nleaves, of.stride))
     gt = np.zeros((8, 4))
     rc = lib().orc_render_grad(C.byref(of.s), C.byref(cs), C.byref(ist), _ptr(gb, C.c_double),
-                               _ptr(gn, C.c_double), _ptr(gt, C.c_double), int(nthreads))
+                               _ptr(gn, C.c_double), _ptr(gt, C.c_double), int(nthreads),
+                               int(bool(decide32)))
+    if rc == -1:
+        raise MemoryError("oracle gradient: allocation failed")
     if rc != 0:
         raise ValueError("oracle gradient: only RK4 and DOPRI5 are differentiated")
     return gn, gt

@@ -10,6 +10,7 @@
  */
 #include "ocr_oracle.h"
 
+#include <float.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -320,6 +321,10 @@ static int ray_cube_leaf(const orc_forest *F, int leaf, const double *org, const
   for (int a = 0; a < 3; ++a) {
     double b0 = lo[a], b1 = lo[a] + h;
     if (dir[a] == 0.0) {
+      /* parallel to the slab: a tie when the ray runs within the band of a face */
+      double sc = fabs(org[a]) > 1.0 ? fabs(org[a]) : 1.0;
+      if (tie && (fabs(org[a] - b0) <= band_rel * sc || fabs(org[a] - b1) <= band_rel * sc))
+        *tie = 1;
       if (org[a] < b0 || org[a] > b1) { /* parallel to the slab and outside it */
         a_in[0] = INFINITY;
         a_out[0] = -INFINITY;
@@ -360,7 +365,8 @@ static int ray_shell_leaf(const orc_forest *F, int leaf, const double *org, cons
     double tn = eq_tan(lo[s / 2] + ((s & 1) ? h : 0.0)), sg = (s & 1) ? -1.0 : 1.0, m[3];
     for (int c = 0; c < 3; ++c) m[c] = sg * (e[c] - tn * fr[0][c]);
     double g0 = dot3(org, m), g1 = dot3(dir, m);
-    if (g1 == 0.0) {
+    if (g1 == 0.0) { /* parallel to the plane: a tie when it runs within the band of it */
+      if (tie && fabs(g0) <= band_rel * sqrt(dot3(org, org) * dot3(m, m))) *tie = 1;
       if (g0 < 0.0) return 0;
       continue;
     }
@@ -414,6 +420,277 @@ int orc_ray_leaf_tie(const orc_forest *F, int leaf, const double *org, const dou
 int orc_ray_leaf(const orc_forest *F, int leaf, const double *org, const double *dir, double amin,
                  double amax, double *a_in, double *a_out) {
   return orc_ray_leaf_tie(F, leaf, org, dir, amin, amax, a_in, a_out, 0.0, NULL);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Index decisions in FP32                                                   */
+/* ------------------------------------------------------------------------ */
+/* Which leaves a camera sees, which (leaf, ray) pairs give segments and where
+ * a segment ends are thresholds decided by floating point.  The oracle takes
+ * these decisions in FP32, the precision of the GPU path, by one canonical
+ * evaluation of the formulas above: the camera constants of Eq. 2.5 rounded
+ * once from FP64 to FP32 (step a1 of the path), then every operation rounded
+ * to nearest once, in the order written here, a fused multiply-add only where
+ * fma32 is written, subnormal operands and results flushed to signed zero
+ * (the GPU runs with flush-to-zero).  The mathematics is that of
+ * orc_pixel_ray, orc_leaf_rect and orc_ray_leaf; only the precision and the
+ * fixed order differ.  The segment values are still integrated in FP64, over
+ * the FP32 ray and end points. */
+
+static float fz(float x) { return fabsf(x) < FLT_MIN ? copysignf(0.0f, x) : x; }
+static float add32(float a, float b) { return fz(fz(a) + fz(b)); }
+static float sub32(float a, float b) { return fz(fz(a) - fz(b)); }
+static float mul32(float a, float b) { return fz(fz(a) * fz(b)); }
+static float div32(float a, float b) { return fz(fz(a) / fz(b)); }
+static float fma32(float a, float b, float c) { return fz(fmaf(fz(a), fz(b), fz(c))); }
+static float sqrt32(float a) { return fz(sqrtf(fz(a))); }
+static float min32(float a, float b) { return fminf(fz(a), fz(b)); }
+static float max32(float a, float b) { return fmaxf(fz(a), fz(b)); }
+
+void orc_camera32(const orc_camera *C, orc_cam32 *K) {
+  for (int a = 0; a < 3; ++a) {
+    K->o[a] = (float)C->o[a];
+    K->v[a] = (float)(C->ortho ? C->v[a] / C->near_ : C->v[a]);
+    K->lt[a] = (float)(C->ell * C->t[a]);
+    K->lu[a] = (float)(C->ell * C->u[a]);
+    K->t[a] = (float)C->t[a];
+    K->u[a] = (float)C->u[a];
+    K->vn[a] = (float)(C->v[a] / C->near_);
+  }
+  K->n = (float)C->near_;
+  K->f = (float)C->far_;
+  K->ell = (float)C->ell;
+  K->cw = 0.5f * (float)(C->w - 1);
+  K->ch = 0.5f * (float)(C->h - 1);
+  K->amin = C->ortho ? 0.0f : 1.0f;
+  K->amax = (float)(C->ortho ? C->far_ : C->far_ / C->near_);
+  K->w = C->w;
+  K->h = C->h;
+  K->ortho = C->ortho;
+}
+
+/* Eq. 2.5 in FP32: offset ell ((i - cw) t + (j - ch) u) with ell t, ell u
+ * rounded once; perspective: origin o, direction v + offset; orthographic:
+ * origin o + offset, direction v/n. */
+void orc_pixel_ray32(const orc_cam32 *K, int i, int j, float *org, float *dir) {
+  float di = sub32((float)i, K->cw), dj = sub32((float)j, K->ch);
+  for (int a = 0; a < 3; ++a) {
+    float off = fma32(dj, K->lu[a], mul32(di, K->lt[a]));
+    if (K->ortho) {
+      org[a] = add32(K->o[a], off);
+      dir[a] = K->v[a];
+    } else {
+      org[a] = K->o[a];
+      dir[a] = add32(K->v[a], off);
+    }
+  }
+}
+
+/* Sec. 2.2: project the camera-space box [blo, bhi] clipped to the visible
+ * depth range; the rectangle of the pixel centres inside (closed), clipped to
+ * the image.  Returns 1 if it is not empty. */
+static int project_box32(const orc_cam32 *K, const float *blo, const float *bhi, int32_t *rect) {
+  rect[0] = 0; rect[1] = -1; rect[2] = 0; rect[3] = -1;
+  float zlo = max32(blo[2], K->ortho ? 0.0f : K->n), zhi = min32(bhi[2], K->f);
+  if (!(zlo <= zhi)) return 0;
+  float pmin[2], pmax[2];
+  for (int a = 0; a < 2; ++a) {
+    float x0 = blo[a], x1 = bhi[a], lo_p, hi_p;
+    if (K->ortho) {
+      lo_p = div32(x0, K->ell);
+      hi_p = div32(x1, K->ell);
+    } else {
+      /* the projection x n / (z ell) at the box's nearest and farthest depth */
+      float sl = div32(K->n, mul32(zlo, K->ell)), sh = div32(K->n, mul32(zhi, K->ell));
+      float p00 = mul32(x0, sl), p01 = mul32(x0, sh), p10 = mul32(x1, sl), p11 = mul32(x1, sh);
+      lo_p = min32(min32(p00, p01), min32(p10, p11));
+      hi_p = max32(max32(p00, p01), max32(p10, p11));
+    }
+    float cen = a == 0 ? K->cw : K->ch;
+    pmin[a] = add32(lo_p, cen);
+    pmax[a] = add32(hi_p, cen);
+  }
+  float i0 = fmaxf(ceilf(pmin[0]), 0.0f), i1 = fminf(floorf(pmax[0]), (float)(K->w - 1));
+  float j0 = fmaxf(ceilf(pmin[1]), 0.0f), j1 = fminf(floorf(pmax[1]), (float)(K->h - 1));
+  if (!(i0 <= i1 && j0 <= j1)) return 0;
+  rect[0] = (int32_t)i0; rect[1] = (int32_t)i1; rect[2] = (int32_t)j0; rect[3] = (int32_t)j1;
+  return 1;
+}
+
+/* The shell's plane and radius tables in FP32: tan(pi/4 (2 k 2^-L - 1)) (odd
+ * about the tree centre, exactly -+1 at its edges) and r0 + (r1 - r0) k 2^-L,
+ * k = 0 .. 2^L, each rounded once from FP64.  tan and rad hold 2^L + 1 floats. */
+void orc_shell_tables32(const orc_forest *F, float *tan_t, float *rad_t) {
+  int L = F->max_level, n = (1 << L) + 1;
+  for (int k = 0; k < n; ++k) {
+    double x = ldexp(2.0 * k, -L) - 1.0, ax = fabs(x);
+    double v = ax == 1.0 ? 1.0 : tan(0.25 * ORC_PI * ax);
+    tan_t[k] = (float)(x < 0.0 ? -v : v);
+    rad_t[k] = (float)(F->r0 + (F->r1 - F->r0) * ldexp((double)k, -L));
+  }
+}
+
+/* One shell leaf in FP32: its frame, the tangents of its four planes (xi low,
+ * xi high, eta low, eta high) and its radii. */
+typedef struct {
+  float n[3], e1[3], e2[3], T[4], rin, rout;
+} leaf32;
+
+static void shell_leaf32(const orc_forest *F, const float *tan_t, const float *rad_t, int leaf,
+                         leaf32 *q) {
+  int L = F->max_level, sz = 1 << (L - F->level[leaf]);
+  const int32_t *a = F->anchor + 3 * (size_t)leaf;
+  const double(*fr)[3] = F->frames[F->tree[leaf]];
+  for (int c = 0; c < 3; ++c) {
+    q->n[c] = (float)fr[0][c];
+    q->e1[c] = (float)fr[1][c];
+    q->e2[c] = (float)fr[2][c];
+  }
+  q->T[0] = tan_t[a[0]];
+  q->T[1] = tan_t[a[0] + sz];
+  q->T[2] = tan_t[a[1]];
+  q->T[3] = tan_t[a[1] + sz];
+  q->rin = rad_t[a[2]];
+  q->rout = rad_t[a[2] + sz];
+}
+
+/* Sec. 2.2 in FP32, cube: the box [lo, lo + h]^3 mapped by Eq. 2.6 (an affine
+ * map: centre +- half-extent |R| h/2 per camera axis); shell: the 8 mapped
+ * corners' box widened by delta = r_out (1 - min_i d_i . c) (the bound of
+ * leaf_corners) times |t|, |u|, |v|/n.  Then project_box32. */
+int orc_leaf_rect32(const orc_forest *F, const orc_cam32 *K, const float *tan_t,
+                    const float *rad_t, int leaf, int32_t *rect) {
+  const float *rows[3] = {K->t, K->u, K->vn};
+  float blo[3], bhi[3];
+  if (F->geometry != 1) {
+    float scale = ldexpf(1.0f, -F->max_level), h = ldexpf(1.0f, -(int)F->level[leaf]);
+    float hh = mul32(0.5f, h), cc[3];
+    for (int a = 0; a < 3; ++a)
+      cc[a] = sub32(add32((float)F->anchor[3 * (size_t)leaf + a] * scale, hh), K->o[a]);
+    for (int r = 0; r < 3; ++r) {
+      const float *R = rows[r];
+      float X = fma32(R[0], cc[0], fma32(R[1], cc[1], mul32(R[2], cc[2])));
+      float E = mul32(hh, add32(add32(fabsf(R[0]), fabsf(R[1])), fabsf(R[2])));
+      blo[r] = sub32(X, E);
+      bhi[r] = add32(X, E);
+    }
+    return project_box32(K, blo, bhi, rect);
+  }
+  leaf32 q;
+  shell_leaf32(F, tan_t, rad_t, leaf, &q);
+  float len[3];
+  for (int r = 0; r < 3; ++r) {
+    const float *R = rows[r];
+    len[r] = sqrt32(fma32(R[2], R[2], fma32(R[1], R[1], mul32(R[0], R[0]))));
+  }
+  float d[4][3], cs[3] = {0.0f, 0.0f, 0.0f};
+  for (int c = 0; c < 4; ++c) {
+    float ta = (c & 1) ? q.T[1] : q.T[0], tb = (c & 2) ? q.T[3] : q.T[2];
+    for (int a = 0; a < 3; ++a) d[c][a] = fma32(tb, q.e2[a], fma32(ta, q.e1[a], q.n[a]));
+    float nn = fma32(d[c][2], d[c][2], fma32(d[c][1], d[c][1], mul32(d[c][0], d[c][0])));
+    float inv = div32(1.0f, sqrt32(nn));
+    for (int a = 0; a < 3; ++a) {
+      d[c][a] = mul32(d[c][a], inv);
+      cs[a] = add32(cs[a], d[c][a]);
+    }
+  }
+  float csn = div32(1.0f, sqrt32(fma32(cs[2], cs[2], fma32(cs[1], cs[1], mul32(cs[0], cs[0])))));
+  float cmin = 1.0f;
+  for (int c = 0; c < 4; ++c)
+    cmin = min32(cmin, mul32(fma32(d[c][2], cs[2], fma32(d[c][1], cs[1], mul32(d[c][0], cs[0]))),
+                             csn));
+  float delta = mul32(q.rout, sub32(1.0f, cmin));
+  for (int r = 0; r < 3; ++r) {
+    blo[r] = INFINITY;
+    bhi[r] = -INFINITY;
+  }
+  for (int c = 0; c < 8; ++c) {
+    float rad = (c & 4) ? q.rout : q.rin, x[3];
+    for (int a = 0; a < 3; ++a) x[a] = fma32(rad, d[c & 3][a], -K->o[a]);
+    for (int r = 0; r < 3; ++r) {
+      const float *R = rows[r];
+      float X = fma32(R[0], x[0], fma32(R[1], x[1], mul32(R[2], x[2])));
+      blo[r] = min32(blo[r], X);
+      bhi[r] = max32(bhi[r], X);
+    }
+  }
+  for (int r = 0; r < 3; ++r) {
+    float ext = mul32(delta, len[r]);
+    blo[r] = sub32(blo[r], ext);
+    bhi[r] = add32(bhi[r], ext);
+  }
+  return project_box32(K, blo, bhi, rect);
+}
+
+/* Ray / leaf intersection in FP32, clipped to [amin, amax]: the slab test for
+ * the cube (1/d rounded once, 0 for d = 0); for the shell the four half-spaces
+ * of ray_shell_leaf, each crossing -(o . m) / (r . m) with m = e - T n, and the
+ * spheres at -b -+ sqrt((R^2 - |p|^2) / |r|^2), b = (o . r) / |r|^2,
+ * p = o - b r.  Returns the number of intervals (0..2), nearest first. */
+int orc_ray_leaf32(const orc_forest *F, const float *tan_t, const float *rad_t, int leaf,
+                   const float *org, const float *dir, float amin, float amax, float *a_in,
+                   float *a_out) {
+  float t0 = amin, t1 = amax;
+  if (F->geometry != 1) {
+    float scale = ldexpf(1.0f, -F->max_level), h = ldexpf(1.0f, -(int)F->level[leaf]);
+    for (int a = 0; a < 3; ++a) {
+      float b0 = (float)F->anchor[3 * (size_t)leaf + a] * scale, b1 = add32(b0, h);
+      if (dir[a] == 0.0f) {
+        if (org[a] < b0 || org[a] > b1) return 0;
+        continue;
+      }
+      float iv = div32(1.0f, dir[a]);
+      float s0 = mul32(sub32(b0, org[a]), iv), s1 = mul32(sub32(b1, org[a]), iv);
+      t0 = max32(t0, min32(s0, s1));
+      t1 = min32(t1, max32(s0, s1));
+    }
+    if (!(t1 > t0)) return 0;
+    a_in[0] = t0;
+    a_out[0] = t1;
+    return 1;
+  }
+  leaf32 q;
+  shell_leaf32(F, tan_t, rad_t, leaf, &q);
+  for (int s = 0; s < 4; ++s) {
+    const float *e = s < 2 ? q.e1 : q.e2;
+    float m[3];
+    for (int c = 0; c < 3; ++c) m[c] = fma32(-q.T[s], q.n[c], e[c]);
+    float g0 = fma32(m[0], org[0], fma32(m[1], org[1], mul32(m[2], org[2])));
+    float g1 = fma32(m[0], dir[0], fma32(m[1], dir[1], mul32(m[2], dir[2])));
+    int upper = s & 1; /* the cone is x . m >= 0 for the lower planes, <= 0 for the upper */
+    if (g1 == 0.0f) {
+      if ((upper ? -g0 : g0) < 0.0f) return 0;
+      continue;
+    }
+    float a = div32(-g0, g1);
+    if ((upper ? -g1 : g1) > 0.0f)
+      t0 = max32(t0, a);
+    else
+      t1 = min32(t1, a);
+  }
+  float rr = fma32(dir[0], dir[0], fma32(dir[1], dir[1], mul32(dir[2], dir[2])));
+  float b = div32(fma32(org[0], dir[0], fma32(org[1], dir[1], mul32(org[2], dir[2]))), rr);
+  float p[3];
+  for (int c = 0; c < 3; ++c) p[c] = fma32(-b, dir[c], org[c]);
+  float pp = fma32(p[0], p[0], fma32(p[1], p[1], mul32(p[2], p[2])));
+  float hout = fma32(q.rout, q.rout, -pp);
+  if (!(hout > 0.0f)) return 0;
+  float so = sqrt32(div32(hout, rr));
+  t0 = max32(t0, sub32(-b, so));
+  t1 = min32(t1, add32(-b, so));
+  float hin = fma32(q.rin, q.rin, -pp);
+  int n = 0;
+  if (hin > 0.0f) { /* the inner ball's chord is cut out */
+    float si = sqrt32(div32(hin, rr));
+    float c0 = min32(t1, sub32(-b, si)), c1 = max32(t0, add32(-b, si));
+    if (c0 > t0) { a_in[n] = t0; a_out[n] = c0; ++n; }
+    if (t1 > c1) { a_in[n] = c1; a_out[n] = t1; ++n; }
+  } else if (t1 > t0) {
+    a_in[0] = t0;
+    a_out[0] = t1;
+    n = 1;
+  }
+  return n;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -727,17 +1004,43 @@ void orc_segment_ab(const orc_forest *F, const orc_integrator *I, int leaf, cons
 /* Culling and rendering                                                     */
 /* ------------------------------------------------------------------------ */
 
+/* The shell's FP32 tables for the decisions (NULL for the cube); freed by
+ * the caller. */
+static int tables32(const orc_forest *F, float **tan_t, float **rad_t) {
+  *tan_t = *rad_t = NULL;
+  if (F->geometry != 1) return 0;
+  size_t n = ((size_t)1 << F->max_level) + 1;
+  *tan_t = (float *)malloc(sizeof(float) * n);
+  *rad_t = (float *)malloc(sizeof(float) * n);
+  if (!*tan_t || !*rad_t) {
+    free(*tan_t);
+    free(*rad_t);
+    return -1;
+  }
+  orc_shell_tables32(F, *tan_t, *rad_t);
+  return 0;
+}
+
 void orc_cull(const orc_forest *F, const orc_camera *C, int32_t *rect, uint8_t *visible,
-              uint8_t *uncertain, double band_px) {
+              uint8_t *uncertain, double band_px, int decide32) {
+  orc_cam32 K;
+  float *tan_t = NULL, *rad_t = NULL;
+  if (decide32) {
+    orc_camera32(C, &K);
+    if (tables32(F, &tan_t, &rad_t)) return;
+  }
 #pragma omp parallel for schedule(static)
   for (int l = 0; l < F->nleaves; ++l) {
     int32_t r[4];
     int unc = 0;
-    int vis = orc_leaf_rect(F, C, l, r, NULL, band_px, &unc);
+    int vis = decide32 ? orc_leaf_rect32(F, &K, tan_t, rad_t, l, r)
+                       : orc_leaf_rect(F, C, l, r, NULL, band_px, &unc);
     if (rect) memcpy(rect + 4 * (size_t)l, r, sizeof r);
     visible[l] = (uint8_t)vis;
     if (uncertain) uncertain[l] = (uint8_t)unc;
   }
+  free(tan_t);
+  free(rad_t);
 }
 
 typedef struct {
@@ -805,27 +1108,36 @@ int64_t orc_render(const orc_forest *F, const orc_camera *C, const orc_integrato
                    uint8_t *uncertain, double band_px, double band_rel, int nthreads,
                    int64_t *nsteps_total) {
   return orc_render_ex(F, C, I, rows, nrows, rgba, counts, NULL, uncertain, band_px, band_rel,
-                       nthreads, nsteps_total);
+                       nthreads, nsteps_total, 1);
 }
 
 int64_t orc_render_ex(const orc_forest *F, const orc_camera *C, const orc_integrator *I,
                       const int *rows, int nrows, double *rgba, int32_t *counts,
                       int32_t *crossings, uint8_t *uncertain, double band_px, double band_rel,
-                      int nthreads, int64_t *nsteps_total) {
+                      int nthreads, int64_t *nsteps_total, int decide32) {
   const int W = C->w, H = C->h;
   /* isosurface ties: a sample within this of s_iso (FP32 field values carry
    * relative errors of a few 1e-7 of the data's magnitude) */
   const double smag = fabs(F->s_max) > fabs(F->s_min) ? fabs(F->s_max) : fabs(F->s_min);
   const double sband = 10.0 * band_rel * (smag > 0.0 ? smag : 1.0);
   if (!rows) nrows = H;
-  /* candidate rectangle of every leaf: its pixel rectangle widened by one
-   * pixel, so that a ray hitting the leaf is never missed through rounding */
+  /* FP32 decisions: the candidate pairs are exactly those of the FP32
+   * rectangles.  FP64 decisions: every leaf's pixel rectangle widened by one
+   * pixel, so that a ray hitting the leaf is never missed through rounding,
+   * and the decisions' margins reported as ties. */
+  const int widen = decide32 ? 0 : 1;
+  orc_cam32 K;
+  float *tan_t = NULL, *rad_t = NULL;
+  if (decide32) {
+    orc_camera32(C, &K);
+    if (tables32(F, &tan_t, &rad_t)) return -1;
+  }
   int32_t *rect = (int32_t *)malloc(sizeof(int32_t) * 4 * (size_t)F->nleaves);
   uint8_t *vis = (uint8_t *)malloc((size_t)F->nleaves);
   double *pext = (double *)malloc(sizeof(double) * 4 * (size_t)F->nleaves);
   int *rowpos = (int *)malloc(sizeof(int) * (size_t)H);
   if (!rect || !vis || !pext || !rowpos) {
-    free(rect); free(vis); free(pext); free(rowpos);
+    free(rect); free(vis); free(pext); free(rowpos); free(tan_t); free(rad_t);
     return -1;
   }
   for (int j = 0; j < H; ++j) rowpos[j] = -1;
@@ -833,14 +1145,15 @@ int64_t orc_render_ex(const orc_forest *F, const orc_camera *C, const orc_integr
 #pragma omp parallel for schedule(static)
   for (int l = 0; l < F->nleaves; ++l) {
     int unc = 0;
-    vis[l] = (uint8_t)orc_leaf_rect(F, C, l, rect + 4 * (size_t)l, pext + 4 * (size_t)l, band_px,
-                                    &unc);
+    vis[l] = (uint8_t)(decide32 ? orc_leaf_rect32(F, &K, tan_t, rad_t, l, rect + 4 * (size_t)l)
+                                : orc_leaf_rect(F, C, l, rect + 4 * (size_t)l,
+                                                pext + 4 * (size_t)l, band_px, &unc));
   }
   /* rows -> candidate leaves (CSR) */
   int64_t *rstart = (int64_t *)calloc((size_t)nrows + 1, sizeof(int64_t));
   for (int l = 0; l < F->nleaves; ++l) {
     if (!vis[l]) continue;
-    int j0 = rect[4 * l + 2] - 1, j1 = rect[4 * l + 3] + 1;
+    int j0 = rect[4 * l + 2] - widen, j1 = rect[4 * l + 3] + widen;
     if (j0 < 0) j0 = 0;
     if (j1 > H - 1) j1 = H - 1;
     for (int j = j0; j <= j1; ++j)
@@ -852,7 +1165,7 @@ int64_t orc_render_ex(const orc_forest *F, const orc_camera *C, const orc_integr
   memcpy(fill, rstart, sizeof(int64_t) * (size_t)(nrows + 1));
   for (int l = 0; l < F->nleaves; ++l) {
     if (!vis[l]) continue;
-    int j0 = rect[4 * l + 2] - 1, j1 = rect[4 * l + 3] + 1;
+    int j0 = rect[4 * l + 2] - widen, j1 = rect[4 * l + 3] + widen;
     if (j0 < 0) j0 = 0;
     if (j1 > H - 1) j1 = H - 1;
     for (int j = j0; j <= j1; ++j)
@@ -876,7 +1189,7 @@ int64_t orc_render_ex(const orc_forest *F, const orc_camera *C, const orc_integr
       int np = 0;
       for (int64_t q = rstart[r]; q < rstart[r + 1]; ++q) {
         int l = rleaf[q];
-        int i0 = rect[4 * l] - 1, i1 = rect[4 * l + 1] + 1;
+        int i0 = rect[4 * l] - widen, i1 = rect[4 * l + 1] + widen;
         if (i0 < 0) i0 = 0;
         if (i1 > W - 1) i1 = W - 1;
         for (int i = i0; i <= i1; ++i) {
@@ -900,19 +1213,33 @@ int64_t orc_render_ex(const orc_forest *F, const orc_camera *C, const orc_integr
       cstart[0] = 0;
       for (int i = 0; i < W; ++i) {
         double org[3], dir[3], amin, amax;
-        orc_pixel_ray(C, i, j, org, dir, &amin, &amax);
+        float org32[3], dir32[3];
+        if (decide32) { /* the FP32 ray; its values integrated in FP64 */
+          orc_pixel_ray32(&K, i, j, org32, dir32);
+          for (int a = 0; a < 3; ++a) { org[a] = org32[a]; dir[a] = dir32[a]; }
+          amin = K.amin;
+          amax = K.amax;
+        } else {
+          orc_pixel_ray(C, i, j, org, dir, &amin, &amax);
+        }
         int ns = 0, nties = 0, ncross = 0;
         for (int q = cstart[i]; q < cstart[i + 1]; ++q) {
           int l = pl[pord[q]];
           double a_in[2], a_out[2];
-          int tie = 0;
-          int nhit = orc_ray_leaf_tie(F, l, org, dir, amin, amax, a_in, a_out, band_rel, &tie);
-          /* a hit outside the leaf's own rectangle, or within band_px of its edge */
-          if (nhit) {
-            const double *pe = pext + 4 * (size_t)l;
-            if (i < pe[0] + band_px || i > pe[1] - band_px || j < pe[2] + band_px ||
-                j > pe[3] - band_px)
-              tie = 1;
+          int tie = 0, nhit;
+          if (decide32) {
+            float f_in[2], f_out[2];
+            nhit = orc_ray_leaf32(F, tan_t, rad_t, l, org32, dir32, K.amin, K.amax, f_in, f_out);
+            for (int k = 0; k < nhit; ++k) { a_in[k] = f_in[k]; a_out[k] = f_out[k]; }
+          } else {
+            nhit = orc_ray_leaf_tie(F, l, org, dir, amin, amax, a_in, a_out, band_rel, &tie);
+            /* a hit outside the leaf's own rectangle, or within band_px of its edge */
+            if (nhit) {
+              const double *pe = pext + 4 * (size_t)l;
+              if (i < pe[0] + band_px || i > pe[1] - band_px || j < pe[2] + band_px ||
+                  j > pe[3] - band_px)
+                tie = 1;
+            }
           }
           nties += tie;
           if (!nhit) continue;
@@ -943,6 +1270,7 @@ int64_t orc_render_ex(const orc_forest *F, const orc_camera *C, const orc_integr
     free(pl); free(pi); free(cstart); free(pord); free(sg);
   }
   free(rect); free(vis); free(pext); free(rowpos); free(rstart); free(rleaf); free(fill);
+  free(tan_t); free(rad_t);
   if (nsteps_total) *nsteps_total = steps;
   return total;
 }
@@ -1100,14 +1428,61 @@ static void segment_bwd(const orc_forest *F, const orc_integrator *I, int leaf, 
 }
 
 int orc_render_grad(const orc_forest *F, const orc_camera *C, const orc_integrator *I,
-                    const double *dL_drgba, double *g_nodal, double *g_tf, int nthreads) {
+                    const double *dL_drgba, double *g_nodal, double *g_tf, int nthreads,
+                    int decide32) {
   if (I->method != ORC_RK4 && I->method != ORC_DOPRI5) return -2;
-  const int W = C->w, H = C->h;
+  const int W = C->w, H = C->h, widen = decide32 ? 0 : 1;
+  orc_cam32 K;
+  float *tan_t = NULL, *rad_t = NULL;
+  if (decide32) {
+    orc_camera32(C, &K);
+    if (tables32(F, &tan_t, &rad_t)) return -1;
+  }
   int32_t *rect = (int32_t *)malloc(sizeof(int32_t) * 4 * (size_t)F->nleaves);
-  if (!rect) return -1;
+  if (!rect) {
+    free(tan_t);
+    free(rad_t);
+    return -1;
+  }
+#pragma omp parallel for schedule(static)
   for (int l = 0; l < F->nleaves; ++l) {
     int unc = 0;
-    orc_leaf_rect(F, C, l, rect + 4 * (size_t)l, NULL, 0.0, &unc);
+    if (decide32)
+      orc_leaf_rect32(F, &K, tan_t, rad_t, l, rect + 4 * (size_t)l);
+    else
+      orc_leaf_rect(F, C, l, rect + 4 * (size_t)l, NULL, 0.0, &unc);
+  }
+  /* the leaves whose (widened) rectangle meets each row with a non-zero
+   * image adjoint (CSR) */
+  int64_t *rs = (int64_t *)calloc((size_t)H + 1, sizeof(int64_t));
+  uint8_t *live = (uint8_t *)calloc((size_t)H, 1);
+  if (!rs || !live) {
+    free(rs); free(live); free(rect); free(tan_t); free(rad_t);
+    return -1;
+  }
+  for (int p = 0; p < W * H; ++p) {
+    const double *gb = dL_drgba + 4 * (size_t)p;
+    if (gb[0] != 0.0 || gb[1] != 0.0 || gb[2] != 0.0 || gb[3] != 0.0) live[p / W] = 1;
+  }
+  for (int l = 0; l < F->nleaves; ++l) {
+    const int32_t *rc = rect + 4 * (size_t)l;
+    if (rc[0] > rc[1]) continue;
+    for (int j = rc[2] - widen; j <= rc[3] + widen; ++j)
+      if (j >= 0 && j < H && live[j]) rs[j + 1]++;
+  }
+  for (int j = 0; j < H; ++j) rs[j + 1] += rs[j];
+  int32_t *rl = (int32_t *)malloc(sizeof(int32_t) * (size_t)(rs[H] > 0 ? rs[H] : 1));
+  int64_t *fillp = (int64_t *)malloc(sizeof(int64_t) * (size_t)(H + 1));
+  if (!rl || !fillp) {
+    free(rs); free(live); free(rect); free(rl); free(fillp); free(tan_t); free(rad_t);
+    return -1;
+  }
+  memcpy(fillp, rs, sizeof(int64_t) * (size_t)(H + 1));
+  for (int l = 0; l < F->nleaves; ++l) {
+    const int32_t *rc = rect + 4 * (size_t)l;
+    if (rc[0] > rc[1]) continue;
+    for (int j = rc[2] - widen; j <= rc[3] + widen; ++j)
+      if (j >= 0 && j < H && live[j]) rl[fillp[j]++] = l;
   }
   memset(g_nodal, 0, sizeof(double) * (size_t)nodal_stride(F) * (size_t)F->nleaves);
   memset(g_tf, 0, sizeof(double) * 32);
@@ -1126,13 +1501,29 @@ int orc_render_grad(const orc_forest *F, const orc_camera *C, const orc_integrat
       const double *gb = dL_drgba + 4 * (size_t)p;
       if (gb[0] == 0.0 && gb[1] == 0.0 && gb[2] == 0.0 && gb[3] == 0.0) continue;
       double org[3], dir[3], amin, amax;
-      orc_pixel_ray(C, i, j, org, dir, &amin, &amax);
+      float org32[3], dir32[3];
+      if (decide32) {
+        orc_pixel_ray32(&K, i, j, org32, dir32);
+        for (int a = 0; a < 3; ++a) { org[a] = org32[a]; dir[a] = dir32[a]; }
+        amin = K.amin;
+        amax = K.amax;
+      } else {
+        orc_pixel_ray(C, i, j, org, dir, &amin, &amax);
+      }
       int ns = 0;
-      for (int l = 0; l < F->nleaves; ++l) {
+      for (int64_t qq = rs[j]; qq < rs[j + 1]; ++qq) {
+        const int l = rl[qq];
         const int32_t *rc = rect + 4 * (size_t)l;
-        if (i < rc[0] - 1 || i > rc[1] + 1 || j < rc[2] - 1 || j > rc[3] + 1) continue;
+        if (i < rc[0] - widen || i > rc[1] + widen) continue;
         double a0[2], a1[2];
-        int nhit = orc_ray_leaf(F, l, org, dir, amin, amax, a0, a1);
+        int nhit;
+        if (decide32) {
+          float f0[2], f1[2];
+          nhit = orc_ray_leaf32(F, tan_t, rad_t, l, org32, dir32, K.amin, K.amax, f0, f1);
+          for (int k = 0; k < nhit; ++k) { a0[k] = f0[k]; a1[k] = f1[k]; }
+        } else {
+          nhit = orc_ray_leaf(F, l, org, dir, amin, amax, a0, a1);
+        }
         for (int k = 0; k < nhit; ++k) {
           if (ns == cap) {
             cap *= 2;
@@ -1182,6 +1573,6 @@ int orc_render_grad(const orc_forest *F, const orc_camera *C, const orc_integrat
     free(sg);
     free(sl);
   }
-  free(rect);
+  free(rect); free(rs); free(live); free(rl); free(fillp); free(tan_t); free(rad_t);
   return 0;
 }

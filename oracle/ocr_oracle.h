@@ -74,6 +74,15 @@ typedef struct {
   double s_iso, a_s, i_s[3];
 } orc_integrator;
 
+/* FP32 camera constants of step a1 (Eq. 2.5), each rounded once from FP64:
+ * o, v (v/n when orthographic), ell t, ell u, t, u, v/n, n, f, ell, the image
+ * centre (w-1)/2, (h-1)/2, and the alpha range [1, f/n] ([0, f]). */
+typedef struct {
+  float o[3], v[3], lt[3], lu[3], t[3], u[3], vn[3];
+  float n, f, ell, cw, ch, amin, amax;
+  int w, h, ortho;
+} orc_cam32;
+
 /* Segment algebra on (A, B_r, B_g, B_b). */
 void orc_combine(const double *near_seg, const double *far_seg, double *out);
 void orc_inverse(const double *s, double *out);
@@ -113,6 +122,22 @@ int orc_ray_leaf_tie(const orc_forest *F, int leaf, const double *org, const dou
                      double amin, double amax, double *a_in, double *a_out, double band_rel,
                      int *tie);
 
+/* Index decisions in FP32 (the GPU path's precision), by one canonical
+ * evaluation: every operation rounded once, in a fixed order, subnormals
+ * flushed.  orc_camera32 rounds the camera; orc_pixel_ray32 is Eq. 2.5;
+ * orc_shell_tables32 fills the shell's plane tangents and radii
+ * (2^max_level + 1 floats each; unused for the cube, may be NULL there);
+ * orc_leaf_rect32 is orc_leaf_rect's rectangle and orc_ray_leaf32
+ * orc_ray_leaf's intervals. */
+void orc_camera32(const orc_camera *C, orc_cam32 *K);
+void orc_pixel_ray32(const orc_cam32 *K, int i, int j, float *org, float *dir);
+void orc_shell_tables32(const orc_forest *F, float *tan_t, float *rad_t);
+int orc_leaf_rect32(const orc_forest *F, const orc_cam32 *K, const float *tan_t,
+                    const float *rad_t, int leaf, int32_t *rect);
+int orc_ray_leaf32(const orc_forest *F, const float *tan_t, const float *rad_t, int leaf,
+                   const float *org, const float *dir, float amin, float amax, float *a_in,
+                   float *a_out);
+
 /* The equiangular map of tree reference coordinates to space and its inverse
  * (shell forests). */
 void orc_shell_map(const orc_forest *F, int tree, const double *ref, double *x);
@@ -126,9 +151,11 @@ void orc_segment_ab(const orc_forest *F, const orc_integrator *I, int leaf,
                     const double *org, const double *dir, double a_in, double a_out,
                     double *seg4, int64_t *nsteps);
 
-/* Visibility of every leaf.  rect may be NULL. */
+/* Visibility of every leaf.  rect may be NULL.  decide32 != 0: the
+ * rectangles of orc_leaf_rect32 (uncertain all 0); else orc_leaf_rect's with
+ * its tie flags. */
 void orc_cull(const orc_forest *F, const orc_camera *C, int32_t *rect, uint8_t *visible,
-              uint8_t *uncertain, double band_px);
+              uint8_t *uncertain, double band_px, int decide32);
 
 /* Render the listed image rows (rows == NULL: all rows).  rgba[nrows*w*4],
  * counts[nrows*w] (segments per ray), uncertain[nrows*w] (the number of this
@@ -142,11 +169,15 @@ int64_t orc_render(const orc_forest *F, const orc_camera *C, const orc_integrato
 
 /* The same, also writing crossings[nrows*w] (isosurface crossings per ray;
  * may be NULL); a ray with a sample within the tie band of s_iso counts as a
- * tie in uncertain. */
+ * tie in uncertain.  decide32 != 0 (orc_render's choice): rectangles, rays
+ * and intervals from the FP32 decisions (orc_leaf_rect32, orc_pixel_ray32,
+ * orc_ray_leaf32; no geometric ties are flagged), the segment values in FP64
+ * over the FP32 ray and end points; decide32 == 0: all in FP64, geometric
+ * ties flagged. */
 int64_t orc_render_ex(const orc_forest *F, const orc_camera *C, const orc_integrator *I,
                       const int *rows, int nrows, double *rgba, int32_t *counts,
                       int32_t *crossings, uint8_t *uncertain, double band_px, double band_rel,
-                      int nthreads, int64_t *nsteps_total);
+                      int nthreads, int64_t *nsteps_total, int decide32);
 
 /* Gradient of L with respect to the nodal values and the transfer-function
  * knots, given dL/d(rgba) per pixel [h*w*4] (row-major).  FP64 reverse mode:
@@ -156,10 +187,11 @@ int64_t orc_render_ex(const orc_forest *F, const orc_camera *C, const orc_integr
  * (RK4 or Algorithm 1 with DOPRI5; the step tree is re-derived with the same
  * tests), the transfer function and the trilinear (cube) or triquadratic
  * (shell) interpolation.  g_nodal [nleaves*8 or *27], g_tf [32] are
- * overwritten.  Every pixel is tested against
- * every leaf: for small cases.  Returns 0, or -2 for other integrators. */
+ * overwritten.  decide32 as in orc_render_ex.  Returns 0, -1 when out of
+ * memory, or -2 for other integrators. */
 int orc_render_grad(const orc_forest *F, const orc_camera *C, const orc_integrator *I,
-                    const double *dL_drgba, double *g_nodal, double *g_tf, int nthreads);
+                    const double *dL_drgba, double *g_nodal, double *g_tf, int nthreads,
+                    int decide32);
 
 #ifdef __cplusplus
 }

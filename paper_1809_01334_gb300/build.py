@@ -20,8 +20,10 @@ SOURCES = ["ocr_capi.cu", "ocr_kernels.cu", "ocr_backward.cu", "ocr_shell.cu"]
 PEAK_SOURCE = "ocr_fp32_peak.cu"
 PEAK_LIB = os.path.join(OUT_DIR, "libocrpeak.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--use_fast_math",
-         "-Xptxas", "-v"]
+# host code: -ffp-contract=off keeps the FP64 tables (plane tangents, radii) as
+# written, so that their rounding to float is the same on every host
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
+         "-ffp-contract=off", "--use_fast_math", "-Xptxas", "-v"]
 
 
 def _nvcc() -> str:

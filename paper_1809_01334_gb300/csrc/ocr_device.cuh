@@ -105,21 +105,33 @@ __device__ __forceinline__ float4 seg_combine(float4 n, float4 f) {
   return make_float4(n.x * f.x, fmaf(n.x, f.y, n.y), fmaf(n.x, f.z, n.z), fmaf(n.x, f.w, n.w));
 }
 
+// ------------------------------------------------- index decisions (FP32) --
+// Which leaves a camera sees, which (leaf, ray) pairs give segments and where
+// those segments end are decided by the floating-point code below (pixel_ray,
+// slab, box_rect / project_box, and the shell's intersection and culling in
+// ocr_shell.cuh / ocr_shell.cu).  It is written in one canonical FP32
+// evaluation: every operation rounded to nearest once (the _rn intrinsics,
+// which the compiler neither fuses nor approximates under fast math), in the
+// order written, a fused multiply-add exactly where fmaf is written.  The
+// oracle takes these decisions with the same evaluation, so index results
+// (visible leaves, rectangles, per-ray segment counts) agree bit for bit.
+
 __device__ __forceinline__ void pixel_ray(const Cam &c, int i, int j, float3 &org, float3 &dir) {
-  float di = (float)i - c.cw, dj = (float)j - c.ch;
-  float ox = fmaf(dj, c.lu[0], fmaf(di, c.lt[0], 0.f));
-  float oy = fmaf(dj, c.lu[1], fmaf(di, c.lt[1], 0.f));
-  float oz = fmaf(dj, c.lu[2], fmaf(di, c.lt[2], 0.f));
+  const float di = __fsub_rn((float)i, c.cw), dj = __fsub_rn((float)j, c.ch);
+  const float ox = fmaf(dj, c.lu[0], __fmul_rn(di, c.lt[0]));
+  const float oy = fmaf(dj, c.lu[1], __fmul_rn(di, c.lt[1]));
+  const float oz = fmaf(dj, c.lu[2], __fmul_rn(di, c.lt[2]));
   if (c.ortho) {
-    org = make_float3(c.o[0] + ox, c.o[1] + oy, c.o[2] + oz);
+    org = make_float3(__fadd_rn(c.o[0], ox), __fadd_rn(c.o[1], oy), __fadd_rn(c.o[2], oz));
     dir = make_float3(c.v[0], c.v[1], c.v[2]);
   } else {
     org = make_float3(c.o[0], c.o[1], c.o[2]);
-    dir = make_float3(c.v[0] + ox, c.v[1] + oy, c.v[2] + oz);
+    dir = make_float3(__fadd_rn(c.v[0], ox), __fadd_rn(c.v[1], oy), __fadd_rn(c.v[2], oz));
   }
 }
 
-__device__ __forceinline__ float recip_or_zero(float d) { return d != 0.f ? 1.f / d : 0.f; }
+// 1/d rounded to nearest (IEEE), 0 for d == 0
+__device__ __forceinline__ float recip_or_zero(float d) { return d != 0.f ? __frcp_rn(d) : 0.f; }
 
 // Slab test of the ray against the axis-aligned box [lo, lo + h]^3, clipped to
 // [amin, amax].  A zero direction component keeps the ray inside the slab or
@@ -131,11 +143,12 @@ __device__ __forceinline__ bool slab(float3 org, float3 dir, float3 inv, float3 
   const float iv[3] = {inv.x, inv.y, inv.z}, l[3] = {lo.x, lo.y, lo.z};
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    float b0 = l[a], b1 = l[a] + h;
+    const float b0 = l[a], b1 = __fadd_rn(l[a], h);
     if (d[a] == 0.f) {
       if (o[a] < b0 || o[a] > b1) return false;
     } else {
-      float s0 = (b0 - o[a]) * iv[a], s1 = (b1 - o[a]) * iv[a];
+      const float s0 = __fmul_rn(__fsub_rn(b0, o[a]), iv[a]);
+      const float s1 = __fmul_rn(__fsub_rn(b1, o[a]), iv[a]);
       t0 = fmaxf(t0, fminf(s0, s1));
       t1 = fminf(t1, fmaxf(s0, s1));
     }
@@ -447,16 +460,19 @@ __device__ int4 project_box(const Cam &c, const float *blo, const float *bhi) {
     const float x0 = blo[a], x1 = bhi[a];
     float lo_p, hi_p;
     if (c.ortho) {
-      lo_p = x0 / c.ell;
-      hi_p = x1 / c.ell;
+      lo_p = __fdiv_rn(x0, c.ell);
+      hi_p = __fdiv_rn(x1, c.ell);
     } else {
-      const float sl = c.n / (zlo * c.ell), sh = c.n / (zhi * c.ell);
-      lo_p = fminf(fminf(x0 * sl, x0 * sh), fminf(x1 * sl, x1 * sh));
-      hi_p = fmaxf(fmaxf(x0 * sl, x0 * sh), fmaxf(x1 * sl, x1 * sh));
+      const float sl = __fdiv_rn(c.n, __fmul_rn(zlo, c.ell));
+      const float sh = __fdiv_rn(c.n, __fmul_rn(zhi, c.ell));
+      const float p00 = __fmul_rn(x0, sl), p01 = __fmul_rn(x0, sh);
+      const float p10 = __fmul_rn(x1, sl), p11 = __fmul_rn(x1, sh);
+      lo_p = fminf(fminf(p00, p01), fminf(p10, p11));
+      hi_p = fmaxf(fmaxf(p00, p01), fmaxf(p10, p11));
     }
     const float cen = a == 0 ? c.cw : c.ch;
-    pmin[a] = lo_p + cen;
-    pmax[a] = hi_p + cen;
+    pmin[a] = __fadd_rn(lo_p, cen);
+    pmax[a] = __fadd_rn(hi_p, cen);
   }
   const float wl = (float)(c.w - 1), hl = (float)(c.h - 1);
   const float i0 = fmaxf(ceilf(pmin[0]), 0.f), i1 = fminf(floorf(pmax[0]), wl);
@@ -466,17 +482,19 @@ __device__ int4 project_box(const Cam &c, const float *blo, const float *bhi) {
 }
 
 __device__ int4 box_rect(const Cam &c, float3 lo, float h) {
-  const float hh = 0.5f * h;
-  const float cx = lo.x + hh - c.o[0], cy = lo.y + hh - c.o[1], cz = lo.z + hh - c.o[2];
+  const float hh = __fmul_rn(0.5f, h);
+  const float cx = __fsub_rn(__fadd_rn(lo.x, hh), c.o[0]);
+  const float cy = __fsub_rn(__fadd_rn(lo.y, hh), c.o[1]);
+  const float cz = __fsub_rn(__fadd_rn(lo.z, hh), c.o[2]);
   float blo[3], bhi[3];
   const float *rows[3] = {c.t, c.u, c.vn};
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     const float *R = rows[r];
-    const float X = fmaf(R[0], cx, fmaf(R[1], cy, R[2] * cz));
-    const float E = hh * (fabsf(R[0]) + fabsf(R[1]) + fabsf(R[2]));
-    blo[r] = X - E;
-    bhi[r] = X + E;
+    const float X = fmaf(R[0], cx, fmaf(R[1], cy, __fmul_rn(R[2], cz)));
+    const float E = __fmul_rn(hh, __fadd_rn(__fadd_rn(fabsf(R[0]), fabsf(R[1])), fabsf(R[2])));
+    blo[r] = __fsub_rn(X, E);
+    bhi[r] = __fadd_rn(X, E);
   }
   return project_box(c, blo, bhi);
 }

@@ -95,35 +95,37 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     shell_cull_kernel(const int4 *__restrict__ geo, int N, Shell S, Cam c, int4 *rect,
                       unsigned char *visible, unsigned long long *stats) {
+  // the canonical FP32 evaluation of the index decisions (ocr_device.cuh)
   int nvis = 0;
-  const float tn = sqrtf(c.t[0] * c.t[0] + c.t[1] * c.t[1] + c.t[2] * c.t[2]);
-  const float un = sqrtf(c.u[0] * c.u[0] + c.u[1] * c.u[1] + c.u[2] * c.u[2]);
-  const float vn = sqrtf(c.vn[0] * c.vn[0] + c.vn[1] * c.vn[1] + c.vn[2] * c.vn[2]);
+  const float tn = __fsqrt_rn(fmaf(c.t[2], c.t[2], fmaf(c.t[1], c.t[1], __fmul_rn(c.t[0], c.t[0]))));
+  const float un = __fsqrt_rn(fmaf(c.u[2], c.u[2], fmaf(c.u[1], c.u[1], __fmul_rn(c.u[0], c.u[0]))));
+  const float vn =
+      __fsqrt_rn(fmaf(c.vn[2], c.vn[2], fmaf(c.vn[1], c.vn[1], __fmul_rn(c.vn[0], c.vn[0]))));
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
     const LeafShell q = leaf_shell(S, __ldg(geo + k));
     float d[4][3], cs[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int cc = 0; cc < 4; ++cc) {
       const float ta = (cc & 1) ? q.ta1 : q.ta0, tb = (cc & 2) ? q.tb1 : q.tb0;
-      float nn = 0.f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) d[cc][a] = fmaf(tb, q.e2[a], fmaf(ta, q.e1[a], q.n[a]));
+      const float nn = fmaf(d[cc][2], d[cc][2], fmaf(d[cc][1], d[cc][1], __fmul_rn(d[cc][0], d[cc][0])));
+      const float inv = __fdiv_rn(1.f, __fsqrt_rn(nn));
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        d[cc][a] = fmaf(tb, q.e2[a], fmaf(ta, q.e1[a], q.n[a]));
-        nn = fmaf(d[cc][a], d[cc][a], nn);
-      }
-      const float inv = 1.f / sqrtf(nn);
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        d[cc][a] *= inv;
-        cs[a] += d[cc][a];
+        d[cc][a] = __fmul_rn(d[cc][a], inv);
+        cs[a] = __fadd_rn(cs[a], d[cc][a]);
       }
     }
-    const float csn = 1.f / sqrtf(cs[0] * cs[0] + cs[1] * cs[1] + cs[2] * cs[2]);
+    const float csn =
+        __fdiv_rn(1.f, __fsqrt_rn(fmaf(cs[2], cs[2], fmaf(cs[1], cs[1], __fmul_rn(cs[0], cs[0])))));
     float cmin = 1.f;
 #pragma unroll
     for (int cc = 0; cc < 4; ++cc)
-      cmin = fminf(cmin, (d[cc][0] * cs[0] + d[cc][1] * cs[1] + d[cc][2] * cs[2]) * csn);
-    const float delta = q.rout * (1.f - cmin);
+      cmin = fminf(cmin, __fmul_rn(fmaf(d[cc][2], cs[2], fmaf(d[cc][1], cs[1],
+                                                             __fmul_rn(d[cc][0], cs[0]))),
+                                   csn));
+    const float delta = __fmul_rn(q.rout, __fsub_rn(1.f, cmin));
     float blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
     const float *rows[3] = {c.t, c.u, c.vn};
 #pragma unroll
@@ -133,16 +135,16 @@ __global__ void __launch_bounds__(256)
                   z = fmaf(r, d[cc & 3][2], -c.o[2]);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        const float X = fmaf(rows[a][0], x, fmaf(rows[a][1], y, rows[a][2] * z));
+        const float X = fmaf(rows[a][0], x, fmaf(rows[a][1], y, __fmul_rn(rows[a][2], z)));
         blo[a] = fminf(blo[a], X);
         bhi[a] = fmaxf(bhi[a], X);
       }
     }
-    const float ext[3] = {delta * tn, delta * un, delta * vn};
+    const float ext[3] = {__fmul_rn(delta, tn), __fmul_rn(delta, un), __fmul_rn(delta, vn)};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      blo[a] -= ext[a];
-      bhi[a] += ext[a];
+      blo[a] = __fsub_rn(blo[a], ext[a]);
+      bhi[a] = __fadd_rn(bhi[a], ext[a]);
     }
     const int4 r = project_box(c, blo, bhi);
     rect[k] = r;

@@ -61,36 +61,37 @@ __device__ __forceinline__ float3 plane_normal(const LeafShell &q, int s) {
 __device__ __forceinline__ int shell_ray_leaf_m(const float3 *m, float rin, float rout,
                                                 float3 org, float3 dir, float amin, float amax,
                                                 float *a_in, float *a_out) {
+  // the canonical FP32 evaluation of the index decisions (ocr_device.cuh)
   float t0 = amin, t1 = amax;
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
-    const float g0 = fmaf(m[s].x, org.x, fmaf(m[s].y, org.y, m[s].z * org.z));
-    const float g1 = fmaf(m[s].x, dir.x, fmaf(m[s].y, dir.y, m[s].z * dir.z));
+    const float g0 = fmaf(m[s].x, org.x, fmaf(m[s].y, org.y, __fmul_rn(m[s].z, org.z)));
+    const float g1 = fmaf(m[s].x, dir.x, fmaf(m[s].y, dir.y, __fmul_rn(m[s].z, dir.z)));
     const bool upper = (s & 1) != 0;
     if (g1 == 0.f) {
       if ((upper ? -g0 : g0) < 0.f) return 0;  // parallel to the plane and outside
       continue;
     }
-    const float a = -g0 / g1;
+    const float a = __fdiv_rn(-g0, g1);
     if ((upper ? -g1 : g1) > 0.f)
       t0 = fmaxf(t0, a);
     else
       t1 = fminf(t1, a);
   }
-  const float rr = fmaf(dir.x, dir.x, fmaf(dir.y, dir.y, dir.z * dir.z));
-  const float b = fmaf(org.x, dir.x, fmaf(org.y, dir.y, org.z * dir.z)) / rr;
+  const float rr = fmaf(dir.x, dir.x, fmaf(dir.y, dir.y, __fmul_rn(dir.z, dir.z)));
+  const float b = __fdiv_rn(fmaf(org.x, dir.x, fmaf(org.y, dir.y, __fmul_rn(org.z, dir.z))), rr);
   const float px = fmaf(-b, dir.x, org.x), py = fmaf(-b, dir.y, org.y), pz = fmaf(-b, dir.z, org.z);
-  const float pp = fmaf(px, px, fmaf(py, py, pz * pz));
+  const float pp = fmaf(px, px, fmaf(py, py, __fmul_rn(pz, pz)));
   const float hout = fmaf(rout, rout, -pp);
   if (!(hout > 0.f)) return 0;
-  const float so = sqrtf(hout / rr);
-  t0 = fmaxf(t0, -b - so);
-  t1 = fminf(t1, -b + so);
+  const float so = __fsqrt_rn(__fdiv_rn(hout, rr));
+  t0 = fmaxf(t0, __fsub_rn(-b, so));
+  t1 = fminf(t1, __fadd_rn(-b, so));
   const float hin = fmaf(rin, rin, -pp);
   int n = 0;
   if (hin > 0.f) {
-    const float si = sqrtf(hin / rr);
-    const float c0 = fminf(t1, -b - si), c1 = fmaxf(t0, -b + si);
+    const float si = __fsqrt_rn(__fdiv_rn(hin, rr));
+    const float c0 = fminf(t1, __fsub_rn(-b, si)), c1 = fmaxf(t0, __fadd_rn(-b, si));
     if (c0 > t0) {
       a_in[n] = t0;
       a_out[n] = c0;

@@ -51,7 +51,8 @@ def compute():
 
 def main():
     with open(OUT, "w") as fh:
-        fh.write("# FP64 oracle regression values (see make_oracle_regression.py).\n")
+        fh.write("# FP64 oracle regression values (see make_oracle_regression.py); index\n")
+        fh.write("# decisions (visibility, rays, segment end points) in FP32, values in FP64.\n")
         fh.write("# case i j segments r g b alpha\n")
         for name, i, j, n, r, g, b, a in compute():
             fh.write(f"{name} {i} {j} {n} {r:.17g} {g:.17g} {b:.17g} {a:.17g}\n")

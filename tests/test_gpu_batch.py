@@ -90,11 +90,11 @@ def test_every_tile_depth_matches_the_oracle(depth, merge):
         flat, views, st = r.render_batch(with_index=True)
         torch.cuda.synchronize()
         for k in (0, 2):
-            ref = O.render(f, tf, cams[k], INTEG, band_px=4e-3, band_rel=2e-6)
+            ref = O.render(f, tf, cams[k], INTEG)
             assert np.abs(views[k].cpu().numpy() - ref["rgba"]).max() <= 1e-4
             at = sum(c.w * c.h for c in cams[:k])
             cnt = st["counts"][at:at + cams[k].w * cams[k].h].cpu().numpy().reshape(ref["counts"].shape)
-            assert not ((cnt != ref["counts"]) & ~ref["uncertain"]).any()
+            np.testing.assert_array_equal(cnt, ref["counts"])
     r.close()
 
 

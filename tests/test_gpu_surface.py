@@ -35,8 +35,9 @@ def test_isosurface_matches_the_oracle(base, a_s):
     assert ref["crossings"].sum() > 50  # the surface is really there
     err = np.abs(img.cpu().numpy() - ref["rgba"]).max(axis=-1)
     assert err[~unc].max() <= 1e-4, err[~unc].max()
-    counts = st["counts"].cpu().numpy()
-    assert not ((counts != ref["counts"]) & ~unc).any()
+    # segment counts are FP32 geometric decisions, equal on every ray; only the
+    # isosurface's sign tests near s_iso are left out of the image comparison
+    np.testing.assert_array_equal(st["counts"].cpu().numpy(), ref["counts"])
     r.close()
 
 

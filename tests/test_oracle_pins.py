@@ -375,9 +375,12 @@ def test_render_matches_quadrature_of_the_closed_form(level):
     f, tf = _tiny(level)
     cam = I.perspective_camera(11 + level, 8, 6, dist=(1.8, 2.2))
     bg = (0.2, 0.1, 0.05)
+    # the FP64 definition (decide32=False): rays and intervals in FP64, as the
+    # quadrature below takes them
     fine = O.render(f, tf, cam, {"method": "dopri5", "tol": 1e-12, "c_rk": 0.1, "max_depth": 30},
-                    bg=bg)
-    coarse = [O.render(f, tf, cam, {"method": "rk4", "nsteps": n}, bg=bg)["rgba"] for n in (4, 8)]
+                    bg=bg, decide32=False)
+    coarse = [O.render(f, tf, cam, {"method": "rk4", "nsteps": n}, bg=bg, decide32=False)["rgba"]
+              for n in (4, 8)]
     ref = np.zeros((cam.h, cam.w, 4))
     for j in range(cam.h):
         for i in range(cam.w):

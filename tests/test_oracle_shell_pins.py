@@ -270,7 +270,7 @@ def test_constant_field_closed_form():
     tf.s_min, tf.s_max = -1.0, 1.0
     bg = (0.3, 0.2, 0.1)
     r = O.render(f, tf, cam, {"method": "dopri5", "tol": 1e-10, "c_rk": 0.2, "max_depth": 30},
-                 bg=bg)
+                 bg=bg, decide32=False)  # the FP64 definition, as the closed form below
     kq = BF.tf_numpy(tf, np.array([0.3]))[0]
     for j in range(cam.h):
         for i in range(cam.w):
@@ -293,7 +293,7 @@ def test_shell_render_matches_quadrature_of_the_closed_form(level):
     cam = I.perspective_camera(3 + level, 8, 6, dist=(2.0, 2.4), target=(0.0, 0.0, 0.0))
     bg = (0.2, 0.1, 0.05)
     fine = O.render(f, tf, cam, {"method": "dopri5", "tol": 1e-12, "c_rk": 0.1, "max_depth": 30},
-                    bg=bg)
+                    bg=bg, decide32=False)  # the FP64 definition, as the quadrature below
     ref = np.zeros((cam.h, cam.w, 4))
     for j in range(cam.h):
         for i in range(cam.w):
