@@ -234,32 +234,56 @@ def run_batch(args, forest, tf, integ, dev, flush):
     npix = sum(c.w * c.h for c in cams)
     r = Renderer(forest, tf, integ, device=dev)
     r.set_cameras(cams)
-    tune = r.autotune(reps=2)
+    tune = r.autotune(reps=1)
     out = torch.empty((npix, 4), dtype=torch.float32, device=dev)
-    _, _, st = r.render_batch(out, with_index=True)
-    segments = st["segments"]
-    s = torch.cuda.Stream(dev)
-    s.wait_stream(torch.cuda.current_stream(dev))
-    with torch.cuda.stream(s):
-        r.render_batch(out, stream=s)
-    torch.cuda.current_stream(dev).wait_stream(s)
-    torch.cuda.synchronize(dev)
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g):
-        r.render_batch(out, stream=torch.cuda.current_stream(dev))
     stream = torch.cuda.current_stream(dev)
     reps = 3
-    gms = []
-    for k in range(1 + reps):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        g.replay()
-        b.record(stream)
+
+    def graph_ms():
+        """Device time of one replay of the batch captured in a CUDA graph."""
+        s = torch.cuda.Stream(dev)
+        s.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(s):
+            r.render_batch(out, stream=s)  # warm-up outside the capture
+        torch.cuda.current_stream(dev).wait_stream(s)
         torch.cuda.synchronize(dev)
-        if k:
-            gms.append(a.elapsed_time(b))
-    del g
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            r.render_batch(out, stream=torch.cuda.current_stream(dev))
+        ms = []
+        for k in range(1 + reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.replay()
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            if k:
+                ms.append(a.elapsed_time(b))
+        del g
+        return sum(ms) / len(ms)
+
+    # the best decomposition of each kind: the persistent kernel and the
+    # per-camera kernel chains on the internal streams
+    best = {}
+    for t in tune["tried"]:
+        kind = "persistent" if t["persistent"] and not t["merge"] else "streams"
+        if kind not in best or t["ms"] < best[kind]["ms"]:
+            best[kind] = t
+    modes = {}
+    for kind in ("streams", "persistent"):
+        if kind in best:
+            t = best[kind]
+            r.set_tuning(t["tile_depth"], t["streams"], t["shell_warps"], t["merge"],
+                         1 if kind == "persistent" else 0, t["chunks_per_item"], t["ctas_per_sm"])
+            modes[kind] = {"graph_ms": graph_ms(), "tuning": t}
+    win = min(modes, key=lambda k: modes[k]["graph_ms"])
+    t = modes[win]["tuning"]
+    r.set_tuning(t["tile_depth"], t["streams"], t["shell_warps"], t["merge"],
+                 1 if win == "persistent" else 0, t["chunks_per_item"], t["ctas_per_sm"])
+    _, _, st = r.render_batch(out, with_index=True)
+    segments = st["segments"]
+    gms = [modes[win]["graph_ms"]]
     # one view at a time: the same planned cameras (planning is outside the
     # timed region for both arms), each view rendered alone on the stream
     # after the previous one, device time
@@ -280,6 +304,9 @@ def run_batch(args, forest, tf, integ, dev, flush):
     sq = sum(seq) / len(seq)
     return {"cameras": len(cams), "pixels": npix, "segments": segments,
             "graph_ms": gm, "sequential_ms": sq, "speedup_vs_sequential": sq / gm,
+            "decomposition": win, "launches_per_batch": st["launches"],
+            "persistent_graph_ms": modes.get("persistent", {}).get("graph_ms"),
+            "streams_graph_ms": modes.get("streams", {}).get("graph_ms"),
             "segments_per_s": segments / (gm * 1e-3), "mpixel_per_s": npix / (gm * 1e-3) / 1e6,
             "autotune": {"best": tune["best"], "tried": tune["tried"]},
             "sequential": "the same planned cameras, one ocr_render_view per view in "

@@ -290,13 +290,27 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
  *               pass in which each pixel's thread walks those levels top-down
  *               in its front-to-back octant order (1).  Equal up to rounding
  *               order (Eq. 2.14 is associative).
+ *   persistent  cube forests, several cameras, merge 0, no surface: render
+ *               the whole batch in one persistent kernel (1) -- its CTAs draw
+ *               work items (a camera's pruning block, union block, prefix-sum
+ *               block, chunk of a subtree or coarsening pass, or pixel
+ *               chunk) from a device queue ordered stage after stage, each
+ *               waiting for its camera's previous stage -- or each camera's
+ *               own kernel chain on the internal streams (0).
+ *   chunks_per_item  persistent: 128-slot chunks of the subtree, coarsening
+ *               and pixel passes handed out per ticket (1..64).
+ *   ctas_per_sm persistent: resident CTAs per SM (1..8; 0 = as many as fit).
  *   ms          ocr_autotune: the measured device time of one ocr_render.
- * Defaults: tile_depth 3, streams 4, shell_warps 0, merge 0. */
+ * Defaults: tile_depth 3, streams 4, shell_warps 0, merge 0, persistent 1,
+ * chunks_per_item 1, ctas_per_sm 0. */
 typedef struct {
   int tile_depth;
   int streams;
   int shell_warps;
   int merge;
+  int persistent;
+  int chunks_per_item;
+  int ctas_per_sm;
   float ms;
 } ocr_tuning;
 
@@ -306,7 +320,9 @@ int ocr_set_tuning(ocr_forest *F, const ocr_tuning *t);
 int ocr_get_tuning(const ocr_forest *F, ocr_tuning *t);
 
 /* Autotuner: render the cameras, data and integrator last set under every
- * candidate tuning (cube: tile_depth 1..3 x merge {0, 1} x streams {1, 2, 4, 8}; shell:
+ * candidate tuning (cube: tile_depth 1..3 x merge {0, 1} x streams {1, 2, 4, 8},
+ * and with several cameras the persistent kernel: tile_depth 1..3 x
+ * chunks_per_item {1, 2, 4} x ctas_per_sm {all, 4}; shell:
  * shell_warps {1, 2, 4, 8} x streams; streams only with several cameras),
  * one warm-up and `reps` timed renders each (CUDA events on an internal
  * stream, 1 <= reps <= 100), and keep the fastest, returned in *best.  The

@@ -118,7 +118,7 @@ def lib():
                                        C.c_double, C.c_double, C.c_int, P(C.c_int64), C.c_int]
         _lib.orc_render_ex.restype = C.c_int64
         _lib.orc_render_grad.argtypes = [P(Forest_), P(Camera_), P(Integrator_), d, d, d, C.c_int,
-                                         C.c_int]
+                                         C.c_int, P(C.c_uint8), C.c_double, d, d]
         _lib.orc_render_grad.restype = C.c_int
     return _lib
 
@@ -391,20 +391,36 @@ def render(forest, tf, cam, integ: dict, rows=None, bg=(0.0, 0.0, 0.0), nthreads
 
 
 def render_grad(forest, tf, cam, integ: dict, dL_drgba, bg=(0.0, 0.0, 0.0), nthreads: int = 0,
-                decide32: bool = True):
+                decide32: bool = True, tree_band: float | None = None, magnitudes: bool = False):
     """FP64 gradient of L with respect to nodal values [N, 8] (cube) or
-    [N, 27] (shell) and knots [8, 4], given dL/d(rgba) [h, w, 4]."""
+    [N, 27] (shell) and knots [8, 4], given dL/d(rgba) [h, w, 4].  With
+    tree_band, also the per-leaf flags of DOPRI5 split tests within that
+    relative band of their thresholds (another precision may take another
+    step tree there).  With magnitudes, also per coordinate the sum of the
+    magnitudes of the terms summed into it (nodal, knots): the scale of the
+    sum's rounding error in another precision."""
     of = OracleForest(forest, tf)
     cs = camera_struct(cam)
     ist = integrator_struct(integ, bg)
     gb = np.ascontiguousarray(dL_drgba, dtype=np.float64).reshape(cam.h, cam.w, 4)
     gn = np.zeros((forest.nleaves, of.stride))
     gt = np.zeros((8, 4))
+    tie = np.zeros(forest.nleaves, np.uint8) if tree_band is not None else None
+    an = np.zeros_like(gn) if magnitudes else None
+    at = np.zeros_like(gt) if magnitudes else None
     rc = lib().orc_render_grad(C.byref(of.s), C.byref(cs), C.byref(ist), _ptr(gb, C.c_double),
                                _ptr(gn, C.c_double), _ptr(gt, C.c_double), int(nthreads),
-                               int(bool(decide32)))
+                               int(bool(decide32)), None if tie is None else _ptr(tie, C.c_uint8),
+                               float(tree_band or 0.0),
+                               None if an is None else _ptr(an, C.c_double),
+                               None if at is None else _ptr(at, C.c_double))
     if rc == -1:
         raise MemoryError("oracle gradient: allocation failed")
     if rc != 0:
         raise ValueError("oracle gradient: only RK4 and DOPRI5 are differentiated")
-    return gn, gt
+    out = (gn, gt)
+    if tree_band is not None:
+        out += (tie.astype(bool),)
+    if magnitudes:
+        out += (an, at)
+    return out

@@ -1282,6 +1282,11 @@ int64_t orc_render_ex(const orc_forest *F, const orc_camera *C, const orc_integr
 typedef struct {
   double *g_nodal; /* [N*8] */
   double *g_tf;    /* [32] */
+  uint8_t *tree_tie; /* [N] or NULL: a split test of Algorithm 1 near its threshold */
+  double tree_band;
+  double *a_nodal, *a_tf; /* or NULL: the sums of the terms' magnitudes (the sums'
+                             condition: the scale of their rounding in another
+                             precision) */
 } grad_acc;
 
 /* Adjoint of the medium at distance x from the far end: vbar = dL/d(kappa,
@@ -1298,15 +1303,24 @@ static void medium_bwd(const seg_ctx *S, int leaf, double x, const double *vbar,
   double z = zr < 0.0 ? 0.0 : (zr > 7.0 ? 7.0 : zr);
   int k = (int)floor(z);
   if (k > 6) k = 6;
-  double w = z - k, sbar = 0.0;
+  double w = z - k, sbar = 0.0, sabs = 0.0;
   for (int c = 0; c < 4; ++c) {
 #pragma omp atomic
     G->g_tf[4 * k + c] += (1.0 - w) * vbar[c];
 #pragma omp atomic
     G->g_tf[4 * (k + 1) + c] += w * vbar[c];
-    if (inside)
-      sbar += vbar[c] * ((double)F->tf[4 * (k + 1) + c] - (double)F->tf[4 * k + c]) * 7.0 /
-              (F->s_max - F->s_min);
+    if (G->a_tf) {
+#pragma omp atomic
+      G->a_tf[4 * k + c] += fabs((1.0 - w) * vbar[c]);
+#pragma omp atomic
+      G->a_tf[4 * (k + 1) + c] += fabs(w * vbar[c]);
+    }
+    if (inside) {
+      double t = vbar[c] * ((double)F->tf[4 * (k + 1) + c] - (double)F->tf[4 * k + c]) * 7.0 /
+                 (F->s_max - F->s_min);
+      sbar += t;
+      sabs += fabs(t);
+    }
   }
   if (F->geometry == 1) {
     double lu[3], lv[3], lw[3];
@@ -1314,8 +1328,13 @@ static void medium_bwd(const seg_ctx *S, int leaf, double x, const double *vbar,
     quad_basis(u[1], lv);
     quad_basis(u[2], lw);
     for (int c = 0; c < 27; ++c) {
+      double wt = lu[c % 3] * lv[(c / 3) % 3] * lw[c / 9];
 #pragma omp atomic
-      G->g_nodal[27 * (size_t)leaf + c] += sbar * lu[c % 3] * lv[(c / 3) % 3] * lw[c / 9];
+      G->g_nodal[27 * (size_t)leaf + c] += sbar * wt;
+      if (G->a_nodal) {
+#pragma omp atomic
+        G->a_nodal[27 * (size_t)leaf + c] += sabs * fabs(wt);
+      }
     }
     return;
   }
@@ -1325,6 +1344,10 @@ static void medium_bwd(const seg_ctx *S, int leaf, double x, const double *vbar,
     double wz = (c & 4) ? u[2] : 1.0 - u[2];
 #pragma omp atomic
     G->g_nodal[8 * (size_t)leaf + c] += sbar * wx * wy * wz;
+    if (G->a_nodal) {
+#pragma omp atomic
+      G->a_nodal[8 * (size_t)leaf + c] += sabs * fabs(wx * wy * wz);
+    }
   }
 }
 
@@ -1379,6 +1402,14 @@ static void segeval_bwd(const seg_ctx *S, const orc_integrator *I, int leaf, dou
                         int depth, const double *ybar, grad_acc *G) {
   double y5[4], kmax, err;
   dopri_step(S, x1, x2, y5, &kmax, &err);
+  /* a test within the band of its threshold can go either way in another
+   * precision: the gradient of that leaf then belongs to another step tree */
+  if (G->tree_tie && depth < I->max_depth &&
+      (fabs(err - I->tol) <= G->tree_band * I->tol ||
+       fabs(kmax - I->c_rk) <= G->tree_band * I->c_rk)) {
+#pragma omp atomic write
+    G->tree_tie[leaf] = 1;
+  }
   if (depth < I->max_depth && (kmax > I->c_rk || err > I->tol)) {
     double xm = 0.5 * (x1 + x2), nr[4], fr[4], nb[4], fb[4];
     int64_t dummy = 0;
@@ -1429,7 +1460,8 @@ static void segment_bwd(const orc_forest *F, const orc_integrator *I, int leaf, 
 
 int orc_render_grad(const orc_forest *F, const orc_camera *C, const orc_integrator *I,
                     const double *dL_drgba, double *g_nodal, double *g_tf, int nthreads,
-                    int decide32) {
+                    int decide32, uint8_t *tree_tie, double tree_band, double *a_nodal,
+                    double *a_tf) {
   if (I->method != ORC_RK4 && I->method != ORC_DOPRI5) return -2;
   const int W = C->w, H = C->h, widen = decide32 ? 0 : 1;
   orc_cam32 K;
@@ -1486,7 +1518,10 @@ int orc_render_grad(const orc_forest *F, const orc_camera *C, const orc_integrat
   }
   memset(g_nodal, 0, sizeof(double) * (size_t)nodal_stride(F) * (size_t)F->nleaves);
   memset(g_tf, 0, sizeof(double) * 32);
-  grad_acc G = {g_nodal, g_tf};
+  grad_acc G = {g_nodal, g_tf, tree_tie, tree_band, a_nodal, a_tf};
+  if (tree_tie) memset(tree_tie, 0, (size_t)F->nleaves);
+  if (a_nodal) memset(a_nodal, 0, sizeof(double) * (size_t)nodal_stride(F) * (size_t)F->nleaves);
+  if (a_tf) memset(a_tf, 0, sizeof(double) * 32);
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #endif

@@ -187,11 +187,19 @@ int64_t orc_render_ex(const orc_forest *F, const orc_camera *C, const orc_integr
  * (RK4 or Algorithm 1 with DOPRI5; the step tree is re-derived with the same
  * tests), the transfer function and the trilinear (cube) or triquadratic
  * (shell) interpolation.  g_nodal [nleaves*8 or *27], g_tf [32] are
- * overwritten.  decide32 as in orc_render_ex.  Returns 0, -1 when out of
- * memory, or -2 for other integrators. */
+ * overwritten.  decide32 as in orc_render_ex.  tree_tie [nleaves] (may be
+ * NULL) flags the leaves with a DOPRI5 split test of Algorithm 1 within
+ * tree_band (relative) of its threshold (the embedded error against tol, or
+ * dx kappa against c_RK): a computation in another precision may take
+ * another step tree there, and with it the derivative of another
+ * discretisation.  a_nodal, a_tf (may be NULL) receive, per coordinate, the
+ * sum of the magnitudes of the terms summed into it (at the transfer function
+ * and the interpolation weights): the scale of the rounding error of that
+ * sum.  Returns 0, -1 when out of memory, or -2 for other integrators. */
 int orc_render_grad(const orc_forest *F, const orc_camera *C, const orc_integrator *I,
                     const double *dL_drgba, double *g_nodal, double *g_tf, int nthreads,
-                    int decide32);
+                    int decide32, uint8_t *tree_tie, double tree_band, double *a_nodal,
+                    double *a_tf);
 
 #ifdef __cplusplus
 }

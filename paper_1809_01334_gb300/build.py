@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libocraycast.so")
-SOURCES = ["ocr_capi.cu", "ocr_kernels.cu", "ocr_backward.cu", "ocr_shell.cu"]
+SOURCES = ["ocr_capi.cu", "ocr_kernels.cu", "ocr_batch.cu", "ocr_backward.cu", "ocr_shell.cu"]
 PEAK_SOURCE = "ocr_fp32_peak.cu"
 PEAK_LIB = os.path.join(OUT_DIR, "libocrpeak.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -55,7 +55,8 @@ class Stats(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("tile_depth", C.c_int), ("streams", C.c_int), ("shell_warps", C.c_int),
-                ("merge", C.c_int), ("ms", C.c_float)]
+                ("merge", C.c_int), ("persistent", C.c_int), ("chunks_per_item", C.c_int),
+                ("ctas_per_sm", C.c_int), ("ms", C.c_float)]
 
 
 class OcrError(RuntimeError):
@@ -210,12 +211,15 @@ def render_host(h, h_nodal, h_tf, s_min: float, s_max: float, h_rgba, stream=Non
 
 def _tuning_dict(t: Tuning) -> dict:
     return {"tile_depth": t.tile_depth, "streams": t.streams, "shell_warps": t.shell_warps,
-            "merge": t.merge, "ms": float(t.ms)}
+            "merge": t.merge, "persistent": t.persistent, "chunks_per_item": t.chunks_per_item,
+            "ctas_per_sm": t.ctas_per_sm, "ms": float(t.ms)}
 
 
-def set_tuning(h, tile_depth: int = 3, streams: int = 4, shell_warps: int = 0, merge: int = 0):
+def set_tuning(h, tile_depth: int = 3, streams: int = 4, shell_warps: int = 0, merge: int = 0,
+               persistent: int = 1, chunks_per_item: int = 1, ctas_per_sm: int = 0):
     """ocr_set_tuning (a cube forest re-plans its cameras when tile_depth changes)."""
-    t = Tuning(int(tile_depth), int(streams), int(shell_warps), int(merge), 0.0)
+    t = Tuning(int(tile_depth), int(streams), int(shell_warps), int(merge), int(persistent),
+               int(chunks_per_item), int(ctas_per_sm), 0.0)
     L = lib()
     L.ocr_set_tuning.argtypes = [C.c_void_p, C.POINTER(Tuning)]
     _check(L.ocr_set_tuning(h, C.byref(t)), "ocr_set_tuning")
@@ -233,12 +237,12 @@ def autotune(h, reps: int = 3) -> dict:
     """ocr_autotune: times every candidate tuning on the current cameras and
     keeps the fastest.  Returns {"best": ..., "tried": [...]}."""
     best = Tuning()
-    tried = (Tuning * 64)()
+    tried = (Tuning * 128)()
     n = C.c_int(0)
     L = lib()
     L.ocr_autotune.argtypes = [C.c_void_p, C.c_int, C.POINTER(Tuning), C.POINTER(Tuning), C.c_int,
                                C.POINTER(C.c_int)]
-    _check(L.ocr_autotune(h, int(reps), C.byref(best), tried, 64, C.byref(n)), "ocr_autotune")
+    _check(L.ocr_autotune(h, int(reps), C.byref(best), tried, 128, C.byref(n)), "ocr_autotune")
     return {"best": _tuning_dict(best), "tried": [_tuning_dict(tried[k]) for k in range(n.value)]}
 
 

@@ -82,6 +82,18 @@ struct ocr_forest {
   int shell_warps = 0;                // shell: warps per CTA of the per-ray kernel (0: most)
   int merge = 0;                      // cube: levels above the tile level by per-level passes
                                       // (0) or by one top-down pass per pixel (1)
+  int persistent = 1;                 // cube, several cameras: one persistent kernel (1) or
+                                      // per-camera kernel chains over the streams (0)
+  int chunks_per_item = 1;            // persistent: chunks of the chunk passes per ticket
+  int ctas_per_sm = 0;                // persistent: CTAs per SM (0: as many as fit)
+  // persistent batch: the work queue (segments), per-camera device records and
+  // the control words; rebuilt when the cameras or the decomposition change
+  BatchSeg *d_bseg = nullptr;
+  BatchCam *d_bcam = nullptr;
+  unsigned *d_bctl = nullptr;
+  int nbseg = 0, nbcam = 0;
+  long long nbtickets = 0;
+  bool batch_ready = false;
   long long *h_group_slots = nullptr; // pinned [L + 1 + kStats]
   unsigned long long *d_stats = nullptr;  // [kStats]
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // start, layout, subtree, end
@@ -228,6 +240,9 @@ void free_all(ocr_forest *F) {
   if (F->copy_st) cudaStreamDestroy(F->copy_st);
   if (F->copy_ev) cudaEventDestroy(F->copy_ev);
   cudaFree(F->d_err);
+  cudaFree(F->d_bseg);
+  cudaFree(F->d_bcam);
+  cudaFree(F->d_bctl);
   if (F->h_group_slots) cudaFreeHost(F->h_group_slots);
   for (cudaEvent_t &e : F->ev)
     if (e) cudaEventDestroy(e);
@@ -386,6 +401,7 @@ int build_shell(const ocr_forest_desc *desc, cudaStream_t st, ocr_forest **out) 
 }
 
 int plan_cameras(ocr_forest *F);
+int plan_batch(ocr_forest *F);
 
 // Plan one camera of a shell forest: its pruning and pair space, the segment
 // count of every ray, the size of the lists and the longest one.  Runs on the
@@ -807,6 +823,92 @@ int plan_cameras(ocr_forest *F) {
         (rc = dev_alloc(&P.d_entries, (size_t)(total > 0 ? total : 1), F->bytes)))
       return rc;
   }
+  return plan_batch(F);
+}
+
+// The persistent kernel's work queue for the cameras just planned (cube
+// forests): per pipeline stage, for every camera, one segment of items, each
+// waiting for the camera's previous non-empty stage.  Marks the batch
+// unavailable (the stream path renders) when it does not apply.
+int plan_batch(ocr_forest *F) {
+  F->batch_ready = false;
+  if (F->geometry != OCR_GEOM_CUBE || F->M < 1 || F->plans.empty()) return OCR_OK;
+  const int K = (int)F->plans.size(), L = F->L;
+  const long long per = F->chunks_per_item;
+  std::vector<BatchSeg> segs;
+  std::vector<int> last(K, -1);
+  long long tickets = 0;
+  auto add = [&](int k, int kind, long long nitems, long long a, long long b, int nb, int ne,
+                 long long p) {
+    if (nitems <= 0) return;
+    BatchSeg g{};
+    g.first = tickets;
+    g.nitems = nitems;
+    g.per = (int)p;
+    g.ntickets = (nitems + p - 1) / p;
+    g.a = a;
+    g.b = b;
+    g.cam = k;
+    g.kind = kind;
+    g.dep = last[k];
+    g.nb = nb;
+    g.ne = ne;
+    last[k] = (int)segs.size();
+    tickets += g.ntickets;
+    segs.push_back(g);
+  };
+  const long long tile = 8ll * kChunk;  // leaves or nodes per set-up item
+  auto up = [](long long n, long long d) { return (n + d - 1) / d; };
+  for (int k = 0; k < K; ++k) add(k, kBatchCull, up(F->N, tile), 0, F->N, 0, 0, 1);
+  for (int l = L - 1; l >= 0; --l)
+    for (int k = 0; k < K; ++k)
+      add(k, kBatchUnion, up(F->level_count[l], tile), F->level_base[l],
+          F->level_base[l] + F->level_count[l], 0, 0, 1);
+  for (int k = 0; k < K; ++k) add(k, kBatchReduce, up(F->M, tile), 0, F->M, 0, 0, 1);
+  for (int k = 0; k < K; ++k) add(k, kBatchDown, up(F->M, tile), 0, F->M, 0, 0, 1);
+  for (int k = 0; k < K; ++k) add(k, kBatchChunkMap, up(F->M, tile), 0, F->M, 0, 0, 1);
+  const int G = (int)F->h_group_nodes.size();
+  for (int g = 0; g + 1 < G; ++g) {  // levels L - 1 .. 0: the tile level, then coarser
+    const int level = L - 1 - g;
+    if (level > F->lt) continue;
+    for (int k = 0; k < K; ++k) {
+      const long long a = F->plans[k].gslots[g], b = F->plans[k].gslots[g + 1];
+      if (b <= a) continue;
+      add(k, level == F->lt ? kBatchSubtree : kBatchCoarse, (b - 1) / kChunk - a / kChunk + 1, a,
+          b, F->h_group_nodes[g], F->h_group_nodes[g + 1], per);
+    }
+  }
+  for (int k = 0; k < K; ++k)
+    add(k, kBatchPixel, up(F->plans[k].npix, kChunk), 0, F->plans[k].npix, 0, 0, per);
+  if ((int)segs.size() > kBatchMaxSegs || tickets >= (1ll << 31)) return OCR_OK;
+  std::vector<BatchCam> cams(K);
+  for (int k = 0; k < K; ++k) {
+    const CamPlan &P = F->plans[k];
+    cams[k] = BatchCam{P.cam, P.d_rect, P.d_off, P.d_bsums, P.d_chunk, P.d_entries, P.pix_off};
+  }
+  cudaFree(F->d_bseg);
+  F->d_bseg = nullptr;
+  if (K > F->nbcam) {
+    cudaFree(F->d_bcam);
+    F->d_bcam = nullptr;
+    F->nbcam = 0;
+  }
+  int rc;
+  if ((rc = dev_alloc(&F->d_bseg, segs.size(), F->bytes))) return rc;
+  if (!F->d_bcam) {
+    if ((rc = dev_alloc(&F->d_bcam, (size_t)K, F->bytes))) return rc;
+    F->nbcam = K;
+  }
+  if (!F->d_bctl && (rc = dev_alloc(&F->d_bctl, (size_t)kBatchCtlWords, F->bytes))) return rc;
+  cudaStream_t ps = F->plan_st;
+  OCR_CUDA(cudaMemcpyAsync(F->d_bseg, segs.data(), sizeof(BatchSeg) * segs.size(),
+                           cudaMemcpyHostToDevice, ps));
+  OCR_CUDA(cudaMemcpyAsync(F->d_bcam, cams.data(), sizeof(BatchCam) * (size_t)K,
+                           cudaMemcpyHostToDevice, ps));
+  OCR_CUDA(cudaStreamSynchronize(ps));  // the host vectors die on return
+  F->nbseg = (int)segs.size();
+  F->nbtickets = tickets;
+  F->batch_ready = true;
   return OCR_OK;
 }
 
@@ -906,7 +1008,18 @@ int render_plans(ocr_forest *F, int first, int K, float *d_rgba, void *stream,
     OCR_CUDA(shell_monomials(F->d_nodal, F->d_coef, F->N, st));
     ++launches;
   }
-  if (K == 1) {
+  const bool whole = first == 0 && K == (int)F->plans.size();
+  if (whole && K > 1 && F->persistent && F->batch_ready && F->merge == 0 && !F->integ.surface) {
+    // every camera in one persistent kernel
+    Topo T{F->d_geo, F->d_child, F->d_leaves, F->N, F->M, F->L, F->lt};
+    Field Fd{F->d_nodal, reinterpret_cast<const float4 *>(F->d_tf), F->s_min,
+             7.f / (F->s_max - F->s_min)};
+    if (F->data_ready) OCR_CUDA(cudaStreamWaitEvent(st, F->data_ready, 0));
+    OCR_CUDA(launch_batch(T, Fd, F->integ, F->d_bseg, F->nbseg, F->d_bcam, F->d_bctl,
+                          F->nbtickets, rgba, counts, visible, F->d_stats, F->nsm,
+                          F->ctas_per_sm, st));
+    launches += 1;
+  } else if (K == 1) {
     int rc = F->geometry == OCR_GEOM_SHELL
                  ? enqueue_shell(F, plans[0], rgba, counts, visible, st, timed, launches)
                  : enqueue_camera(F, plans[0], rgba, counts, visible, st, timed, subtree_ran,
@@ -1199,20 +1312,29 @@ int ocr_set_tuning(ocr_forest *F, const ocr_tuning *t) {
   if (!F || !t) return OCR_ERR_INVALID;
   if (t->tile_depth < 1 || t->tile_depth > kSubtreeDepth || t->streams < 1 ||
       t->streams > kMaxStreams || t->shell_warps < 0 || t->shell_warps > 8 || t->merge < 0 ||
-      t->merge > 1)
+      t->merge > 1 || t->persistent < 0 || t->persistent > 1 || t->chunks_per_item < 1 ||
+      t->chunks_per_item > 64 || t->ctas_per_sm < 0 || t->ctas_per_sm > 8)
     return OCR_ERR_INVALID;
   F->nstreams = t->streams;
   F->shell_warps = t->shell_warps;
   F->merge = t->merge;
+  F->persistent = t->persistent;
+  F->ctas_per_sm = t->ctas_per_sm;
+  const bool requeue = t->chunks_per_item != F->chunks_per_item;
+  F->chunks_per_item = t->chunks_per_item;
   if (t->tile_depth != F->tile_depth) {
     F->tile_depth = t->tile_depth;
     F->lt = F->L > F->tile_depth ? F->L - F->tile_depth : 0;
     if (F->has_cam && F->geometry == OCR_GEOM_CUBE) {
       F->has_cam = false;
-      const int rc = plan_cameras(F);
+      const int rc = plan_cameras(F);  // also rebuilds the batch queue
       if (rc) return rc;
       F->has_cam = true;
     }
+  } else if (requeue && F->has_cam && F->geometry == OCR_GEOM_CUBE) {
+    if (!F->plan_st) OCR_CUDA(cudaStreamCreateWithFlags(&F->plan_st, cudaStreamNonBlocking));
+    const int rc = plan_batch(F);
+    if (rc) return rc;
   }
   return OCR_OK;
 }
@@ -1223,6 +1345,9 @@ int ocr_get_tuning(const ocr_forest *F, ocr_tuning *t) {
   t->streams = F->nstreams;
   t->shell_warps = F->shell_warps;
   t->merge = F->merge;
+  t->persistent = F->persistent;
+  t->chunks_per_item = F->chunks_per_item;
+  t->ctas_per_sm = F->ctas_per_sm;
   t->ms = 0.f;
   return OCR_OK;
 }
@@ -1236,15 +1361,36 @@ int ocr_autotune(ocr_forest *F, int reps, ocr_tuning *best, ocr_tuning *tried, i
   std::vector<ocr_tuning> cand;
   const int streams[] = {1, 2, 4, 8};
   const int warps[] = {1, 2, 4, 8};
+  auto tuning = [&](int d, int s, int w, int m, int p, int c, int o) {
+    ocr_tuning t{};
+    t.tile_depth = d;
+    t.streams = s;
+    t.shell_warps = w;
+    t.merge = m;
+    t.persistent = p;
+    t.chunks_per_item = c;
+    t.ctas_per_sm = o;
+    return t;
+  };
   for (int si = 0; si < 4; ++si) {
     if (K == 1 && streams[si] != F->nstreams) continue;  // one camera: streams are unused
     if (F->geometry == OCR_GEOM_SHELL) {
-      for (int w : warps) cand.push_back({F->tile_depth, streams[si], w, 0, 0.f});
+      for (int w : warps)
+        cand.push_back(tuning(F->tile_depth, streams[si], w, 0, 0, F->chunks_per_item, 0));
     } else {
       for (int m = 0; m <= 1; ++m)
         for (int d = 1; d <= kSubtreeDepth; ++d)
-          if (d <= F->L || d == kSubtreeDepth) cand.push_back({d, streams[si], 0, m, 0.f});
+          if (d <= F->L || d == kSubtreeDepth)
+            cand.push_back(tuning(d, streams[si], 0, m, 0, F->chunks_per_item, 0));
     }
+  }
+  if (F->geometry == OCR_GEOM_CUBE && K > 1) {
+    // the persistent kernel: tile depth x chunks per ticket x CTAs per SM
+    const int chunks[] = {1, 2, 4}, occ[] = {0, 4};
+    for (int d = 1; d <= kSubtreeDepth; ++d)
+      if (d <= F->L || d == kSubtreeDepth)
+        for (int c : chunks)
+          for (int o : occ) cand.push_back(tuning(d, F->nstreams, 0, 0, 1, c, o));
   }
   float4 *rgba = nullptr;
   cudaStream_t st = nullptr;

@@ -121,6 +121,41 @@ cudaError_t launch_coarsen(const Topo &T, const Field &Fd, const Cam &C, const I
 cudaError_t launch_topdown(const Topo &T, const Field &Fd, const Cam &C, const Integ &I, Scratch S,
                            long long npix, float4 *rgba, int nsm, cudaStream_t stream);
 
+// Persistent multi-camera render of a cube forest (ocr_batch.cu).  The work
+// queue is a list of segments, one per (pipeline stage, camera), in queue
+// order (stage after stage, each stage for every camera); a segment's items
+// are grouped `per` to a ticket.
+constexpr int kBatchCull = 0, kBatchUnion = 1, kBatchReduce = 2, kBatchDown = 3,
+              kBatchChunkMap = 4, kBatchSubtree = 5, kBatchCoarse = 6, kBatchPixel = 7;
+constexpr int kBatchMaxSegs = 8192;
+// control words: [1] abort, [2, 2 + kBatchMaxSegs) finished tickets per
+// segment, then the 64-bit ticket counter; zeroed before every launch
+constexpr int kBatchCtlWords = 2 + kBatchMaxSegs + 2;
+struct BatchSeg {
+  long long first;     // first ticket of the segment
+  long long nitems;    // items of the stage for this camera
+  long long ntickets;  // ceil(nitems / per)
+  long long a, b;      // union: internal nodes [a, b); subtree / coarse: slots [a, b);
+                       // pixel: b = the camera's pixels
+  int cam, kind;
+  int dep;             // the segment of the camera's previous stage, -1 for pruning
+  int per;             // items per ticket
+  int nb, ne;          // subtree / coarse: internal nodes [nb, ne) of the level
+};
+struct BatchCam {
+  Cam cam;
+  int4 *rect;
+  long long *off, *bsums;
+  int *chunk;
+  float4 *entries;
+  long long pix_off;
+};
+cudaError_t launch_batch(const Topo &T, const Field &Fd, const Integ &I, const BatchSeg *d_seg,
+                         int nseg, const BatchCam *d_cams, unsigned *d_ctl, long long ntickets,
+                         float4 *rgba, int *counts, unsigned char *visible,
+                         unsigned long long *stats, int nsm, int ctas_per_sm,
+                         cudaStream_t stream);
+
 // Adjoint (ocr_backward.cu)
 cudaError_t bwd_leaf_scan(const Topo &T, const int4 *rect, long long *bs, long long bs_cap,
                           long long *leaf_off, cudaStream_t st);

@@ -145,7 +145,7 @@ def test_null_handles_are_rejected(lib):
     assert lib.ocr_render_backward(None, None, None, None, None) == capi.ERR_INVALID
     assert lib.ocr_forest_set_data(None, None, None, 0.0, 1.0, None) == capi.ERR_INVALID
     assert lib.ocr_device_bytes(None) == 0
-    t = capi.Tuning(3, 4, 0, 0, 0.0)
+    t = capi.Tuning(3, 4, 0, 0, 1, 1, 0, 0.0)
     lib.ocr_set_tuning.argtypes = [C.c_void_p, C.POINTER(capi.Tuning)]
     assert lib.ocr_set_tuning(None, C.byref(t)) == capi.ERR_INVALID
     lib.ocr_autotune.argtypes = [C.c_void_p, C.c_int, C.POINTER(capi.Tuning),

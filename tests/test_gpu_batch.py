@@ -155,3 +155,54 @@ def test_render_view_equals_the_batch(kind):
         capi.render_view(r.h, len(cams), views[0])
     assert e.value.code == capi.ERR_INVALID
     r.close()
+
+
+@pytest.mark.parametrize("chunks,ctas", [(1, 0), (2, 4), (4, 0), (3, 1)])
+def test_persistent_kernel_equals_the_stream_path(chunks, ctas):
+    """The persistent multi-camera kernel (one launch drawing every camera's
+    pruning, prefix-sum, subtree, coarsening and pixel items from one queue)
+    gives the per-camera kernel chains' pixels and counts bit for bit, for
+    several ticket sizes and occupancies, at every tile depth."""
+    from paper_1809_01334_gb300 import Renderer
+    f, tf, _ = I.preset_small()
+    cams = _cams() + [I.perspective_camera(35, 23, 31), I.perspective_camera(36, 70, 5)]
+    r = Renderer(f, tf, INTEG)
+    r.set_cameras(cams)
+    for depth in (1, 2, 3):
+        r.set_tuning(tile_depth=depth, streams=2, persistent=0)
+        ref, _, sref = r.render_batch(with_index=True)
+        ref = ref.clone()
+        r.set_tuning(tile_depth=depth, streams=2, persistent=1, chunks_per_item=chunks,
+                     ctas_per_sm=ctas)
+        out, _, st = r.render_batch(with_index=True)
+        torch.cuda.synchronize()
+        assert st["launches"] == 1
+        assert torch.equal(out, ref)
+        assert torch.equal(st["counts"], sref["counts"])
+        assert torch.equal(st["visible"], sref["visible"])
+        assert st["segments"] == sref["segments"] and st["rk_steps"] == sref["rk_steps"]
+    r.close()
+
+
+def test_persistent_batch_of_the_large_forest_against_the_oracle():
+    """The batching workload's forest (2,053,451 leaves, DOPRI5 tol 1e-6) with
+    six seeded cameras of uneven square sizes in one persistent launch: every
+    pixel of every camera within 1e-4 of the oracle, every ray's segment count
+    equal."""
+    from paper_1809_01334_gb300 import Renderer
+    f, tf, _, integ = I.preset_c2(w=8, h=8)
+    cams = I.batch_cameras(6, lo=48, ratio=4.0)
+    r = Renderer(f, tf, integ)
+    r.set_cameras(cams)
+    assert r.get_tuning()["persistent"] == 1
+    flat, views, st = r.render_batch(with_index=True)
+    torch.cuda.synchronize()
+    assert st["launches"] == 1
+    at = 0
+    for cam, v in zip(cams, views):
+        ref = O.render(f, tf, cam, integ)
+        assert np.abs(v.cpu().numpy() - ref["rgba"]).max() <= 1e-4
+        cnt = st["counts"][at:at + cam.w * cam.h].cpu().numpy().reshape(ref["counts"].shape)
+        np.testing.assert_array_equal(cnt, ref["counts"])
+        at += cam.w * cam.h
+    r.close()

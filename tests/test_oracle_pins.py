@@ -759,3 +759,32 @@ def test_oracle_gradient_matches_central_differences(integ, part):
         assert abs(g[k] - fd) <= 2e-5 * abs(fd) + 1e-6 * scale, (part, k, g[k], fd)
         checked += 1
     assert checked >= (28 if part == "knots" else 20)
+
+
+def test_gradient_term_magnitudes():
+    """The oracle's per-coordinate sum of term magnitudes (the scale of a
+    gradient sum's rounding): never below the sum's own magnitude, unchanged
+    when dL/d(rgba) changes sign (the gradient flips), linear in its scale,
+    and equal to |g| where every term has one sign (dL/d alpha only, with a
+    transfer function rising in kappa and constant in q: all terms of
+    dL/d(nodal) then share the sign of the slope)."""
+    f = I.uniform_cube_forest(1, I.gaussian_field(4, 7))
+    tf = I.transfer_function(f.nodal, 3, kappa_max=8.0)
+    cam = I.perspective_camera(5, 8, 6, dist=(1.8, 2.2))
+    integ = {"method": "rk4", "nsteps": 4}
+    W = np.random.default_rng(2).uniform(-1, 1, (cam.h, cam.w, 4))
+    gn, gt, an, at = O.render_grad(f, tf, cam, integ, W, magnitudes=True)
+    assert (an >= np.abs(gn) * (1 - 1e-12)).all() and (at >= np.abs(gt) * (1 - 1e-12)).all()
+    assert an.max() > np.abs(gn).max()  # some terms cancel
+    gn2, gt2, an2, at2 = O.render_grad(f, tf, cam, integ, -2.0 * W, magnitudes=True)
+    np.testing.assert_allclose(gn2, -2.0 * gn, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(an2, 2.0 * an, rtol=1e-12, atol=1e-15)
+    k = np.arange(8)
+    tf.knots[:] = np.column_stack([0.5 + k, np.full(8, 0.3), np.full(8, 0.2), np.full(8, 0.1)])
+    span = float(f.nodal.max() - f.nodal.min())
+    tf.s_min, tf.s_max = float(f.nodal.min()) - span, float(f.nodal.max()) + span
+    Wa = np.zeros((cam.h, cam.w, 4))
+    Wa[..., 3] = 1.0
+    gn, gt, an, at = O.render_grad(f, tf, cam, integ, Wa, magnitudes=True)
+    assert np.abs(gn).max() > 0
+    np.testing.assert_allclose(an, np.abs(gn), rtol=1e-6, atol=1e-15)
