@@ -302,7 +302,7 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
  *   ctas_per_sm persistent: resident CTAs per SM (1..8; 0 = as many as fit).
  *   ms          ocr_autotune: the measured device time of one ocr_render.
  * Defaults: tile_depth 3, streams 4, shell_warps 0, merge 0, persistent 1,
- * chunks_per_item 1, ctas_per_sm 0. */
+ * chunks_per_item 4, ctas_per_sm 0. */
 typedef struct {
   int tile_depth;
   int streams;
@@ -322,7 +322,7 @@ int ocr_get_tuning(const ocr_forest *F, ocr_tuning *t);
 /* Autotuner: render the cameras, data and integrator last set under every
  * candidate tuning (cube: tile_depth 1..3 x merge {0, 1} x streams {1, 2, 4, 8},
  * and with several cameras the persistent kernel: tile_depth 1..3 x
- * chunks_per_item {1, 2, 4} x ctas_per_sm {all, 4}; shell:
+ * chunks_per_item {2, 4, 8, 16}; shell:
  * shell_warps {1, 2, 4, 8} x streams; streams only with several cameras),
  * one warm-up and `reps` timed renders each (CUDA events on an internal
  * stream, 1 <= reps <= 100), and keep the fastest, returned in *best.  The

@@ -101,23 +101,30 @@ __global__ void __launch_bounds__(kBT, 8)
                  float4 *rgba, int *counts, unsigned char *visible,
                  unsigned long long *stats) {
   __shared__ BatchSmem sm;
+  // the current item's camera and scratch, its segment and ticket, and the
+  // queue state of thread 0 (kept in shared memory, not in registers)
   __shared__ Cam s_cam;
+  __shared__ Scratch s_S;
+  __shared__ float4 *s_rgba;
   __shared__ BatchSeg s_seg;
-  __shared__ long long s_ticket;
-  __shared__ int s_go;
+  __shared__ long long s_ticket, s_next;
+  __shared__ int s_go, s_cs, s_ready, s_cur_cam;
   const int tid = threadIdx.x;
   unsigned *abort_word = ctl + 1, *done = ctl + 2;
   unsigned long long *ticket_ctr = reinterpret_cast<unsigned long long *>(ctl + 2 + kBatchMaxSegs);
-  int cur_cam = -1;
-  int cs = 0;  // thread 0: the segment the last ticket fell in
-  long long next = 0;
-  if (tid == 0) next = (long long)atomicAdd(ticket_ctr, 1ull);
+  if (tid == 0) {
+    s_next = (long long)atomicAdd(ticket_ctr, 1ull);
+    s_cs = 0;
+    s_ready = -1;  // a segment whose previous stage was seen complete
+    s_cur_cam = -1;
+  }
   for (;;) {
     if (tid == 0) {
-      long long t = next;
+      const long long t = s_next;
       if (t < ntickets && !ld_acquire(abort_word)) {
-        next = (long long)atomicAdd(ticket_ctr, 1ull);  // used at the next trip
+        s_next = (long long)atomicAdd(ticket_ctr, 1ull);  // used at the next trip
         // the segment holding ticket t (tickets rise with the segment index)
+        int cs = s_cs;
         if (!(t >= seg[cs].first && (cs + 1 == nseg || t < seg[cs + 1].first))) {
           int lo = 0, hi = nseg - 1;
           while (lo < hi) {
@@ -125,13 +132,14 @@ __global__ void __launch_bounds__(kBT, 8)
             if (seg[mid].first <= t) lo = mid; else hi = mid - 1;
           }
           cs = lo;
+          s_cs = cs;
         }
         s_seg = seg[cs];
         s_ticket = t - seg[cs].first;
         s_go = 1;
-        // wait for the camera's previous stage
+        // wait for the camera's previous stage (once per segment and CTA)
         const int dep = seg[cs].dep;
-        if (dep >= 0) {
+        if (dep >= 0 && s_ready != cs) {
           const unsigned need = (unsigned)seg[dep].ntickets;
           const long long t0 = clock64();
           while (ld_acquire(done + dep) < need) {
@@ -147,6 +155,14 @@ __global__ void __launch_bounds__(kBT, 8)
             }
             __nanosleep(256);
           }
+          s_ready = cs;
+        }
+        const int cam = seg[cs].cam;
+        if (cam != s_cur_cam) {  // this camera's scratch
+          const BatchCam &bc = cams[cam];
+          s_S = Scratch{bc.rect, bc.off, bc.entries, stats,
+                        counts ? counts + bc.pix_off : nullptr, visible, bc.chunk};
+          s_rgba = rgba + bc.pix_off;
         }
       } else {
         s_go = 0;
@@ -154,18 +170,16 @@ __global__ void __launch_bounds__(kBT, 8)
     }
     __syncthreads();
     if (!s_go) break;
-    const BatchSeg g = s_seg;
+    const BatchSeg &g = s_seg;
     const long long tk = s_ticket;
-    if (g.cam != cur_cam) {  // this camera's constants into shared memory
+    if (g.cam != s_cur_cam) {  // this camera's constants into shared memory
       const int *src = reinterpret_cast<const int *>(&cams[g.cam].cam);
       int *dst = reinterpret_cast<int *>(&s_cam);
       for (int q = tid; q < (int)(sizeof(Cam) / sizeof(int)); q += kBT) dst[q] = __ldg(src + q);
-      cur_cam = g.cam;
       __syncthreads();
+      if (tid == 0) s_cur_cam = g.cam;
     }
-    const BatchCam &bc = cams[g.cam];
-    Scratch S{bc.rect, bc.off, bc.entries, stats, counts ? counts + bc.pix_off : nullptr, visible,
-              bc.chunk};
+    const Scratch &S = s_S;
     const float scale = ldexpf(1.f, -T.L);
     for (long long it = tk * g.per; it < min((tk + 1) * g.per, g.nitems); ++it) {
       if (g.kind == kBatchCull) {
@@ -208,11 +222,12 @@ __global__ void __launch_bounds__(kBT, 8)
           if (k < T.M) v += node_slots_b(T, S.rect, (int)k);
         }
         const long long tot = cta_sum(v, sm.sc);
-        if (tid == 0) bc.bsums[it] = tot;
+        if (tid == 0) cams[g.cam].bsums[it] = tot;
       } else if (g.kind == kBatchDown) {
         // the prefix of the earlier blocks, then this block's 1024 nodes in order
         long long v = 0;
-        for (long long b = tid; b < it; b += kBT) v += __ldcg(bc.bsums + b);
+        const long long *bsums = cams[g.cam].bsums;
+        for (long long b = tid; b < it; b += kBT) v += __ldcg(bsums + b);
         long long run = cta_sum(v, sm.sc);
         const long long base = it * kBTile + (long long)tid * kBItems;
         long long a[kBItems], s = 0;
@@ -244,8 +259,8 @@ __global__ void __launch_bounds__(kBT, 8)
         coarsen_chunk<false, false, true>(T, Fd, s_cam, I, S, g.nb, g.ne, g.a, g.b, it, nullptr,
                                           sm.co);
       } else {  // kBatchPixel
-        coarsen_chunk<true, false, true>(T, Fd, s_cam, I, S, T.M, T.M, 0, g.b, it,
-                                         rgba + bc.pix_off, sm.co);
+        coarsen_chunk<true, false, true>(T, Fd, s_cam, I, S, T.M, T.M, 0, g.b, it, s_rgba,
+                                         sm.co);
       }
       __syncthreads();  // shared memory free for the next item
     }
@@ -253,7 +268,7 @@ __global__ void __launch_bounds__(kBT, 8)
     // segment thread 0 found for it
     __threadfence();
     __syncthreads();
-    if (tid == 0) atomicAdd(done + cs, 1u);
+    if (tid == 0) atomicAdd(done + s_cs, 1u);
   }
 }
 

@@ -13,18 +13,23 @@ namespace {
 // ---------------------------------------------------------------- coarsen --
 constexpr int kCoarsenThreads = kChunk;
 
-// Loads of the per-render scratch (rectangles, slot offsets, chunk map,
-// aggregates).  COH: the data may have been written earlier in the same launch
-// by another CTA (the persistent batch kernel), so it is read through L2
-// (ld.global.cg), never from a possibly stale L1 line; otherwise earlier
-// launches wrote it and the read-only path serves.
+// Loads of the per-render scratch.  The rectangles, slot offsets and chunk
+// map (ldp) are complete before any chunk of a pass reads them: the read-only
+// path serves the single-camera kernels (written by earlier launches); in the
+// persistent batch kernel (COH) they were written earlier in the same launch,
+// but every item that reads them waits for the stages that write them and no
+// line of them is read (and cached in L1) before, so plain loads serve there.
+// The aggregates of the previous level (ldw) are different: in the persistent
+// kernel a cache line of them can hold slots of the level being written, so
+// they are read through L2 (ld.global.cg), never from a possibly stale L1
+// line.
 template <bool COH, class V>
 __device__ __forceinline__ V ldp(const V *p) {
-  if constexpr (COH) return __ldcg(p);
+  if constexpr (COH) return *p;
   else return __ldg(p);
 }
 template <bool COH, class V>
-__device__ __forceinline__ V ldw(const V *p) {  // data written by earlier passes
+__device__ __forceinline__ V ldw(const V *p) {
   if constexpr (COH) return __ldcg(p);
   else return *p;
 }
@@ -35,16 +40,16 @@ template <bool COH>
 __device__ __forceinline__ void slot_lookup(const Topo &T, const Scratch &S, int nb, int ne,
                                             long long chunk, long long slot, int &node, int &i,
                                             int &j) {
-  const long long nch = (ldw<COH>(S.off + T.M) + kChunk - 1) / kChunk;
-  int lo = max(ldw<COH>(S.chunk_node + chunk), nb);
-  int hi = (chunk + 1 < nch) ? min(ldw<COH>(S.chunk_node + chunk + 1), ne - 1) + 1 : ne;
+  const long long nch = (S.off[T.M] + kChunk - 1) / kChunk;
+  int lo = max(S.chunk_node[chunk], nb);
+  int hi = (chunk + 1 < nch) ? min(S.chunk_node[chunk + 1], ne - 1) + 1 : ne;
   while (lo < hi) {  // first node whose offset exceeds the slot
     const int mid = (lo + hi) >> 1;
-    if (ldw<COH>(S.off + mid) <= slot) lo = mid + 1; else hi = mid;
+    if (S.off[mid] <= slot) lo = mid + 1; else hi = mid;
   }
   node = lo - 1;
-  const int4 r = ldw<COH>(S.rect + T.N + node);
-  const unsigned local = (unsigned)(slot - ldw<COH>(S.off + node));  // < w * h < 2^31
+  const int4 r = S.rect[T.N + node];
+  const unsigned local = (unsigned)(slot - S.off[node]);  // < w * h < 2^31
   const unsigned rw = (unsigned)(r.y - r.x + 1);
   const unsigned row = local / rw;
   i = r.x + (int)(local - row * rw);
@@ -79,7 +84,7 @@ constexpr int kWarpBatch = 32; // hits per warp batch of phase C
 // Shared memory of one subtree chunk.
 struct SubtreeSmem {
   float4 tfv[8], tfs[8];
-  float ray[6][kSubtreeThreads];                   // ray origin and direction, by component
+  float ray[6][kSubtreeThreads];                   // ray: varying part, reciprocal direction
   signed char liveq[kSubtreeThreads];              // live ray: index of its node, else -1
   int4 qinfo[kSubtreeThreads];                     // node: {rect x0, rect y0, width, off - cs}
   int2 qlr[kSubtreeThreads];                       // node: its leaves [first, end)
@@ -147,12 +152,15 @@ __device__ __forceinline__ void subtree_chunk(const Topo &T, const Field &Fd, co
     float a0, a1;
     live = slab(org, dir, inv, node_lo(gn, scale), ldexpf(1.f, -gn.w), c.amin, c.amax, a0, a1);
   }
-  s_ray[0][tid] = org.x;
-  s_ray[1][tid] = org.y;
-  s_ray[2][tid] = org.z;
-  s_ray[3][tid] = dir.x;
-  s_ray[4][tid] = dir.y;
-  s_ray[5][tid] = dir.z;
+  // the part of the ray that varies over the pixels (the origin of an
+  // orthographic camera, the direction of a perspective one) and the
+  // reciprocal direction, taken once per ray
+  s_ray[0][tid] = c.ortho ? org.x : dir.x;
+  s_ray[1][tid] = c.ortho ? org.y : dir.y;
+  s_ray[2][tid] = c.ortho ? org.z : dir.z;
+  s_ray[3][tid] = inv.x;
+  s_ray[4][tid] = inv.y;
+  s_ray[5][tid] = inv.z;
   int *s_node = s_cnt;  // node of each slot (-1 inactive) until phase A
   s_node[tid] = active ? node : -1;
   __syncthreads();
@@ -250,9 +258,10 @@ __device__ __forceinline__ void subtree_chunk(const Topo &T, const Field &Fd, co
       const unsigned long long gq = s_qgeo[q];
       const int4 g = make_int4((int)(gq & 0x1fffffu) + (int)rx, (int)((gq >> 21) & 0x1fffffu) + (int)ry,
                                (int)(gq >> 42) + (int)rz, (int)(rel >> 24));
-      const float3 ro = make_float3(s_ray[0][t], s_ray[1][t], s_ray[2][t]);
-      const float3 rd = make_float3(s_ray[3][t], s_ray[4][t], s_ray[5][t]);
-      const float3 ri = make_float3(recip_or_zero(rd.x), recip_or_zero(rd.y), recip_or_zero(rd.z));
+      const float3 rv = make_float3(s_ray[0][t], s_ray[1][t], s_ray[2][t]);
+      const float3 ro = c.ortho ? rv : make_float3(c.o[0], c.o[1], c.o[2]);
+      const float3 rd = c.ortho ? make_float3(c.v[0], c.v[1], c.v[2]) : rv;
+      const float3 ri = make_float3(s_ray[3][t], s_ray[4][t], s_ray[5][t]);
       float b0, b1;
       if (!slab(ro, rd, ri, node_lo(g, scale), ldexpf(1.f, -g.w), c.amin, c.amax, b0, b1))
         continue;
@@ -376,12 +385,12 @@ __device__ __forceinline__ void subtree_chunk(const Topo &T, const Field &Fd, co
       if (h < b1) {
         const int t = wid * 32 + ow;
         const int leaf = leaf_base + (int)(s_list[h - owpre][t] & 0x3fffffu);
-        const float3 ro = make_float3(s_ray[0][t], s_ray[1][t], s_ray[2][t]);
-        const float3 rd = make_float3(s_ray[3][t], s_ray[4][t], s_ray[5][t]);
+        const float3 rv = make_float3(s_ray[0][t], s_ray[1][t], s_ray[2][t]);
+        const float3 ro = c.ortho ? rv : make_float3(c.o[0], c.o[1], c.o[2]);
+        const float3 rd = c.ortho ? make_float3(c.v[0], c.v[1], c.v[2]) : rv;
         s_res[wid][h - b0] = leaf_segment<SURF>(T, Fd, c, I, tf, leaf, ro, rd,
-                                          make_float3(recip_or_zero(rd.x), recip_or_zero(rd.y),
-                                                      recip_or_zero(rd.z)),
-                                          scale, steps);
+                                                make_float3(s_ray[3][t], s_ray[4][t], s_ray[5][t]),
+                                                scale, steps);
       }
     }
     __syncwarp();
