@@ -216,7 +216,7 @@ def _tuning_dict(t: Tuning) -> dict:
 
 
 def set_tuning(h, tile_depth: int = 3, streams: int = 4, shell_warps: int = 0, merge: int = 0,
-               persistent: int = 1, chunks_per_item: int = 4, ctas_per_sm: int = 0):
+               persistent: int = 1, chunks_per_item: int = 16, ctas_per_sm: int = 0):
     """ocr_set_tuning (a cube forest re-plans its cameras when tile_depth changes)."""
     t = Tuning(int(tile_depth), int(streams), int(shell_warps), int(merge), int(persistent),
                int(chunks_per_item), int(ctas_per_sm), 0.0)

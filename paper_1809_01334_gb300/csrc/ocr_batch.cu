@@ -95,7 +95,10 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
   return v;
 }
 
-__global__ void __launch_bounds__(kBT, 8)
+// MINB: the CTAs per SM the kernel is compiled for (8: at most 64 registers,
+// with some spills; 6: up to 80, none).
+template <int MINB>
+__global__ void __launch_bounds__(kBT, MINB)
     batch_kernel(Topo T, Field Fd, Integ I, const BatchSeg *__restrict__ seg, int nseg,
                  const BatchCam *__restrict__ cams, unsigned *ctl, long long ntickets,
                  float4 *rgba, int *counts, unsigned char *visible,
@@ -282,9 +285,14 @@ cudaError_t launch_batch(const Topo &T, const Field &Fd, const Integ &I, const B
   if (nseg < 1 || nseg > kBatchMaxSegs || ntickets < 1) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(d_ctl, 0, sizeof(unsigned) * kBatchCtlWords, stream);
   if (e != cudaSuccess) return e;
-  static int fit = 0;  // resident CTAs per SM (a property of the kernel and the device)
+  // ctas_per_sm 1..6: the variant compiled for 6 CTAs per SM (more registers);
+  // 0 or 7..8: the one for 8, as many CTAs as fit (or ctas_per_sm)
+  const bool six = ctas_per_sm > 0 && ctas_per_sm <= 6;
+  static int fit8 = 0, fit6 = 0;  // resident CTAs per SM of each variant
+  int &fit = six ? fit6 : fit8;
   if (!fit) {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, batch_kernel, kBT, 0);
+    e = six ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, batch_kernel<6>, kBT, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, batch_kernel<8>, kBT, 0);
     if (e != cudaSuccess) return e;
   }
   int per_sm = fit;
@@ -292,8 +300,12 @@ cudaError_t launch_batch(const Topo &T, const Field &Fd, const Integ &I, const B
   if (per_sm < 1) per_sm = 1;
   long long grid = (long long)(nsm > 0 ? nsm : 1) * per_sm;
   if (grid > ntickets) grid = ntickets;
-  batch_kernel<<<(unsigned)grid, kBT, 0, stream>>>(T, Fd, I, d_seg, nseg, d_cams, d_ctl, ntickets,
-                                                    rgba, counts, visible, stats);
+  if (six)
+    batch_kernel<6><<<(unsigned)grid, kBT, 0, stream>>>(T, Fd, I, d_seg, nseg, d_cams, d_ctl,
+                                                         ntickets, rgba, counts, visible, stats);
+  else
+    batch_kernel<8><<<(unsigned)grid, kBT, 0, stream>>>(T, Fd, I, d_seg, nseg, d_cams, d_ctl,
+                                                         ntickets, rgba, counts, visible, stats);
   return cudaGetLastError();
 }
 

@@ -84,7 +84,7 @@ struct ocr_forest {
                                       // (0) or by one top-down pass per pixel (1)
   int persistent = 1;                 // cube, several cameras: one persistent kernel (1) or
                                       // per-camera kernel chains over the streams (0)
-  int chunks_per_item = 4;            // persistent: chunks of the chunk passes per ticket
+  int chunks_per_item = 16;           // persistent: chunks of the chunk passes per ticket
   int ctas_per_sm = 0;                // persistent: CTAs per SM (0: as many as fit)
   // persistent batch: the work queue (segments), per-camera device records and
   // the control words; rebuilt when the cameras or the decomposition change
@@ -1386,7 +1386,7 @@ int ocr_autotune(ocr_forest *F, int reps, ocr_tuning *best, ocr_tuning *tried, i
   }
   if (F->geometry == OCR_GEOM_CUBE && K > 1) {
     // the persistent kernel: tile depth x chunks per ticket x CTAs per SM
-    const int chunks[] = {2, 4, 8, 16}, occ[] = {0};
+    const int chunks[] = {4, 8, 16, 32}, occ[] = {0, 6};
     for (int d = 1; d <= kSubtreeDepth; ++d)
       if (d <= F->L || d == kSubtreeDepth)
         for (int c : chunks)
