@@ -79,6 +79,8 @@ constexpr int kSubtreeThreads = kChunk;  // one chunk per CTA
 constexpr int kCand = kSubtreeThreads;  // candidate table of phase A
 constexpr int kPairWin = 1024;          // (candidate, pixel) pairs resolved per window
 static_assert(kCand <= 256, "candidate indices are stored in one byte");
+static_assert(sizeof(int4) * kCand == sizeof(float4) * kChunk,
+              "phase A's candidate boxes and phase C's values share their storage");
 constexpr int kWarpBatch = 32; // hits per warp batch of phase C
 
 // Shared memory of one subtree chunk.
@@ -90,14 +92,16 @@ struct SubtreeSmem {
   int2 qlr[kSubtreeThreads];                       // node: its leaves [first, end)
   int2 qrows[kSubtreeThreads];                     // node: its rows in the chunk
   unsigned long long qgeo[kSubtreeThreads];        // node: anchor x | y << 21 | z << 42
-  int4 cbox[kCand];                                // candidate: rectangle within the rows
+  union {
+    int4 cbox[kCand];                              // phase A: candidate rectangle within the rows
+    float4 res[kSubtreeThreads / 32][kWarpBatch];  // phase C: the warps' segment values
+  };
   int cpre[kCand + 1];                             // candidate: pair count, then prefix
   unsigned crel[kCand];                            // candidate: anchor in the node, level
   int cl[kCand];                                   // candidate: (node index << 22) | leaf - base
   unsigned char pc[kPairWin];                      // candidate of each pair in the window
   int cnt[kSubtreeThreads];                        // hits of each ray
   unsigned list[kMaxSubtreeHits][kSubtreeThreads]; // (mirrored key << 22) | leaf - base
-  float4 res[kSubtreeThreads / 32][kWarpBatch];
   int wcnt[kSubtreeThreads / 32], nn, leaf_base, ncand, ltot;
 };
 
