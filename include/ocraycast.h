@@ -300,7 +300,8 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
  *   chunks_per_item  persistent: 128-slot chunks of the subtree, coarsening
  *               and pixel passes handed out per ticket (1..64).
  *   ctas_per_sm persistent: resident CTAs per SM (1..8; 0 = as many as fit:
- *               8); 1..6 select a variant compiled for 6 (more registers).
+ *               8); 6 and 7 select variants compiled for that many, with more
+ *               registers per thread (1..5 use the one for 6).
  *   ms          ocr_autotune: the measured device time of one ocr_render.
  * Defaults: tile_depth 3, streams 4, shell_warps 0, merge 0, persistent 1,
  * chunks_per_item 16, ctas_per_sm 0. */
@@ -323,7 +324,7 @@ int ocr_get_tuning(const ocr_forest *F, ocr_tuning *t);
 /* Autotuner: render the cameras, data and integrator last set under every
  * candidate tuning (cube: tile_depth 1..3 x merge {0, 1} x streams {1, 2, 4, 8},
  * and with several cameras the persistent kernel: tile_depth 1..3 x
- * chunks_per_item {4, 8, 16, 32} x ctas_per_sm {all, 6}; shell:
+ * chunks_per_item {8, 16, 32} x ctas_per_sm {8, 7, 6}; shell:
  * shell_warps {1, 2, 4, 8} x streams; streams only with several cameras),
  * one warm-up and `reps` timed renders each (CUDA events on an internal
  * stream, 1 <= reps <= 100), and keep the fastest, returned in *best.  The

@@ -96,7 +96,7 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
 }
 
 // MINB: the CTAs per SM the kernel is compiled for (8: at most 64 registers,
-// with some spills; 6: up to 80, none).
+// with some spills; 7: 72; 6: up to 80, none).
 template <int MINB>
 __global__ void __launch_bounds__(kBT, MINB)
     batch_kernel(Topo T, Field Fd, Integ I, const BatchSeg *__restrict__ seg, int nseg,
@@ -285,27 +285,31 @@ cudaError_t launch_batch(const Topo &T, const Field &Fd, const Integ &I, const B
   if (nseg < 1 || nseg > kBatchMaxSegs || ntickets < 1) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(d_ctl, 0, sizeof(unsigned) * kBatchCtlWords, stream);
   if (e != cudaSuccess) return e;
-  // ctas_per_sm 1..6: the variant compiled for 6 CTAs per SM (more registers);
-  // 0 or 7..8: the one for 8, as many CTAs as fit (or ctas_per_sm)
-  const bool six = ctas_per_sm > 0 && ctas_per_sm <= 6;
-  static int fit8 = 0, fit6 = 0;  // resident CTAs per SM of each variant
-  int &fit = six ? fit6 : fit8;
-  if (!fit) {
-    e = six ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, batch_kernel<6>, kBT, 0)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, batch_kernel<8>, kBT, 0);
+  // the variant compiled for the CTAs per SM asked for (1..6: the one for 6,
+  // 7: for 7, 0 or 8: for 8 -- fewer CTAs per SM leave more registers)
+  const int v = ctas_per_sm == 0 ? 8 : ctas_per_sm <= 6 ? 6 : ctas_per_sm;
+  static int fit[9] = {};  // resident CTAs per SM of each variant
+  if (!fit[v]) {
+    e = v == 6   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit[v], batch_kernel<6>, kBT, 0)
+        : v == 7 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit[v], batch_kernel<7>, kBT, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit[v], batch_kernel<8>, kBT, 0);
     if (e != cudaSuccess) return e;
   }
-  int per_sm = fit;
+  int per_sm = fit[v];
   if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
   if (per_sm < 1) per_sm = 1;
   long long grid = (long long)(nsm > 0 ? nsm : 1) * per_sm;
   if (grid > ntickets) grid = ntickets;
-  if (six)
-    batch_kernel<6><<<(unsigned)grid, kBT, 0, stream>>>(T, Fd, I, d_seg, nseg, d_cams, d_ctl,
-                                                         ntickets, rgba, counts, visible, stats);
+  const unsigned g = (unsigned)grid;
+  if (v == 6)
+    batch_kernel<6><<<g, kBT, 0, stream>>>(T, Fd, I, d_seg, nseg, d_cams, d_ctl, ntickets, rgba,
+                                           counts, visible, stats);
+  else if (v == 7)
+    batch_kernel<7><<<g, kBT, 0, stream>>>(T, Fd, I, d_seg, nseg, d_cams, d_ctl, ntickets, rgba,
+                                           counts, visible, stats);
   else
-    batch_kernel<8><<<(unsigned)grid, kBT, 0, stream>>>(T, Fd, I, d_seg, nseg, d_cams, d_ctl,
-                                                         ntickets, rgba, counts, visible, stats);
+    batch_kernel<8><<<g, kBT, 0, stream>>>(T, Fd, I, d_seg, nseg, d_cams, d_ctl, ntickets, rgba,
+                                           counts, visible, stats);
   return cudaGetLastError();
 }
 

@@ -1386,7 +1386,7 @@ int ocr_autotune(ocr_forest *F, int reps, ocr_tuning *best, ocr_tuning *tried, i
   }
   if (F->geometry == OCR_GEOM_CUBE && K > 1) {
     // the persistent kernel: tile depth x chunks per ticket x CTAs per SM
-    const int chunks[] = {4, 8, 16, 32}, occ[] = {0, 6};
+    const int chunks[] = {8, 16, 32}, occ[] = {0, 7, 6};
     for (int d = 1; d <= kSubtreeDepth; ++d)
       if (d <= F->L || d == kSubtreeDepth)
         for (int c : chunks)

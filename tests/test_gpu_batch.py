@@ -157,7 +157,7 @@ def test_render_view_equals_the_batch(kind):
     r.close()
 
 
-@pytest.mark.parametrize("chunks,ctas", [(1, 0), (2, 4), (4, 0), (3, 1)])
+@pytest.mark.parametrize("chunks,ctas", [(1, 0), (2, 4), (16, 0), (3, 7), (32, 6)])
 def test_persistent_kernel_equals_the_stream_path(chunks, ctas):
     """The persistent multi-camera kernel (one launch drawing every camera's
     pruning, prefix-sum, subtree, coarsening and pixel items from one queue)
