@@ -417,7 +417,7 @@ def render_grad(forest, tf, cam, integ: dict, dL_drgba, bg=(0.0, 0.0, 0.0), nthr
     if rc == -1:
         raise MemoryError("oracle gradient: allocation failed")
     if rc != 0:
-        raise ValueError("oracle gradient: only RK4 and DOPRI5 are differentiated")
+        raise ValueError("oracle gradient: surfaces are not differentiated")
     out = (gn, gt)
     if tree_band is not None:
         out += (tie.astype(bool),)

@@ -1397,11 +1397,98 @@ static void combine_bwd(const double *nr, const double *fr, const double *ybar, 
   fbar[0] = ybar[0] * nr[0];
 }
 
+/* Adjoint of the Gauss-2 closed form (Eqs. 2.32-2.33) over [x1, x2]: A and B
+ * are rational in (kappa, q) at the two Gauss nodes; ybar = dL/d(A, B). */
+static void gauss2_step_bwd(const seg_ctx *S, int leaf, double x1, double x2, const double *ybar,
+                            grad_acc *G) {
+  const double r3 = sqrt(3.0), dx = x2 - x1;
+  const double xa = x1 + (0.5 - r3 / 6.0) * dx, xb = x1 + (0.5 + r3 / 6.0) * dx;
+  double k0[4], k1[4];
+  medium_at(S, xa, k0);
+  medium_at(S, xb, k1);
+  const double a1 = dx * (k0[0] + k1[0]) / 4.0, a2 = dx * dx * k0[0] * k1[0] / 12.0;
+  const double den = 1.0 + a1 + a2, s = dx * dx * r3 / 12.0;
+  /* d(den)/d(kappa_0), d(den)/d(kappa_1); d(numerator of A) = d(den) - dx/2 */
+  const double d0 = dx / 4.0 + dx * dx * k1[0] / 12.0, d1 = dx / 4.0 + dx * dx * k0[0] / 12.0;
+  double v0[4], v1[4];
+  v0[0] = ybar[0] * (2.0 * a1 * d0 - 0.5 * dx * den) / (den * den);
+  v1[0] = ybar[0] * (2.0 * a1 * d1 - 0.5 * dx * den) / (den * den);
+  for (int c = 1; c < 4; ++c) {
+    const double Bc = (dx * (k0[c] + k1[c]) / 2.0 + s * (k0[0] * k1[c] - k1[0] * k0[c])) / den;
+    v0[0] += ybar[c] * (s * k1[c] - Bc * d0) / den;
+    v1[0] += ybar[c] * (-s * k0[c] - Bc * d1) / den;
+    v0[c] = ybar[c] * (0.5 * dx - s * k1[0]) / den;
+    v1[c] = ybar[c] * (0.5 * dx + s * k0[0]) / den;
+  }
+  medium_bwd(S, leaf, xa, v0, G);
+  medium_bwd(S, leaf, xb, v1, G);
+}
+
+/* Adjoint of Simpson's rule on the closed form (Eq. 2.34), nodes far end,
+ * midpoint, near end: A = exp(e), e = -dx (k_0 + 4 k_h + k_2) / 6,
+ * B_c = dx (A q_0 + 4 sqrt(A) q_h + q_2) / 6. */
+static void simpson_step_bwd(const seg_ctx *S, int leaf, double x1, double x2, const double *ybar,
+                             grad_acc *G) {
+  const double dx = x2 - x1, xm = 0.5 * (x1 + x2);
+  double k0[4], kh[4], k2[4];
+  medium_at(S, x1, k0);
+  medium_at(S, xm, kh);
+  medium_at(S, x2, k2);
+  const double A = exp(-dx * (k0[0] + 4.0 * kh[0] + k2[0]) / 6.0), sa = sqrt(A);
+  double s0 = 0.0, sh = 0.0;
+  for (int c = 1; c < 4; ++c) {
+    s0 += ybar[c] * k0[c];
+    sh += ybar[c] * kh[c];
+  }
+  /* dL/de: through A directly and through A and sqrt(A) in B */
+  const double Fe = ybar[0] * A + dx / 6.0 * (s0 * A + 2.0 * sh * sa);
+  double v0[4], vh[4], v2[4];
+  v0[0] = -dx / 6.0 * Fe;
+  vh[0] = -4.0 * dx / 6.0 * Fe;
+  v2[0] = -dx / 6.0 * Fe;
+  for (int c = 1; c < 4; ++c) {
+    v0[c] = ybar[c] * dx * A / 6.0;
+    vh[c] = ybar[c] * 4.0 * dx * sa / 6.0;
+    v2[c] = ybar[c] * dx / 6.0;
+  }
+  medium_bwd(S, leaf, x1, v0, G);
+  medium_bwd(S, leaf, xm, vh, G);
+  medium_bwd(S, leaf, x2, v2, G);
+}
+
+/* Adjoint of the Eq. 2.18 interface: A = exp(e) (Simpson's rule on the optical
+ * depth), B_c = I_c (1 - A) with I_c read at the midpoint. */
+static void equilibrium_step_bwd(const seg_ctx *S, int leaf, double x1, double x2,
+                                 const double *ybar, grad_acc *G) {
+  const double dx = x2 - x1, xm = 0.5 * (x1 + x2);
+  double k0[4], kh[4], k2[4];
+  medium_at(S, x1, k0);
+  medium_at(S, xm, kh);
+  medium_at(S, x2, k2);
+  const double e = -dx * (k0[0] + 4.0 * kh[0] + k2[0]) / 6.0, A = exp(e), om = -expm1(e);
+  double sI = 0.0;
+  for (int c = 1; c < 4; ++c) sI += ybar[c] * kh[c];
+  const double Fe = A * (ybar[0] - sI); /* dL/de */
+  double v0[4] = {-dx / 6.0 * Fe, 0.0, 0.0, 0.0}, v2[4] = {-dx / 6.0 * Fe, 0.0, 0.0, 0.0};
+  double vh[4] = {-4.0 * dx / 6.0 * Fe, 0.0, 0.0, 0.0};
+  for (int c = 1; c < 4; ++c) vh[c] = ybar[c] * om;
+  medium_bwd(S, leaf, x1, v0, G);
+  medium_bwd(S, leaf, xm, vh, G);
+  medium_bwd(S, leaf, x2, v2, G);
+}
+
 /* Adjoint of Algorithm 1 (the step tree is re-derived with the same tests). */
 static void segeval_bwd(const seg_ctx *S, const orc_integrator *I, int leaf, double x1, double x2,
                         int depth, const double *ybar, grad_acc *G) {
-  double y5[4], kmax, err;
-  dopri_step(S, x1, x2, y5, &kmax, &err);
+  double y5[4], kmax, err = 0.0;
+  if (I->method == ORC_GAUSS2)
+    gauss2_step(S, x1, x2, y5, &kmax);
+  else if (I->method == ORC_SIMPSON)
+    simpson_step(S, x1, x2, y5, &kmax);
+  else if (I->method == ORC_EQUILIBRIUM)
+    equilibrium_step(S, x1, x2, y5, &kmax);
+  else
+    dopri_step(S, x1, x2, y5, &kmax, &err);
   /* a test within the band of its threshold can go either way in another
    * precision: the gradient of that leaf then belongs to another step tree */
   if (G->tree_tie && depth < I->max_depth &&
@@ -1420,7 +1507,14 @@ static void segeval_bwd(const seg_ctx *S, const orc_integrator *I, int leaf, dou
     segeval_bwd(S, I, leaf, xm, x2, depth + 1, nb, G);
     return;
   }
-  rk_step_bwd(S, leaf, x1, x2 - x1, 6, DP_C, &DP_A[0][0], 6, DP_B, ybar, G);
+  if (I->method == ORC_GAUSS2)
+    gauss2_step_bwd(S, leaf, x1, x2, ybar, G);
+  else if (I->method == ORC_SIMPSON)
+    simpson_step_bwd(S, leaf, x1, x2, ybar, G);
+  else if (I->method == ORC_EQUILIBRIUM)
+    equilibrium_step_bwd(S, leaf, x1, x2, ybar, G);
+  else
+    rk_step_bwd(S, leaf, x1, x2 - x1, 6, DP_C, &DP_A[0][0], 6, DP_B, ybar, G);
 }
 
 /* Adjoint of orc_segment_ab (RK4 and DOPRI5). */
@@ -1462,7 +1556,7 @@ int orc_render_grad(const orc_forest *F, const orc_camera *C, const orc_integrat
                     const double *dL_drgba, double *g_nodal, double *g_tf, int nthreads,
                     int decide32, uint8_t *tree_tie, double tree_band, double *a_nodal,
                     double *a_tf) {
-  if (I->method != ORC_RK4 && I->method != ORC_DOPRI5) return -2;
+  if (I->surface) return -2;
   const int W = C->w, H = C->h, widen = decide32 ? 0 : 1;
   orc_cam32 K;
   float *tan_t = NULL, *rad_t = NULL;

@@ -184,7 +184,8 @@ int64_t orc_render_ex(const orc_forest *F, const orc_camera *C, const orc_integr
  * per pixel the segments are ordered by alpha, each one's adjoint follows
  * from the transmittance of the nearer ones and the aggregate of the farther
  * ones (with the background), and is carried back through the integrator
- * (RK4 or Algorithm 1 with DOPRI5; the step tree is re-derived with the same
+ * (RK4, or Algorithm 1 with DOPRI5, the Gauss-2 closed form, Simpson's rule
+ * or the Eq. 2.18 interface; the step tree is re-derived with the same
  * tests), the transfer function and the trilinear (cube) or triquadratic
  * (shell) interpolation.  g_nodal [nleaves*8 or *27], g_tf [32] are
  * overwritten.  decide32 as in orc_render_ex.  tree_tie [nleaves] (may be
@@ -195,7 +196,7 @@ int64_t orc_render_ex(const orc_forest *F, const orc_camera *C, const orc_integr
  * discretisation.  a_nodal, a_tf (may be NULL) receive, per coordinate, the
  * sum of the magnitudes of the terms summed into it (at the transfer function
  * and the interpolation weights): the scale of the rounding error of that
- * sum.  Returns 0, -1 when out of memory, or -2 for other integrators. */
+ * sum.  Returns 0, -1 when out of memory, or -2 with a surface. */
 int orc_render_grad(const orc_forest *F, const orc_camera *C, const orc_integrator *I,
                     const double *dL_drgba, double *g_nodal, double *g_tf, int nthreads,
                     int decide32, uint8_t *tree_tie, double tree_band, double *a_nodal,

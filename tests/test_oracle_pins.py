@@ -713,7 +713,10 @@ def _loss(forest, tf, cam, integ, W, bg):
 
 
 @pytest.mark.parametrize("integ", [{"method": "rk4", "nsteps": 4},
-                                   {"method": "dopri5", "tol": 1e-6, "c_rk": 0.5, "max_depth": 16}])
+                                   {"method": "dopri5", "tol": 1e-6, "c_rk": 0.5, "max_depth": 16},
+                                   {"method": "gauss2", "c_rk": 0.05, "max_depth": 16},
+                                   {"method": "simpson", "c_rk": 0.2, "max_depth": 16},
+                                   {"method": "equilibrium", "c_rk": 0.2, "max_depth": 16}])
 @pytest.mark.parametrize("part", ["knots", "nodal"])
 def test_oracle_gradient_matches_central_differences(integ, part):
     """The FP64 reverse-mode gradient of L = sum(W * rgba) equals central

