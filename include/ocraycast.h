@@ -269,8 +269,10 @@ int ocr_render_host(ocr_forest *F, const float *h_nodal, const float *h_tf, floa
  * by entry depth; overlapping rounding slivers are combined as if they did
  * not overlap.  More than 2^32 - 2 segments in all: OCR_ERR_UNSUPPORTED.  The
  * library keeps 32 B of scratch per segment for the adjoint (grown on demand,
- * OCR_ERR_OOM if that fails).  RK4 and DOPRI5 only (OCR_ERR_UNSUPPORTED
- * otherwise).  Blocks the host (cube: three times, for the sizes of the pair
+ * OCR_ERR_OOM if that fails).  Every integrator: RK4, and inside Algorithm 1
+ * DOPRI5 (stage recurrences run backwards), the Gauss-2 closed form, Simpson's
+ * rule and the Eq. 2.18 interface (their closed forms differentiated, Eqs.
+ * 2.32-2.34); surfaces return OCR_ERR_UNSUPPORTED.  Blocks the host (cube: three times, for the sizes of the pair
  * space and of the hit lists and the error word; shell: once, for the error
  * word). */
 int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_nodal,

@@ -443,6 +443,66 @@ __device__ void dopri_step_bwd(SA &S, const TF &tf, float t0, float dtau, float 
   }
 }
 
+// adjoints of the closed-form steps of Algorithm 1 over [t0, t0 + dtau] of
+// tau (world length H), from ybar = dL/d(A, B) of the step.  The medium at
+// the nodes is passed as the forward step evaluated it.
+// Gauss-2 (Eqs. 2.32-2.33): A, B rational in (kappa, q) at the two nodes.
+template <class SA>
+__device__ void gauss2_step_bwd(SA &S, const TF &tf, float ta, float tb, float H, float4 g0,
+                                float4 g1, float4 Sv, float4 ybar, TfGrad &tg) {
+  const float a1 = 0.25f * H * (g0.x + g1.x), a2 = (H * H / 12.f) * g0.x * g1.x;
+  const float den = 1.f + a1 + a2, inv = 1.f / den;
+  const float h2 = H * H * 0.14433756729740644f;  // H^2 sqrt(3) / 12
+  const float d0 = fmaf(H * H / 12.f, g1.x, 0.25f * H), d1 = fmaf(H * H / 12.f, g0.x, 0.25f * H);
+  float4 v0, v1;
+  v0.x = ybar.x * (2.f * a1 * d0 - 0.5f * H * den) * inv * inv;
+  v1.x = ybar.x * (2.f * a1 * d1 - 0.5f * H * den) * inv * inv;
+  const float q0[3] = {g0.y, g0.z, g0.w}, q1[3] = {g1.y, g1.z, g1.w};
+  const float yb[3] = {ybar.y, ybar.z, ybar.w}, B[3] = {Sv.y, Sv.z, Sv.w};
+  float w0[3], w1[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    v0.x += yb[c] * (h2 * q1[c] - B[c] * d0) * inv;
+    v1.x += yb[c] * (-h2 * q0[c] - B[c] * d1) * inv;
+    w0[c] = yb[c] * (0.5f * H - h2 * g1.x) * inv;
+    w1[c] = yb[c] * (0.5f * H + h2 * g0.x) * inv;
+  }
+  v0.y = w0[0]; v0.z = w0[1]; v0.w = w0[2];
+  v1.y = w1[0]; v1.z = w1[1]; v1.w = w1[2];
+  S.bwd(tf, ta, v0, tg);
+  S.bwd(tf, tb, v1, tg);
+}
+
+// Simpson's rule on the closed form (Eq. 2.34) and the Eq. 2.18 interface:
+// nodes at the far end, midpoint and near end, A = exp(e) with
+// e = -H (k_0 + 4 k_h + k_1) / 6; Simpson: B = H (A q_0 + 4 sqrt(A) q_h + q_1) / 6;
+// Eq. 2.18: B = I_h (1 - A).
+template <class SA>
+__device__ void simpson_step_bwd(SA &S, const TF &tf, bool equilibrium, float t0, float dtau,
+                                 float H, float4 k0, float4 kh, float4 k1, float A, float sa,
+                                 float4 ybar, TfGrad &tg) {
+  const float h6 = H / 6.f;
+  float4 v0, vh, v1;
+  if (equilibrium) {
+    const float om = 1.f - A;
+    const float Fe = A * (ybar.x - (ybar.y * kh.y + ybar.z * kh.z + ybar.w * kh.w));
+    v0 = make_float4(-h6 * Fe, 0.f, 0.f, 0.f);
+    v1 = v0;
+    vh = make_float4(-4.f * h6 * Fe, ybar.y * om, ybar.z * om, ybar.w * om);
+  } else {
+    const float s0 = ybar.y * k0.y + ybar.z * k0.z + ybar.w * k0.w;
+    const float sh = ybar.y * kh.y + ybar.z * kh.z + ybar.w * kh.w;
+    const float Fe = fmaf(ybar.x, A, h6 * fmaf(s0, A, 2.f * sh * sa));
+    const float w0 = h6 * A, wh = 4.f * h6 * sa;
+    v0 = make_float4(-h6 * Fe, ybar.y * w0, ybar.z * w0, ybar.w * w0);
+    vh = make_float4(-4.f * h6 * Fe, ybar.y * wh, ybar.z * wh, ybar.w * wh);
+    v1 = make_float4(-h6 * Fe, ybar.y * h6, ybar.z * h6, ybar.w * h6);
+  }
+  S.bwd(tf, t0, v0, tg);
+  S.bwd(tf, t0 + 0.5f * dtau, vh, tg);
+  S.bwd(tf, t0 + dtau, v1, tg);
+}
+
 // adjoint of one step with value Sm, near transmittance Tm and far aggregate
 // Gm (background folded in through bg): dL/d(A, B) of the step
 __device__ __forceinline__ float4 step_adjoint(float Tm, float4 Gm, float4 Ib, float ab,
@@ -479,6 +539,69 @@ __device__ void segment_steps_bwd(SA &S, const TF &tf, float dx, const Integ &I,
   unsigned idx = 0;
   float4 kq0 = S.kq(tf, 0.f);
   const float4 one = seg_identity();
+  if (I.method != 1) {  // the closed forms inside Algorithm 1 (c_RK test alone)
+    for (;;) {
+      const float dtau = ldexpf(1.f, -depth);
+      const float t0 = (float)idx * dtau;
+      const float H = dx * dtau;
+      // the forward step (value, split test) exactly as integrate_segment
+      float4 Sv, kq1 = kq0, g0, g1, kh;
+      float kmax, A = 0.f, sa = 0.f;
+      const float ta = fmaf(0.21132486540518713f, dtau, t0);
+      const float tb = fmaf(0.78867513459481287f, dtau, t0);
+      if (I.method == 2) {
+        g0 = S.kq(tf, ta);
+        g1 = S.kq(tf, tb);
+        const float a1 = 0.25f * H * (g0.x + g1.x), a2 = (H * H / 12.f) * g0.x * g1.x;
+        const float inv = 1.f / (1.f + a1 + a2);
+        const float h2 = H * H * 0.14433756729740644f;
+        Sv.x = (1.f - a1 + a2) * inv;
+        Sv.y = (0.5f * H * (g0.y + g1.y) + h2 * (g0.x * g1.y - g1.x * g0.y)) * inv;
+        Sv.z = (0.5f * H * (g0.z + g1.z) + h2 * (g0.x * g1.z - g1.x * g0.z)) * inv;
+        Sv.w = (0.5f * H * (g0.w + g1.w) + h2 * (g0.x * g1.w - g1.x * g0.w)) * inv;
+        kmax = H * fmaxf(g0.x, g1.x);
+      } else {
+        kh = S.kq(tf, t0 + 0.5f * dtau);
+        kq1 = S.kq(tf, t0 + dtau);
+        const float e = -(H / 6.f) * (kq0.x + 4.f * kh.x + kq1.x);
+        if (I.method == 4) {
+          const float om = -expm1f(e);
+          A = 1.f - om;
+          Sv = make_float4(A, kh.y * om, kh.z * om, kh.w * om);
+        } else {
+          sa = __expf(0.5f * e);
+          A = sa * sa;
+          const float w0 = (H / 6.f) * A, wh = (H / 6.f) * 4.f * sa, w1 = H / 6.f;
+          Sv = make_float4(A, fmaf(w0, kq0.y, fmaf(wh, kh.y, w1 * kq1.y)),
+                           fmaf(w0, kq0.z, fmaf(wh, kh.z, w1 * kq1.z)),
+                           fmaf(w0, kq0.w, fmaf(wh, kh.w, w1 * kq1.w)));
+        }
+        kmax = H * fmaxf(fmaxf(kq0.x, kh.x), kq1.x);
+      }
+      if (depth < I.max_depth && kmax > I.c_rk) {
+        ++depth;
+        idx <<= 1;
+        continue;
+      }
+      const float4 accn = seg_combine(Sv, acc);
+      const float Tm = Tn * (Aseg / accn.x);
+      const float4 Gm = seg_combine(acc, G);
+      const float4 yb = step_adjoint(Tm, Gm, Ib, ab, I.bg);
+      if (I.method == 2)
+        gauss2_step_bwd(S, tf, ta, tb, H, g0, g1, Sv, yb, tg);
+      else
+        simpson_step_bwd(S, tf, I.method == 4, t0, dtau, H, kq0, kh, kq1, A, sa, yb, tg);
+      acc = accn;
+      kq0 = kq1;
+      ++idx;
+      while (depth > 0 && !(idx & 1u)) {
+        idx >>= 1;
+        --depth;
+      }
+      if (depth == 0) break;
+    }
+    return;
+  }
   for (;;) {
     const float dtau = ldexpf(1.f, -depth);
     const float t0 = (float)idx * dtau;

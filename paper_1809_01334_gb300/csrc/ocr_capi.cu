@@ -1194,7 +1194,6 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
                         float *d_grad_tf, void *stream) {
   if (!F || !d_dL_drgba || !d_grad_nodal || !d_grad_tf) return OCR_ERR_INVALID;
   if (!F->has_data || !F->has_cam || !F->has_integ) return OCR_ERR_STATE;
-  if (F->integ.method != OCR_RK4 && F->integ.method != OCR_DOPRI5) return OCR_ERR_UNSUPPORTED;
   if (F->integ.surface) return OCR_ERR_UNSUPPORTED;
   if ((uintptr_t)d_dL_drgba & 15) return OCR_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;

@@ -22,7 +22,10 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
-@pytest.mark.parametrize("integ", [{"method": "rk4", "nsteps": 4}, DOPRI])
+@pytest.mark.parametrize("integ", [{"method": "rk4", "nsteps": 4}, DOPRI,
+                                   {"method": "gauss2", "c_rk": 0.05, "max_depth": 16},
+                                   {"method": "simpson", "c_rk": 0.2, "max_depth": 16},
+                                   {"method": "equilibrium", "c_rk": 0.2, "max_depth": 16}])
 def test_shell_gradient_matches_oracle(integ):
     from paper_1809_01334_gb300 import Renderer
     f, tf, _ = I.preset_shell_small()
@@ -39,7 +42,7 @@ def test_shell_gradient_matches_oracle(integ):
     en = _rel(gn.cpu().numpy().astype(np.float64), rn)
     et = _rel(gt.cpu().numpy().astype(np.float64), rt)
     assert en <= 1e-3 and et <= 1e-3, (en, et)
-    adaptive = integ["method"] == "dopri5"
+    adaptive = integ["method"] != "rk4"  # Algorithm 1: step trees in FP32 and FP64
     gradcheck.check(gn.cpu().numpy(), rn, "nodal", None if adaptive else an, max_frac=1e-3,
                     abs_frac=1e-3 if adaptive else 1e-4)
     gradcheck.check(gt.cpu().numpy(), rt, "knots", None if adaptive else at, max_frac=0.1,
