@@ -105,14 +105,15 @@ typedef struct {
  * kappa_near) / 6) and B = I_mid (1 - A), split by the c_rk test of
  * Algorithm 1.  bg is the background intensity I_b per channel.
  *
- * surface != 0 (cube forests; Sec. 2.8): the isosurface s = s_iso of the
+ * surface != 0 (Sec. 2.8, both geometries): the isosurface s = s_iso of the
  * field is rendered as a surface of transparency a_s (in [0, 1]) and
  * intensity i_s.  Where the field along a segment changes sign against s_iso
  * between two of 9 equally spaced samples (far end to near end), the crossing
  * is located by bisection, the segment is cut there and the surface segment
  * A = a_s^(1 / cos phi), B = i_s (1 - A) (Eqs. 2.18 and 2.35; phi the angle
- * between the ray and the field gradient) goes between the two pieces.
- * OCR_ERR_UNSUPPORTED for shell forests; the adjoint does not support it. */
+ * between the ray and the field gradient; on the shell the gradient goes
+ * through the inverse map) goes between the two pieces.  The adjoint does not
+ * support it (OCR_ERR_UNSUPPORTED). */
 typedef struct {
   int method;
   int nsteps;

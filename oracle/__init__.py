@@ -117,6 +117,7 @@ def lib():
                                        C.c_int, d, P(C.c_int32), P(C.c_int32), P(C.c_uint8),
                                        C.c_double, C.c_double, C.c_int, P(C.c_int64), C.c_int]
         _lib.orc_render_ex.restype = C.c_int64
+        _lib.orc_field_probe.argtypes = [P(Forest_), C.c_int, d, d, C.c_double, C.c_double, d, d]
         _lib.orc_render_grad.argtypes = [P(Forest_), P(Camera_), P(Integrator_), d, d, d, C.c_int,
                                          C.c_int, P(C.c_uint8), C.c_double, d, d]
         _lib.orc_render_grad.restype = C.c_int
@@ -272,6 +273,15 @@ def ray_leaf_intervals(of: OracleForest, leaf, org, d, amin, amax, band_rel: flo
                                _ptr(a, C.c_double), _ptr(b, C.c_double), float(band_rel),
                                C.byref(tie))
     return [(float(a[k]), float(b[k])) for k in range(n)], bool(tie.value)
+
+
+def field_probe(of: OracleForest, leaf, org, d, a_out, x):
+    """Field value and its spatial gradient at alpha = a_out - x / |d| in the leaf."""
+    s, g = C.c_double(0.0), np.zeros(3)
+    lib().orc_field_probe(C.byref(of.s), int(leaf), _ptr(np.ascontiguousarray(org, float), C.c_double),
+                          _ptr(np.ascontiguousarray(d, float), C.c_double), float(a_out), float(x),
+                          C.byref(s), _ptr(g, C.c_double))
+    return float(s.value), g
 
 
 def segment_ab(of: OracleForest, integ: dict, leaf, org, d, a_in, a_out):

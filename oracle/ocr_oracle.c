@@ -905,10 +905,41 @@ static void volume_piece(const seg_ctx *S, const orc_integrator *I, double x1, d
   }
 }
 
-/* Trilinear gradient of the field in space at distance x from the far end. */
+/* Gradient of the field in space at distance x from the far end: the
+ * derivatives of the interpolant in the leaf's local coordinates times the
+ * derivatives of those coordinates in space (cube: 1/h; shell: through the
+ * inverse map, xi = atan2(x.e1, x.n) 2/pi + 1/2 (eta with e2) and
+ * zeta = (|x| - r0) / (r1 - r0), divided by h). */
 static void field_grad(const seg_ctx *S, double x, double *g) {
   double u[3], d[3] = {0.0, 0.0, 0.0};
   local_coords(S, x, u);
+  if (S->F->geometry == 1) {
+    double l[3][3], dl[3][3];
+    for (int a = 0; a < 3; ++a) {
+      quad_basis(u[a], l[a]);
+      dl[a][0] = 4.0 * u[a] - 3.0; /* derivatives of the degree-2 Lagrange basis */
+      dl[a][1] = 4.0 - 8.0 * u[a];
+      dl[a][2] = 4.0 * u[a] - 1.0;
+    }
+    for (int c = 0; c < 27; ++c) {
+      int i = c % 3, j = (c / 3) % 3, k = c / 9;
+      double v = (double)S->nodal[c];
+      d[0] += v * dl[0][i] * l[1][j] * l[2][k];
+      d[1] += v * l[0][i] * dl[1][j] * l[2][k];
+      d[2] += v * l[0][i] * l[1][j] * dl[2][k];
+    }
+    double alpha = S->a_out - x / S->rlen, p[3];
+    for (int a = 0; a < 3; ++a) p[a] = S->org[a] + alpha * S->dir[a];
+    const double(*fr)[3] = S->F->frames[S->tree];
+    double z = dot3(p, fr[0]), y1 = dot3(p, fr[1]), y2 = dot3(p, fr[2]), r = sqrt(dot3(p, p));
+    double k_ang = 2.0 / ORC_PI / S->h, k_rad = 1.0 / ((S->F->r1 - S->F->r0) * S->h);
+    for (int a = 0; a < 3; ++a) {
+      double dxi = (z * fr[1][a] - y1 * fr[0][a]) / (y1 * y1 + z * z);
+      double deta = (z * fr[2][a] - y2 * fr[0][a]) / (y2 * y2 + z * z);
+      g[a] = d[0] * k_ang * dxi + d[1] * k_ang * deta + d[2] * k_rad * p[a] / r;
+    }
+    return;
+  }
   for (int c = 0; c < 8; ++c) {
     double w[3], dw[3];
     for (int a = 0; a < 3; ++a) {
@@ -967,6 +998,16 @@ static void iso_segment(const seg_ctx *S, const orc_integrator *I, double x, dou
   for (int c = 0; c < 3; ++c) seg4[1 + c] = I->i_s[c] * (1.0 - A);
 }
 
+void orc_field_probe(const orc_forest *F, int leaf, const double *org, const double *dir,
+                     double a_out, double x, double *s, double *grad) {
+  seg_ctx S;
+  seg_init(&S, F, leaf, org, dir, a_out);
+  double u[3];
+  local_coords(&S, x, u);
+  *s = field_at(&S, u);
+  field_grad(&S, x, grad);
+}
+
 static void segment_value(const orc_forest *F, const orc_integrator *I, int leaf,
                           const double *org, const double *dir, double a_in, double a_out,
                           double *seg4, int64_t *nsteps, int *ncross, double band, int *tie) {
@@ -975,7 +1016,7 @@ static void segment_value(const orc_forest *F, const orc_integrator *I, int leaf
   double dx = S.rlen * (a_out - a_in);
   int64_t dummy = 0;
   if (!nsteps) nsteps = &dummy;
-  if (!I->surface || F->geometry != 0) {
+  if (!I->surface) {
     volume_piece(&S, I, 0.0, dx, seg4, nsteps);
     return;
   }

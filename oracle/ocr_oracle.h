@@ -69,7 +69,8 @@ typedef struct {
    * segment A_phi = a_s^(1 / cos phi), B_phi = i_s (1 - A_phi) (Eqs. 2.18,
    * 2.35) inserted, phi the angle between the ray and the field gradient.
    * Crossings are the sign changes of s - s_iso between 9 equally spaced
-   * samples of the segment (far end to near end), located by bisection. */
+   * samples of the segment (far end to near end), located by bisection.
+   * Both geometries (the shell's gradient through its inverse map). */
   int surface;
   double s_iso, a_s, i_s[3];
 } orc_integrator;
@@ -145,6 +146,12 @@ void orc_shell_inverse(const orc_forest *F, int tree, const double *x, double *r
 
 /* Degree-2 Lagrange interpolation on the nodes {0, 1/2, 1}^3. */
 double orc_triquadratic(const float *nodal27, double u, double v, double w);
+
+/* The field s and its gradient in space at the point of the ray o + alpha r
+ * inside the leaf with alpha = a_out - x / |r| (the surfaces' normal,
+ * Sec. 2.8). */
+void orc_field_probe(const orc_forest *F, int leaf, const double *org, const double *dir,
+                     double a_out, double x, double *s, double *grad);
 
 /* (A, B) of the segment [a_in, a_out] of the ray inside the leaf. */
 void orc_segment_ab(const orc_forest *F, const orc_integrator *I, int leaf,

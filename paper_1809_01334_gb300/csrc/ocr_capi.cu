@@ -730,7 +730,6 @@ int ocr_set_integrator(ocr_forest *F, const ocr_integrator *I) {
     return OCR_ERR_UNSUPPORTED;
   }
   if (I->surface) {
-    if (F->geometry != OCR_GEOM_CUBE) return OCR_ERR_UNSUPPORTED;
     if (!(I->a_s >= 0.f && I->a_s <= 1.f) || !std::isfinite(I->s_iso)) return OCR_ERR_INVALID;
   }
   F->integ.method = I->method;

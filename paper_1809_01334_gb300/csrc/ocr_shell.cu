@@ -355,6 +355,7 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+template <bool SURF>
 __global__ void __launch_bounds__(256, 2)
     shell_rays_kernel(const int4 *__restrict__ geo, int N, Shell S, Field Fd, Cam c, Integ I,
                                   const long long *__restrict__ ray_off, long long npix,
@@ -401,7 +402,7 @@ __global__ void __launch_bounds__(256, 2)
     float3 org, dir;
     pixel_ray(c, i, j, org, dir);
     const float rl = sqrtf(fmaf(dir.x, dir.x, fmaf(dir.y, dir.y, dir.z * dir.z)));
-    errs += shell_ray_values(geo, N, S, Fd.nodal, c, I, tf, key, n, org, dir, rl, val, iv,
+    errs += shell_ray_values<SURF>(geo, N, S, Fd.nodal, c, I, tf, key, n, org, dir, rl, val, iv,
                              lane, steps);
     segs += n;
     __syncwarp();
@@ -542,8 +543,11 @@ cudaError_t shell_rays_prepare() {
     most = most > shell_ray_smem(cap, 0) ? most : shell_ray_smem(cap, 0);
     most_sort = most_sort > sort_smem(cap) ? most_sort : sort_smem(cap);
   }
-  cudaError_t e = cudaFuncSetAttribute(shell_rays_kernel,
+  cudaError_t e = cudaFuncSetAttribute(shell_rays_kernel<false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(shell_rays_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)most);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(shell_sort_lists_kernel,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most_sort);
@@ -570,8 +574,13 @@ cudaError_t shell_rays(const int4 *geo, int N, const Shell &S, const Field &Fd, 
   const int warps = shell_ray_warps(cap, want_warps);
   const long long need = (npix + warps - 1) / warps;
   const long long grid = need < (long long)nsm * 8 ? need : (long long)nsm * 8;
-  shell_rays_kernel<<<(unsigned)(grid > 0 ? grid : 1), warps * 32, smem, st>>>(
-      geo, N, S, Fd, C, I, ray_off, npix, keys, key_cap, cap, rgba, counts, stats);
+  const unsigned g = (unsigned)(grid > 0 ? grid : 1);
+  if (I.surface)  // the isosurface of Sec. 2.8: a separate instantiation
+    shell_rays_kernel<true><<<g, warps * 32, smem, st>>>(geo, N, S, Fd, C, I, ray_off, npix, keys,
+                                                         key_cap, cap, rgba, counts, stats);
+  else
+    shell_rays_kernel<false><<<g, warps * 32, smem, st>>>(geo, N, S, Fd, C, I, ray_off, npix,
+                                                          keys, key_cap, cap, rgba, counts, stats);
   return cudaGetLastError();
 }
 

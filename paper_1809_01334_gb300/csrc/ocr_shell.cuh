@@ -213,6 +213,97 @@ __device__ __forceinline__ float4 medium(const ShellSeg &g, const TF &tf, float 
   return tf_lookup(tf, shell_field(g, tau, u, v, w));
 }
 
+// ------------------------------------------------------------ surfaces --
+// The piece [ta, ta + L] of a segment's parameter, rescaled to [0, 1].
+struct ShellSub {
+  const ShellSeg *g;
+  float ta, L;
+};
+
+__device__ __forceinline__ float4 medium(const ShellSub &s, const TF &tf, float tau) {
+  return medium(*s.g, tf, fmaf(tau, s.L, s.ta));
+}
+
+// cos phi between the segment and the field's gradient at tau (Sec. 2.8, the
+// surface normal of Eq. 2.35).  In the tree frame (components along n, e1,
+// e2, where p = (pn, p1, p2)): the local coordinates change with p as
+//   du/dp = ka (-p1, pn, 0) / (pn^2 + p1^2),  dv/dp = ka (-p2, 0, pn) / (pn^2 + p2^2),
+//   dw/dp = kr p / |p|,
+// and the polynomial's derivatives in (u, v, w) come from its monomial form.
+// The frame is orthonormal, so the angle is the one in space.
+__device__ __forceinline__ float shell_cos_phi(const ShellSeg &g, float tau) {
+  float u, v, w;
+  shell_field(g, tau, u, v, w);
+  float Q[3], Qu[3], Qv[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float R[3], Ru[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float *c = g.cf + 9 * k + 3 * j;
+      R[j] = fmaf(fmaf(c[2], u, c[1]), u, c[0]);
+      Ru[j] = fmaf(2.f * c[2], u, c[1]);
+    }
+    Q[k] = fmaf(fmaf(R[2], v, R[1]), v, R[0]);
+    Qu[k] = fmaf(fmaf(Ru[2], v, Ru[1]), v, Ru[0]);
+    Qv[k] = fmaf(2.f * R[2], v, R[1]);
+  }
+  const float Pu = fmaf(fmaf(Qu[2], w, Qu[1]), w, Qu[0]);
+  const float Pv = fmaf(fmaf(Qv[2], w, Qv[1]), w, Qv[0]);
+  const float Pw = fmaf(2.f * Q[2], w, Q[1]);
+  const float pn = fmaf(tau, g.dp[0], g.pf[0]), p1 = fmaf(tau, g.dp[1], g.pf[1]),
+              p2 = fmaf(tau, g.dp[2], g.pf[2]);
+  const float a = Pu * g.ka / fmaf(pn, pn, p1 * p1), b = Pv * g.ka / fmaf(pn, pn, p2 * p2);
+  const float c = Pw * g.kr / sqrtf(fmaf(pn, pn, fmaf(p1, p1, p2 * p2)));
+  const float gx = fmaf(-a, p1, fmaf(-b, p2, c * pn)), gy = fmaf(a, pn, c * p1),
+              gz = fmaf(b, pn, c * p2);
+  const float gn2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+  const float dn2 = fmaf(g.dp[0], g.dp[0], fmaf(g.dp[1], g.dp[1], g.dp[2] * g.dp[2]));
+  const float dot = fmaf(gx, g.dp[0], fmaf(gy, g.dp[1], gz * g.dp[2]));
+  return gn2 > 0.f && dn2 > 0.f ? fabsf(dot) / sqrtf(gn2 * dn2) : 1.f;
+}
+
+// Sec. 2.8 on the isosurface s = s_iso of a shell segment, as for the cube:
+// sign changes of s - s_iso between 9 equally spaced samples (far end to near
+// end), each located by 24 bisection steps; the segment is cut there and the
+// surface segment A = a_s^(1 / cos phi), B = i_s (1 - A) (Eqs. 2.18, 2.35)
+// goes between the pieces.
+__device__ float4 shell_iso_split(const ShellSeg &g, const TF &tf, float dx, const Integ &I,
+                                  int &steps) {
+  float4 acc = seg_identity();
+  float t1 = 0.f, u, v, w;
+  float gp = shell_field(g, 0.f, u, v, w) - I.s_iso;
+  for (int k = 0; k < 8; ++k) {
+    const float tk1 = (float)(k + 1) * 0.125f;
+    const float gn = shell_field(g, tk1, u, v, w) - I.s_iso;
+    if ((gp < 0.f && gn > 0.f) || (gp > 0.f && gn < 0.f)) {
+      float lo = (float)k * 0.125f, hi = tk1, glo = gp;
+      for (int it = 0; it < 24; ++it) {
+        const float mid = 0.5f * (lo + hi), gm = shell_field(g, mid, u, v, w) - I.s_iso;
+        if ((gm < 0.f) == (glo < 0.f)) {
+          lo = mid;
+          glo = gm;
+        } else {
+          hi = mid;
+        }
+      }
+      const float tc = 0.5f * (lo + hi);
+      acc = seg_combine(integrate_segment(ShellSub{&g, t1, tc - t1}, tf, dx * (tc - t1), I, steps),
+                        acc);
+      const float cphi = shell_cos_phi(g, tc);
+      const float A = I.a_s >= 1.f ? 1.f
+                      : (I.a_s <= 0.f || cphi <= 0.f) ? 0.f
+                                                      : exp2f(log2f(I.a_s) / cphi);
+      const float om = 1.f - A;
+      acc = seg_combine(make_float4(A, I.i_s[0] * om, I.i_s[1] * om, I.i_s[2] * om), acc);
+      t1 = tc;
+    }
+    gp = gn;
+  }
+  return seg_combine(integrate_segment(ShellSub{&g, t1, 1.f - t1}, tf, dx * (1.f - t1), I, steps),
+                     acc);
+}
+
 // The segment of the ray inside one leaf (the piece-th of its intervals):
 // its field (coef: the monomial coefficients of every leaf), its world length,
 // and the interval itself.  Returns false if the
@@ -256,6 +347,8 @@ __device__ __forceinline__ bool shell_segment(const Shell &S, const float *__res
 // a time and takes the ray's next segment as soon as it is done, so the lanes
 // stay busy while some of them bisect.  Returns this lane's count of entries
 // that are not a segment of the ray (unwritten entries, missing pieces).
+// SURF: the isosurface of Sec. 2.8 is rendered inside the segments.
+template <bool SURF = false>
 __device__ __forceinline__ int shell_ray_values(const int4 *__restrict__ geo, int N,
                                                 const Shell &S, const float *__restrict__ nodal,
                                                 const Cam &c, const Integ &I, const TF &tf,
@@ -263,7 +356,7 @@ __device__ __forceinline__ int shell_ray_values(const int4 *__restrict__ geo, in
                                                 float3 org, float3 dir, float rl, float4 *val,
                                                 float2 *iv, int lane, int &steps) {
   int errs = 0;
-  if (I.method == 1) {
+  if (I.method == 1 && !SURF) {
     int next = 0, k = 0, depth = 0;
     unsigned idx = 0;
     bool busy = false;
@@ -316,7 +409,7 @@ __device__ __forceinline__ int shell_ray_values(const int4 *__restrict__ geo, in
         if (iv) iv[k] = make_float2(0.f, 0.f);
         continue;
       }
-      val[k] = integrate_segment(g, tf, dx, I, steps);
+      val[k] = SURF ? shell_iso_split(g, tf, dx, I, steps) : integrate_segment(g, tf, dx, I, steps);
       if (iv) iv[k] = ivk;
     }
   }

@@ -350,3 +350,91 @@ def test_shell_gradient_matches_central_differences(part, integ):
         assert abs(g[k] - fd) <= 2e-5 * abs(fd) + 1e-6 * scale, (part, k, g[k], fd)
         checked += 1
     assert checked >= (24 if part == "knots" else 20)  # the rest changed the step tree
+
+
+# ------------------------------------------------------------------ surfaces --
+def _radial_shell(level):
+    """A uniform shell whose nodal values are the normalised radius zeta
+    (exactly representable by the degree-2 data): the isosurfaces of the
+    field are the spheres |x| = r0 + zeta (r1 - r0)."""
+    f, tf = _shell(level, level)
+    r0, r1 = f.meta["r0"], f.meta["r1"]
+    L = f.max_level
+    for k in range(f.nleaves):
+        z0 = f.anchor[k, 2] * 2.0 ** -L
+        h = 2.0 ** -int(f.level[k])
+        for c in range(27):
+            f.nodal[k, c] = np.float32(z0 + h * (c // 9) / 2.0)
+    return f, tf, r0, r1
+
+
+def test_shell_field_gradient_matches_central_differences():
+    """The field's spatial gradient (the surface normal of Sec. 2.8) through
+    the inverse map and the degree-2 basis, against central differences of
+    the field in space at points inside leaves of a noise-field shell."""
+    f, tf = _shell(1, 2)
+    of = O.OracleForest(f, tf)
+    rng = np.random.default_rng(4)
+    checked = 0
+    for _ in range(200):
+        leaf = int(rng.integers(f.nleaves))
+        L = f.max_level
+        h = 2.0 ** -int(f.level[leaf])
+        ref = f.anchor[leaf] * 2.0 ** -L + h * rng.uniform(0.2, 0.8, 3)
+        x = np.asarray(O.shell_map(of, int(f.tree[leaf]), ref))
+        d = np.array([0.3, -0.2, 0.9])
+        s, g = O.field_probe(of, leaf, x, d, 0.0, 0.0)
+        fd = np.zeros(3)
+        e = 1e-6
+        for a in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[a] += e
+            xm[a] -= e
+            fd[a] = (O.field_probe(of, leaf, xp, d, 0.0, 0.0)[0] -
+                     O.field_probe(of, leaf, xm, d, 0.0, 0.0)[0]) / (2 * e)
+        assert np.abs(g - fd).max() <= 1e-6 * max(1.0, np.abs(fd).max()), (leaf, g, fd)
+        checked += 1
+    assert checked == 200
+
+
+def test_shell_isosurface_segment_closed_form():
+    """Sec. 2.8 on the shell: with the field equal to the normalised radius
+    and a constant medium, a ray through one leaf that crosses the sphere
+    |x| = R_iso (s_iso = 1/2) gives near volume (+) surface (+) far volume in
+    closed form: each volume piece exp(-kappa L), q (1 - A) / kappa over its
+    chord, the surface A = a_s^(1/cos phi), B = i_s (1 - A) with phi the angle
+    between the ray and the radial normal at the crossing (Eqs. 2.18, 2.35)."""
+    f, tf, r0, r1 = _radial_shell(0)
+    kap, q = 2.5, np.array([0.3, 0.6, 0.9], np.float32).astype(float)  # the knots are float32
+    tf.knots[:] = np.concatenate([[kap], q])
+    tf.s_min, tf.s_max = -1.0, 2.0
+    of = O.OracleForest(f, tf)
+    integ = {"method": "dopri5", "tol": 1e-12, "c_rk": 0.05, "max_depth": 30,
+             "surface": {"s_iso": 0.5, "a_s": 0.6, "i_s": (1.0, 0.5, 0.25)}}
+    R = r0 + 0.5 * (r1 - r0)
+    org = np.array([2.0, 0.05, 0.1])
+    d = np.array([-1.0, 0.02, -0.03])  # enters tree +x through the outer sphere
+    hits = [(leaf, iv) for leaf in range(f.nleaves)
+            for iv in O.ray_leaf_intervals(of, leaf, org, d, 0.0, 1e9)[0]]
+    leaf, (a_in, a_out) = next((l, iv) for l, iv in hits
+                               if np.linalg.norm(org + iv[0] * d) > R > np.linalg.norm(org + iv[1] * d)
+                               or np.linalg.norm(org + iv[1] * d) > R > np.linalg.norm(org + iv[0] * d))
+    seg, _ = O.segment_ab(of, integ, leaf, org, d, a_in, a_out)
+    # crossing of |o + a d| = R inside [a_in, a_out]
+    b, c = org @ d / (d @ d), (org @ org - R * R) / (d @ d)
+    roots = [-b - math.sqrt(b * b - c), -b + math.sqrt(b * b - c)]
+    ac = next(a for a in roots if a_in < a < a_out)
+    xc = org + ac * d
+    cphi = abs(xc @ d) / (np.linalg.norm(xc) * np.linalg.norm(d))
+    rl = np.linalg.norm(d)
+
+    def piece(L):
+        A = math.exp(-kap * L)
+        return np.array([A, *(q * (1 - A) / kap)])
+
+    def comb(n, fa):  # Eq. 2.14, n nearer
+        return np.array([n[0] * fa[0], *(n[1:] + n[0] * fa[1:])])
+    As = 0.6 ** (1.0 / cphi)
+    surf = np.array([As, *(np.array([1.0, 0.5, 0.25]) * (1 - As))])
+    exp = comb(piece((ac - a_in) * rl), comb(surf, piece((a_out - ac) * rl)))
+    np.testing.assert_allclose(seg, exp, rtol=1e-9, atol=1e-12)
