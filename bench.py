@@ -444,9 +444,11 @@ def main():
     if args.only_shell:
         dev = torch.device("cuda", local)
         flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-        c3, c5 = run_shell(args, dev, flush)
+        with ClockSampler(local) as clk:
+            c3, c5 = run_shell(args, dev, flush)
         if rank == 0:
-            print(json.dumps({"shell_render": c3, "shell_backward": c5}), flush=True)
+            print(json.dumps({"shell_render": c3, "shell_backward": c5,
+                              "fp32_peak": args.fp32_peak, "clocks": clk.summary()}), flush=True)
         return
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
