@@ -31,12 +31,15 @@ UNIT = "segments/s"
 WORKLOAD = ("adaptive unit cube, levels 2-8 (2,053,451 leaves, 2:1 balanced, trilinear FP32), "
             "perspective 45deg 1920x1080, DOPRI5 tol 1e-6, c_RK 0.5")
 # Algorithmic FP32 operations (FADD/FMUL/FFMA/FMNMX, one each) of the render
-# path, counted from the kernel source: per (leaf, ray) slab test, per segment
-# set-up (slab interval, reference coordinates, the field's cubic along the
-# segment, the first medium evaluation) and per Dormand-Prince step (five
-# medium evaluations, seven stages on (A, B_r, B_g, B_b), the embedded error,
-# the split test and the Eq. 2.14 fold).
-FP32_OPS_SLAB = 30
+# path, counted from the kernel source: per (node, ray) visit of the subtree
+# descent (the node's corner, per axis its three faces, their crossings and
+# the two halves' min / max, then the 8 children's max / min chains sharing
+# their x and y prefixes), per segment set-up
+# (slab interval, reference coordinates, the field's cubic along the segment,
+# the first medium evaluation) and per Dormand-Prince step (five medium
+# evaluations, seven stages on (A, B_r, B_g, B_b), the embedded error, the
+# split test and the Eq. 2.14 fold).
+FP32_OPS_VISIT = 67
 FP32_OPS_SEGMENT = 128
 FP32_OPS_DOPRI_STEP = 234
 # The same for the shell's per-ray kernel: per segment the ray / leaf
@@ -540,7 +543,7 @@ def main():
         sm = sum(sub_ms) / len(sub_ms)
         # the dominant kernel is the subtree pass: FP32-ALU bound (its DRAM
         # traffic is a few percent of peak); peak = SMs x FP32 lanes x clock
-        ops = (FP32_OPS_SLAB * st0["subtree_leaf_tests"] +
+        ops = (FP32_OPS_VISIT * st0["subtree_node_visits"] +
                FP32_OPS_SEGMENT * st0["subtree_segments"] +
                FP32_OPS_DOPRI_STEP * st0["subtree_rk_steps"])
         nsm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -556,7 +559,8 @@ def main():
                        WORKLOAD.replace("1920x1080", f"{w}x{h}"),
                        "image": [cam.w, cam.h], "leaves": forest.nleaves,
                        "segments_per_step": segments, "rk_steps_per_step": st0["rk_steps"],
-                       "slots_per_step": st0["slots"], "leaf_tests_per_step": st0["leaf_tests"],
+                       "slots_per_step": st0["slots"], "slab_tests_per_step": st0["leaf_tests"],
+                       "subtree_node_visits_per_step": st0["subtree_node_visits"],
                        "mpixel_per_s": world * cam.w * cam.h / (ms_max * 1e-3) / 1e6,
                        "l2": "flushed (512 MB write) before every timed step",
                        "parallelism": f"replicas x{world}"},

@@ -141,11 +141,13 @@ typedef struct {
   int64_t visible_leaves; /* (camera, leaf) pairs that survived pruning */
   int64_t segments;       /* ray segments integrated (sum of d_counts) */
   int64_t rk_steps;       /* Runge-Kutta steps taken over all segments */
-  int64_t leaf_tests;     /* (leaf, ray) slab tests performed */
+  int64_t leaf_tests;     /* (cell, ray) slab tests performed: 8 per subtree node visit
+                             plus the coarsening passes' (leaf, ray) tests */
   int64_t slots;          /* (node, ray) aggregates formed while merging */
   int64_t subtree_segments; /* segments integrated by the subtree pass */
   int64_t subtree_rk_steps; /* RK steps taken by the subtree pass */
-  int64_t subtree_leaf_tests; /* (leaf, ray) slab tests of the subtree pass */
+  int64_t subtree_node_visits; /* (internal node, ray) visits of the subtree pass, each
+                                  testing the node's 8 children */
   int64_t launches;       /* kernels launched by this call */
   float ms_prune;         /* cube: pruning, rectangle unions, slot layout, host readback;
                              shell: the monomial form, pruning, the per-ray lists */

@@ -48,7 +48,7 @@ class Stats(C.Structure):
                 ("visible_leaves", C.c_int64), ("segments", C.c_int64), ("rk_steps", C.c_int64),
                 ("leaf_tests", C.c_int64), ("slots", C.c_int64),
                 ("subtree_segments", C.c_int64), ("subtree_rk_steps", C.c_int64),
-                ("subtree_leaf_tests", C.c_int64),
+                ("subtree_node_visits", C.c_int64),
                 ("launches", C.c_int64), ("ms_prune", C.c_float), ("ms_merge", C.c_float),
                 ("ms_subtree", C.c_float)]
 
@@ -183,7 +183,7 @@ def render(h, d_rgba, stream=None, d_counts=None, d_visible=None, d_rects=None,
     return {"visible_leaves": s.visible_leaves, "segments": s.segments, "rk_steps": s.rk_steps,
             "leaf_tests": s.leaf_tests, "slots": s.slots,
             "subtree_segments": s.subtree_segments, "subtree_rk_steps": s.subtree_rk_steps,
-            "subtree_leaf_tests": s.subtree_leaf_tests,
+            "subtree_node_visits": s.subtree_node_visits,
             "launches": s.launches, "ms_prune": s.ms_prune, "ms_merge": s.ms_merge,
             "ms_subtree": s.ms_subtree}
 

@@ -1068,16 +1068,17 @@ int render_plans(ocr_forest *F, int first, int K, float *d_rgba, void *stream,
       memcpy(h, F->h_group_slots + G, sizeof(h));
       stats->segments = (int64_t)(h[kStatSegments] + h[kStatCoarse + kStatSegments]);
       stats->rk_steps = (int64_t)(h[kStatSteps] + h[kStatCoarse + kStatSteps]);
-      stats->leaf_tests = (int64_t)(h[kStatTests] + h[kStatCoarse + kStatTests]);
+      stats->leaf_tests = (int64_t)(8 * h[kStatTests] + h[kStatCoarse + kStatTests]);
       stats->slots = (int64_t)(h[kStatSlots] + h[kStatCoarse + kStatSlots]);
       stats->subtree_segments = (int64_t)h[kStatSegments];
       stats->subtree_rk_steps = (int64_t)h[kStatSteps];
-      stats->subtree_leaf_tests = (int64_t)h[kStatTests];
+      stats->subtree_node_visits = (int64_t)h[kStatTests];
       stats->visible_leaves = (int64_t)h[kStatVisible];
       if (F->geometry == OCR_GEOM_SHELL) {  // two passes over every (leaf, pixel) pair
         int64_t pairs = 0;
         for (int k = 0; k < K; ++k) pairs += 2 * plans[k].npairs;
-        stats->leaf_tests = stats->subtree_leaf_tests = pairs;
+        stats->leaf_tests = pairs;
+        stats->subtree_node_visits = 0;
         stats->slots = 0;
       }
       if (h[kStatErrors]) return OCR_ERR_DEVICE;

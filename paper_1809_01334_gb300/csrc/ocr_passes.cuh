@@ -34,76 +34,131 @@ __device__ __forceinline__ V ldw(const V *p) {
   else return *p;
 }
 
-// Node and pixel of a slot of the non-final passes.  The CTA's chunk of slots
-// lies in the nodes [chunk_node[chunk], chunk_node[chunk + 1]].
-template <bool COH>
+// Node, its box and the pixel of a slot of the non-final passes.  The CTA's
+// chunk of slots lies in the nodes [chunk_node[chunk], chunk_node[chunk + 1]];
+// the first of them holds most of the chunk, so its offsets, rectangle and
+// box are loaded at once and the search runs only for the slots past its end.
 __device__ __forceinline__ void slot_lookup(const Topo &T, const Scratch &S, int nb, int ne,
                                             long long chunk, long long slot, int &node, int &i,
-                                            int &j) {
-  const long long nch = (S.off[T.M] + kChunk - 1) / kChunk;
-  int lo = max(S.chunk_node[chunk], nb);
-  int hi = (chunk + 1 < nch) ? min(S.chunk_node[chunk + 1], ne - 1) + 1 : ne;
-  while (lo < hi) {  // first node whose offset exceeds the slot
-    const int mid = (lo + hi) >> 1;
-    if (S.off[mid] <= slot) lo = mid + 1; else hi = mid;
+                                            int &j, int4 &geo) {
+  node = max(S.chunk_node[chunk], nb);
+  long long o0 = S.off[node];
+  const long long o1 = S.off[node + 1];
+  int4 r = S.rect[T.N + node];
+  geo = __ldg(T.geo + T.N + node);
+  if (slot >= o1) {
+    const long long nch = (S.off[T.M] + kChunk - 1) / kChunk;
+    int lo = node + 1;
+    int hi = (chunk + 1 < nch) ? min(S.chunk_node[chunk + 1], ne - 1) + 1 : ne;
+    while (lo < hi) {  // first node whose offset exceeds the slot
+      const int mid = (lo + hi) >> 1;
+      if (S.off[mid] <= slot) lo = mid + 1; else hi = mid;
+    }
+    node = lo - 1;
+    o0 = S.off[node];
+    r = S.rect[T.N + node];
+    geo = __ldg(T.geo + T.N + node);
   }
-  node = lo - 1;
-  const int4 r = S.rect[T.N + node];
-  const unsigned local = (unsigned)(slot - S.off[node]);  // < w * h < 2^31
+  const unsigned local = (unsigned)(slot - o0);  // < w * h < 2^31
   const unsigned rw = (unsigned)(r.y - r.x + 1);
   const unsigned row = local / rw;
   i = r.x + (int)(local - row * rw);
   j = r.z + (int)row;
 }
 
-__device__ __forceinline__ unsigned spread3_9(unsigned v) {  // 3 bits -> positions 0, 3, 6
-  return (v & 1u) | ((v & 2u) << 2) | ((v & 4u) << 4);
-}
-
 // Subtree pass (Sec. 3.2 + Sec. 3.3 for the deepest levels).  A CTA owns a
 // chunk of kChunk consecutive (tile-level node, ray) slots, one thread each.
-//  A. per node of the chunk, the leaves of its subtree whose pixel rectangle
-//     meets the node's rows in the chunk are compacted into a shared table
-//     (Morton order): each with its box (rectangle within those rows), its
-//     anchor relative to the node and its level.  The table's (candidate,
-//     pixel) pairs are spread evenly over the CTA by a prefix sum of the box
-//     areas; every pair whose pixel is a live ray of the candidate's node is
-//     slab-tested and a hit appended to that ray's list;
-//  B. each ray sorts its hits by their Morton key inside the tile node with
-//     every axis mirrored where the ray runs towards negative coordinates:
-//     the ray's front-to-back order for disjoint cells;
-//  C. each warp integrates the hits of its 32 rays, one hit per lane, in
-//     batches, and
-//  D. every lane folds its own ray's results nearest-first with Eq. 2.14.
+//  A. every ray descends its tile node's subtree front to back: at each
+//     internal node its box is cut by the three mid-planes, and the ray's
+//     crossings of the node's planes give the slab interval of all 8 children
+//     at once (the same rounded operands as a slab test of each child, so the
+//     same decisions); the children it meets are taken in the order of their
+//     octant index mirrored by the direction's sign bits, which is the ray's
+//     front-to-back order for the disjoint cells of an octree.  A leaf met
+//     is appended to the ray's list, an internal node is descended into.  A
+//     child box nests in its parent, and monotone rounding keeps its FP32
+//     slab interval inside the parent's, so a subtree the ray misses holds no
+//     leaf the ray meets;
+//  B. each warp integrates the hits of its 32 rays, one hit per lane, in
+//     batches; a hit whose leaf's pixel rectangle does not hold the pixel (a
+//     rounding edge case: the pair is no candidate) gives no segment, and
+//  C. every lane folds its own ray's results nearest-first with Eq. 2.14.
 constexpr int kSubtreeThreads = kChunk;  // one chunk per CTA
-constexpr int kCand = kSubtreeThreads;  // candidate table of phase A
-constexpr int kPairWin = 1024;          // (candidate, pixel) pairs resolved per window
-static_assert(kCand <= 256, "candidate indices are stored in one byte");
-static_assert(sizeof(int4) * kCand == sizeof(float4) * kChunk,
-              "phase A's candidate boxes and phase C's values share their storage");
-constexpr int kWarpBatch = 32; // hits per warp batch of phase C
+constexpr int kWarpBatch = 32;           // hits per warp batch of phase B
+static_assert(kSubtreeDepth <= 3, "the descent keeps two ancestors in registers");
 
 // Shared memory of one subtree chunk.
 struct SubtreeSmem {
   float4 tfv[8], tfs[8];
   float ray[6][kSubtreeThreads];                   // ray: varying part, reciprocal direction
-  signed char liveq[kSubtreeThreads];              // live ray: index of its node, else -1
-  int4 qinfo[kSubtreeThreads];                     // node: {rect x0, rect y0, width, off - cs}
-  int2 qlr[kSubtreeThreads];                       // node: its leaves [first, end)
-  int2 qrows[kSubtreeThreads];                     // node: its rows in the chunk
-  unsigned long long qgeo[kSubtreeThreads];        // node: anchor x | y << 21 | z << 42
-  union {
-    int4 cbox[kCand];                              // phase A: candidate rectangle within the rows
-    float4 res[kSubtreeThreads / 32][kWarpBatch];  // phase C: the warps' segment values
-  };
-  int cpre[kCand + 1];                             // candidate: pair count, then prefix
-  unsigned crel[kCand];                            // candidate: anchor in the node, level
-  int cl[kCand];                                   // candidate: (node index << 22) | leaf - base
-  unsigned char pc[kPairWin];                      // candidate of each pair in the window
-  int cnt[kSubtreeThreads];                        // hits of each ray
-  unsigned list[kMaxSubtreeHits][kSubtreeThreads]; // (mirrored key << 22) | leaf - base
-  int wcnt[kSubtreeThreads / 32], nn, leaf_base, ncand, ltot;
+  float4 res[kSubtreeThreads / 32][kWarpBatch];    // phase B: the warps' segment values
+  int2 pix[kSubtreeThreads];                       // pixel of each ray
+  int drop[kSubtreeThreads];                       // hits outside the leaf's rectangle
+  int list[kMaxSubtreeHits][kSubtreeThreads];      // hits of each ray (leaf ids), in order
 };
+
+// Child id of octant q from the node's 8 children held in two int4.
+__device__ __forceinline__ int pick_child(int4 c0, int4 c1, int q) {
+  const int4 c = (q & 4) ? c1 : c0;
+  return (q & 2) ? ((q & 1) ? c.w : c.z) : ((q & 1) ? c.y : c.x);
+}
+
+// The children of the node with low corner lo whose boxes (side hc) the ray
+// meets, as a mask over the mirrored octants (bit q ^ flip for octant
+// q = bx + 2 by + 4 bz).  Anchors are integers below 2^20 in units of 2^-L
+// (L <= 20), so every face is exact in FP32: per axis the faces lo,
+// lo + hc, lo + 2 hc are the very values a slab test of each child forms
+// (its low corner, and low corner + side rounded once), their crossings
+// (face - o) x (1/d) are formed once, and each child's interval is the same
+// max / min chain over the axes x, y, z as its own slab test (the chains
+// share their common prefixes).
+__device__ __forceinline__ unsigned child_hits(float3 o, float3 d, float3 iv, float3 lo,
+                                               float hc, float amin, float amax,
+                                               unsigned flip) {
+  const float oa[3] = {o.x, o.y, o.z}, da[3] = {d.x, d.y, d.z}, va[3] = {iv.x, iv.y, iv.z};
+  const float la[3] = {lo.x, lo.y, lo.z};
+  constexpr unsigned kHalf[3][2] = {{0x55u, 0xaau}, {0x33u, 0xccu}, {0x0fu, 0xf0u}};
+  float mn[3][2], mx[3][2];
+  unsigned ok = 0xffu;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float p0 = la[a], p1 = __fadd_rn(p0, hc), p2 = __fadd_rn(p1, hc);
+    if (da[a] == 0.f) {  // parallel: inside a half's slab or not, no bound on alpha
+      if (oa[a] < p0 || oa[a] > p1) ok &= ~kHalf[a][0];
+      if (oa[a] < p1 || oa[a] > p2) ok &= ~kHalf[a][1];
+      mn[a][0] = mn[a][1] = -INFINITY;
+      mx[a][0] = mx[a][1] = INFINITY;
+    } else {
+      const float s0 = __fmul_rn(__fsub_rn(p0, oa[a]), va[a]);
+      const float s1 = __fmul_rn(__fsub_rn(p1, oa[a]), va[a]);
+      const float s2 = __fmul_rn(__fsub_rn(p2, oa[a]), va[a]);
+      mn[a][0] = fminf(s0, s1);
+      mx[a][0] = fmaxf(s0, s1);
+      mn[a][1] = fminf(s1, s2);
+      mx[a][1] = fmaxf(s1, s2);
+    }
+  }
+  float e0[4], e1[4];  // the chains after x and y, per (bx, by)
+#pragma unroll
+  for (int x = 0; x < 2; ++x) {
+    const float f0 = fmaxf(amin, mn[0][x]), f1 = fminf(amax, mx[0][x]);
+#pragma unroll
+    for (int y = 0; y < 2; ++y) {
+      e0[x + 2 * y] = fmaxf(f0, mn[1][y]);
+      e1[x + 2 * y] = fminf(f1, mx[1][y]);
+    }
+  }
+  unsigned m = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    m |= (fminf(e1[q & 3], mx[2][q >> 2]) > fmaxf(e0[q & 3], mn[2][q >> 2]) ? 1u : 0u) << q;
+  m &= ok;
+  // octant q -> bit q ^ flip
+  if (flip & 1u) m = ((m & 0x55u) << 1) | ((m >> 1) & 0x55u);
+  if (flip & 2u) m = ((m & 0x33u) << 2) | ((m >> 2) & 0x33u);
+  if (flip & 4u) m = ((m & 0x0fu) << 4) | ((m >> 4) & 0x0fu);
+  return m;
+}
 
 // One chunk (CTA bid of the pass over the slots [s0, s1) of the nodes
 // [nb, ne)); a CTA of kSubtreeThreads threads.
@@ -113,25 +168,13 @@ __device__ __forceinline__ void subtree_chunk(const Topo &T, const Field &Fd, co
                                               long long s0, long long s1, long long bid,
                                               SubtreeSmem &sm) {
   constexpr int NT = kSubtreeThreads, NW = NT / 32;
-  static_assert(kCand == NT, "one table entry per thread in the prefix sum");
   float4(&s_tfv)[8] = sm.tfv;
   float4(&s_tfs)[8] = sm.tfs;
   float(&s_ray)[6][NT] = sm.ray;
-  signed char(&s_liveq)[NT] = sm.liveq;
-  int4(&s_qinfo)[NT] = sm.qinfo;
-  int2(&s_qlr)[NT] = sm.qlr;
-  int2(&s_qrows)[NT] = sm.qrows;
-  unsigned long long(&s_qgeo)[NT] = sm.qgeo;
-  int4(&s_cbox)[kCand] = sm.cbox;
-  int(&s_cpre)[kCand + 1] = sm.cpre;
-  unsigned(&s_crel)[kCand] = sm.crel;
-  int(&s_cl)[kCand] = sm.cl;
-  unsigned char(&s_pc)[kPairWin] = sm.pc;
-  int(&s_cnt)[NT] = sm.cnt;
-  unsigned(&s_list)[kMaxSubtreeHits][NT] = sm.list;
+  int(&s_list)[kMaxSubtreeHits][NT] = sm.list;
   float4(&s_res)[NW][kWarpBatch] = sm.res;
-  int(&s_wcnt)[NW] = sm.wcnt;
-  int &s_nn = sm.nn, &s_leaf_base = sm.leaf_base, &s_ncand = sm.ncand, &s_ltot = sm.ltot;
+  int2(&s_pix)[NT] = sm.pix;
+  int(&s_drop)[NT] = sm.drop;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid < 8) {
     const float4 v = Fd.tf[tid];
@@ -145,14 +188,14 @@ __device__ __forceinline__ void subtree_chunk(const Topo &T, const Field &Fd, co
   const long long slot = cs + tid;
   const bool active = slot >= s0 && slot < s1;
   int node = -1, i = 0, j = 0;
-  if (active) slot_lookup<COH>(T, S, nb, ne, slot / kChunk, slot, node, i, j);
+  int4 gn = make_int4(0, 0, 0, 0);
+  if (active) slot_lookup(T, S, nb, ne, slot / kChunk, slot, node, i, j, gn);
   float3 org, dir;
   pixel_ray(c, i, j, org, dir);
   const float3 inv = make_float3(recip_or_zero(dir.x), recip_or_zero(dir.y), recip_or_zero(dir.z));
   const float scale = ldexpf(1.f, -T.L);
   bool live = false;
   if (active) {
-    const int4 gn = __ldg(T.geo + T.N + node);
     float a0, a1;
     live = slab(org, dir, inv, node_lo(gn, scale), ldexpf(1.f, -gn.w), c.amin, c.amax, a0, a1);
   }
@@ -165,203 +208,89 @@ __device__ __forceinline__ void subtree_chunk(const Topo &T, const Field &Fd, co
   s_ray[3][tid] = inv.x;
   s_ray[4][tid] = inv.y;
   s_ray[5][tid] = inv.z;
-  int *s_node = s_cnt;  // node of each slot (-1 inactive) until phase A
-  s_node[tid] = active ? node : -1;
-  __syncthreads();
+  s_pix[tid] = make_int2(i, j);
+  s_drop[tid] = 0;
 
-  // distinct nodes of the chunk (a node's slots are contiguous), this slot's
-  // node index among them, and each node's layout in the chunk
-  {
-    const bool head = active && (tid == 0 || s_node[tid - 1] != node);
-    const unsigned bal = __ballot_sync(0xffffffffu, head);
-    if (lane == 0) s_wcnt[wid] = __popc(bal);
-    __syncthreads();
-    int base = 0;
-    for (int w = 0; w < wid; ++w) base += s_wcnt[w];
-    const int myq = base + __popc(bal & (0xffffffffu >> (31 - lane))) - 1;
-    if (head) {
-      const int4 rn = ldp<COH>(S.rect + T.N + node);
-      const long long off = ldp<COH>(S.off + node), off1 = ldp<COH>(S.off + node + 1);
-      const int4 gq = __ldg(T.geo + T.N + node);
-      const int2 lr = __ldg(T.leaves + node);
-      const int w = rn.y - rn.x + 1, ow = (int)(off - cs);
-      s_qinfo[myq] = make_int4(rn.x, rn.z, w, ow);
-      s_qgeo[myq] = (unsigned long long)gq.x | (unsigned long long)gq.y << 21 |
-                    (unsigned long long)gq.z << 42;
-      s_qlr[myq] = lr;
-      // the node's slots [la, lb) in the chunk, and their rows
-      const int la = max(0, -ow), lb = (int)(min(min(cs + NT, s1), off1) - off);
-      s_qrows[myq] = make_int2(rn.z + la / w, rn.z + (lb - 1) / w);
-    }
-    s_liveq[tid] = (signed char)(live ? myq : -1);
-    if (tid == NT - 1) {
-      int tot = 0;
-      for (int w = 0; w < NW; ++w) tot += s_wcnt[w];
-      s_nn = tot;
-      s_ncand = 0;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      int lt = 0;
-      for (int q = 0; q < s_nn; ++q) lt += s_qlr[q].y - s_qlr[q].x;
-      s_ltot = lt;
-      s_leaf_base = s_nn ? s_qlr[0].x : 0;
-    }
+  __syncthreads();  // the transfer function table
+
+  // A. front-to-back descent; the path's ancestors (node, children still to
+  // visit) in registers, the current anchor cleared to an ancestor's on the
+  // way up, the current node's children loaded once per visit; the leaves
+  // up to the next internal child are taken in one run
+  const unsigned flip = (dir.x < 0.f ? 1u : 0u) | (dir.y < 0.f ? 2u : 0u) | (dir.z < 0.f ? 4u : 0u);
+  int cur = node, lev = gn.w, gx = gn.x, gy = gn.y, gz = gn.z, d = 0;
+  unsigned msk = live ? child_hits(org, dir, inv, node_lo(gn, scale), ldexpf(1.f, -(lev + 1)),
+                                   c.amin, c.amax, flip)
+                      : 0u;
+  const int4 *child4 = reinterpret_cast<const int4 *>(T.child);
+  int4 c0 = make_int4(-1, -1, -1, -1), c1 = c0;
+  if (msk) {
+    c0 = __ldg(child4 + 2 * cur);
+    c1 = __ldg(child4 + 2 * cur + 1);
   }
-  __syncthreads();
-
-  // A. candidates and hits
-  unsigned ntest = 0;
-  const int nn = s_nn, leaf_base = s_leaf_base;
-  s_cnt[tid] = 0;
-  // the table's pairs: prefix of the pair counts, then one pair per thread at a time
-  auto flush = [&]() {
-    __syncthreads();
-    const int nc = s_ncand;
-    const int n0 = tid < nc ? s_cpre[tid] : 0;
-    int x = n0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) s_wcnt[wid] = x;
-    __syncthreads();
-    int base = 0, tot = 0;
-    for (int w = 0; w < NW; ++w) {
-      if (w < wid) base += s_wcnt[w];
-      tot += s_wcnt[w];
-    }
-    if (tid < nc) s_cpre[tid] = base + x - n0;
-    if (tid == 0) s_cpre[nc] = tot;
-    __syncthreads();
-    // pairs in windows of kPairWin: each candidate marks its pairs in the
-    // window with its index, then every pair finds its candidate in one load
-    const int my_pre = tid < nc ? s_cpre[tid] : 0, my_end = my_pre + n0;
-    for (int w0 = 0; w0 < tot; w0 += kPairWin) {
-      const int w1 = min(tot, w0 + kPairWin);
-      for (int p = max(my_pre, w0); p < min(my_end, w1); ++p) s_pc[p - w0] = (unsigned char)tid;
-      __syncthreads();
-    for (int pq = w0 + tid; pq < w1; pq += NT) {
-      const int lo = s_pc[pq - w0];
-      const int4 b = s_cbox[lo];
-      const int loc = pq - s_cpre[lo];
-      // row = floor(loc / width) from the rounded reciprocal: exact, as the
-      // quotient of (loc + 1/2) stays 1/(2 width) away from an integer
-      const int bw = b.y - b.x + 1;
-      const int row = (int)(((float)loc + 0.5f) * (1.f / (float)bw));
-      const int ii = b.x + loc - row * bw, jj = b.z + row;
-      const int tl = s_cl[lo];
-      const int q = tl >> 22;
-      const int4 qi = s_qinfo[q];
-      const int t = qi.w + (jj - qi.y) * qi.z + (ii - qi.x);
-      if (t < 0 || t >= NT || s_liveq[t] != q) continue;
-      ++ntest;
-      const unsigned rel = s_crel[lo];
-      const unsigned rx = rel & 255u, ry = (rel >> 8) & 255u, rz = (rel >> 16) & 255u;
-      const unsigned long long gq = s_qgeo[q];
-      const int4 g = make_int4((int)(gq & 0x1fffffu) + (int)rx, (int)((gq >> 21) & 0x1fffffu) + (int)ry,
-                               (int)(gq >> 42) + (int)rz, (int)(rel >> 24));
-      const float3 rv = make_float3(s_ray[0][t], s_ray[1][t], s_ray[2][t]);
-      const float3 ro = c.ortho ? rv : make_float3(c.o[0], c.o[1], c.o[2]);
-      const float3 rd = c.ortho ? make_float3(c.v[0], c.v[1], c.v[2]) : rv;
-      const float3 ri = make_float3(s_ray[3][t], s_ray[4][t], s_ray[5][t]);
-      float b0, b1;
-      if (!slab(ro, rd, ri, node_lo(g, scale), ldexpf(1.f, -g.w), c.amin, c.amax, b0, b1))
-        continue;
-      const unsigned key = spread3_9(rx) | (spread3_9(ry) << 1) | (spread3_9(rz) << 2);
-      const unsigned flip =
-          (rd.x < 0.f ? 0x49u : 0u) | (rd.y < 0.f ? 0x92u : 0u) | (rd.z < 0.f ? 0x124u : 0u);
-      const int k = atomicAdd(&s_cnt[t], 1);
-      if (k < kMaxSubtreeHits) s_list[k][t] = ((key ^ flip) << 22) | (unsigned)(tl & 0x3fffff);
-    }
-      __syncthreads();
-    }
-    if (tid == 0) s_ncand = 0;
-  };
-  // the candidate leaf l of node q: kept if its rectangle meets the node's
-  // columns and its rows in the chunk
-  auto candidate = [&](int q, int l, bool in_range, int &cnt) -> int4 {
-    int4 box = empty_rect();
-    cnt = 0;
-    if (in_range) {
-      const int4 qi = s_qinfo[q];
-      const int2 rows = s_qrows[q];
-      const int4 r = ldp<COH>(S.rect + l);
-      box = make_int4(max(r.x, qi.x), min(r.y, qi.x + qi.z - 1), max(r.z, rows.x), min(r.w, rows.y));
-      if (box.x <= box.y && box.z <= box.w) cnt = (box.y - box.x + 1) * (box.w - box.z + 1);
-    }
-    return box;
-  };
-  auto store = [&](int at, int q, int l, int4 box, int cnt) {
-    const unsigned long long gq = s_qgeo[q];
-    const int4 g = __ldg(T.geo + l);
-    s_cbox[at] = box;
-    s_cpre[at] = cnt;
-    s_crel[at] = (unsigned)(g.x - (int)(gq & 0x1fffffu)) |
-                 (unsigned)(g.y - (int)((gq >> 21) & 0x1fffffu)) << 8 |
-                 (unsigned)(g.z - (int)(gq >> 42)) << 16 | (unsigned)g.w << 24;
-    s_cl[at] = (q << 22) | (l - leaf_base);
-  };
-  if (s_ltot <= kCand) {
-    // all the chunk's leaves fit the table: the warps take 32-leaf blocks in
-    // turn and append their candidates without CTA barriers
-    int q = 0, b = wid;  // this warp's block: the b-th 32-leaf block of node q
-    while (q < nn) {
-      const int2 lr = s_qlr[q];
-      const int nb32 = (lr.y - lr.x + 31) >> 5;
-      if (b >= nb32) {
-        b -= nb32;
-        ++q;
-        continue;
-      }
-      const int l = lr.x + 32 * b + lane;
-      int cnt;
-      const int4 box = candidate(q, l, l < lr.y, cnt);
-      const unsigned bal = __ballot_sync(0xffffffffu, cnt > 0);
-      int base = 0;
-      if (lane == 0 && bal) base = atomicAdd(&s_ncand, __popc(bal));
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (cnt > 0) store(base + __popc(bal & ((1u << lane) - 1u)), q, l, box, cnt);
-      b += NW;
-    }
-  } else {
-    for (int q = 0; q < nn; ++q) {
-      const int2 lr = s_qlr[q];
-      for (int l0 = lr.x; l0 < lr.y; l0 += NT) {
-        __syncthreads();
-        if (s_ncand + NT > kCand) flush();
-        const int l = l0 + tid;
-        int cnt;
-        const int4 box = candidate(q, l, l < lr.y, cnt);
-        const unsigned bal = __ballot_sync(0xffffffffu, cnt > 0);
-        if (lane == 0) s_wcnt[wid] = __popc(bal);
-        __syncthreads();
-        int base = s_ncand;
-        for (int w = 0; w < wid; ++w) base += s_wcnt[w];
-        if (cnt > 0) store(base + __popc(bal & ((1u << lane) - 1u)), q, l, box, cnt);
-        __syncthreads();
-        if (tid == NT - 1) s_ncand = base + __popc(bal);
+  int an0 = 0, an1 = 0;
+  unsigned am0 = 0, am1 = 0;
+  unsigned nhit = 0, nvisit = live ? 1u : 0u;
+  bool deep = false;
+  while (true) {
+    int q = 0, id = -1;
+    while (msk) {
+      q = (__ffs(msk) - 1) ^ (int)flip;
+      msk &= msk - 1u;
+      id = pick_child(c0, c1, q);
+      if (id >= T.N) break;
+      if (id >= 0) {
+        if (nhit < (unsigned)kMaxSubtreeHits) s_list[nhit][tid] = id;
+        ++nhit;
       }
     }
+    if (id < T.N) {  // this node is done: back to its parent
+      if (d == 0) break;
+      --d;
+      --lev;
+      const int keep = ~((1 << (T.L - lev)) - 1);
+      gx &= keep;
+      gy &= keep;
+      gz &= keep;
+      cur = d == 0 ? an0 : an1;
+      msk = d == 0 ? am0 : am1;
+      if (msk) {
+        c0 = __ldg(child4 + 2 * cur);
+        c1 = __ldg(child4 + 2 * cur + 1);
+      }
+      continue;
+    }
+    if (d >= 2) {  // below the subtree depth: not a tile node's subtree
+      deep = true;
+      continue;
+    }
+    if (d == 0) {
+      an0 = cur;
+      am0 = msk;
+    } else {
+      an1 = cur;
+      am1 = msk;
+    }
+    const int hs = 1 << (T.L - lev - 1);
+    gx += (q & 1) * hs;
+    gy += ((q >> 1) & 1) * hs;
+    gz += (q >> 2) * hs;
+    ++d;
+    ++lev;
+    cur = id - T.N;
+    msk = child_hits(org, dir, inv, node_lo(make_int4(gx, gy, gz, 0), scale),
+                     ldexpf(1.f, -(lev + 1)), c.amin, c.amax, flip);
+    ++nvisit;
+    if (msk) {
+      c0 = __ldg(child4 + 2 * cur);
+      c1 = __ldg(child4 + 2 * cur + 1);
+    }
   }
-  flush();
-  __syncthreads();
-  const unsigned nhit = (unsigned)s_cnt[tid];
+  __syncwarp();  // the warp's rays and lists
 
-  // B. sort the ray's hits into its front-to-back order
+
+  // B + C. per warp: integrate the warp's hits, one per lane; fold per ray
   const int n = min((int)nhit, kMaxSubtreeHits);
-  for (int a = 1; a < n; ++a) {
-    const unsigned v = s_list[a][tid];
-    int b = a - 1;
-    while (b >= 0 && s_list[b][tid] > v) {
-      s_list[b + 1][tid] = s_list[b][tid];
-      --b;
-    }
-    s_list[b + 1][tid] = v;
-  }
-
-  // C + D. per warp: integrate the warp's hits, one per lane; fold per ray
   int pre = n;  // inclusive prefix of the hit counts over the warp's lanes
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -388,26 +317,39 @@ __device__ __forceinline__ void subtree_chunk(const Topo &T, const Field &Fd, co
       const int owpre = __shfl_sync(0xffffffffu, my0, ow);
       if (h < b1) {
         const int t = wid * 32 + ow;
-        const int leaf = leaf_base + (int)(s_list[h - owpre][t] & 0x3fffffu);
+        const int leaf = s_list[h - owpre][t];
         const float3 rv = make_float3(s_ray[0][t], s_ray[1][t], s_ray[2][t]);
         const float3 ro = c.ortho ? rv : make_float3(c.o[0], c.o[1], c.o[2]);
         const float3 rd = c.ortho ? make_float3(c.v[0], c.v[1], c.v[2]) : rv;
-        s_res[wid][h - b0] = leaf_segment<SURF>(T, Fd, c, I, tf, leaf, ro, rd,
-                                                make_float3(s_ray[3][t], s_ray[4][t], s_ray[5][t]),
-                                                scale, steps);
+        const int4 r = ldp<COH>(S.rect + leaf);
+        const int2 p = s_pix[t];
+        const bool inside = p.x >= r.x && p.x <= r.y && p.y >= r.z && p.y <= r.w;
+        int st = 0;
+        const float4 sg = leaf_segment<SURF>(T, Fd, c, I, tf, leaf, ro, rd,
+                                             make_float3(s_ray[3][t], s_ray[4][t], s_ray[5][t]),
+                                             scale, st);
+        if (inside) {
+          s_res[wid][h - b0] = sg;
+          steps += st;
+        } else {
+          s_res[wid][h - b0] = seg_identity();
+          atomicAdd(&s_drop[t], 1);
+        }
       }
     }
     __syncwarp();
     for (int h = max(my0, b0); h < min(my0 + n, b1); ++h) acc = seg_combine(acc, s_res[wid][h - b0]);
     __syncwarp();
   }
+  __syncwarp();
+  if (nhit > (unsigned)kMaxSubtreeHits || deep) atomicAdd(S.stats + kStatErrors, 1ull);
+  nhit -= (unsigned)s_drop[tid];
   if (active) {
     S.entries[slot] = acc;
-    if (nhit > (unsigned)kMaxSubtreeHits) atomicAdd(S.stats + kStatErrors, 1ull);
     if (nhit && S.counts) atomicAdd(S.counts + (size_t)j * c.w + i, (int)nhit);
   }
   // counters: one atomic per warp and counter, no CTA-wide barrier at the end
-  unsigned long long v[4] = {nhit, (unsigned long long)steps, ntest, active ? 1ull : 0ull};
+  unsigned long long v[4] = {nhit, (unsigned long long)steps, nvisit, active ? 1ull : 0ull};
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     unsigned long long x = v[q];
@@ -464,12 +406,13 @@ __device__ __forceinline__ void coarsen_chunk(const Topo &T, const Field &Fd, co
   const bool active = slot >= s0 && slot < s1;
   int node = T.M;  // super-root in the final pass
   int i = 0, j = 0;
+  int4 g = make_int4(0, 0, 0, 0);
   if (active) {
     if (FINAL) {
       i = (int)(slot % c.w);
       j = (int)(slot / c.w);
     } else {
-      slot_lookup<COH>(T, S, nb, ne, chunk, slot, node, i, j);
+      slot_lookup(T, S, nb, ne, chunk, slot, node, i, j, g);
     }
   }
   s_pix[tid] = make_int2(i, j);
@@ -487,7 +430,6 @@ __device__ __forceinline__ void coarsen_chunk(const Topo &T, const Field &Fd, co
   // identity and all child work is skipped
   bool live = active;
   if (!FINAL && active) {
-    const int4 g = __ldg(T.geo + T.N + node);
     float a0, a1;
     live = slab(org, dir, inv, node_lo(g, scale), ldexpf(1.f, -g.w), c.amin, c.amax, a0, a1);
   }
