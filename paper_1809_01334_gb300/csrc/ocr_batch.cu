@@ -39,7 +39,7 @@ struct ScanSmem {
 };
 
 union BatchSmem {
-  SubtreeSmem st;
+  SubtreeSmem st[kBT / 32];
   CoarsenSmem co;
   ScanSmem sc;
 };
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kBT, MINB)
     batch_kernel(Topo T, Field Fd, Integ I, const BatchSeg *__restrict__ seg, int nseg,
                  const BatchCam *__restrict__ cams, unsigned *ctl, long long ntickets,
                  float4 *rgba, int *counts, unsigned char *visible,
-                 unsigned long long *stats) {
+                 unsigned long long *stats, unsigned long long *counters) {
   __shared__ BatchSmem sm;
   // the current item's camera and scratch, its segment and ticket, and the
   // queue state of thread 0 (kept in shared memory, not in registers)
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kBT, MINB)
         if (cam != s_cur_cam) {  // this camera's scratch
           const BatchCam &bc = cams[cam];
           s_S = Scratch{bc.rect, bc.off, bc.entries, stats,
-                        counts ? counts + bc.pix_off : nullptr, visible, bc.chunk};
+                        counts ? counts + bc.pix_off : nullptr, visible, bc.chunk, counters};
           s_rgba = rgba + bc.pix_off;
         }
       } else {
@@ -250,14 +250,12 @@ __global__ void __launch_bounds__(kBT, MINB)
       } else if (g.kind == kBatchChunkMap) {
 #pragma unroll 1
         for (int q = 0; q < kBItems; ++q) {
-          const long long n = it * kBTile + q * kBT + tid;
-          if (n >= T.M) continue;
-          const long long a = __ldcg(S.off + n), b = __ldcg(S.off + n + 1);
-          for (long long c = (a + kChunk - 1) / kChunk; c * kChunk < b; ++c)
-            S.chunk_node[c] = (int)n;
+          const long long gi = it * kBTile + q * kBT + tid;  // a group of kGroup slots
+          if (gi < g.b) S.chunk_node[gi] = node_of_slot<true>(S.off, T.M, gi * kGroup);
         }
       } else if (g.kind == kBatchSubtree) {
-        subtree_chunk<false, true>(T, Fd, s_cam, I, S, g.nb, g.ne, g.a, g.b, it, sm.st);
+        subtree_warp<false, true>(T, Fd, s_cam, I, S, g.nb, g.ne, g.a, g.b,
+                                  (g.a / kChunk + it) * kChunk + (tid & ~31), sm.st[tid >> 5]);
       } else if (g.kind == kBatchCoarse) {
         coarsen_chunk<false, false, true>(T, Fd, s_cam, I, S, g.nb, g.ne, g.a, g.b, it, nullptr,
                                           sm.co);
@@ -280,8 +278,9 @@ __global__ void __launch_bounds__(kBT, MINB)
 cudaError_t launch_batch(const Topo &T, const Field &Fd, const Integ &I, const BatchSeg *d_seg,
                          int nseg, const BatchCam *d_cams, unsigned *d_ctl, long long ntickets,
                          float4 *rgba, int *counts, unsigned char *visible,
-                         unsigned long long *stats, int nsm, int ctas_per_sm,
+                         unsigned long long *stats, bool count, int nsm, int ctas_per_sm,
                          cudaStream_t stream) {
+  unsigned long long *counters = count ? stats : nullptr;
   if (nseg < 1 || nseg > kBatchMaxSegs || ntickets < 1) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(d_ctl, 0, sizeof(unsigned) * kBatchCtlWords, stream);
   if (e != cudaSuccess) return e;
@@ -303,13 +302,13 @@ cudaError_t launch_batch(const Topo &T, const Field &Fd, const Integ &I, const B
   const unsigned g = (unsigned)grid;
   if (v == 6)
     batch_kernel<6><<<g, kBT, 0, stream>>>(T, Fd, I, d_seg, nseg, d_cams, d_ctl, ntickets, rgba,
-                                           counts, visible, stats);
+                                           counts, visible, stats, counters);
   else if (v == 7)
     batch_kernel<7><<<g, kBT, 0, stream>>>(T, Fd, I, d_seg, nseg, d_cams, d_ctl, ntickets, rgba,
-                                           counts, visible, stats);
+                                           counts, visible, stats, counters);
   else
     batch_kernel<8><<<g, kBT, 0, stream>>>(T, Fd, I, d_seg, nseg, d_cams, d_ctl, ntickets, rgba,
-                                           counts, visible, stats);
+                                           counts, visible, stats, counters);
   return cudaGetLastError();
 }
 

@@ -31,7 +31,7 @@ struct CamPlan {
   long long *d_off = nullptr;         // [M + 1]
   long long *d_bsums = nullptr;       // [area_scan_blocks(M) + 1]
   long long *d_gslots = nullptr;      // [L + 1]
-  int *d_chunk = nullptr;             // [total / kChunk + 2]
+  int *d_chunk = nullptr;             // [total / kGroup + 2]
   float4 *d_entries = nullptr;        // [total slots]
   // shell forests: the (leaf, pixel) pair space and the per-ray segment lists
   long long npairs = 0, nhits = 0, bs_cap = 0;
@@ -818,7 +818,7 @@ int plan_cameras(ocr_forest *F) {
     OCR_CUDA(cudaStreamSynchronize(ps));
     P.gslots.assign(F->h_group_slots, F->h_group_slots + G);
     const long long total = P.gslots[G - 1];
-    if ((rc = dev_alloc(&P.d_chunk, (size_t)(total / kChunk + 2), F->bytes)) ||
+    if ((rc = dev_alloc(&P.d_chunk, (size_t)(total / kGroup + 2), F->bytes)) ||
         (rc = dev_alloc(&P.d_entries, (size_t)(total > 0 ? total : 1), F->bytes)))
       return rc;
   }
@@ -865,8 +865,11 @@ int plan_batch(ocr_forest *F) {
           F->level_base[l] + F->level_count[l], 0, 0, 1);
   for (int k = 0; k < K; ++k) add(k, kBatchReduce, up(F->M, tile), 0, F->M, 0, 0, 1);
   for (int k = 0; k < K; ++k) add(k, kBatchDown, up(F->M, tile), 0, F->M, 0, 0, 1);
-  for (int k = 0; k < K; ++k) add(k, kBatchChunkMap, up(F->M, tile), 0, F->M, 0, 0, 1);
   const int G = (int)F->h_group_nodes.size();
+  for (int k = 0; k < K; ++k) {
+    const long long ng = up(F->plans[k].gslots[G - 1], kGroup);
+    if (ng > 0) add(k, kBatchChunkMap, up(ng, tile), 0, ng, 0, 0, 1);
+  }
   for (int g = 0; g + 1 < G; ++g) {  // levels L - 1 .. 0: the tile level, then coarser
     const int level = L - 1 - g;
     if (level > F->lt) continue;
@@ -919,12 +922,14 @@ namespace {
 // layout (recomputed; equal to the plan), subtree pass, coarsening passes and
 // the pixel pass into rgba.  No host synchronisation.
 int enqueue_camera(ocr_forest *F, CamPlan &P, float4 *rgba, int *counts, unsigned char *visible,
-                   cudaStream_t st, bool timed, bool &subtree_ran, int64_t &launches) {
+                   cudaStream_t st, bool timed, bool count, bool &subtree_ran,
+                   int64_t &launches) {
   const int G = (int)F->h_group_nodes.size();
   Topo T{F->d_geo, F->d_child, F->d_leaves, F->N, F->M, F->L, F->lt};
   Field Fd{F->d_nodal, reinterpret_cast<const float4 *>(F->d_tf), F->s_min,
            7.f / (F->s_max - F->s_min)};
-  Scratch S{P.d_rect, P.d_off, P.d_entries, F->d_stats, counts, visible, P.d_chunk};
+  Scratch S{P.d_rect, P.d_off, P.d_entries, F->d_stats, counts,
+            visible, P.d_chunk, count ? F->d_stats : nullptr};
   OCR_CUDA(launch_cull_leaves(T, P.cam, S, st));
   ++launches;
   for (int l = F->L - 1; l >= 0; --l) {
@@ -935,7 +940,7 @@ int enqueue_camera(ocr_forest *F, CamPlan &P, float4 *rgba, int *counts, unsigne
   OCR_CUDA(launch_area_scan(T, S, P.d_bsums, F->bsums_blocks, P.d_gslots, F->d_group_nodes, G,
                             st));
   launches += area_scan_blocks(F->M) > 0 ? 4 : 1;
-  OCR_CUDA(launch_chunk_map(T, S, st));
+  OCR_CUDA(launch_chunk_map(T, S, P.gslots[G - 1], st));
   launches += F->M > 0;
   // the passes below read the field: with host data, wait for its copy here
   // (the pruning and layout above overlap it)
@@ -995,6 +1000,7 @@ int render_plans(ocr_forest *F, int first, int K, float *d_rgba, void *stream,
   if (counts) OCR_CUDA(cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)range_pix, st));
   if (visible) OCR_CUDA(cudaMemsetAsync(visible, 0, (size_t)F->N, st));
   const bool timed = stats && stats->time_phases && K == 1;
+  const bool count = stats && stats->fill_counters;  // the passes' work counters
   if (timed && !F->ev[0])
     for (cudaEvent_t &e : F->ev) OCR_CUDA(cudaEventCreate(&e));
   int64_t launches = 0;
@@ -1015,14 +1021,14 @@ int render_plans(ocr_forest *F, int first, int K, float *d_rgba, void *stream,
              7.f / (F->s_max - F->s_min)};
     if (F->data_ready) OCR_CUDA(cudaStreamWaitEvent(st, F->data_ready, 0));
     OCR_CUDA(launch_batch(T, Fd, F->integ, F->d_bseg, F->nbseg, F->d_bcam, F->d_bctl,
-                          F->nbtickets, rgba, counts, visible, F->d_stats, F->nsm,
+                          F->nbtickets, rgba, counts, visible, F->d_stats, count, F->nsm,
                           F->ctas_per_sm, st));
     launches += 1;
   } else if (K == 1) {
     int rc = F->geometry == OCR_GEOM_SHELL
                  ? enqueue_shell(F, plans[0], rgba, counts, visible, st, timed, launches)
-                 : enqueue_camera(F, plans[0], rgba, counts, visible, st, timed, subtree_ran,
-                                  launches);
+                 : enqueue_camera(F, plans[0], rgba, counts, visible, st, timed, count,
+                                  subtree_ran, launches);
     subtree_ran |= F->geometry == OCR_GEOM_SHELL;
     if (rc) return rc;
     if (timed) OCR_CUDA(cudaEventRecord(F->ev[4], st));
@@ -1039,7 +1045,7 @@ int render_plans(ocr_forest *F, int first, int K, float *d_rgba, void *stream,
                    ? enqueue_shell(F, P, rgba + at, cnt, visible, F->sub[k % ns], false,
                                    launches)
                    : enqueue_camera(F, P, rgba + at, cnt, visible, F->sub[k % ns], false,
-                                    subtree_ran, launches);
+                                    count, subtree_ran, launches);
       if (rc) return rc;
     }
     for (int q = 0; q < ns; ++q) {

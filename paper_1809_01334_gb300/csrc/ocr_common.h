@@ -68,18 +68,23 @@ struct Scratch {
   unsigned long long *stats; // [kStats] counters, see below
   int *counts;               // optional [w * h]
   unsigned char *visible;    // optional [N]
-  int *chunk_node;           // [ceil(total / kChunk) + 1] internal node holding slot c * kChunk
+  int *chunk_node;           // [ceil(total / kGroup) + 1] internal node holding slot g * kGroup
+  unsigned long long *counters;  // optional [kStats]: the passes' work counters, when asked for
 };
 
 // Device counters: [0, 4) subtree pass, [kStatCoarse, kStatCoarse + 4) coarse
-// passes, each {segments, RK steps, leaf slab tests, slots}; then device
-// errors and visible leaves.
+// passes, each {segments, RK steps, slab tests (subtree: node visits), slots},
+// counted only when Scratch::counters is set; then device errors and visible
+// leaves, always counted.
 constexpr int kStats = 16;
 constexpr int kStatSegments = 0, kStatSteps = 1, kStatTests = 2, kStatSlots = 3;
 constexpr int kStatCoarse = 8, kStatErrors = 4, kStatVisible = 5;
 
-// Slots are processed in chunks of kChunk consecutive slots, one chunk per CTA.
+// Slots are processed in chunks of kChunk consecutive slots, one chunk per CTA;
+// the slot map (Scratch::chunk_node) has one entry per group of kGroup slots
+// (one warp's slots).
 constexpr int kChunk = 128;
+constexpr int kGroup = 32;
 
 // (leaf, pixel) pair spaces (the adjoint, the shell) are cut into chunks of
 // kPairChunk pairs, one CTA each.
@@ -109,7 +114,7 @@ cudaError_t launch_area_scan(const Topo &T, Scratch S, long long *d_block_sums, 
                              long long *d_level_slots, const int *d_level_nodes, int nlevels,
                              cudaStream_t stream);
 int area_scan_blocks(int M);
-cudaError_t launch_chunk_map(const Topo &T, Scratch S, cudaStream_t stream);
+cudaError_t launch_chunk_map(const Topo &T, Scratch S, long long total, cudaStream_t stream);
 cudaError_t launch_subtree(const Topo &T, const Field &Fd, const Cam &C, const Integ &I, Scratch S,
                            int node_begin, int node_end, long long slot_begin, long long slot_end,
                            cudaStream_t stream);
@@ -153,7 +158,7 @@ struct BatchCam {
 cudaError_t launch_batch(const Topo &T, const Field &Fd, const Integ &I, const BatchSeg *d_seg,
                          int nseg, const BatchCam *d_cams, unsigned *d_ctl, long long ntickets,
                          float4 *rgba, int *counts, unsigned char *visible,
-                         unsigned long long *stats, int nsm, int ctas_per_sm,
+                         unsigned long long *stats, bool count, int nsm, int ctas_per_sm,
                          cudaStream_t stream);
 
 // Adjoint (ocr_backward.cu)

@@ -146,13 +146,12 @@ __global__ void __launch_bounds__(kScanThreads) area_downsweep_kernel(Topo T, Sc
   if (blockIdx.x == 0 && threadIdx.x == 0) S.off[T.M] = block_sums[nblk];
 }
 
-// chunk_node[c] = the internal node whose slot range holds slot c * kChunk
-__global__ void chunk_map_kernel(Topo T, Scratch S) {
-  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < T.M; n += gridDim.x * blockDim.x) {
-    const long long a = S.off[n], b = S.off[n + 1];
-    if (b <= a) continue;
-    for (long long c = (a + kChunk - 1) / kChunk; c * kChunk < b; ++c) S.chunk_node[c] = n;
-  }
+// chunk_node[g] = the internal node whose slot range holds slot g * kGroup:
+// one thread per group
+__global__ void chunk_map_kernel(Topo T, Scratch S, long long ngroups) {
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < ngroups;
+       g += (long long)gridDim.x * blockDim.x)
+    S.chunk_node[g] = node_of_slot<false>(S.off, T.M, g * kGroup);
 }
 
 __global__ void gather_level_slots_kernel(const long long *off, const int *level_nodes, int n,
@@ -164,11 +163,11 @@ __global__ void gather_level_slots_kernel(const long long *off, const int *level
 // ------------------------------------------------- subtree and coarsen --
 // One CTA per chunk; the bodies are in ocr_passes.cuh.
 template <bool SURF>
-__global__ void __launch_bounds__(kSubtreeThreads, 1024 / kSubtreeThreads)
+__global__ void __launch_bounds__(32, 32)
     subtree_kernel(Topo T, Field Fd, Cam c, Integ I, Scratch S, int nb, int ne, long long s0,
                    long long s1) {
   __shared__ SubtreeSmem sm;
-  subtree_chunk<SURF, false>(T, Fd, c, I, S, nb, ne, s0, s1, blockIdx.x, sm);
+  subtree_warp<SURF, false>(T, Fd, c, I, S, nb, ne, s0, s1, (s0 / 32 + blockIdx.x) * 32, sm);
 }
 
 template <bool FINAL, bool SURF>
@@ -313,9 +312,10 @@ cudaError_t launch_area_scan(const Topo &T, Scratch S, long long *block_sums, in
   return cudaGetLastError();
 }
 
-cudaError_t launch_chunk_map(const Topo &T, Scratch S, cudaStream_t stream) {
-  if (T.M < 1) return cudaSuccess;
-  chunk_map_kernel<<<grid_for(T.M, 256), 256, 0, stream>>>(T, S);
+cudaError_t launch_chunk_map(const Topo &T, Scratch S, long long total, cudaStream_t stream) {
+  const long long ngroups = (total + kGroup - 1) / kGroup;
+  if (T.M < 1 || ngroups < 1) return cudaSuccess;
+  chunk_map_kernel<<<grid_for(ngroups, 256), 256, 0, stream>>>(T, S, ngroups);
   return cudaGetLastError();
 }
 
@@ -323,15 +323,12 @@ cudaError_t launch_subtree(const Topo &T, const Field &Fd, const Cam &C, const I
                            Scratch S, int nb, int ne, long long s0, long long s1,
                            cudaStream_t stream) {
   if (s1 <= s0) return cudaSuccess;
-  const long long per = kSubtreeThreads / kChunk;  // chunks per CTA
-  const long long nblk = ((s1 - 1) / kChunk - s0 / kChunk + per) / per;
+  const long long nblk = (s1 - 1) / 32 - s0 / 32 + 1;  // one warp per 32 slots
   if (nblk > 0x7fffffffll) return cudaErrorInvalidValue;
   if (I.surface)  // isosurface segments (Sec. 2.8): a separate instantiation
-    subtree_kernel<true><<<(unsigned)nblk, kSubtreeThreads, 0, stream>>>(T, Fd, C, I, S, nb, ne,
-                                                                         s0, s1);
+    subtree_kernel<true><<<(unsigned)nblk, 32, 0, stream>>>(T, Fd, C, I, S, nb, ne, s0, s1);
   else
-    subtree_kernel<false><<<(unsigned)nblk, kSubtreeThreads, 0, stream>>>(T, Fd, C, I, S, nb, ne,
-                                                                          s0, s1);
+    subtree_kernel<false><<<(unsigned)nblk, 32, 0, stream>>>(T, Fd, C, I, S, nb, ne, s0, s1);
   return cudaGetLastError();
 }
 

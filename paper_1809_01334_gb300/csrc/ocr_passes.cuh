@@ -34,22 +34,37 @@ __device__ __forceinline__ V ldw(const V *p) {
   else return *p;
 }
 
-// Node, its box and the pixel of a slot of the non-final passes.  The CTA's
-// chunk of slots lies in the nodes [chunk_node[chunk], chunk_node[chunk + 1]];
-// the first of them holds most of the chunk, so its offsets, rectangle and
-// box are loaded at once and the search runs only for the slots past its end.
+// The internal node whose slot range holds the slot (a binary search of the
+// slot offsets; COH: offsets written earlier in the same launch, read
+// through L2).
+template <bool COH>
+__device__ __forceinline__ int node_of_slot(const long long *off, int M, long long slot) {
+  int lo = 0, hi = M;
+  while (lo < hi) {  // first node whose offset exceeds the slot
+    const int mid = (lo + hi) >> 1;
+    if (ldw<COH>(off + mid) <= slot) lo = mid + 1; else hi = mid;
+  }
+  return lo - 1;
+}
+
+// Node, its box and the pixel of a slot of the non-final passes.  The group
+// of kGroup slots holding the slot lies in the nodes [chunk_node[grp],
+// chunk_node[grp + 1]]; the first of them holds most of the group, so its
+// offsets, rectangle and box are loaded at once and the search runs only for
+// the slots past its end.
 __device__ __forceinline__ void slot_lookup(const Topo &T, const Scratch &S, int nb, int ne,
-                                            long long chunk, long long slot, int &node, int &i,
-                                            int &j, int4 &geo) {
-  node = max(S.chunk_node[chunk], nb);
+                                            long long slot, int &node, int &i, int &j,
+                                            int4 &geo) {
+  const long long grp = slot / kGroup;
+  node = max(S.chunk_node[grp], nb);
   long long o0 = S.off[node];
   const long long o1 = S.off[node + 1];
   int4 r = S.rect[T.N + node];
   geo = __ldg(T.geo + T.N + node);
   if (slot >= o1) {
-    const long long nch = (S.off[T.M] + kChunk - 1) / kChunk;
+    const long long ngr = (S.off[T.M] + kGroup - 1) / kGroup;
     int lo = node + 1;
-    int hi = (chunk + 1 < nch) ? min(S.chunk_node[chunk + 1], ne - 1) + 1 : ne;
+    int hi = (grp + 1 < ngr) ? min(S.chunk_node[grp + 1], ne - 1) + 1 : ne;
     while (lo < hi) {  // first node whose offset exceeds the slot
       const int mid = (lo + hi) >> 1;
       if (S.off[mid] <= slot) lo = mid + 1; else hi = mid;
@@ -66,8 +81,10 @@ __device__ __forceinline__ void slot_lookup(const Topo &T, const Scratch &S, int
   j = r.z + (int)row;
 }
 
-// Subtree pass (Sec. 3.2 + Sec. 3.3 for the deepest levels).  A CTA owns a
-// chunk of kChunk consecutive (tile-level node, ray) slots, one thread each.
+// Subtree pass (Sec. 3.2 + Sec. 3.3 for the deepest levels).  A warp owns 32
+// consecutive (tile-level node, ray) slots, one lane each, and works alone
+// (no CTA barrier): the standalone kernel runs one-warp CTAs, so that a warp
+// that is done frees its place at once.
 //  A. every ray descends its tile node's subtree front to back: at each
 //     internal node its box is cut by the three mid-planes, and the ray's
 //     crossings of the node's planes give the slab interval of all 8 children
@@ -83,18 +100,17 @@ __device__ __forceinline__ void slot_lookup(const Topo &T, const Scratch &S, int
 //     batches; a hit whose leaf's pixel rectangle does not hold the pixel (a
 //     rounding edge case: the pair is no candidate) gives no segment, and
 //  C. every lane folds its own ray's results nearest-first with Eq. 2.14.
-constexpr int kSubtreeThreads = kChunk;  // one chunk per CTA
-constexpr int kWarpBatch = 32;           // hits per warp batch of phase B
+constexpr int kWarpBatch = 32;  // hits per warp batch of phase B
 static_assert(kSubtreeDepth <= 3, "the descent keeps two ancestors in registers");
 
-// Shared memory of one subtree chunk.
+// Shared memory of one subtree warp.
 struct SubtreeSmem {
   float4 tfv[8], tfs[8];
-  float ray[6][kSubtreeThreads];                   // ray: varying part, reciprocal direction
-  float4 res[kSubtreeThreads / 32][kWarpBatch];    // phase B: the warps' segment values
-  int2 pix[kSubtreeThreads];                       // pixel of each ray
-  int drop[kSubtreeThreads];                       // hits outside the leaf's rectangle
-  int list[kMaxSubtreeHits][kSubtreeThreads];      // hits of each ray (leaf ids), in order
+  float ray[6][32];                  // ray: varying part, reciprocal direction
+  float4 res[kWarpBatch];            // phase B: segment values of a batch
+  int2 pix[32];                      // pixel of each ray
+  int drop[32];                      // hits outside the leaf's rectangle
+  int list[kMaxSubtreeHits][32];     // hits of each ray (leaf ids), in order
 };
 
 // Child id of octant q from the node's 8 children held in two int4.
@@ -160,22 +176,21 @@ __device__ __forceinline__ unsigned child_hits(float3 o, float3 d, float3 iv, fl
   return m;
 }
 
-// One chunk (CTA bid of the pass over the slots [s0, s1) of the nodes
-// [nb, ne)); a CTA of kSubtreeThreads threads.
+// The 32 slots [ws, ws + 32) of the pass over the slots [s0, s1) of the
+// nodes [nb, ne), ws a multiple of 32; one warp, its own shared memory.
 template <bool SURF, bool COH>
-__device__ __forceinline__ void subtree_chunk(const Topo &T, const Field &Fd, const Cam &c,
-                                              const Integ &I, const Scratch &S, int nb, int ne,
-                                              long long s0, long long s1, long long bid,
-                                              SubtreeSmem &sm) {
-  constexpr int NT = kSubtreeThreads, NW = NT / 32;
+__device__ __forceinline__ void subtree_warp(const Topo &T, const Field &Fd, const Cam &c,
+                                             const Integ &I, const Scratch &S, int nb, int ne,
+                                             long long s0, long long s1, long long ws,
+                                             SubtreeSmem &sm) {
   float4(&s_tfv)[8] = sm.tfv;
   float4(&s_tfs)[8] = sm.tfs;
-  float(&s_ray)[6][NT] = sm.ray;
-  int(&s_list)[kMaxSubtreeHits][NT] = sm.list;
-  float4(&s_res)[NW][kWarpBatch] = sm.res;
-  int2(&s_pix)[NT] = sm.pix;
-  int(&s_drop)[NT] = sm.drop;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  float(&s_ray)[6][32] = sm.ray;
+  int(&s_list)[kMaxSubtreeHits][32] = sm.list;
+  float4(&s_res)[kWarpBatch] = sm.res;
+  int2(&s_pix)[32] = sm.pix;
+  int(&s_drop)[32] = sm.drop;
+  const int tid = threadIdx.x & 31, lane = tid;
   if (tid < 8) {
     const float4 v = Fd.tf[tid];
     const float4 w = Fd.tf[tid < 7 ? tid + 1 : 7];
@@ -184,12 +199,11 @@ __device__ __forceinline__ void subtree_chunk(const Topo &T, const Field &Fd, co
   }
 
   // slot -> node, pixel, ray; rays that miss the node's box skip all leaves
-  const long long cs = (s0 / kChunk) * kChunk + bid * NT;
-  const long long slot = cs + tid;
+  const long long slot = ws + tid;
   const bool active = slot >= s0 && slot < s1;
   int node = -1, i = 0, j = 0;
   int4 gn = make_int4(0, 0, 0, 0);
-  if (active) slot_lookup(T, S, nb, ne, slot / kChunk, slot, node, i, j, gn);
+  if (active) slot_lookup(T, S, nb, ne, slot, node, i, j, gn);
   float3 org, dir;
   pixel_ray(c, i, j, org, dir);
   const float3 inv = make_float3(recip_or_zero(dir.x), recip_or_zero(dir.y), recip_or_zero(dir.z));
@@ -211,7 +225,7 @@ __device__ __forceinline__ void subtree_chunk(const Topo &T, const Field &Fd, co
   s_pix[tid] = make_int2(i, j);
   s_drop[tid] = 0;
 
-  __syncthreads();  // the transfer function table
+  __syncwarp();  // the transfer function table
 
   // A. front-to-back descent; the path's ancestors (node, children still to
   // visit) in registers, the current anchor cleared to an ancestor's on the
@@ -316,7 +330,7 @@ __device__ __forceinline__ void subtree_chunk(const Topo &T, const Field &Fd, co
       const int ow = lo & 31;
       const int owpre = __shfl_sync(0xffffffffu, my0, ow);
       if (h < b1) {
-        const int t = wid * 32 + ow;
+        const int t = ow;
         const int leaf = s_list[h - owpre][t];
         const float3 rv = make_float3(s_ray[0][t], s_ray[1][t], s_ray[2][t]);
         const float3 ro = c.ortho ? rv : make_float3(c.o[0], c.o[1], c.o[2]);
@@ -329,16 +343,16 @@ __device__ __forceinline__ void subtree_chunk(const Topo &T, const Field &Fd, co
                                              make_float3(s_ray[3][t], s_ray[4][t], s_ray[5][t]),
                                              scale, st);
         if (inside) {
-          s_res[wid][h - b0] = sg;
+          s_res[h - b0] = sg;
           steps += st;
         } else {
-          s_res[wid][h - b0] = seg_identity();
+          s_res[h - b0] = seg_identity();
           atomicAdd(&s_drop[t], 1);
         }
       }
     }
     __syncwarp();
-    for (int h = max(my0, b0); h < min(my0 + n, b1); ++h) acc = seg_combine(acc, s_res[wid][h - b0]);
+    for (int h = max(my0, b0); h < min(my0 + n, b1); ++h) acc = seg_combine(acc, s_res[h - b0]);
     __syncwarp();
   }
   __syncwarp();
@@ -348,14 +362,14 @@ __device__ __forceinline__ void subtree_chunk(const Topo &T, const Field &Fd, co
     S.entries[slot] = acc;
     if (nhit && S.counts) atomicAdd(S.counts + (size_t)j * c.w + i, (int)nhit);
   }
-  // counters: one atomic per warp and counter, no CTA-wide barrier at the end
-  unsigned long long v[4] = {nhit, (unsigned long long)steps, nvisit, active ? 1ull : 0ull};
+  // counters, when asked for: one atomic per warp and counter
+  if (S.counters) {
+    const unsigned v[4] = {nhit, (unsigned)steps, nvisit, active ? 1u : 0u};
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    unsigned long long x = v[q];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if (lane == 0 && x) atomicAdd(S.stats + q, x);
+    for (int q = 0; q < 4; ++q) {
+      const unsigned x = __reduce_add_sync(0xffffffffu, v[q]);
+      if (lane == 0 && x) atomicAdd(S.counters + q, (unsigned long long)x);
+    }
   }
 }
 
@@ -412,7 +426,7 @@ __device__ __forceinline__ void coarsen_chunk(const Topo &T, const Field &Fd, co
       i = (int)(slot % c.w);
       j = (int)(slot / c.w);
     } else {
-      slot_lookup(T, S, nb, ne, chunk, slot, node, i, j, g);
+      slot_lookup(T, S, nb, ne, slot, node, i, j, g);
     }
   }
   s_pix[tid] = make_int2(i, j);
@@ -520,18 +534,17 @@ __device__ __forceinline__ void coarsen_chunk(const Topo &T, const Field &Fd, co
     }
   }
 
-  // counters: segments, RK steps, leaf tests, slots
-  unsigned long long v[4] = {local_hits, (unsigned long long)steps, local_tests,
-                             active ? 1ull : 0ull};
+  // counters, when asked for: segments, RK steps, leaf tests, slots
+  if (S.counters) {
+    const unsigned v[4] = {local_hits, (unsigned)steps, local_tests, active ? 1u : 0u};
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    unsigned long long x = v[q];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if ((tid & 31) == 0 && x) atomicAdd(&s_cnt[q], x);
+    for (int q = 0; q < 4; ++q) {
+      const unsigned x = __reduce_add_sync(0xffffffffu, v[q]);
+      if ((tid & 31) == 0 && x) atomicAdd(&s_cnt[q], (unsigned long long)x);
+    }
+    __syncthreads();
+    if (tid < 4 && s_cnt[tid]) atomicAdd(S.counters + kStatCoarse + tid, s_cnt[tid]);
   }
-  __syncthreads();
-  if (tid < 4 && s_cnt[tid]) atomicAdd(S.stats + kStatCoarse + tid, s_cnt[tid]);
 }
 
 }  // namespace
