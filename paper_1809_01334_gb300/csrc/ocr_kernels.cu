@@ -179,21 +179,25 @@ __global__ void __launch_bounds__(kCoarsenThreads, 8)
 }
 
 // Top-down merge of the levels above the tile level, one thread per pixel:
-// the octree is walked from the super-root in the ray's front-to-back order
-// of octants (q ^ mask, mask the direction's sign bits), descending into
-// internal nodes whose rectangle holds the pixel; a tile-level node
-// contributes its (node, ray) aggregate, a leaf above the tile level its
-// segment; the contributions are combined nearest first (Eq. 2.14).  The same
-// result as the per-level passes up to rounding order (Eq. 2.14 is
-// associative), in one launch and without intermediate aggregates in HBM.
+// the octree is walked from the tree root in the ray's front-to-back order of
+// octants (bit q ^ flip, flip the direction's sign bits).  At each internal
+// node above the tile level the children the ray meets come from one
+// child_hits (the children's exact slab tests); a leaf among them whose pixel
+// rectangle holds the pixel gives its segment, a tile-level node its (node,
+// ray) aggregate of the subtree pass, an internal node is descended into.
+// The contributions are combined nearest first (Eq. 2.14): the result of the
+// per-level passes up to rounding order (Eq. 2.14 is associative), in one
+// launch and without intermediate aggregates in HBM.  A node the ray misses
+// holds nothing the ray meets (nested boxes, monotone rounding), and a node
+// whose rectangle misses the pixel holds no leaf whose rectangle holds it, so
+// only the contributors' rectangles are checked.
 constexpr int kTopDownThreads = 128;
-constexpr int kMaxTopDownDepth = 24;
 
 template <bool SURF>
-__global__ void __launch_bounds__(kTopDownThreads)
+__global__ void __launch_bounds__(kTopDownThreads, 8)
     topdown_kernel(Topo T, Field Fd, Cam c, Integ I, Scratch S, long long npix, float4 *rgba) {
   __shared__ float4 s_tfv[8], s_tfs[8];
-  __shared__ unsigned long long s_cnt[3];
+  extern __shared__ int2 s_stk[];  // [(lt + 1) * kTopDownThreads] ancestors: node, children left
   const int tid = threadIdx.x;
   if (tid < 8) {
     const float4 v = Fd.tf[tid];
@@ -201,74 +205,95 @@ __global__ void __launch_bounds__(kTopDownThreads)
     s_tfv[tid] = v;
     s_tfs[tid] = make_float4(w.x - v.x, w.y - v.y, w.z - v.z, w.w - v.w);
   }
-  if (tid < 3) s_cnt[tid] = 0ull;
   __syncthreads();
   const TF tf{s_tfv, s_tfs, Fd.s_min, Fd.inv_ds7};
   const float scale = ldexpf(1.f, -T.L);
-  unsigned hits = 0, tests = 0;
+  const long long pix = (long long)blockIdx.x * kTopDownThreads + tid;
+  unsigned nhit = 0, ntest = 0;
   int steps = 0;
-  for (long long pix = (long long)blockIdx.x * kTopDownThreads + tid; pix < npix;
-       pix += (long long)gridDim.x * kTopDownThreads) {
+  if (pix < npix) {
     const int i = (int)(pix % c.w), j = (int)(pix / c.w);
     float3 org, dir;
     pixel_ray(c, i, j, org, dir);
     const float3 inv = make_float3(recip_or_zero(dir.x), recip_or_zero(dir.y), recip_or_zero(dir.z));
-    const int mask = (dir.x < 0.f ? 1 : 0) | (dir.y < 0.f ? 2 : 0) | (dir.z < 0.f ? 4 : 0);
+    const unsigned flip =
+        (dir.x < 0.f ? 1u : 0u) | (dir.y < 0.f ? 2u : 0u) | (dir.z < 0.f ? 4u : 0u);
+    const int4 *child4 = reinterpret_cast<const int4 *>(T.child);
     float4 acc = seg_identity();
-    int nhit = 0;
-    int stk[kMaxTopDownDepth];  // internal index of the node and the next octant to visit
-    unsigned char sq[kMaxTopDownDepth];
-    int sp = 0;
-    stk[0] = T.M;  // the super-root
-    sq[0] = 0;
-    sp = 1;
-    while (sp > 0) {
-      const int nd = stk[sp - 1];
-      const int q = sq[sp - 1];
-      if (q == 8) {
-        --sp;
+    // the super-root (internal index M, level -1): its one child is the tree root
+    int cur = T.M, lev = -1, gx = 0, gy = 0, gz = 0, d = 0;
+    int4 c0 = __ldg(child4 + 2 * T.M), c1 = __ldg(child4 + 2 * T.M + 1);
+    unsigned msk = 0u;
+    if (c0.x >= 0) {
+      const int4 g = __ldg(T.geo + c0.x);
+      float a0, a1;
+      if (slab(org, dir, inv, node_lo(g, scale), ldexpf(1.f, -g.w), c.amin, c.amax, a0, a1))
+        msk = 1u << flip;  // octant 0, mirrored
+    }
+    while (true) {
+      if (msk == 0u) {  // this node is done: back to its parent
+        if (d == 0) break;
+        --d;
+        --lev;
+        const int keep = ~((1 << (T.L - lev)) - 1);
+        gx &= keep;
+        gy &= keep;
+        gz &= keep;
+        const int2 e = s_stk[d * kTopDownThreads + tid];
+        cur = e.x;
+        msk = (unsigned)e.y;
+        c0 = __ldg(child4 + 2 * cur);
+        c1 = __ldg(child4 + 2 * cur + 1);
         continue;
       }
-      sq[sp - 1] = (unsigned char)(q + 1);
-      const int ch = __ldg(T.child + 8 * nd + (q ^ mask));
-      if (ch < 0) continue;
-      const int4 r = __ldg(S.rect + ch);
-      if (i < r.x || i > r.y || j < r.z || j > r.w) continue;
-      if (ch < T.N) {  // a leaf above the tile level
-        ++tests;
-        const int4 g = __ldg(T.geo + ch);
-        float a0, a1;
-        if (slab(org, dir, inv, node_lo(g, scale), ldexpf(1.f, -g.w), c.amin, c.amax, a0, a1)) {
-          acc = seg_combine(acc, leaf_segment<SURF>(T, Fd, c, I, tf, ch, org, dir, inv, scale,
+      const int q = (__ffs(msk) - 1) ^ (int)flip;
+      msk &= msk - 1u;
+      const int id = pick_child(c0, c1, q);
+      if (id < 0) continue;
+      if (id < T.N || lev + 1 == T.lt) {
+        const int4 r = __ldg(S.rect + id);
+        if (i < r.x || i > r.y || j < r.z || j > r.w) continue;
+        if (id < T.N) {  // a leaf at or above the tile level: its segment
+          ++ntest;
+          acc = seg_combine(acc, leaf_segment<SURF>(T, Fd, c, I, tf, id, org, dir, inv, scale,
                                                     steps));
           ++nhit;
+        } else {  // a tile-level node: its aggregate
+          const long long e = __ldg(S.off + id - T.N) + (long long)(j - r.z) * (r.y - r.x + 1) +
+                              (i - r.x);
+          acc = seg_combine(acc, S.entries[e]);
         }
-      } else if (__ldg(T.geo + ch).w == T.lt) {  // a tile-level node: its aggregate
-        const long long e = __ldg(S.off + ch - T.N) + (long long)(j - r.z) * (r.y - r.x + 1) +
-                            (i - r.x);
-        acc = seg_combine(acc, S.entries[e]);
-      } else if (sp < kMaxTopDownDepth) {
-        stk[sp] = ch - T.N;
-        sq[sp] = 0;
-        ++sp;
+        continue;
+      }
+      // an internal node above the tile level
+      s_stk[d * kTopDownThreads + tid] = make_int2(cur, (int)msk);
+      ++d;
+      const int hs = 1 << (T.L - lev - 1);
+      gx += (q & 1) * hs;
+      gy += ((q >> 1) & 1) * hs;
+      gz += (q >> 2) * hs;
+      ++lev;
+      cur = id - T.N;
+      msk = child_hits(org, dir, inv, node_lo(make_int4(gx, gy, gz, 0), scale),
+                       ldexpf(1.f, -(lev + 1)), c.amin, c.amax, flip);
+      if (msk) {
+        c0 = __ldg(child4 + 2 * cur);
+        c1 = __ldg(child4 + 2 * cur + 1);
       }
     }
     rgba[pix] = make_float4(fmaf(acc.x, I.bg[0], acc.y), fmaf(acc.x, I.bg[1], acc.z),
                             fmaf(acc.x, I.bg[2], acc.w), kOne - acc.x);
     if (nhit && S.counts) S.counts[pix] += nhit;  // after the subtree pass, in stream order
-    hits += nhit;
   }
-  // counters: segments, RK steps and leaf tests of the levels above the tile level
-  unsigned long long v[3] = {hits, (unsigned long long)steps, tests};
+  // counters, when asked for: segments, RK steps and leaf tests above the tile level
+  if (S.counters) {
+    const unsigned v[3] = {nhit, (unsigned)steps, ntest};
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    unsigned long long x = v[q];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if ((tid & 31) == 0 && x) atomicAdd(&s_cnt[q], x);
+    for (int q = 0; q < 3; ++q) {
+      const unsigned x = __reduce_add_sync(0xffffffffu, v[q]);
+      if ((tid & 31) == 0 && x) atomicAdd(S.counters + kStatCoarse + q, (unsigned long long)x);
+    }
   }
-  __syncthreads();
-  if (tid < 3 && s_cnt[tid]) atomicAdd(S.stats + kStatCoarse + tid, s_cnt[tid]);
 }
 
 }  // namespace
@@ -359,12 +384,14 @@ cudaError_t launch_topdown(const Topo &T, const Field &Fd, const Cam &C, const I
                            long long npix, float4 *rgba, int nsm, cudaStream_t stream) {
   if (npix <= 0) return cudaSuccess;
   const long long need = (npix + kTopDownThreads - 1) / kTopDownThreads;
-  const long long cap = (long long)(nsm > 0 ? nsm : 1) * 16;
-  const unsigned g = (unsigned)(need < cap ? need : cap);
+  if (need > 0x7fffffffll) return cudaErrorInvalidValue;
+  const unsigned g = (unsigned)need;
+  (void)nsm;
+  const size_t stk = sizeof(int2) * kTopDownThreads * (size_t)(T.lt + 1);  // the walk's ancestors
   if (I.surface)
-    topdown_kernel<true><<<g, kTopDownThreads, 0, stream>>>(T, Fd, C, I, S, npix, rgba);
+    topdown_kernel<true><<<g, kTopDownThreads, stk, stream>>>(T, Fd, C, I, S, npix, rgba);
   else
-    topdown_kernel<false><<<g, kTopDownThreads, 0, stream>>>(T, Fd, C, I, S, npix, rgba);
+    topdown_kernel<false><<<g, kTopDownThreads, stk, stream>>>(T, Fd, C, I, S, npix, rgba);
   return cudaGetLastError();
 }
 

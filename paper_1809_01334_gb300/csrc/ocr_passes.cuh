@@ -208,11 +208,6 @@ __device__ __forceinline__ void subtree_warp(const Topo &T, const Field &Fd, con
   pixel_ray(c, i, j, org, dir);
   const float3 inv = make_float3(recip_or_zero(dir.x), recip_or_zero(dir.y), recip_or_zero(dir.z));
   const float scale = ldexpf(1.f, -T.L);
-  bool live = false;
-  if (active) {
-    float a0, a1;
-    live = slab(org, dir, inv, node_lo(gn, scale), ldexpf(1.f, -gn.w), c.amin, c.amax, a0, a1);
-  }
   // the part of the ray that varies over the pixels (the origin of an
   // orthographic camera, the direction of a perspective one) and the
   // reciprocal direction, taken once per ray
@@ -232,10 +227,11 @@ __device__ __forceinline__ void subtree_warp(const Topo &T, const Field &Fd, con
   // way up, the current node's children loaded once per visit; the leaves
   // up to the next internal child are taken in one run
   const unsigned flip = (dir.x < 0.f ? 1u : 0u) | (dir.y < 0.f ? 2u : 0u) | (dir.z < 0.f ? 4u : 0u);
+  // (a ray that misses the tile node meets none of its children)
   int cur = node, lev = gn.w, gx = gn.x, gy = gn.y, gz = gn.z, d = 0;
-  unsigned msk = live ? child_hits(org, dir, inv, node_lo(gn, scale), ldexpf(1.f, -(lev + 1)),
-                                   c.amin, c.amax, flip)
-                      : 0u;
+  unsigned msk = active ? child_hits(org, dir, inv, node_lo(gn, scale), ldexpf(1.f, -(lev + 1)),
+                                     c.amin, c.amax, flip)
+                        : 0u;
   const int4 *child4 = reinterpret_cast<const int4 *>(T.child);
   int4 c0 = make_int4(-1, -1, -1, -1), c1 = c0;
   if (msk) {
@@ -244,7 +240,7 @@ __device__ __forceinline__ void subtree_warp(const Topo &T, const Field &Fd, con
   }
   int an0 = 0, an1 = 0;
   unsigned am0 = 0, am1 = 0;
-  unsigned nhit = 0, nvisit = live ? 1u : 0u;
+  unsigned nhit = 0, nvisit = active ? 1u : 0u;
   bool deep = false;
   while (true) {
     int q = 0, id = -1;
@@ -410,8 +406,6 @@ __device__ __forceinline__ void coarsen_chunk(const Topo &T, const Field &Fd, co
   }
   if (tid < 4) s_cnt[tid] = 0ull;
   if (tid == 0) s_nhit = 0;
-#pragma unroll
-  for (int q = 0; q < 8; ++q) s_seg[q][tid] = seg_identity();
 
   // non-final passes work on whole chunks of the global slot space, so that
   // chunk_node gives the first node of the CTA without a search
@@ -440,33 +434,42 @@ __device__ __forceinline__ void coarsen_chunk(const Topo &T, const Field &Fd, co
   const float3 inv = make_float3(recip_or_zero(dir.x), recip_or_zero(dir.y), recip_or_zero(dir.z));
   const float scale = ldexpf(1.f, -T.L);
 
-  // a ray that misses the node's box misses every child: its aggregate is the
-  // identity and all child work is skipped
-  bool live = active;
-  if (!FINAL && active) {
-    float a0, a1;
-    live = slab(org, dir, inv, node_lo(g, scale), ldexpf(1.f, -g.w), c.amin, c.amax, a0, a1);
+  // the children the ray meets (by octant), from the node's shared face
+  // crossings: a ray that misses the node meets none of them, and a child it
+  // misses contributes the identity.  The final pass's node is the
+  // super-root, whose one child is the tree root.
+  unsigned msk = 0u;
+  if (active) {
+    if (FINAL) {
+      if (ch[0] >= 0) {
+        const int4 gr = __ldg(T.geo + ch[0]);
+        float a0, a1;
+        if (slab(org, dir, inv, node_lo(gr, scale), ldexpf(1.f, -gr.w), c.amin, c.amax, a0, a1))
+          msk = 1u;
+      }
+    } else {
+      msk = child_hits(org, dir, inv, node_lo(g, scale), ldexpf(1.f, -(g.w + 1)), c.amin,
+                       c.amax, 0u);
+    }
   }
   __syncthreads();
 
-  // phase 1: slab tests against the leaf children whose rectangle holds the ray
-  unsigned local_tests = 0, local_hits = 0;
-  if (live) {
+  // phase 1: the leaf children the ray meets whose rectangle holds the pixel
+  unsigned local_tests = 0, local_hits = 0, lhit = 0u;
+  if (msk) {
     int4 rc[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q)
-      rc[q] = (ch[q] >= 0 && ch[q] < T.N) ? ldp<COH>(S.rect + ch[q]) : empty_rect();
+      rc[q] = ((msk >> q) & 1u) && ch[q] >= 0 && ch[q] < T.N ? ldp<COH>(S.rect + ch[q])
+                                                               : empty_rect();
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
+      local_tests += (ch[q] >= 0 && ch[q] < T.N) ? 1u : 0u;
       const int4 r = rc[q];
       if (i < r.x || i > r.y || j < r.z || j > r.w) continue;
-      ++local_tests;
-      const int4 g = __ldg(T.geo + ch[q]);
-      float a0, a1;
-      if (slab(org, dir, inv, node_lo(g, scale), ldexpf(1.f, -g.w), c.amin, c.amax, a0, a1)) {
-        s_hit[atomicAdd(&s_nhit, 1)] = (unsigned short)((tid << 3) | q);
-        ++local_hits;
-      }
+      s_hit[atomicAdd(&s_nhit, 1)] = (unsigned short)((tid << 3) | q);
+      lhit |= 1u << q;
+      ++local_hits;
     }
     if (local_hits && S.counts) atomicAdd(S.counts + (size_t)j * c.w + i, (int)local_hits);
   }
@@ -501,7 +504,7 @@ __device__ __forceinline__ void coarsen_chunk(const Topo &T, const Field &Fd, co
     for (int q = 0; q < 8; ++q) {
       const int id = ch[q];
       e[q] = -1;
-      if (live && id >= T.N) {
+      if (((msk >> q) & 1u) && id >= T.N) {
         const int4 r = ldp<COH>(S.rect + id);
         const long long o = ldp<COH>(S.off + id - T.N);
         if (i >= r.x && i <= r.y && j >= r.z && j <= r.w)
@@ -513,7 +516,7 @@ __device__ __forceinline__ void coarsen_chunk(const Topo &T, const Field &Fd, co
     for (int q = 0; q < 8; ++q) {
       const int id = ch[q];
       float4 s = seg_identity();
-      if (live && id >= 0 && id < T.N) s = s_seg[q][tid];
+      if ((lhit >> q) & 1u) s = s_seg[q][tid];
       else if (e[q] >= 0) s = ldw<COH>(S.entries + e[q]);
       cs[q] = s;
     }
