@@ -266,7 +266,7 @@ int ocr_render_host(ocr_forest *F, const float *h_nodal, const float *h_tf, floa
  * overwritten with dL/d(nodal) and dL/d(knots).  Segments are recomputed, not
  * taken from a previous render.  Cube: each ray's segments are put in
  * front-to-back order by their mirrored Morton key; a ray with more than 4096
- * segments is skipped and reported as OCR_ERR_DEVICE.  Shell: the render's
+ * segments is skipped and recorded as a device error.  Shell: the render's
  * per-ray lists are rebuilt in the first camera's scratch (so a backward call
  * must not overlap a render of the same forest on another stream) and ordered
  * by entry depth; overlapping rounding slivers are combined as if they did
@@ -275,11 +275,21 @@ int ocr_render_host(ocr_forest *F, const float *h_nodal, const float *h_tf, floa
  * OCR_ERR_OOM if that fails).  Every integrator: RK4, and inside Algorithm 1
  * DOPRI5 (stage recurrences run backwards), the Gauss-2 closed form, Simpson's
  * rule and the Eq. 2.18 interface (their closed forms differentiated, Eqs.
- * 2.32-2.34); surfaces return OCR_ERR_UNSUPPORTED.  Blocks the host (cube: three times, for the sizes of the pair
- * space and of the hit lists and the error word; shell: once, for the error
- * word). */
+ * 2.32-2.34); surfaces return OCR_ERR_UNSUPPORTED.  Stream-ordered: the call
+ * enqueues its work on `stream` and returns without waiting, so that it can be
+ * captured in a CUDA graph -- except the first call after an ocr_set_camera
+ * of a cube forest, which finds the sizes of that camera's pair space and hit
+ * lists (geometry only) and blocks the host for them (and may allocate).
+ * Device-side errors (a list overflow, a too long ray) are recorded in the
+ * forest and returned by the next ocr_sync. */
 int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_nodal,
                         float *d_grad_tf, void *stream);
+
+/* Wait for the work enqueued on `stream` and report the device-side errors
+ * that the stream-ordered calls (ocr_render_backward) recorded since the last
+ * ocr_sync: OCR_ERR_DEVICE if there were any (the record is then cleared),
+ * else OCR_OK.  Blocks the host.  Not a step of the paper's method. */
+int ocr_sync(ocr_forest *F, void *stream);
 
 /* Tuning of the render's decomposition (the batching autotuner's knobs):
  *   tile_depth  cube forests: how many octree levels (1..3) one CTA merges in

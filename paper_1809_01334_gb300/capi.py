@@ -20,7 +20,7 @@ RK4, DOPRI5, GAUSS2, SIMPSON, EQUILIBRIUM = 0, 1, 2, 3, 4
 EXPORTS = ["ocr_build_forest", "ocr_forest_set_data", "ocr_set_integrator", "ocr_set_camera",
            "ocr_render", "ocr_render_view", "ocr_render_host", "ocr_render_backward",
            "ocr_set_tuning", "ocr_get_tuning", "ocr_autotune", "ocr_prune_noalloc",
-           "ocr_device_bytes", "ocr_destroy", "ocr_strerror"]
+           "ocr_device_bytes", "ocr_destroy", "ocr_strerror", "ocr_sync"]
 
 
 class ForestDesc(C.Structure):
@@ -280,3 +280,10 @@ def render_backward(h, d_dL_drgba, d_grad_nodal, d_grad_tf, stream=None):
     fn.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     _check(fn(h, _ptr(d_dL_drgba), _ptr(d_grad_nodal), _ptr(d_grad_tf), _ptr(stream)),
            "ocr_render_backward")
+
+
+def sync(h, stream=None):
+    """ocr_sync: wait for the stream; raise if a stream-ordered call recorded a device error."""
+    fn = lib().ocr_sync
+    fn.argtypes = [C.c_void_p, C.c_void_p]
+    _check(fn(h, _ptr(stream)), "ocr_sync")

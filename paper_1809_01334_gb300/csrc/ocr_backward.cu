@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kPairThreads)
     const unsigned rw = (unsigned)(r.y - r.x + 1), row = local / rw;
     const int i = r.x + (int)(local - row * rw), j = r.z + (int)row;
     pix = (long long)j * c.w + i;
-    const float4 g = dL[pix];
+    const float4 g = dL ? dL[pix] : make_float4(1.f, 0.f, 0.f, 0.f);  // no dL: every ray
     if (g.x != 0.f || g.y != 0.f || g.z != 0.f || g.w != 0.f) {  // else no gradient on this ray
       float3 org;
       pixel_ray(c, i, j, org, dir);
@@ -805,7 +805,8 @@ __device__ __forceinline__ void seg_range(long long nseg, long long &b, long lon
 // segment's value (A, B) into val[e].  Cube leaves.
 __global__ void __launch_bounds__(kSegThreads)
     cube_seg_values_kernel(Topo T, Field Fd, Cam c, Integ I, const int2 *lm, long long nseg,
-                           float4 *val) {
+                           const unsigned long long *ncount, float4 *val) {
+  if (ncount) nseg = min(nseg, (long long)*ncount);  // the entries written, within the capacity
   __shared__ float4 s_tfv[8], s_tfs[8];
   load_tf(Fd, s_tfv, s_tfs);
   __syncthreads();
@@ -995,7 +996,8 @@ __device__ __forceinline__ void leaf_group_flush(const float *s_rows, int leaf, 
 __global__ void __launch_bounds__(kSegThreads, 4)
     cube_seg_adjoint_kernel(Topo T, Field Fd, Cam c, Integ I, const float4 *dL, const int2 *lm,
                             const float2 *rec_ta, const float4 *rec_g, long long nseg,
-                            float *g_nodal, float *g_tf) {
+                            const unsigned long long *ncount, float *g_nodal, float *g_tf) {
+  if (ncount) nseg = min(nseg, (long long)*ncount);  // the entries written, within the capacity
   __shared__ float s_g8[8 * kSegStride];
   __shared__ float s_gt[32 * kSegThreads];
   __shared__ float4 s_tfv[8], s_tfs[8];
@@ -1143,6 +1145,17 @@ cudaError_t bwd_pair_hits(int mode, const Topo &T, const Cam &C, const int4 *rec
   return cudaGetLastError();
 }
 
+// err += the device error counter of the render passes (one thread)
+__global__ void fold_errors_kernel(unsigned long long *err, const unsigned long long *stat_err) {
+  if (*stat_err) *err += *stat_err;
+}
+
+cudaError_t bwd_fold_errors(unsigned long long *err, const unsigned long long *stat_err,
+                            cudaStream_t st) {
+  fold_errors_kernel<<<1, 1, 0, st>>>(err, stat_err);
+  return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(256) hits_max_kernel(const int *counts, long long n,
                                                        unsigned long long *out) {
   int m = 0;
@@ -1170,11 +1183,11 @@ static unsigned seg_grid(long long nseg, int nsm, int per_sm) {
 }
 
 cudaError_t bwd_cube_values(const Topo &T, const Field &Fd, const Cam &C, const Integ &I,
-                            const int2 *lm, long long nseg, float4 *val, int nsm,
-                            cudaStream_t st) {
+                            const int2 *lm, long long nseg, const unsigned long long *ncount,
+                            float4 *val, int nsm, cudaStream_t st) {
   if (nseg <= 0) return cudaSuccess;
   cube_seg_values_kernel<<<seg_grid(nseg, nsm, 16), kSegThreads, 0, st>>>(T, Fd, C, I, lm, nseg,
-                                                                          val);
+                                                                          ncount, val);
   return cudaGetLastError();
 }
 
@@ -1224,11 +1237,12 @@ cudaError_t bwd_ray_scans(const Cam &C, const float4 *dL, const long long *ray_o
 
 cudaError_t bwd_cube_adjoint(const Topo &T, const Field &Fd, const Cam &C, const Integ &I,
                              const float4 *dL, const int2 *lm, const float2 *rec_ta,
-                             const float4 *rec_g, long long nseg, float *g_nodal, float *g_tf,
+                             const float4 *rec_g, long long nseg,
+                             const unsigned long long *ncount, float *g_nodal, float *g_tf,
                              int nsm, cudaStream_t st) {
   if (nseg <= 0) return cudaSuccess;
   cube_seg_adjoint_kernel<<<seg_grid(nseg, nsm, 16), kSegThreads, 0, st>>>(
-      T, Fd, C, I, dL, lm, rec_ta, rec_g, nseg, g_nodal, g_tf);
+      T, Fd, C, I, dL, lm, rec_ta, rec_g, nseg, ncount, g_nodal, g_tf);
   return cudaGetLastError();
 }
 

@@ -43,6 +43,11 @@ struct CamPlan {
   int *d_rcount = nullptr, *d_rcursor = nullptr;  // [npix]
   long long *d_ray_off = nullptr;     // [npix + 1]
   unsigned long long *d_keys = nullptr;  // [nhits]
+  // cube adjoint: sizes of its pair space and hit lists for this camera
+  // (geometry only: found by the first backward call after ocr_set_camera)
+  bool bwd_ready = false;
+  long long bwd_npairs = 0, bwd_nh = 0;  // (leaf, pixel) pairs; hits of every ray
+  int bwd_cap = 0;                      // longest list, rounded up to a power of two
 };
 
 constexpr int kMaxStreams = 8;      // cameras of a batch are spread over up to this many
@@ -94,7 +99,8 @@ struct ocr_forest {
   int nbseg = 0, nbcam = 0;
   long long nbtickets = 0;
   bool batch_ready = false;
-  long long *h_group_slots = nullptr; // pinned [L + 1 + kStats]
+  long long *h_group_slots = nullptr; // pinned [L + 1 + kStats + 1] (shell [kStats + 3]); last
+                                      // word: ocr_sync's
   unsigned long long *d_stats = nullptr;  // [kStats]
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // start, layout, subtree, end
   // adjoint
@@ -368,12 +374,17 @@ int build_shell(const ocr_forest_desc *desc, cudaStream_t st, ocr_forest **out) 
     delete F;
     return rc;
   }
-  if (cudaMallocHost((void **)&F->h_group_slots, sizeof(long long) * (kStats + 2)) !=
+  if (cudaMallocHost((void **)&F->h_group_slots, sizeof(long long) * (kStats + 3)) !=
       cudaSuccess) {
     F->h_group_slots = nullptr;
     free_all(F);
     delete F;
     return OCR_ERR_OOM;
+  }
+  if (cudaMemsetAsync(F->d_err, 0, sizeof(unsigned long long), st) != cudaSuccess) {
+    free_all(F);
+    delete F;
+    return OCR_ERR_CUDA;
   }
   F->shell.frames = F->d_shell_tabs;
   F->shell.tan_tab = F->d_shell_tabs + 54;
@@ -669,7 +680,7 @@ int ocr_build_forest(const ocr_forest_desc *desc, void *stream, ocr_forest **out
     }
   }
   if (cudaMallocHost((void **)&F->h_group_slots,
-                     sizeof(long long) * (F->h_group_nodes.size() + kStats)) !=
+                     sizeof(long long) * (F->h_group_nodes.size() + kStats + 1)) !=
       cudaSuccess) {
     F->h_group_slots = nullptr;
     free_all(F);
@@ -691,6 +702,7 @@ int ocr_build_forest(const ocr_forest_desc *desc, void *stream, ocr_forest **out
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(F->d_group_nodes, F->h_group_nodes.data(),
                         F->h_group_nodes.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(F->d_err, 0, sizeof(unsigned long long), st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host vectors die on return
   if (e != cudaSuccess) {
     free_all(F);
@@ -1215,7 +1227,6 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
     OCR_CUDA(cudaMemsetAsync(d_grad_nodal, 0, sizeof(float) * 27 * (size_t)F->N, st));
     OCR_CUDA(cudaMemsetAsync(d_grad_tf, 0, sizeof(float) * 32, st));
     OCR_CUDA(cudaMemsetAsync(F->d_stats, 0, kStats * sizeof(unsigned long long), st));
-    OCR_CUDA(cudaMemsetAsync(F->d_err, 0, sizeof(unsigned long long), st));
     OCR_CUDA(shell_monomials(F->d_nodal, F->d_coef, F->N, st));
     rc = enqueue_shell_lists(F, P, nullptr, st, true);
     if (rc) return rc;
@@ -1227,12 +1238,8 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
     OCR_CUDA(bwd_shell_adjoint(F->d_geo, F->N, F->shell, Fd, P.cam, F->integ, dL, F->d_slm,
                                F->d_srta, F->d_srg, P.nhits, d_grad_nodal, d_grad_tf, F->nsm,
                                st));
-    long long *h = F->h_group_slots;
-    OCR_CUDA(cudaMemcpyAsync(h, F->d_err, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-    OCR_CUDA(cudaMemcpyAsync(h + 1, F->d_stats + kStatErrors, sizeof(unsigned long long),
-                             cudaMemcpyDeviceToHost, st));
-    OCR_CUDA(cudaStreamSynchronize(st));
-    return (h[0] || h[1]) ? OCR_ERR_DEVICE : OCR_OK;
+    OCR_CUDA(bwd_fold_errors(F->d_err, F->d_stats + kStatErrors, st));
+    return OCR_OK;
   }
   CamPlan &P0 = F->plans[0];
   const Cam &cam = P0.cam;
@@ -1262,55 +1269,89 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
         return rc;
     }
   }
+  const float4 *dL = reinterpret_cast<const float4 *>(d_dL_drgba);
+  if (!P0.bwd_ready) {
+    // the sizes of the pair space and of the hit lists depend on the camera
+    // alone: found once, blocking the host twice, with every ray counted
+    OCR_CUDA(launch_cull_leaves(T, cam, S, st));
+    OCR_CUDA(bwd_leaf_scan(T, P0.d_rect, F->d_bsums, F->bsums_cap, F->d_leaf_off, st));
+    long long *h = F->h_group_slots + F->h_group_nodes.size();  // pinned scratch
+    OCR_CUDA(cudaMemcpyAsync(h, F->d_leaf_off + F->N, sizeof(long long), cudaMemcpyDeviceToHost,
+                             st));
+    OCR_CUDA(cudaStreamSynchronize(st));
+    const long long npairs = h[0];
+    if ((rc = grow(F, &F->d_pchunk, F->pchunk_cap, npairs / 256 + 2))) return rc;
+    OCR_CUDA(bwd_chunk_map(F->d_leaf_off, F->N, F->d_pchunk, st));
+    OCR_CUDA(cudaMemsetAsync(F->d_rcount, 0, sizeof(int) * (size_t)npix, st));
+    OCR_CUDA(bwd_pair_hits(0, T, cam, P0.d_rect, F->d_leaf_off, F->d_pchunk, npairs, nullptr,
+                           F->d_rcount, nullptr, nullptr, F->d_mkey, F->fx, nullptr, nullptr,
+                           nullptr, nullptr, 0, nullptr, st));
+    OCR_CUDA(bwd_count_scan(F->d_rcount, npix, F->d_bsums, F->bsums_cap, F->d_ray_off, st));
+    OCR_CUDA(cudaMemsetAsync(F->d_stats + kStatMaxHits, 0, sizeof(unsigned long long), st));
+    OCR_CUDA(bwd_max_hits(F->d_rcount, npix, F->d_stats + kStatMaxHits, st));
+    OCR_CUDA(cudaMemcpyAsync(h, F->d_ray_off + npix, sizeof(long long), cudaMemcpyDeviceToHost,
+                             st));
+    OCR_CUDA(cudaMemcpyAsync(h + 1, F->d_stats + kStatMaxHits, sizeof(long long),
+                             cudaMemcpyDeviceToHost, st));
+    OCR_CUDA(cudaStreamSynchronize(st));
+    const long long nh = h[0];
+    if (nh >= 0xffffffffll) return OCR_ERR_UNSUPPORTED;  // list indices are 32-bit
+    int cap = 32;  // per-warp lists sized for the longest ray (longer ones: device error)
+    while (cap < h[1] && cap < kShellMaxCap) cap <<= 1;
+    if ((rc = grow(F, &F->d_hkey, F->hit_cap, nh)) || (rc = grow_adjoint(F, nh))) return rc;
+    P0.bwd_npairs = npairs;
+    P0.bwd_nh = nh;
+    P0.bwd_cap = cap;
+    P0.bwd_ready = true;
+  }
+  const long long npairs = P0.bwd_npairs, nh = P0.bwd_nh;
   OCR_CUDA(cudaMemsetAsync(d_grad_nodal, 0, sizeof(float) * 8 * (size_t)F->N, st));
   OCR_CUDA(cudaMemsetAsync(d_grad_tf, 0, sizeof(float) * 32, st));
   OCR_CUDA(cudaMemsetAsync(F->d_stats, 0, kStats * sizeof(unsigned long long), st));
 
-  // leaf rectangles, then the (leaf, pixel) pair space in Morton order
+  // leaf rectangles, then the (leaf, pixel) pair space in Morton order (as
+  // planned: the same camera)
   OCR_CUDA(launch_cull_leaves(T, cam, S, st));
   OCR_CUDA(bwd_leaf_scan(T, P0.d_rect, F->d_bsums, F->bsums_cap, F->d_leaf_off, st));
-  long long *h = F->h_group_slots + F->h_group_nodes.size();  // pinned scratch
-  OCR_CUDA(cudaMemcpyAsync(h, F->d_leaf_off + F->N, sizeof(long long), cudaMemcpyDeviceToHost, st));
-  OCR_CUDA(cudaStreamSynchronize(st));
-  const long long npairs = h[0];
-  if ((rc = grow(F, &F->d_pchunk, F->pchunk_cap, npairs / 256 + 2))) return rc;
   OCR_CUDA(bwd_chunk_map(F->d_leaf_off, F->N, F->d_pchunk, st));
-  const float4 *dL = reinterpret_cast<const float4 *>(d_dL_drgba);
 
-  // hits per ray, their offsets, then the hit lists (mirrored Morton keys) and
-  // the leaf-grouped list
+  // hits per ray (rays without an image adjoint skipped), their offsets, then
+  // the hit lists (mirrored Morton keys) and the leaf-grouped list, within the
+  // planned capacity of every ray's hits
   OCR_CUDA(cudaMemsetAsync(F->d_rcount, 0, sizeof(int) * (size_t)npix, st));
   OCR_CUDA(bwd_pair_hits(0, T, cam, P0.d_rect, F->d_leaf_off, F->d_pchunk, npairs, dL,
                          F->d_rcount, nullptr, nullptr, F->d_mkey, F->fx, nullptr, nullptr,
                          nullptr, nullptr, 0, nullptr, st));
   OCR_CUDA(bwd_count_scan(F->d_rcount, npix, F->d_bsums, F->bsums_cap, F->d_ray_off, st));
-  OCR_CUDA(bwd_max_hits(F->d_rcount, npix, F->d_stats + kStatMaxHits, st));
-  OCR_CUDA(cudaMemcpyAsync(h, F->d_ray_off + npix, sizeof(long long), cudaMemcpyDeviceToHost, st));
-  OCR_CUDA(cudaMemcpyAsync(h + 1, F->d_stats + kStatMaxHits, sizeof(long long),
-                           cudaMemcpyDeviceToHost, st));
-  OCR_CUDA(cudaStreamSynchronize(st));
-  const long long nh = h[0];
-  if (nh >= 0xffffffffll) return OCR_ERR_UNSUPPORTED;  // list indices are 32-bit
-  int cap = 32;  // per-warp lists sized for the longest ray (longer ones: device error)
-  while (cap < h[1] && cap < kShellMaxCap) cap <<= 1;
-  if ((rc = grow(F, &F->d_hkey, F->hit_cap, nh)) || (rc = grow_adjoint(F, nh))) return rc;
   OCR_CUDA(cudaMemsetAsync(F->d_rcursor, 0, sizeof(int) * (size_t)npix, st));
   OCR_CUDA(cudaMemsetAsync(F->d_lmcount, 0, sizeof(unsigned long long), st));
-  OCR_CUDA(cudaMemsetAsync(F->d_err, 0, sizeof(unsigned long long), st));
   OCR_CUDA(bwd_pair_hits(2, T, cam, P0.d_rect, F->d_leaf_off, F->d_pchunk, npairs, dL, nullptr,
                          F->d_ray_off, F->d_rcursor, F->d_mkey, F->fx, F->d_hkey, F->d_skpos,
                          F->d_slm, F->d_lmcount, nh, F->d_err, st));
 
-  // segment values, per-ray scans, segment adjoints
-  OCR_CUDA(bwd_cube_values(T, Fd, cam, F->integ, F->d_slm, nh, F->d_srg, F->nsm, st));
-  OCR_CUDA(bwd_ray_scans(cam, dL, F->d_ray_off, F->d_hkey, F->d_skpos, nh, cap, F->d_srta,
-                         F->d_srg, F->d_err, F->nsm, st));
+  // segment values, per-ray scans, segment adjoints over the entries written
+  OCR_CUDA(bwd_cube_values(T, Fd, cam, F->integ, F->d_slm, nh, F->d_lmcount, F->d_srg, F->nsm,
+                           st));
+  OCR_CUDA(bwd_ray_scans(cam, dL, F->d_ray_off, F->d_hkey, F->d_skpos, nh, P0.bwd_cap,
+                         F->d_srta, F->d_srg, F->d_err, F->nsm, st));
   OCR_CUDA(bwd_cube_adjoint(T, Fd, cam, F->integ, dL, F->d_slm, F->d_srta, F->d_srg, nh,
-                            d_grad_nodal, d_grad_tf, F->nsm, st));
+                            F->d_lmcount, d_grad_nodal, d_grad_tf, F->nsm, st));
+  OCR_CUDA(bwd_fold_errors(F->d_err, F->d_stats + kStatErrors, st));
+  return OCR_OK;
+}
+
+int ocr_sync(ocr_forest *F, void *stream) {
+  if (!F) return OCR_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the last word of the pinned scratch is ocr_sync's own
+  const size_t at = F->geometry == OCR_GEOM_SHELL ? kStats + 2 : F->h_group_nodes.size() + kStats;
+  unsigned long long *h = reinterpret_cast<unsigned long long *>(F->h_group_slots) + at;
   OCR_CUDA(cudaMemcpyAsync(h, F->d_err, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
   OCR_CUDA(cudaStreamSynchronize(st));
-  if (h[0]) return OCR_ERR_DEVICE;
-  return OCR_OK;
+  if (!h[0]) return OCR_OK;
+  OCR_CUDA(cudaMemsetAsync(F->d_err, 0, sizeof(unsigned long long), st));
+  OCR_CUDA(cudaStreamSynchronize(st));
+  return OCR_ERR_DEVICE;
 }
 
 int ocr_set_tuning(ocr_forest *F, const ocr_tuning *t) {

@@ -168,7 +168,8 @@ cudaError_t bwd_count_scan(const int *counts, long long n, long long *bs, long l
                            long long *ray_off, cudaStream_t st);
 long long bwd_scan_blocks(long long n);
 cudaError_t bwd_chunk_map(const long long *leaf_off, int N, int *chunk_leaf, cudaStream_t st);
-// mode 0: hits per ray into counts (rays with a zero image adjoint skipped);
+// mode 0: hits per ray into counts (rays with a zero image adjoint skipped;
+// dL null: every ray);
 // mode 2: each hit's mirrored Morton key into its ray's list, and the hit
 // appended to the leaf-grouped list lm (pixel, leaf) through *lm_count (zeroed
 // by the caller), its index in kpos beside the key; more than key_cap hits
@@ -183,12 +184,16 @@ cudaError_t bwd_pair_hits(int mode, const Topo &T, const Cam &C, const int4 *rec
 // the most hits on one ray (atomicMax into *out, which the caller zeroes)
 cudaError_t bwd_max_hits(const int *counts, long long n, unsigned long long *out,
                          cudaStream_t st);
-// The three passes over a leaf-grouped list of nseg entries.  Values: one
-// thread per entry, the segment's (A, B) into val (shell: entries of rays with
-// a zero image adjoint are skipped; missing pieces counted in err).
-cudaError_t bwd_cube_values(const Topo &T, const Field &Fd, const Cam &C, const Integ &I,
-                            const int2 *lm, long long nseg, float4 *val, int nsm,
+// *err += *stat_err (the render passes' device error counter), on the stream
+cudaError_t bwd_fold_errors(unsigned long long *err, const unsigned long long *stat_err,
                             cudaStream_t st);
+// The three passes over a leaf-grouped list of nseg entries (cube: at most
+// nseg, the count read from *ncount on the device when it is given).  Values:
+// one thread per entry, the segment's (A, B) into val (shell: entries of rays
+// with a zero image adjoint are skipped; missing pieces counted in err).
+cudaError_t bwd_cube_values(const Topo &T, const Field &Fd, const Cam &C, const Integ &I,
+                            const int2 *lm, long long nseg, const unsigned long long *ncount,
+                            float4 *val, int nsm, cudaStream_t st);
 cudaError_t bwd_shell_values(const int4 *geo, int N, const Shell &S, const Field &Fd,
                              const Cam &C, const Integ &I, const float4 *dL, const int2 *lm,
                              long long nseg, float4 *val, unsigned long long *err, int nsm,
@@ -208,7 +213,8 @@ cudaError_t bwd_ray_scans(const Cam &C, const float4 *dL, const long long *ray_o
 // the same leaf, then accumulated into g_nodal, the knot adjoints into g_tf.
 cudaError_t bwd_cube_adjoint(const Topo &T, const Field &Fd, const Cam &C, const Integ &I,
                              const float4 *dL, const int2 *lm, const float2 *rec_ta,
-                             const float4 *rec_g, long long nseg, float *g_nodal, float *g_tf,
+                             const float4 *rec_g, long long nseg,
+                             const unsigned long long *ncount, float *g_nodal, float *g_tf,
                              int nsm, cudaStream_t st);
 
 // Cubed-sphere shell (ocr_shell.cu)

@@ -158,14 +158,22 @@ class Renderer:
         return capi.render_host(self.h, nodal_h, tf_h, self.s_min, self.s_max, out_h,
                                 _stream_ptr(stream))
 
-    def backward(self, grad_rgba: torch.Tensor, stream=None):
+    def backward(self, grad_rgba: torch.Tensor, stream=None, check: bool = True):
         """dL/d(nodal) [N, 8] and dL/d(knots) [8, 4] (cube forests) for the data, camera and
-        integrator last set, given dL/d(rgba) [h, w, 4] on the device."""
+        integrator last set, given dL/d(rgba) [h, w, 4] on the device.  The adjoint is
+        stream-ordered; check=True waits for it and raises on a device error (ocr_sync),
+        check=False returns at once (call sync() later)."""
         g = grad_rgba.detach().to(self.device, torch.float32).contiguous()
         gn = torch.empty_like(self.nodal)
         gt = torch.empty_like(self.tf)
         capi.render_backward(self.h, g, gn, gt, _stream_ptr(stream))
+        if check:
+            capi.sync(self.h, _stream_ptr(stream))
         return gn, gt
+
+    def sync(self, stream=None):
+        """Wait for the stream; raise if a stream-ordered call recorded a device error."""
+        capi.sync(self.h, _stream_ptr(stream))
 
     def autotune(self, reps: int = 3) -> dict:
         """Time the candidate decompositions on the current cameras and keep

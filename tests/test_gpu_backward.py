@@ -178,3 +178,37 @@ def test_empty_view_gradient_is_zero(geometry):
     torch.cuda.synchronize()
     assert float(gn.abs().max()) == 0.0 and float(gt.abs().max()) == 0.0
     r.close()
+
+
+def test_backward_is_stream_ordered_and_graph_capturable():
+    """After the first call for a camera (which finds the sizes of its pair
+    space and hit lists), the adjoint enqueues its work without waiting: it is
+    captured in a CUDA graph, and replays of the graph give the gradient of a
+    direct call (atomic sums: equal up to their order); ocr_sync reports no
+    device error."""
+    from paper_1809_01334_gb300 import Renderer
+    integ = {"method": "dopri5", "tol": 1e-6, "c_rk": 0.5, "max_depth": 16}
+    f, tf, cam = _setup("adaptive", integ, w=40, h=30)
+    r = Renderer(f, tf, integ)
+    r.set_camera(cam)
+    W = torch.from_numpy(np.random.default_rng(7).uniform(-1, 1, (cam.h, cam.w, 4))
+                         .astype(np.float32)).cuda()
+    gn, gt = r.backward(W)  # the first call plans (blocking)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        r.backward(W, check=False)  # warm-up on the capture stream
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        gn_c, gt_c = r.backward(W, check=False)
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    r.sync()
+    a, b = gn.cpu().numpy(), gn_c.cpu().numpy()
+    assert np.abs(a - b).max() <= 1e-5 * max(np.abs(a).max(), 1e-30)
+    a, b = gt.cpu().numpy(), gt_c.cpu().numpy()
+    assert np.abs(a - b).max() <= 1e-5 * max(np.abs(a).max(), 1e-30)
+    r.close()

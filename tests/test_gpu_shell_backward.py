@@ -137,3 +137,33 @@ def test_c5_full_size_gradient_on_sampled_rows():
     gradcheck.check(gn.cpu().numpy(), rn, "nodal", max_frac=1e-4, abs_frac=2e-3)
     gradcheck.check(gt.cpu().numpy(), rt, "knots", max_frac=0.1, abs_frac=2e-3)
     r.close()
+
+
+def test_shell_backward_is_graph_capturable():
+    """The shell adjoint enqueues its work without waiting (its list sizes
+    come from the camera's plan): captured in a CUDA graph, its replays give
+    the gradient of a direct call (atomic sums: equal up to their order)."""
+    from paper_1809_01334_gb300 import Renderer
+    f, tf, _ = I.preset_shell_small()
+    cam = I.perspective_camera(21, 40, 30, dist=(2.2, 2.6), target=(0.0, 0.0, 0.0))
+    r = Renderer(f, tf, DOPRI)
+    r.set_camera(cam)
+    W = torch.from_numpy(np.random.default_rng(9).uniform(-1, 1, (cam.h, cam.w, 4))
+                         .astype(np.float32)).cuda()
+    gn, gt = r.backward(W)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        r.backward(W, check=False)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        gn_c, gt_c = r.backward(W, check=False)
+    graph.replay()
+    graph.replay()
+    torch.cuda.synchronize()
+    r.sync()
+    for a, b in ((gn.cpu().numpy(), gn_c.cpu().numpy()), (gt.cpu().numpy(), gt_c.cpu().numpy())):
+        assert np.abs(a - b).max() <= 1e-5 * max(np.abs(a).max(), 1e-30)
+    r.close()
