@@ -516,11 +516,14 @@ __device__ __forceinline__ float4 step_adjoint(float Tm, float4 Gm, float4 Ib, f
 // The steps of one segment, revisited far to near with the forward's step
 // tree: near transmittance Tn, far aggregate G (with the background folded in
 // through bg), the segment's own transmittance Aseg.
-template <class SA>
+// METHOD: the integrator (Integ::method: 0 RK4, 1 Dormand-Prince, 2 Gauss-2,
+// 3 Simpson, 4 the Eq. 2.18 interface), a template parameter so that each
+// kernel holds the registers of its own step adjoint only.
+template <int METHOD, class SA>
 __device__ void segment_steps_bwd(SA &S, const TF &tf, float dx, const Integ &I, float Tn,
                                   float4 G, float Aseg, float4 Ib, float ab, TfGrad &tg) {
   float4 acc = seg_identity();  // steps farther than the current one
-  if (I.method == 0) {
+  if constexpr (METHOD == 0) {
     const int n = I.nsteps;
     const float H = dx / (float)n, dt = 1.f / (float)n;
     for (int s = 0; s < n; ++s) {
@@ -539,7 +542,7 @@ __device__ void segment_steps_bwd(SA &S, const TF &tf, float dx, const Integ &I,
   unsigned idx = 0;
   float4 kq0 = S.kq(tf, 0.f);
   const float4 one = seg_identity();
-  if (I.method != 1) {  // the closed forms inside Algorithm 1 (c_RK test alone)
+  if constexpr (METHOD != 1) {  // the closed forms inside Algorithm 1 (c_RK test alone)
     for (;;) {
       const float dtau = ldexpf(1.f, -depth);
       const float t0 = (float)idx * dtau;
@@ -549,7 +552,7 @@ __device__ void segment_steps_bwd(SA &S, const TF &tf, float dx, const Integ &I,
       float kmax, A = 0.f, sa = 0.f;
       const float ta = fmaf(0.21132486540518713f, dtau, t0);
       const float tb = fmaf(0.78867513459481287f, dtau, t0);
-      if (I.method == 2) {
+      if constexpr (METHOD == 2) {
         g0 = S.kq(tf, ta);
         g1 = S.kq(tf, tb);
         const float a1 = 0.25f * H * (g0.x + g1.x), a2 = (H * H / 12.f) * g0.x * g1.x;
@@ -564,7 +567,7 @@ __device__ void segment_steps_bwd(SA &S, const TF &tf, float dx, const Integ &I,
         kh = S.kq(tf, t0 + 0.5f * dtau);
         kq1 = S.kq(tf, t0 + dtau);
         const float e = -(H / 6.f) * (kq0.x + 4.f * kh.x + kq1.x);
-        if (I.method == 4) {
+        if constexpr (METHOD == 4) {
           const float om = -expm1f(e);
           A = 1.f - om;
           Sv = make_float4(A, kh.y * om, kh.z * om, kh.w * om);
@@ -587,10 +590,10 @@ __device__ void segment_steps_bwd(SA &S, const TF &tf, float dx, const Integ &I,
       const float Tm = Tn * (Aseg / accn.x);
       const float4 Gm = seg_combine(acc, G);
       const float4 yb = step_adjoint(Tm, Gm, Ib, ab, I.bg);
-      if (I.method == 2)
+      if constexpr (METHOD == 2)
         gauss2_step_bwd(S, tf, ta, tb, H, g0, g1, Sv, yb, tg);
       else
-        simpson_step_bwd(S, tf, I.method == 4, t0, dtau, H, kq0, kh, kq1, A, sa, yb, tg);
+        simpson_step_bwd(S, tf, METHOD == 4, t0, dtau, H, kq0, kh, kq1, A, sa, yb, tg);
       acc = accn;
       kq0 = kq1;
       ++idx;
@@ -664,6 +667,7 @@ __device__ void segment_steps_bwd(SA &S, const TF &tf, float dx, const Integ &I,
 
 // Adjoint of one segment of a cube leaf: near transmittance T, far aggregate
 // G, its value A_seg; the adjoints of the leaf's 8 nodal values into g8.
+template <int METHOD>
 __device__ void segment_bwd(const Topo &T, const Field &Fd, const Cam &c, const Integ &I,
                             const TF &tf, int leaf, float3 org, float3 dir, float3 inv,
                             float scale, float Tn, float4 G, float Aseg, float4 Ib, float ab,
@@ -684,7 +688,7 @@ __device__ void segment_bwd(const Topo &T, const Field &Fd, const Cam &c, const 
   S.cu = field_cubic(Fd.nodal + 8 * (size_t)leaf, S.uf, S.du);
 #pragma unroll
   for (int q = 0; q < 8; ++q) S.g8[q] = 0.f;
-  segment_steps_bwd(S, tf, dx, I, Tn, G, Aseg, Ib, ab, tg);
+  segment_steps_bwd<METHOD>(S, tf, dx, I, Tn, G, Aseg, Ib, ab, tg);
 #pragma unroll
   for (int q = 0; q < 8; ++q) g8[q] = S.g8[q];
 }
@@ -866,7 +870,7 @@ __global__ void __launch_bounds__(kSegThreads)
 // the segment's own (rec_ta) and the aggregate of the farther ones (rec_g).
 // Rays without an image adjoint are skipped.  Geometry-free.
 __global__ void __launch_bounds__(256)
-    ray_scans_kernel(Cam c, const float4 *dL, const long long *ray_off,
+    ray_scans_kernel(Cam c, const float4 *dL, const long long *ray_off, const int *count,
                      const unsigned long long *keys, const unsigned *kpos, long long key_cap,
                      int cap, float2 *rec_ta, float4 *rec_g, unsigned long long *err) {
   extern __shared__ __align__(16) unsigned char s_raw[];
@@ -885,7 +889,7 @@ __global__ void __launch_bounds__(256)
   int bad = 0;
   for (long long pix = (long long)blockIdx.x * nw + wid; pix < npix; pix += nwarp) {
     const long long h0 = ray_off[pix];
-    const int n = (int)(ray_off[pix + 1] - h0);
+    const int n = count ? count[pix] : (int)(ray_off[pix + 1] - h0);
     if (n == 0) continue;
     if (n > cap || h0 + n > key_cap) {
       if (lane == 0) ++bad;
@@ -993,6 +997,7 @@ __device__ __forceinline__ void leaf_group_flush(const float *s_rows, int leaf, 
 // adjoints with the near transmittance and far aggregate of pass 2, through
 // the trilinear weights; the 8 nodal adjoints summed over the warp's lanes of
 // the same leaf (the list keeps a leaf's segments together).  Cube leaves.
+template <int METHOD>
 __global__ void __launch_bounds__(kSegThreads, 4)
     cube_seg_adjoint_kernel(Topo T, Field Fd, Cam c, Integ I, const float4 *dL, const int2 *lm,
                             const float2 *rec_ta, const float4 *rec_g, long long nseg,
@@ -1027,7 +1032,7 @@ __global__ void __launch_bounds__(kSegThreads, 4)
             make_float3(recip_or_zero(dir.x), recip_or_zero(dir.y), recip_or_zero(dir.z));
         const float2 ta = rec_ta[e];
         float g8[8];
-        segment_bwd(T, Fd, c, I, tf, m.y, org, dir, inv, scale, ta.x, rec_g[e], ta.y,
+        segment_bwd<METHOD>(T, Fd, c, I, tf, m.y, org, dir, inv, scale, ta.x, rec_g[e], ta.y,
                     make_float4(gp.x, gp.y, gp.z, 0.f), gp.w, g8, tg);
 #pragma unroll
         for (int q = 0; q < 8; ++q) s_g8[q * kSegStride + tid] = g8[q];
@@ -1045,6 +1050,7 @@ __global__ void __launch_bounds__(kSegThreads, 4)
 // The same for shell leaves: the field through the inverse map and the
 // degree-2 weights; the 27 nodal adjoints go to this thread's column of the
 // shared array directly.  Rays without an image adjoint are skipped.
+template <int METHOD>
 __global__ void __launch_bounds__(kSegThreads, 4)
     shell_seg_adjoint_kernel(const int4 *__restrict__ geo, int N, Shell S, Field Fd, Cam c,
                              Integ I, const float4 *dL, const int2 *lm, const float2 *rec_ta,
@@ -1087,7 +1093,7 @@ __global__ void __launch_bounds__(kSegThreads, 4)
             A.g27 = g27;
             A.stride = kSegStride;
             const float2 ta = rec_ta[e];
-            segment_steps_bwd(A, tf, dx, I, ta.x, rec_g[e], ta.y,
+            segment_steps_bwd<METHOD>(A, tf, dx, I, ta.x, rec_g[e], ta.y,
                               make_float4(gp.x, gp.y, gp.z, 0.f), gp.w, tg);
             leaf = lf;
           }
@@ -1222,16 +1228,16 @@ cudaError_t bwd_scans_prepare() {
 }
 
 cudaError_t bwd_ray_scans(const Cam &C, const float4 *dL, const long long *ray_off,
-                          const unsigned long long *keys, const unsigned *kpos, long long key_cap,
-                          int cap, float2 *rec_ta, float4 *rec_g, unsigned long long *err,
-                          int nsm, cudaStream_t st) {
+                          const int *count, const unsigned long long *keys, const unsigned *kpos,
+                          long long key_cap, int cap, float2 *rec_ta, float4 *rec_g,
+                          unsigned long long *err, int nsm, cudaStream_t st) {
   if (cap < 32 || cap > kShellMaxCap || (cap & (cap - 1))) return cudaErrorInvalidValue;
   const int warps = scans_warps(cap);
   const long long npix = (long long)C.w * C.h;
   const long long need = (npix + warps - 1) / warps;
   const long long grid = need < (long long)nsm * 8 ? need : (long long)nsm * 8;
   ray_scans_kernel<<<(unsigned)(grid > 0 ? grid : 1), warps * 32, bwd_scans_smem(cap), st>>>(
-      C, dL, ray_off, keys, kpos, key_cap, cap, rec_ta, rec_g, err);
+      C, dL, ray_off, count, keys, kpos, key_cap, cap, rec_ta, rec_g, err);
   return cudaGetLastError();
 }
 
@@ -1241,8 +1247,20 @@ cudaError_t bwd_cube_adjoint(const Topo &T, const Field &Fd, const Cam &C, const
                              const unsigned long long *ncount, float *g_nodal, float *g_tf,
                              int nsm, cudaStream_t st) {
   if (nseg <= 0) return cudaSuccess;
-  cube_seg_adjoint_kernel<<<seg_grid(nseg, nsm, 16), kSegThreads, 0, st>>>(
-      T, Fd, C, I, dL, lm, rec_ta, rec_g, nseg, ncount, g_nodal, g_tf);
+  const unsigned g = seg_grid(nseg, nsm, 16);
+  switch (I.method) {  // one kernel per integrator
+    case 0: cube_seg_adjoint_kernel<0><<<g, kSegThreads, 0, st>>>(
+                T, Fd, C, I, dL, lm, rec_ta, rec_g, nseg, ncount, g_nodal, g_tf); break;
+    case 1: cube_seg_adjoint_kernel<1><<<g, kSegThreads, 0, st>>>(
+                T, Fd, C, I, dL, lm, rec_ta, rec_g, nseg, ncount, g_nodal, g_tf); break;
+    case 2: cube_seg_adjoint_kernel<2><<<g, kSegThreads, 0, st>>>(
+                T, Fd, C, I, dL, lm, rec_ta, rec_g, nseg, ncount, g_nodal, g_tf); break;
+    case 3: cube_seg_adjoint_kernel<3><<<g, kSegThreads, 0, st>>>(
+                T, Fd, C, I, dL, lm, rec_ta, rec_g, nseg, ncount, g_nodal, g_tf); break;
+    case 4: cube_seg_adjoint_kernel<4><<<g, kSegThreads, 0, st>>>(
+                T, Fd, C, I, dL, lm, rec_ta, rec_g, nseg, ncount, g_nodal, g_tf); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
@@ -1251,8 +1269,20 @@ cudaError_t bwd_shell_adjoint(const int4 *geo, int N, const Shell &S, const Fiel
                               const float2 *rec_ta, const float4 *rec_g, long long nseg,
                               float *g_nodal, float *g_tf, int nsm, cudaStream_t st) {
   if (nseg <= 0) return cudaSuccess;
-  shell_seg_adjoint_kernel<<<seg_grid(nseg, nsm, 16), kSegThreads, 0, st>>>(
-      geo, N, S, Fd, C, I, dL, lm, rec_ta, rec_g, nseg, g_nodal, g_tf);
+  const unsigned g = seg_grid(nseg, nsm, 16);
+  switch (I.method) {  // one kernel per integrator
+    case 0: shell_seg_adjoint_kernel<0><<<g, kSegThreads, 0, st>>>(
+                geo, N, S, Fd, C, I, dL, lm, rec_ta, rec_g, nseg, g_nodal, g_tf); break;
+    case 1: shell_seg_adjoint_kernel<1><<<g, kSegThreads, 0, st>>>(
+                geo, N, S, Fd, C, I, dL, lm, rec_ta, rec_g, nseg, g_nodal, g_tf); break;
+    case 2: shell_seg_adjoint_kernel<2><<<g, kSegThreads, 0, st>>>(
+                geo, N, S, Fd, C, I, dL, lm, rec_ta, rec_g, nseg, g_nodal, g_tf); break;
+    case 3: shell_seg_adjoint_kernel<3><<<g, kSegThreads, 0, st>>>(
+                geo, N, S, Fd, C, I, dL, lm, rec_ta, rec_g, nseg, g_nodal, g_tf); break;
+    case 4: shell_seg_adjoint_kernel<4><<<g, kSegThreads, 0, st>>>(
+                geo, N, S, Fd, C, I, dL, lm, rec_ta, rec_g, nseg, g_nodal, g_tf); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -1233,7 +1233,7 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
     const float4 *dL = reinterpret_cast<const float4 *>(d_dL_drgba);
     OCR_CUDA(bwd_shell_values(F->d_geo, F->N, F->shell, Fd, P.cam, F->integ, dL, F->d_slm,
                               P.nhits, F->d_srg, F->d_err, F->nsm, st));
-    OCR_CUDA(bwd_ray_scans(P.cam, dL, P.d_ray_off, P.d_keys, F->d_skpos, P.nhits, P.cap,
+    OCR_CUDA(bwd_ray_scans(P.cam, dL, P.d_ray_off, nullptr, P.d_keys, F->d_skpos, P.nhits, P.cap,
                            F->d_srta, F->d_srg, F->d_err, F->nsm, st));
     OCR_CUDA(bwd_shell_adjoint(F->d_geo, F->N, F->shell, Fd, P.cam, F->integ, dL, F->d_slm,
                                F->d_srta, F->d_srg, P.nhits, d_grad_nodal, d_grad_tf, F->nsm,
@@ -1271,8 +1271,9 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
   }
   const float4 *dL = reinterpret_cast<const float4 *>(d_dL_drgba);
   if (!P0.bwd_ready) {
-    // the sizes of the pair space and of the hit lists depend on the camera
-    // alone: found once, blocking the host twice, with every ray counted
+    // the sizes of the pair space and of the hit lists, and the lists' layout
+    // (every ray's hits, an exclusive prefix in d_ray_off), depend on the
+    // camera alone: found once, blocking the host twice
     OCR_CUDA(launch_cull_leaves(T, cam, S, st));
     OCR_CUDA(bwd_leaf_scan(T, P0.d_rect, F->d_bsums, F->bsums_cap, F->d_leaf_off, st));
     long long *h = F->h_group_slots + F->h_group_nodes.size();  // pinned scratch
@@ -1315,14 +1316,9 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
   OCR_CUDA(bwd_leaf_scan(T, P0.d_rect, F->d_bsums, F->bsums_cap, F->d_leaf_off, st));
   OCR_CUDA(bwd_chunk_map(F->d_leaf_off, F->N, F->d_pchunk, st));
 
-  // hits per ray (rays without an image adjoint skipped), their offsets, then
-  // the hit lists (mirrored Morton keys) and the leaf-grouped list, within the
-  // planned capacity of every ray's hits
-  OCR_CUDA(cudaMemsetAsync(F->d_rcount, 0, sizeof(int) * (size_t)npix, st));
-  OCR_CUDA(bwd_pair_hits(0, T, cam, P0.d_rect, F->d_leaf_off, F->d_pchunk, npairs, dL,
-                         F->d_rcount, nullptr, nullptr, F->d_mkey, F->fx, nullptr, nullptr,
-                         nullptr, nullptr, 0, nullptr, st));
-  OCR_CUDA(bwd_count_scan(F->d_rcount, npix, F->d_bsums, F->bsums_cap, F->d_ray_off, st));
+  // the hit lists (mirrored Morton keys) of the rays with an image adjoint,
+  // each in its place of the camera's list layout (every ray's hits, from the
+  // plan), and the leaf-grouped list
   OCR_CUDA(cudaMemsetAsync(F->d_rcursor, 0, sizeof(int) * (size_t)npix, st));
   OCR_CUDA(cudaMemsetAsync(F->d_lmcount, 0, sizeof(unsigned long long), st));
   OCR_CUDA(bwd_pair_hits(2, T, cam, P0.d_rect, F->d_leaf_off, F->d_pchunk, npairs, dL, nullptr,
@@ -1332,8 +1328,8 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
   // segment values, per-ray scans, segment adjoints over the entries written
   OCR_CUDA(bwd_cube_values(T, Fd, cam, F->integ, F->d_slm, nh, F->d_lmcount, F->d_srg, F->nsm,
                            st));
-  OCR_CUDA(bwd_ray_scans(cam, dL, F->d_ray_off, F->d_hkey, F->d_skpos, nh, P0.bwd_cap,
-                         F->d_srta, F->d_srg, F->d_err, F->nsm, st));
+  OCR_CUDA(bwd_ray_scans(cam, dL, F->d_ray_off, F->d_rcursor, F->d_hkey, F->d_skpos, nh,
+                         P0.bwd_cap, F->d_srta, F->d_srg, F->d_err, F->nsm, st));
   OCR_CUDA(bwd_cube_adjoint(T, Fd, cam, F->integ, dL, F->d_slm, F->d_srta, F->d_srg, nh,
                             F->d_lmcount, d_grad_nodal, d_grad_tf, F->nsm, st));
   OCR_CUDA(bwd_fold_errors(F->d_err, F->d_stats + kStatErrors, st));

@@ -199,16 +199,18 @@ cudaError_t bwd_shell_values(const int4 *geo, int N, const Shell &S, const Field
                              long long nseg, float4 *val, unsigned long long *err, int nsm,
                              cudaStream_t st);
 // Scans: one warp per ray, lists of up to cap entries (a power of two,
-// 32..kShellMaxCap; longer lists are counted in err): the values gathered from
-// rec_g by the list indices in kpos, then per entry the near transmittance and
-// own transmittance into rec_ta and the far aggregate into rec_g.
+// 32..kShellMaxCap; longer lists are counted in err) starting at ray_off[pix],
+// count[pix] entries long (count null: up to ray_off[pix + 1]): the values
+// gathered from rec_g by the list indices in kpos, then per entry the near
+// transmittance and own transmittance into rec_ta and the far aggregate into
+// rec_g.
 // bwd_scans_prepare raises the kernel's shared-memory limit for every cap.
 size_t bwd_scans_smem(int cap);
 cudaError_t bwd_scans_prepare();
 cudaError_t bwd_ray_scans(const Cam &C, const float4 *dL, const long long *ray_off,
-                          const unsigned long long *keys, const unsigned *kpos, long long key_cap,
-                          int cap, float2 *rec_ta, float4 *rec_g, unsigned long long *err,
-                          int nsm, cudaStream_t st);
+                          const int *count, const unsigned long long *keys, const unsigned *kpos,
+                          long long key_cap, int cap, float2 *rec_ta, float4 *rec_g,
+                          unsigned long long *err, int nsm, cudaStream_t st);
 // Adjoint: one thread per entry; nodal adjoints summed over a warp's lanes of
 // the same leaf, then accumulated into g_nodal, the knot adjoints into g_tf.
 cudaError_t bwd_cube_adjoint(const Topo &T, const Field &Fd, const Cam &C, const Integ &I,

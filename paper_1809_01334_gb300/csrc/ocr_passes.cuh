@@ -514,7 +514,6 @@ __device__ __forceinline__ void coarsen_chunk(const Topo &T, const Field &Fd, co
     float4 cs[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const int id = ch[q];
       float4 s = seg_identity();
       if ((lhit >> q) & 1u) s = s_seg[q][tid];
       else if (e[q] >= 0) s = ldw<COH>(S.entries + e[q]);
