@@ -39,7 +39,6 @@ struct CamPlan {
   long long *d_leaf_off = nullptr;    // [N + 1]
   long long *d_sbsums = nullptr;      // [bs_cap]
   int *d_pchunk = nullptr;            // [npairs / kPairChunk + 2]
-  unsigned *d_pmask = nullptr;        // [npairs / kPairChunk + 1] x 8: pairs that hit
   int *d_rcount = nullptr, *d_rcursor = nullptr;  // [npix]
   long long *d_ray_off = nullptr;     // [npix + 1]
   unsigned long long *d_keys = nullptr;  // [nhits]
@@ -187,7 +186,7 @@ int dev_alloc(T **p, size_t n, int64_t &bytes) {
 // free one plan's device scratch (its camera and sizes stay)
 void free_plan_buffers(ocr_forest *F, CamPlan &P) {
   void *bufs[] = {P.d_rect, P.d_off, P.d_bsums, P.d_gslots, P.d_chunk, P.d_entries, P.d_leaf_off,
-                  P.d_sbsums, P.d_pchunk, P.d_pmask, P.d_rcount, P.d_rcursor, P.d_ray_off,
+                  P.d_sbsums, P.d_pchunk, P.d_rcount, P.d_rcursor, P.d_ray_off,
                   P.d_keys};
   for (void *b : bufs) cudaFree(b);
   P.d_rect = nullptr;
@@ -199,7 +198,6 @@ void free_plan_buffers(ocr_forest *F, CamPlan &P) {
   P.d_leaf_off = nullptr;
   P.d_sbsums = nullptr;
   P.d_pchunk = nullptr;
-  P.d_pmask = nullptr;
   P.d_rcount = nullptr;
   P.d_rcursor = nullptr;
   P.d_ray_off = nullptr;
@@ -437,15 +435,12 @@ int plan_shell(ocr_forest *F, CamPlan &P) {
   OCR_CUDA(cudaMemcpyAsync(h, P.d_leaf_off + F->N, sizeof(long long), cudaMemcpyDeviceToHost, ps));
   OCR_CUDA(cudaStreamSynchronize(ps));
   P.npairs = h[0];
-  if ((rc = dev_alloc(&P.d_pchunk, (size_t)(P.npairs / kPairChunk + 2), F->bytes)) ||
-      (rc = dev_alloc(&P.d_pmask, (size_t)(P.npairs / kPairChunk + 1) * (kPairChunk / 32),
-                      F->bytes)))
-    return rc;
+  if ((rc = dev_alloc(&P.d_pchunk, (size_t)(P.npairs / kPairChunk + 2), F->bytes))) return rc;
   OCR_CUDA(bwd_chunk_map(P.d_leaf_off, F->N, P.d_pchunk, ps));
   OCR_CUDA(cudaMemsetAsync(P.d_rcount, 0, sizeof(int) * (size_t)npix, ps));
   OCR_CUDA(shell_pairs(0, F->d_geo, F->N, F->shell, P.cam, P.d_rect, P.d_leaf_off,
                        P.d_pchunk, P.npairs, P.d_rcount, nullptr, nullptr, nullptr, 0,
-                       F->d_stats, P.d_pmask, ps));
+                       F->d_stats, nullptr, ps));
   OCR_CUDA(bwd_count_scan(P.d_rcount, npix, P.d_sbsums, P.bs_cap, P.d_ray_off, ps));
   OCR_CUDA(cudaMemcpyAsync(h, P.d_ray_off + npix, sizeof(long long), cudaMemcpyDeviceToHost, ps));
   OCR_CUDA(cudaMemcpyAsync(h + 1, F->d_stats + kStatMaxHits, sizeof(long long),
@@ -460,8 +455,10 @@ int plan_shell(ocr_forest *F, CamPlan &P) {
 }
 
 // Enqueue the segment lists of one camera of a shell forest on st: pruning,
-// pair space, counts, list offsets, lists (for the adjoint also the
-// leaf-grouped list, into F's adjoint buffers).  No host synchronisation.
+// pair space, then one pass that intersects every pair and writes each
+// segment into its ray's list, laid out by the camera's plan (every ray's
+// segment count; for the adjoint also the leaf-grouped list, into F's adjoint
+// buffers).  No host synchronisation.
 int enqueue_shell_lists(ocr_forest *F, CamPlan &P, unsigned char *visible, cudaStream_t st,
                         bool adjoint = false) {
   const long long npix = P.npix;
@@ -469,22 +466,17 @@ int enqueue_shell_lists(ocr_forest *F, CamPlan &P, unsigned char *visible, cudaS
   OCR_CUDA(shell_cull(F->d_geo, F->N, F->shell, P.cam, P.d_rect, visible, F->d_stats, st));
   OCR_CUDA(bwd_leaf_scan(T, P.d_rect, P.d_sbsums, P.bs_cap, P.d_leaf_off, st));
   OCR_CUDA(bwd_chunk_map(P.d_leaf_off, F->N, P.d_pchunk, st));
-  OCR_CUDA(cudaMemsetAsync(P.d_rcount, 0, sizeof(int) * (size_t)npix, st));
-  OCR_CUDA(shell_pairs(0, F->d_geo, F->N, F->shell, P.cam, P.d_rect, P.d_leaf_off,
-                       P.d_pchunk, P.npairs, P.d_rcount, nullptr, nullptr, nullptr, 0, nullptr,
-                       P.d_pmask, st));
-  OCR_CUDA(bwd_count_scan(P.d_rcount, npix, P.d_sbsums, P.bs_cap, P.d_ray_off, st));
   OCR_CUDA(cudaMemsetAsync(P.d_rcursor, 0, sizeof(int) * (size_t)npix, st));
   if (adjoint) {
     OCR_CUDA(cudaMemsetAsync(F->d_lmcount, 0, sizeof(unsigned long long), st));
     OCR_CUDA(shell_pairs(2, F->d_geo, F->N, F->shell, P.cam, P.d_rect, P.d_leaf_off,
                          P.d_pchunk, P.npairs, nullptr, P.d_ray_off, P.d_rcursor, P.d_keys,
-                         P.nhits, F->d_stats, P.d_pmask, st, F->d_skpos, F->d_slm,
+                         P.nhits, F->d_stats, nullptr, st, F->d_skpos, F->d_slm,
                          F->d_lmcount));
   } else {
     OCR_CUDA(shell_pairs(1, F->d_geo, F->N, F->shell, P.cam, P.d_rect, P.d_leaf_off,
                          P.d_pchunk, P.npairs, nullptr, P.d_ray_off, P.d_rcursor, P.d_keys,
-                         P.nhits, F->d_stats, P.d_pmask, st));
+                         P.nhits, F->d_stats, nullptr, st));
   }
   return OCR_OK;
 }
@@ -1092,9 +1084,9 @@ int render_plans(ocr_forest *F, int first, int K, float *d_rgba, void *stream,
       stats->subtree_rk_steps = (int64_t)h[kStatSteps];
       stats->subtree_node_visits = (int64_t)h[kStatTests];
       stats->visible_leaves = (int64_t)h[kStatVisible];
-      if (F->geometry == OCR_GEOM_SHELL) {  // two passes over every (leaf, pixel) pair
+      if (F->geometry == OCR_GEOM_SHELL) {  // one pass over every (leaf, pixel) pair
         int64_t pairs = 0;
-        for (int k = 0; k < K; ++k) pairs += 2 * plans[k].npairs;
+        for (int k = 0; k < K; ++k) pairs += plans[k].npairs;
         stats->leaf_tests = pairs;
         stats->subtree_node_visits = 0;
         stats->slots = 0;

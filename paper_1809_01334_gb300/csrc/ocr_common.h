@@ -230,11 +230,12 @@ cudaError_t shell_monomials(const float *nodal, float *coef, int N, cudaStream_t
 cudaError_t shell_cull(const int4 *geo, int N, const Shell &S, const Cam &C, int4 *rect,
                        unsigned char *visible, unsigned long long *stats, cudaStream_t st);
 // mode 0, the count pass: segments per ray into counts, which pairs hit into
-// hitmask (one bit per pair, [ceil(npairs / kPairChunk) * kPairChunk / 32]
-// words), and, when stats is given, the longest list into
-// stats[kStatMaxHits]; mode 1, the fill pass over the pairs that hit (the
-// count pass's mask): the keys, at most key_cap of them (a list that would
-// pass key_cap is a device error); mode 2: the fill pass that also appends
+// hitmask when it is given (one bit per pair, [ceil(npairs / kPairChunk) *
+// kPairChunk / 32] words), and, when stats is given, the longest list into
+// stats[kStatMaxHits]; mode 1, the fill pass: every pair intersected, each
+// segment's key written at ray_off[pixel] + its place among the ray's
+// segments (through cursor), at most key_cap of them and within the ray's
+// list (more is a device error); mode 2: the fill pass that also appends
 // every segment to the leaf-grouped list lm (pixel, 2 leaf + piece) through
 // the counter *lm_count (zeroed by the caller) and stores its index there in
 // kpos beside the key

@@ -159,12 +159,13 @@ __global__ void __launch_bounds__(256)
 }
 
 // ------------------------------------------------------- segment lists --
-// MODE 0 counts segments per ray and records which pairs hit (one ballot word
-// per warp in hitmask); MODE 1 writes the keys, intersecting only the pairs
-// that hit (packed to the CTA's first threads, in pair order); MODE 2 also
-// appends every segment to a list grouped by leaf (one global append per CTA,
-// whose pairs are consecutive in leaf order): lm[pos] = (pixel, 2 leaf +
-// piece), and kpos[at] = pos beside the key, for the adjoint.
+// MODE 0 counts segments per ray (and records which pairs hit, one ballot
+// word per warp, when hitmask is given); MODE 1 writes each segment's key into
+// its ray's list at ray_off (the camera's plan) plus its place among the
+// ray's segments; MODE 2 also appends every segment to a list grouped by leaf
+// (one global append per CTA, whose pairs are consecutive in leaf order):
+// lm[pos] = (pixel, 2 leaf + piece), and kpos[at] = pos beside the key, for
+// the adjoint.  Every mode intersects every pair of the CTA's chunk.
 template <int MODE>
 __global__ void __launch_bounds__(kPairChunk)
     shell_pairs_kernel(const int4 *__restrict__ geo, int N, Shell S, Cam c,
@@ -176,35 +177,11 @@ __global__ void __launch_bounds__(kPairChunk)
                        unsigned long long *lm_count) {
   constexpr int NW = kPairChunk / 32;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int t = threadIdx.x;  // the chunk's pair this thread intersects
-  bool has = true;
-  if (MODE != 0) {
-    __shared__ unsigned short s_idx[kPairChunk];
-    __shared__ int s_h[NW + 1];
-    const unsigned word = hitmask[(size_t)blockIdx.x * NW + wid];
-    if (lane == 0) s_h[wid] = __popc(word);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int tot = 0;
-      for (int w = 0; w < NW; ++w) {
-        const int h = s_h[w];
-        s_h[w] = tot;
-        tot += h;
-      }
-      s_h[NW] = tot;
-    }
-    __syncthreads();
-    if ((word >> lane) & 1u)
-      s_idx[s_h[wid] + __popc(word & ((1u << lane) - 1u))] = (unsigned short)threadIdx.x;
-    __syncthreads();
-    has = (int)threadIdx.x < s_h[NW];
-    t = has ? s_idx[threadIdx.x] : 0;
-  }
-  const long long p = (long long)blockIdx.x * kPairChunk + t;
+  const long long p = (long long)blockIdx.x * kPairChunk + threadIdx.x;  // this thread's pair
   int n = 0, leaf = 0;
   long long pix = 0;
   float ai[2], ao[2];
-  if (has && p < npairs) {
+  if (p < npairs) {
     const long long nch = (npairs + kPairChunk - 1) / kPairChunk;
     int lo = chunk_leaf[blockIdx.x];
     int hi = (blockIdx.x + 1 < nch) ? chunk_leaf[blockIdx.x + 1] + 1 : N;
@@ -225,7 +202,7 @@ __global__ void __launch_bounds__(kPairChunk)
   }
   if (MODE == 0) {
     const unsigned bal = __ballot_sync(0xffffffffu, n > 0);
-    if (lane == 0) hitmask[(size_t)blockIdx.x * NW + wid] = bal;
+    if (hitmask && lane == 0) hitmask[(size_t)blockIdx.x * NW + wid] = bal;
     if (n) atomicAdd(counts + pix, n);
     return;
   }
@@ -485,7 +462,7 @@ cudaError_t shell_pairs(int mode, const int4 *geo, int N, const Shell &S, const 
                         unsigned long long *keys, long long key_cap, unsigned long long *stats,
                         unsigned *hitmask, cudaStream_t st, unsigned *kpos, int2 *lm,
                         unsigned long long *lm_count) {
-  if (mode < 0 || mode > 2 || !hitmask || (mode == 2 && (!kpos || !lm || !lm_count)))
+  if (mode < 0 || mode > 2 || (mode == 2 && (!kpos || !lm || !lm_count)))
     return cudaErrorInvalidValue;
   if (npairs > 0) {
     const long long nblk = (npairs + kPairChunk - 1) / kPairChunk;
