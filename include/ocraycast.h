@@ -291,6 +291,20 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
  * else OCR_OK.  Blocks the host.  Not a step of the paper's method. */
 int ocr_sync(ocr_forest *F, void *stream);
 
+/* The per-ray merge of the shell render, on one list the caller gives: n
+ * segments in order of entry along the ray, d_val [n*4] float32 (A, B_r, B_g,
+ * B_b) and d_iv [n*2] float32 (alpha_in, alpha_out), combined nearest first
+ * with Eq. 2.14; where consecutive segments overlap, the pieces before, inside
+ * and after each overlap are cut with Eq. 2.20 and the overlapped pieces
+ * averaged with Eq. 2.21 (Sec. 2.5).  The result (A, B_r, B_g, B_b) goes to
+ * d_out [4] float32.  Device pointers (d_val and d_out 16-byte, d_iv 8-byte
+ * aligned), 1 <= n <= 2^20, else OCR_ERR_INVALID; stream-ordered, no forest
+ * needed.  It runs the device function the shell render uses, so that the
+ * overlap handling (rounding slivers only, in a valid forest) can be checked
+ * on lists with real overlaps. */
+int ocr_fold_segments(const float *d_val, const float *d_iv, int n, float *d_out,
+                      void *stream);
+
 /* Tuning of the render's decomposition (the batching autotuner's knobs):
  *   tile_depth  cube forests: how many octree levels (1..3) one CTA merges in
  *               shared memory before per-(node, ray) aggregates go to HBM; the

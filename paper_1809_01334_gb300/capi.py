@@ -20,7 +20,7 @@ RK4, DOPRI5, GAUSS2, SIMPSON, EQUILIBRIUM = 0, 1, 2, 3, 4
 EXPORTS = ["ocr_build_forest", "ocr_forest_set_data", "ocr_set_integrator", "ocr_set_camera",
            "ocr_render", "ocr_render_view", "ocr_render_host", "ocr_render_backward",
            "ocr_set_tuning", "ocr_get_tuning", "ocr_autotune", "ocr_prune_noalloc",
-           "ocr_device_bytes", "ocr_destroy", "ocr_strerror", "ocr_sync"]
+           "ocr_device_bytes", "ocr_destroy", "ocr_strerror", "ocr_sync", "ocr_fold_segments"]
 
 
 class ForestDesc(C.Structure):
@@ -280,6 +280,15 @@ def render_backward(h, d_dL_drgba, d_grad_nodal, d_grad_tf, stream=None):
     fn.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     _check(fn(h, _ptr(d_dL_drgba), _ptr(d_grad_nodal), _ptr(d_grad_tf), _ptr(stream)),
            "ocr_render_backward")
+
+
+def fold_segments(d_val, d_iv, d_out, stream=None):
+    """ocr_fold_segments: the shell's per-ray merge (Eq. 2.14; cut and average of
+    overlaps, Eqs. 2.20-2.21) of one list: d_val [n, 4], d_iv [n, 2] -> d_out [4]."""
+    fn = lib().ocr_fold_segments
+    fn.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
+    _check(fn(_ptr(d_val), _ptr(d_iv), int(d_val.shape[0]), _ptr(d_out), _ptr(stream)),
+           "ocr_fold_segments")
 
 
 def sync(h, stream=None):

@@ -1328,6 +1328,17 @@ int ocr_render_backward(ocr_forest *F, const float *d_dL_drgba, float *d_grad_no
   return OCR_OK;
 }
 
+int ocr_fold_segments(const float *d_val, const float *d_iv, int n, float *d_out,
+                      void *stream) {
+  if (!d_val || !d_iv || !d_out || n < 1 || n > (1 << 20)) return OCR_ERR_INVALID;
+  if (((uintptr_t)d_val & 15) || ((uintptr_t)d_iv & 7) || ((uintptr_t)d_out & 15))
+    return OCR_ERR_INVALID;
+  OCR_CUDA(shell_fold_segments(reinterpret_cast<const float4 *>(d_val),
+                               reinterpret_cast<const float2 *>(d_iv), n,
+                               reinterpret_cast<float4 *>(d_out), (cudaStream_t)stream));
+  return OCR_OK;
+}
+
 int ocr_sync(ocr_forest *F, void *stream) {
   if (!F) return OCR_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;

@@ -253,6 +253,10 @@ constexpr int kShellMaxCap = 4096;
 int shell_ray_warps(int cap, int want);
 size_t shell_ray_smem(int cap, int want);
 cudaError_t shell_rays_prepare();
+// the shell's per-ray merge (Eq. 2.14, cut and average of overlaps) of one
+// list of n segments (values, intervals in order of entry) into *out
+cudaError_t shell_fold_segments(const float4 *val, const float2 *iv, int n, float4 *out,
+                                cudaStream_t st);
 // every ray's list sorted in place by its key (before shell_rays)
 cudaError_t shell_sort_lists(const long long *ray_off, long long npix, unsigned long long *keys,
                              long long key_cap, int cap, int nsm, cudaStream_t st);

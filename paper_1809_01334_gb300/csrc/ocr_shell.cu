@@ -286,6 +286,54 @@ __device__ float4 resolve_overlap(float4 N, float2 in, float4 F, float2 iF) {
   return r;
 }
 
+// The merge of one ray's n segments (values val, intervals iv, in order of
+// entry depth) by the warp: nearest first with Eq. 2.14; where consecutive
+// segments overlap (rounding slivers), the pieces before, inside and after
+// each overlap are cut (Eq. 2.20) and the overlapped ones averaged (Eq.
+// 2.21).  The result in lane 0.
+__device__ float4 fold_ray_segments(const float4 *val, const float2 *iv, int n, int lane) {
+  bool ov = false;
+  for (int k = lane; k + 1 < n; k += 32) ov |= iv[k + 1].x < iv[k].y;
+  float4 acc = seg_identity();
+  if (!__any_sync(0xffffffffu, ov)) {
+    // lane l folds a contiguous run, then the runs are combined in order
+    const int q = (n + 31) >> 5, k0 = lane * q, k1 = min(k0 + q, n);
+    for (int k = k0; k < k1; ++k) acc = seg_combine(acc, val[k]);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      float4 y;
+      y.x = __shfl_down_sync(0xffffffffu, acc.x, o);
+      y.y = __shfl_down_sync(0xffffffffu, acc.y, o);
+      y.z = __shfl_down_sync(0xffffffffu, acc.z, o);
+      y.w = __shfl_down_sync(0xffffffffu, acc.w, o);
+      if ((lane & (2 * o - 1)) == 0) acc = seg_combine(acc, y);
+    }
+  } else if (lane == 0) {
+    float4 cur = val[0];
+    float2 ci = iv[0];
+    for (int k = 1; k < n; ++k) {
+      const float4 nv = val[k];
+      const float2 ni = iv[k];
+      if (ni.x < ci.y) {
+        cur = resolve_overlap(cur, ci, nv, ni);
+        ci = make_float2(ci.x, fmaxf(ci.y, ni.y));
+      } else {
+        acc = seg_combine(acc, cur);
+        cur = nv;
+        ci = ni;
+      }
+    }
+    acc = seg_combine(acc, cur);
+  }
+  return acc;
+}
+
+// One caller-given list through fold_ray_segments (one warp).
+__global__ void fold_segments_kernel(const float4 *val, const float2 *iv, int n, float4 *out) {
+  const float4 acc = fold_ray_segments(val, iv, n, threadIdx.x);
+  if (threadIdx.x == 0) *out = acc;
+}
+
 // Sorts every ray's list in place by its key (entry depth, then tree and
 // Morton key through the leaf index): one warp per ray, in registers for lists
 // of up to 512 keys, else bitonic in shared memory (cap keys per warp).
@@ -384,39 +432,7 @@ __global__ void __launch_bounds__(256, 2)
     segs += n;
     __syncwarp();
     // overlaps of consecutive segments are rounding slivers, if any
-    bool ov = false;
-    for (int k = lane; k + 1 < n; k += 32) ov |= iv[k + 1].x < iv[k].y;
-    float4 acc = seg_identity();
-    if (!__any_sync(0xffffffffu, ov)) {
-      // lane l folds a contiguous run, then the runs are combined in order
-      const int q = (n + 31) >> 5, k0 = lane * q, k1 = min(k0 + q, n);
-      for (int k = k0; k < k1; ++k) acc = seg_combine(acc, val[k]);
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        float4 y;
-        y.x = __shfl_down_sync(0xffffffffu, acc.x, o);
-        y.y = __shfl_down_sync(0xffffffffu, acc.y, o);
-        y.z = __shfl_down_sync(0xffffffffu, acc.z, o);
-        y.w = __shfl_down_sync(0xffffffffu, acc.w, o);
-        if ((lane & (2 * o - 1)) == 0) acc = seg_combine(acc, y);
-      }
-    } else if (lane == 0) {
-      float4 cur = val[0];
-      float2 ci = iv[0];
-      for (int k = 1; k < n; ++k) {
-        const float4 nv = val[k];
-        const float2 ni = iv[k];
-        if (ni.x < ci.y) {
-          cur = resolve_overlap(cur, ci, nv, ni);
-          ci = make_float2(ci.x, fmaxf(ci.y, ni.y));
-        } else {
-          acc = seg_combine(acc, cur);
-          cur = nv;
-          ci = ni;
-        }
-      }
-      acc = seg_combine(acc, cur);
-    }
+    const float4 acc = fold_ray_segments(val, iv, n, lane);
     if (lane == 0)
       rgba[pix] = make_float4(fmaf(acc.x, bg[0], acc.y), fmaf(acc.x, bg[1], acc.z),
                               fmaf(acc.x, bg[2], acc.w), 1.f - acc.x);
@@ -453,6 +469,13 @@ cudaError_t shell_cull(const int4 *geo, int N, const Shell &S, const Cam &C, int
                        unsigned char *visible, unsigned long long *stats, cudaStream_t st) {
   const int grid = (N + 255) / 256 > 8192 ? 8192 : (N + 255) / 256;
   shell_cull_kernel<<<grid > 0 ? grid : 1, 256, 0, st>>>(geo, N, S, C, rect, visible, stats);
+  return cudaGetLastError();
+}
+
+cudaError_t shell_fold_segments(const float4 *val, const float2 *iv, int n, float4 *out,
+                                cudaStream_t st) {
+  if (n < 1 || !val || !iv || !out) return cudaErrorInvalidValue;
+  fold_segments_kernel<<<1, 32, 0, st>>>(val, iv, n, out);
   return cudaGetLastError();
 }
 
