@@ -52,6 +52,11 @@ struct RayCount {
   const int *cnt;
   __device__ long long operator()(long long k) const { return (long long)cnt[k]; }
 };
+struct ListedLeafArea {  // the rectangle areas of the leaves listed in ids
+  const int4 *rect;
+  const int *ids;
+  __device__ long long operator()(long long k) const { return area_of(rect[ids[k]]); }
+};
 
 __device__ long long block_excl_scan(long long v, long long *wt, long long &total) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1114,6 +1119,11 @@ __global__ void __launch_bounds__(kSegThreads, 4)
 cudaError_t bwd_leaf_scan(const Topo &T, const int4 *rect, long long *bs, long long bs_cap,
                           long long *leaf_off, cudaStream_t st) {
   return exclusive_scan(LeafArea{rect}, (long long)T.N, bs, bs_cap, leaf_off, st);
+}
+
+cudaError_t listed_leaf_scan(const int4 *rect, const int *ids, long long n, long long *bs,
+                             long long bs_cap, long long *off, cudaStream_t st) {
+  return exclusive_scan(ListedLeafArea{rect, ids}, n, bs, bs_cap, off, st);
 }
 
 cudaError_t bwd_count_scan(const int *counts, long long n, long long *bs, long long bs_cap,

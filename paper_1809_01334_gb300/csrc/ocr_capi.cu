@@ -33,6 +33,12 @@ struct CamPlan {
   long long *d_gslots = nullptr;      // [L + 1]
   int *d_chunk = nullptr;             // [total / kGroup + 2]
   float4 *d_entries = nullptr;        // [total slots]
+  // cube, top-down merge: the slots of the leaves at or above the tile level
+  long long ctotal = 0;               // their slots (rectangle areas)
+  long long *d_coff = nullptr;        // [nc + 1] exclusive prefix of their areas
+  long long *d_cbsums = nullptr;      // [bwd_scan_blocks(nc) + 2] block sums of that scan
+  int *d_cgroup = nullptr;            // [ctotal / kGroup + 2] their slot map
+  float4 *d_cval = nullptr;           // [ctotal] their (leaf, ray) segments
   // shell forests: the (leaf, pixel) pair space and the per-ray segment lists
   long long npairs = 0, nhits = 0, bs_cap = 0;
   int cap = 0;                        // longest list found, rounded up to a power of two
@@ -68,6 +74,11 @@ struct ocr_forest {
   int *d_child = nullptr;             // [(M + 1) * 8]
   int2 *d_leaves = nullptr;           // [M] leaf range of each internal node
   int lt = 0;                         // tile level: deepest level with stored aggregates
+  // cube: every leaf's level (host), and the leaves at or above the tile level
+  std::vector<uint8_t> h_leaf_level;
+  int nc = 0;                         // those leaves
+  int *d_cids = nullptr;              // [nc] their ids, Morton order
+  int *d_cindex = nullptr;            // [N] a leaf's place among them, -1 for the others
   int *d_group_nodes = nullptr;       // [L + 1]
   // data
   const float *d_nodal = nullptr;
@@ -98,8 +109,9 @@ struct ocr_forest {
   int nbseg = 0, nbcam = 0;
   long long nbtickets = 0;
   bool batch_ready = false;
-  long long *h_group_slots = nullptr; // pinned [L + 1 + kStats + 1] (shell [kStats + 3]); last
-                                      // word: ocr_sync's
+  long long *h_group_slots = nullptr; // pinned [L + 1 + kStats + 2] (shell [kStats + 3]); at
+                                      // L + 1 + kStats: ocr_sync's word, then the cube
+                                      // plan's listed-leaf slot total
   unsigned long long *d_stats = nullptr;  // [kStats]
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // start, layout, subtree, end
   // adjoint
@@ -187,8 +199,12 @@ int dev_alloc(T **p, size_t n, int64_t &bytes) {
 void free_plan_buffers(ocr_forest *F, CamPlan &P) {
   void *bufs[] = {P.d_rect, P.d_off, P.d_bsums, P.d_gslots, P.d_chunk, P.d_entries, P.d_leaf_off,
                   P.d_sbsums, P.d_pchunk, P.d_rcount, P.d_rcursor, P.d_ray_off,
-                  P.d_keys};
+                  P.d_keys, P.d_coff, P.d_cbsums, P.d_cgroup, P.d_cval};
   for (void *b : bufs) cudaFree(b);
+  P.d_coff = nullptr;
+  P.d_cbsums = nullptr;
+  P.d_cgroup = nullptr;
+  P.d_cval = nullptr;
   P.d_rect = nullptr;
   P.d_off = nullptr;
   P.d_bsums = nullptr;
@@ -243,6 +259,8 @@ void free_all(ocr_forest *F) {
   cudaFree(F->d_hrgba);
   if (F->copy_st) cudaStreamDestroy(F->copy_st);
   if (F->copy_ev) cudaEventDestroy(F->copy_ev);
+  cudaFree(F->d_cids);
+  cudaFree(F->d_cindex);
   cudaFree(F->d_err);
   cudaFree(F->d_bseg);
   cudaFree(F->d_bcam);
@@ -411,6 +429,36 @@ int build_shell(const ocr_forest_desc *desc, cudaStream_t st, ocr_forest **out) 
 
 int plan_cameras(ocr_forest *F);
 int plan_batch(ocr_forest *F);
+
+// The leaves at or above the tile level of a cube forest (their ids in Morton
+// order, and every leaf's place among them), whose segments the top-down
+// merge takes from a pass of their own; rebuilt when the tile level changes.
+// Blocks the host on st until the copies are done.
+int build_listed_leaves(ocr_forest *F, cudaStream_t st) {
+  if (F->d_cids) F->bytes -= (int64_t)sizeof(int) * ((F->nc > 0 ? F->nc : 1) + (int64_t)F->N);
+  cudaFree(F->d_cids);
+  cudaFree(F->d_cindex);
+  F->d_cids = nullptr;
+  F->d_cindex = nullptr;
+  std::vector<int> ids, index((size_t)F->N, -1);
+  for (int k = 0; k < F->N; ++k)
+    if ((int)F->h_leaf_level[(size_t)k] <= F->lt) {
+      index[(size_t)k] = (int)ids.size();
+      ids.push_back(k);
+    }
+  F->nc = (int)ids.size();
+  int rc;
+  if ((rc = dev_alloc(&F->d_cids, ids.empty() ? 1 : ids.size(), F->bytes)) ||
+      (rc = dev_alloc(&F->d_cindex, (size_t)F->N, F->bytes)))
+    return rc;
+  if (!ids.empty())
+    OCR_CUDA(cudaMemcpyAsync(F->d_cids, ids.data(), sizeof(int) * ids.size(),
+                             cudaMemcpyHostToDevice, st));
+  OCR_CUDA(cudaMemcpyAsync(F->d_cindex, index.data(), sizeof(int) * index.size(),
+                           cudaMemcpyHostToDevice, st));
+  OCR_CUDA(cudaStreamSynchronize(st));  // the host vectors die on return
+  return OCR_OK;
+}
 
 // Plan one camera of a shell forest: its pruning and pair space, the segment
 // count of every ray, the size of the lists and the longest one.  Runs on the
@@ -672,7 +720,7 @@ int ocr_build_forest(const ocr_forest_desc *desc, void *stream, ocr_forest **out
     }
   }
   if (cudaMallocHost((void **)&F->h_group_slots,
-                     sizeof(long long) * (F->h_group_nodes.size() + kStats + 1)) !=
+                     sizeof(long long) * (F->h_group_nodes.size() + kStats + 2)) !=
       cudaSuccess) {
     F->h_group_slots = nullptr;
     free_all(F);
@@ -700,6 +748,12 @@ int ocr_build_forest(const ocr_forest_desc *desc, void *stream, ocr_forest **out
     free_all(F);
     delete F;
     return cuda_fail(e);
+  }
+  F->h_leaf_level.assign(desc->h_level, desc->h_level + N);
+  if ((rc = build_listed_leaves(F, st))) {
+    free_all(F);
+    delete F;
+    return rc;
   }
   *out = F;
   return OCR_OK;
@@ -817,13 +871,24 @@ int plan_cameras(ocr_forest *F) {
                                   S, ps));
     OCR_CUDA(launch_area_scan(T, S, P.d_bsums, F->bsums_blocks, P.d_gslots, F->d_group_nodes, G,
                               ps));
+    // the listed leaves' slots (the top-down merge's own pass)
+    const long long cbs = bwd_scan_blocks(F->nc) + 2;
+    if ((rc = dev_alloc(&P.d_coff, (size_t)F->nc + 1, F->bytes)) ||
+        (rc = dev_alloc(&P.d_cbsums, (size_t)cbs, F->bytes)))
+      return rc;
+    OCR_CUDA(listed_leaf_scan(P.d_rect, F->d_cids, F->nc, P.d_cbsums, cbs, P.d_coff, ps));
     OCR_CUDA(cudaMemcpyAsync(F->h_group_slots, P.d_gslots, sizeof(long long) * G,
                              cudaMemcpyDeviceToHost, ps));
+    OCR_CUDA(cudaMemcpyAsync(F->h_group_slots + G + kStats + 1, P.d_coff + F->nc,
+                             sizeof(long long), cudaMemcpyDeviceToHost, ps));
     OCR_CUDA(cudaStreamSynchronize(ps));
     P.gslots.assign(F->h_group_slots, F->h_group_slots + G);
+    P.ctotal = F->h_group_slots[G + kStats + 1];
     const long long total = P.gslots[G - 1];
     if ((rc = dev_alloc(&P.d_chunk, (size_t)(total / kGroup + 2), F->bytes)) ||
-        (rc = dev_alloc(&P.d_entries, (size_t)(total > 0 ? total : 1), F->bytes)))
+        (rc = dev_alloc(&P.d_entries, (size_t)(total > 0 ? total : 1), F->bytes)) ||
+        (rc = dev_alloc(&P.d_cgroup, (size_t)(P.ctotal / kGroup + 2), F->bytes)) ||
+        (rc = dev_alloc(&P.d_cval, (size_t)(P.ctotal > 0 ? P.ctotal : 1), F->bytes)))
       return rc;
   }
   return plan_batch(F);
@@ -946,6 +1011,13 @@ int enqueue_camera(ocr_forest *F, CamPlan &P, float4 *rgba, int *counts, unsigne
   launches += area_scan_blocks(F->M) > 0 ? 4 : 1;
   OCR_CUDA(launch_chunk_map(T, S, P.gslots[G - 1], st));
   launches += F->M > 0;
+  const CoarseLeaves CL{F->d_cids, F->d_cindex, P.d_coff, P.d_cgroup, P.d_cval, F->nc, P.ctotal};
+  if (F->merge == 1) {  // the listed leaves' slots (as planned)
+    OCR_CUDA(listed_leaf_scan(P.d_rect, F->d_cids, F->nc, P.d_cbsums, bwd_scan_blocks(F->nc) + 2,
+                              P.d_coff, st));
+    OCR_CUDA(launch_coarse_leaf_map(CL, st));
+    launches += 4;
+  }
   // the passes below read the field: with host data, wait for its copy here
   // (the pruning and layout above overlap it)
   if (F->data_ready) OCR_CUDA(cudaStreamWaitEvent(st, F->data_ready, 0));
@@ -970,9 +1042,11 @@ int enqueue_camera(ocr_forest *F, CamPlan &P, float4 *rgba, int *counts, unsigne
     ++launches;
   }
   // the super-root pass writes every pixel
-  if (F->merge == 1)
-    OCR_CUDA(launch_topdown(T, Fd, P.cam, F->integ, S, P.npix, rgba, F->nsm, st));
-  else
+  if (F->merge == 1) {
+    OCR_CUDA(launch_coarse_leaves(T, Fd, P.cam, F->integ, S, CL, st));
+    OCR_CUDA(launch_topdown(T, P.cam, F->integ, S, CL, P.npix, rgba, st));
+    ++launches;
+  } else
     OCR_CUDA(launch_coarsen(T, Fd, P.cam, F->integ, S, F->M, F->M, 0, P.npix, rgba, st));
   ++launches;
   return OCR_OK;
@@ -1370,6 +1444,11 @@ int ocr_set_tuning(ocr_forest *F, const ocr_tuning *t) {
   if (t->tile_depth != F->tile_depth) {
     F->tile_depth = t->tile_depth;
     F->lt = F->L > F->tile_depth ? F->L - F->tile_depth : 0;
+    if (F->geometry == OCR_GEOM_CUBE) {
+      if (!F->plan_st) OCR_CUDA(cudaStreamCreateWithFlags(&F->plan_st, cudaStreamNonBlocking));
+      const int rc = build_listed_leaves(F, F->plan_st);
+      if (rc) return rc;
+    }
     if (F->has_cam && F->geometry == OCR_GEOM_CUBE) {
       F->has_cam = false;
       const int rc = plan_cameras(F);  // also rebuilds the batch queue

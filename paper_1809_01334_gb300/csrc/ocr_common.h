@@ -121,10 +121,31 @@ cudaError_t launch_subtree(const Topo &T, const Field &Fd, const Cam &C, const I
 cudaError_t launch_coarsen(const Topo &T, const Field &Fd, const Cam &C, const Integ &I, Scratch S,
                            int node_begin, int node_end, long long slot_begin, long long slot_end,
                            float4 *rgba, cudaStream_t stream);
+// The leaves at or above the tile level (level <= lt) of a cube forest, for
+// the top-down merge: their (leaf, ray) segments are formed by one pass of
+// their own, one slot per pixel of each listed leaf's rectangle.
+struct CoarseLeaves {
+  const int *ids;        // [n] the listed leaves, in Morton order
+  const int *index;      // [N] a leaf's place in ids, -1 for the others
+  long long *off;        // [n + 1] exclusive prefix of their rectangle areas (per render)
+  int *group;            // [ceil(total / kGroup) + 1] listed leaf holding slot g * kGroup
+  float4 *val;           // [total] (A, B) of each (leaf, ray) slot, the identity where the
+                         // ray misses the leaf
+  int n;
+  long long total;       // slots (the plan's; every render has the same)
+};
+// the slot map of the listed leaves (after their offsets)
+cudaError_t launch_coarse_leaf_map(const CoarseLeaves &CL, cudaStream_t stream);
+// the listed leaves' segments, one thread per slot; the segment counts of
+// S.counts and the coarse counters of S.counters
+cudaError_t launch_coarse_leaves(const Topo &T, const Field &Fd, const Cam &C, const Integ &I,
+                                 Scratch S, const CoarseLeaves &CL, cudaStream_t stream);
 // the levels above the tile level and the pixels in one pass: one thread per
-// pixel walks the octree top-down (instead of the per-level coarsen passes)
-cudaError_t launch_topdown(const Topo &T, const Field &Fd, const Cam &C, const Integ &I, Scratch S,
-                           long long npix, float4 *rgba, int nsm, cudaStream_t stream);
+// pixel walks the octree top-down, combining the tile-level aggregates and
+// the listed leaves' segments (instead of the per-level coarsen passes)
+cudaError_t launch_topdown(const Topo &T, const Cam &C, const Integ &I, Scratch S,
+                           const CoarseLeaves &CL, long long npix, float4 *rgba,
+                           cudaStream_t stream);
 
 // Persistent multi-camera render of a cube forest (ocr_batch.cu).  The work
 // queue is a list of segments, one per (pipeline stage, camera), in queue
@@ -168,6 +189,10 @@ cudaError_t bwd_count_scan(const int *counts, long long n, long long *bs, long l
                            long long *ray_off, cudaStream_t st);
 long long bwd_scan_blocks(long long n);
 cudaError_t bwd_chunk_map(const long long *leaf_off, int N, int *chunk_leaf, cudaStream_t st);
+// exclusive prefix of the rectangle areas of the leaves ids[0..n) into off
+// [n + 1] (bs: block sums, [bwd_scan_blocks(n) + 1] at least)
+cudaError_t listed_leaf_scan(const int4 *rect, const int *ids, long long n, long long *bs,
+                             long long bs_cap, long long *off, cudaStream_t st);
 // mode 0: hits per ray into counts (rays with a zero image adjoint skipped;
 // dL null: every ray);
 // mode 2: each hit's mirrored Morton key into its ray's list, and the hit

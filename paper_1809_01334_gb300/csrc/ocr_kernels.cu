@@ -178,26 +178,15 @@ __global__ void __launch_bounds__(kCoarsenThreads, 8)
   coarsen_chunk<FINAL, SURF, false>(T, Fd, c, I, S, nb, ne, s0, s1, blockIdx.x, rgba, sm);
 }
 
-// Top-down merge of the levels above the tile level, one thread per pixel:
-// the octree is walked from the tree root in the ray's front-to-back order of
-// octants (bit q ^ flip, flip the direction's sign bits).  At each internal
-// node above the tile level the children the ray meets come from one
-// child_hits (the children's exact slab tests); a leaf among them whose pixel
-// rectangle holds the pixel gives its segment, a tile-level node its (node,
-// ray) aggregate of the subtree pass, an internal node is descended into.
-// The contributions are combined nearest first (Eq. 2.14): the result of the
-// per-level passes up to rounding order (Eq. 2.14 is associative), in one
-// launch and without intermediate aggregates in HBM.  A node the ray misses
-// holds nothing the ray meets (nested boxes, monotone rounding), and a node
-// whose rectangle misses the pixel holds no leaf whose rectangle holds it, so
-// only the contributors' rectangles are checked.
-constexpr int kTopDownThreads = 128;
-
+// The segments of the leaves at or above the tile level, one thread per
+// (leaf, ray) slot of the listed leaves' rectangles: the slot's leaf (the
+// group's slot-map entry, a search past that leaf's end), pixel and ray; a
+// ray that meets the leaf (slab test) gets the leaf's segment, integrated as
+// in the other passes, else the identity.
 template <bool SURF>
-__global__ void __launch_bounds__(kTopDownThreads, 8)
-    topdown_kernel(Topo T, Field Fd, Cam c, Integ I, Scratch S, long long npix, float4 *rgba) {
+__global__ void __launch_bounds__(128)
+    coarse_leaves_kernel(Topo T, Field Fd, Cam c, Integ I, Scratch S, CoarseLeaves CL) {
   __shared__ float4 s_tfv[8], s_tfs[8];
-  extern __shared__ int2 s_stk[];  // [(lt + 1) * kTopDownThreads] ancestors: node, children left
   const int tid = threadIdx.x;
   if (tid < 8) {
     const float4 v = Fd.tf[tid];
@@ -208,92 +197,149 @@ __global__ void __launch_bounds__(kTopDownThreads, 8)
   __syncthreads();
   const TF tf{s_tfv, s_tfs, Fd.s_min, Fd.inv_ds7};
   const float scale = ldexpf(1.f, -T.L);
-  const long long pix = (long long)blockIdx.x * kTopDownThreads + tid;
-  unsigned nhit = 0, ntest = 0;
+  const long long slot = (long long)blockIdx.x * 128 + tid;
+  unsigned hit = 0;
   int steps = 0;
-  if (pix < npix) {
-    const int i = (int)(pix % c.w), j = (int)(pix / c.w);
+  if (slot < CL.total) {
+    int k = CL.group[slot / kGroup];
+    if (slot >= CL.off[k + 1]) {  // past the group's first leaf: the last k with off[k] <= slot
+      int lo = k + 1, hi = CL.n;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (CL.off[mid] <= slot) lo = mid + 1; else hi = mid;
+      }
+      k = lo - 1;
+    }
+    const int leaf = CL.ids[k];
+    const int4 r = S.rect[leaf];
+    const unsigned local = (unsigned)(slot - CL.off[k]);  // < w * h < 2^31
+    const unsigned rw = (unsigned)(r.y - r.x + 1), row = local / rw;
+    const int i = r.x + (int)(local - row * rw), j = r.z + (int)row;
     float3 org, dir;
     pixel_ray(c, i, j, org, dir);
     const float3 inv = make_float3(recip_or_zero(dir.x), recip_or_zero(dir.y), recip_or_zero(dir.z));
-    const unsigned flip =
-        (dir.x < 0.f ? 1u : 0u) | (dir.y < 0.f ? 2u : 0u) | (dir.z < 0.f ? 4u : 0u);
-    const int4 *child4 = reinterpret_cast<const int4 *>(T.child);
-    float4 acc = seg_identity();
-    // the super-root (internal index M, level -1): its one child is the tree root
-    int cur = T.M, lev = -1, gx = 0, gy = 0, gz = 0, d = 0;
-    int4 c0 = __ldg(child4 + 2 * T.M), c1 = __ldg(child4 + 2 * T.M + 1);
-    unsigned msk = 0u;
-    if (c0.x >= 0) {
-      const int4 g = __ldg(T.geo + c0.x);
-      float a0, a1;
-      if (slab(org, dir, inv, node_lo(g, scale), ldexpf(1.f, -g.w), c.amin, c.amax, a0, a1))
-        msk = 1u << flip;  // octant 0, mirrored
+    const int4 g = __ldg(T.geo + leaf);
+    float a0, a1;
+    float4 v = seg_identity();
+    if (slab(org, dir, inv, node_lo(g, scale), ldexpf(1.f, -g.w), c.amin, c.amax, a0, a1)) {
+      v = leaf_segment<SURF>(T, Fd, c, I, tf, leaf, org, dir, inv, scale, steps);
+      hit = 1;
+      if (S.counts) atomicAdd(S.counts + (size_t)j * c.w + i, 1);
     }
-    while (true) {
-      if (msk == 0u) {  // this node is done: back to its parent
-        if (d == 0) break;
-        --d;
-        --lev;
-        const int keep = ~((1 << (T.L - lev)) - 1);
-        gx &= keep;
-        gy &= keep;
-        gz &= keep;
-        const int2 e = s_stk[d * kTopDownThreads + tid];
-        cur = e.x;
-        msk = (unsigned)e.y;
-        c0 = __ldg(child4 + 2 * cur);
-        c1 = __ldg(child4 + 2 * cur + 1);
-        continue;
-      }
-      const int q = (__ffs(msk) - 1) ^ (int)flip;
-      msk &= msk - 1u;
-      const int id = pick_child(c0, c1, q);
-      if (id < 0) continue;
-      if (id < T.N || lev + 1 == T.lt) {
-        const int4 r = __ldg(S.rect + id);
-        if (i < r.x || i > r.y || j < r.z || j > r.w) continue;
-        if (id < T.N) {  // a leaf at or above the tile level: its segment
-          ++ntest;
-          acc = seg_combine(acc, leaf_segment<SURF>(T, Fd, c, I, tf, id, org, dir, inv, scale,
-                                                    steps));
-          ++nhit;
-        } else {  // a tile-level node: its aggregate
-          const long long e = __ldg(S.off + id - T.N) + (long long)(j - r.z) * (r.y - r.x + 1) +
-                              (i - r.x);
-          acc = seg_combine(acc, S.entries[e]);
-        }
-        continue;
-      }
-      // an internal node above the tile level
-      s_stk[d * kTopDownThreads + tid] = make_int2(cur, (int)msk);
-      ++d;
-      const int hs = 1 << (T.L - lev - 1);
-      gx += (q & 1) * hs;
-      gy += ((q >> 1) & 1) * hs;
-      gz += (q >> 2) * hs;
-      ++lev;
-      cur = id - T.N;
-      msk = child_hits(org, dir, inv, node_lo(make_int4(gx, gy, gz, 0), scale),
-                       ldexpf(1.f, -(lev + 1)), c.amin, c.amax, flip);
-      if (msk) {
-        c0 = __ldg(child4 + 2 * cur);
-        c1 = __ldg(child4 + 2 * cur + 1);
-      }
-    }
-    rgba[pix] = make_float4(fmaf(acc.x, I.bg[0], acc.y), fmaf(acc.x, I.bg[1], acc.z),
-                            fmaf(acc.x, I.bg[2], acc.w), kOne - acc.x);
-    if (nhit && S.counts) S.counts[pix] += nhit;  // after the subtree pass, in stream order
+    CL.val[slot] = v;
   }
-  // counters, when asked for: segments, RK steps and leaf tests above the tile level
-  if (S.counters) {
-    const unsigned v[3] = {nhit, (unsigned)steps, ntest};
+  if (S.counters) {  // segments, RK steps, slab tests above the tile level
+    const unsigned v[3] = {hit, (unsigned)steps, slot < CL.total ? 1u : 0u};
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       const unsigned x = __reduce_add_sync(0xffffffffu, v[q]);
       if ((tid & 31) == 0 && x) atomicAdd(S.counters + kStatCoarse + q, (unsigned long long)x);
     }
   }
+}
+
+// group[g] = the listed leaf whose slots hold slot g * kGroup
+__global__ void coarse_leaf_map_kernel(CoarseLeaves CL, long long ngroups) {
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < ngroups;
+       g += (long long)gridDim.x * blockDim.x) {
+    const long long slot = g * kGroup;
+    int lo = 0, hi = CL.n;
+    while (lo < hi) {  // first leaf whose offset exceeds the slot
+      const int mid = (lo + hi) >> 1;
+      if (CL.off[mid] <= slot) lo = mid + 1; else hi = mid;
+    }
+    CL.group[g] = lo - 1;
+  }
+}
+
+// Top-down merge of the levels above the tile level, one thread per pixel:
+// the octree is walked from the tree root in the ray's front-to-back order of
+// octants (bit q ^ flip, flip the direction's sign bits).  At each internal
+// node above the tile level the children the ray meets come from one
+// child_hits (the children's exact slab tests); a tile-level node whose pixel
+// rectangle holds the pixel contributes its (node, ray) aggregate of the
+// subtree pass, a leaf (at or above the tile level) whose rectangle holds it
+// its segment from the listed leaves' pass, and an internal node is descended
+// into.  The contributions are combined nearest first (Eq. 2.14): the result
+// of the per-level passes up to rounding order (Eq. 2.14 is associative), in
+// one launch and without intermediate aggregates in HBM.  A node the ray
+// misses holds nothing the ray meets (nested boxes, monotone rounding), and a
+// node whose rectangle misses the pixel holds no leaf whose rectangle holds
+// it, so only the contributors' rectangles are checked.
+constexpr int kTopDownThreads = 128;
+
+__global__ void __launch_bounds__(kTopDownThreads)
+    topdown_kernel(Topo T, Cam c, Integ I, Scratch S, CoarseLeaves CL, long long npix,
+                   float4 *rgba) {
+  extern __shared__ int2 s_stk[];  // [(lt + 1) * kTopDownThreads] ancestors: node, children left
+  const int tid = threadIdx.x;
+  const float scale = ldexpf(1.f, -T.L);
+  const long long pix = (long long)blockIdx.x * kTopDownThreads + tid;
+  if (pix >= npix) return;
+  const int i = (int)(pix % c.w), j = (int)(pix / c.w);
+  float3 org, dir;
+  pixel_ray(c, i, j, org, dir);
+  const float3 inv = make_float3(recip_or_zero(dir.x), recip_or_zero(dir.y), recip_or_zero(dir.z));
+  const unsigned flip = (dir.x < 0.f ? 1u : 0u) | (dir.y < 0.f ? 2u : 0u) | (dir.z < 0.f ? 4u : 0u);
+  const int4 *child4 = reinterpret_cast<const int4 *>(T.child);
+  float4 acc = seg_identity();
+  // the super-root (internal index M, level -1): its one child is the tree root
+  int cur = T.M, lev = -1, gx = 0, gy = 0, gz = 0, d = 0;
+  int4 c0 = __ldg(child4 + 2 * T.M), c1 = __ldg(child4 + 2 * T.M + 1);
+  unsigned msk = 0u;
+  if (c0.x >= 0) {
+    const int4 g = __ldg(T.geo + c0.x);
+    float a0, a1;
+    if (slab(org, dir, inv, node_lo(g, scale), ldexpf(1.f, -g.w), c.amin, c.amax, a0, a1))
+      msk = 1u << flip;  // octant 0, mirrored
+  }
+  while (true) {
+    if (msk == 0u) {  // this node is done: back to its parent
+      if (d == 0) break;
+      --d;
+      --lev;
+      const int keep = ~((1 << (T.L - lev)) - 1);
+      gx &= keep;
+      gy &= keep;
+      gz &= keep;
+      const int2 e = s_stk[d * kTopDownThreads + tid];
+      cur = e.x;
+      msk = (unsigned)e.y;
+      c0 = __ldg(child4 + 2 * cur);
+      c1 = __ldg(child4 + 2 * cur + 1);
+      continue;
+    }
+    const int q = (__ffs(msk) - 1) ^ (int)flip;
+    msk &= msk - 1u;
+    const int id = pick_child(c0, c1, q);
+    if (id < 0) continue;
+    if (id < T.N || lev + 1 == T.lt) {
+      const bool leaf = id < T.N;
+      const int4 r = __ldg(S.rect + id);
+      const long long o = leaf ? __ldg(CL.off + __ldg(CL.index + id)) : __ldg(S.off + id - T.N);
+      if (i < r.x || i > r.y || j < r.z || j > r.w) continue;
+      const long long e = o + (long long)(j - r.z) * (r.y - r.x + 1) + (i - r.x);
+      acc = seg_combine(acc, leaf ? CL.val[e] : S.entries[e]);
+      continue;
+    }
+    // an internal node above the tile level
+    s_stk[d * kTopDownThreads + tid] = make_int2(cur, (int)msk);
+    ++d;
+    const int hs = 1 << (T.L - lev - 1);
+    gx += (q & 1) * hs;
+    gy += ((q >> 1) & 1) * hs;
+    gz += (q >> 2) * hs;
+    ++lev;
+    cur = id - T.N;
+    msk = child_hits(org, dir, inv, node_lo(make_int4(gx, gy, gz, 0), scale),
+                     ldexpf(1.f, -(lev + 1)), c.amin, c.amax, flip);
+    if (msk) {
+      c0 = __ldg(child4 + 2 * cur);
+      c1 = __ldg(child4 + 2 * cur + 1);
+    }
+  }
+  rgba[pix] = make_float4(fmaf(acc.x, I.bg[0], acc.y), fmaf(acc.x, I.bg[1], acc.z),
+                          fmaf(acc.x, I.bg[2], acc.w), kOne - acc.x);
 }
 
 }  // namespace
@@ -380,18 +426,33 @@ cudaError_t launch_coarsen(const Topo &T, const Field &Fd, const Cam &C, const I
   return cudaGetLastError();
 }
 
-cudaError_t launch_topdown(const Topo &T, const Field &Fd, const Cam &C, const Integ &I, Scratch S,
-                           long long npix, float4 *rgba, int nsm, cudaStream_t stream) {
+cudaError_t launch_coarse_leaf_map(const CoarseLeaves &CL, cudaStream_t stream) {
+  const long long ngroups = (CL.total + kGroup - 1) / kGroup;
+  if (CL.n < 1 || ngroups < 1) return cudaSuccess;
+  coarse_leaf_map_kernel<<<grid_for(ngroups, 256), 256, 0, stream>>>(CL, ngroups);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_leaves(const Topo &T, const Field &Fd, const Cam &C, const Integ &I,
+                                 Scratch S, const CoarseLeaves &CL, cudaStream_t stream) {
+  if (CL.n < 1 || CL.total < 1) return cudaSuccess;
+  const long long need = (CL.total + 127) / 128;
+  if (need > 0x7fffffffll) return cudaErrorInvalidValue;
+  if (I.surface)  // isosurface segments (Sec. 2.8): a separate instantiation
+    coarse_leaves_kernel<true><<<(unsigned)need, 128, 0, stream>>>(T, Fd, C, I, S, CL);
+  else
+    coarse_leaves_kernel<false><<<(unsigned)need, 128, 0, stream>>>(T, Fd, C, I, S, CL);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_topdown(const Topo &T, const Cam &C, const Integ &I, Scratch S,
+                           const CoarseLeaves &CL, long long npix, float4 *rgba,
+                           cudaStream_t stream) {
   if (npix <= 0) return cudaSuccess;
   const long long need = (npix + kTopDownThreads - 1) / kTopDownThreads;
   if (need > 0x7fffffffll) return cudaErrorInvalidValue;
-  const unsigned g = (unsigned)need;
-  (void)nsm;
   const size_t stk = sizeof(int2) * kTopDownThreads * (size_t)(T.lt + 1);  // the walk's ancestors
-  if (I.surface)
-    topdown_kernel<true><<<g, kTopDownThreads, stk, stream>>>(T, Fd, C, I, S, npix, rgba);
-  else
-    topdown_kernel<false><<<g, kTopDownThreads, stk, stream>>>(T, Fd, C, I, S, npix, rgba);
+  topdown_kernel<<<(unsigned)need, kTopDownThreads, stk, stream>>>(T, C, I, S, CL, npix, rgba);
   return cudaGetLastError();
 }
 
