@@ -306,19 +306,20 @@ int ocr_fold_segments(const float *d_val, const float *d_iv, int n, float *d_out
                       void *stream);
 
 /* Tuning of the render's decomposition (the batching autotuner's knobs):
- *   tile_depth  cube forests: how many octree levels (1..3) one CTA merges in
- *               shared memory before per-(node, ray) aggregates go to HBM; the
- *               levels above are merged by one pass per level.  Deeper tiles
- *               mean fewer passes and more candidate leaves per CTA.
+ *   tile_depth  cube forests: how many octree levels (1..3) the subtree pass
+ *               walks per (tile node, ray) before the aggregates go to HBM.
+ *               Deeper tiles mean fewer levels above and longer walks.
  *   streams     internal streams (1..8) over which the cameras of a
  *               multi-camera render are spread.
  *   shell_warps shell forests: warps per CTA of the per-ray kernel (1..8;
  *               0 = as many as fit in 96 KB of shared memory).
  *   merge       cube forests: the levels above the tile level are merged by
- *               one pass per level over (node, ray) aggregates (0), or by one
- *               pass in which each pixel's thread walks those levels top-down
- *               in its front-to-back octant order (1).  Equal up to rounding
- *               order (Eq. 2.14 is associative).
+ *               one pass per level over (node, ray) aggregates (0), or (1) by
+ *               a pass that forms the segments of the leaves at or above the
+ *               tile level, one thread per (leaf, ray), and one pass in which
+ *               each pixel's thread walks those levels top-down in its
+ *               front-to-back octant order.  Equal up to rounding order (Eq.
+ *               2.14 is associative).
  *   persistent  cube forests, several cameras, merge 0, no surface: render
  *               the whole batch in one persistent kernel (1) -- its CTAs draw
  *               work items (a camera's pruning block, union block, prefix-sum
@@ -332,7 +333,7 @@ int ocr_fold_segments(const float *d_val, const float *d_iv, int n, float *d_out
  *               8); 6 and 7 select variants compiled for that many, with more
  *               registers per thread (1..5 use the one for 6).
  *   ms          ocr_autotune: the measured device time of one ocr_render.
- * Defaults: tile_depth 3, streams 4, shell_warps 0, merge 0, persistent 1,
+ * Defaults: tile_depth 3, streams 4, shell_warps 0, merge 1, persistent 1,
  * chunks_per_item 16, ctas_per_sm 0. */
 typedef struct {
   int tile_depth;

@@ -95,7 +95,7 @@ struct ocr_forest {
   int tile_depth = kSubtreeDepth;     // cube: octree levels aggregated inside one CTA
   int nstreams = 4;                   // internal streams of multi-camera renders
   int shell_warps = 0;                // shell: warps per CTA of the per-ray kernel (0: most)
-  int merge = 0;                      // cube: levels above the tile level by per-level passes
+  int merge = 1;                      // cube: levels above the tile level by the top-down pass
                                       // (0) or by one top-down pass per pixel (1)
   int persistent = 1;                 // cube, several cameras: one persistent kernel (1) or
                                       // per-camera kernel chains over the streams (0)

@@ -45,11 +45,13 @@ def test_batch_equals_single_renders_and_oracle():
     r.close()
 
 
-def test_batch_in_a_cuda_graph():
+@pytest.mark.parametrize("merge", [0, 1])  # 0: the persistent kernel; 1: kernel chains on streams
+def test_batch_in_a_cuda_graph(merge):
     from paper_1809_01334_gb300 import Renderer
     f, tf, _ = I.preset_small()
     r = Renderer(f, tf, INTEG)
     r.set_cameras(_cams())
+    r.set_tuning(merge=merge, persistent=1)
     nodal = r.nodal.clone()
     r.set_data(nodal, r.tf)
     out = torch.empty((r.batch_pixels(), 4), dtype=torch.float32, device="cuda")
@@ -169,10 +171,10 @@ def test_persistent_kernel_equals_the_stream_path(chunks, ctas):
     r = Renderer(f, tf, INTEG)
     r.set_cameras(cams)
     for depth in (1, 2, 3):
-        r.set_tuning(tile_depth=depth, streams=2, persistent=0)
+        r.set_tuning(tile_depth=depth, streams=2, persistent=0, merge=0)
         ref, _, sref = r.render_batch(with_index=True)
         ref = ref.clone()
-        r.set_tuning(tile_depth=depth, streams=2, persistent=1, chunks_per_item=chunks,
+        r.set_tuning(tile_depth=depth, streams=2, persistent=1, merge=0, chunks_per_item=chunks,
                      ctas_per_sm=ctas)
         out, _, st = r.render_batch(with_index=True)
         torch.cuda.synchronize()
@@ -194,6 +196,7 @@ def test_persistent_batch_of_the_large_forest_against_the_oracle():
     cams = I.batch_cameras(6, lo=48, ratio=4.0)
     r = Renderer(f, tf, integ)
     r.set_cameras(cams)
+    r.set_tuning(merge=0, persistent=1)  # the persistent kernel
     assert r.get_tuning()["persistent"] == 1
     flat, views, st = r.render_batch(with_index=True)
     torch.cuda.synchronize()
