@@ -306,7 +306,7 @@ int ocr_fold_segments(const float *d_val, const float *d_iv, int n, float *d_out
                       void *stream);
 
 /* Tuning of the render's decomposition (the batching autotuner's knobs):
- *   tile_depth  cube forests: how many octree levels (1..3) the subtree pass
+ *   tile_depth  cube forests: how many octree levels (1..4) the subtree pass
  *               walks per (tile node, ray) before the aggregates go to HBM.
  *               Deeper tiles mean fewer levels above and longer walks.
  *   streams     internal streams (1..8) over which the cameras of a
@@ -333,7 +333,7 @@ int ocr_fold_segments(const float *d_val, const float *d_iv, int n, float *d_out
  *               8); 6 and 7 select variants compiled for that many, with more
  *               registers per thread (1..5 use the one for 6).
  *   ms          ocr_autotune: the measured device time of one ocr_render.
- * Defaults: tile_depth 3, streams 4, shell_warps 0, merge 1, persistent 1,
+ * Defaults: tile_depth 4, streams 4, shell_warps 0, merge 1, persistent 1,
  * chunks_per_item 16, ctas_per_sm 0. */
 typedef struct {
   int tile_depth;
@@ -352,8 +352,8 @@ int ocr_set_tuning(ocr_forest *F, const ocr_tuning *t);
 int ocr_get_tuning(const ocr_forest *F, ocr_tuning *t);
 
 /* Autotuner: render the cameras, data and integrator last set under every
- * candidate tuning (cube: tile_depth 1..3 x merge {0, 1} x streams {1, 2, 4, 8},
- * and with several cameras the persistent kernel: tile_depth 1..3 x
+ * candidate tuning (cube: tile_depth 1..4 x merge {0, 1} x streams {1, 2, 4, 8},
+ * and with several cameras the persistent kernel: tile_depth 1..4 x
  * chunks_per_item {8, 16, 32} x ctas_per_sm {8, 7, 6}; shell:
  * shell_warps {1, 2, 4, 8} x streams; streams only with several cameras),
  * one warm-up and `reps` timed renders each (CUDA events on an internal

@@ -215,7 +215,7 @@ def _tuning_dict(t: Tuning) -> dict:
             "ctas_per_sm": t.ctas_per_sm, "ms": float(t.ms)}
 
 
-def set_tuning(h, tile_depth: int = 3, streams: int = 4, shell_warps: int = 0, merge: int = 1,
+def set_tuning(h, tile_depth: int = 4, streams: int = 4, shell_warps: int = 0, merge: int = 1,
                persistent: int = 1, chunks_per_item: int = 16, ctas_per_sm: int = 0):
     """ocr_set_tuning (a cube forest re-plans its cameras when tile_depth changes)."""
     t = Tuning(int(tile_depth), int(streams), int(shell_warps), int(merge), int(persistent),

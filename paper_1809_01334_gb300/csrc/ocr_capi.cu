@@ -92,7 +92,7 @@ struct ocr_forest {
   cudaStream_t plan_st = nullptr;     // ocr_set_camera's planning (created on first use)
   cudaEvent_t fork = nullptr, join[kMaxStreams] = {};
   // tuning (ocr_set_tuning / ocr_autotune)
-  int tile_depth = kSubtreeDepth;     // cube: octree levels aggregated inside one CTA
+  int tile_depth = kDefaultTileDepth; // cube: octree levels the subtree pass walks
   int nstreams = 4;                   // internal streams of multi-camera renders
   int shell_warps = 0;                // shell: warps per CTA of the per-ray kernel (0: most)
   int merge = 1;                      // cube: levels above the tile level by the top-down pass
@@ -689,7 +689,7 @@ int ocr_build_forest(const ocr_forest_desc *desc, void *stream, ocr_forest **out
       const int b = (int)(std::lower_bound(key.begin(), key.end(), k1) - key.begin());
       lrange[(size_t)F->level_base[l] + q] = make_int2(a, b);
     }
-  F->lt = L > kSubtreeDepth ? L - kSubtreeDepth : 0;
+  F->lt = L > F->tile_depth ? L - F->tile_depth : 0;
 
   // group boundaries: internal levels from the deepest, then M
   for (int l = L - 1; l >= 0; --l) F->h_group_nodes.push_back(F->level_base[l]);

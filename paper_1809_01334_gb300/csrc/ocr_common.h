@@ -48,12 +48,13 @@ struct Topo {
   int N, M, L, lt;
 };
 
-// Subtree pass: a ray crosses at most 3 * 2^D - 2 = 22 cells of a depth-3
-// subtree; the per-ray list holds 24 to leave room for rays running exactly
+// Subtree pass: a ray crosses at most 3 * 2^D - 2 = 46 cells of a depth-4
+// subtree; the per-ray list holds 48 to leave room for rays running exactly
 // along cell faces (closed slab tests accept both sides).  Overflow is counted
 // as a device error.
-constexpr int kSubtreeDepth = 3;
-constexpr int kMaxSubtreeHits = 24;
+constexpr int kSubtreeDepth = 4;
+constexpr int kMaxSubtreeHits = 48;
+constexpr int kDefaultTileDepth = 4;  // the tile depth of a new forest (1..kSubtreeDepth)
 
 struct Field {
   const float *nodal;  // [N * 8]

@@ -101,7 +101,7 @@ __device__ __forceinline__ void slot_lookup(const Topo &T, const Scratch &S, int
 //     rounding edge case: the pair is no candidate) gives no segment, and
 //  C. every lane folds its own ray's results nearest-first with Eq. 2.14.
 constexpr int kWarpBatch = 32;  // hits per warp batch of phase B
-static_assert(kSubtreeDepth <= 3, "the descent keeps two ancestors in registers");
+static_assert(kSubtreeDepth <= 4, "the descent keeps three ancestors in registers");
 
 // Shared memory of one subtree warp.
 struct SubtreeSmem {
@@ -110,8 +110,11 @@ struct SubtreeSmem {
   float4 res[kWarpBatch];            // phase B: segment values of a batch
   int2 pix[32];                      // pixel of each ray
   int drop[32];                      // hits outside the leaf's rectangle
-  int list[kMaxSubtreeHits][32];     // hits of each ray (leaf ids), in order
+  int first[32];                     // first leaf of each ray's tile node
+  unsigned short list[kMaxSubtreeHits][32];  // hits of each ray in order: leaf - first
 };
+// a tile node's subtree holds at most 8^kSubtreeDepth leaves
+static_assert(kSubtreeDepth <= 5, "list entries are 16-bit leaf offsets");
 
 // Child id of octant q from the node's 8 children held in two int4.
 __device__ __forceinline__ int pick_child(int4 c0, int4 c1, int q) {
@@ -186,7 +189,8 @@ __device__ __forceinline__ void subtree_warp(const Topo &T, const Field &Fd, con
   float4(&s_tfv)[8] = sm.tfv;
   float4(&s_tfs)[8] = sm.tfs;
   float(&s_ray)[6][32] = sm.ray;
-  int(&s_list)[kMaxSubtreeHits][32] = sm.list;
+  unsigned short(&s_list)[kMaxSubtreeHits][32] = sm.list;
+  int(&s_first)[32] = sm.first;
   float4(&s_res)[kWarpBatch] = sm.res;
   int2(&s_pix)[32] = sm.pix;
   int(&s_drop)[32] = sm.drop;
@@ -219,6 +223,8 @@ __device__ __forceinline__ void subtree_warp(const Topo &T, const Field &Fd, con
   s_ray[5][tid] = inv.z;
   s_pix[tid] = make_int2(i, j);
   s_drop[tid] = 0;
+  const int first = active ? __ldg(T.leaves + node).x : 0;  // the tile node's first leaf
+  s_first[tid] = first;
 
   __syncwarp();  // the transfer function table
 
@@ -238,8 +244,8 @@ __device__ __forceinline__ void subtree_warp(const Topo &T, const Field &Fd, con
     c0 = __ldg(child4 + 2 * cur);
     c1 = __ldg(child4 + 2 * cur + 1);
   }
-  int an0 = 0, an1 = 0;
-  unsigned am0 = 0, am1 = 0;
+  int an0 = 0, an1 = 0, an2 = 0;
+  unsigned am0 = 0, am1 = 0, am2 = 0;
   unsigned nhit = 0, nvisit = active ? 1u : 0u;
   bool deep = false;
   while (true) {
@@ -250,7 +256,7 @@ __device__ __forceinline__ void subtree_warp(const Topo &T, const Field &Fd, con
       id = pick_child(c0, c1, q);
       if (id >= T.N) break;
       if (id >= 0) {
-        if (nhit < (unsigned)kMaxSubtreeHits) s_list[nhit][tid] = id;
+        if (nhit < (unsigned)kMaxSubtreeHits) s_list[nhit][tid] = (unsigned short)(id - first);
         ++nhit;
       }
     }
@@ -262,24 +268,27 @@ __device__ __forceinline__ void subtree_warp(const Topo &T, const Field &Fd, con
       gx &= keep;
       gy &= keep;
       gz &= keep;
-      cur = d == 0 ? an0 : an1;
-      msk = d == 0 ? am0 : am1;
+      cur = d == 0 ? an0 : d == 1 ? an1 : an2;
+      msk = d == 0 ? am0 : d == 1 ? am1 : am2;
       if (msk) {
         c0 = __ldg(child4 + 2 * cur);
         c1 = __ldg(child4 + 2 * cur + 1);
       }
       continue;
     }
-    if (d >= 2) {  // below the subtree depth: not a tile node's subtree
+    if (d >= kSubtreeDepth - 1) {  // below the subtree depth: not a tile node's subtree
       deep = true;
       continue;
     }
     if (d == 0) {
       an0 = cur;
       am0 = msk;
-    } else {
+    } else if (d == 1) {
       an1 = cur;
       am1 = msk;
+    } else {
+      an2 = cur;
+      am2 = msk;
     }
     const int hs = 1 << (T.L - lev - 1);
     gx += (q & 1) * hs;
@@ -327,7 +336,7 @@ __device__ __forceinline__ void subtree_warp(const Topo &T, const Field &Fd, con
       const int owpre = __shfl_sync(0xffffffffu, my0, ow);
       if (h < b1) {
         const int t = ow;
-        const int leaf = s_list[h - owpre][t];
+        const int leaf = s_first[t] + (int)s_list[h - owpre][t];
         const float3 rv = make_float3(s_ray[0][t], s_ray[1][t], s_ray[2][t]);
         const float3 ro = c.ortho ? rv : make_float3(c.o[0], c.o[1], c.o[2]);
         const float3 rd = c.ortho ? make_float3(c.v[0], c.v[1], c.v[2]) : rv;

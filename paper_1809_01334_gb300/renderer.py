@@ -180,7 +180,7 @@ class Renderer:
         the fastest (ocr_autotune)."""
         return capi.autotune(self.h, reps)
 
-    def set_tuning(self, tile_depth: int = 3, streams: int = 4, shell_warps: int = 0,
+    def set_tuning(self, tile_depth: int = 4, streams: int = 4, shell_warps: int = 0,
                    merge: int = 1, persistent: int = 1, chunks_per_item: int = 16,
                    ctas_per_sm: int = 0):
         capi.set_tuning(self.h, tile_depth, streams, shell_warps, merge, persistent,

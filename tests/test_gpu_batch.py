@@ -75,7 +75,7 @@ def test_batch_in_a_cuda_graph(merge):
 
 
 @pytest.mark.parametrize("merge", [0, 1])
-@pytest.mark.parametrize("depth", [1, 2, 3])
+@pytest.mark.parametrize("depth", [1, 2, 3, 4])
 def test_every_tile_depth_matches_the_oracle(depth, merge):
     """The autotuner's tile depths (octree levels merged inside one CTA) and
     both merges of the levels above (per-level passes, one top-down pass) all
@@ -170,7 +170,7 @@ def test_persistent_kernel_equals_the_stream_path(chunks, ctas):
     cams = _cams() + [I.perspective_camera(35, 23, 31), I.perspective_camera(36, 70, 5)]
     r = Renderer(f, tf, INTEG)
     r.set_cameras(cams)
-    for depth in (1, 2, 3):
+    for depth in (1, 2, 3, 4):
         r.set_tuning(tile_depth=depth, streams=2, persistent=0, merge=0)
         ref, _, sref = r.render_batch(with_index=True)
         ref = ref.clone()
