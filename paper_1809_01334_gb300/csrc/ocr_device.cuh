@@ -445,6 +445,28 @@ __device__ float4 integrate_segment(const Fld &cu, const TF &tf, float dx, const
 // ----------------------------------------------------------------- culling --
 __device__ __forceinline__ int4 empty_rect() { return make_int4(0, -1, 0, -1); }
 
+// The order of a rectangle's (node, ray) slots: the rectangle is cut into
+// bands of 4 rows and a band's slots go column by column, 4 to a column (the
+// last band's height to a column), so that 32 consecutive slots cover an 8 x 4
+// block of pixels, whose rays are closer to one another than a row's.
+// slot_pixel: the pixel of the local-th slot; slot_of_pixel: the inverse.
+__device__ __forceinline__ void slot_pixel(int4 r, unsigned local, int &i, int &j) {
+  const unsigned w = (unsigned)(r.y - r.x + 1), h = (unsigned)(r.w - r.z + 1);
+  const unsigned band = local / (4u * w);  // 4 w h < 2^32 for rectangles of the image
+  const unsigned rem = local - band * 4u * w;
+  const unsigned hb = min(4u, h - 4u * band);
+  const unsigned col = hb == 4u ? rem >> 2 : rem / hb;
+  i = r.x + (int)col;
+  j = r.z + (int)(4u * band + rem - col * hb);
+}
+
+__device__ __forceinline__ long long slot_of_pixel(int4 r, int i, int j) {
+  const unsigned w = (unsigned)(r.y - r.x + 1), h = (unsigned)(r.w - r.z + 1);
+  const unsigned dj = (unsigned)(j - r.z), band = dj >> 2;
+  const unsigned hb = min(4u, h - 4u * band);
+  return (long long)(4u * w) * band + (long long)(i - r.x) * hb + (dj & 3u);
+}
+
 // Pixel rectangle of the camera-space bounding box of the cube [lo, lo+h]^3:
 // the box is mapped by X = (t, u, v/n)^T (x - o) (an affine map, so its AABB is
 // centre +- half-extent), clipped to the visible depth range, and projected.

@@ -212,9 +212,8 @@ __global__ void __launch_bounds__(128)
     }
     const int leaf = CL.ids[k];
     const int4 r = S.rect[leaf];
-    const unsigned local = (unsigned)(slot - CL.off[k]);  // < w * h < 2^31
-    const unsigned rw = (unsigned)(r.y - r.x + 1), row = local / rw;
-    const int i = r.x + (int)(local - row * rw), j = r.z + (int)row;
+    int i, j;
+    slot_pixel(r, (unsigned)(slot - CL.off[k]), i, j);  // < w * h < 2^31
     float3 org, dir;
     pixel_ray(c, i, j, org, dir);
     const float3 inv = make_float3(recip_or_zero(dir.x), recip_or_zero(dir.y), recip_or_zero(dir.z));
@@ -318,7 +317,7 @@ __global__ void __launch_bounds__(kTopDownThreads)
       const int4 r = __ldg(S.rect + id);
       const long long o = leaf ? __ldg(CL.off + __ldg(CL.index + id)) : __ldg(S.off + id - T.N);
       if (i < r.x || i > r.y || j < r.z || j > r.w) continue;
-      const long long e = o + (long long)(j - r.z) * (r.y - r.x + 1) + (i - r.x);
+      const long long e = o + slot_of_pixel(r, i, j);
       acc = seg_combine(acc, leaf ? CL.val[e] : S.entries[e]);
       continue;
     }

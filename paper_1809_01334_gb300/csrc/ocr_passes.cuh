@@ -74,11 +74,7 @@ __device__ __forceinline__ void slot_lookup(const Topo &T, const Scratch &S, int
     r = S.rect[T.N + node];
     geo = __ldg(T.geo + T.N + node);
   }
-  const unsigned local = (unsigned)(slot - o0);  // < w * h < 2^31
-  const unsigned rw = (unsigned)(r.y - r.x + 1);
-  const unsigned row = local / rw;
-  i = r.x + (int)(local - row * rw);
-  j = r.z + (int)row;
+  slot_pixel(r, (unsigned)(slot - o0), i, j);  // < w * h < 2^31
 }
 
 // Subtree pass (Sec. 3.2 + Sec. 3.3 for the deepest levels).  A warp owns 32
@@ -517,7 +513,7 @@ __device__ __forceinline__ void coarsen_chunk(const Topo &T, const Field &Fd, co
         const int4 r = ldp<COH>(S.rect + id);
         const long long o = ldp<COH>(S.off + id - T.N);
         if (i >= r.x && i <= r.y && j >= r.z && j <= r.w)
-          e[q] = o + (long long)(j - r.z) * (r.y - r.x + 1) + (i - r.x);
+          e[q] = o + slot_of_pixel(r, i, j);
       }
     }
     float4 cs[8];
