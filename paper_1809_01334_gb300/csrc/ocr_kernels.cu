@@ -273,9 +273,13 @@ __global__ void __launch_bounds__(kTopDownThreads)
   extern __shared__ int2 s_stk[];  // [(lt + 1) * kTopDownThreads] ancestors: node, children left
   const int tid = threadIdx.x;
   const float scale = ldexpf(1.f, -T.L);
-  const long long pix = (long long)blockIdx.x * kTopDownThreads + tid;
-  if (pix >= npix) return;
-  const int i = (int)(pix % c.w), j = (int)(pix / c.w);
+  // a CTA takes a 16 x 8 tile of pixels (rays closer together than a row's)
+  const int tiles_x = (c.w + 15) / 16;
+  const int i = (int)(blockIdx.x % tiles_x) * 16 + (tid & 15);
+  const int j = (int)(blockIdx.x / tiles_x) * 8 + (tid >> 4);
+  if (i >= c.w || j >= c.h) return;
+  const long long pix = (long long)j * c.w + i;
+  (void)npix;
   float3 org, dir;
   pixel_ray(c, i, j, org, dir);
   const float3 inv = make_float3(recip_or_zero(dir.x), recip_or_zero(dir.y), recip_or_zero(dir.z));
@@ -448,8 +452,9 @@ cudaError_t launch_topdown(const Topo &T, const Cam &C, const Integ &I, Scratch 
                            const CoarseLeaves &CL, long long npix, float4 *rgba,
                            cudaStream_t stream) {
   if (npix <= 0) return cudaSuccess;
-  const long long need = (npix + kTopDownThreads - 1) / kTopDownThreads;
-  if (need > 0x7fffffffll) return cudaErrorInvalidValue;
+  static_assert(kTopDownThreads == 128, "16 x 8 pixel tiles");
+  const long long need = (long long)((C.w + 15) / 16) * ((C.h + 7) / 8);
+  if (need > 0x7fffffffll || (long long)C.w * C.h != npix) return cudaErrorInvalidValue;
   const size_t stk = sizeof(int2) * kTopDownThreads * (size_t)(T.lt + 1);  // the walk's ancestors
   topdown_kernel<<<(unsigned)need, kTopDownThreads, stk, stream>>>(T, C, I, S, CL, npix, rgba);
   return cudaGetLastError();
