@@ -244,20 +244,29 @@ __device__ __forceinline__ void subtree_warp(const Topo &T, const Field &Fd, con
   unsigned am0 = 0, am1 = 0, am2 = 0;
   unsigned nhit = 0, nvisit = active ? 1u : 0u;
   bool deep = false;
+  // each round of the outer loop visits one internal node per lane: the inner
+  // loop takes the leaves up to the lane's next internal child, going back up
+  // through the nodes it finishes, so that the lanes' visits line up
   while (true) {
     int q = 0, id = -1;
-    while (msk) {
-      q = (__ffs(msk) - 1) ^ (int)flip;
-      msk &= msk - 1u;
-      id = pick_child(c0, c1, q);
-      if (id >= T.N) break;
-      if (id >= 0) {
-        if (nhit < (unsigned)kMaxSubtreeHits) s_list[nhit][tid] = (unsigned short)(id - first);
-        ++nhit;
+    bool done = false;
+    while (true) {
+      while (msk) {
+        q = (__ffs(msk) - 1) ^ (int)flip;
+        msk &= msk - 1u;
+        id = pick_child(c0, c1, q);
+        if (id >= T.N) break;
+        if (id >= 0) {
+          if (nhit < (unsigned)kMaxSubtreeHits) s_list[nhit][tid] = (unsigned short)(id - first);
+          ++nhit;
+        }
       }
-    }
-    if (id < T.N) {  // this node is done: back to its parent
-      if (d == 0) break;
+      if (id >= T.N) break;  // the next internal child to visit
+      if (d == 0) {          // the walk is over
+        done = true;
+        break;
+      }
+      // this node is done: back to its parent
       --d;
       --lev;
       const int keep = ~((1 << (T.L - lev)) - 1);
@@ -266,12 +275,13 @@ __device__ __forceinline__ void subtree_warp(const Topo &T, const Field &Fd, con
       gz &= keep;
       cur = d == 0 ? an0 : d == 1 ? an1 : an2;
       msk = d == 0 ? am0 : d == 1 ? am1 : am2;
+      id = -1;
       if (msk) {
         c0 = __ldg(child4 + 2 * cur);
         c1 = __ldg(child4 + 2 * cur + 1);
       }
-      continue;
     }
+    if (done) break;
     if (d >= kSubtreeDepth - 1) {  // below the subtree depth: not a tile node's subtree
       deep = true;
       continue;
