@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(kPairThreads)
           make_float3(recip_or_zero(dir.x), recip_or_zero(dir.y), recip_or_zero(dir.z));
       const int4 gl = T.geo[leaf];
       float a0, a1;
-      hit = slab(org, dir, inv, node_lo(gl, ldexpf(1.f, -T.L)), ldexpf(1.f, -gl.w), c.amin,
+      hit = slab(org, dir, inv, node_lo(gl, exp2i(-T.L)), exp2i(-gl.w), c.amin,
                  c.amax, a0, a1);
     }
   }
@@ -549,7 +549,7 @@ __device__ void segment_steps_bwd(SA &S, const TF &tf, float dx, const Integ &I,
   const float4 one = seg_identity();
   if constexpr (METHOD != 1) {  // the closed forms inside Algorithm 1 (c_RK test alone)
     for (;;) {
-      const float dtau = ldexpf(1.f, -depth);
+      const float dtau = exp2i(-depth);
       const float t0 = (float)idx * dtau;
       const float H = dx * dtau;
       // the forward step (value, split test) exactly as integrate_segment
@@ -611,7 +611,7 @@ __device__ void segment_steps_bwd(SA &S, const TF &tf, float dx, const Integ &I,
     return;
   }
   for (;;) {
-    const float dtau = ldexpf(1.f, -depth);
+    const float dtau = exp2i(-depth);
     const float t0 = (float)idx * dtau;
     const float H = dx * dtau;
     // the forward step (value, split test) exactly as integrate_segment
@@ -678,10 +678,10 @@ __device__ void segment_bwd(const Topo &T, const Field &Fd, const Cam &c, const 
                             float scale, float Tn, float4 G, float Aseg, float4 Ib, float ab,
                             float *g8, TfGrad &tg) {
   const int4 g = __ldg(T.geo + leaf);
-  const float ih = ldexpf(1.f, g.w);
+  const float ih = exp2i(g.w);
   const float3 lo = node_lo(g, scale);
   float a_in, a_out;
-  slab(org, dir, inv, lo, ldexpf(1.f, -g.w), c.amin, c.amax, a_in, a_out);
+  slab(org, dir, inv, lo, exp2i(-g.w), c.amin, c.amax, a_in, a_out);
   SegAdj S;
   S.uf = make_float3((fmaf(a_out, dir.x, org.x) - lo.x) * ih,
                      (fmaf(a_out, dir.y, org.y) - lo.y) * ih,
@@ -820,7 +820,7 @@ __global__ void __launch_bounds__(kSegThreads)
   load_tf(Fd, s_tfv, s_tfs);
   __syncthreads();
   const TF tf{s_tfv, s_tfs, Fd.s_min, Fd.inv_ds7};
-  const float scale = ldexpf(1.f, -T.L);
+  const float scale = exp2i(-T.L);
   const long long npix = (long long)c.w * c.h;
   int steps = 0;
   for (long long e = (long long)blockIdx.x * kSegThreads + threadIdx.x; e < nseg;
@@ -1020,7 +1020,7 @@ __global__ void __launch_bounds__(kSegThreads, 4)
   TfGrad tg;
   tg.col = s_gt + tid;
   tg.stride = kSegThreads;
-  const float scale = ldexpf(1.f, -T.L);
+  const float scale = exp2i(-T.L);
   const long long npix = (long long)c.w * c.h;
   long long b, end;
   seg_range(nseg, b, end);

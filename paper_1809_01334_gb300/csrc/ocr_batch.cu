@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(kBT, MINB)
       if (tid == 0) s_cur_cam = g.cam;
     }
     const Scratch &S = s_S;
-    const float scale = ldexpf(1.f, -T.L);
+    const float scale = exp2i(-T.L);
     for (long long it = tk * g.per; it < min((tk + 1) * g.per, g.nitems); ++it) {
       if (g.kind == kBatchCull) {
         unsigned nvis = 0;
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kBT, MINB)
           bool vis = false;
           if (k < T.N) {
             const int4 gg = __ldg(T.geo + k);
-            const int4 r = box_rect(s_cam, node_lo(gg, scale), ldexpf(1.f, -gg.w));
+            const int4 r = box_rect(s_cam, node_lo(gg, scale), exp2i(-gg.w));
             S.rect[k] = r;
             vis = r.x <= r.y;
             if (visible && vis) visible[k] = 1;

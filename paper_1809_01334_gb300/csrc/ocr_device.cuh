@@ -98,6 +98,10 @@ __device__ __forceinline__ void warp_sort_list(const unsigned long long *__restr
   __syncwarp();
 }
 
+// 2^e for an integer e in [-126, 127]: the biased exponent written directly
+// (exact, like ldexpf(1, e), without its range handling).
+__device__ __forceinline__ float exp2i(int e) { return __int_as_float((e + 127) << 23); }
+
 __device__ __forceinline__ float4 seg_identity() { return make_float4(1.f, 0.f, 0.f, 0.f); }
 
 // Eq. 2.14: (A2, B2) (+) (A1, B1) = (A2 A1, B2 + A2 B1), n = nearer, f = farther.
@@ -273,7 +277,7 @@ __device__ __forceinline__ void dopri_eval(const Fld &cu, const TF &tf, float dx
                                            unsigned idx, float4 kq0, float4 &Y5, float4 &kq6,
                                            float &err, float &hkmax) {
   const float4 one = seg_identity();
-  const float dtau = ldexpf(1.f, -depth);
+  const float dtau = exp2i(-depth);
   const float t0 = (float)idx * dtau;
   const float H = dx * dtau;
   const float4 kq2 = medium(cu, tf, fmaf(dp::c2, dtau, t0));
@@ -365,7 +369,7 @@ __device__ float4 integrate_segment(const Fld &cu, const TF &tf, float dx, const
   const float4 one = seg_identity();
   if (I.method != 1) {  // Gauss-2 (Eqs. 2.32-2.33), Simpson (Eq. 2.34) or Eq. 2.18, Algorithm 1
     for (;;) {
-      const float dtau = ldexpf(1.f, -depth);
+      const float dtau = exp2i(-depth);
       const float t0 = (float)idx * dtau;
       const float H = dx * dtau;
       float4 S, kq1 = kq0;
@@ -594,25 +598,34 @@ __device__ float4 iso_split_segment(const Cubic &cu, const float *__restrict__ n
                      acc);
 }
 
-// The segment of one leaf along one ray: slab interval, reference coordinates
-// of its far end and their change to the near end, field cubic, integration.
+// The set-up of one leaf's segment along one ray: slab interval, reference
+// coordinates of its far end (ufar) and their change to the near end (du),
+// world length dx, the field's cubic along the segment.
+__device__ __forceinline__ Cubic leaf_setup(const Topo &T, const Field &Fd, const Cam &c,
+                                            int leaf, float3 org, float3 dir, float3 inv,
+                                            float scale, float3 &ufar, float3 &du, float &dx) {
+  const int4 g = __ldg(T.geo + leaf);
+  const float ih = exp2i(g.w);  // 1 / edge length
+  const float3 lo = node_lo(g, scale);
+  float a_in, a_out;
+  slab(org, dir, inv, lo, exp2i(-g.w), c.amin, c.amax, a_in, a_out);
+  ufar = make_float3((fmaf(a_out, dir.x, org.x) - lo.x) * ih,
+                     (fmaf(a_out, dir.y, org.y) - lo.y) * ih,
+                     (fmaf(a_out, dir.z, org.z) - lo.z) * ih);
+  const float da = a_in - a_out;
+  du = make_float3(da * dir.x * ih, da * dir.y * ih, da * dir.z * ih);
+  dx = fmaxf(a_out - a_in, 0.f) * sqrtf(dir.x * dir.x + dir.y * dir.y + dir.z * dir.z);
+  return field_cubic(Fd.nodal + 8 * (size_t)leaf, ufar, du);
+}
+
+// The segment of one leaf along one ray: its set-up, then the integration.
 template <bool SURF = false>
 __device__ __forceinline__ float4 leaf_segment(const Topo &T, const Field &Fd, const Cam &c,
                                                const Integ &I, const TF &tf, int leaf, float3 org,
                                                float3 dir, float3 inv, float scale, int &steps) {
-  const int4 g = __ldg(T.geo + leaf);
-  const float ih = ldexpf(1.f, g.w);  // 1 / edge length
-  const float3 lo = node_lo(g, scale);
-  float a_in, a_out;
-  slab(org, dir, inv, lo, ldexpf(1.f, -g.w), c.amin, c.amax, a_in, a_out);
-  const float3 ufar = make_float3((fmaf(a_out, dir.x, org.x) - lo.x) * ih,
-                                  (fmaf(a_out, dir.y, org.y) - lo.y) * ih,
-                                  (fmaf(a_out, dir.z, org.z) - lo.z) * ih);
-  const float da = a_in - a_out;
-  const float3 du = make_float3(da * dir.x * ih, da * dir.y * ih, da * dir.z * ih);
-  const float dx =
-      fmaxf(a_out - a_in, 0.f) * sqrtf(dir.x * dir.x + dir.y * dir.y + dir.z * dir.z);
-  const Cubic cu = field_cubic(Fd.nodal + 8 * (size_t)leaf, ufar, du);
+  float3 ufar, du;
+  float dx;
+  const Cubic cu = leaf_setup(T, Fd, c, leaf, org, dir, inv, scale, ufar, du, dx);
   if (SURF)
     return iso_split_segment(cu, Fd.nodal + 8 * (size_t)leaf, ufar, du, dir, tf, dx, I, steps);
   return integrate_segment(cu, tf, dx, I, steps);

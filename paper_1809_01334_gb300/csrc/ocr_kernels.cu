@@ -24,7 +24,7 @@ namespace ocr {
 namespace {
 
 __global__ void cull_leaves_kernel(Topo T, Cam c, Scratch S) {
-  const float scale = ldexpf(1.f, -T.L);
+  const float scale = exp2i(-T.L);
   unsigned nvis = 0;
   // the loop bound is warp-uniform so that the ballot below sees full warps
   const int stride = gridDim.x * blockDim.x;
@@ -33,7 +33,7 @@ __global__ void cull_leaves_kernel(Topo T, Cam c, Scratch S) {
     bool vis = false;
     if (k < T.N) {
       const int4 g = T.geo[k];
-      const int4 r = box_rect(c, node_lo(g, scale), ldexpf(1.f, -g.w));
+      const int4 r = box_rect(c, node_lo(g, scale), exp2i(-g.w));
       S.rect[k] = r;
       vis = r.x <= r.y;
       if (S.visible && vis) S.visible[k] = 1;  // zeroed by the host; OR over cameras
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(128)
   }
   __syncthreads();
   const TF tf{s_tfv, s_tfs, Fd.s_min, Fd.inv_ds7};
-  const float scale = ldexpf(1.f, -T.L);
+  const float scale = exp2i(-T.L);
   const long long slot = (long long)blockIdx.x * 128 + tid;
   unsigned hit = 0;
   int steps = 0;
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(128)
     const int4 g = __ldg(T.geo + leaf);
     float a0, a1;
     float4 v = seg_identity();
-    if (slab(org, dir, inv, node_lo(g, scale), ldexpf(1.f, -g.w), c.amin, c.amax, a0, a1)) {
+    if (slab(org, dir, inv, node_lo(g, scale), exp2i(-g.w), c.amin, c.amax, a0, a1)) {
       v = leaf_segment<SURF>(T, Fd, c, I, tf, leaf, org, dir, inv, scale, steps);
       hit = 1;
       if (S.counts) atomicAdd(S.counts + (size_t)j * c.w + i, 1);
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kTopDownThreads)
                    float4 *rgba) {
   extern __shared__ int2 s_stk[];  // [(lt + 1) * kTopDownThreads] ancestors: node, children left
   const int tid = threadIdx.x;
-  const float scale = ldexpf(1.f, -T.L);
+  const float scale = exp2i(-T.L);
   // a CTA takes a 16 x 8 tile of pixels (rays closer together than a row's)
   const int tiles_x = (c.w + 15) / 16;
   const int i = (int)(blockIdx.x % tiles_x) * 16 + (tid & 15);
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(kTopDownThreads)
   if (c0.x >= 0) {
     const int4 g = __ldg(T.geo + c0.x);
     float a0, a1;
-    if (slab(org, dir, inv, node_lo(g, scale), ldexpf(1.f, -g.w), c.amin, c.amax, a0, a1))
+    if (slab(org, dir, inv, node_lo(g, scale), exp2i(-g.w), c.amin, c.amax, a0, a1))
       msk = 1u << flip;  // octant 0, mirrored
   }
   while (true) {
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(kTopDownThreads)
     ++lev;
     cur = id - T.N;
     msk = child_hits(org, dir, inv, node_lo(make_int4(gx, gy, gz, 0), scale),
-                     ldexpf(1.f, -(lev + 1)), c.amin, c.amax, flip);
+                     exp2i(-(lev + 1)), c.amin, c.amax, flip);
     if (msk) {
       c0 = __ldg(child4 + 2 * cur);
       c1 = __ldg(child4 + 2 * cur + 1);
@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(kNoAllocThreads)
   __syncthreads();
   const int tile = s_tile;
   const int base = tile * kNoAllocTile + tid * kNoAllocItems;
-  const float scale = ldexpf(1.f, -L);
+  const float scale = exp2i(-L);
   bool vis[kNoAllocItems];
   int cnt = 0;
 #pragma unroll
@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(kNoAllocThreads)
         if (rects) rects[k] = empty_rect();
         continue;
       }
-      const int4 r = box_rect(c, node_lo(g, scale), ldexpf(1.f, -g.w));
+      const int4 r = box_rect(c, node_lo(g, scale), exp2i(-g.w));
       if (rects) rects[k] = r;
       vis[q] = r.x <= r.y;
       cnt += vis[q];

@@ -175,63 +175,23 @@ __device__ __forceinline__ unsigned child_hits(float3 o, float3 d, float3 iv, fl
   return m;
 }
 
-// The 32 slots [ws, ws + 32) of the pass over the slots [s0, s1) of the
-// nodes [nb, ne), ws a multiple of 32; one warp, its own shared memory.
-template <bool SURF, bool COH>
-__device__ __forceinline__ void subtree_warp(const Topo &T, const Field &Fd, const Cam &c,
-                                             const Integ &I, const Scratch &S, int nb, int ne,
-                                             long long s0, long long s1, long long ws,
-                                             SubtreeSmem &sm) {
-  float4(&s_tfv)[8] = sm.tfv;
-  float4(&s_tfs)[8] = sm.tfs;
-  float(&s_ray)[6][32] = sm.ray;
-  unsigned short(&s_list)[kMaxSubtreeHits][32] = sm.list;
-  int(&s_first)[32] = sm.first;
-  float4(&s_res)[kWarpBatch] = sm.res;
-  int2(&s_pix)[32] = sm.pix;
-  int(&s_drop)[32] = sm.drop;
-  const int tid = threadIdx.x & 31, lane = tid;
-  if (tid < 8) {
-    const float4 v = Fd.tf[tid];
-    const float4 w = Fd.tf[tid < 7 ? tid + 1 : 7];
-    s_tfv[tid] = v;
-    s_tfs[tid] = make_float4(w.x - v.x, w.y - v.y, w.z - v.z, w.w - v.w);
-  }
-
-  // slot -> node, pixel, ray; rays that miss the node's box skip all leaves
-  const long long slot = ws + tid;
-  const bool active = slot >= s0 && slot < s1;
-  int node = -1, i = 0, j = 0;
-  int4 gn = make_int4(0, 0, 0, 0);
-  if (active) slot_lookup(T, S, nb, ne, slot, node, i, j, gn);
-  float3 org, dir;
-  pixel_ray(c, i, j, org, dir);
-  const float3 inv = make_float3(recip_or_zero(dir.x), recip_or_zero(dir.y), recip_or_zero(dir.z));
-  const float scale = ldexpf(1.f, -T.L);
-  // the part of the ray that varies over the pixels (the origin of an
-  // orthographic camera, the direction of a perspective one) and the
-  // reciprocal direction, taken once per ray
-  s_ray[0][tid] = c.ortho ? org.x : dir.x;
-  s_ray[1][tid] = c.ortho ? org.y : dir.y;
-  s_ray[2][tid] = c.ortho ? org.z : dir.z;
-  s_ray[3][tid] = inv.x;
-  s_ray[4][tid] = inv.y;
-  s_ray[5][tid] = inv.z;
-  s_pix[tid] = make_int2(i, j);
-  s_drop[tid] = 0;
-  const int first = active ? __ldg(T.leaves + node).x : 0;  // the tile node's first leaf
-  s_first[tid] = first;
-
-  __syncwarp();  // the transfer function table
-
-  // A. front-to-back descent; the path's ancestors (node, children still to
-  // visit) in registers, the current anchor cleared to an ancestor's on the
-  // way up, the current node's children loaded once per visit; the leaves
-  // up to the next internal child are taken in one run
+// Phase A of the subtree pass for one ray: the descent of its tile node's
+// subtree (node, box gn) front to back, the leaves met appended to list (16-bit
+// offsets from the tile node's first leaf, entry k at list[k * stride], at
+// most kMaxSubtreeHits kept; nhit counts them all).  The path's ancestors
+// (node, children still to visit) are kept in registers, the current anchor is
+// cleared to an ancestor's on the way up and the current node's children are
+// loaded once per visit; the leaves up to the next internal child are taken in
+// one run.  deep: an internal node below the subtree depth was met.
+__device__ __forceinline__ void subtree_walk(const Topo &T, const Cam &c, bool active, int node,
+                                             int4 gn, float3 org, float3 dir, float3 inv,
+                                             float scale, int first, unsigned short *list,
+                                             int stride, unsigned &nhit, unsigned &nvisit,
+                                             bool &deep) {
   const unsigned flip = (dir.x < 0.f ? 1u : 0u) | (dir.y < 0.f ? 2u : 0u) | (dir.z < 0.f ? 4u : 0u);
   // (a ray that misses the tile node meets none of its children)
   int cur = node, lev = gn.w, gx = gn.x, gy = gn.y, gz = gn.z, d = 0;
-  unsigned msk = active ? child_hits(org, dir, inv, node_lo(gn, scale), ldexpf(1.f, -(lev + 1)),
+  unsigned msk = active ? child_hits(org, dir, inv, node_lo(gn, scale), exp2i(-(lev + 1)),
                                      c.amin, c.amax, flip)
                         : 0u;
   const int4 *child4 = reinterpret_cast<const int4 *>(T.child);
@@ -242,8 +202,9 @@ __device__ __forceinline__ void subtree_warp(const Topo &T, const Field &Fd, con
   }
   int an0 = 0, an1 = 0, an2 = 0;
   unsigned am0 = 0, am1 = 0, am2 = 0;
-  unsigned nhit = 0, nvisit = active ? 1u : 0u;
-  bool deep = false;
+  nhit = 0;
+  nvisit = active ? 1u : 0u;
+  deep = false;
   // each round of the outer loop visits one internal node per lane: the inner
   // loop takes the leaves up to the lane's next internal child, going back up
   // through the nodes it finishes, so that the lanes' visits line up
@@ -257,7 +218,7 @@ __device__ __forceinline__ void subtree_warp(const Topo &T, const Field &Fd, con
         id = pick_child(c0, c1, q);
         if (id >= T.N) break;
         if (id >= 0) {
-          if (nhit < (unsigned)kMaxSubtreeHits) s_list[nhit][tid] = (unsigned short)(id - first);
+          if (nhit < (unsigned)kMaxSubtreeHits) list[nhit * stride] = (unsigned short)(id - first);
           ++nhit;
         }
       }
@@ -304,13 +265,69 @@ __device__ __forceinline__ void subtree_warp(const Topo &T, const Field &Fd, con
     ++lev;
     cur = id - T.N;
     msk = child_hits(org, dir, inv, node_lo(make_int4(gx, gy, gz, 0), scale),
-                     ldexpf(1.f, -(lev + 1)), c.amin, c.amax, flip);
+                     exp2i(-(lev + 1)), c.amin, c.amax, flip);
     ++nvisit;
     if (msk) {
       c0 = __ldg(child4 + 2 * cur);
       c1 = __ldg(child4 + 2 * cur + 1);
     }
   }
+}
+
+// The 32 slots [ws, ws + 32) of the pass over the slots [s0, s1) of the
+// nodes [nb, ne), ws a multiple of 32; one warp, its own shared memory.
+template <bool SURF, bool COH>
+__device__ __forceinline__ void subtree_warp(const Topo &T, const Field &Fd, const Cam &c,
+                                             const Integ &I, const Scratch &S, int nb, int ne,
+                                             long long s0, long long s1, long long ws,
+                                             SubtreeSmem &sm) {
+  float4(&s_tfv)[8] = sm.tfv;
+  float4(&s_tfs)[8] = sm.tfs;
+  float(&s_ray)[6][32] = sm.ray;
+  unsigned short(&s_list)[kMaxSubtreeHits][32] = sm.list;
+  int(&s_first)[32] = sm.first;
+  float4(&s_res)[kWarpBatch] = sm.res;
+  int2(&s_pix)[32] = sm.pix;
+  int(&s_drop)[32] = sm.drop;
+  const int tid = threadIdx.x & 31, lane = tid;
+  if (tid < 8) {
+    const float4 v = Fd.tf[tid];
+    const float4 w = Fd.tf[tid < 7 ? tid + 1 : 7];
+    s_tfv[tid] = v;
+    s_tfs[tid] = make_float4(w.x - v.x, w.y - v.y, w.z - v.z, w.w - v.w);
+  }
+
+  // slot -> node, pixel, ray; rays that miss the node's box skip all leaves
+  const long long slot = ws + tid;
+  const bool active = slot >= s0 && slot < s1;
+  int node = -1, i = 0, j = 0;
+  int4 gn = make_int4(0, 0, 0, 0);
+  if (active) slot_lookup(T, S, nb, ne, slot, node, i, j, gn);
+  float3 org, dir;
+  pixel_ray(c, i, j, org, dir);
+  const float3 inv = make_float3(recip_or_zero(dir.x), recip_or_zero(dir.y), recip_or_zero(dir.z));
+  const float scale = exp2i(-T.L);
+  // the part of the ray that varies over the pixels (the origin of an
+  // orthographic camera, the direction of a perspective one) and the
+  // reciprocal direction, taken once per ray
+  s_ray[0][tid] = c.ortho ? org.x : dir.x;
+  s_ray[1][tid] = c.ortho ? org.y : dir.y;
+  s_ray[2][tid] = c.ortho ? org.z : dir.z;
+  s_ray[3][tid] = inv.x;
+  s_ray[4][tid] = inv.y;
+  s_ray[5][tid] = inv.z;
+  s_pix[tid] = make_int2(i, j);
+  s_drop[tid] = 0;
+  const int first = active ? __ldg(T.leaves + node).x : 0;  // the tile node's first leaf
+  s_first[tid] = first;
+
+  __syncwarp();  // the transfer function table
+
+  // A. the ray's front-to-back descent of its tile node's subtree
+  unsigned nhit, nvisit;
+  bool deep;
+  subtree_walk(T, c, active, node, gn, org, dir, inv, scale, first, &s_list[0][tid], 32, nhit,
+               nvisit, deep);
   __syncwarp();  // the warp's rays and lists
 
 
@@ -447,7 +464,7 @@ __device__ __forceinline__ void coarsen_chunk(const Topo &T, const Field &Fd, co
   float3 org, dir;
   pixel_ray(c, i, j, org, dir);
   const float3 inv = make_float3(recip_or_zero(dir.x), recip_or_zero(dir.y), recip_or_zero(dir.z));
-  const float scale = ldexpf(1.f, -T.L);
+  const float scale = exp2i(-T.L);
 
   // the children the ray meets (by octant), from the node's shared face
   // crossings: a ray that misses the node meets none of them, and a child it
@@ -459,11 +476,11 @@ __device__ __forceinline__ void coarsen_chunk(const Topo &T, const Field &Fd, co
       if (ch[0] >= 0) {
         const int4 gr = __ldg(T.geo + ch[0]);
         float a0, a1;
-        if (slab(org, dir, inv, node_lo(gr, scale), ldexpf(1.f, -gr.w), c.amin, c.amax, a0, a1))
+        if (slab(org, dir, inv, node_lo(gr, scale), exp2i(-gr.w), c.amin, c.amax, a0, a1))
           msk = 1u;
       }
     } else {
-      msk = child_hits(org, dir, inv, node_lo(g, scale), ldexpf(1.f, -(g.w + 1)), c.amin,
+      msk = child_hits(org, dir, inv, node_lo(g, scale), exp2i(-(g.w + 1)), c.amin,
                        c.amax, 0u);
     }
   }
