@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(kTopDownThreads)
     ++lev;
     cur = id - T.N;
     msk = child_hits(org, dir, inv, node_lo(make_int4(gx, gy, gz, 0), scale),
-                     exp2i(-(lev + 1)), c.amin, c.amax, flip);
+                     exp2i(-(lev + 1)), c.amin, c.amax);
     if (msk) {
       c0 = __ldg(child4 + 2 * cur);
       c1 = __ldg(child4 + 2 * cur + 1);

@@ -120,16 +120,19 @@ __device__ __forceinline__ int pick_child(int4 c0, int4 c1, int q) {
 
 // The children of the node with low corner lo whose boxes (side hc) the ray
 // meets, as a mask over the mirrored octants (bit q ^ flip for octant
-// q = bx + 2 by + 4 bz).  Anchors are integers below 2^20 in units of 2^-L
-// (L <= 20), so every face is exact in FP32: per axis the faces lo,
-// lo + hc, lo + 2 hc are the very values a slab test of each child forms
-// (its low corner, and low corner + side rounded once), their crossings
-// (face - o) x (1/d) are formed once, and each child's interval is the same
-// max / min chain over the axes x, y, z as its own slab test (the chains
-// share their common prefixes).
+// q = bx + 2 by + 4 bz, flip the direction's sign bits).  Anchors are integers
+// below 2^20 in units of 2^-L (L <= 20), so every face is exact in FP32: per
+// axis the faces lo, lo + hc, lo + 2 hc are the very values a slab test of
+// each child forms (its low corner, and low corner + side rounded once), and
+// their crossings (face - o) x (1/d) are formed once.  Rounding is monotone, so
+// the crossings are ordered like the faces along the ray: the half the ray
+// enters first spans (first face, mid face), the other (mid face, last face),
+// which are the min / max a slab test takes, and taking the halves in that
+// order gives the mirrored bits directly.  Each child's interval is the same
+// max / min chain over the axes x, y, z as its own slab test (the chains share
+// their common prefixes).
 __device__ __forceinline__ unsigned child_hits(float3 o, float3 d, float3 iv, float3 lo,
-                                               float hc, float amin, float amax,
-                                               unsigned flip) {
+                                               float hc, float amin, float amax) {
   const float oa[3] = {o.x, o.y, o.z}, da[3] = {d.x, d.y, d.z}, va[3] = {iv.x, iv.y, iv.z};
   const float la[3] = {lo.x, lo.y, lo.z};
   constexpr unsigned kHalf[3][2] = {{0x55u, 0xaau}, {0x33u, 0xccu}, {0x0fu, 0xf0u}};
@@ -138,19 +141,20 @@ __device__ __forceinline__ unsigned child_hits(float3 o, float3 d, float3 iv, fl
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const float p0 = la[a], p1 = __fadd_rn(p0, hc), p2 = __fadd_rn(p1, hc);
-    if (da[a] == 0.f) {  // parallel: inside a half's slab or not, no bound on alpha
+    if (da[a] == 0.f) {  // parallel (no mirroring): inside a half's slab or not, no bound on alpha
       if (oa[a] < p0 || oa[a] > p1) ok &= ~kHalf[a][0];
       if (oa[a] < p1 || oa[a] > p2) ok &= ~kHalf[a][1];
       mn[a][0] = mn[a][1] = -INFINITY;
       mx[a][0] = mx[a][1] = INFINITY;
     } else {
-      const float s0 = __fmul_rn(__fsub_rn(p0, oa[a]), va[a]);
+      const bool neg = da[a] < 0.f;
+      const float s0 = __fmul_rn(__fsub_rn(neg ? p2 : p0, oa[a]), va[a]);
       const float s1 = __fmul_rn(__fsub_rn(p1, oa[a]), va[a]);
-      const float s2 = __fmul_rn(__fsub_rn(p2, oa[a]), va[a]);
-      mn[a][0] = fminf(s0, s1);
-      mx[a][0] = fmaxf(s0, s1);
-      mn[a][1] = fminf(s1, s2);
-      mx[a][1] = fmaxf(s1, s2);
+      const float s2 = __fmul_rn(__fsub_rn(neg ? p0 : p2, oa[a]), va[a]);
+      mn[a][0] = s0;
+      mx[a][0] = s1;
+      mn[a][1] = s1;
+      mx[a][1] = s2;
     }
   }
   float e0[4], e1[4];  // the chains after x and y, per (bx, by)
@@ -167,8 +171,12 @@ __device__ __forceinline__ unsigned child_hits(float3 o, float3 d, float3 iv, fl
 #pragma unroll
   for (int q = 0; q < 8; ++q)
     m |= (fminf(e1[q & 3], mx[2][q >> 2]) > fmaxf(e0[q & 3], mn[2][q >> 2]) ? 1u : 0u) << q;
-  m &= ok;
-  // octant q -> bit q ^ flip
+  return m & ok;
+}
+
+// A child mask in octant order from one in mirrored order, or back: bit
+// q ^ flip <-> bit q.
+__device__ __forceinline__ unsigned mirror_bits(unsigned m, unsigned flip) {
   if (flip & 1u) m = ((m & 0x55u) << 1) | ((m >> 1) & 0x55u);
   if (flip & 2u) m = ((m & 0x33u) << 2) | ((m >> 2) & 0x33u);
   if (flip & 4u) m = ((m & 0x0fu) << 4) | ((m >> 4) & 0x0fu);
@@ -192,7 +200,7 @@ __device__ __forceinline__ void subtree_walk(const Topo &T, const Cam &c, bool a
   // (a ray that misses the tile node meets none of its children)
   int cur = node, lev = gn.w, gx = gn.x, gy = gn.y, gz = gn.z, d = 0;
   unsigned msk = active ? child_hits(org, dir, inv, node_lo(gn, scale), exp2i(-(lev + 1)),
-                                     c.amin, c.amax, flip)
+                                     c.amin, c.amax)
                         : 0u;
   const int4 *child4 = reinterpret_cast<const int4 *>(T.child);
   int4 c0 = make_int4(-1, -1, -1, -1), c1 = c0;
@@ -265,7 +273,7 @@ __device__ __forceinline__ void subtree_walk(const Topo &T, const Cam &c, bool a
     ++lev;
     cur = id - T.N;
     msk = child_hits(org, dir, inv, node_lo(make_int4(gx, gy, gz, 0), scale),
-                     exp2i(-(lev + 1)), c.amin, c.amax, flip);
+                     exp2i(-(lev + 1)), c.amin, c.amax);
     ++nvisit;
     if (msk) {
       c0 = __ldg(child4 + 2 * cur);
@@ -480,8 +488,11 @@ __device__ __forceinline__ void coarsen_chunk(const Topo &T, const Field &Fd, co
           msk = 1u;
       }
     } else {
-      msk = child_hits(org, dir, inv, node_lo(g, scale), exp2i(-(g.w + 1)), c.amin,
-                       c.amax, 0u);
+      const unsigned flip =
+          (dir.x < 0.f ? 1u : 0u) | (dir.y < 0.f ? 2u : 0u) | (dir.z < 0.f ? 4u : 0u);
+      msk = mirror_bits(child_hits(org, dir, inv, node_lo(g, scale), exp2i(-(g.w + 1)), c.amin,
+                                   c.amax),
+                        flip);
     }
   }
   __syncthreads();
