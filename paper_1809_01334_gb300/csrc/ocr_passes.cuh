@@ -97,7 +97,6 @@ __device__ __forceinline__ void slot_lookup(const Topo &T, const Scratch &S, int
 //     rounding edge case: the pair is no candidate) gives no segment, and
 //  C. every lane folds its own ray's results nearest-first with Eq. 2.14.
 constexpr int kWarpBatch = 32;  // hits per warp batch of phase B
-static_assert(kSubtreeDepth <= 4, "the descent keeps three ancestors in registers");
 
 // Shared memory of one subtree warp.
 struct SubtreeSmem {
@@ -107,6 +106,7 @@ struct SubtreeSmem {
   int2 pix[32];                      // pixel of each ray
   int drop[32];                      // hits outside the leaf's rectangle
   int first[32];                     // first leaf of each ray's tile node
+  int2 stk[kSubtreeDepth - 1][32];   // the descent's ancestors: node, children left
   unsigned short list[kMaxSubtreeHits][32];  // hits of each ray in order: leaf - first
 };
 // a tile node's subtree holds at most 8^kSubtreeDepth leaves
@@ -187,15 +187,16 @@ __device__ __forceinline__ unsigned mirror_bits(unsigned m, unsigned flip) {
 // subtree (node, box gn) front to back, the leaves met appended to list (16-bit
 // offsets from the tile node's first leaf, entry k at list[k * stride], at
 // most kMaxSubtreeHits kept; nhit counts them all).  The path's ancestors
-// (node, children still to visit) are kept in registers, the current anchor is
-// cleared to an ancestor's on the way up and the current node's children are
-// loaded once per visit; the leaves up to the next internal child are taken in
-// one run.  deep: an internal node below the subtree depth was met.
+// (node, children still to visit) are kept at stk[d * stride], the current
+// anchor is cleared to an ancestor's on the way up and the current node's
+// children are loaded once per visit; the leaves up to the next internal child
+// are taken in one run.  deep: an internal node below the subtree depth was
+// met.
 __device__ __forceinline__ void subtree_walk(const Topo &T, const Cam &c, bool active, int node,
                                              int4 gn, float3 org, float3 dir, float3 inv,
                                              float scale, int first, unsigned short *list,
-                                             int stride, unsigned &nhit, unsigned &nvisit,
-                                             bool &deep) {
+                                             int2 *stk, int stride, unsigned &nhit,
+                                             unsigned &nvisit, bool &deep) {
   const unsigned flip = (dir.x < 0.f ? 1u : 0u) | (dir.y < 0.f ? 2u : 0u) | (dir.z < 0.f ? 4u : 0u);
   // (a ray that misses the tile node meets none of its children)
   int cur = node, lev = gn.w, gx = gn.x, gy = gn.y, gz = gn.z, d = 0;
@@ -208,8 +209,6 @@ __device__ __forceinline__ void subtree_walk(const Topo &T, const Cam &c, bool a
     c0 = __ldg(child4 + 2 * cur);
     c1 = __ldg(child4 + 2 * cur + 1);
   }
-  int an0 = 0, an1 = 0, an2 = 0;
-  unsigned am0 = 0, am1 = 0, am2 = 0;
   nhit = 0;
   nvisit = active ? 1u : 0u;
   deep = false;
@@ -242,8 +241,9 @@ __device__ __forceinline__ void subtree_walk(const Topo &T, const Cam &c, bool a
       gx &= keep;
       gy &= keep;
       gz &= keep;
-      cur = d == 0 ? an0 : d == 1 ? an1 : an2;
-      msk = d == 0 ? am0 : d == 1 ? am1 : am2;
+      const int2 e = stk[d * stride];
+      cur = e.x;
+      msk = (unsigned)e.y;
       id = -1;
       if (msk) {
         c0 = __ldg(child4 + 2 * cur);
@@ -255,16 +255,7 @@ __device__ __forceinline__ void subtree_walk(const Topo &T, const Cam &c, bool a
       deep = true;
       continue;
     }
-    if (d == 0) {
-      an0 = cur;
-      am0 = msk;
-    } else if (d == 1) {
-      an1 = cur;
-      am1 = msk;
-    } else {
-      an2 = cur;
-      am2 = msk;
-    }
+    stk[d * stride] = make_int2(cur, (int)msk);
     const int hs = 1 << (T.L - lev - 1);
     gx += (q & 1) * hs;
     gy += ((q >> 1) & 1) * hs;
@@ -334,8 +325,8 @@ __device__ __forceinline__ void subtree_warp(const Topo &T, const Field &Fd, con
   // A. the ray's front-to-back descent of its tile node's subtree
   unsigned nhit, nvisit;
   bool deep;
-  subtree_walk(T, c, active, node, gn, org, dir, inv, scale, first, &s_list[0][tid], 32, nhit,
-               nvisit, deep);
+  subtree_walk(T, c, active, node, gn, org, dir, inv, scale, first, &s_list[0][tid],
+               &sm.stk[0][tid], 32, nhit, nvisit, deep);
   __syncwarp();  // the warp's rays and lists
 
 
