@@ -33,6 +33,7 @@ struct CamPlan {
   long long *d_gslots = nullptr;      // [L + 1]
   int *d_chunk = nullptr;             // [total / kGroup + 2]
   float4 *d_entries = nullptr;        // [total slots]
+  unsigned *d_ticket = nullptr;       // [1] the subtree pass's group counter
   // cube, top-down merge: the slots of the leaves at or above the tile level
   long long ctotal = 0;               // their slots (rectangle areas)
   long long *d_coff = nullptr;        // [nc + 1] exclusive prefix of their areas
@@ -199,8 +200,9 @@ int dev_alloc(T **p, size_t n, int64_t &bytes) {
 void free_plan_buffers(ocr_forest *F, CamPlan &P) {
   void *bufs[] = {P.d_rect, P.d_off, P.d_bsums, P.d_gslots, P.d_chunk, P.d_entries, P.d_leaf_off,
                   P.d_sbsums, P.d_pchunk, P.d_rcount, P.d_rcursor, P.d_ray_off,
-                  P.d_keys, P.d_coff, P.d_cbsums, P.d_cgroup, P.d_cval};
+                  P.d_keys, P.d_coff, P.d_cbsums, P.d_cgroup, P.d_cval, P.d_ticket};
   for (void *b : bufs) cudaFree(b);
+  P.d_ticket = nullptr;
   P.d_coff = nullptr;
   P.d_cbsums = nullptr;
   P.d_cgroup = nullptr;
@@ -887,6 +889,7 @@ int plan_cameras(ocr_forest *F) {
     const long long total = P.gslots[G - 1];
     if ((rc = dev_alloc(&P.d_chunk, (size_t)(total / kGroup + 2), F->bytes)) ||
         (rc = dev_alloc(&P.d_entries, (size_t)(total > 0 ? total : 1), F->bytes)) ||
+        (rc = dev_alloc(&P.d_ticket, 1, F->bytes)) ||
         (rc = dev_alloc(&P.d_cgroup, (size_t)(P.ctotal / kGroup + 2), F->bytes)) ||
         (rc = dev_alloc(&P.d_cval, (size_t)(P.ctotal > 0 ? P.ctotal : 1), F->bytes)))
       return rc;
@@ -998,7 +1001,7 @@ int enqueue_camera(ocr_forest *F, CamPlan &P, float4 *rgba, int *counts, unsigne
   Field Fd{F->d_nodal, reinterpret_cast<const float4 *>(F->d_tf), F->s_min,
            7.f / (F->s_max - F->s_min)};
   Scratch S{P.d_rect, P.d_off, P.d_entries, F->d_stats, counts,
-            visible, P.d_chunk, count ? F->d_stats : nullptr};
+            visible, P.d_chunk, count ? F->d_stats : nullptr, P.d_ticket};
   OCR_CUDA(launch_cull_leaves(T, P.cam, S, st));
   ++launches;
   for (int l = F->L - 1; l >= 0; --l) {
@@ -1030,6 +1033,7 @@ int enqueue_camera(ocr_forest *F, CamPlan &P, float4 *rgba, int *counts, unsigne
     if (b <= a) continue;
     if (F->merge == 1 && level != F->lt) continue;
     if (level == F->lt) {
+      if (P.d_ticket) OCR_CUDA(cudaMemsetAsync(P.d_ticket, 0, sizeof(unsigned), st));
       if (timed) OCR_CUDA(cudaEventRecord(F->ev[2], st));
       OCR_CUDA(launch_subtree(T, Fd, P.cam, F->integ, S, F->h_group_nodes[g],
                               F->h_group_nodes[g + 1], a, b, st));

@@ -71,6 +71,7 @@ struct Scratch {
   unsigned char *visible;    // optional [N]
   int *chunk_node;           // [ceil(total / kGroup) + 1] internal node holding slot g * kGroup
   unsigned long long *counters;  // optional [kStats]: the passes' work counters, when asked for
+  unsigned *ticket;          // optional, zeroed: the subtree pass's warps draw their groups here
 };
 
 // Device counters: [0, 4) subtree pass, [kStatCoarse, kStatCoarse + 4) coarse
@@ -116,6 +117,7 @@ cudaError_t launch_area_scan(const Topo &T, Scratch S, long long *d_block_sums, 
                              cudaStream_t stream);
 int area_scan_blocks(int M);
 cudaError_t launch_chunk_map(const Topo &T, Scratch S, long long total, cudaStream_t stream);
+// S.ticket is required and must be zero (stream-ordered) before the launch.
 cudaError_t launch_subtree(const Topo &T, const Field &Fd, const Cam &C, const Integ &I, Scratch S,
                            int node_begin, int node_end, long long slot_begin, long long slot_end,
                            cudaStream_t stream);

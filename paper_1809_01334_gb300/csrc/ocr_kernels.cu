@@ -18,6 +18,7 @@
 #include "ocr_device.cuh"
 #include "ocr_passes.cuh"
 
+#include <algorithm>
 #include <cstdio>
 
 namespace ocr {
@@ -161,13 +162,23 @@ __global__ void gather_level_slots_kernel(const long long *off, const int *level
 }
 
 // ------------------------------------------------- subtree and coarsen --
-// One CTA per chunk; the bodies are in ocr_passes.cuh.
+// The bodies are in ocr_passes.cuh.  The subtree pass: resident one-warp
+// CTAs, 32 per SM, that draw the groups of 32 slots in turn from a counter
+// (a warp that is done takes the next group at once, with no block launch per
+// group).
 template <bool SURF>
 __global__ void __launch_bounds__(32, 32)
-    subtree_kernel(Topo T, Field Fd, Cam c, Integ I, Scratch S, int nb, int ne, long long s0,
-                   long long s1) {
+    subtree_kernel(Topo T, Field Fd, Cam c, Integ I, Scratch S, int nb, int ne,
+                          long long s0, long long s1, unsigned ngroups) {
   __shared__ SubtreeSmem sm;
-  subtree_warp<SURF, false>(T, Fd, c, I, S, nb, ne, s0, s1, (s0 / 32 + blockIdx.x) * 32, sm);
+  while (true) {
+    unsigned t = 0;
+    if (threadIdx.x == 0) t = atomicAdd(S.ticket, 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= ngroups) break;
+    subtree_warp<SURF, false>(T, Fd, c, I, S, nb, ne, s0, s1, (s0 / 32 + t) * 32, sm);
+    __syncwarp();
+  }
 }
 
 template <bool FINAL, bool SURF>
@@ -398,11 +409,19 @@ cudaError_t launch_subtree(const Topo &T, const Field &Fd, const Cam &C, const I
                            cudaStream_t stream) {
   if (s1 <= s0) return cudaSuccess;
   const long long nblk = (s1 - 1) / 32 - s0 / 32 + 1;  // one warp per 32 slots
-  if (nblk > 0x7fffffffll) return cudaErrorInvalidValue;
+  if (nblk > 0x7fffffffll || !S.ticket) return cudaErrorInvalidValue;
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+  const unsigned g = (unsigned)std::min<long long>(nblk, 32ll * nsm);
   if (I.surface)  // isosurface segments (Sec. 2.8): a separate instantiation
-    subtree_kernel<true><<<(unsigned)nblk, 32, 0, stream>>>(T, Fd, C, I, S, nb, ne, s0, s1);
+    subtree_kernel<true><<<g, 32, 0, stream>>>(T, Fd, C, I, S, nb, ne, s0, s1, (unsigned)nblk);
   else
-    subtree_kernel<false><<<(unsigned)nblk, 32, 0, stream>>>(T, Fd, C, I, S, nb, ne, s0, s1);
+    subtree_kernel<false><<<g, 32, 0, stream>>>(T, Fd, C, I, S, nb, ne, s0, s1, (unsigned)nblk);
   return cudaGetLastError();
 }
 

@@ -79,8 +79,9 @@ __device__ __forceinline__ void slot_lookup(const Topo &T, const Scratch &S, int
 
 // Subtree pass (Sec. 3.2 + Sec. 3.3 for the deepest levels).  A warp owns 32
 // consecutive (tile-level node, ray) slots, one lane each, and works alone
-// (no CTA barrier): the standalone kernel runs one-warp CTAs, so that a warp
-// that is done frees its place at once.
+// (no CTA barrier): the standalone kernel runs resident one-warp CTAs that
+// draw their groups of 32 slots from a counter, so that a warp that is done
+// takes the next group at once.
 //  A. every ray descends its tile node's subtree front to back: at each
 //     internal node its box is cut by the three mid-planes, and the ray's
 //     crossings of the node's planes give the slab interval of all 8 children
