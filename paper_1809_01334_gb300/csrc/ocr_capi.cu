@@ -33,7 +33,8 @@ struct CamPlan {
   long long *d_gslots = nullptr;      // [L + 1]
   int *d_chunk = nullptr;             // [total / kGroup + 2]
   float4 *d_entries = nullptr;        // [total slots]
-  unsigned *d_ticket = nullptr;       // [1] the subtree pass's group counter
+  unsigned *d_ticket = nullptr;       // [2] work counters: the subtree pass's (cube), the
+                                      // sort's and the per-ray kernel's (shell)
   // cube, top-down merge: the slots of the leaves at or above the tile level
   long long ctotal = 0;               // their slots (rectangle areas)
   long long *d_coff = nullptr;        // [nc + 1] exclusive prefix of their areas
@@ -476,7 +477,8 @@ int plan_shell(ocr_forest *F, CamPlan &P) {
       (rc = dev_alloc(&P.d_sbsums, (size_t)P.bs_cap, F->bytes)) ||
       (rc = dev_alloc(&P.d_rcount, (size_t)npix, F->bytes)) ||
       (rc = dev_alloc(&P.d_rcursor, (size_t)npix, F->bytes)) ||
-      (rc = dev_alloc(&P.d_ray_off, (size_t)npix + 1, F->bytes)))
+      (rc = dev_alloc(&P.d_ray_off, (size_t)npix + 1, F->bytes)) ||
+      (rc = dev_alloc(&P.d_ticket, 2, F->bytes)))
     return rc;
   long long *h = F->h_group_slots;
   OCR_CUDA(cudaMemsetAsync(F->d_stats, 0, kStats * sizeof(unsigned long long), ps));
@@ -541,10 +543,12 @@ int enqueue_shell(ocr_forest *F, CamPlan &P, float4 *rgba, int *counts, unsigned
   const int rc = enqueue_shell_lists(F, P, visible, st);
   if (rc) return rc;
   if (timed) OCR_CUDA(cudaEventRecord(F->ev[1], st));
-  OCR_CUDA(shell_sort_lists(P.d_ray_off, npix, P.d_keys, P.nhits, P.cap, F->nsm, st));
+  OCR_CUDA(cudaMemsetAsync(P.d_ticket, 0, 2 * sizeof(unsigned), st));
+  OCR_CUDA(shell_sort_lists(P.d_ray_off, npix, P.d_keys, P.nhits, P.cap, F->nsm, P.d_ticket, st));
   if (timed) OCR_CUDA(cudaEventRecord(F->ev[2], st));
   OCR_CUDA(shell_rays(F->d_geo, F->N, F->shell, Fd, P.cam, F->integ, P.d_ray_off, npix, P.d_keys,
-                      P.nhits, P.cap, rgba, counts, F->d_stats, F->nsm, F->shell_warps, st));
+                      P.nhits, P.cap, rgba, counts, F->d_stats, F->nsm, F->shell_warps,
+                      P.d_ticket + 1, st));
   if (timed) OCR_CUDA(cudaEventRecord(F->ev[3], st));
   // cull, 2 scans of 3 kernels (1 when empty), chunk map, 2 pair passes, sort, rays
   launches += 1 + (bwd_scan_blocks(F->N) > 0 ? 3 : 0) + 1 + (P.npairs > 0 ? 2 : 0) +
@@ -889,7 +893,7 @@ int plan_cameras(ocr_forest *F) {
     const long long total = P.gslots[G - 1];
     if ((rc = dev_alloc(&P.d_chunk, (size_t)(total / kGroup + 2), F->bytes)) ||
         (rc = dev_alloc(&P.d_entries, (size_t)(total > 0 ? total : 1), F->bytes)) ||
-        (rc = dev_alloc(&P.d_ticket, 1, F->bytes)) ||
+        (rc = dev_alloc(&P.d_ticket, 2, F->bytes)) ||
         (rc = dev_alloc(&P.d_cgroup, (size_t)(P.ctotal / kGroup + 2), F->bytes)) ||
         (rc = dev_alloc(&P.d_cval, (size_t)(P.ctotal > 0 ? P.ctotal : 1), F->bytes)))
       return rc;

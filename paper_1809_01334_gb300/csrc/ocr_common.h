@@ -285,14 +285,16 @@ cudaError_t shell_rays_prepare();
 // list of n segments (values, intervals in order of entry) into *out
 cudaError_t shell_fold_segments(const float4 *val, const float2 *iv, int n, float4 *out,
                                 cudaStream_t st);
-// every ray's list sorted in place by its key (before shell_rays)
+// every ray's list sorted in place by its key (before shell_rays); ticket: a
+// counter zeroed before the launch (the warps draw their rays there)
 cudaError_t shell_sort_lists(const long long *ray_off, long long npix, unsigned long long *keys,
-                             long long key_cap, int cap, int nsm, cudaStream_t st);
+                             long long key_cap, int cap, int nsm, unsigned *ticket,
+                             cudaStream_t st);
 cudaError_t shell_rays(const int4 *geo, int N, const Shell &S, const Field &Fd, const Cam &C,
                        const Integ &I, const long long *ray_off, long long npix,
                        const unsigned long long *keys, long long key_cap, int cap, float4 *rgba,
                        int *counts, unsigned long long *stats, int nsm, int want_warps,
-                       cudaStream_t st);
+                       unsigned *ticket, cudaStream_t st);
 
 // Shell adjoint, the cube's three passes with the shell's geometry and field
 // (values by bwd_shell_values, scans by bwd_ray_scans) over lists built by

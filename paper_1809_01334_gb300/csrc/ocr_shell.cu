@@ -334,17 +334,34 @@ __global__ void fold_segments_kernel(const float4 *val, const float2 *iv, int n,
   if (threadIdx.x == 0) *out = acc;
 }
 
+// The per-ray kernels' warps draw runs of kRayRun consecutive rays from a
+// counter (zeroed before the launch): a warp that is done takes the next run
+// at once, whatever the other warps' lists.  Returns false when none is left.
+constexpr int kRayRun = 8;
+__device__ __forceinline__ bool next_rays(unsigned *ticket, long long npix, int lane,
+                                          long long &pix, long long &pend) {
+  unsigned t = 0;
+  if (lane == 0) t = atomicAdd(ticket, 1u);
+  t = __shfl_sync(0xffffffffu, t, 0);
+  pix = (long long)t * kRayRun;
+  pend = pix + kRayRun < npix ? pix + kRayRun : npix;
+  return pix < npix;
+}
+
 // Sorts every ray's list in place by its key (entry depth, then tree and
 // Morton key through the leaf index): one warp per ray, in registers for lists
 // of up to 512 keys, else bitonic in shared memory (cap keys per warp).
 __global__ void __launch_bounds__(256)
     shell_sort_lists_kernel(const long long *__restrict__ ray_off, long long npix,
-                            unsigned long long *keys, long long key_cap, int cap) {
+                            unsigned long long *keys, long long key_cap, int cap,
+                            unsigned *ticket) {
   extern __shared__ __align__(16) unsigned char s_raw[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned long long *key = reinterpret_cast<unsigned long long *>(s_raw) + (size_t)wid * cap;
-  const long long nwarp = (long long)gridDim.x * nw;
-  for (long long pix = (long long)blockIdx.x * nw + wid; pix < npix; pix += nwarp) {
+  for (long long pix = 0, pend = 0;; ++pix) {
+    if (pix == pend) {  // the warp's next run of rays
+      if (!next_rays(ticket, npix, lane, pix, pend)) break;
+    }
     const long long h0 = ray_off[pix];
     const int n = (int)(ray_off[pix + 1] - h0);
     if (n < 2 || n > cap || h0 + n > key_cap) continue;  // the render counts the bad ones
@@ -386,7 +403,7 @@ __global__ void __launch_bounds__(256, 2)
                                   const long long *__restrict__ ray_off, long long npix,
                                   const unsigned long long *__restrict__ keys, long long key_cap,
                                   int cap, float4 *rgba, int *counts,
-                                  unsigned long long *stats) {
+                                  unsigned long long *stats, unsigned *ticket) {
   extern __shared__ __align__(16) unsigned char s_raw[];
   __shared__ float4 s_tfv[8], s_tfs[8];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
@@ -405,8 +422,10 @@ __global__ void __launch_bounds__(256, 2)
   float2 *iv = reinterpret_cast<float2 *>(key);  // the intervals replace the keys once sorted
   const float bg[3] = {I.bg[0], I.bg[1], I.bg[2]};
   int steps = 0, segs = 0, errs = 0;
-  const long long nwarp = (long long)gridDim.x * nw;
-  for (long long pix = (long long)blockIdx.x * nw + wid; pix < npix; pix += nwarp) {
+  for (long long pix = 0, pend = 0;; ++pix) {
+    if (pix == pend) {  // the warp's next run of rays
+      if (!next_rays(ticket, npix, lane, pix, pend)) break;
+    }
     const long long h0 = ray_off[pix];
     const int n = (int)(ray_off[pix + 1] - h0);
     if (counts && lane == 0) counts[pix] = n;
@@ -553,14 +572,27 @@ cudaError_t shell_rays_prepare() {
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most_sort);
 }
 
+// CTAs of a kernel resident on the whole GPU at once (at least one).
+template <class K>
+static long long resident_ctas(K kernel, int threads, size_t smem, int nsm) {
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess ||
+      per < 1)
+    per = 1;
+  return (long long)per * nsm;
+}
+
 cudaError_t shell_sort_lists(const long long *ray_off, long long npix, unsigned long long *keys,
-                             long long key_cap, int cap, int nsm, cudaStream_t st) {
-  if (cap < 32 || cap > kShellMaxCap || (cap & (cap - 1))) return cudaErrorInvalidValue;
+                             long long key_cap, int cap, int nsm, unsigned *ticket,
+                             cudaStream_t st) {
+  if (cap < 32 || cap > kShellMaxCap || (cap & (cap - 1)) || !ticket)
+    return cudaErrorInvalidValue;
   const int warps = sort_warps(cap);
-  const long long need = (npix + warps - 1) / warps;
-  const long long grid = need < (long long)nsm * 16 ? need : (long long)nsm * 16;
+  const long long need = (npix + (long long)warps * kRayRun - 1) / ((long long)warps * kRayRun);
+  const long long res = resident_ctas(shell_sort_lists_kernel, warps * 32, sort_smem(cap), nsm);
+  const long long grid = need < res ? need : res;
   shell_sort_lists_kernel<<<(unsigned)(grid > 0 ? grid : 1), warps * 32, sort_smem(cap), st>>>(
-      ray_off, npix, keys, key_cap, cap);
+      ray_off, npix, keys, key_cap, cap, ticket);
   return cudaGetLastError();
 }
 
@@ -568,19 +600,24 @@ cudaError_t shell_rays(const int4 *geo, int N, const Shell &S, const Field &Fd, 
                        const Integ &I, const long long *ray_off, long long npix,
                        const unsigned long long *keys, long long key_cap, int cap, float4 *rgba,
                        int *counts, unsigned long long *stats, int nsm, int want_warps,
-                       cudaStream_t st) {
-  if (cap < 32 || cap > kShellMaxCap || (cap & (cap - 1))) return cudaErrorInvalidValue;
+                       unsigned *ticket, cudaStream_t st) {
+  if (cap < 32 || cap > kShellMaxCap || (cap & (cap - 1)) || !ticket)
+    return cudaErrorInvalidValue;
   const size_t smem = shell_ray_smem(cap, want_warps);
   const int warps = shell_ray_warps(cap, want_warps);
-  const long long need = (npix + warps - 1) / warps;
-  const long long grid = need < (long long)nsm * 8 ? need : (long long)nsm * 8;
+  const long long need = (npix + (long long)warps * kRayRun - 1) / ((long long)warps * kRayRun);
+  const long long res = I.surface ? resident_ctas(shell_rays_kernel<true>, warps * 32, smem, nsm)
+                                  : resident_ctas(shell_rays_kernel<false>, warps * 32, smem, nsm);
+  const long long grid = need < res ? need : res;
   const unsigned g = (unsigned)(grid > 0 ? grid : 1);
   if (I.surface)  // the isosurface of Sec. 2.8: a separate instantiation
     shell_rays_kernel<true><<<g, warps * 32, smem, st>>>(geo, N, S, Fd, C, I, ray_off, npix, keys,
-                                                         key_cap, cap, rgba, counts, stats);
+                                                         key_cap, cap, rgba, counts, stats,
+                                                         ticket);
   else
     shell_rays_kernel<false><<<g, warps * 32, smem, st>>>(geo, N, S, Fd, C, I, ray_off, npix,
-                                                          keys, key_cap, cap, rgba, counts, stats);
+                                                          keys, key_cap, cap, rgba, counts, stats,
+                                                          ticket);
   return cudaGetLastError();
 }
 
