@@ -581,7 +581,9 @@ def main():
                          "nominal_peak": nominal / 1e12,
                          "nominal_source": f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                            f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({src})",
-                         "ms_merge": mm, "ms_prune": sum(prune_ms) / len(prune_ms)},
+                         "ms_merge": mm, "ms_prune": sum(prune_ms) / len(prune_ms),
+                         # the same operations over the whole render's step
+                         "render_frac": ops / (ms_max * 1e-3) / peak_ops},
             "clocks": clk.summary(),
         }
         if batch:
